@@ -1,0 +1,323 @@
+"""Throughput of the LES time step on GB300: Mcell-steps/s with every step's
+SOR solved to relative residual 1e-6 (so |div u| <= 1e-6 relative after each
+projection).
+
+Workload: the paper's default domain size (150 x 150 x 90, Sec. 2.7) with 100
+random cuboid buildings at 30% plan density, stretched dz 2->8 m, log-law
+inflow with 10% turbulence; all inputs synthetic and seeded (scene.py).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line (rank 0).  ``value`` times each step with CUDA events on
+the library's stream, the fields resident in HBM, L2 flushed (256 MiB write)
+before every timed step.  ``e2e`` times the same steps through the C ABI with
+pinned host buffers: les_set_fields (H2D) + les_step + les_get_fields (D2H).
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
+workload (see ``cpu_sample``).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1504_02264_gb300 import scene  # noqa: E402
+
+METRIC = "LES Mcell-steps/s to |div|<=1e-6 (150x150x90, 100 buildings)"
+UNIT = "Mcell-steps/s"
+SOR_BYTES_PER_CELL = 13.0       # per sweep: read p, rhs (4+4), flags (1), write p (4)
+L2_FLUSH_BYTES = 256 << 20
+# mean SOR sweeps per step of this workload after the default warm-up, from the
+# GPU arm (the FP64 path takes the same sweeps as the oracle); used only to scale
+# the bounded oracle sample to a full step when no GPU run is available
+REF_SWEEPS_PER_STEP = 400
+
+
+def workload(seed=0):
+    sc = scene.random_scene(seed=seed)          # 150 x 150 x 90, tol 1e-6
+    sc.check_every = 10
+    sc.max_sweeps = 20000
+    return sc
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# nvidia-smi clock sampling during the timed region
+
+class Clocks:
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle, bounded sample
+
+def oracle_sample(sc, sweeps_per_step, n_sample_sweeps=40, state=None):
+    """Time one oracle step phase by phase with a fixed SOR sample and scale the
+    SOR part to ``sweeps_per_step``.  Returns (seconds per full step, detail)."""
+    from oracle.oracle import Oracle, A_FU, A_FV, A_FW
+
+    o = Oracle(sc, fixed_sweeps=1, max_sweeps=n_sample_sweeps)
+    if state is not None:
+        o.set_fields(*state["fields"])
+        for a, arr in zip((A_FU, A_FV, A_FW), state["F"]):
+            o.set(a, arr)
+        o.step_index = state["step"]
+    t0 = time.perf_counter()
+    o.bc_fill()
+    o.les_nut()
+    o.momentum()
+    o.outflow_fix()
+    o.make_rhs()
+    t1 = time.perf_counter()
+    o.sor_sweeps(n_sample_sweeps)
+    t2 = time.perf_counter()
+    o.residual()
+    t3 = time.perf_counter()
+    o.gauge()
+    o.project()
+    t4 = time.perf_counter()
+    t_sweep = (t2 - t1) / n_sample_sweeps
+    checks = sweeps_per_step / max(sc.check_every, 1)
+    t_step = (t1 - t0) + (t4 - t3) + sweeps_per_step * t_sweep + checks * (t3 - t2)
+    return t_step, {"non_sor_s": (t1 - t0) + (t4 - t3), "sweep_s": t_sweep, "residual_s": t3 - t2,
+                    "sample_wall_s": t4 - t0}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    sc = workload()
+    n = sc.ncells
+    times = []
+    for s in range(args.warmup + args.steps):
+        t, det = oracle_sample(sc, REF_SWEEPS_PER_STEP, n_sample_sweeps=10)
+        if s >= args.warmup:
+            times.append(t)
+    t = float(np.mean(times))
+    val = n / t / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded scene.py)",
+            "config": {"workload": "random_150x150x90", "nx": 150, "ny": 150, "nz": 90,
+                       "buildings": 100, "tol": 1e-6, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"per step: one single-threaded FP64 oracle step of the "
+                                       f"150x150x90 workload from its initial state with 10 SOR "
+                                       f"sweeps, timed phase by phase, SOR part scaled to "
+                                       f"{REF_SWEEPS_PER_STEP} sweeps/step"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1504_02264_gb300 import les
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    # independent domain per rank (weak scaling: replicas, no data-path collective)
+    sc = workload(seed=rank)
+    n = sc.ncells
+    dom = les.Domain(sc, precision=les.LES_FP32)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    for _ in range(args.warmup):
+        st = dom.step(1)
+        if st["rc"] < 0:
+            raise RuntimeError(st)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    dom.set_timing(True)
+    l0 = dom.timing()["launches"]
+    clocks = Clocks(local) if rank == 0 else None
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sweeps = []
+    worst = 0.0
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        flush.zero_()
+        ev[s][0].record(stream)
+        st = dom.step(1)
+        ev[s][1].record(stream)
+        sweeps.append(st["sweeps"])
+        worst = max(worst, st["rel_residual"])
+        if st["rc"] != 0:
+            raise RuntimeError(f"step did not converge: {st}")
+    torch.cuda.synchronize()
+    tm = dom.timing()
+    clk = clocks.stop() if clocks else None
+    launches = tm["launches"] - l0
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    dom.set_timing(False)
+
+    # end to end through the C ABI with pinned host buffers
+    shapes = dom.shapes()
+    host = [torch.empty(s, dtype=torch.float32, pin_memory=True).numpy() for s in shapes]
+    dom_e2e = dom
+    fields0 = dom.fields()
+    for h, f in zip(host, fields0):
+        h[...] = f
+    e2e_steps = max(1, min(args.steps, 10))
+    h2d = sum(h.nbytes for h in host)
+    torch.cuda.synchronize()
+    ee = []
+    for s in range(e2e_steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        les.les_set_fields(dom_e2e.h, *host)
+        les.les_step(dom_e2e.h, 1, les.les_stats_t())
+        les.les_get_fields(dom_e2e.h, *host)
+        b.record(stream)
+        b.synchronize()
+        ee.append(a.elapsed_time(b))
+    e2e_ms = float(np.mean(ee))
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    if rank == 0:
+        peak, peak_kind = peaks()
+        sweep_ms = tm["ms_sor"] / max(tm["sor_sweeps"], 1)
+        launch_ms = tm["ms_sor"] / max(tm["sor_launches"], 1)
+        launches_per_sweep = tm["sor_launches"] / max(tm["sor_sweeps"], 1)
+        bytes_per_launch = SOR_BYTES_PER_CELL * n / launches_per_sweep
+        achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
+        mean_sweeps = float(np.mean(sweeps))
+        line = {
+            "metric": METRIC, "value": n * world / (ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 norms)",
+            "data": "synthetic (seeded scene.py: random city, log-law inflow, 10% turbulence)",
+            "config": {"workload": "random_150x150x90", "nx": 150, "ny": 150, "nz": 90, "buildings": 100,
+                       "tol": 1e-6, "check_every": sc.check_every, "mean_sweeps_per_step": mean_sweeps,
+                       "max_rel_residual": worst, "parallelism": f"replicas x{world}",
+                       "l2": "flushed (256 MiB write) before every timed step"},
+            "roofline": {"kernel": "k_sor_half (red-black SOR half-sweep)", "bound": "hbm",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind, "traffic": None,
+                         "bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms,
+                         "note": "150x150x90 SOR state (p, rhs, flags ~18 MB) is L2-resident"},
+            "phase_ms_per_step": {k: tm[k] / max(tm["steps"], 1) for k in
+                                  ("ms_momentum", "ms_sor", "ms_residual", "ms_project")},
+            "sor_ms_per_sweep": sweep_ms,
+            "gpu_launches": int(launches),
+            "e2e": {"value": n * world / (e2e_ms * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": h2d, "ms_per_step": e2e_ms, "steps": e2e_steps},
+            "clocks": clk,
+        }
+        if not args.no_cpu_baseline:
+            state = {"fields": [f.astype(np.float64) for f in dom.fields()],
+                     "F": [dom.aux(a).astype(np.float64) for a in (les.LES_AUX_FU, les.LES_AUX_FV, les.LES_AUX_FW)],
+                     "step": dom.step(0)["step"]}
+            t_step, det = oracle_sample(sc, mean_sweeps, n_sample_sweeps=40, state=state)
+            line["cpu_baseline"] = {
+                "value": n / t_step / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": (f"one single-threaded FP64 oracle step of the same 150x150x90 state with 40 "
+                           f"SOR sweeps, timed phase by phase (wall {det['sample_wall_s']:.1f} s), SOR "
+                           f"part scaled to the GPU run's {mean_sweeps:.0f} sweeps/step"),
+                "detail": det}
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,203 @@
+/*
+ * les.h -- C ABI of the GB300-native time step of the DPRI urban-flow LES
+ * (Vanderbauwhede, "Model Coupling between the Weather Research and
+ * Forecasting Model and the DPRI Large Eddy Simulator for Urban Flows on
+ * GPU-accelerated Multicore Systems", arXiv:1504.02264).
+ *
+ * One time step runs the paper's routines (Sec. 2.1 "LES Code Structure --
+ * Functional") on one GPU:
+ *   bondv1  boundary conditions: log-law inflow (standing in for the WRF
+ *           wind profile of Sec. 4), zero-gradient outflow with an FP64
+ *           mass-flux correction, free-slip / no-slip / periodic walls;
+ *   les     Smagorinsky eddy viscosity and the SGS stress divergence;
+ *   velfg   advection + diffusion "body force" (Sec. 2.5, printed u-formula);
+ *   adam    second-order Adams-Bashforth on the tendency;
+ *   feedbf  building forcing: zero velocity on faces touching a building;
+ *   press   Poisson equation for the pressure by red-black SOR (Sec. 2.6),
+ *           FP64 residual norms and stop test;
+ *   velnw   projection u = u* - dt grad p, so every step ends divergence-free
+ *           to the SOR tolerance.
+ *
+ * Conventions shared by every entry point
+ *  - Return value: LES_OK (0) on success; a negative LES_E* code on error
+ *    (the handle, when given, keeps a message for les_last_error); the
+ *    positive status LES_ENOCONV when SOR stopped at max_sweeps above the
+ *    tolerance (the step still completed and is usable).
+ *  - Host arrays are owned by the caller and only read/written during the
+ *    call.  Device memory is owned by the handle (allocated in les_create,
+ *    released in les_destroy).
+ *  - Grid: nx x ny x nz cells, i fastest.  Host array layout is C order
+ *    [k][j][i].  Staggered I/O shapes: u (nz, ny, nx+1) on x-faces
+ *    i = 0..nx; v (nz, ny+1, nx) on y-faces j = 0..ny; w (nz+1, ny, nx) on
+ *    z-faces k = 0..nz; cell arrays p, rhs, nu_t (nz, ny, nx).  On a periodic
+ *    axis face 0 and face n are the same face (equal values).
+ *  - Element type of field arrays: float when grid.precision == LES_FP32,
+ *    double when LES_FP64.  Norms, means and the mass flux are always FP64.
+ *  - Units: metres, seconds, m/s; p is the kinematic pressure (p / rho).
+ *  - A handle is not thread-safe; all its work is ordered on its stream.
+ */
+#ifndef LES_H
+#define LES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status / error codes */
+#define LES_OK 0
+#define LES_ENOCONV 1        /* SOR hit max_sweeps above tol (not fatal) */
+#define LES_EINVAL (-1)      /* bad argument or grid */
+#define LES_ENOMEM (-2)      /* device or host allocation failed */
+#define LES_ECUDA (-3)       /* a CUDA call failed (message in les_last_error) */
+#define LES_ETIMEOUT (-4)    /* a bounded device-side wait gave up */
+#define LES_ENONFINITE (-5)  /* an FP64 norm came out NaN or Inf */
+#define LES_ESTATE (-6)      /* checkpoint blob does not match this handle */
+
+/* boundary condition per axis */
+#define LES_BC_INOUT 0       /* x only: log-law inflow at x=0, outflow at x=L */
+#define LES_BC_FREESLIP 1    /* y only: free-slip side walls */
+#define LES_BC_WALL 2        /* z only: no-slip ground, free-slip lid */
+#define LES_BC_PERIODIC 3    /* any axis; n must be even (red-black colouring) */
+
+#define LES_FP32 0           /* FP32 fields and sweeps, FP64 norms */
+#define LES_FP64 1           /* FP64 everywhere (parity / debugging) */
+
+typedef struct les_s* les_handle;
+
+/* Grid and step parameters; copied by les_create (dz is read during the call). */
+typedef struct {
+    int32_t nx, ny, nz;          /* interior cells, each >= 2 */
+    int32_t bc_x, bc_y, bc_z;    /* LES_BC_* (x: INOUT|PERIODIC, y: FREESLIP|PERIODIC,
+                                    z: WALL|PERIODIC) */
+    double dx, dy;               /* uniform horizontal spacing (m) */
+    const double* dz;            /* [nz] cell heights (m), may be stretched */
+    double dt;                   /* time step (s) */
+    double cs;                   /* Smagorinsky constant */
+    double nu;                   /* molecular viscosity (m^2/s) */
+    double omega;                /* SOR over-relaxation factor, 0 < omega < 2 */
+    double tol;                  /* SOR stop: ||rhs - A p||_2 / ||rhs||_2 <= tol */
+    int32_t max_sweeps;          /* SOR sweep cap per solve (one red + one black) */
+    int32_t check_every;         /* residual test every this many sweeps */
+    int32_t fixed_sweeps;        /* 1: always exactly max_sweeps, no stop test */
+    int32_t precision;           /* LES_FP32 | LES_FP64 */
+    double turb;                 /* inflow turbulence intensity (0 = laminar) */
+    uint64_t seed;               /* counter-based inflow noise seed */
+} les_grid_t;
+
+/* Per-call statistics (values of the last step of the call). */
+typedef struct {
+    int32_t sweeps;              /* SOR sweeps in the last solve */
+    int32_t status;              /* LES_OK or LES_ENOCONV */
+    double rel_residual;         /* FP64 ||rhs - A p|| / ||rhs|| after the solve */
+    double rhs_norm;             /* FP64 ||rhs||_2 (mean removed) */
+    double rhs_mean;             /* FP64 dz-weighted fluid mean removed from rhs */
+    double mass_factor;          /* outflow scaling Q_in / Q_out (1 if periodic x) */
+    double q_in, q_out;          /* FP64 volume fluxes after the correction */
+    double p_mean;               /* FP64 dz-weighted mean removed from p (gauge) */
+    int64_t step;                /* step counter after the call */
+    int64_t launches;            /* kernels launched by the call */
+} les_stats_t;
+
+/*
+ * les_create: allocate device state for one domain and upload the obstacles.
+ *   grid      parameters (validated: sizes >= 2, even n on periodic axes,
+ *             dz > 0, 0 < omega < 2, max_sweeps >= 1, check_every >= 1).
+ *   solid     [nz][ny][nx] bytes, nonzero = building cell.
+ *   inflow_u  [nz] inflow speed at cell-centre heights (m/s), ignored on a
+ *             periodic x axis.
+ *   stream    cudaStream_t to order all work on (NULL = legacy default).
+ *   out       receives the handle.
+ * Initial state: all velocities, p and the Adams-Bashforth history zero,
+ * step counter 0.  Returns LES_EINVAL / LES_ENOMEM / LES_ECUDA on failure
+ * (no handle is returned then).
+ */
+int les_create(const les_grid_t* grid, const uint8_t* solid, const double* inflow_u,
+               void* stream, les_handle* out);
+
+/* les_destroy: free device memory; NULL is ignored. */
+void les_destroy(les_handle h);
+
+/* les_last_error: message of the last failing call on h (static string if h == NULL). */
+const char* les_last_error(les_handle h);
+
+/* les_set_fields: copy host u, v, w, p (I/O shapes above) into the state.
+ * Keeps the Adams-Bashforth history and the step counter.  Any pointer may
+ * be NULL to leave that field unchanged. */
+int les_set_fields(les_handle h, const void* u, const void* v, const void* w, const void* p);
+
+/* les_get_fields: copy the state into host buffers (NULL pointers skipped);
+ * synchronises the handle's stream. */
+int les_get_fields(les_handle h, void* u, void* v, void* w, void* p);
+
+/* les_set_inflow: replace the inflow profile [nz] (m/s), intensity and seed. */
+int les_set_inflow(les_handle h, const double* inflow_u, double turb, uint64_t seed);
+
+/*
+ * les_step: advance nsteps time steps (Sec. 2.1 routine sequence, velnw last).
+ * stats (nullable) receives the statistics of the last step; the call
+ * synchronises the stream when stats is non-NULL or the stop test needs the
+ * residual on the host.  Returns LES_ENOCONV if any step's SOR did not reach
+ * tol, LES_ENONFINITE if a norm is not finite.
+ */
+int les_step(les_handle h, int32_t nsteps, les_stats_t* stats);
+
+/*
+ * les_pressure_solve: the press routine alone (Sec. 2.6).  rhs (nullable,
+ * [nz][ny][nx], element type per precision) replaces the right-hand side
+ * (non-fluid entries ignored, dz-weighted fluid mean removed); NULL reuses
+ * the rhs of the last step.  Iterates red-black SOR from the current p
+ * under the grid's stop rule, then removes the dz-weighted fluid mean of p.
+ */
+int les_pressure_solve(les_handle h, const void* rhs, les_stats_t* stats);
+
+/* Intermediate arrays for inspection (copied to host, synchronising). */
+#define LES_AUX_NUT 0        /* nu_t (nz, ny, nx) of the last step */
+#define LES_AUX_RHS 1        /* Poisson rhs (nz, ny, nx), mean removed */
+#define LES_AUX_USTAR 2      /* u* (nz, ny, nx+1) of the last step */
+#define LES_AUX_VSTAR 3      /* v* (nz, ny+1, nx) */
+#define LES_AUX_WSTAR 4      /* w* (nz+1, ny, nx) */
+#define LES_AUX_FU 5         /* Adams-Bashforth history F_u (u shape) */
+#define LES_AUX_FV 6
+#define LES_AUX_FW 7
+int les_get_aux(les_handle h, int32_t which, void* out);
+
+/*
+ * Checkpoint / restart: the full state (velocities, p, AB2 history, step
+ * counter, inflow profile and noise seed) as an opaque blob.  les_get_state
+ * with buf == NULL stores the required size in *len; otherwise *len must be
+ * at least that size.  les_set_state accepts only a blob of a handle with the
+ * same grid (else LES_ESTATE).  A restored handle continues bit-identically.
+ */
+int les_get_state(les_handle h, void* buf, size_t* len);
+int les_set_state(les_handle h, const void* buf, size_t len);
+
+/*
+ * Phase timing with CUDA events recorded on the handle's stream (the
+ * per-routine breakdown the paper reports for its kernels, Sec. 2.7).
+ * les_set_timing(h, 1) zeroes and enables the accumulators; 0 disables.
+ * Enabled timing adds one stream synchronisation per step.
+ */
+typedef struct {
+    double ms_momentum;          /* bondv1 + les + velfg + adam + feedbf + rhs */
+    double ms_sor;               /* SOR sweep kernels only */
+    double ms_residual;          /* FP64 residual / stop-test kernels */
+    double ms_project;           /* velnw (projection + gauge) */
+    int64_t steps;               /* steps timed */
+    int64_t sor_sweeps;          /* SOR sweeps timed */
+    int64_t sor_launches;        /* SOR kernel launches timed */
+    int64_t launches;            /* all kernels launched by the handle so far */
+} les_timing_t;
+int les_set_timing(les_handle h, int32_t enable);
+int les_get_timing(les_handle h, les_timing_t* t);
+
+/* Library version string. */
+const char* les_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LES_H */

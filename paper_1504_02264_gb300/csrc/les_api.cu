@@ -1,0 +1,729 @@
+// Host side of the C ABI declared in include/les.h: handle, validation,
+// device allocation, host <-> device staging and the per-step launch order.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/les.h"
+#include "les_internal.cuh"
+
+using namespace les;
+
+namespace {
+
+const char* kVersion = "les-gb300 0.1 (sm_103a)";
+
+// packing kernels between the padded device layout and the dense I/O layout
+template <typename T>
+__global__ void k_pack(Dom d, const T* src, T* dst, int i0, int j0, int k0, int ni, int nj, int nk) {
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long n = (long long)ni * nj * nk;
+    if (q >= n) return;
+    int i = (int)(q % ni);
+    long long r = q / ni;
+    int j = (int)(r % nj);
+    int k = (int)(r / nj);
+    dst[q] = src[d.at(i0 + i, j0 + j, k0 + k)];
+}
+template <typename T>
+__global__ void k_unpack(Dom d, const T* src, T* dst, int i0, int j0, int k0, int ni, int nj, int nk) {
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long n = (long long)ni * nj * nk;
+    if (q >= n) return;
+    int i = (int)(q % ni);
+    long long r = q / ni;
+    int j = (int)(r % nj);
+    int k = (int)(r / nj);
+    dst[d.at(i0 + i, j0 + j, k0 + k)] = src[q];
+}
+
+// open-face flags from the padded solid mask (ghost cells are fluid and are
+// never consulted across a non-periodic domain face)
+__global__ void k_flags(Dom d, const uint8_t* solid, uint8_t* flags) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    int k = blockIdx.z + 1;
+    if (i > d.nx || j > d.ny) return;
+    auto fl = [&](int a, int b, int c) -> bool {
+        if (d.perx) a = a < 1 ? a + d.nx : (a > d.nx ? a - d.nx : a);
+        if (d.pery) b = b < 1 ? b + d.ny : (b > d.ny ? b - d.ny : b);
+        if (d.perz) c = c < 1 ? c + d.nz : (c > d.nz ? c - d.nz : c);
+        if (a < 1 || a > d.nx || b < 1 || b > d.ny || c < 1 || c > d.nz) return false;
+        return solid[d.at(a, b, c)] == 0;
+    };
+    uint8_t f = 0;
+    if (fl(i, j, k)) {
+        f |= F_FLUID;
+        if (fl(i + 1, j, k)) f |= F_E;
+        if (fl(i - 1, j, k)) f |= F_W;
+        if (fl(i, j + 1, k)) f |= F_N;
+        if (fl(i, j - 1, k)) f |= F_S;
+        if (fl(i, j, k + 1)) f |= F_T;
+        if (fl(i, j, k - 1)) f |= F_B;
+        if (f & (F_E | F_W | F_N | F_S | F_T | F_B)) f |= F_UNK;
+    }
+    flags[d.at(i, j, k)] = f;
+}
+
+}  // namespace
+
+struct les_s {
+    les_grid_t g;
+    std::vector<double> dz;        // [nz]
+    std::vector<double> inflow;    // [nz+2] padded
+    Dom d;
+    int prec;
+    size_t es;                     // element size
+    size_t n;                      // elements per padded array
+    // device arrays (element type per precision)
+    void *u = nullptr, *v = nullptr, *w = nullptr, *us = nullptr, *vs = nullptr, *ws = nullptr;
+    void *fu = nullptr, *fv = nullptr, *fw = nullptr, *nut = nullptr, *rhs = nullptr, *tmp = nullptr;
+    void* p[2] = {nullptr, nullptr};
+    void* stage = nullptr;         // dense I/O staging
+    size_t stage_elems = 0;
+    uint8_t* flags = nullptr;
+    void *kdz = nullptr, *kdzs = nullptr, *kcT = nullptr, *kcB = nullptr, *kdel = nullptr;
+    double* dz64 = nullptr;
+    double* inflow64 = nullptr;
+    double* partials = nullptr;
+    unsigned* counter = nullptr;
+    Scalars* sc = nullptr;
+    Scalars* sc_host = nullptr;    // pinned
+    cudaStream_t stream = nullptr;
+    int cur = 0;
+    long long step = 0;
+    double vfluid = 0.0;
+    long long launches = 0;
+    std::vector<void*> allocs;
+    // phase timing
+    bool timing = false;
+    cudaEvent_t ev[8] = {};
+    les_timing_t tm = {};
+    char err[512] = {0};
+};
+
+namespace {
+
+char g_static_err[512] = "";
+
+int fail(les_s* h, int code, const char* fmt, ...) {
+    char* buf = h ? h->err : g_static_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(h, LES_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+    } while (0)
+
+int dalloc(les_s* h, void** p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return fail(h, LES_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    h->allocs.push_back(*p);
+    e = cudaMemsetAsync(*p, 0, bytes, h->stream);
+    if (e != cudaSuccess) return fail(h, LES_ECUDA, "cudaMemset failed: %s", cudaGetErrorString(e));
+    return LES_OK;
+}
+
+// staggering: 0 cell, 1 x-face, 2 y-face, 3 z-face
+void io_box(const les_s* h, int stag, int& i0, int& j0, int& k0, int& ni, int& nj, int& nk) {
+    ni = h->g.nx + (stag == 1);
+    nj = h->g.ny + (stag == 2);
+    nk = h->g.nz + (stag == 3);
+    i0 = stag == 1 ? 0 : 1;
+    j0 = stag == 2 ? 0 : 1;
+    k0 = stag == 3 ? 0 : 1;
+}
+
+size_t io_elems(const les_s* h, int stag) {
+    int i0, j0, k0, ni, nj, nk;
+    io_box(h, stag, i0, j0, k0, ni, nj, nk);
+    return (size_t)ni * nj * nk;
+}
+
+template <typename T>
+int upload(les_s* h, void* dev, int stag, const void* host, size_t stage_off) {
+    int i0, j0, k0, ni, nj, nk;
+    io_box(h, stag, i0, j0, k0, ni, nj, nk);
+    size_t n = (size_t)ni * nj * nk;
+    T* st = (T*)h->stage + stage_off;
+    CK(cudaMemcpyAsync(st, host, n * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+    k_unpack<T><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->d, st, (T*)dev, i0, j0, k0, ni, nj, nk);
+    h->launches++;
+    CK(cudaGetLastError());
+    return LES_OK;
+}
+
+template <typename T>
+int download(les_s* h, const void* dev, int stag, void* host, size_t stage_off) {
+    int i0, j0, k0, ni, nj, nk;
+    io_box(h, stag, i0, j0, k0, ni, nj, nk);
+    size_t n = (size_t)ni * nj * nk;
+    T* st = (T*)h->stage + stage_off;
+    k_pack<T><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->d, (const T*)dev, st, i0, j0, k0, ni, nj, nk);
+    h->launches++;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(host, st, n * sizeof(T), cudaMemcpyDeviceToHost, h->stream));
+    return LES_OK;
+}
+
+template <typename T>
+Geo<T> geo(les_s* h) {
+    Geo<T> g;
+    g.d = h->d;
+    g.dx = (T)h->g.dx;
+    g.dy = (T)h->g.dy;
+    g.rdx = (T)(1.0 / h->g.dx);
+    g.rdy = (T)(1.0 / h->g.dy);
+    g.dt = (T)h->g.dt;
+    g.nu = (T)h->g.nu;
+    g.omega = (T)h->g.omega;
+    g.cx = (T)(1.0 / (h->g.dx * h->g.dx));
+    g.cy = (T)(1.0 / (h->g.dy * h->g.dy));
+    g.dz = (const T*)h->kdz;
+    g.dzs = (const T*)h->kdzs;
+    g.cT = (const T*)h->kcT;
+    g.cB = (const T*)h->kcB;
+    g.delta2 = (const T*)h->kdel;
+    g.dz64 = h->dz64;
+    g.flags = h->flags;
+    return g;
+}
+
+Reduce reducer(les_s* h) { return Reduce{h->partials, h->counter, h->sc}; }
+
+template <typename T>
+int upload_table(les_s* h, void* dev, const std::vector<double>& v) {
+    std::vector<T> t(v.begin(), v.end());
+    CK(cudaMemcpyAsync(dev, t.data(), t.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LES_OK;
+}
+
+int fetch_scalars(les_s* h) {
+    CK(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LES_OK;
+}
+
+void rec(les_s* h, int e) {
+    if (h->timing) cudaEventRecord(h->ev[e], h->stream);
+}
+double elapsed(les_s* h, int a, int b) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev[a], h->ev[b]);
+    return ms;
+}
+
+// press: SOR iterations under the stop rule, FP64 residual, gauge mean
+template <typename T>
+int sor_solve(les_s* h) {
+    Geo<T> g = geo<T>(h);
+    Reduce r = reducer(h);
+    T* p = (T*)h->p[h->cur];
+    const T* rhs = (const T*)h->rhs;
+    const les_grid_t& G = h->g;
+    int sweeps = 0;
+    auto batch = [&](int n) -> int {
+        rec(h, 2);
+        long long l0 = h->launches;
+        for (int s = 0; s < n; ++s) h->launches += launch_sor_sweep<T>(g, p, rhs, h->sc, h->stream);
+        long long nl = h->launches - l0;
+        rec(h, 3);
+        h->launches += launch_residual<T>(g, p, rhs, G.tol, h->vfluid, r, h->stream);
+        rec(h, 4);
+        CK(cudaGetLastError());
+        int rc = fetch_scalars(h);
+        if (rc) return rc;
+        if (h->timing) {
+            h->tm.ms_sor += elapsed(h, 2, 3);
+            h->tm.ms_residual += elapsed(h, 3, 4);
+            h->tm.sor_sweeps += n;
+            h->tm.sor_launches += nl;
+        }
+        return LES_OK;
+    };
+    if (G.fixed_sweeps) {
+        int rc = batch(G.max_sweeps);
+        if (rc) return rc;
+        sweeps = G.max_sweeps;
+    } else {
+        while (sweeps < G.max_sweeps) {
+            int n = G.check_every < G.max_sweeps - sweeps ? G.check_every : G.max_sweeps - sweeps;
+            int rc = batch(n);
+            if (rc) return rc;
+            sweeps += n;
+            if (h->sc_host->converged || h->sc_host->nonfinite) break;
+        }
+    }
+    h->sc_host->sweeps = sweeps;
+    if (h->sc_host->nonfinite) return fail(h, LES_ENONFINITE, "SOR residual is not finite");
+    return (!G.fixed_sweeps && !h->sc_host->converged) ? LES_ENOCONV : LES_OK;
+}
+
+template <typename T>
+int project(les_s* h) {
+    Geo<T> g = geo<T>(h);
+    h->launches += launch_project<T>(g, (const T*)h->us, (const T*)h->vs, (const T*)h->ws, (T*)h->u, (T*)h->v,
+                                     (T*)h->w, (const T*)h->p[h->cur], (T*)h->p[1 - h->cur], h->sc, h->stream);
+    CK(cudaGetLastError());
+    h->cur = 1 - h->cur;
+    return LES_OK;
+}
+
+// Mean of p for the gauge: the last residual kernel of a solve computes it
+// from the same p that velnw then reads, so no extra pass is needed.
+template <typename T>
+int step_once(les_s* h) {
+    Geo<T> g = geo<T>(h);
+    cudaStream_t s = h->stream;
+    T* u = (T*)h->u;
+    T* v = (T*)h->v;
+    T* w = (T*)h->w;
+    rec(h, 0);
+    h->launches += launch_bc<T>(g, u, v, w, h->inflow64, h->g.turb, h->g.seed, h->step, s);
+    h->launches += launch_nut<T>(g, u, v, w, (T*)h->nut, s);
+    h->launches += launch_momentum<T>(g, u, v, w, (const T*)h->nut, (T*)h->fu, (T*)h->fv, (T*)h->fw, (T*)h->us,
+                                      (T*)h->vs, (T*)h->ws, h->step == 0, s);
+    h->launches += launch_outflow<T>(g, u, (T*)h->us, (T*)h->vs, (T*)h->ws, h->sc, s);
+    h->launches += launch_rhs<T>(g, (const T*)h->us, (const T*)h->vs, (const T*)h->ws, (T*)h->rhs, h->vfluid,
+                                 reducer(h), s);
+    rec(h, 1);
+    CK(cudaGetLastError());
+    int rc = sor_solve<T>(h);
+    if (rc < 0) return rc;
+    rec(h, 5);
+    int rp = project<T>(h);
+    if (rp) return rp;
+    rec(h, 6);
+    if (h->timing) {
+        CK(cudaEventSynchronize(h->ev[6]));
+        h->tm.ms_momentum += elapsed(h, 0, 1);
+        h->tm.ms_project += elapsed(h, 5, 6);
+        h->tm.steps += 1;
+    }
+    h->step += 1;
+    return rc;
+}
+
+void fill_stats(les_s* h, les_stats_t* st, int status) {
+    if (!st) return;
+    const Scalars& s = *h->sc_host;
+    st->sweeps = s.sweeps;
+    st->status = status;
+    st->rel_residual = s.rel;
+    st->rhs_norm = std::sqrt(s.rhs2);
+    st->rhs_mean = s.rhs_mean;
+    st->mass_factor = s.mass_factor;
+    st->q_in = s.q_in;
+    st->q_out = s.q_out;
+    st->p_mean = s.p_mean;
+    st->step = h->step;
+    st->launches = h->launches;
+}
+
+int validate(const les_grid_t* g) {
+    if (!g) return fail(nullptr, LES_EINVAL, "grid is NULL");
+    if (g->nx < 2 || g->ny < 2 || g->nz < 2) return fail(nullptr, LES_EINVAL, "nx, ny, nz must be >= 2");
+    if ((long long)g->nx * g->ny * g->nz > (1LL << 31))
+        return fail(nullptr, LES_EINVAL, "grid larger than 2^31 cells");
+    if (g->bc_x != LES_BC_INOUT && g->bc_x != LES_BC_PERIODIC) return fail(nullptr, LES_EINVAL, "bad bc_x");
+    if (g->bc_y != LES_BC_FREESLIP && g->bc_y != LES_BC_PERIODIC) return fail(nullptr, LES_EINVAL, "bad bc_y");
+    if (g->bc_z != LES_BC_WALL && g->bc_z != LES_BC_PERIODIC) return fail(nullptr, LES_EINVAL, "bad bc_z");
+    if ((g->bc_x == LES_BC_PERIODIC && g->nx % 2) || (g->bc_y == LES_BC_PERIODIC && g->ny % 2) ||
+        (g->bc_z == LES_BC_PERIODIC && g->nz % 2))
+        return fail(nullptr, LES_EINVAL, "a periodic axis needs an even cell count (red-black colouring)");
+    if (!(g->dx > 0) || !(g->dy > 0) || !(g->dt > 0)) return fail(nullptr, LES_EINVAL, "dx, dy, dt must be > 0");
+    if (!g->dz) return fail(nullptr, LES_EINVAL, "dz is NULL");
+    for (int k = 0; k < g->nz; ++k)
+        if (!(g->dz[k] > 0)) return fail(nullptr, LES_EINVAL, "dz[%d] must be > 0", k);
+    if (!(g->omega > 0 && g->omega < 2)) return fail(nullptr, LES_EINVAL, "omega must be in (0, 2)");
+    if (g->max_sweeps < 1 || g->check_every < 1) return fail(nullptr, LES_EINVAL, "max_sweeps, check_every >= 1");
+    if (g->precision != LES_FP32 && g->precision != LES_FP64) return fail(nullptr, LES_EINVAL, "bad precision");
+    if (!(g->cs >= 0) || !(g->nu >= 0) || !(g->turb >= 0) || !(g->tol >= 0))
+        return fail(nullptr, LES_EINVAL, "cs, nu, turb, tol must be >= 0");
+    return LES_OK;
+}
+
+template <typename T>
+int init_tables(les_s* h) {
+    const int nz = h->g.nz;
+    std::vector<double> dzp(nz + 2), dzs(nz + 2), cT(nz + 2, 0.0), cB(nz + 2, 0.0), del(nz + 2, 0.0);
+    for (int k = 1; k <= nz; ++k) dzp[k] = h->dz[k - 1];
+    if (h->g.bc_z == LES_BC_PERIODIC) {
+        dzp[0] = dzp[nz];
+        dzp[nz + 1] = dzp[1];
+    } else {
+        dzp[0] = dzp[1];
+        dzp[nz + 1] = dzp[nz];
+    }
+    for (int k = 0; k <= nz; ++k) dzs[k] = 0.5 * (dzp[k] + dzp[k + 1]);
+    dzs[nz + 1] = dzp[nz + 1];
+    for (int k = 1; k <= nz; ++k) {
+        cT[k] = 1.0 / (dzp[k] * dzs[k]);
+        cB[k] = 1.0 / (dzp[k] * dzs[k - 1]);
+        double l = h->g.cs * std::cbrt(h->g.dx * h->g.dy * dzp[k]);
+        del[k] = l * l;
+    }
+    int rc;
+    if ((rc = upload_table<T>(h, h->kdz, dzp))) return rc;
+    if ((rc = upload_table<T>(h, h->kdzs, dzs))) return rc;
+    if ((rc = upload_table<T>(h, h->kcT, cT))) return rc;
+    if ((rc = upload_table<T>(h, h->kcB, cB))) return rc;
+    if ((rc = upload_table<T>(h, h->kdel, del))) return rc;
+    if ((rc = upload_table<double>(h, h->dz64, dzp))) return rc;
+    return LES_OK;
+}
+
+void release(les_s* h) {
+    for (cudaEvent_t& e : h->ev)
+        if (e) {
+            cudaEventDestroy(e);
+            e = nullptr;
+        }
+    for (void* p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+    if (h->sc_host) cudaFreeHost(h->sc_host);
+    h->sc_host = nullptr;
+}
+
+int create_impl(les_s* h, const uint8_t* solid) {
+    const les_grid_t& G = h->g;
+    Dom& d = h->d;
+    d.nx = G.nx;
+    d.ny = G.ny;
+    d.nz = G.nz;
+    d.px = ((G.nx + 2 + OX) + 15) / 16 * 16;
+    d.py = G.ny + 2;
+    d.plane = (long long)d.px * d.py;
+    d.perx = G.bc_x == LES_BC_PERIODIC;
+    d.pery = G.bc_y == LES_BC_PERIODIC;
+    d.perz = G.bc_z == LES_BC_PERIODIC;
+    h->n = (size_t)d.total() + 16;     // slack so a vector load past the last row stays in bounds
+    const size_t B = h->n * h->es;
+    int rc;
+    void** fields[] = {&h->u, &h->v, &h->w, &h->us, &h->vs, &h->ws, &h->fu, &h->fv, &h->fw,
+                       &h->nut, &h->rhs, &h->tmp, &h->p[0], &h->p[1]};
+    for (void** f : fields)
+        if ((rc = dalloc(h, f, B))) return rc;
+    if ((rc = dalloc(h, (void**)&h->flags, h->n))) return rc;
+    const size_t nt = (size_t)G.nz + 2;
+    void** tabs[] = {&h->kdz, &h->kdzs, &h->kcT, &h->kcB, &h->kdel};
+    for (void** t : tabs)
+        if ((rc = dalloc(h, t, nt * h->es))) return rc;
+    if ((rc = dalloc(h, (void**)&h->dz64, nt * sizeof(double)))) return rc;
+    if ((rc = dalloc(h, (void**)&h->inflow64, nt * sizeof(double)))) return rc;
+    const int nb = max_reduce_blocks(d);
+    if ((rc = dalloc(h, (void**)&h->partials, (size_t)3 * nb * sizeof(double)))) return rc;
+    if ((rc = dalloc(h, (void**)&h->counter, sizeof(unsigned)))) return rc;
+    if ((rc = dalloc(h, (void**)&h->sc, sizeof(Scalars)))) return rc;
+    h->stage_elems = io_elems(h, 1) + io_elems(h, 2) + io_elems(h, 3) + io_elems(h, 0);
+    if ((rc = dalloc(h, &h->stage, h->stage_elems * h->es))) return rc;
+    if (cudaMallocHost((void**)&h->sc_host, sizeof(Scalars)) != cudaSuccess)
+        return fail(h, LES_ENOMEM, "cudaMallocHost failed");
+    memset(h->sc_host, 0, sizeof(Scalars));
+    h->sc_host->mass_factor = 1.0;
+
+    // obstacles: padded solid mask -> open-face flags (on the device)
+    uint8_t* solid_d = nullptr;
+    if ((rc = dalloc(h, (void**)&solid_d, h->n))) return rc;
+    std::vector<uint8_t> tmp((size_t)G.nx * G.ny * G.nz);
+    double vf = 0.0;
+    for (int k = 0; k < G.nz; ++k)
+        for (int j = 0; j < G.ny; ++j)
+            for (int i = 0; i < G.nx; ++i) {
+                size_t q = ((size_t)k * G.ny + j) * G.nx + i;
+                tmp[q] = solid[q] ? 1 : 0;
+                if (!tmp[q]) vf += h->dz[k];
+            }
+    h->vfluid = vf;
+    uint8_t* st8 = (uint8_t*)h->stage;   // stage holds at least nx*ny*nz bytes
+    CK(cudaMemcpyAsync(st8, tmp.data(), tmp.size(), cudaMemcpyHostToDevice, h->stream));
+    {
+        size_t n = tmp.size();
+        k_unpack<uint8_t><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(d, st8, solid_d, 1, 1, 1, G.nx, G.ny, G.nz);
+        k_flags<<<dim3((G.nx + 31) / 32, (G.ny + 7) / 8, G.nz), dim3(32, 8), 0, h->stream>>>(d, solid_d, h->flags);
+        CK(cudaGetLastError());
+    }
+    CK(cudaMemcpyAsync(h->inflow64, h->inflow.data(), nt * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    rc = h->prec == LES_FP64 ? init_tables<double>(h) : init_tables<float>(h);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(h->stream));
+    return LES_OK;
+}
+
+template <typename T>
+int set_fields_impl(les_s* h, const void* u, const void* v, const void* w, const void* p) {
+    int rc;
+    size_t off = 0;
+    if (u && (rc = upload<T>(h, h->u, 1, u, off))) return rc;
+    off += io_elems(h, 1);
+    if (v && (rc = upload<T>(h, h->v, 2, v, off))) return rc;
+    off += io_elems(h, 2);
+    if (w && (rc = upload<T>(h, h->w, 3, w, off))) return rc;
+    off += io_elems(h, 3);
+    if (p && (rc = upload<T>(h, h->p[h->cur], 0, p, off))) return rc;
+    return LES_OK;
+}
+
+template <typename T>
+int get_fields_impl(les_s* h, void* u, void* v, void* w, void* p) {
+    int rc;
+    size_t off = 0;
+    if (u && (rc = download<T>(h, h->u, 1, u, off))) return rc;
+    off += io_elems(h, 1);
+    if (v && (rc = download<T>(h, h->v, 2, v, off))) return rc;
+    off += io_elems(h, 2);
+    if (w && (rc = download<T>(h, h->w, 3, w, off))) return rc;
+    off += io_elems(h, 3);
+    if (p && (rc = download<T>(h, h->p[h->cur], 0, p, off))) return rc;
+    CK(cudaStreamSynchronize(h->stream));
+    return LES_OK;
+}
+
+template <typename T>
+int get_aux_impl(les_s* h, int which, void* out) {
+    const void* src = nullptr;
+    int stag = 0;
+    switch (which) {
+        case LES_AUX_NUT: src = h->nut; break;
+        case LES_AUX_RHS: {
+            Geo<T> g = geo<T>(h);
+            h->launches += launch_rhs_eff<T>(g, (const T*)h->rhs, (T*)h->tmp, h->sc, h->stream);
+            CK(cudaGetLastError());
+            src = h->tmp;
+            break;
+        }
+        case LES_AUX_USTAR: src = h->us; stag = 1; break;
+        case LES_AUX_VSTAR: src = h->vs; stag = 2; break;
+        case LES_AUX_WSTAR: src = h->ws; stag = 3; break;
+        case LES_AUX_FU: src = h->fu; stag = 1; break;
+        case LES_AUX_FV: src = h->fv; stag = 2; break;
+        case LES_AUX_FW: src = h->fw; stag = 3; break;
+        default: return fail(h, LES_EINVAL, "unknown aux array %d", which);
+    }
+    int rc = download<T>(h, src, stag, out, 0);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(h->stream));
+    return LES_OK;
+}
+
+template <typename T>
+int pressure_solve_impl(les_s* h, const void* rhs, les_stats_t* st) {
+    Geo<T> g = geo<T>(h);
+    if (rhs) {
+        int rc = upload<T>(h, h->rhs, 0, rhs, 0);
+        if (rc) return rc;
+        h->launches += launch_rhs_mean<T>(g, (T*)h->rhs, h->vfluid, reducer(h), h->stream);
+        CK(cudaGetLastError());
+    }
+    int rc = sor_solve<T>(h);
+    if (rc < 0) return rc;
+    // gauge: p_out = p - mean (velocities untouched)
+    T* pin = (T*)h->p[h->cur];
+    T* pout = (T*)h->p[1 - h->cur];
+    h->launches += launch_gauge<T>(g, pin, pout, h->sc, h->stream);
+    CK(cudaGetLastError());
+    h->cur = 1 - h->cur;
+    CK(cudaStreamSynchronize(h->stream));
+    fill_stats(h, st, rc);
+    return rc;
+}
+
+// checkpoint blob: header, then the raw padded arrays and the inflow
+struct StateHeader {
+    uint64_t magic;
+    int32_t nx, ny, nz, prec;
+    int64_t step;
+    double turb;
+    uint64_t seed;
+    uint64_t n, es;
+};
+constexpr uint64_t kMagic = 0x4c45534742333030ull;  // "LESGB300"
+
+size_t state_size(const les_s* h) {
+    return sizeof(StateHeader) + 7 * h->n * h->es + h->inflow.size() * sizeof(double);
+}
+
+}  // namespace
+
+// ===========================================================================
+// extern "C" entry points
+
+extern "C" {
+
+const char* les_version(void) { return kVersion; }
+
+const char* les_last_error(les_handle h) { return h ? h->err : g_static_err; }
+
+int les_create(const les_grid_t* grid, const uint8_t* solid, const double* inflow_u, void* stream,
+               les_handle* out) {
+    if (!out) return fail(nullptr, LES_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = validate(grid);
+    if (rc) return rc;
+    if (!solid) return fail(nullptr, LES_EINVAL, "solid is NULL");
+    if (!inflow_u && grid->bc_x == LES_BC_INOUT) return fail(nullptr, LES_EINVAL, "inflow_u is NULL");
+    les_s* h = new (std::nothrow) les_s();
+    if (!h) return fail(nullptr, LES_ENOMEM, "out of host memory");
+    h->g = *grid;
+    h->dz.assign(grid->dz, grid->dz + grid->nz);
+    h->g.dz = nullptr;
+    h->prec = grid->precision;
+    h->es = h->prec == LES_FP64 ? sizeof(double) : sizeof(float);
+    h->stream = (cudaStream_t)stream;
+    h->inflow.assign((size_t)grid->nz + 2, 0.0);
+    if (inflow_u)
+        for (int k = 1; k <= grid->nz; ++k) h->inflow[k] = inflow_u[k - 1];
+    rc = create_impl(h, solid);
+    if (rc) {
+        snprintf(g_static_err, sizeof g_static_err, "%s", h->err);
+        release(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return LES_OK;
+}
+
+void les_destroy(les_handle h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    release(h);
+    delete h;
+}
+
+int les_set_fields(les_handle h, const void* u, const void* v, const void* w, const void* p) {
+    if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
+    return h->prec == LES_FP64 ? set_fields_impl<double>(h, u, v, w, p) : set_fields_impl<float>(h, u, v, w, p);
+}
+
+int les_get_fields(les_handle h, void* u, void* v, void* w, void* p) {
+    if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
+    return h->prec == LES_FP64 ? get_fields_impl<double>(h, u, v, w, p) : get_fields_impl<float>(h, u, v, w, p);
+}
+
+int les_set_inflow(les_handle h, const double* inflow_u, double turb, uint64_t seed) {
+    if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
+    if (!inflow_u) return fail(h, LES_EINVAL, "inflow_u is NULL");
+    if (!(turb >= 0)) return fail(h, LES_EINVAL, "turb must be >= 0");
+    for (int k = 1; k <= h->g.nz; ++k) h->inflow[k] = inflow_u[k - 1];
+    h->g.turb = turb;
+    h->g.seed = seed;
+    CK(cudaMemcpyAsync(h->inflow64, h->inflow.data(), h->inflow.size() * sizeof(double), cudaMemcpyHostToDevice,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LES_OK;
+}
+
+int les_step(les_handle h, int32_t nsteps, les_stats_t* stats) {
+    if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
+    if (nsteps < 0) return fail(h, LES_EINVAL, "nsteps < 0");
+    int worst = LES_OK;
+    if (nsteps == 0 && stats) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return fail(h, LES_ECUDA, "step: %s", cudaGetErrorString(e));
+        fill_stats(h, stats, LES_OK);
+        return LES_OK;
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        int rc = h->prec == LES_FP64 ? step_once<double>(h) : step_once<float>(h);
+        if (rc < 0) return rc;
+        if (rc == LES_ENOCONV) worst = LES_ENOCONV;
+        if (stats && s == nsteps - 1) {
+            cudaError_t e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) return fail(h, LES_ECUDA, "step: %s", cudaGetErrorString(e));
+            fill_stats(h, stats, rc);
+        }
+    }
+    return worst;
+}
+
+int les_pressure_solve(les_handle h, const void* rhs, les_stats_t* stats) {
+    if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
+    return h->prec == LES_FP64 ? pressure_solve_impl<double>(h, rhs, stats)
+                               : pressure_solve_impl<float>(h, rhs, stats);
+}
+
+int les_get_aux(les_handle h, int32_t which, void* out) {
+    if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
+    if (!out) return fail(h, LES_EINVAL, "out is NULL");
+    return h->prec == LES_FP64 ? get_aux_impl<double>(h, which, out) : get_aux_impl<float>(h, which, out);
+}
+
+int les_get_state(les_handle h, void* buf, size_t* len) {
+    if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
+    if (!len) return fail(h, LES_EINVAL, "len is NULL");
+    size_t need = state_size(h);
+    if (!buf) {
+        *len = need;
+        return LES_OK;
+    }
+    if (*len < need) return fail(h, LES_EINVAL, "state buffer too small (%zu < %zu)", *len, need);
+    StateHeader hd{kMagic, h->g.nx, h->g.ny, h->g.nz, h->prec, h->step, h->g.turb, h->g.seed, h->n, h->es};
+    char* b = (char*)buf;
+    memcpy(b, &hd, sizeof hd);
+    b += sizeof hd;
+    const void* arrs[] = {h->u, h->v, h->w, h->p[h->cur], h->fu, h->fv, h->fw};
+    const size_t B = h->n * h->es;
+    for (const void* a : arrs) {
+        CK(cudaMemcpyAsync(b, a, B, cudaMemcpyDeviceToHost, h->stream));
+        b += B;
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    memcpy(b, h->inflow.data(), h->inflow.size() * sizeof(double));
+    *len = need;
+    return LES_OK;
+}
+
+int les_set_state(les_handle h, const void* buf, size_t len) {
+    if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
+    if (!buf || len < sizeof(StateHeader)) return fail(h, LES_ESTATE, "state blob too small");
+    StateHeader hd;
+    memcpy(&hd, buf, sizeof hd);
+    if (hd.magic != kMagic || hd.nx != h->g.nx || hd.ny != h->g.ny || hd.nz != h->g.nz || hd.prec != h->prec ||
+        hd.n != h->n || hd.es != h->es || len != state_size(h))
+        return fail(h, LES_ESTATE, "state blob does not match this handle");
+    const char* b = (const char*)buf + sizeof hd;
+    void* arrs[] = {h->u, h->v, h->w, h->p[h->cur], h->fu, h->fv, h->fw};
+    const size_t B = h->n * h->es;
+    for (void* a : arrs) {
+        CK(cudaMemcpyAsync(a, b, B, cudaMemcpyHostToDevice, h->stream));
+        b += B;
+    }
+    memcpy(h->inflow.data(), b, h->inflow.size() * sizeof(double));
+    CK(cudaMemcpyAsync(h->inflow64, h->inflow.data(), h->inflow.size() * sizeof(double), cudaMemcpyHostToDevice,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->step = hd.step;
+    h->g.turb = hd.turb;
+    h->g.seed = hd.seed;
+    return LES_OK;
+}
+
+int les_set_timing(les_handle h, int32_t enable) {
+    if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
+    if (enable && !h->ev[0])
+        for (cudaEvent_t& e : h->ev) CK(cudaEventCreate(&e));
+    h->timing = enable != 0;
+    h->tm = les_timing_t{};
+    return LES_OK;
+}
+
+int les_get_timing(les_handle h, les_timing_t* t) {
+    if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
+    if (!t) return fail(h, LES_EINVAL, "t is NULL");
+    *t = h->tm;
+    t->launches = h->launches;
+    return LES_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,99 @@
+// Internal declarations of the LES CUDA library (not part of the C ABI).
+//
+// Device layout: every field is one padded 3-D array of (nz+2) planes of
+// (ny+2) rows of `px` elements, i fastest.  Index 0 and n+1 are the ghost
+// layer on each axis (1-based interior like the paper's Fortran).  Column
+// OX + i holds index i, so the first interior element (i = 1) of every row
+// sits on a 16-byte boundary for vector loads; px is a multiple of 16
+// elements so every row starts 64-byte aligned.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace les {
+
+constexpr int OX = 3;
+
+// per-cell flag bits: open faces of the cell, Poisson unknown, fluid
+enum : uint8_t {
+    F_E = 1, F_W = 2, F_N = 4, F_S = 8, F_T = 16, F_B = 32, F_UNK = 64, F_FLUID = 128
+};
+
+struct Dom {
+    int nx, ny, nz;
+    int px, py;                 // row pitch (elements), rows per plane (ny + 2)
+    long long plane;            // px * py
+    int perx, pery, perz;       // periodic axes
+    __host__ __device__ __forceinline__ long long at(int i, int j, int k) const {
+        return ((long long)k * py + j) * px + (i + OX);
+    }
+    __host__ __device__ __forceinline__ long long total() const { return plane * (nz + 2); }
+};
+
+// FP64 scalars produced and consumed on the device
+struct Scalars {
+    double rhs_mean;        // dz-weighted fluid mean of div(u*)/dt
+    double rhs2;            // sum (rhs - mean)^2 over unknowns
+    double res2;            // sum r^2 over unknowns
+    double rel;             // sqrt(res2 / rhs2)
+    double p_mean;          // dz-weighted fluid mean of p
+    double q_in, q_out;     // volume fluxes after the outflow correction
+    double mass_factor;     // Q_in / Q_out
+    int converged;          // rel <= tol
+    int nonfinite;          // a norm was NaN/Inf
+    int sweeps;             // sweeps done in the current solve (graph path)
+    int pad_;
+};
+
+// constant per-run data in the compute type
+template <typename T>
+struct Geo {
+    Dom d;
+    T dx, dy, rdx, rdy, dt, nu, omega;
+    T cx, cy;               // 1/dx^2, 1/dy^2
+    const T* dz;            // [nz+2] padded cell heights
+    const T* dzs;           // [nz+2] centre-to-centre spacing dzs_k = (dz_k + dz_{k+1})/2
+    const T* cT;            // [nz+2] 1/(dz_k dzs_k)
+    const T* cB;            // [nz+2] 1/(dz_k dzs_{k-1})
+    const T* delta2;        // [nz+2] (Cs Delta_k)^2
+    const double* dz64;     // [nz+2]
+    const uint8_t* flags;   // padded cell flags
+};
+
+struct Reduce {
+    double* partials;       // [3 * max_blocks]
+    unsigned* counter;      // zero between launches
+    Scalars* sc;
+};
+
+// launchers (les_kernels.cu); each returns the number of kernels launched
+template <typename T> int launch_bc(const Geo<T>& g, T* u, T* v, T* w, const double* inflow,
+                                    double turb, uint64_t seed, long long step, cudaStream_t s);
+template <typename T> int launch_nut(const Geo<T>& g, const T* u, const T* v, const T* w, T* nut,
+                                     cudaStream_t s);
+template <typename T> int launch_momentum(const Geo<T>& g, const T* u, const T* v, const T* w,
+                                          const T* nut, T* fu, T* fv, T* fw, T* us, T* vs, T* ws,
+                                          int first, cudaStream_t s);
+template <typename T> int launch_outflow(const Geo<T>& g, const T* u, T* us, T* vs, T* ws,
+                                         Scalars* sc, cudaStream_t s);
+template <typename T> int launch_rhs(const Geo<T>& g, const T* us, const T* vs, const T* ws, T* rhs,
+                                     double vfluid, const Reduce& r, cudaStream_t s);
+template <typename T> int launch_rhs_mean(const Geo<T>& g, T* rhs, double vfluid, const Reduce& r,
+                                          cudaStream_t s);
+template <typename T> int launch_sor_sweep(const Geo<T>& g, T* p, const T* rhs, const Scalars* sc,
+                                           cudaStream_t s);
+template <typename T> int launch_residual(const Geo<T>& g, const T* p, const T* rhs, double tol,
+                                          double vfluid, const Reduce& r, cudaStream_t s);
+template <typename T> int launch_project(const Geo<T>& g, const T* us, const T* vs, const T* ws,
+                                         T* u, T* v, T* w, const T* p_in, T* p_out,
+                                         const Scalars* sc, cudaStream_t s);
+template <typename T> int launch_rhs_eff(const Geo<T>& g, const T* rhs, T* out, const Scalars* sc,
+                                         cudaStream_t s);
+
+template <typename T> int launch_gauge(const Geo<T>& g, const T* p_in, T* p_out, const Scalars* sc,
+                                       cudaStream_t s);
+
+int max_reduce_blocks(const Dom& d);
+
+}  // namespace les

@@ -1,0 +1,750 @@
+// CUDA kernels of one LES time step (sm_103a), templated on the field type
+// (float for the production path, double for bit-level parity checks).
+//
+// Routine map (paper Sec. 2.1): k_bc_* = bondv1, k_nut = les (eddy
+// viscosity), k_momentum = velfg + les (SGS divergence) + adam + feedbf,
+// k_outflow = bondv1 outflow and mass-flux correction, k_rhs / k_sor_half /
+// k_residual = press (Sec. 2.6), k_project = velnw.
+#include "les_internal.cuh"
+
+namespace les {
+
+// ---------------------------------------------------------------------------
+// counter-based inflow noise: splitmix64 as a hash of (seed, counter)
+// (Steele, Lea & Flood 2014), then Box-Muller, in FP64.
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t ctr) {
+    uint64_t z = seed + (ctr + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ double unit_open(uint64_t x) {
+    return ((double)(x >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+}
+__device__ double gauss_at(uint64_t seed, uint64_t c) {
+    double u1 = unit_open(splitmix64_at(seed, 2ull * c));
+    double u2 = unit_open(splitmix64_at(seed, 2ull * c + 1ull));
+    return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+}
+
+// ---------------------------------------------------------------------------
+// bondv1, three passes (x over interior j,k; y over all i; z over all i,j) so
+// corner ghosts take the rules in that order.
+
+template <typename T>
+__global__ void k_bc_x(Dom d, T* u, T* v, T* w, const double* inflow, double turb, uint64_t seed,
+                       long long step) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    int k = blockIdx.y + 1;
+    if (j > d.ny) return;
+    const int nx = d.nx;
+    if (d.perx) {
+        u[d.at(0, j, k)] = u[d.at(nx, j, k)];
+        u[d.at(nx + 1, j, k)] = u[d.at(1, j, k)];
+        v[d.at(0, j, k)] = v[d.at(nx, j, k)];
+        v[d.at(nx + 1, j, k)] = v[d.at(1, j, k)];
+        w[d.at(0, j, k)] = w[d.at(nx, j, k)];
+        w[d.at(nx + 1, j, k)] = w[d.at(1, j, k)];
+        return;
+    }
+    double U = inflow[k];
+    double xu = 0.0, xv = 0.0, xw = 0.0;
+    if (turb != 0.0) {
+        const uint64_t sy = (uint64_t)(d.ny + 2), sz = (uint64_t)(d.nz + 2);
+        uint64_t base = (uint64_t)step * 3ull;
+        xu = gauss_at(seed, ((base + 0) * sy + (uint64_t)j) * sz + (uint64_t)k);
+        xv = gauss_at(seed, ((base + 1) * sy + (uint64_t)j) * sz + (uint64_t)k);
+        xw = gauss_at(seed, ((base + 2) * sy + (uint64_t)j) * sz + (uint64_t)k);
+    }
+    u[d.at(0, j, k)] = (T)(U * (1.0 + turb * xu));
+    v[d.at(0, j, k)] = (T)(turb * U * xv);
+    w[d.at(0, j, k)] = (T)(turb * U * xw);
+    T t = u[d.at(nx - 1, j, k)];
+    u[d.at(nx, j, k)] = t;
+    u[d.at(nx + 1, j, k)] = t;
+    v[d.at(nx + 1, j, k)] = v[d.at(nx, j, k)];
+    w[d.at(nx + 1, j, k)] = w[d.at(nx, j, k)];
+}
+
+template <typename T>
+__global__ void k_bc_y(Dom d, T* u, T* v, T* w) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int k = blockIdx.y + 1;
+    if (i > d.nx + 1) return;
+    const int ny = d.ny;
+    if (d.pery) {
+        u[d.at(i, 0, k)] = u[d.at(i, ny, k)];
+        u[d.at(i, ny + 1, k)] = u[d.at(i, 1, k)];
+        v[d.at(i, 0, k)] = v[d.at(i, ny, k)];
+        v[d.at(i, ny + 1, k)] = v[d.at(i, 1, k)];
+        w[d.at(i, 0, k)] = w[d.at(i, ny, k)];
+        w[d.at(i, ny + 1, k)] = w[d.at(i, 1, k)];
+        return;
+    }
+    v[d.at(i, 0, k)] = T(0);
+    v[d.at(i, ny, k)] = T(0);
+    v[d.at(i, ny + 1, k)] = -v[d.at(i, ny - 1, k)];
+    u[d.at(i, 0, k)] = u[d.at(i, 1, k)];
+    u[d.at(i, ny + 1, k)] = u[d.at(i, ny, k)];
+    w[d.at(i, 0, k)] = w[d.at(i, 1, k)];
+    w[d.at(i, ny + 1, k)] = w[d.at(i, ny, k)];
+}
+
+template <typename T>
+__global__ void k_bc_z(Dom d, T* u, T* v, T* w) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (i > d.nx + 1) return;
+    const int nz = d.nz;
+    if (d.perz) {
+        u[d.at(i, j, 0)] = u[d.at(i, j, nz)];
+        u[d.at(i, j, nz + 1)] = u[d.at(i, j, 1)];
+        v[d.at(i, j, 0)] = v[d.at(i, j, nz)];
+        v[d.at(i, j, nz + 1)] = v[d.at(i, j, 1)];
+        w[d.at(i, j, 0)] = w[d.at(i, j, nz)];
+        w[d.at(i, j, nz + 1)] = w[d.at(i, j, 1)];
+        return;
+    }
+    w[d.at(i, j, 0)] = T(0);
+    w[d.at(i, j, nz)] = T(0);
+    w[d.at(i, j, nz + 1)] = -w[d.at(i, j, nz - 1)];
+    u[d.at(i, j, 0)] = -u[d.at(i, j, 1)];
+    u[d.at(i, j, nz + 1)] = u[d.at(i, j, nz)];
+    v[d.at(i, j, 0)] = -v[d.at(i, j, 1)];
+    v[d.at(i, j, nz + 1)] = v[d.at(i, j, nz)];
+}
+
+template <typename T>
+int launch_bc(const Geo<T>& g, T* u, T* v, T* w, const double* inflow, double turb, uint64_t seed,
+              long long step, cudaStream_t s) {
+    const Dom& d = g.d;
+    k_bc_x<T><<<dim3((d.ny + 127) / 128, d.nz), 128, 0, s>>>(d, u, v, w, inflow, turb, seed, step);
+    k_bc_y<T><<<dim3((d.nx + 2 + 127) / 128, d.nz), 128, 0, s>>>(d, u, v, w);
+    k_bc_z<T><<<dim3((d.nx + 2 + 127) / 128, d.ny + 2), 128, 0, s>>>(d, u, v, w);
+    return 3;
+}
+
+// ---------------------------------------------------------------------------
+// les: Smagorinsky eddy viscosity at cell centres
+
+template <typename T>
+struct Stencil {
+    const Geo<T>& g;
+    const T* u;
+    const T* v;
+    const T* w;
+    __device__ __forceinline__ T U(int i, int j, int k) const { return u[g.d.at(i, j, k)]; }
+    __device__ __forceinline__ T V(int i, int j, int k) const { return v[g.d.at(i, j, k)]; }
+    __device__ __forceinline__ T W(int i, int j, int k) const { return w[g.d.at(i, j, k)]; }
+    // shear rates on cell edges
+    __device__ __forceinline__ T s12(int i, int j, int k) const {
+        return T(0.5) * ((U(i, j + 1, k) - U(i, j, k)) / g.dy + (V(i + 1, j, k) - V(i, j, k)) / g.dx);
+    }
+    __device__ __forceinline__ T s13(int i, int j, int k) const {
+        return T(0.5) * ((U(i, j, k + 1) - U(i, j, k)) / g.dzs[k] + (W(i + 1, j, k) - W(i, j, k)) / g.dx);
+    }
+    __device__ __forceinline__ T s23(int i, int j, int k) const {
+        return T(0.5) * ((V(i, j, k + 1) - V(i, j, k)) / g.dzs[k] + (W(i, j + 1, k) - W(i, j, k)) / g.dy);
+    }
+};
+
+template <typename T>
+__global__ void k_nut(Geo<T> g, const T* u, const T* v, const T* w, T* nut) {
+    const Dom& d = g.d;
+    int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    int k = blockIdx.z + 1;
+    if (i > d.nx || j > d.ny) return;
+    long long c = d.at(i, j, k);
+    if (!(g.flags[c] & F_FLUID)) { nut[c] = T(0); return; }
+    Stencil<T> S{g, u, v, w};
+    T s11 = (u[c] - S.U(i - 1, j, k)) / g.dx;
+    T s22 = (v[c] - S.V(i, j - 1, k)) / g.dy;
+    T s33 = (w[c] - S.W(i, j, k - 1)) / g.dz[k];
+    T s12 = T(0.25) * (S.s12(i - 1, j - 1, k) + S.s12(i, j - 1, k) + S.s12(i - 1, j, k) + S.s12(i, j, k));
+    T s13 = T(0.25) * (S.s13(i - 1, j, k - 1) + S.s13(i, j, k - 1) + S.s13(i - 1, j, k) + S.s13(i, j, k));
+    T s23 = T(0.25) * (S.s23(i, j - 1, k - 1) + S.s23(i, j, k - 1) + S.s23(i, j - 1, k) + S.s23(i, j, k));
+    T smag = sqrt(T(2) * (s11 * s11 + s22 * s22 + s33 * s33) + T(4) * (s12 * s12 + s13 * s13 + s23 * s23));
+    nut[c] = g.delta2[k] * smag;
+}
+
+template <typename T>
+int launch_nut(const Geo<T>& g, const T* u, const T* v, const T* w, T* nut, cudaStream_t s) {
+    const Dom& d = g.d;
+    k_nut<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(g, u, v, w, nut);
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// velfg + les (SGS) + adam + feedbf.  nu_t is read with its ghost rule applied
+// to the index (zero gradient = clamp, periodic = wrap), so no ghost pass.
+
+template <typename T>
+struct Nut {
+    const Dom& d;
+    const T* nut;
+    __device__ __forceinline__ int cx(int i) const { return d.perx ? (i < 1 ? i + d.nx : (i > d.nx ? i - d.nx : i)) : min(max(i, 1), d.nx); }
+    __device__ __forceinline__ int cy(int j) const { return d.pery ? (j < 1 ? j + d.ny : (j > d.ny ? j - d.ny : j)) : min(max(j, 1), d.ny); }
+    __device__ __forceinline__ int cz(int k) const { return d.perz ? (k < 1 ? k + d.nz : (k > d.nz ? k - d.nz : k)) : min(max(k, 1), d.nz); }
+    __device__ __forceinline__ T operator()(int i, int j, int k) const { return nut[d.at(cx(i), cy(j), cz(k))]; }
+    __device__ __forceinline__ T xy(int i, int j, int k) const {
+        return T(0.25) * ((*this)(i, j, k) + (*this)(i + 1, j, k) + (*this)(i, j + 1, k) + (*this)(i + 1, j + 1, k));
+    }
+    __device__ __forceinline__ T xz(int i, int j, int k) const {
+        return T(0.25) * ((*this)(i, j, k) + (*this)(i + 1, j, k) + (*this)(i, j, k + 1) + (*this)(i + 1, j, k + 1));
+    }
+    __device__ __forceinline__ T yz(int i, int j, int k) const {
+        return T(0.25) * ((*this)(i, j, k) + (*this)(i, j + 1, k) + (*this)(i, j, k + 1) + (*this)(i, j + 1, k + 1));
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ T velfg_u(const Geo<T>& g, const Stencil<T>& S, int i, int j, int k) {
+    const T dx = g.dx, dy = g.dy;
+    T um = S.U(i - 1, j, k), uc = S.U(i, j, k), up = S.U(i + 1, j, k);
+    T cov1_i = T(0.5) * (um + uc) * (uc - um) / dx;
+    T cov1_ip = T(0.5) * (uc + up) * (up - uc) / dx;
+    T covx = (dx * cov1_i + dx * cov1_ip) / (dx + dx);
+    T vn = T(0.5) * (S.V(i, j, k) + S.V(i + 1, j, k));
+    T vs = T(0.5) * (S.V(i, j - 1, k) + S.V(i + 1, j - 1, k));
+    T un = S.U(i, j + 1, k), us = S.U(i, j - 1, k);
+    T covy = (vs * (uc - us) / dy + vn * (un - uc) / dy) / T(2);
+    T wt = T(0.5) * (S.W(i, j, k) + S.W(i + 1, j, k));
+    T wb = T(0.5) * (S.W(i, j, k - 1) + S.W(i + 1, j, k - 1));
+    T ut = S.U(i, j, k + 1), ub = S.U(i, j, k - 1);
+    T covz = (wb * (uc - ub) / g.dzs[k - 1] + wt * (ut - uc) / g.dzs[k]) / T(2);
+    T diu1_i = (uc - um) / dx, diu1_ip = (up - uc) / dx;
+    T dfu = T(2) * (diu1_ip - diu1_i) / (dx + dx) + ((un - uc) / dy - (uc - us) / dy) / dy +
+            ((ut - uc) / g.dzs[k] - (uc - ub) / g.dzs[k - 1]) / g.dz[k];
+    return -(covx + covy + covz) + g.nu * dfu;
+}
+
+template <typename T>
+__device__ __forceinline__ T velfg_v(const Geo<T>& g, const Stencil<T>& S, int i, int j, int k) {
+    const T dx = g.dx, dy = g.dy;
+    T vm = S.V(i, j - 1, k), vc = S.V(i, j, k), vp = S.V(i, j + 1, k);
+    T cov_j = T(0.5) * (vm + vc) * (vc - vm) / dy;
+    T cov_jp = T(0.5) * (vc + vp) * (vp - vc) / dy;
+    T covy = (dy * cov_j + dy * cov_jp) / (dy + dy);
+    T ue = T(0.5) * (S.U(i, j, k) + S.U(i, j + 1, k));
+    T uw = T(0.5) * (S.U(i - 1, j, k) + S.U(i - 1, j + 1, k));
+    T ve = S.V(i + 1, j, k), vw = S.V(i - 1, j, k);
+    T covx = (uw * (vc - vw) / dx + ue * (ve - vc) / dx) / T(2);
+    T wt = T(0.5) * (S.W(i, j, k) + S.W(i, j + 1, k));
+    T wb = T(0.5) * (S.W(i, j, k - 1) + S.W(i, j + 1, k - 1));
+    T vt = S.V(i, j, k + 1), vb = S.V(i, j, k - 1);
+    T covz = (wb * (vc - vb) / g.dzs[k - 1] + wt * (vt - vc) / g.dzs[k]) / T(2);
+    T dfv = ((ve - vc) / dx - (vc - vw) / dx) / dx + T(2) * ((vp - vc) / dy - (vc - vm) / dy) / (dy + dy) +
+            ((vt - vc) / g.dzs[k] - (vc - vb) / g.dzs[k - 1]) / g.dz[k];
+    return -(covx + covy + covz) + g.nu * dfv;
+}
+
+template <typename T>
+__device__ __forceinline__ T velfg_w(const Geo<T>& g, const Stencil<T>& S, int i, int j, int k) {
+    const T dx = g.dx, dy = g.dy;
+    const T dzk = g.dz[k], dzp = g.dz[k + 1];
+    T wm = S.W(i, j, k - 1), wc = S.W(i, j, k), wp = S.W(i, j, k + 1);
+    T cov_k = T(0.5) * (wm + wc) * (wc - wm) / dzk;
+    T cov_kp = T(0.5) * (wc + wp) * (wp - wc) / dzp;
+    T covz = (dzp * cov_k + dzk * cov_kp) / (dzk + dzp);
+    T ue = (dzp * S.U(i, j, k) + dzk * S.U(i, j, k + 1)) / (dzk + dzp);
+    T uw = (dzp * S.U(i - 1, j, k) + dzk * S.U(i - 1, j, k + 1)) / (dzk + dzp);
+    T we = S.W(i + 1, j, k), ww = S.W(i - 1, j, k);
+    T covx = (uw * (wc - ww) / dx + ue * (we - wc) / dx) / T(2);
+    T vn = (dzp * S.V(i, j, k) + dzk * S.V(i, j, k + 1)) / (dzk + dzp);
+    T vs = (dzp * S.V(i, j - 1, k) + dzk * S.V(i, j - 1, k + 1)) / (dzk + dzp);
+    T wn = S.W(i, j + 1, k), wsv = S.W(i, j - 1, k);
+    T covy = (vs * (wc - wsv) / dy + vn * (wn - wc) / dy) / T(2);
+    T dfw = ((we - wc) / dx - (wc - ww) / dx) / dx + ((wn - wc) / dy - (wc - wsv) / dy) / dy +
+            T(2) * ((wp - wc) / dzp - (wc - wm) / dzk) / (dzk + dzp);
+    return -(covx + covy + covz) + g.nu * dfw;
+}
+
+template <typename T>
+__device__ __forceinline__ T sgs_u(const Geo<T>& g, const Stencil<T>& S, const Nut<T>& N, int i, int j, int k) {
+    T t11_i = T(2) * N(i, j, k) * (S.U(i, j, k) - S.U(i - 1, j, k)) / g.dx;
+    T t11_ip = T(2) * N(i + 1, j, k) * (S.U(i + 1, j, k) - S.U(i, j, k)) / g.dx;
+    T t12_n = T(2) * N.xy(i, j, k) * S.s12(i, j, k);
+    T t12_s = T(2) * N.xy(i, j - 1, k) * S.s12(i, j - 1, k);
+    T t13_t = T(2) * N.xz(i, j, k) * S.s13(i, j, k);
+    T t13_b = T(2) * N.xz(i, j, k - 1) * S.s13(i, j, k - 1);
+    return (t11_ip - t11_i) / g.dx + (t12_n - t12_s) / g.dy + (t13_t - t13_b) / g.dz[k];
+}
+template <typename T>
+__device__ __forceinline__ T sgs_v(const Geo<T>& g, const Stencil<T>& S, const Nut<T>& N, int i, int j, int k) {
+    T t22_j = T(2) * N(i, j, k) * (S.V(i, j, k) - S.V(i, j - 1, k)) / g.dy;
+    T t22_jp = T(2) * N(i, j + 1, k) * (S.V(i, j + 1, k) - S.V(i, j, k)) / g.dy;
+    T t12_e = T(2) * N.xy(i, j, k) * S.s12(i, j, k);
+    T t12_w = T(2) * N.xy(i - 1, j, k) * S.s12(i - 1, j, k);
+    T t23_t = T(2) * N.yz(i, j, k) * S.s23(i, j, k);
+    T t23_b = T(2) * N.yz(i, j, k - 1) * S.s23(i, j, k - 1);
+    return (t12_e - t12_w) / g.dx + (t22_jp - t22_j) / g.dy + (t23_t - t23_b) / g.dz[k];
+}
+template <typename T>
+__device__ __forceinline__ T sgs_w(const Geo<T>& g, const Stencil<T>& S, const Nut<T>& N, int i, int j, int k) {
+    T t33_k = T(2) * N(i, j, k) * (S.W(i, j, k) - S.W(i, j, k - 1)) / g.dz[k];
+    T t33_kp = T(2) * N(i, j, k + 1) * (S.W(i, j, k + 1) - S.W(i, j, k)) / g.dz[k + 1];
+    T t13_e = T(2) * N.xz(i, j, k) * S.s13(i, j, k);
+    T t13_w = T(2) * N.xz(i - 1, j, k) * S.s13(i - 1, j, k);
+    T t23_n = T(2) * N.yz(i, j, k) * S.s23(i, j, k);
+    T t23_s = T(2) * N.yz(i, j - 1, k) * S.s23(i, j - 1, k);
+    return (t13_e - t13_w) / g.dx + (t23_n - t23_s) / g.dy + (t33_kp - t33_k) / g.dzs[k];
+}
+
+template <typename T>
+__global__ void k_momentum(Geo<T> g, const T* u, const T* v, const T* w, const T* nut, T* fu, T* fv,
+                           T* fw, T* us, T* vs, T* ws, int first) {
+    const Dom& d = g.d;
+    int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    int k = blockIdx.z + 1;
+    if (i > d.nx || j > d.ny) return;
+    long long c = d.at(i, j, k);
+    const uint8_t f = g.flags[c];
+    Stencil<T> S{g, u, v, w};
+    Nut<T> N{d, nut};
+    if (i <= (d.perx ? d.nx : d.nx - 1)) {
+        T F = velfg_u(g, S, i, j, k) + sgs_u(g, S, N, i, j, k);
+        T Fh = first ? F : T(1.5) * F - T(0.5) * fu[c];
+        fu[c] = F;
+        us[c] = (f & F_E) ? u[c] + g.dt * Fh : T(0);
+    }
+    if (j <= (d.pery ? d.ny : d.ny - 1)) {
+        T F = velfg_v(g, S, i, j, k) + sgs_v(g, S, N, i, j, k);
+        T Fh = first ? F : T(1.5) * F - T(0.5) * fv[c];
+        fv[c] = F;
+        vs[c] = (f & F_N) ? v[c] + g.dt * Fh : T(0);
+    }
+    if (k <= (d.perz ? d.nz : d.nz - 1)) {
+        T F = velfg_w(g, S, i, j, k) + sgs_w(g, S, N, i, j, k);
+        T Fh = first ? F : T(1.5) * F - T(0.5) * fw[c];
+        fw[c] = F;
+        ws[c] = (f & F_T) ? w[c] + g.dt * Fh : T(0);
+    }
+}
+
+template <typename T>
+int launch_momentum(const Geo<T>& g, const T* u, const T* v, const T* w, const T* nut, T* fu, T* fv,
+                    T* fw, T* us, T* vs, T* ws, int first, cudaStream_t s) {
+    const Dom& d = g.d;
+    k_momentum<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(
+        g, u, v, w, nut, fu, fv, fw, us, vs, ws, first);
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 block reductions (warp shuffles, then one value per warp in shared
+// memory); deterministic for a fixed launch shape.
+
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&x)[NV]) {
+    __shared__ double sh[NV][32];
+    const int lane = (threadIdx.x + threadIdx.y * blockDim.x) & 31;
+    const int warp = (threadIdx.x + threadIdx.y * blockDim.x) >> 5;
+    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+        for (int o = 16; o > 0; o >>= 1) x[q] += __shfl_down_sync(0xffffffffu, x[q], o);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) sh[q][warp] = x[q];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            x[q] = lane < nw ? sh[q][lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) x[q] += __shfl_down_sync(0xffffffffu, x[q], o);
+        }
+    }
+}
+
+// Each block stores its partial sums; the last block to finish adds all the
+// partials in block order and returns true (with the totals in x on thread 0).
+template <int NV>
+__device__ bool grid_sum(double (&x)[NV], const Reduce& r) {
+    block_sum<NV>(x);
+    const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    __shared__ bool last;
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) r.partials[(size_t)q * nb + b] = x[q];
+        __threadfence();
+        unsigned t = atomicAdd(r.counter, 1u);
+        last = (t == nb - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    const int nt = blockDim.x * blockDim.y;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double s = 0.0;
+        for (unsigned m = tid; m < nb; m += nt) s += __ldcg(&r.partials[(size_t)q * nb + m]);
+        x[q] = s;
+    }
+    block_sum<NV>(x);
+    if (tid == 0) *r.counter = 0u;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// bondv1 on u*: inflow face copied, zero-gradient outflow, FP64 mass-flux
+// correction (one block; the plane is small), periodic face copies.
+
+template <typename T>
+__global__ void k_outflow(Geo<T> g, const T* u, T* us, T* vs, T* ws, Scalars* sc) {
+    const Dom& d = g.d;
+    const int n = d.ny * d.nz;
+    if (d.perx) {
+        for (int q = threadIdx.x; q < n; q += blockDim.x) {
+            int j = q % d.ny + 1, k = q / d.ny + 1;
+            us[d.at(0, j, k)] = us[d.at(d.nx, j, k)];
+        }
+        if (threadIdx.x == 0) { sc->mass_factor = 1.0; sc->q_in = sc->q_out = 0.0; }
+        return;
+    }
+    double x[2] = {0.0, 0.0};
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        int j = q % d.ny + 1, k = q / d.ny + 1;
+        T ui = u[d.at(0, j, k)];
+        T uo = us[d.at(d.nx - 1, j, k)];
+        us[d.at(0, j, k)] = ui;
+        x[0] += (double)ui * (double)g.dy * g.dz64[k];
+        x[1] += (double)uo * (double)g.dy * g.dz64[k];
+    }
+    block_sum<2>(x);
+    __shared__ double fac;
+    if (threadIdx.x == 0) {
+        double f = fabs(x[1]) > 1e-300 ? x[0] / x[1] : 1.0;
+        fac = f;
+        sc->mass_factor = f;
+        sc->q_in = x[0];
+        sc->q_out = x[1] * f;
+    }
+    __syncthreads();
+    const double f = fac;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        int j = q % d.ny + 1, k = q / d.ny + 1;
+        us[d.at(d.nx, j, k)] = (T)((double)us[d.at(d.nx - 1, j, k)] * f);
+    }
+}
+
+template <typename T>
+__global__ void k_wrap_faces(Dom d, T* vs, T* ws, int zaxis) {
+    int a = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    int b = blockIdx.y + 1;
+    if (a > d.nx) return;
+    if (!zaxis) vs[d.at(a, 0, b)] = vs[d.at(a, d.ny, b)];     // periodic y: a = i, b = k
+    else ws[d.at(a, b, 0)] = ws[d.at(a, b, d.nz)];            // periodic z: a = i, b = j
+}
+
+template <typename T>
+int launch_outflow(const Geo<T>& g, const T* u, T* us, T* vs, T* ws, Scalars* sc, cudaStream_t s) {
+    const Dom& d = g.d;
+    k_outflow<T><<<1, 1024, 0, s>>>(g, u, us, vs, ws, sc);
+    int n = 1;
+    if (d.pery) {
+        k_wrap_faces<T><<<dim3((d.nx + 127) / 128, d.nz), 128, 0, s>>>(d, vs, ws, 0);
+        n++;
+    }
+    if (d.perz) {
+        k_wrap_faces<T><<<dim3((d.nx + 127) / 128, d.ny), 128, 0, s>>>(d, vs, ws, 1);
+        n++;
+    }
+    return n;
+}
+
+// ---------------------------------------------------------------------------
+// press: rhs = div(u*)/dt on fluid cells; FP64 dz-weighted mean (last block)
+
+template <typename T>
+__global__ void k_rhs(Geo<T> g, const T* us, const T* vs, const T* ws, T* rhs, double vfluid, Reduce r) {
+    const Dom& d = g.d;
+    int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    int k = blockIdx.z + 1;
+    double x[1] = {0.0};
+    if (i <= d.nx && j <= d.ny) {
+        long long c = d.at(i, j, k);
+        T val = T(0);
+        if (g.flags[c] & F_FLUID) {
+            T div = (us[c] - us[c - 1]) / g.dx + (vs[c] - vs[c - d.px]) / g.dy + (ws[c] - ws[c - d.plane]) / g.dz[k];
+            val = div / g.dt;
+            x[0] = g.dz64[k] * (double)val;
+        }
+        rhs[c] = val;
+    }
+    if (grid_sum<1>(x, r)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) r.sc->rhs_mean = vfluid > 0.0 ? x[0] / vfluid : 0.0;
+    }
+}
+
+template <typename T>
+int launch_rhs(const Geo<T>& g, const T* us, const T* vs, const T* ws, T* rhs, double vfluid,
+               const Reduce& r, cudaStream_t s) {
+    const Dom& d = g.d;
+    k_rhs<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(g, us, vs, ws, rhs, vfluid, r);
+    return 1;
+}
+
+// caller-supplied rhs: zero non-fluid cells and compute the mean
+template <typename T>
+__global__ void k_rhs_mean(Geo<T> g, T* rhs, double vfluid, Reduce r) {
+    const Dom& d = g.d;
+    int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    int k = blockIdx.z + 1;
+    double x[1] = {0.0};
+    if (i <= d.nx && j <= d.ny) {
+        long long c = d.at(i, j, k);
+        if (g.flags[c] & F_FLUID) x[0] = g.dz64[k] * (double)rhs[c];
+        else rhs[c] = T(0);
+    }
+    if (grid_sum<1>(x, r)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) r.sc->rhs_mean = vfluid > 0.0 ? x[0] / vfluid : 0.0;
+    }
+}
+
+template <typename T>
+int launch_rhs_mean(const Geo<T>& g, T* rhs, double vfluid, const Reduce& r, cudaStream_t s) {
+    const Dom& d = g.d;
+    k_rhs_mean<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(g, rhs, vfluid, r);
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// press: red-black SOR half-sweep (Sec. 2.6), in place.  Colour nrd updates
+// the cells i = 1 + mod(k+j+nrd, 2) + 2 m; a colour reads only the other
+// colour, so the in-place update gives the sequential result.
+
+template <typename T>
+struct Poisson {
+    const Geo<T>& g;
+    __device__ __forceinline__ void coefs(uint8_t f, int k, T& ae, T& aw, T& an, T& as, T& at, T& ab) const {
+        ae = (f & F_E) ? g.cx : T(0);
+        aw = (f & F_W) ? g.cx : T(0);
+        an = (f & F_N) ? g.cy : T(0);
+        as = (f & F_S) ? g.cy : T(0);
+        at = (f & F_T) ? g.cT[k] : T(0);
+        ab = (f & F_B) ? g.cB[k] : T(0);
+    }
+    // sum of a_nb p_nb (neighbour indices wrapped on periodic axes)
+    __device__ __forceinline__ T nb(const T* p, int i, int j, int k, T ae, T aw, T an, T as, T at, T ab) const {
+        const Dom& d = g.d;
+        int ie = (d.perx && i == d.nx) ? 1 : i + 1;
+        int iw = (d.perx && i == 1) ? d.nx : i - 1;
+        int jn = (d.pery && j == d.ny) ? 1 : j + 1;
+        int js = (d.pery && j == 1) ? d.ny : j - 1;
+        int kt = (d.perz && k == d.nz) ? 1 : k + 1;
+        int kb = (d.perz && k == 1) ? d.nz : k - 1;
+        T s = T(0);
+        s += ae * p[d.at(ie, j, k)];
+        s += aw * p[d.at(iw, j, k)];
+        s += an * p[d.at(i, jn, k)];
+        s += as * p[d.at(i, js, k)];
+        s += at * p[d.at(i, j, kt)];
+        s += ab * p[d.at(i, j, kb)];
+        return s;
+    }
+};
+
+template <typename T>
+__global__ void k_sor_half(Geo<T> g, T* p, const T* rhs, const Scalars* sc, int nrd) {
+    const Dom& d = g.d;
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    int k = blockIdx.z + 1;
+    if (j > d.ny) return;
+    int i = 1 + ((k + j + nrd) & 1) + 2 * m;
+    if (i > d.nx) return;
+    long long c = d.at(i, j, k);
+    const uint8_t f = g.flags[c];
+    if (!(f & F_UNK)) return;
+    Poisson<T> P{g};
+    T ae, aw, an, as, at, ab;
+    P.coefs(f, k, ae, aw, an, as, at, ab);
+    T cn1 = T(1) / (ae + aw + an + as + at + ab);
+    T b = rhs[c] - (T)sc->rhs_mean;
+    T s = P.nb(p, i, j, k, ae, aw, an, as, at, ab);
+    T reltmp = g.omega * (cn1 * (s - b) - p[c]);
+    p[c] = p[c] + reltmp;
+}
+
+template <typename T>
+int launch_sor_sweep(const Geo<T>& g, T* p, const T* rhs, const Scalars* sc, cudaStream_t s) {
+    const Dom& d = g.d;
+    dim3 grid(((d.nx + 1) / 2 + 31) / 32, (d.ny + 7) / 8, d.nz);
+    k_sor_half<T><<<grid, dim3(32, 8), 0, s>>>(g, p, rhs, sc, 0);
+    k_sor_half<T><<<grid, dim3(32, 8), 0, s>>>(g, p, rhs, sc, 1);
+    return 2;
+}
+
+// FP64 residual norms and the dz-weighted p mean
+template <typename T>
+__global__ void k_residual(Geo<T> g, const T* p, const T* rhs, double tol, double vfluid, Reduce r) {
+    const Dom& d = g.d;
+    int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    int k = blockIdx.z + 1;
+    double x[3] = {0.0, 0.0, 0.0};
+    if (i <= d.nx && j <= d.ny) {
+        long long c = d.at(i, j, k);
+        const uint8_t f = g.flags[c];
+        if (f & F_UNK) {
+            Poisson<T> P{g};
+            T ae, aw, an, as, at, ab;
+            P.coefs(f, k, ae, aw, an, as, at, ab);
+            T diag = ae + aw + an + as + at + ab;
+            T b = rhs[c] - (T)r.sc->rhs_mean;
+            T res = b - (P.nb(p, i, j, k, ae, aw, an, as, at, ab) - diag * p[c]);
+            x[0] = (double)res * (double)res;
+            x[1] = (double)b * (double)b;
+        }
+        if (f & F_FLUID) x[2] = g.dz64[k] * (double)p[c];
+    }
+    if (grid_sum<3>(x, r)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            Scalars* sc = r.sc;
+            sc->res2 = x[0];
+            sc->rhs2 = x[1];
+            double rel = x[1] == 0.0 ? sqrt(x[0]) : sqrt(x[0] / x[1]);
+            sc->rel = rel;
+            sc->converged = rel <= tol;
+            sc->nonfinite = !isfinite(rel);
+            sc->p_mean = vfluid > 0.0 ? x[2] / vfluid : 0.0;
+        }
+    }
+}
+
+template <typename T>
+int launch_residual(const Geo<T>& g, const T* p, const T* rhs, double tol, double vfluid, const Reduce& r,
+                    cudaStream_t s) {
+    const Dom& d = g.d;
+    k_residual<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(g, p, rhs, tol, vfluid, r);
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// velnw: gauge (p -= dz-weighted fluid mean) and u = u* - dt grad p.
+// Reads p_in, writes the gauged p to p_out (no in-place race).
+
+template <typename T>
+__global__ void k_project(Geo<T> g, const T* us, const T* vs, const T* ws, T* u, T* v, T* w,
+                          const T* p_in, T* p_out, const Scalars* sc) {
+    const Dom& d = g.d;
+    int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    int k = blockIdx.z + 1;
+    if (i > d.nx || j > d.ny) return;
+    long long c = d.at(i, j, k);
+    const uint8_t f = g.flags[c];
+    const T pm = (T)sc->p_mean;
+    auto gp = [&](long long q) -> T { return (g.flags[q] & F_FLUID) ? p_in[q] - pm : p_in[q]; };
+    const T pc = gp(c);
+    p_out[c] = pc;
+    // u on the east face of cell i
+    if (i <= (d.perx ? d.nx : d.nx - 1)) {
+        int ie = (d.perx && i == d.nx) ? 1 : i + 1;
+        T val = (f & F_E) ? us[c] - g.dt * (gp(d.at(ie, j, k)) - pc) / g.dx : T(0);
+        u[c] = val;
+        if (d.perx && i == d.nx) u[d.at(0, j, k)] = val;
+    } else {
+        u[c] = us[c];
+    }
+    if (!d.perx && i == 1) u[d.at(0, j, k)] = us[d.at(0, j, k)];
+    // v on the north face of cell j
+    if (j <= (d.pery ? d.ny : d.ny - 1)) {
+        int jn = (d.pery && j == d.ny) ? 1 : j + 1;
+        T val = (f & F_N) ? vs[c] - g.dt * (gp(d.at(i, jn, k)) - pc) / g.dy : T(0);
+        v[c] = val;
+        if (d.pery && j == d.ny) v[d.at(i, 0, k)] = val;
+    } else {
+        v[c] = vs[c];
+    }
+    if (!d.pery && j == 1) v[d.at(i, 0, k)] = vs[d.at(i, 0, k)];
+    // w on the top face of cell k
+    if (k <= (d.perz ? d.nz : d.nz - 1)) {
+        int kt = (d.perz && k == d.nz) ? 1 : k + 1;
+        T val = (f & F_T) ? ws[c] - g.dt * (gp(d.at(i, j, kt)) - pc) / g.dzs[k] : T(0);
+        w[c] = val;
+        if (d.perz && k == d.nz) w[d.at(i, j, 0)] = val;
+    } else {
+        w[c] = ws[c];
+    }
+    if (!d.perz && k == 1) w[d.at(i, j, 0)] = ws[d.at(i, j, 0)];
+}
+
+template <typename T>
+int launch_project(const Geo<T>& g, const T* us, const T* vs, const T* ws, T* u, T* v, T* w,
+                   const T* p_in, T* p_out, const Scalars* sc, cudaStream_t s) {
+    const Dom& d = g.d;
+    k_project<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(
+        g, us, vs, ws, u, v, w, p_in, p_out, sc);
+    return 1;
+}
+
+// gauge alone (les_pressure_solve): p_out = p_in - dz-weighted fluid mean
+template <typename T>
+__global__ void k_gauge(Geo<T> g, const T* p_in, T* p_out, const Scalars* sc) {
+    const Dom& d = g.d;
+    int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    int k = blockIdx.z + 1;
+    if (i > d.nx || j > d.ny) return;
+    long long c = d.at(i, j, k);
+    p_out[c] = (g.flags[c] & F_FLUID) ? p_in[c] - (T)sc->p_mean : p_in[c];
+}
+
+template <typename T>
+int launch_gauge(const Geo<T>& g, const T* p_in, T* p_out, const Scalars* sc, cudaStream_t s) {
+    const Dom& d = g.d;
+    k_gauge<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(g, p_in, p_out, sc);
+    return 1;
+}
+
+// mean-removed rhs for inspection
+template <typename T>
+__global__ void k_rhs_eff(Geo<T> g, const T* rhs, T* out, const Scalars* sc) {
+    const Dom& d = g.d;
+    int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    int k = blockIdx.z + 1;
+    if (i > d.nx || j > d.ny) return;
+    long long c = d.at(i, j, k);
+    out[c] = (g.flags[c] & F_FLUID) ? rhs[c] - (T)sc->rhs_mean : T(0);
+}
+
+template <typename T>
+int launch_rhs_eff(const Geo<T>& g, const T* rhs, T* out, const Scalars* sc, cudaStream_t s) {
+    const Dom& d = g.d;
+    k_rhs_eff<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(g, rhs, out, sc);
+    return 1;
+}
+
+int max_reduce_blocks(const Dom& d) { return ((d.nx + 31) / 32) * ((d.ny + 7) / 8) * d.nz; }
+
+#define LES_INSTANTIATE(T)                                                                              \
+    template int launch_bc<T>(const Geo<T>&, T*, T*, T*, const double*, double, uint64_t, long long,    \
+                              cudaStream_t);                                                            \
+    template int launch_nut<T>(const Geo<T>&, const T*, const T*, const T*, T*, cudaStream_t);          \
+    template int launch_momentum<T>(const Geo<T>&, const T*, const T*, const T*, const T*, T*, T*, T*,  \
+                                    T*, T*, T*, int, cudaStream_t);                                     \
+    template int launch_outflow<T>(const Geo<T>&, const T*, T*, T*, T*, Scalars*, cudaStream_t);        \
+    template int launch_rhs<T>(const Geo<T>&, const T*, const T*, const T*, T*, double, const Reduce&,  \
+                               cudaStream_t);                                                           \
+    template int launch_rhs_mean<T>(const Geo<T>&, T*, double, const Reduce&, cudaStream_t);            \
+    template int launch_sor_sweep<T>(const Geo<T>&, T*, const T*, const Scalars*, cudaStream_t);        \
+    template int launch_residual<T>(const Geo<T>&, const T*, const T*, double, double, const Reduce&,   \
+                                    cudaStream_t);                                                      \
+    template int launch_project<T>(const Geo<T>&, const T*, const T*, const T*, T*, T*, T*, const T*,   \
+                                   T*, const Scalars*, cudaStream_t);                                   \
+    template int launch_rhs_eff<T>(const Geo<T>&, const T*, T*, const Scalars*, cudaStream_t);          \
+    template int launch_gauge<T>(const Geo<T>&, const T*, T*, const Scalars*, cudaStream_t);
+
+LES_INSTANTIATE(float)
+LES_INSTANTIATE(double)
+
+}  // namespace les

@@ -1,0 +1,282 @@
+"""Thin ctypes binding of the C ABI in ``include/les.h`` (argument marshalling only).
+
+Every function keeps the C name and signature; host arrays are numpy arrays in
+the I/O layout of the header.  All computation happens in the CUDA library:
+if ``lib/libles.so`` is missing this module raises instead of falling back.
+``Domain`` is a small convenience wrapper over the same calls.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LES_OK, LES_ENOCONV = 0, 1
+LES_EINVAL, LES_ENOMEM, LES_ECUDA, LES_ETIMEOUT, LES_ENONFINITE, LES_ESTATE = -1, -2, -3, -4, -5, -6
+LES_BC_INOUT, LES_BC_FREESLIP, LES_BC_WALL, LES_BC_PERIODIC = 0, 1, 2, 3
+LES_FP32, LES_FP64 = 0, 1
+(LES_AUX_NUT, LES_AUX_RHS, LES_AUX_USTAR, LES_AUX_VSTAR, LES_AUX_WSTAR,
+ LES_AUX_FU, LES_AUX_FV, LES_AUX_FW) = range(8)
+
+
+class les_grid_t(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32), ("bc_z", ctypes.c_int32),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("dz", ctypes.POINTER(ctypes.c_double)),
+                ("dt", ctypes.c_double), ("cs", ctypes.c_double), ("nu", ctypes.c_double),
+                ("omega", ctypes.c_double), ("tol", ctypes.c_double),
+                ("max_sweeps", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("fixed_sweeps", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("turb", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class les_stats_t(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("rel_residual", ctypes.c_double), ("rhs_norm", ctypes.c_double),
+                ("rhs_mean", ctypes.c_double), ("mass_factor", ctypes.c_double),
+                ("q_in", ctypes.c_double), ("q_out", ctypes.c_double),
+                ("p_mean", ctypes.c_double), ("step", ctypes.c_int64),
+                ("launches", ctypes.c_int64)]
+
+
+class les_timing_t(ctypes.Structure):
+    _fields_ = [("ms_momentum", ctypes.c_double), ("ms_sor", ctypes.c_double),
+                ("ms_residual", ctypes.c_double), ("ms_project", ctypes.c_double),
+                ("steps", ctypes.c_int64), ("sor_sweeps", ctypes.c_int64),
+                ("sor_launches", ctypes.c_int64), ("launches", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = False):
+    """Load ``libles.so``; raises if it is missing (no CPU fallback exists)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"LES CUDA library not built ({path}); run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.les_version.restype = ctypes.c_char_p
+        L.les_last_error.restype = ctypes.c_char_p
+        L.les_last_error.argtypes = [vp]
+        L.les_create.argtypes = [ctypes.POINTER(les_grid_t), vp, vp, vp, ctypes.POINTER(vp)]
+        L.les_destroy.argtypes = [vp]
+        L.les_destroy.restype = None
+        L.les_set_fields.argtypes = [vp, vp, vp, vp, vp]
+        L.les_get_fields.argtypes = [vp, vp, vp, vp, vp]
+        L.les_set_inflow.argtypes = [vp, vp, ctypes.c_double, ctypes.c_uint64]
+        L.les_step.argtypes = [vp, i32, ctypes.POINTER(les_stats_t)]
+        L.les_pressure_solve.argtypes = [vp, vp, ctypes.POINTER(les_stats_t)]
+        L.les_get_aux.argtypes = [vp, i32, vp]
+        L.les_get_state.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
+        L.les_set_state.argtypes = [vp, vp, ctypes.c_size_t]
+        L.les_set_timing.argtypes = [vp, i32]
+        L.les_get_timing.argtypes = [vp, ctypes.POINTER(les_timing_t)]
+        for name in ("les_set_timing", "les_get_timing", "les_create", "les_set_fields", "les_get_fields", "les_set_inflow", "les_step",
+                     "les_pressure_solve", "les_get_aux", "les_get_state", "les_set_state"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+class LesError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+def _check(rc, h=None):
+    if rc < 0:
+        msg = lib().les_last_error(h)
+        raise LesError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+# ---------------------------------------------------------------------------
+# C-named functions
+
+def les_version() -> str:
+    return lib().les_version().decode()
+
+
+def les_create(grid: les_grid_t, solid: np.ndarray, inflow_u: np.ndarray, stream=None) -> int:
+    h = ctypes.c_void_p()
+    rc = lib().les_create(ctypes.byref(grid), _ptr(solid), _ptr(inflow_u), stream, ctypes.byref(h))
+    _check(rc)
+    return h.value
+
+
+def les_destroy(h):
+    lib().les_destroy(h)
+
+
+def les_set_fields(h, u, v, w, p):
+    return _check(lib().les_set_fields(h, _ptr(u), _ptr(v), _ptr(w), _ptr(p)), h)
+
+
+def les_get_fields(h, u, v, w, p):
+    return _check(lib().les_get_fields(h, _ptr(u), _ptr(v), _ptr(w), _ptr(p)), h)
+
+
+def les_set_inflow(h, inflow_u, turb, seed):
+    return _check(lib().les_set_inflow(h, _ptr(inflow_u), float(turb), int(seed)), h)
+
+
+def les_step(h, nsteps, stats: les_stats_t | None = None):
+    return _check(lib().les_step(h, nsteps, ctypes.byref(stats) if stats is not None else None), h)
+
+
+def les_pressure_solve(h, rhs, stats: les_stats_t | None = None):
+    return _check(lib().les_pressure_solve(h, _ptr(rhs), ctypes.byref(stats) if stats is not None else None), h)
+
+
+def les_get_aux(h, which, out):
+    return _check(lib().les_get_aux(h, which, _ptr(out)), h)
+
+
+def les_get_state(h, buf, length: ctypes.c_size_t):
+    return _check(lib().les_get_state(h, buf, ctypes.byref(length)), h)
+
+
+def les_set_state(h, buf, length):
+    return _check(lib().les_set_state(h, buf, length), h)
+
+
+def les_set_timing(h, enable):
+    return _check(lib().les_set_timing(h, 1 if enable else 0), h)
+
+
+def les_get_timing(h, t: les_timing_t):
+    return _check(lib().les_get_timing(h, ctypes.byref(t)), h)
+
+
+def les_last_error(h) -> str:
+    m = lib().les_last_error(h)
+    return m.decode() if m else ""
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+
+def current_stream():
+    """The current torch CUDA stream handle (torch supplies streams only)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return None
+
+
+class Domain:
+    """One LES domain on the GPU, built from a ``scene.Scene``."""
+
+    def __init__(self, sc, precision=LES_FP32, stream="torch", **override):
+        prm = sc.params()
+        prm.update(override)
+        self.nx, self.ny, self.nz = prm["nx"], prm["ny"], prm["nz"]
+        self.dtype = np.float64 if precision == LES_FP64 else np.float32
+        self._dz = np.ascontiguousarray(sc.dz, dtype=np.float64)
+        g = les_grid_t(nx=prm["nx"], ny=prm["ny"], nz=prm["nz"], bc_x=prm["bc_x"], bc_y=prm["bc_y"],
+                       bc_z=prm["bc_z"], dx=prm["dx"], dy=prm["dy"],
+                       dz=self._dz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                       dt=prm["dt"], cs=prm["cs"], nu=prm["nu"], omega=prm["omega"], tol=prm["tol"],
+                       max_sweeps=prm["max_sweeps"], check_every=prm["check_every"],
+                       fixed_sweeps=prm["fixed_sweeps"], precision=precision, turb=prm["turb"],
+                       seed=prm["seed"])
+        solid = np.ascontiguousarray(sc.solid, dtype=np.uint8)
+        inflow = np.ascontiguousarray(sc.inflow_u, dtype=np.float64)
+        st = current_stream() if stream == "torch" else stream
+        self.h = les_create(g, solid, inflow, st)
+        if sc.u0 is not None:
+            self.set_fields(sc.u0, sc.v0, sc.w0, sc.p0)
+
+    def close(self):
+        if getattr(self, "h", None):
+            les_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def shapes(self):
+        nx, ny, nz = self.nx, self.ny, self.nz
+        return (nz, ny, nx + 1), (nz, ny + 1, nx), (nz + 1, ny, nx), (nz, ny, nx)
+
+    def _c(self, a):
+        return None if a is None else np.ascontiguousarray(a, dtype=self.dtype)
+
+    def set_fields(self, u=None, v=None, w=None, p=None):
+        les_set_fields(self.h, self._c(u), self._c(v), self._c(w), self._c(p))
+
+    def fields(self):
+        out = [np.empty(s, dtype=self.dtype) for s in self.shapes()]
+        les_get_fields(self.h, *out)
+        return out
+
+    def step(self, n=1) -> dict:
+        st = les_stats_t()
+        rc = les_step(self.h, n, st)
+        d = {f: getattr(st, f) for f, _ in les_stats_t._fields_}
+        d["rc"] = rc
+        return d
+
+    def pressure_solve(self, rhs=None) -> dict:
+        st = les_stats_t()
+        rc = les_pressure_solve(self.h, self._c(rhs), st)
+        d = {f: getattr(st, f) for f, _ in les_stats_t._fields_}
+        d["rc"] = rc
+        return d
+
+    def aux(self, which) -> np.ndarray:
+        nx, ny, nz = self.nx, self.ny, self.nz
+        shape = {LES_AUX_NUT: (nz, ny, nx), LES_AUX_RHS: (nz, ny, nx),
+                 LES_AUX_USTAR: (nz, ny, nx + 1), LES_AUX_FU: (nz, ny, nx + 1),
+                 LES_AUX_VSTAR: (nz, ny + 1, nx), LES_AUX_FV: (nz, ny + 1, nx),
+                 LES_AUX_WSTAR: (nz + 1, ny, nx), LES_AUX_FW: (nz + 1, ny, nx)}[which]
+        out = np.empty(shape, dtype=self.dtype)
+        les_get_aux(self.h, which, out)
+        return out
+
+    def get_state(self) -> bytes:
+        n = ctypes.c_size_t(0)
+        les_get_state(self.h, None, n)
+        buf = ctypes.create_string_buffer(n.value)
+        les_get_state(self.h, buf, n)
+        return buf.raw
+
+    def set_state(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        les_set_state(self.h, buf, len(blob))
+
+    def set_timing(self, enable=True):
+        les_set_timing(self.h, enable)
+
+    def timing(self) -> dict:
+        t = les_timing_t()
+        les_get_timing(self.h, t)
+        return {f: getattr(t, f) for f, _ in les_timing_t._fields_}
+
+    def set_inflow(self, inflow_u, turb, seed):
+        les_set_inflow(self.h, np.ascontiguousarray(inflow_u, dtype=np.float64), turb, seed)

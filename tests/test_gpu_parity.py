@@ -1,0 +1,213 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle.
+
+The FP64 instantiation of the kernels must agree with the oracle to ~1e-11
+(same discretisation, only rounding order differs), which separates indexing
+mistakes from rounding.  The FP32 production path must keep the max relative
+velocity error <= 1e-4 after 20 steps of the 64x64x32 lattice workload.
+Relative error = max |gpu - oracle| / max |oracle| over the array."""
+
+import numpy as np
+import pytest
+
+from oracle.oracle import (Oracle, A_U, A_V, A_W, A_P, A_NUT, A_RHS, A_US, A_VS, A_WS,
+                           A_FU, A_FV, A_FW)
+from paper_1504_02264_gb300 import scene
+
+pytestmark = pytest.mark.gpu
+
+les = pytest.importorskip("paper_1504_02264_gb300.les")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    les.lib()
+    yield
+
+
+def rel(a, b):
+    scale = max(np.abs(b).max(), 1e-300)
+    return float(np.abs(np.asarray(a, np.float64) - b).max() / scale)
+
+
+def city(nx=40, ny=24, nz=12, turb=0.0, periodic_y=False, seed=3, **kw):
+    rng = np.random.default_rng(seed)
+    solid = np.zeros((nz, ny, nx), np.uint8)
+    for _ in range(4):
+        x0 = int(rng.integers(4, nx - 10))
+        y0 = int(rng.integers(1, ny - 6))
+        h = int(rng.integers(2, nz - 2))
+        solid[:h, y0:y0 + 5, x0:x0 + 6] = 1
+    bc = (scene.BC_INOUT, scene.BC_PERIODIC if periodic_y else scene.BC_FREESLIP, scene.BC_WALL)
+    return scene.box_scene(nx, ny, nz, dz=scene.stretched_dz(nz), solid=solid, bc=bc, turb=turb,
+                           seed=seed, **kw)
+
+
+def compare_fields(dom, o, tol):
+    errs = {}
+    for name, g, r in zip("uvwp", dom.fields(), o.fields()):
+        errs[name] = rel(g, r)
+    assert max(errs.values()) <= tol, errs
+    return errs
+
+
+# ---------------------------------------------------------------------------
+# FP64: discretisation parity, phase by phase and over several steps
+
+@pytest.mark.parametrize("turb", [0.0, 0.1])
+def test_fp64_phases_one_step(turb):
+    sc = city(turb=turb, fixed_sweeps=1, max_sweeps=15)
+    d = les.Domain(sc, precision=les.LES_FP64)
+    o = Oracle(sc)
+    d.step(1)
+    o.step(1)
+    pairs = [(les.LES_AUX_NUT, A_NUT), (les.LES_AUX_RHS, A_RHS), (les.LES_AUX_USTAR, A_US),
+             (les.LES_AUX_VSTAR, A_VS), (les.LES_AUX_WSTAR, A_WS), (les.LES_AUX_FU, A_FU),
+             (les.LES_AUX_FV, A_FV), (les.LES_AUX_FW, A_FW)]
+    for aux, arr in pairs:
+        assert rel(d.aux(aux), o.get(arr)) <= 1e-12, aux
+    compare_fields(d, o, 1e-11)
+
+
+@pytest.mark.parametrize("case", ["city", "city_turb", "periodic_y", "odd_sizes", "tiny", "periodic_xyz"])
+def test_fp64_multi_step(case):
+    if case == "city":
+        sc = city(fixed_sweeps=1, max_sweeps=20)
+    elif case == "city_turb":
+        sc = city(turb=0.1, fixed_sweeps=1, max_sweeps=20)
+    elif case == "periodic_y":
+        sc = city(periodic_y=True, ny=24, turb=0.1, fixed_sweeps=1, max_sweeps=20)
+    elif case == "odd_sizes":
+        sc = city(nx=33, ny=17, nz=9, fixed_sweeps=1, max_sweeps=20)
+    elif case == "tiny":
+        sc = scene.box_scene(2, 2, 2, fixed_sweeps=1, max_sweeps=3)
+    else:
+        n = 16
+        sc = scene.box_scene(n, n, 4, dx=0.4, dy=0.4, dz=np.full(4, 0.4),
+                             bc=(scene.BC_PERIODIC,) * 3, nu=0.01, dt=0.02, fixed_sweeps=1,
+                             max_sweeps=30)
+        u, v, w, p = scene.random_fields(sc, 5, amp=0.3)
+        u[:, :, 0] = u[:, :, -1]
+        v[:, 0, :] = v[:, -1, :]
+        w[0] = w[-1]
+        sc.u0, sc.v0, sc.w0, sc.p0 = u, v, w, 0 * p
+    d = les.Domain(sc, precision=les.LES_FP64)
+    o = Oracle(sc)
+    for _ in range(5):
+        sd = d.step(1)
+        o.step(1)
+        so = o.stats()
+        assert abs(sd["rel_residual"] - so["rel_residual"]) <= 1e-9 * max(1.0, so["rel_residual"])
+        assert abs(sd["mass_factor"] - so["mass_factor"]) <= 1e-12
+    compare_fields(d, o, 1e-11)
+
+
+def test_fp64_pressure_solve_random_rhs():
+    sc = city(fixed_sweeps=1, max_sweeps=60)
+    rhs = scene.random_rhs(sc, 9)
+    d = les.Domain(sc, precision=les.LES_FP64)
+    o = Oracle(sc)
+    sd = d.pressure_solve(rhs)
+    o.pressure_solve(rhs)
+    assert rel(d.fields()[3], o.get(A_P)) <= 1e-11
+    assert abs(sd["rel_residual"] - o.stats()["rel_residual"]) <= 1e-10
+
+
+def test_fp64_tolerance_mode_same_sweeps():
+    sc = city(fixed_sweeps=0, tol=1e-6, max_sweeps=5000, check_every=10)
+    d = les.Domain(sc, precision=les.LES_FP64)
+    o = Oracle(sc)
+    for _ in range(3):
+        sd = d.step(1)
+        o.step(1)
+        assert sd["sweeps"] == o.stats()["sweeps"]
+        assert sd["rc"] == 0 and sd["rel_residual"] <= 1e-6
+    compare_fields(d, o, 1e-10)
+
+
+# ---------------------------------------------------------------------------
+# FP32 production path
+
+def test_fp32_lattice_20_steps_parity():
+    """64x64x32 lattice, 20 steps, exactly 50 sweeps per step: max relative
+    velocity error against the FP64 oracle <= 1e-4."""
+    sc = scene.lattice_scene(0)
+    d = les.Domain(sc, precision=les.LES_FP32)
+    o = Oracle(sc)
+    d.step(20)
+    o.step(20)
+    g = d.fields()
+    r = o.fields()
+    vel_scale = max(np.abs(a).max() for a in r[:3])
+    err = max(np.abs(np.asarray(a, np.float64) - b).max() for a, b in zip(g[:3], r[:3])) / vel_scale
+    print(f"FP32 lattice 20 steps: max relative velocity error {err:.3e}")
+    assert err <= 1e-4
+
+
+def test_fp32_phases_and_solve():
+    sc = city(turb=0.1, fixed_sweeps=1, max_sweeps=40)
+    d = les.Domain(sc, precision=les.LES_FP32)
+    o = Oracle(sc)
+    d.step(3)
+    o.step(3)
+    for aux, arr in [(les.LES_AUX_NUT, A_NUT), (les.LES_AUX_USTAR, A_US), (les.LES_AUX_RHS, A_RHS)]:
+        assert rel(d.aux(aux), o.get(arr)) <= 2e-4, aux
+    compare_fields(d, o, 2e-4)
+
+
+def test_fp32_converged_step_is_divergence_free():
+    """Tolerance mode: every step reaches rel. residual 1e-6 and the projected
+    GPU velocity has |div u| <= ~1e-6 of |div u*| (checked by the oracle)."""
+    sc = city(turb=0.1, fixed_sweeps=0, tol=1e-6, max_sweeps=20000, check_every=10)
+    d = les.Domain(sc, precision=les.LES_FP32)
+    for _ in range(3):
+        st = d.step(1)
+        assert st["rc"] == 0 and st["rel_residual"] <= 1e-6
+    ustar_div = Oracle(sc)
+    ustar_div.set(A_U, d.aux(les.LES_AUX_USTAR).astype(np.float64))
+    ustar_div.set(A_V, d.aux(les.LES_AUX_VSTAR).astype(np.float64))
+    ustar_div.set(A_W, d.aux(les.LES_AUX_WSTAR).astype(np.float64))
+    div_star = ustar_div.divergence()
+    chk = Oracle(sc)
+    u, v, w, p = d.fields()
+    chk.set_fields(u.astype(np.float64), v.astype(np.float64), w.astype(np.float64), p.astype(np.float64))
+    div = chk.divergence()
+    ratio = np.linalg.norm(div) / np.linalg.norm(div_star)
+    assert ratio <= 5e-6, ratio
+
+
+# ---------------------------------------------------------------------------
+# checkpoint / restart and error paths
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_checkpoint_resume_bitwise(prec):
+    p = les.LES_FP64 if prec == "fp64" else les.LES_FP32
+    sc = city(turb=0.1, fixed_sweeps=0, tol=1e-5, max_sweeps=3000, check_every=10)
+    a = les.Domain(sc, precision=p)
+    a.step(4)
+    ref = a.fields()
+    b = les.Domain(sc, precision=p)
+    b.step(2)
+    blob = b.get_state()
+    c = les.Domain(sc, precision=p)
+    c.set_state(blob)
+    c.step(2)
+    for x, y in zip(ref, c.fields()):
+        assert np.array_equal(x, y)
+
+
+def test_set_state_rejects_other_grid():
+    a = les.Domain(city(), precision=les.LES_FP32)
+    b = les.Domain(city(nx=42), precision=les.LES_FP32)
+    with pytest.raises(les.LesError) as e:
+        b.set_state(a.get_state())
+    assert e.value.code == les.LES_ESTATE
+
+
+def test_no_convergence_status():
+    sc = city(fixed_sweeps=0, tol=1e-14, max_sweeps=20, check_every=10)
+    d = les.Domain(sc, precision=les.LES_FP32)
+    st = d.step(1)
+    assert st["rc"] == les.LES_ENOCONV and st["sweeps"] == 20
