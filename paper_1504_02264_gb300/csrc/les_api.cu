@@ -16,8 +16,8 @@ namespace {
 const char* kVersion = "les-gb300 0.1 (sm_103a)";
 
 // packing kernels between the padded device layout and the dense I/O layout
-template <typename T>
-__global__ void k_pack(Dom d, const T* src, T* dst, int i0, int j0, int k0, int ni, int nj, int nk) {
+template <typename S, typename T>
+__global__ void k_pack(Dom d, const S* src, T* dst, int i0, int j0, int k0, int ni, int nj, int nk) {
     long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long n = (long long)ni * nj * nk;
     if (q >= n) return;
@@ -25,10 +25,10 @@ __global__ void k_pack(Dom d, const T* src, T* dst, int i0, int j0, int k0, int 
     long long r = q / ni;
     int j = (int)(r % nj);
     int k = (int)(r / nj);
-    dst[q] = src[d.at(i0 + i, j0 + j, k0 + k)];
+    dst[q] = (T)src[d.at(i0 + i, j0 + j, k0 + k)];
 }
-template <typename T>
-__global__ void k_unpack(Dom d, const T* src, T* dst, int i0, int j0, int k0, int ni, int nj, int nk) {
+template <typename S, typename T>
+__global__ void k_unpack(Dom d, const S* src, T* dst, int i0, int j0, int k0, int ni, int nj, int nk) {
     long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long n = (long long)ni * nj * nk;
     if (q >= n) return;
@@ -36,7 +36,7 @@ __global__ void k_unpack(Dom d, const T* src, T* dst, int i0, int j0, int k0, in
     long long r = q / ni;
     int j = (int)(r % nj);
     int k = (int)(r / nj);
-    dst[d.at(i0 + i, j0 + j, k0 + k)] = src[q];
+    dst[d.at(i0 + i, j0 + j, k0 + k)] = (T)src[q];
 }
 
 // open-face flags from the padded solid mask (ghost cells are fluid and are
@@ -80,12 +80,14 @@ struct les_s {
     // device arrays (element type per precision)
     void *u = nullptr, *v = nullptr, *w = nullptr, *us = nullptr, *vs = nullptr, *ws = nullptr;
     void *fu = nullptr, *fv = nullptr, *fw = nullptr, *nut = nullptr, *rhs = nullptr, *tmp = nullptr;
-    void* p[2] = {nullptr, nullptr};
+    double* ph[2] = {nullptr, nullptr};   // FP64 pressure (velnw writes the gauged copy to the other)
+    void *dl = nullptr, *rr = nullptr;    // SOR correction and its FP64-formed right-hand side
     void* stage = nullptr;         // dense I/O staging
     size_t stage_elems = 0;
     uint8_t* flags = nullptr;
     void *kdz = nullptr, *kdzs = nullptr, *kcT = nullptr, *kcB = nullptr, *kdel = nullptr;
     double* dz64 = nullptr;
+    double *dzs64 = nullptr, *cT64 = nullptr, *cB64 = nullptr;
     double* inflow64 = nullptr;
     double* partials = nullptr;
     unsigned* counter = nullptr;
@@ -149,26 +151,28 @@ size_t io_elems(const les_s* h, int stag) {
     return (size_t)ni * nj * nk;
 }
 
-template <typename T>
+// host (type T, dense) -> device array of type D (padded)
+template <typename T, typename D = T>
 int upload(les_s* h, void* dev, int stag, const void* host, size_t stage_off) {
     int i0, j0, k0, ni, nj, nk;
     io_box(h, stag, i0, j0, k0, ni, nj, nk);
     size_t n = (size_t)ni * nj * nk;
     T* st = (T*)h->stage + stage_off;
     CK(cudaMemcpyAsync(st, host, n * sizeof(T), cudaMemcpyHostToDevice, h->stream));
-    k_unpack<T><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->d, st, (T*)dev, i0, j0, k0, ni, nj, nk);
+    k_unpack<T, D><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->d, st, (D*)dev, i0, j0, k0, ni, nj, nk);
     h->launches++;
     CK(cudaGetLastError());
     return LES_OK;
 }
 
-template <typename T>
+// device array of type D (padded) -> host (type T, dense)
+template <typename T, typename D = T>
 int download(les_s* h, const void* dev, int stag, void* host, size_t stage_off) {
     int i0, j0, k0, ni, nj, nk;
     io_box(h, stag, i0, j0, k0, ni, nj, nk);
     size_t n = (size_t)ni * nj * nk;
     T* st = (T*)h->stage + stage_off;
-    k_pack<T><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->d, (const T*)dev, st, i0, j0, k0, ni, nj, nk);
+    k_pack<D, T><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->d, (const D*)dev, st, i0, j0, k0, ni, nj, nk);
     h->launches++;
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(host, st, n * sizeof(T), cudaMemcpyDeviceToHost, h->stream));
@@ -194,6 +198,13 @@ Geo<T> geo(les_s* h) {
     g.cB = (const T*)h->kcB;
     g.delta2 = (const T*)h->kdel;
     g.dz64 = h->dz64;
+    g.dx64 = h->g.dx;
+    g.dy64 = h->g.dy;
+    g.cx64 = 1.0 / (h->g.dx * h->g.dx);
+    g.cy64 = 1.0 / (h->g.dy * h->g.dy);
+    g.dzs64 = h->dzs64;
+    g.cT64 = h->cT64;
+    g.cB64 = h->cB64;
     g.flags = h->flags;
     return g;
 }
@@ -223,22 +234,36 @@ double elapsed(les_s* h, int a, int b) {
     return ms;
 }
 
-// press: SOR iterations under the stop rule, FP64 residual, gauge mean
+// press: SOR iterations under the stop rule.  The FP64 pressure ph[cur] is
+// refined by batches of sweeps on the correction (see k_refine); the FP64
+// relative residual is tested after each batch of check_every sweeps and at
+// max_sweeps, exactly where the sequential algorithm tests it.
 template <typename T>
 int sor_solve(les_s* h) {
     Geo<T> g = geo<T>(h);
     Reduce r = reducer(h);
-    T* p = (T*)h->p[h->cur];
+    T* dl = (T*)h->dl;
+    T* rr = (T*)h->rr;
     const T* rhs = (const T*)h->rhs;
     const les_grid_t& G = h->g;
     int sweeps = 0;
+    rec(h, 2);
+    h->launches += launch_refine<T>(g, h->ph[h->cur], nullptr, dl, rhs, rr, 0, G.tol, h->vfluid, r, h->stream);
+    rec(h, 3);
+    CK(cudaGetLastError());
+    if (h->timing) {
+        CK(cudaEventSynchronize(h->ev[3]));
+        h->tm.ms_residual += elapsed(h, 2, 3);
+    }
     auto batch = [&](int n) -> int {
         rec(h, 2);
         long long l0 = h->launches;
-        for (int s = 0; s < n; ++s) h->launches += launch_sor_sweep<T>(g, p, rhs, h->sc, h->stream);
+        for (int s = 0; s < n; ++s) h->launches += launch_sor_sweep<T>(g, dl, rr, s == 0, h->stream);
         long long nl = h->launches - l0;
         rec(h, 3);
-        h->launches += launch_residual<T>(g, p, rhs, G.tol, h->vfluid, r, h->stream);
+        h->launches += launch_refine<T>(g, h->ph[h->cur], h->ph[1 - h->cur], dl, rhs, rr, 1, G.tol, h->vfluid,
+                                        r, h->stream);
+        h->cur = 1 - h->cur;
         rec(h, 4);
         CK(cudaGetLastError());
         int rc = fetch_scalars(h);
@@ -273,7 +298,7 @@ template <typename T>
 int project(les_s* h) {
     Geo<T> g = geo<T>(h);
     h->launches += launch_project<T>(g, (const T*)h->us, (const T*)h->vs, (const T*)h->ws, (T*)h->u, (T*)h->v,
-                                     (T*)h->w, (const T*)h->p[h->cur], (T*)h->p[1 - h->cur], h->sc, h->stream);
+                                     (T*)h->w, h->ph[h->cur], h->ph[1 - h->cur], h->sc, h->stream);
     CK(cudaGetLastError());
     h->cur = 1 - h->cur;
     return LES_OK;
@@ -380,6 +405,9 @@ int init_tables(les_s* h) {
     if ((rc = upload_table<T>(h, h->kcB, cB))) return rc;
     if ((rc = upload_table<T>(h, h->kdel, del))) return rc;
     if ((rc = upload_table<double>(h, h->dz64, dzp))) return rc;
+    if ((rc = upload_table<double>(h, h->dzs64, dzs))) return rc;
+    if ((rc = upload_table<double>(h, h->cT64, cT))) return rc;
+    if ((rc = upload_table<double>(h, h->cB64, cB))) return rc;
     return LES_OK;
 }
 
@@ -411,15 +439,20 @@ int create_impl(les_s* h, const uint8_t* solid) {
     const size_t B = h->n * h->es;
     int rc;
     void** fields[] = {&h->u, &h->v, &h->w, &h->us, &h->vs, &h->ws, &h->fu, &h->fv, &h->fw,
-                       &h->nut, &h->rhs, &h->tmp, &h->p[0], &h->p[1]};
+                       &h->nut, &h->rhs, &h->tmp, &h->dl, &h->rr};
     for (void** f : fields)
         if ((rc = dalloc(h, f, B))) return rc;
+    for (double*& f : h->ph)
+        if ((rc = dalloc(h, (void**)&f, h->n * sizeof(double)))) return rc;
     if ((rc = dalloc(h, (void**)&h->flags, h->n))) return rc;
     const size_t nt = (size_t)G.nz + 2;
     void** tabs[] = {&h->kdz, &h->kdzs, &h->kcT, &h->kcB, &h->kdel};
     for (void** t : tabs)
         if ((rc = dalloc(h, t, nt * h->es))) return rc;
     if ((rc = dalloc(h, (void**)&h->dz64, nt * sizeof(double)))) return rc;
+    if ((rc = dalloc(h, (void**)&h->dzs64, nt * sizeof(double)))) return rc;
+    if ((rc = dalloc(h, (void**)&h->cT64, nt * sizeof(double)))) return rc;
+    if ((rc = dalloc(h, (void**)&h->cB64, nt * sizeof(double)))) return rc;
     if ((rc = dalloc(h, (void**)&h->inflow64, nt * sizeof(double)))) return rc;
     const int nb = max_reduce_blocks(d);
     if ((rc = dalloc(h, (void**)&h->partials, (size_t)3 * nb * sizeof(double)))) return rc;
@@ -449,7 +482,7 @@ int create_impl(les_s* h, const uint8_t* solid) {
     CK(cudaMemcpyAsync(st8, tmp.data(), tmp.size(), cudaMemcpyHostToDevice, h->stream));
     {
         size_t n = tmp.size();
-        k_unpack<uint8_t><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(d, st8, solid_d, 1, 1, 1, G.nx, G.ny, G.nz);
+        k_unpack<uint8_t, uint8_t><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(d, st8, solid_d, 1, 1, 1, G.nx, G.ny, G.nz);
         k_flags<<<dim3((G.nx + 31) / 32, (G.ny + 7) / 8, G.nz), dim3(32, 8), 0, h->stream>>>(d, solid_d, h->flags);
         CK(cudaGetLastError());
     }
@@ -470,7 +503,7 @@ int set_fields_impl(les_s* h, const void* u, const void* v, const void* w, const
     off += io_elems(h, 2);
     if (w && (rc = upload<T>(h, h->w, 3, w, off))) return rc;
     off += io_elems(h, 3);
-    if (p && (rc = upload<T>(h, h->p[h->cur], 0, p, off))) return rc;
+    if (p && (rc = upload<T, double>(h, h->ph[h->cur], 0, p, off))) return rc;
     return LES_OK;
 }
 
@@ -484,7 +517,7 @@ int get_fields_impl(les_s* h, void* u, void* v, void* w, void* p) {
     off += io_elems(h, 2);
     if (w && (rc = download<T>(h, h->w, 3, w, off))) return rc;
     off += io_elems(h, 3);
-    if (p && (rc = download<T>(h, h->p[h->cur], 0, p, off))) return rc;
+    if (p && (rc = download<T, double>(h, h->ph[h->cur], 0, p, off))) return rc;
     CK(cudaStreamSynchronize(h->stream));
     return LES_OK;
 }
@@ -528,9 +561,7 @@ int pressure_solve_impl(les_s* h, const void* rhs, les_stats_t* st) {
     int rc = sor_solve<T>(h);
     if (rc < 0) return rc;
     // gauge: p_out = p - mean (velocities untouched)
-    T* pin = (T*)h->p[h->cur];
-    T* pout = (T*)h->p[1 - h->cur];
-    h->launches += launch_gauge<T>(g, pin, pout, h->sc, h->stream);
+    h->launches += launch_gauge<T>(g, h->ph[h->cur], h->ph[1 - h->cur], h->sc, h->stream);
     CK(cudaGetLastError());
     h->cur = 1 - h->cur;
     CK(cudaStreamSynchronize(h->stream));
@@ -550,7 +581,7 @@ struct StateHeader {
 constexpr uint64_t kMagic = 0x4c45534742333030ull;  // "LESGB300"
 
 size_t state_size(const les_s* h) {
-    return sizeof(StateHeader) + 7 * h->n * h->es + h->inflow.size() * sizeof(double);
+    return sizeof(StateHeader) + 6 * h->n * h->es + h->n * sizeof(double) + h->inflow.size() * sizeof(double);
 }
 
 }  // namespace
@@ -672,10 +703,10 @@ int les_get_state(les_handle h, void* buf, size_t* len) {
     char* b = (char*)buf;
     memcpy(b, &hd, sizeof hd);
     b += sizeof hd;
-    const void* arrs[] = {h->u, h->v, h->w, h->p[h->cur], h->fu, h->fv, h->fw};
-    const size_t B = h->n * h->es;
-    for (const void* a : arrs) {
-        CK(cudaMemcpyAsync(b, a, B, cudaMemcpyDeviceToHost, h->stream));
+    const void* arrs[] = {h->u, h->v, h->w, h->fu, h->fv, h->fw, h->ph[h->cur]};
+    for (int a = 0; a < 7; ++a) {
+        const size_t B = h->n * (a == 6 ? sizeof(double) : h->es);
+        CK(cudaMemcpyAsync(b, arrs[a], B, cudaMemcpyDeviceToHost, h->stream));
         b += B;
     }
     CK(cudaStreamSynchronize(h->stream));
@@ -693,10 +724,10 @@ int les_set_state(les_handle h, const void* buf, size_t len) {
         hd.n != h->n || hd.es != h->es || len != state_size(h))
         return fail(h, LES_ESTATE, "state blob does not match this handle");
     const char* b = (const char*)buf + sizeof hd;
-    void* arrs[] = {h->u, h->v, h->w, h->p[h->cur], h->fu, h->fv, h->fw};
-    const size_t B = h->n * h->es;
-    for (void* a : arrs) {
-        CK(cudaMemcpyAsync(a, b, B, cudaMemcpyHostToDevice, h->stream));
+    void* arrs[] = {h->u, h->v, h->w, h->fu, h->fv, h->fw, h->ph[h->cur]};
+    for (int a = 0; a < 7; ++a) {
+        const size_t B = h->n * (a == 6 ? sizeof(double) : h->es);
+        CK(cudaMemcpyAsync(arrs[a], b, B, cudaMemcpyHostToDevice, h->stream));
         b += B;
     }
     memcpy(h->inflow.data(), b, h->inflow.size() * sizeof(double));

@@ -58,6 +58,10 @@ struct Geo {
     const T* cB;            // [nz+2] 1/(dz_k dzs_{k-1})
     const T* delta2;        // [nz+2] (Cs Delta_k)^2
     const double* dz64;     // [nz+2]
+    double dx64, dy64, cx64, cy64;
+    const double* dzs64;    // [nz+2]
+    const double* cT64;     // [nz+2]
+    const double* cB64;     // [nz+2]
     const uint8_t* flags;   // padded cell flags
 };
 
@@ -81,18 +85,19 @@ template <typename T> int launch_rhs(const Geo<T>& g, const T* us, const T* vs, 
                                      double vfluid, const Reduce& r, cudaStream_t s);
 template <typename T> int launch_rhs_mean(const Geo<T>& g, T* rhs, double vfluid, const Reduce& r,
                                           cudaStream_t s);
-template <typename T> int launch_sor_sweep(const Geo<T>& g, T* p, const T* rhs, const Scalars* sc,
+template <typename T> int launch_sor_sweep(const Geo<T>& g, T* dl, const T* r, int zero_start,
                                            cudaStream_t s);
-template <typename T> int launch_residual(const Geo<T>& g, const T* p, const T* rhs, double tol,
-                                          double vfluid, const Reduce& r, cudaStream_t s);
+template <typename T> int launch_refine(const Geo<T>& g, const double* ph_in, double* ph_out, const T* dl,
+                                        const T* rhs, T* r, int with_delta, double tol, double vfluid,
+                                        const Reduce& red, cudaStream_t s);
 template <typename T> int launch_project(const Geo<T>& g, const T* us, const T* vs, const T* ws,
-                                         T* u, T* v, T* w, const T* p_in, T* p_out,
+                                         T* u, T* v, T* w, const double* ph_in, double* ph_out,
                                          const Scalars* sc, cudaStream_t s);
 template <typename T> int launch_rhs_eff(const Geo<T>& g, const T* rhs, T* out, const Scalars* sc,
                                          cudaStream_t s);
 
-template <typename T> int launch_gauge(const Geo<T>& g, const T* p_in, T* p_out, const Scalars* sc,
-                                       cudaStream_t s);
+template <typename T> int launch_gauge(const Geo<T>& g, const double* p_in, double* p_out,
+                                       const Scalars* sc, cudaStream_t s);
 
 int max_reduce_blocks(const Dom& d);
 

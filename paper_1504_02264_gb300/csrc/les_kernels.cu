@@ -4,7 +4,7 @@
 // Routine map (paper Sec. 2.1): k_bc_* = bondv1, k_nut = les (eddy
 // viscosity), k_momentum = velfg + les (SGS divergence) + adam + feedbf,
 // k_outflow = bondv1 outflow and mass-flux correction, k_rhs / k_sor_half /
-// k_residual = press (Sec. 2.6), k_project = velnw.
+// k_refine = press (Sec. 2.6), k_project = velnw.
 #include "les_internal.cuh"
 
 namespace les {
@@ -516,23 +516,30 @@ int launch_rhs_mean(const Geo<T>& g, T* rhs, double vfluid, const Reduce& r, cud
 }
 
 // ---------------------------------------------------------------------------
-// press: red-black SOR half-sweep (Sec. 2.6), in place.  Colour nrd updates
-// the cells i = 1 + mod(k+j+nrd, 2) + 2 m; a colour reads only the other
-// colour, so the in-place update gives the sequential result.
+// press: red-black SOR (Sec. 2.6) as mixed-precision iterative refinement.
+//
+// The pressure p is kept in FP64.  Each batch of sweeps runs the printed SOR
+// update in the field type T on the correction d, A d = r, from d = 0, where
+// r = (rhs - mean) - A p is formed in FP64.  SOR is a linear stationary
+// iteration, so p + d after m sweeps equals m plain SOR sweeps on p in exact
+// arithmetic; keeping p in FP64 removes the FP32 residual floor.
 
 template <typename T>
 struct Poisson {
     const Geo<T>& g;
-    __device__ __forceinline__ void coefs(uint8_t f, int k, T& ae, T& aw, T& an, T& as, T& at, T& ab) const {
-        ae = (f & F_E) ? g.cx : T(0);
-        aw = (f & F_W) ? g.cx : T(0);
-        an = (f & F_N) ? g.cy : T(0);
-        as = (f & F_S) ? g.cy : T(0);
-        at = (f & F_T) ? g.cT[k] : T(0);
-        ab = (f & F_B) ? g.cB[k] : T(0);
+    template <typename R>
+    __device__ __forceinline__ void coefs(uint8_t f, int k, R cx, R cy, const R* cT, const R* cB, R& ae, R& aw,
+                                          R& an, R& as, R& at, R& ab) const {
+        ae = (f & F_E) ? cx : R(0);
+        aw = (f & F_W) ? cx : R(0);
+        an = (f & F_N) ? cy : R(0);
+        as = (f & F_S) ? cy : R(0);
+        at = (f & F_T) ? cT[k] : R(0);
+        ab = (f & F_B) ? cB[k] : R(0);
     }
-    // sum of a_nb p_nb (neighbour indices wrapped on periodic axes)
-    __device__ __forceinline__ T nb(const T* p, int i, int j, int k, T ae, T aw, T an, T as, T at, T ab) const {
+    // neighbour indices (wrapped on periodic axes)
+    __device__ __forceinline__ void nbr(int i, int j, int k, long long& e, long long& w, long long& n,
+                                        long long& s, long long& t, long long& b) const {
         const Dom& d = g.d;
         int ie = (d.perx && i == d.nx) ? 1 : i + 1;
         int iw = (d.perx && i == 1) ? d.nx : i - 1;
@@ -540,19 +547,19 @@ struct Poisson {
         int js = (d.pery && j == 1) ? d.ny : j - 1;
         int kt = (d.perz && k == d.nz) ? 1 : k + 1;
         int kb = (d.perz && k == 1) ? d.nz : k - 1;
-        T s = T(0);
-        s += ae * p[d.at(ie, j, k)];
-        s += aw * p[d.at(iw, j, k)];
-        s += an * p[d.at(i, jn, k)];
-        s += as * p[d.at(i, js, k)];
-        s += at * p[d.at(i, j, kt)];
-        s += ab * p[d.at(i, j, kb)];
-        return s;
+        e = d.at(ie, j, k);
+        w = d.at(iw, j, k);
+        n = d.at(i, jn, k);
+        s = d.at(i, js, k);
+        t = d.at(i, j, kt);
+        b = d.at(i, j, kb);
     }
 };
 
+// One half-sweep on the correction d (in place; a colour reads only the other
+// colour).  zero_start: first sweep of a batch, d = 0 everywhere before it.
 template <typename T>
-__global__ void k_sor_half(Geo<T> g, T* p, const T* rhs, const Scalars* sc, int nrd) {
+__global__ void k_sor_half(Geo<T> g, T* dl, const T* r, int nrd, int zero_start) {
     const Dom& d = g.d;
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
@@ -565,26 +572,40 @@ __global__ void k_sor_half(Geo<T> g, T* p, const T* rhs, const Scalars* sc, int 
     if (!(f & F_UNK)) return;
     Poisson<T> P{g};
     T ae, aw, an, as, at, ab;
-    P.coefs(f, k, ae, aw, an, as, at, ab);
+    P.coefs(f, k, g.cx, g.cy, g.cT, g.cB, ae, aw, an, as, at, ab);
     T cn1 = T(1) / (ae + aw + an + as + at + ab);
-    T b = rhs[c] - (T)sc->rhs_mean;
-    T s = P.nb(p, i, j, k, ae, aw, an, as, at, ab);
-    T reltmp = g.omega * (cn1 * (s - b) - p[c]);
-    p[c] = p[c] + reltmp;
+    long long e, w, n, s_, t, b;
+    P.nbr(i, j, k, e, w, n, s_, t, b);
+    T s = T(0);
+    const bool nb_zero = zero_start && nrd == 0;   // red reads black, still zero
+    if (!nb_zero) {
+        s += ae * dl[e];
+        s += aw * dl[w];
+        s += an * dl[n];
+        s += as * dl[s_];
+        s += at * dl[t];
+        s += ab * dl[b];
+    }
+    T own = zero_start ? T(0) : dl[c];
+    T reltmp = g.omega * (cn1 * (s - r[c]) - own);
+    dl[c] = own + reltmp;
 }
 
 template <typename T>
-int launch_sor_sweep(const Geo<T>& g, T* p, const T* rhs, const Scalars* sc, cudaStream_t s) {
+int launch_sor_sweep(const Geo<T>& g, T* dl, const T* r, int zero_start, cudaStream_t s) {
     const Dom& d = g.d;
     dim3 grid(((d.nx + 1) / 2 + 31) / 32, (d.ny + 7) / 8, d.nz);
-    k_sor_half<T><<<grid, dim3(32, 8), 0, s>>>(g, p, rhs, sc, 0);
-    k_sor_half<T><<<grid, dim3(32, 8), 0, s>>>(g, p, rhs, sc, 1);
+    k_sor_half<T><<<grid, dim3(32, 8), 0, s>>>(g, dl, r, 0, zero_start);
+    k_sor_half<T><<<grid, dim3(32, 8), 0, s>>>(g, dl, r, 1, zero_start);
     return 2;
 }
 
-// FP64 residual norms and the dz-weighted p mean
+// Refinement step: P = ph_in + d (with_delta) is written to ph_out, and
+// r = (rhs - mean) - A P is formed in FP64, stored in T, and reduced to
+// FP64 norms; the dz-weighted fluid mean of P (for the gauge) comes along.
 template <typename T>
-__global__ void k_residual(Geo<T> g, const T* p, const T* rhs, double tol, double vfluid, Reduce r) {
+__global__ void k_refine(Geo<T> g, const double* ph_in, double* ph_out, const T* dl, const T* rhs, T* r,
+                         int with_delta, double tol, double vfluid, Reduce red) {
     const Dom& d = g.d;
     int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
     int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
@@ -593,21 +614,34 @@ __global__ void k_residual(Geo<T> g, const T* p, const T* rhs, double tol, doubl
     if (i <= d.nx && j <= d.ny) {
         long long c = d.at(i, j, k);
         const uint8_t f = g.flags[c];
+        auto P = [&](long long q) -> double { return with_delta ? ph_in[q] + (double)dl[q] : ph_in[q]; };
+        const double pc = P(c);
+        if (with_delta) ph_out[c] = pc;
         if (f & F_UNK) {
-            Poisson<T> P{g};
-            T ae, aw, an, as, at, ab;
-            P.coefs(f, k, ae, aw, an, as, at, ab);
-            T diag = ae + aw + an + as + at + ab;
-            T b = rhs[c] - (T)r.sc->rhs_mean;
-            T res = b - (P.nb(p, i, j, k, ae, aw, an, as, at, ab) - diag * p[c]);
-            x[0] = (double)res * (double)res;
-            x[1] = (double)b * (double)b;
+            Poisson<T> Q{g};
+            double ae, aw, an, as, at, ab;
+            Q.coefs(f, k, g.cx64, g.cy64, g.cT64, g.cB64, ae, aw, an, as, at, ab);
+            long long e, w, n, s_, t, b;
+            Q.nbr(i, j, k, e, w, n, s_, t, b);
+            double s = 0.0;
+            s += ae * P(e);
+            s += aw * P(w);
+            s += an * P(n);
+            s += as * P(s_);
+            s += at * P(t);
+            s += ab * P(b);
+            const double diag = ae + aw + an + as + at + ab;
+            const double bb = (double)rhs[c] - red.sc->rhs_mean;
+            const double res = bb - (s - diag * pc);
+            r[c] = (T)res;
+            x[0] = res * res;
+            x[1] = bb * bb;
         }
-        if (f & F_FLUID) x[2] = g.dz64[k] * (double)p[c];
+        if (f & F_FLUID) x[2] = g.dz64[k] * pc;
     }
-    if (grid_sum<3>(x, r)) {
+    if (grid_sum<3>(x, red)) {
         if (threadIdx.x == 0 && threadIdx.y == 0) {
-            Scalars* sc = r.sc;
+            Scalars* sc = red.sc;
             sc->res2 = x[0];
             sc->rhs2 = x[1];
             double rel = x[1] == 0.0 ? sqrt(x[0]) : sqrt(x[0] / x[1]);
@@ -620,20 +654,22 @@ __global__ void k_residual(Geo<T> g, const T* p, const T* rhs, double tol, doubl
 }
 
 template <typename T>
-int launch_residual(const Geo<T>& g, const T* p, const T* rhs, double tol, double vfluid, const Reduce& r,
-                    cudaStream_t s) {
+int launch_refine(const Geo<T>& g, const double* ph_in, double* ph_out, const T* dl, const T* rhs, T* r,
+                  int with_delta, double tol, double vfluid, const Reduce& red, cudaStream_t s) {
     const Dom& d = g.d;
-    k_residual<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(g, p, rhs, tol, vfluid, r);
+    k_refine<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(
+        g, ph_in, ph_out, dl, rhs, r, with_delta, tol, vfluid, red);
     return 1;
 }
 
 // ---------------------------------------------------------------------------
-// velnw: gauge (p -= dz-weighted fluid mean) and u = u* - dt grad p.
-// Reads p_in, writes the gauged p to p_out (no in-place race).
+// velnw: gauge (p -= dz-weighted fluid mean) and u = u* - dt grad p, the
+// gradient taken in FP64 from the FP64 pressure.  Reads ph_in, writes the
+// gauged pressure to ph_out (no in-place race).
 
 template <typename T>
 __global__ void k_project(Geo<T> g, const T* us, const T* vs, const T* ws, T* u, T* v, T* w,
-                          const T* p_in, T* p_out, const Scalars* sc) {
+                          const double* ph_in, double* ph_out, const Scalars* sc) {
     const Dom& d = g.d;
     int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
     int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
@@ -641,14 +677,15 @@ __global__ void k_project(Geo<T> g, const T* us, const T* vs, const T* ws, T* u,
     if (i > d.nx || j > d.ny) return;
     long long c = d.at(i, j, k);
     const uint8_t f = g.flags[c];
-    const T pm = (T)sc->p_mean;
-    auto gp = [&](long long q) -> T { return (g.flags[q] & F_FLUID) ? p_in[q] - pm : p_in[q]; };
-    const T pc = gp(c);
-    p_out[c] = pc;
+    const double pm = sc->p_mean;
+    const double dt = (double)g.dt;
+    auto gp = [&](long long q) -> double { return (g.flags[q] & F_FLUID) ? ph_in[q] - pm : ph_in[q]; };
+    const double pc = gp(c);
+    ph_out[c] = pc;
     // u on the east face of cell i
     if (i <= (d.perx ? d.nx : d.nx - 1)) {
         int ie = (d.perx && i == d.nx) ? 1 : i + 1;
-        T val = (f & F_E) ? us[c] - g.dt * (gp(d.at(ie, j, k)) - pc) / g.dx : T(0);
+        T val = (f & F_E) ? (T)((double)us[c] - dt * (gp(d.at(ie, j, k)) - pc) / g.dx64) : T(0);
         u[c] = val;
         if (d.perx && i == d.nx) u[d.at(0, j, k)] = val;
     } else {
@@ -658,7 +695,7 @@ __global__ void k_project(Geo<T> g, const T* us, const T* vs, const T* ws, T* u,
     // v on the north face of cell j
     if (j <= (d.pery ? d.ny : d.ny - 1)) {
         int jn = (d.pery && j == d.ny) ? 1 : j + 1;
-        T val = (f & F_N) ? vs[c] - g.dt * (gp(d.at(i, jn, k)) - pc) / g.dy : T(0);
+        T val = (f & F_N) ? (T)((double)vs[c] - dt * (gp(d.at(i, jn, k)) - pc) / g.dy64) : T(0);
         v[c] = val;
         if (d.pery && j == d.ny) v[d.at(i, 0, k)] = val;
     } else {
@@ -668,7 +705,7 @@ __global__ void k_project(Geo<T> g, const T* us, const T* vs, const T* ws, T* u,
     // w on the top face of cell k
     if (k <= (d.perz ? d.nz : d.nz - 1)) {
         int kt = (d.perz && k == d.nz) ? 1 : k + 1;
-        T val = (f & F_T) ? ws[c] - g.dt * (gp(d.at(i, j, kt)) - pc) / g.dzs[k] : T(0);
+        T val = (f & F_T) ? (T)((double)ws[c] - dt * (gp(d.at(i, j, kt)) - pc) / g.dzs64[k]) : T(0);
         w[c] = val;
         if (d.perz && k == d.nz) w[d.at(i, j, 0)] = val;
     } else {
@@ -679,27 +716,27 @@ __global__ void k_project(Geo<T> g, const T* us, const T* vs, const T* ws, T* u,
 
 template <typename T>
 int launch_project(const Geo<T>& g, const T* us, const T* vs, const T* ws, T* u, T* v, T* w,
-                   const T* p_in, T* p_out, const Scalars* sc, cudaStream_t s) {
+                   const double* ph_in, double* ph_out, const Scalars* sc, cudaStream_t s) {
     const Dom& d = g.d;
     k_project<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(
-        g, us, vs, ws, u, v, w, p_in, p_out, sc);
+        g, us, vs, ws, u, v, w, ph_in, ph_out, sc);
     return 1;
 }
 
 // gauge alone (les_pressure_solve): p_out = p_in - dz-weighted fluid mean
 template <typename T>
-__global__ void k_gauge(Geo<T> g, const T* p_in, T* p_out, const Scalars* sc) {
+__global__ void k_gauge(Geo<T> g, const double* p_in, double* p_out, const Scalars* sc) {
     const Dom& d = g.d;
     int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
     int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
     int k = blockIdx.z + 1;
     if (i > d.nx || j > d.ny) return;
     long long c = d.at(i, j, k);
-    p_out[c] = (g.flags[c] & F_FLUID) ? p_in[c] - (T)sc->p_mean : p_in[c];
+    p_out[c] = (g.flags[c] & F_FLUID) ? p_in[c] - sc->p_mean : p_in[c];
 }
 
 template <typename T>
-int launch_gauge(const Geo<T>& g, const T* p_in, T* p_out, const Scalars* sc, cudaStream_t s) {
+int launch_gauge(const Geo<T>& g, const double* p_in, double* p_out, const Scalars* sc, cudaStream_t s) {
     const Dom& d = g.d;
     k_gauge<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(g, p_in, p_out, sc);
     return 1;
@@ -736,13 +773,13 @@ int max_reduce_blocks(const Dom& d) { return ((d.nx + 31) / 32) * ((d.ny + 7) / 
     template int launch_rhs<T>(const Geo<T>&, const T*, const T*, const T*, T*, double, const Reduce&,  \
                                cudaStream_t);                                                           \
     template int launch_rhs_mean<T>(const Geo<T>&, T*, double, const Reduce&, cudaStream_t);            \
-    template int launch_sor_sweep<T>(const Geo<T>&, T*, const T*, const Scalars*, cudaStream_t);        \
-    template int launch_residual<T>(const Geo<T>&, const T*, const T*, double, double, const Reduce&,   \
-                                    cudaStream_t);                                                      \
-    template int launch_project<T>(const Geo<T>&, const T*, const T*, const T*, T*, T*, T*, const T*,   \
-                                   T*, const Scalars*, cudaStream_t);                                   \
+    template int launch_sor_sweep<T>(const Geo<T>&, T*, const T*, int, cudaStream_t);                   \
+    template int launch_refine<T>(const Geo<T>&, const double*, double*, const T*, const T*, T*, int,   \
+                                  double, double, const Reduce&, cudaStream_t);                         \
+    template int launch_project<T>(const Geo<T>&, const T*, const T*, const T*, T*, T*, T*,             \
+                                   const double*, double*, const Scalars*, cudaStream_t);               \
     template int launch_rhs_eff<T>(const Geo<T>&, const T*, T*, const Scalars*, cudaStream_t);          \
-    template int launch_gauge<T>(const Geo<T>&, const T*, T*, const Scalars*, cudaStream_t);
+    template int launch_gauge<T>(const Geo<T>&, const double*, double*, const Scalars*, cudaStream_t);
 
 LES_INSTANTIATE(float)
 LES_INSTANTIATE(double)
