@@ -209,6 +209,8 @@ def run_ours(args):
     sweeps = []
     worst = 0.0
     torch.cuda.synchronize()
+    if args.ncu_range:
+        torch.cuda.profiler.start()
     for s in range(args.steps):
         flush.zero_()
         ev[s][0].record(stream)
@@ -219,6 +221,8 @@ def run_ours(args):
         if st["rc"] != 0:
             raise RuntimeError(f"step did not converge: {st}")
     torch.cuda.synchronize()
+    if args.ncu_range:
+        torch.cuda.profiler.stop()
     tm = dom.timing()
     clk = clocks.stop() if clocks else None
     launches = tm["launches"] - l0
@@ -311,6 +315,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-range", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
