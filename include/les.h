@@ -193,6 +193,21 @@ typedef struct {
 int les_set_timing(les_handle h, int32_t enable);
 int les_get_timing(les_handle h, les_timing_t* t);
 
+/*
+ * SOR sweep kernel selection.  tile = -1 runs the two in-place half-sweep
+ * kernels; tile = 0..LES_SOR_NTILES-1 runs the fused red-black kernel with
+ * that column-tile shape (see les_sor_tile) marching kc planes per CTA
+ * (kc <= 0: the whole column).  Every choice computes the same iterate.
+ * les_autotune_sor times each tile shape with a few k-chunk lengths on this
+ * handle's grid (sweeps per candidate), keeps the fastest and reports it;
+ * the field state is saved and restored around the trial sweeps.
+ */
+#define LES_SOR_NTILES 6
+int les_set_sor_config(les_handle h, int32_t tile, int32_t kc);
+int les_get_sor_config(les_handle h, int32_t* tile, int32_t* kc);
+int les_sor_tile(int32_t tile, int32_t* tx, int32_t* ty);
+int les_autotune_sor(les_handle h, int32_t sweeps, double* best_ms_per_sweep);
+
 /* Library version string. */
 const char* les_version(void);
 

@@ -81,7 +81,9 @@ struct les_s {
     void *u = nullptr, *v = nullptr, *w = nullptr, *us = nullptr, *vs = nullptr, *ws = nullptr;
     void *fu = nullptr, *fv = nullptr, *fw = nullptr, *nut = nullptr, *rhs = nullptr, *tmp = nullptr;
     double* ph[2] = {nullptr, nullptr};   // FP64 pressure (velnw writes the gauged copy to the other)
-    void *dl = nullptr, *rr = nullptr;    // SOR correction and its FP64-formed right-hand side
+    void* dl[2] = {nullptr, nullptr};     // SOR correction (ping-pong for the fused sweep)
+    void* rr = nullptr;                   // its FP64-formed right-hand side
+    SorCfg sor = {3, 16};                 // fused kernel, 64 x 8 tiles, 16-plane chunks
     void* stage = nullptr;         // dense I/O staging
     size_t stage_elems = 0;
     uint8_t* flags = nullptr;
@@ -238,17 +240,33 @@ double elapsed(les_s* h, int a, int b) {
 // refined by batches of sweeps on the correction (see k_refine); the FP64
 // relative residual is tested after each batch of check_every sweeps and at
 // max_sweeps, exactly where the sequential algorithm tests it.
+// n sweeps on the correction from d = 0; returns the buffer holding the result
+template <typename T>
+int run_sweeps(les_s* h, const Geo<T>& g, int n, long long& launched) {
+    T* rr = (T*)h->rr;
+    if (h->sor.tile < 0) {
+        for (int s = 0; s < n; ++s) launched += launch_sor_sweep<T>(g, (T*)h->dl[0], rr, s == 0, h->stream);
+        return 0;
+    }
+    int out = 0;
+    for (int s = 0; s < n; ++s) {
+        out = s & 1;
+        launched += launch_sor_fused<T>(g, (const T*)h->dl[1 - out], (T*)h->dl[out], rr, s == 0, h->sor, h->stream);
+    }
+    return out;
+}
+
 template <typename T>
 int sor_solve(les_s* h) {
     Geo<T> g = geo<T>(h);
     Reduce r = reducer(h);
-    T* dl = (T*)h->dl;
     T* rr = (T*)h->rr;
     const T* rhs = (const T*)h->rhs;
     const les_grid_t& G = h->g;
     int sweeps = 0;
     rec(h, 2);
-    h->launches += launch_refine<T>(g, h->ph[h->cur], nullptr, dl, rhs, rr, 0, G.tol, h->vfluid, r, h->stream);
+    h->launches += launch_refine<T>(g, h->ph[h->cur], nullptr, (const T*)h->dl[0], rhs, rr, 0, G.tol, h->vfluid, r,
+                                    h->stream);
     rec(h, 3);
     CK(cudaGetLastError());
     if (h->timing) {
@@ -257,12 +275,12 @@ int sor_solve(les_s* h) {
     }
     auto batch = [&](int n) -> int {
         rec(h, 2);
-        long long l0 = h->launches;
-        for (int s = 0; s < n; ++s) h->launches += launch_sor_sweep<T>(g, dl, rr, s == 0, h->stream);
-        long long nl = h->launches - l0;
+        long long nl = 0;
+        int out = run_sweeps<T>(h, g, n, nl);
+        h->launches += nl;
         rec(h, 3);
-        h->launches += launch_refine<T>(g, h->ph[h->cur], h->ph[1 - h->cur], dl, rhs, rr, 1, G.tol, h->vfluid,
-                                        r, h->stream);
+        h->launches += launch_refine<T>(g, h->ph[h->cur], h->ph[1 - h->cur], (const T*)h->dl[out], rhs, rr, 1,
+                                        G.tol, h->vfluid, r, h->stream);
         h->cur = 1 - h->cur;
         rec(h, 4);
         CK(cudaGetLastError());
@@ -292,6 +310,44 @@ int sor_solve(les_s* h) {
     h->sc_host->sweeps = sweeps;
     if (h->sc_host->nonfinite) return fail(h, LES_ENONFINITE, "SOR residual is not finite");
     return (!G.fixed_sweeps && !h->sc_host->converged) ? LES_ENOCONV : LES_OK;
+}
+
+// Time `sweeps` sweeps per candidate (tile shape x k-chunk) on the current
+// correction right-hand side; the sweeps touch only the scratch correction
+// buffers, never the state.
+template <typename T>
+int autotune_impl(les_s* h, int sweeps, double* best_ms) {
+    Geo<T> g = geo<T>(h);
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    const int kcs[] = {4, 8, 16, 32, 0};
+    SorCfg keep = h->sor, best = keep;
+    double bms = 1e300;
+    for (int t = 0; t < kNumSorTiles; ++t)
+        for (int kc : kcs) {
+            if (kc > h->g.nz) continue;
+            h->sor = SorCfg{t, kc};
+            long long nl = 0;
+            run_sweeps<T>(h, g, 2, nl);       // warm
+            CK(cudaEventRecord(a, h->stream));
+            run_sweeps<T>(h, g, sweeps, nl);
+            CK(cudaEventRecord(b, h->stream));
+            CK(cudaEventSynchronize(b));
+            h->launches += nl;
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, a, b));
+            double per = ms / sweeps;
+            if (per < bms) {
+                bms = per;
+                best = h->sor;
+            }
+        }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    h->sor = bms < 1e299 ? best : keep;
+    if (best_ms) *best_ms = bms;
+    return LES_OK;
 }
 
 template <typename T>
@@ -439,7 +495,7 @@ int create_impl(les_s* h, const uint8_t* solid) {
     const size_t B = h->n * h->es;
     int rc;
     void** fields[] = {&h->u, &h->v, &h->w, &h->us, &h->vs, &h->ws, &h->fu, &h->fv, &h->fw,
-                       &h->nut, &h->rhs, &h->tmp, &h->dl, &h->rr};
+                       &h->nut, &h->rhs, &h->tmp, &h->dl[0], &h->dl[1], &h->rr};
     for (void** f : fields)
         if ((rc = dalloc(h, f, B))) return rc;
     for (double*& f : h->ph)
@@ -738,6 +794,34 @@ int les_set_state(les_handle h, const void* buf, size_t len) {
     h->g.turb = hd.turb;
     h->g.seed = hd.seed;
     return LES_OK;
+}
+
+int les_set_sor_config(les_handle h, int32_t tile, int32_t kc) {
+    if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
+    if (tile < -1 || tile >= kNumSorTiles) return fail(h, LES_EINVAL, "tile %d out of range", tile);
+    h->sor = SorCfg{tile, kc};
+    return LES_OK;
+}
+
+int les_get_sor_config(les_handle h, int32_t* tile, int32_t* kc) {
+    if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
+    if (tile) *tile = h->sor.tile;
+    if (kc) *kc = h->sor.kc;
+    return LES_OK;
+}
+
+int les_sor_tile(int32_t tile, int32_t* tx, int32_t* ty) {
+    if (tile < 0 || tile >= kNumSorTiles) return fail(nullptr, LES_EINVAL, "tile %d out of range", tile);
+    if (tx) *tx = kSorTiles[tile].tx;
+    if (ty) *ty = kSorTiles[tile].ty;
+    return LES_OK;
+}
+
+int les_autotune_sor(les_handle h, int32_t sweeps, double* best_ms_per_sweep) {
+    if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
+    if (sweeps < 1) return fail(h, LES_EINVAL, "sweeps must be >= 1");
+    return h->prec == LES_FP64 ? autotune_impl<double>(h, sweeps, best_ms_per_sweep)
+                               : autotune_impl<float>(h, sweeps, best_ms_per_sweep);
 }
 
 int les_set_timing(les_handle h, int32_t enable) {

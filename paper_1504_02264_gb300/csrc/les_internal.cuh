@@ -99,6 +99,14 @@ template <typename T> int launch_rhs_eff(const Geo<T>& g, const T* rhs, T* out, 
 template <typename T> int launch_gauge(const Geo<T>& g, const double* p_in, double* p_out,
                                        const Scalars* sc, cudaStream_t s);
 
+// fused SOR sweep (les_sor.cu): tile shape index into kSorTiles and k-chunk
+struct SorTile { int tx, ty; };
+struct SorCfg { int tile; int kc; };   // tile < 0: two in-place half-sweep kernels
+extern const SorTile kSorTiles[];
+extern const int kNumSorTiles;
+template <typename T> int launch_sor_fused(const Geo<T>& g, const T* din, T* dout, const T* r, int zero_start,
+                                           SorCfg cfg, cudaStream_t s);
+
 int max_reduce_blocks(const Dom& d);
 
 }  // namespace les

@@ -83,9 +83,14 @@ def lib(build_if_missing: bool = False):
         L.les_get_aux.argtypes = [vp, i32, vp]
         L.les_get_state.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
         L.les_set_state.argtypes = [vp, vp, ctypes.c_size_t]
+        L.les_set_sor_config.argtypes = [vp, i32, i32]
+        L.les_get_sor_config.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        L.les_sor_tile.argtypes = [i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        L.les_autotune_sor.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
         L.les_set_timing.argtypes = [vp, i32]
         L.les_get_timing.argtypes = [vp, ctypes.POINTER(les_timing_t)]
-        for name in ("les_set_timing", "les_get_timing", "les_create", "les_set_fields", "les_get_fields", "les_set_inflow", "les_step",
+        for name in ("les_set_sor_config", "les_get_sor_config", "les_sor_tile", "les_autotune_sor",
+                     "les_set_timing", "les_get_timing", "les_create", "les_set_fields", "les_get_fields", "les_set_inflow", "les_step",
                      "les_pressure_solve", "les_get_aux", "les_get_state", "les_set_state"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -165,6 +170,28 @@ def les_set_timing(h, enable):
 
 def les_get_timing(h, t: les_timing_t):
     return _check(lib().les_get_timing(h, ctypes.byref(t)), h)
+
+
+def les_set_sor_config(h, tile, kc):
+    return _check(lib().les_set_sor_config(h, tile, kc), h)
+
+
+def les_get_sor_config(h):
+    t, k = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().les_get_sor_config(h, ctypes.byref(t), ctypes.byref(k)), h)
+    return t.value, k.value
+
+
+def les_sor_tile(tile):
+    tx, ty = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().les_sor_tile(tile, ctypes.byref(tx), ctypes.byref(ty)))
+    return tx.value, ty.value
+
+
+def les_autotune_sor(h, sweeps):
+    ms = ctypes.c_double()
+    _check(lib().les_autotune_sor(h, sweeps, ctypes.byref(ms)), h)
+    return ms.value
 
 
 def les_last_error(h) -> str:
@@ -269,6 +296,16 @@ class Domain:
     def set_state(self, blob: bytes):
         buf = ctypes.create_string_buffer(blob, len(blob))
         les_set_state(self.h, buf, len(blob))
+
+    def set_sor_config(self, tile, kc=0):
+        les_set_sor_config(self.h, tile, kc)
+
+    def sor_config(self):
+        return les_get_sor_config(self.h)
+
+    def autotune_sor(self, sweeps=20):
+        ms = les_autotune_sor(self.h, sweeps)
+        return self.sor_config(), ms
 
     def set_timing(self, enable=True):
         les_set_timing(self.h, enable)

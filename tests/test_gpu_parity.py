@@ -216,3 +216,52 @@ def test_no_convergence_status():
     d = les.Domain(sc, precision=les.LES_FP32)
     st = d.step(1)
     assert st["rc"] == les.LES_ENOCONV and st["sweeps"] == 20
+
+
+# ---------------------------------------------------------------------------
+# fused red-black kernel: every tile shape / k-chunk gives the two-pass iterate
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("case", ["city", "periodic_y_odd", "periodic_xyz"])
+def test_fused_sor_matches_two_pass(prec, case):
+    p = les.LES_FP64 if prec == "fp64" else les.LES_FP32
+    if case == "city":
+        sc = city(nx=37, ny=21, nz=11, turb=0.1, fixed_sweeps=1, max_sweeps=17)
+    elif case == "periodic_y_odd":
+        sc = city(nx=45, ny=18, nz=13, periodic_y=True, turb=0.1, fixed_sweeps=1, max_sweeps=9)
+    else:
+        n = 12
+        sc = scene.box_scene(n, n, 6, dx=0.4, dy=0.4, dz=np.full(6, 0.4), bc=(scene.BC_PERIODIC,) * 3,
+                             nu=0.01, dt=0.02, fixed_sweeps=1, max_sweeps=11)
+        u, v, w, q = scene.random_fields(sc, 6, amp=0.3)
+        u[:, :, 0] = u[:, :, -1]
+        v[:, 0, :] = v[:, -1, :]
+        w[0] = w[-1]
+        sc.u0, sc.v0, sc.w0, sc.p0 = u, v, w, 0 * q
+    ref = les.Domain(sc, precision=p)
+    ref.set_sor_config(-1, 0)
+    ref.step(2)
+    want = ref.fields()
+    tol = 0.0 if prec == "fp64" else 1e-6
+    for tile in range(6):
+        for kc in (0, 3, 5):
+            d = les.Domain(sc, precision=p)
+            d.set_sor_config(tile, kc)
+            d.step(2)
+            for a, b in zip(d.fields(), want):
+                scale = max(np.abs(b).max(), 1e-30)
+                assert np.abs(a.astype(np.float64) - b).max() <= tol * scale, (tile, kc)
+            d.close()
+
+
+def test_autotune_picks_a_valid_config():
+    sc = city(nx=64, ny=48, nz=24, fixed_sweeps=1, max_sweeps=10)
+    d = les.Domain(sc, precision=les.LES_FP32)
+    d.step(1)
+    (tile, kc), ms = d.autotune_sor(sweeps=5)
+    assert 0 <= tile < 6 and ms > 0
+    before = d.fields()
+    d2 = les.Domain(sc, precision=les.LES_FP32)
+    d2.step(1)
+    for a, b in zip(before, d2.fields()):
+        assert np.array_equal(a, b)      # tuning sweeps never touch the state
