@@ -194,6 +194,16 @@ int les_set_timing(les_handle h, int32_t enable);
 int les_get_timing(les_handle h, les_timing_t* t);
 
 /*
+ * Step execution mode.  enable = 1 (default): each step is one CUDA graph
+ * launch (prefix kernels, device-side SOR stop test in a conditional WHILE
+ * node, projection), with one host synchronisation per les_step call.
+ * enable = 0: host-driven loop, reading the residual back after every batch
+ * of check_every sweeps.  Phase timing (les_set_timing) always uses the
+ * host-driven loop.  Both modes compute the same iterates.
+ */
+int les_set_graph(les_handle h, int32_t enable);
+
+/*
  * SOR sweep kernel selection.  tile = -1 runs the two in-place half-sweep
  * kernels; tile = 0..LES_SOR_NTILES-1 runs the fused red-black kernel with
  * that column-tile shape (see les_sor_tile) marching kc planes per CTA

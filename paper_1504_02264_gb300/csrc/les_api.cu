@@ -101,6 +101,12 @@ struct les_s {
     double vfluid = 0.0;
     long long launches = 0;
     std::vector<void*> allocs;
+    // CUDA graph of one step per pressure-buffer parity
+    bool use_graph = true;
+    bool graph_ok[2] = {false, false};
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaStream_t cap[2] = {nullptr, nullptr};
+    cudaGraphConditionalHandle cond_loop = 0, cond_tail = 0;
     // phase timing
     bool timing = false;
     cudaEvent_t ev[8] = {};
@@ -237,36 +243,68 @@ double elapsed(les_s* h, int a, int b) {
 }
 
 // press: SOR iterations under the stop rule.  The FP64 pressure ph[cur] is
-// refined by batches of sweeps on the correction (see k_refine); the FP64
+// refined by batches of sweeps on the correction d (k_accum adds d, then
+// k_residual64 forms the next right-hand side and the FP64 residual); the
 // relative residual is tested after each batch of check_every sweeps and at
 // max_sweeps, exactly where the sequential algorithm tests it.
+
 // n sweeps on the correction from d = 0; returns the buffer holding the result
 template <typename T>
-int run_sweeps(les_s* h, const Geo<T>& g, int n, long long& launched) {
+int run_sweeps(les_s* h, const Geo<T>& g, int n, long long& launched, cudaStream_t st) {
     T* rr = (T*)h->rr;
     if (h->sor.tile < 0) {
-        for (int s = 0; s < n; ++s) launched += launch_sor_sweep<T>(g, (T*)h->dl[0], rr, s == 0, h->stream);
+        for (int s = 0; s < n; ++s) launched += launch_sor_sweep<T>(g, (T*)h->dl[0], rr, s == 0, st);
         return 0;
     }
     int out = 0;
     for (int s = 0; s < n; ++s) {
         out = s & 1;
-        launched += launch_sor_fused<T>(g, (const T*)h->dl[1 - out], (T*)h->dl[out], rr, s == 0, h->sor, h->stream);
+        launched += launch_sor_fused<T>(g, (const T*)h->dl[1 - out], (T*)h->dl[out], rr, s == 0, h->sor, st);
     }
     return out;
 }
 
+CondArgs cond_args(const les_s* h, int mode, int n, bool use_cond) {
+    CondArgs ca{};
+    ca.loop = h->cond_loop;
+    ca.tail = h->cond_tail;
+    ca.use_cond = use_cond ? 1 : 0;
+    ca.mode = mode;
+    ca.n = n;
+    const les_grid_t& G = h->g;
+    if (G.fixed_sweeps) {
+        ca.n_full = 0;
+        ca.rem = G.max_sweeps;
+    } else {
+        ca.n_full = G.max_sweeps / G.check_every;
+        ca.rem = G.max_sweeps % G.check_every;
+    }
+    return ca;
+}
+
+// one batch: sweeps, accumulate, residual (all on stream st)
+template <typename T>
+int sor_batch(les_s* h, const Geo<T>& g, int n, int mode, bool use_cond, cudaStream_t st, long long* sweep_launches) {
+    long long nl = 0;
+    int out = run_sweeps<T>(h, g, n, nl, st);
+    if (sweep_launches) *sweep_launches = nl;
+    h->launches += nl;
+    if (h->timing && !use_cond) rec(h, 3);
+    h->launches += launch_accum<T>(g, h->ph[h->cur], (const T*)h->dl[out], st);
+    h->launches += launch_residual64<T>(g, h->ph[h->cur], (const T*)h->rhs, (T*)h->rr, h->g.tol, h->vfluid,
+                                        reducer(h), cond_args(h, mode, n, use_cond), st);
+    return LES_OK;
+}
+
+// host-driven loop (stop decision read back after every batch)
 template <typename T>
 int sor_solve(les_s* h) {
     Geo<T> g = geo<T>(h);
-    Reduce r = reducer(h);
-    T* rr = (T*)h->rr;
-    const T* rhs = (const T*)h->rhs;
     const les_grid_t& G = h->g;
     int sweeps = 0;
     rec(h, 2);
-    h->launches += launch_refine<T>(g, h->ph[h->cur], nullptr, (const T*)h->dl[0], rhs, rr, 0, G.tol, h->vfluid, r,
-                                    h->stream);
+    h->launches += launch_residual64<T>(g, h->ph[h->cur], (const T*)h->rhs, (T*)h->rr, G.tol, h->vfluid, reducer(h),
+                                        cond_args(h, RES_INIT, 0, false), h->stream);
     rec(h, 3);
     CK(cudaGetLastError());
     if (h->timing) {
@@ -276,12 +314,7 @@ int sor_solve(les_s* h) {
     auto batch = [&](int n) -> int {
         rec(h, 2);
         long long nl = 0;
-        int out = run_sweeps<T>(h, g, n, nl);
-        h->launches += nl;
-        rec(h, 3);
-        h->launches += launch_refine<T>(g, h->ph[h->cur], h->ph[1 - h->cur], (const T*)h->dl[out], rhs, rr, 1,
-                                        G.tol, h->vfluid, r, h->stream);
-        h->cur = 1 - h->cur;
+        sor_batch<T>(h, g, n, RES_HOST, false, h->stream, &nl);
         rec(h, 4);
         CK(cudaGetLastError());
         int rc = fetch_scalars(h);
@@ -329,9 +362,9 @@ int autotune_impl(les_s* h, int sweeps, double* best_ms) {
             if (kc > h->g.nz) continue;
             h->sor = SorCfg{t, kc};
             long long nl = 0;
-            run_sweeps<T>(h, g, 2, nl);       // warm
+            run_sweeps<T>(h, g, 2, nl, h->stream);       // warm
             CK(cudaEventRecord(a, h->stream));
-            run_sweeps<T>(h, g, sweeps, nl);
+            run_sweeps<T>(h, g, sweeps, nl, h->stream);
             CK(cudaEventRecord(b, h->stream));
             CK(cudaEventSynchronize(b));
             h->launches += nl;
@@ -346,44 +379,46 @@ int autotune_impl(les_s* h, int sweeps, double* best_ms) {
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     h->sor = bms < 1e299 ? best : keep;
+    h->graph_ok[0] = h->graph_ok[1] = false;
     if (best_ms) *best_ms = bms;
     return LES_OK;
 }
 
 template <typename T>
-int project(les_s* h) {
-    Geo<T> g = geo<T>(h);
+void launch_project_step(les_s* h, const Geo<T>& g, int cur, cudaStream_t st) {
     h->launches += launch_project<T>(g, (const T*)h->us, (const T*)h->vs, (const T*)h->ws, (T*)h->u, (T*)h->v,
-                                     (T*)h->w, h->ph[h->cur], h->ph[1 - h->cur], h->sc, h->stream);
-    CK(cudaGetLastError());
-    h->cur = 1 - h->cur;
-    return LES_OK;
+                                     (T*)h->w, h->ph[cur], h->ph[1 - cur], h->sc, st);
 }
 
-// Mean of p for the gauge: the last residual kernel of a solve computes it
-// from the same p that velnw then reads, so no extra pass is needed.
+// bondv1, les, velfg, adam, feedbf, bondv1 (outflow), rhs
 template <typename T>
-int step_once(les_s* h) {
-    Geo<T> g = geo<T>(h);
-    cudaStream_t s = h->stream;
+void launch_prefix(les_s* h, const Geo<T>& g, cudaStream_t s) {
     T* u = (T*)h->u;
     T* v = (T*)h->v;
     T* w = (T*)h->w;
-    rec(h, 0);
-    h->launches += launch_bc<T>(g, u, v, w, h->inflow64, h->g.turb, h->g.seed, h->step, s);
+    h->launches += launch_bc<T>(g, u, v, w, h->inflow64, h->g.turb, h->g.seed, h->sc, s);
     h->launches += launch_nut<T>(g, u, v, w, (T*)h->nut, s);
     h->launches += launch_momentum<T>(g, u, v, w, (const T*)h->nut, (T*)h->fu, (T*)h->fv, (T*)h->fw, (T*)h->us,
-                                      (T*)h->vs, (T*)h->ws, h->step == 0, s);
+                                      (T*)h->vs, (T*)h->ws, h->sc, s);
     h->launches += launch_outflow<T>(g, u, (T*)h->us, (T*)h->vs, (T*)h->ws, h->sc, s);
     h->launches += launch_rhs<T>(g, (const T*)h->us, (const T*)h->vs, (const T*)h->ws, (T*)h->rhs, h->vfluid,
                                  reducer(h), s);
+}
+
+// Host-driven step (used with phase timing and for les_pressure_solve).
+template <typename T>
+int step_host(les_s* h) {
+    Geo<T> g = geo<T>(h);
+    rec(h, 0);
+    launch_prefix<T>(h, g, h->stream);
     rec(h, 1);
     CK(cudaGetLastError());
     int rc = sor_solve<T>(h);
     if (rc < 0) return rc;
     rec(h, 5);
-    int rp = project<T>(h);
-    if (rp) return rp;
+    launch_project_step<T>(h, g, h->cur, h->stream);
+    CK(cudaGetLastError());
+    h->cur = 1 - h->cur;
     rec(h, 6);
     if (h->timing) {
         CK(cudaEventSynchronize(h->ev[6]));
@@ -393,6 +428,136 @@ int step_once(les_s* h) {
     }
     h->step += 1;
     return rc;
+}
+
+// The whole step as one CUDA graph: prefix, initial residual, a conditional
+// WHILE node over full batches of check_every sweeps, a conditional IF node for
+// the remainder batch, projection.  The stop test runs on the device
+// (k_residual64 sets the conditions), so a step needs no host round trip.
+// One graph per pressure buffer parity (velnw writes the gauged p to the other).
+template <typename T>
+int build_graph(les_s* h, int cur) {
+    Geo<T> g = geo<T>(h);
+    const les_grid_t& G = h->g;
+    if (h->gexec[cur]) {
+        cudaGraphExecDestroy(h->gexec[cur]);
+        h->gexec[cur] = nullptr;
+    }
+    cudaStream_t cs = h->cap[0], cb = h->cap[1];
+    const int save_cur = h->cur;
+    h->cur = cur;
+    long long l0 = h->launches;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    launch_prefix<T>(h, g, cs);
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t graph;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    auto abort_capture = [&](cudaError_t e, const char* what) {
+        cudaGraph_t junk;
+        cudaStreamEndCapture(cs, &junk);
+        if (junk) cudaGraphDestroy(junk);
+        h->cur = save_cur;
+        return fail(h, LES_ECUDA, "graph build (%s): %s", what, cudaGetErrorString(e));
+    };
+    cudaError_t e;
+    if (G.fixed_sweeps) {
+        launch_residual64<T>(g, h->ph[cur], (const T*)h->rhs, (T*)h->rr, G.tol, h->vfluid, reducer(h),
+                             cond_args(h, RES_INIT, 0, false), cs);
+        sor_batch<T>(h, g, G.max_sweeps, RES_TAIL, false, cs, nullptr);
+    } else {
+        e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph, nullptr, nullptr, nullptr);
+        if (e != cudaSuccess) return abort_capture(e, "capture info");
+        e = cudaGraphConditionalHandleCreate(&h->cond_loop, graph, 0, 0);
+        if (e != cudaSuccess) return abort_capture(e, "loop handle");
+        e = cudaGraphConditionalHandleCreate(&h->cond_tail, graph, 0, 0);
+        if (e != cudaSuccess) return abort_capture(e, "tail handle");
+        launch_residual64<T>(g, h->ph[cur], (const T*)h->rhs, (T*)h->rr, G.tol, h->vfluid, reducer(h),
+                             cond_args(h, RES_INIT, 0, true), cs);
+        const CondArgs ca = cond_args(h, RES_LOOP, G.check_every, true);
+        // WHILE node over full batches
+        e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph, &deps, nullptr, &ndeps);
+        if (e != cudaSuccess) return abort_capture(e, "capture info");
+        cudaGraphNodeParams wp = {};
+        wp.type = cudaGraphNodeTypeConditional;
+        wp.conditional.handle = h->cond_loop;
+        wp.conditional.type = cudaGraphCondTypeWhile;
+        wp.conditional.size = 1;
+        cudaGraphNode_t wnode;
+        e = cudaGraphAddNode(&wnode, graph, deps, nullptr, ndeps, &wp);
+        if (e != cudaSuccess) return abort_capture(e, "while node");
+        cudaGraph_t body = wp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) return abort_capture(e, "while body");
+        sor_batch<T>(h, g, G.check_every, RES_LOOP, true, cb, nullptr);
+        e = cudaStreamEndCapture(cb, &body);
+        if (e != cudaSuccess) return abort_capture(e, "while body end");
+        (void)ca;
+        cudaGraphNode_t last = wnode;
+        if (cond_args(h, RES_LOOP, 0, true).rem > 0) {
+            cudaGraphNodeParams ip = {};
+            ip.type = cudaGraphNodeTypeConditional;
+            ip.conditional.handle = h->cond_tail;
+            ip.conditional.type = cudaGraphCondTypeIf;
+            ip.conditional.size = 1;
+            cudaGraphNode_t inode;
+            e = cudaGraphAddNode(&inode, graph, &wnode, nullptr, 1, &ip);
+            if (e != cudaSuccess) return abort_capture(e, "if node");
+            cudaGraph_t tbody = ip.conditional.phGraph_out[0];
+            e = cudaStreamBeginCaptureToGraph(cb, tbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+            if (e != cudaSuccess) return abort_capture(e, "if body");
+            sor_batch<T>(h, g, cond_args(h, RES_TAIL, 0, true).rem, RES_TAIL, true, cb, nullptr);
+            e = cudaStreamEndCapture(cb, &tbody);
+            if (e != cudaSuccess) return abort_capture(e, "if body end");
+            last = inode;
+        }
+        e = cudaStreamUpdateCaptureDependencies(cs, &last, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (e != cudaSuccess) return abort_capture(e, "dependencies");
+    }
+    launch_project_step<T>(h, g, cur, cs);
+    cudaGraph_t full;
+    e = cudaStreamEndCapture(cs, &full);
+    h->cur = save_cur;
+    h->launches = l0;          // capture launches nothing
+    if (e != cudaSuccess) return fail(h, LES_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&h->gexec[cur], full, 0);
+    cudaGraphDestroy(full);
+    if (e != cudaSuccess) return fail(h, LES_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    h->graph_ok[cur] = true;
+    return LES_OK;
+}
+
+void fill_stats(les_s* h, les_stats_t* st, int status);
+
+// kernels one graph step launches for a given sweep count (for the counter)
+long long graph_step_launches(const les_s* h, int sweeps) {
+    int pre = 3 + 1 + 1 + 1 + (h->d.pery ? 1 : 0) + (h->d.perz ? 1 : 0) + 1;
+    const les_grid_t& G = h->g;
+    int per_sweep = h->sor.tile < 0 ? 2 : 1;
+    int batches = G.fixed_sweeps ? 1 : (sweeps + G.check_every - 1) / G.check_every;
+    return pre + 1 + (long long)sweeps * per_sweep + 2LL * batches + 1;
+}
+
+template <typename T>
+int step_graph(les_s* h, int nsteps, les_stats_t* stats) {
+    for (int c = 0; c < 2; ++c)
+        if (!h->graph_ok[c]) {
+            int rc = build_graph<T>(h, c);
+            if (rc) return rc;
+        }
+    CK(cudaMemsetAsync(&h->sc->noconv_any, 0, sizeof(int), h->stream));
+    for (int s = 0; s < nsteps; ++s) {
+        CK(cudaGraphLaunch(h->gexec[h->cur], h->stream));
+        h->cur = 1 - h->cur;
+        h->step += 1;
+    }
+    int rc = fetch_scalars(h);
+    if (rc) return rc;
+    h->launches += graph_step_launches(h, h->sc_host->sweeps) * nsteps;   // sweep count of the last step
+    int status = h->sc_host->noconv_any ? LES_ENOCONV : LES_OK;
+    if (h->sc_host->nonfinite) return fail(h, LES_ENONFINITE, "SOR residual is not finite");
+    if (stats) fill_stats(h, stats, status);
+    return status;
 }
 
 void fill_stats(les_s* h, les_stats_t* st, int status) {
@@ -468,6 +633,16 @@ int init_tables(les_s* h) {
 }
 
 void release(les_s* h) {
+    for (cudaGraphExec_t& x : h->gexec)
+        if (x) {
+            cudaGraphExecDestroy(x);
+            x = nullptr;
+        }
+    for (cudaStream_t& c : h->cap)
+        if (c) {
+            cudaStreamDestroy(c);
+            c = nullptr;
+        }
     for (cudaEvent_t& e : h->ev)
         if (e) {
             cudaEventDestroy(e);
@@ -516,6 +691,7 @@ int create_impl(les_s* h, const uint8_t* solid) {
     if ((rc = dalloc(h, (void**)&h->sc, sizeof(Scalars)))) return rc;
     h->stage_elems = io_elems(h, 1) + io_elems(h, 2) + io_elems(h, 3) + io_elems(h, 0);
     if ((rc = dalloc(h, &h->stage, h->stage_elems * h->es))) return rc;
+    for (cudaStream_t& c : h->cap) CK(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
     if (cudaMallocHost((void**)&h->sc_host, sizeof(Scalars)) != cudaSuccess)
         return fail(h, LES_ENOMEM, "cudaMallocHost failed");
     memset(h->sc_host, 0, sizeof(Scalars));
@@ -714,15 +890,17 @@ int les_set_inflow(les_handle h, const double* inflow_u, double turb, uint64_t s
 int les_step(les_handle h, int32_t nsteps, les_stats_t* stats) {
     if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
     if (nsteps < 0) return fail(h, LES_EINVAL, "nsteps < 0");
-    int worst = LES_OK;
-    if (nsteps == 0 && stats) {
+    if (nsteps == 0) {
         cudaError_t e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) return fail(h, LES_ECUDA, "step: %s", cudaGetErrorString(e));
         fill_stats(h, stats, LES_OK);
         return LES_OK;
     }
+    if (h->use_graph && !h->timing)
+        return h->prec == LES_FP64 ? step_graph<double>(h, nsteps, stats) : step_graph<float>(h, nsteps, stats);
+    int worst = LES_OK;
     for (int s = 0; s < nsteps; ++s) {
-        int rc = h->prec == LES_FP64 ? step_once<double>(h) : step_once<float>(h);
+        int rc = h->prec == LES_FP64 ? step_host<double>(h) : step_host<float>(h);
         if (rc < 0) return rc;
         if (rc == LES_ENOCONV) worst = LES_ENOCONV;
         if (stats && s == nsteps - 1) {
@@ -793,6 +971,9 @@ int les_set_state(les_handle h, const void* buf, size_t len) {
     h->step = hd.step;
     h->g.turb = hd.turb;
     h->g.seed = hd.seed;
+    long long st = hd.step;
+    CK(cudaMemcpyAsync(&h->sc->step, &st, sizeof st, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
     return LES_OK;
 }
 
@@ -800,6 +981,13 @@ int les_set_sor_config(les_handle h, int32_t tile, int32_t kc) {
     if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
     if (tile < -1 || tile >= kNumSorTiles) return fail(h, LES_EINVAL, "tile %d out of range", tile);
     h->sor = SorCfg{tile, kc};
+    h->graph_ok[0] = h->graph_ok[1] = false;
+    return LES_OK;
+}
+
+int les_set_graph(les_handle h, int32_t enable) {
+    if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
+    h->use_graph = enable != 0;
     return LES_OK;
 }
 

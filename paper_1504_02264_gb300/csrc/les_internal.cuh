@@ -42,8 +42,23 @@ struct Scalars {
     double mass_factor;     // Q_in / Q_out
     int converged;          // rel <= tol
     int nonfinite;          // a norm was NaN/Inf
-    int sweeps;             // sweeps done in the current solve (graph path)
+    int sweeps;             // sweeps done in the current solve
+    int batches;            // full check_every batches done in the current solve
+    long long step;         // time-step counter (read by bondv1 noise and adam)
+    int noconv_any;         // sticky: a solve ended above tol since the last reset
     int pad_;
+};
+
+// what the residual kernel does with the solve's bookkeeping and, inside a
+// CUDA graph, with the conditional nodes of the SOR loop
+enum ResMode { RES_INIT = 0, RES_LOOP = 1, RES_TAIL = 2, RES_HOST = 3 };
+struct CondArgs {
+    cudaGraphConditionalHandle loop, tail;
+    int use_cond;           // set the conditional handles (graph path)
+    int mode;               // ResMode
+    int n;                  // sweeps in the batch just finished
+    int n_full;             // number of full batches before the remainder
+    int rem;                // remainder batch size (0: none)
 };
 
 // constant per-run data in the compute type
@@ -73,12 +88,12 @@ struct Reduce {
 
 // launchers (les_kernels.cu); each returns the number of kernels launched
 template <typename T> int launch_bc(const Geo<T>& g, T* u, T* v, T* w, const double* inflow,
-                                    double turb, uint64_t seed, long long step, cudaStream_t s);
+                                    double turb, uint64_t seed, const Scalars* sc, cudaStream_t s);
 template <typename T> int launch_nut(const Geo<T>& g, const T* u, const T* v, const T* w, T* nut,
                                      cudaStream_t s);
 template <typename T> int launch_momentum(const Geo<T>& g, const T* u, const T* v, const T* w,
                                           const T* nut, T* fu, T* fv, T* fw, T* us, T* vs, T* ws,
-                                          int first, cudaStream_t s);
+                                          const Scalars* sc, cudaStream_t s);
 template <typename T> int launch_outflow(const Geo<T>& g, const T* u, T* us, T* vs, T* ws,
                                          Scalars* sc, cudaStream_t s);
 template <typename T> int launch_rhs(const Geo<T>& g, const T* us, const T* vs, const T* ws, T* rhs,
@@ -87,12 +102,12 @@ template <typename T> int launch_rhs_mean(const Geo<T>& g, T* rhs, double vfluid
                                           cudaStream_t s);
 template <typename T> int launch_sor_sweep(const Geo<T>& g, T* dl, const T* r, int zero_start,
                                            cudaStream_t s);
-template <typename T> int launch_refine(const Geo<T>& g, const double* ph_in, double* ph_out, const T* dl,
-                                        const T* rhs, T* r, int with_delta, double tol, double vfluid,
-                                        const Reduce& red, cudaStream_t s);
+template <typename T> int launch_accum(const Geo<T>& g, double* ph, const T* dl, cudaStream_t s);
+template <typename T> int launch_residual64(const Geo<T>& g, const double* ph, const T* rhs, T* r, double tol,
+                                            double vfluid, const Reduce& red, CondArgs ca, cudaStream_t s);
 template <typename T> int launch_project(const Geo<T>& g, const T* us, const T* vs, const T* ws,
                                          T* u, T* v, T* w, const double* ph_in, double* ph_out,
-                                         const Scalars* sc, cudaStream_t s);
+                                         Scalars* sc, cudaStream_t s);
 template <typename T> int launch_rhs_eff(const Geo<T>& g, const T* rhs, T* out, const Scalars* sc,
                                          cudaStream_t s);
 

@@ -4,7 +4,7 @@
 // Routine map (paper Sec. 2.1): k_bc_* = bondv1, k_nut = les (eddy
 // viscosity), k_momentum = velfg + les (SGS divergence) + adam + feedbf,
 // k_outflow = bondv1 outflow and mass-flux correction, k_rhs / k_sor_half /
-// k_refine = press (Sec. 2.6), k_project = velnw.
+// k_accum / k_residual64 = press (Sec. 2.6), k_project = velnw.
 #include "les_internal.cuh"
 
 namespace les {
@@ -33,7 +33,7 @@ __device__ double gauss_at(uint64_t seed, uint64_t c) {
 
 template <typename T>
 __global__ void k_bc_x(Dom d, T* u, T* v, T* w, const double* inflow, double turb, uint64_t seed,
-                       long long step) {
+                       const Scalars* sc) {
     int j = blockIdx.x * blockDim.x + threadIdx.x + 1;
     int k = blockIdx.y + 1;
     if (j > d.ny) return;
@@ -51,7 +51,7 @@ __global__ void k_bc_x(Dom d, T* u, T* v, T* w, const double* inflow, double tur
     double xu = 0.0, xv = 0.0, xw = 0.0;
     if (turb != 0.0) {
         const uint64_t sy = (uint64_t)(d.ny + 2), sz = (uint64_t)(d.nz + 2);
-        uint64_t base = (uint64_t)step * 3ull;
+        uint64_t base = (uint64_t)sc->step * 3ull;
         xu = gauss_at(seed, ((base + 0) * sy + (uint64_t)j) * sz + (uint64_t)k);
         xv = gauss_at(seed, ((base + 1) * sy + (uint64_t)j) * sz + (uint64_t)k);
         xw = gauss_at(seed, ((base + 2) * sy + (uint64_t)j) * sz + (uint64_t)k);
@@ -116,9 +116,9 @@ __global__ void k_bc_z(Dom d, T* u, T* v, T* w) {
 
 template <typename T>
 int launch_bc(const Geo<T>& g, T* u, T* v, T* w, const double* inflow, double turb, uint64_t seed,
-              long long step, cudaStream_t s) {
+              const Scalars* sc, cudaStream_t s) {
     const Dom& d = g.d;
-    k_bc_x<T><<<dim3((d.ny + 127) / 128, d.nz), 128, 0, s>>>(d, u, v, w, inflow, turb, seed, step);
+    k_bc_x<T><<<dim3((d.ny + 127) / 128, d.nz), 128, 0, s>>>(d, u, v, w, inflow, turb, seed, sc);
     k_bc_y<T><<<dim3((d.nx + 2 + 127) / 128, d.nz), 128, 0, s>>>(d, u, v, w);
     k_bc_z<T><<<dim3((d.nx + 2 + 127) / 128, d.ny + 2), 128, 0, s>>>(d, u, v, w);
     return 3;
@@ -293,8 +293,9 @@ __device__ __forceinline__ T sgs_w(const Geo<T>& g, const Stencil<T>& S, const N
 
 template <typename T>
 __global__ void k_momentum(Geo<T> g, const T* u, const T* v, const T* w, const T* nut, T* fu, T* fv,
-                           T* fw, T* us, T* vs, T* ws, int first) {
+                           T* fw, T* us, T* vs, T* ws, const Scalars* sc) {
     const Dom& d = g.d;
+    const bool first = sc->step == 0;
     int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
     int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
     int k = blockIdx.z + 1;
@@ -325,10 +326,10 @@ __global__ void k_momentum(Geo<T> g, const T* u, const T* v, const T* w, const T
 
 template <typename T>
 int launch_momentum(const Geo<T>& g, const T* u, const T* v, const T* w, const T* nut, T* fu, T* fv,
-                    T* fw, T* us, T* vs, T* ws, int first, cudaStream_t s) {
+                    T* fw, T* us, T* vs, T* ws, const Scalars* sc, cudaStream_t s) {
     const Dom& d = g.d;
     k_momentum<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(
-        g, u, v, w, nut, fu, fv, fw, us, vs, ws, first);
+        g, u, v, w, nut, fu, fv, fw, us, vs, ws, sc);
     return 1;
 }
 
@@ -600,12 +601,31 @@ int launch_sor_sweep(const Geo<T>& g, T* dl, const T* r, int zero_start, cudaStr
     return 2;
 }
 
-// Refinement step: P = ph_in + d (with_delta) is written to ph_out, and
-// r = (rhs - mean) - A P is formed in FP64, stored in T, and reduced to
-// FP64 norms; the dz-weighted fluid mean of P (for the gauge) comes along.
+// Refinement: ph += d on the unknowns (own cell only, so in place).
 template <typename T>
-__global__ void k_refine(Geo<T> g, const double* ph_in, double* ph_out, const T* dl, const T* rhs, T* r,
-                         int with_delta, double tol, double vfluid, Reduce red) {
+__global__ void k_accum(Geo<T> g, double* ph, const T* dl) {
+    const Dom& d = g.d;
+    int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    int k = blockIdx.z + 1;
+    if (i > d.nx || j > d.ny) return;
+    long long c = d.at(i, j, k);
+    if (g.flags[c] & F_UNK) ph[c] += (double)dl[c];
+}
+
+template <typename T>
+int launch_accum(const Geo<T>& g, double* ph, const T* dl, cudaStream_t s) {
+    const Dom& d = g.d;
+    k_accum<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(g, ph, dl);
+    return 1;
+}
+
+// r = (rhs - mean) - A ph formed in FP64 and stored in T; FP64 norms, the
+// stop test, the dz-weighted fluid mean of ph (for the gauge) and the
+// bookkeeping of the SOR loop (and its graph conditionals) in the last block.
+template <typename T>
+__global__ void k_residual64(Geo<T> g, const double* ph, const T* rhs, T* r, double tol, double vfluid,
+                             Reduce red, CondArgs ca) {
     const Dom& d = g.d;
     int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
     int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
@@ -614,9 +634,7 @@ __global__ void k_refine(Geo<T> g, const double* ph_in, double* ph_out, const T*
     if (i <= d.nx && j <= d.ny) {
         long long c = d.at(i, j, k);
         const uint8_t f = g.flags[c];
-        auto P = [&](long long q) -> double { return with_delta ? ph_in[q] + (double)dl[q] : ph_in[q]; };
-        const double pc = P(c);
-        if (with_delta) ph_out[c] = pc;
+        const double pc = ph[c];
         if (f & F_UNK) {
             Poisson<T> Q{g};
             double ae, aw, an, as, at, ab;
@@ -624,12 +642,12 @@ __global__ void k_refine(Geo<T> g, const double* ph_in, double* ph_out, const T*
             long long e, w, n, s_, t, b;
             Q.nbr(i, j, k, e, w, n, s_, t, b);
             double s = 0.0;
-            s += ae * P(e);
-            s += aw * P(w);
-            s += an * P(n);
-            s += as * P(s_);
-            s += at * P(t);
-            s += ab * P(b);
+            s += ae * ph[e];
+            s += aw * ph[w];
+            s += an * ph[n];
+            s += as * ph[s_];
+            s += at * ph[t];
+            s += ab * ph[b];
             const double diag = ae + aw + an + as + at + ab;
             const double bb = (double)rhs[c] - red.sc->rhs_mean;
             const double res = bb - (s - diag * pc);
@@ -644,21 +662,44 @@ __global__ void k_refine(Geo<T> g, const double* ph_in, double* ph_out, const T*
             Scalars* sc = red.sc;
             sc->res2 = x[0];
             sc->rhs2 = x[1];
-            double rel = x[1] == 0.0 ? sqrt(x[0]) : sqrt(x[0] / x[1]);
+            const double rel = x[1] == 0.0 ? sqrt(x[0]) : sqrt(x[0] / x[1]);
+            const bool conv = rel <= tol;
+            const bool bad = !isfinite(rel);
             sc->rel = rel;
-            sc->converged = rel <= tol;
-            sc->nonfinite = !isfinite(rel);
+            sc->converged = conv;
+            sc->nonfinite = bad;
             sc->p_mean = vfluid > 0.0 ? x[2] / vfluid : 0.0;
+            bool go = false, tail = false, final_check = false;
+            if (ca.mode == RES_INIT) {
+                sc->sweeps = 0;
+                sc->batches = 0;
+                go = ca.n_full > 0;
+                tail = ca.n_full == 0 && ca.rem > 0;
+            } else if (ca.mode == RES_LOOP) {
+                sc->sweeps += ca.n;
+                sc->batches += 1;
+                go = !conv && !bad && sc->batches < ca.n_full;
+                tail = !conv && !bad && sc->batches == ca.n_full && ca.rem > 0;
+                final_check = !go && !tail;
+            } else {
+                sc->sweeps += ca.n;
+                final_check = ca.mode == RES_TAIL;
+            }
+            if (final_check && !conv) sc->noconv_any = 1;
+            if (ca.use_cond) {
+                cudaGraphSetConditional(ca.loop, go ? 1u : 0u);
+                cudaGraphSetConditional(ca.tail, tail ? 1u : 0u);
+            }
         }
     }
 }
 
 template <typename T>
-int launch_refine(const Geo<T>& g, const double* ph_in, double* ph_out, const T* dl, const T* rhs, T* r,
-                  int with_delta, double tol, double vfluid, const Reduce& red, cudaStream_t s) {
+int launch_residual64(const Geo<T>& g, const double* ph, const T* rhs, T* r, double tol, double vfluid,
+                      const Reduce& red, CondArgs ca, cudaStream_t s) {
     const Dom& d = g.d;
-    k_refine<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(
-        g, ph_in, ph_out, dl, rhs, r, with_delta, tol, vfluid, red);
+    k_residual64<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(
+        g, ph, rhs, r, tol, vfluid, red, ca);
     return 1;
 }
 
@@ -669,11 +710,13 @@ int launch_refine(const Geo<T>& g, const double* ph_in, double* ph_out, const T*
 
 template <typename T>
 __global__ void k_project(Geo<T> g, const T* us, const T* vs, const T* ws, T* u, T* v, T* w,
-                          const double* ph_in, double* ph_out, const Scalars* sc) {
+                          const double* ph_in, double* ph_out, Scalars* sc) {
     const Dom& d = g.d;
     int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
     int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
     int k = blockIdx.z + 1;
+    // the step counter advances here, after every reader of it has run
+    if (i == 1 && j == 1 && k == 1) sc->step += 1;
     if (i > d.nx || j > d.ny) return;
     long long c = d.at(i, j, k);
     const uint8_t f = g.flags[c];
@@ -716,7 +759,7 @@ __global__ void k_project(Geo<T> g, const T* us, const T* vs, const T* ws, T* u,
 
 template <typename T>
 int launch_project(const Geo<T>& g, const T* us, const T* vs, const T* ws, T* u, T* v, T* w,
-                   const double* ph_in, double* ph_out, const Scalars* sc, cudaStream_t s) {
+                   const double* ph_in, double* ph_out, Scalars* sc, cudaStream_t s) {
     const Dom& d = g.d;
     k_project<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(
         g, us, vs, ws, u, v, w, ph_in, ph_out, sc);
@@ -764,20 +807,21 @@ int launch_rhs_eff(const Geo<T>& g, const T* rhs, T* out, const Scalars* sc, cud
 int max_reduce_blocks(const Dom& d) { return ((d.nx + 31) / 32) * ((d.ny + 7) / 8) * d.nz; }
 
 #define LES_INSTANTIATE(T)                                                                              \
-    template int launch_bc<T>(const Geo<T>&, T*, T*, T*, const double*, double, uint64_t, long long,    \
-                              cudaStream_t);                                                            \
+    template int launch_bc<T>(const Geo<T>&, T*, T*, T*, const double*, double, uint64_t,               \
+                              const Scalars*, cudaStream_t);                                            \
     template int launch_nut<T>(const Geo<T>&, const T*, const T*, const T*, T*, cudaStream_t);          \
     template int launch_momentum<T>(const Geo<T>&, const T*, const T*, const T*, const T*, T*, T*, T*,  \
-                                    T*, T*, T*, int, cudaStream_t);                                     \
+                                    T*, T*, T*, const Scalars*, cudaStream_t);                          \
     template int launch_outflow<T>(const Geo<T>&, const T*, T*, T*, T*, Scalars*, cudaStream_t);        \
     template int launch_rhs<T>(const Geo<T>&, const T*, const T*, const T*, T*, double, const Reduce&,  \
                                cudaStream_t);                                                           \
     template int launch_rhs_mean<T>(const Geo<T>&, T*, double, const Reduce&, cudaStream_t);            \
     template int launch_sor_sweep<T>(const Geo<T>&, T*, const T*, int, cudaStream_t);                   \
-    template int launch_refine<T>(const Geo<T>&, const double*, double*, const T*, const T*, T*, int,   \
-                                  double, double, const Reduce&, cudaStream_t);                         \
+    template int launch_accum<T>(const Geo<T>&, double*, const T*, cudaStream_t);                      \
+    template int launch_residual64<T>(const Geo<T>&, const double*, const T*, T*, double, double,       \
+                                      const Reduce&, CondArgs, cudaStream_t);                           \
     template int launch_project<T>(const Geo<T>&, const T*, const T*, const T*, T*, T*, T*,             \
-                                   const double*, double*, const Scalars*, cudaStream_t);               \
+                                   const double*, double*, Scalars*, cudaStream_t);                     \
     template int launch_rhs_eff<T>(const Geo<T>&, const T*, T*, const Scalars*, cudaStream_t);          \
     template int launch_gauge<T>(const Geo<T>&, const double*, double*, const Scalars*, cudaStream_t);
 

@@ -265,3 +265,41 @@ def test_autotune_picks_a_valid_config():
     d2.step(1)
     for a, b in zip(before, d2.fields()):
         assert np.array_equal(a, b)      # tuning sweeps never touch the state
+
+
+# ---------------------------------------------------------------------------
+# CUDA-graph step (device-side stop test) against the host-driven loop
+
+@pytest.mark.parametrize("mode", ["tol", "tol_remainder", "fixed"])
+def test_graph_step_matches_host_loop(mode):
+    if mode == "tol":
+        sc = city(turb=0.1, fixed_sweeps=0, tol=1e-6, max_sweeps=5000, check_every=10)
+    elif mode == "tol_remainder":
+        sc = city(turb=0.1, fixed_sweeps=0, tol=1e-12, max_sweeps=37, check_every=10)
+    else:
+        sc = city(turb=0.1, fixed_sweeps=1, max_sweeps=23)
+    a = les.Domain(sc, precision=les.LES_FP64)
+    a.set_graph(False)
+    b = les.Domain(sc, precision=les.LES_FP64)
+    b.set_graph(True)
+    for _ in range(3):
+        sa = a.step(1)
+        sb = b.step(1)
+        assert sa["sweeps"] == sb["sweeps"] and sa["rc"] == sb["rc"], (sa, sb)
+        assert sa["step"] == sb["step"]
+    for x, y in zip(a.fields(), b.fields()):
+        assert np.array_equal(x, y)
+    if mode == "tol_remainder":
+        assert sb["rc"] == les.LES_ENOCONV and sb["sweeps"] == 37
+
+
+def test_graph_multi_step_call_matches_single_steps():
+    sc = city(turb=0.1, fixed_sweeps=0, tol=1e-6, max_sweeps=5000, check_every=10)
+    a = les.Domain(sc, precision=les.LES_FP32)
+    for _ in range(4):
+        a.step(1)
+    b = les.Domain(sc, precision=les.LES_FP32)
+    st = b.step(4)
+    assert st["step"] == 4 and st["rc"] == 0
+    for x, y in zip(a.fields(), b.fields()):
+        assert np.array_equal(x, y)
