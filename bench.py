@@ -41,7 +41,7 @@ L2_FLUSH_BYTES = 256 << 20
 # mean SOR sweeps per step of this workload after the default warm-up, from the
 # GPU arm (the FP64 path takes the same sweeps as the oracle); used only to scale
 # the bounded oracle sample to a full step when no GPU run is available
-REF_SWEEPS_PER_STEP = 400
+REF_SWEEPS_PER_STEP = 13600
 
 
 def workload(seed=0):
@@ -198,13 +198,15 @@ def run_ours(args):
         st = dom.step(1)
         if st["rc"] < 0:
             raise RuntimeError(st)
+    # set-up, not timed: pick the SOR tile shape and k-chunk for this grid
+    (tile, kc), tune_ms = dom.autotune_sor(sweeps=20)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
 
-    dom.set_timing(True)
+    # timed region 1: the library's default step (one CUDA graph per step)
     l0 = dom.timing()["launches"]
-    clocks = Clocks(local) if rank == 0 else None
+    clocks = Clocks(local) if (rank == 0 and not args.ncu_range) else None
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     sweeps = []
     worst = 0.0
@@ -223,24 +225,30 @@ def run_ours(args):
     torch.cuda.synchronize()
     if args.ncu_range:
         torch.cuda.profiler.stop()
-    tm = dom.timing()
     clk = clocks.stop() if clocks else None
-    launches = tm["launches"] - l0
+    launches = dom.timing()["launches"] - l0
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     if world > 1:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
+
+    # timed region 2: same steps, host-driven, with CUDA events around every
+    # batch of SOR sweep launches on the library's stream (kernel roofline)
+    dom.set_timing(True)
+    for s in range(min(args.steps, 3)):
+        flush.zero_()
+        dom.step(1)
+    torch.cuda.synchronize()
+    tm = dom.timing()
     dom.set_timing(False)
 
     # end to end through the C ABI with pinned host buffers
     shapes = dom.shapes()
     host = [torch.empty(s, dtype=torch.float32, pin_memory=True).numpy() for s in shapes]
-    dom_e2e = dom
-    fields0 = dom.fields()
-    for h, f in zip(host, fields0):
+    for h, f in zip(host, dom.fields()):
         h[...] = f
-    e2e_steps = max(1, min(args.steps, 10))
+    e2e_steps = max(1, min(args.steps, 3))
     h2d = sum(h.nbytes for h in host)
     torch.cuda.synchronize()
     ee = []
@@ -248,9 +256,9 @@ def run_ours(args):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        les.les_set_fields(dom_e2e.h, *host)
-        les.les_step(dom_e2e.h, 1, les.les_stats_t())
-        les.les_get_fields(dom_e2e.h, *host)
+        les.les_set_fields(dom.h, *host)
+        les.les_step(dom.h, 1, les.les_stats_t())
+        les.les_get_fields(dom.h, *host)
         b.record(stream)
         b.synchronize()
         ee.append(a.elapsed_time(b))
@@ -277,7 +285,8 @@ def run_ours(args):
                        "tol": 1e-6, "check_every": sc.check_every, "mean_sweeps_per_step": mean_sweeps,
                        "max_rel_residual": worst, "parallelism": f"replicas x{world}",
                        "l2": "flushed (256 MiB write) before every timed step"},
-            "roofline": {"kernel": "k_sor_half (red-black SOR half-sweep)", "bound": "hbm",
+            "roofline": {"kernel": f"k_sor_fused (red-black SOR sweep, tile {les.les_sor_tile(tile) if tile >= 0 else 'two-pass'}, kc {kc})",
+                         "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "traffic": None,
                          "bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms,
@@ -286,6 +295,7 @@ def run_ours(args):
                                   ("ms_momentum", "ms_sor", "ms_residual", "ms_project")},
             "sor_ms_per_sweep": sweep_ms,
             "gpu_launches": int(launches),
+            "sor_autotune": {"tile": tile, "kc": kc, "ms_per_sweep": tune_ms},
             "e2e": {"value": n * world / (e2e_ms * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": h2d, "ms_per_step": e2e_ms, "steps": e2e_steps},
             "clocks": clk,

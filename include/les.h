@@ -218,6 +218,10 @@ int les_get_sor_config(les_handle h, int32_t* tile, int32_t* kc);
 int les_sor_tile(int32_t tile, int32_t* tx, int32_t* ty);
 int les_autotune_sor(les_handle h, int32_t sweeps, double* best_ms_per_sweep);
 
+/* Bracket a region for a profiler started with capture off
+ * (cudaProfilerStart when start != 0, cudaProfilerStop otherwise). */
+int les_profiler_range(int32_t start);
+
 /* Library version string. */
 const char* les_version(void);
 

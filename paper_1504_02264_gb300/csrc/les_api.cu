@@ -6,6 +6,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda_profiler_api.h>
+
 #include "../../include/les.h"
 #include "les_internal.cuh"
 
@@ -105,8 +107,9 @@ struct les_s {
     bool use_graph = true;
     bool graph_ok[2] = {false, false};
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    cudaStream_t cap[2] = {nullptr, nullptr};
-    cudaGraphConditionalHandle cond_loop = 0, cond_tail = 0;
+    cudaStream_t cap[3] = {nullptr, nullptr, nullptr};
+    cudaGraphConditionalHandle cond_loop = 0, cond_tail = 0, cond_refine = 0;
+    int dcur = 0;                         // buffer holding the current SOR correction
     // phase timing
     bool timing = false;
     cudaEvent_t ev[8] = {};
@@ -248,101 +251,108 @@ double elapsed(les_s* h, int a, int b) {
 // relative residual is tested after each batch of check_every sweeps and at
 // max_sweeps, exactly where the sequential algorithm tests it.
 
-// n sweeps on the correction from d = 0; returns the buffer holding the result
+// n sweeps on the correction.  zero: 0 continue from d, 1 start from d = 0,
+// 2 read the device flag.  The fused kernel ping-pongs between the two d
+// buffers starting from dl[h->dcur]; the result's buffer index is returned
+// (and becomes dcur).
 template <typename T>
-int run_sweeps(les_s* h, const Geo<T>& g, int n, long long& launched, cudaStream_t st) {
+int run_sweeps(les_s* h, const Geo<T>& g, int n, int zero, long long& launched, cudaStream_t st) {
     T* rr = (T*)h->rr;
     if (h->sor.tile < 0) {
-        for (int s = 0; s < n; ++s) launched += launch_sor_sweep<T>(g, (T*)h->dl[0], rr, s == 0, st);
-        return 0;
+        for (int s = 0; s < n; ++s) launched += launch_sor_sweep<T>(g, (T*)h->dl[0], rr, s == 0 ? zero : 0, h->sc, st);
+        return h->dcur = 0;
     }
-    int out = 0;
     for (int s = 0; s < n; ++s) {
-        out = s & 1;
-        launched += launch_sor_fused<T>(g, (const T*)h->dl[1 - out], (T*)h->dl[out], rr, s == 0, h->sor, st);
+        const int in = h->dcur, out = 1 - h->dcur;
+        launched += launch_sor_fused<T>(g, (const T*)h->dl[in], (T*)h->dl[out], rr, s == 0 ? zero : 0, h->sc, h->sor,
+                                        st);
+        h->dcur = out;
     }
-    return out;
+    return h->dcur;
 }
 
-CondArgs cond_args(const les_s* h, int mode, int n, bool use_cond) {
+CondArgs cond_args(const les_s* h, int mode, int n, bool use_cond, int limit, int rem) {
     CondArgs ca{};
     ca.loop = h->cond_loop;
     ca.tail = h->cond_tail;
+    ca.refine = h->cond_refine;
     ca.use_cond = use_cond ? 1 : 0;
     ca.mode = mode;
     ca.n = n;
-    const les_grid_t& G = h->g;
-    if (G.fixed_sweeps) {
-        ca.n_full = 0;
-        ca.rem = G.max_sweeps;
-    } else {
-        ca.n_full = G.max_sweeps / G.check_every;
-        ca.rem = G.max_sweeps % G.check_every;
-    }
+    ca.limit = limit;
+    ca.rem = rem;
+    ca.tol = h->g.tol;
     return ca;
 }
 
-// one batch: sweeps, accumulate, residual (all on stream st)
 template <typename T>
-int sor_batch(les_s* h, const Geo<T>& g, int n, int mode, bool use_cond, cudaStream_t st, long long* sweep_launches) {
-    long long nl = 0;
-    int out = run_sweeps<T>(h, g, n, nl, st);
-    if (sweep_launches) *sweep_launches = nl;
-    h->launches += nl;
-    if (h->timing && !use_cond) rec(h, 3);
-    h->launches += launch_accum<T>(g, h->ph[h->cur], (const T*)h->dl[out], st);
-    h->launches += launch_residual64<T>(g, h->ph[h->cur], (const T*)h->rhs, (T*)h->rr, h->g.tol, h->vfluid,
-                                        reducer(h), cond_args(h, mode, n, use_cond), st);
-    return LES_OK;
+void launch_refine(les_s* h, const Geo<T>& g, const CondArgs& ca, cudaStream_t st) {
+    h->launches += launch_accum<T>(g, h->ph[h->cur], (const T*)h->dl[h->dcur], st);
+    h->launches += launch_residual64<T>(g, h->ph[h->cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h), ca, st);
 }
 
-// host-driven loop (stop decision read back after every batch)
+// Host-driven loop.  After each batch of check_every sweeps the cheap
+// estimate is read back; when it asks for it, the FP64 refinement runs and
+// its true relative residual decides convergence.
 template <typename T>
 int sor_solve(les_s* h) {
     Geo<T> g = geo<T>(h);
     const les_grid_t& G = h->g;
-    int sweeps = 0;
+    const int limit = G.max_sweeps;
     rec(h, 2);
-    h->launches += launch_residual64<T>(g, h->ph[h->cur], (const T*)h->rhs, (T*)h->rr, G.tol, h->vfluid, reducer(h),
-                                        cond_args(h, RES_INIT, 0, false), h->stream);
+    h->launches += launch_residual64<T>(g, h->ph[h->cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h),
+                                        cond_args(h, RES_INIT, 0, false, limit, 0), h->stream);
     rec(h, 3);
     CK(cudaGetLastError());
     if (h->timing) {
         CK(cudaEventSynchronize(h->ev[3]));
         h->tm.ms_residual += elapsed(h, 2, 3);
     }
-    auto batch = [&](int n) -> int {
+    int sweeps = 0;
+    bool fresh = true, conv = false;
+    while (sweeps < G.max_sweeps) {
+        const int n = G.fixed_sweeps ? G.max_sweeps
+                                     : (G.check_every < G.max_sweeps - sweeps ? G.check_every : G.max_sweeps - sweeps);
         rec(h, 2);
         long long nl = 0;
-        sor_batch<T>(h, g, n, RES_HOST, false, h->stream, &nl);
+        run_sweeps<T>(h, g, n, fresh ? 1 : 0, nl, h->stream);
+        h->launches += nl;
+        rec(h, 3);
+        sweeps += n;
+        bool need = true;
+        if (!G.fixed_sweeps) {
+            h->launches += launch_sor_est<T>(g, (const T*)h->dl[h->dcur], (const T*)h->rr, reducer(h),
+                                             cond_args(h, RES_HOST, n, false, limit, 0), h->stream);
+            CK(cudaGetLastError());
+            int rc = fetch_scalars(h);
+            if (rc) return rc;
+            need = h->sc_host->refine != 0;
+        }
         rec(h, 4);
-        CK(cudaGetLastError());
-        int rc = fetch_scalars(h);
-        if (rc) return rc;
         if (h->timing) {
+            CK(cudaEventSynchronize(h->ev[4]));
             h->tm.ms_sor += elapsed(h, 2, 3);
             h->tm.ms_residual += elapsed(h, 3, 4);
             h->tm.sor_sweeps += n;
             h->tm.sor_launches += nl;
         }
-        return LES_OK;
-    };
-    if (G.fixed_sweeps) {
-        int rc = batch(G.max_sweeps);
-        if (rc) return rc;
-        sweeps = G.max_sweeps;
-    } else {
-        while (sweeps < G.max_sweeps) {
-            int n = G.check_every < G.max_sweeps - sweeps ? G.check_every : G.max_sweeps - sweeps;
-            int rc = batch(n);
+        fresh = false;
+        if (need) {
+            rec(h, 3);
+            launch_refine<T>(h, g, cond_args(h, G.fixed_sweeps ? RES_TAIL : RES_HOST, n, false, limit, 0), h->stream);
+            rec(h, 4);
+            CK(cudaGetLastError());
+            int rc = fetch_scalars(h);
             if (rc) return rc;
-            sweeps += n;
-            if (h->sc_host->converged || h->sc_host->nonfinite) break;
+            if (h->timing) h->tm.ms_residual += elapsed(h, 3, 4);
+            fresh = true;
+            conv = h->sc_host->converged != 0;
+            if (conv || h->sc_host->nonfinite) break;
         }
     }
     h->sc_host->sweeps = sweeps;
     if (h->sc_host->nonfinite) return fail(h, LES_ENONFINITE, "SOR residual is not finite");
-    return (!G.fixed_sweeps && !h->sc_host->converged) ? LES_ENOCONV : LES_OK;
+    return (!G.fixed_sweeps && !conv) ? LES_ENOCONV : LES_OK;
 }
 
 // Time `sweeps` sweeps per candidate (tile shape x k-chunk) on the current
@@ -362,9 +372,9 @@ int autotune_impl(les_s* h, int sweeps, double* best_ms) {
             if (kc > h->g.nz) continue;
             h->sor = SorCfg{t, kc};
             long long nl = 0;
-            run_sweeps<T>(h, g, 2, nl, h->stream);       // warm
+            run_sweeps<T>(h, g, 2, 0, nl, h->stream);       // warm
             CK(cudaEventRecord(a, h->stream));
-            run_sweeps<T>(h, g, sweeps, nl, h->stream);
+            run_sweeps<T>(h, g, sweeps, 0, nl, h->stream);
             CK(cudaEventRecord(b, h->stream));
             CK(cudaEventSynchronize(b));
             h->launches += nl;
@@ -430,11 +440,13 @@ int step_host(les_s* h) {
     return rc;
 }
 
-// The whole step as one CUDA graph: prefix, initial residual, a conditional
-// WHILE node over full batches of check_every sweeps, a conditional IF node for
-// the remainder batch, projection.  The stop test runs on the device
-// (k_residual64 sets the conditions), so a step needs no host round trip.
-// One graph per pressure buffer parity (velnw writes the gauged p to the other).
+// The whole step as one CUDA graph: prefix kernels, the FP64 initial
+// residual, a conditional WHILE node whose body runs check_every sweeps and
+// the cheap estimate, with a nested IF node for the FP64 refinement, then a
+// conditional IF node for the remainder batch, then the projection.  The stop
+// test runs on the device (k_sor_est / k_residual64 set the conditions), so a
+// step needs no host round trip.  One graph per pressure-buffer parity
+// (velnw writes the gauged p to the other buffer).
 template <typename T>
 int build_graph(les_s* h, int cur) {
     Geo<T> g = geo<T>(h);
@@ -443,81 +455,108 @@ int build_graph(les_s* h, int cur) {
         cudaGraphExecDestroy(h->gexec[cur]);
         h->gexec[cur] = nullptr;
     }
-    cudaStream_t cs = h->cap[0], cb = h->cap[1];
-    const int save_cur = h->cur;
+    cudaStream_t cs = h->cap[0], cb = h->cap[1], cc = h->cap[2];
+    const int save_cur = h->cur, save_dcur = h->dcur;
+    const long long l0 = h->launches;
     h->cur = cur;
-    long long l0 = h->launches;
-    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    h->dcur = 0;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return fail(h, LES_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    auto abort_capture = [&](cudaError_t err, const char* what) {
+        cudaGraph_t junk = nullptr;
+        cudaStreamEndCapture(cs, &junk);
+        if (junk) cudaGraphDestroy(junk);
+        h->cur = save_cur;
+        h->dcur = save_dcur;
+        h->launches = l0;
+        return fail(h, LES_ECUDA, "graph build (%s): %s", what, cudaGetErrorString(err));
+    };
     launch_prefix<T>(h, g, cs);
     cudaStreamCaptureStatus cst;
     cudaGraph_t graph;
     const cudaGraphNode_t* deps = nullptr;
     size_t ndeps = 0;
-    auto abort_capture = [&](cudaError_t e, const char* what) {
-        cudaGraph_t junk;
-        cudaStreamEndCapture(cs, &junk);
-        if (junk) cudaGraphDestroy(junk);
-        h->cur = save_cur;
-        return fail(h, LES_ECUDA, "graph build (%s): %s", what, cudaGetErrorString(e));
+    auto add_cond = [&](cudaGraph_t gr, const cudaGraphNode_t* dp, size_t nd, cudaGraphConditionalHandle hd,
+                        cudaGraphConditionalNodeType type, cudaGraphNode_t* node, cudaGraph_t* body) -> cudaError_t {
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = hd;
+        np.conditional.type = type;
+        np.conditional.size = 1;
+        cudaError_t err = cudaGraphAddNode(node, gr, dp, nullptr, nd, &np);
+        if (err == cudaSuccess) *body = np.conditional.phGraph_out[0];
+        return err;
     };
-    cudaError_t e;
     if (G.fixed_sweeps) {
-        launch_residual64<T>(g, h->ph[cur], (const T*)h->rhs, (T*)h->rr, G.tol, h->vfluid, reducer(h),
-                             cond_args(h, RES_INIT, 0, false), cs);
-        sor_batch<T>(h, g, G.max_sweeps, RES_TAIL, false, cs, nullptr);
+        launch_residual64<T>(g, h->ph[cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h),
+                             cond_args(h, RES_INIT, 0, false, 0, 0), cs);
+        long long nl = 0;
+        run_sweeps<T>(h, g, G.max_sweeps, 1, nl, cs);
+        launch_refine<T>(h, g, cond_args(h, RES_TAIL, G.max_sweeps, false, 0, 0), cs);
     } else {
+        const int limit = (G.max_sweeps / G.check_every) * G.check_every;
+        const int rem = G.max_sweeps - limit;
         e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph, nullptr, nullptr, nullptr);
         if (e != cudaSuccess) return abort_capture(e, "capture info");
         e = cudaGraphConditionalHandleCreate(&h->cond_loop, graph, 0, 0);
-        if (e != cudaSuccess) return abort_capture(e, "loop handle");
-        e = cudaGraphConditionalHandleCreate(&h->cond_tail, graph, 0, 0);
-        if (e != cudaSuccess) return abort_capture(e, "tail handle");
-        launch_residual64<T>(g, h->ph[cur], (const T*)h->rhs, (T*)h->rr, G.tol, h->vfluid, reducer(h),
-                             cond_args(h, RES_INIT, 0, true), cs);
-        const CondArgs ca = cond_args(h, RES_LOOP, G.check_every, true);
-        // WHILE node over full batches
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h->cond_tail, graph, 0, 0);
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h->cond_refine, graph, 0, 0);
+        if (e != cudaSuccess) return abort_capture(e, "conditional handles");
+        launch_residual64<T>(g, h->ph[cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h),
+                             cond_args(h, RES_INIT, 0, true, limit, rem), cs);
         e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph, &deps, nullptr, &ndeps);
         if (e != cudaSuccess) return abort_capture(e, "capture info");
-        cudaGraphNodeParams wp = {};
-        wp.type = cudaGraphNodeTypeConditional;
-        wp.conditional.handle = h->cond_loop;
-        wp.conditional.type = cudaGraphCondTypeWhile;
-        wp.conditional.size = 1;
-        cudaGraphNode_t wnode;
-        e = cudaGraphAddNode(&wnode, graph, deps, nullptr, ndeps, &wp);
+        cudaGraphNode_t wnode, rnode;
+        cudaGraph_t wbody, rbody;
+        e = add_cond(graph, deps, ndeps, h->cond_loop, cudaGraphCondTypeWhile, &wnode, &wbody);
         if (e != cudaSuccess) return abort_capture(e, "while node");
-        cudaGraph_t body = wp.conditional.phGraph_out[0];
-        e = cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        // WHILE body: sweeps + estimate, then IF(refine) { accumulate + FP64 residual }
+        e = cudaStreamBeginCaptureToGraph(cb, wbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
         if (e != cudaSuccess) return abort_capture(e, "while body");
-        sor_batch<T>(h, g, G.check_every, RES_LOOP, true, cb, nullptr);
-        e = cudaStreamEndCapture(cb, &body);
+        long long nl = 0;
+        h->dcur = 0;
+        run_sweeps<T>(h, g, G.check_every, 2, nl, cb);       // check_every even: d returns to dl[0]
+        h->launches += launch_sor_est<T>(g, (const T*)h->dl[h->dcur], (const T*)h->rr, reducer(h),
+                                         cond_args(h, RES_LOOP, G.check_every, true, limit, rem), cb);
+        const cudaGraphNode_t* bdeps = nullptr;
+        size_t nbdeps = 0;
+        cudaGraph_t bgraph;
+        e = cudaStreamGetCaptureInfo(cb, &cst, nullptr, &bgraph, &bdeps, nullptr, &nbdeps);
+        if (e != cudaSuccess) return abort_capture(e, "body capture info");
+        e = add_cond(bgraph, bdeps, nbdeps, h->cond_refine, cudaGraphCondTypeIf, &rnode, &rbody);
+        if (e != cudaSuccess) return abort_capture(e, "refine node");
+        e = cudaStreamUpdateCaptureDependencies(cb, &rnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (e != cudaSuccess) return abort_capture(e, "body dependencies");
+        e = cudaStreamEndCapture(cb, &wbody);
         if (e != cudaSuccess) return abort_capture(e, "while body end");
-        (void)ca;
+        e = cudaStreamBeginCaptureToGraph(cc, rbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) return abort_capture(e, "refine body");
+        launch_refine<T>(h, g, cond_args(h, RES_LOOP, G.check_every, true, limit, rem), cc);
+        e = cudaStreamEndCapture(cc, &rbody);
+        if (e != cudaSuccess) return abort_capture(e, "refine body end");
         cudaGraphNode_t last = wnode;
-        if (cond_args(h, RES_LOOP, 0, true).rem > 0) {
-            cudaGraphNodeParams ip = {};
-            ip.type = cudaGraphNodeTypeConditional;
-            ip.conditional.handle = h->cond_tail;
-            ip.conditional.type = cudaGraphCondTypeIf;
-            ip.conditional.size = 1;
+        if (rem > 0) {
             cudaGraphNode_t inode;
-            e = cudaGraphAddNode(&inode, graph, &wnode, nullptr, 1, &ip);
-            if (e != cudaSuccess) return abort_capture(e, "if node");
-            cudaGraph_t tbody = ip.conditional.phGraph_out[0];
+            cudaGraph_t tbody;
+            e = add_cond(graph, &wnode, 1, h->cond_tail, cudaGraphCondTypeIf, &inode, &tbody);
+            if (e != cudaSuccess) return abort_capture(e, "tail node");
             e = cudaStreamBeginCaptureToGraph(cb, tbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-            if (e != cudaSuccess) return abort_capture(e, "if body");
-            sor_batch<T>(h, g, cond_args(h, RES_TAIL, 0, true).rem, RES_TAIL, true, cb, nullptr);
+            if (e != cudaSuccess) return abort_capture(e, "tail body");
+            h->dcur = 0;
+            run_sweeps<T>(h, g, rem, 1, nl, cb);
+            launch_refine<T>(h, g, cond_args(h, RES_TAIL, rem, true, limit, rem), cb);
             e = cudaStreamEndCapture(cb, &tbody);
-            if (e != cudaSuccess) return abort_capture(e, "if body end");
+            if (e != cudaSuccess) return abort_capture(e, "tail body end");
             last = inode;
         }
         e = cudaStreamUpdateCaptureDependencies(cs, &last, nullptr, 1, cudaStreamSetCaptureDependencies);
         if (e != cudaSuccess) return abort_capture(e, "dependencies");
     }
     launch_project_step<T>(h, g, cur, cs);
-    cudaGraph_t full;
+    cudaGraph_t full = nullptr;
     e = cudaStreamEndCapture(cs, &full);
     h->cur = save_cur;
+    h->dcur = save_dcur;
     h->launches = l0;          // capture launches nothing
     if (e != cudaSuccess) return fail(h, LES_ECUDA, "graph capture: %s", cudaGetErrorString(e));
     e = cudaGraphInstantiate(&h->gexec[cur], full, 0);
@@ -534,8 +573,9 @@ long long graph_step_launches(const les_s* h, int sweeps) {
     int pre = 3 + 1 + 1 + 1 + (h->d.pery ? 1 : 0) + (h->d.perz ? 1 : 0) + 1;
     const les_grid_t& G = h->g;
     int per_sweep = h->sor.tile < 0 ? 2 : 1;
-    int batches = G.fixed_sweeps ? 1 : (sweeps + G.check_every - 1) / G.check_every;
-    return pre + 1 + (long long)sweeps * per_sweep + 2LL * batches + 1;
+    int checks = G.fixed_sweeps ? 0 : (sweeps + G.check_every - 1) / G.check_every;
+    int refines = h->sc_host->batches;
+    return pre + 1 + (long long)sweeps * per_sweep + checks + 2LL * refines + 1;
 }
 
 template <typename T>
@@ -825,6 +865,11 @@ extern "C" {
 
 const char* les_version(void) { return kVersion; }
 
+int les_profiler_range(int32_t start) {
+    cudaError_t e = start ? cudaProfilerStart() : cudaProfilerStop();
+    return e == cudaSuccess ? LES_OK : fail(nullptr, LES_ECUDA, "profiler range: %s", cudaGetErrorString(e));
+}
+
 const char* les_last_error(les_handle h) { return h ? h->err : g_static_err; }
 
 int les_create(const les_grid_t* grid, const uint8_t* solid, const double* inflow_u, void* stream,
@@ -896,7 +941,8 @@ int les_step(les_handle h, int32_t nsteps, les_stats_t* stats) {
         fill_stats(h, stats, LES_OK);
         return LES_OK;
     }
-    if (h->use_graph && !h->timing)
+    const bool graph_ok = h->use_graph && !h->timing && (h->g.fixed_sweeps || h->sor.tile < 0 || h->g.check_every % 2 == 0);
+    if (graph_ok)
         return h->prec == LES_FP64 ? step_graph<double>(h, nsteps, stats) : step_graph<float>(h, nsteps, stats);
     int worst = LES_OK;
     for (int s = 0; s < nsteps; ++s) {

@@ -43,22 +43,33 @@ struct Scalars {
     int converged;          // rel <= tol
     int nonfinite;          // a norm was NaN/Inf
     int sweeps;             // sweeps done in the current solve
-    int batches;            // full check_every batches done in the current solve
+    int batches;            // FP64 refinements done in the current solve
     long long step;         // time-step counter (read by bondv1 noise and adam)
     int noconv_any;         // sticky: a solve ended above tol since the last reset
-    int pad_;
+    int zflag;              // 1: the correction is zero (a refinement just folded it in)
+    int since;              // sweeps since the last refinement
+    int refine;             // the last estimate asked for a refinement
+    double est;             // FP32-arithmetic estimate of the relative residual
+    double rho_ref;         // FP64 relative residual at the last refinement
 };
+
+// A refinement (FP64 accumulate + true residual) is taken when the cheap
+// estimate reaches tol, has dropped kRefineDrop below the last true residual,
+// kRefineEvery sweeps have passed, or the sweep budget is used up.
+constexpr double kRefineDrop = 1e-3;
+constexpr int kRefineEvery = 2000;
 
 // what the residual kernel does with the solve's bookkeeping and, inside a
 // CUDA graph, with the conditional nodes of the SOR loop
 enum ResMode { RES_INIT = 0, RES_LOOP = 1, RES_TAIL = 2, RES_HOST = 3 };
 struct CondArgs {
-    cudaGraphConditionalHandle loop, tail;
+    cudaGraphConditionalHandle loop, tail, refine;
     int use_cond;           // set the conditional handles (graph path)
     int mode;               // ResMode
     int n;                  // sweeps in the batch just finished
-    int n_full;             // number of full batches before the remainder
-    int rem;                // remainder batch size (0: none)
+    int limit;              // sweeps the loop may run (multiple of check_every in the graph path)
+    int rem;                // remainder batch size after the loop (0: none)
+    double tol;
 };
 
 // constant per-run data in the compute type
@@ -100,11 +111,15 @@ template <typename T> int launch_rhs(const Geo<T>& g, const T* us, const T* vs, 
                                      double vfluid, const Reduce& r, cudaStream_t s);
 template <typename T> int launch_rhs_mean(const Geo<T>& g, T* rhs, double vfluid, const Reduce& r,
                                           cudaStream_t s);
-template <typename T> int launch_sor_sweep(const Geo<T>& g, T* dl, const T* r, int zero_start,
+// zero_start: 0 continue from d, 1 treat d as zero, 2 read the device flag sc->zflag
+template <typename T> int launch_sor_sweep(const Geo<T>& g, T* dl, const T* r, int zero_start, const Scalars* sc,
                                            cudaStream_t s);
 template <typename T> int launch_accum(const Geo<T>& g, double* ph, const T* dl, cudaStream_t s);
-template <typename T> int launch_residual64(const Geo<T>& g, const double* ph, const T* rhs, T* r, double tol,
+template <typename T> int launch_residual64(const Geo<T>& g, const double* ph, const T* rhs, T* r,
                                             double vfluid, const Reduce& red, CondArgs ca, cudaStream_t s);
+template <typename T> int launch_sor_est(const Geo<T>& g, const T* dl, const T* r, const Reduce& red, CondArgs ca,
+                                         cudaStream_t s);
+int reduce_blocks(const Dom& d);
 template <typename T> int launch_project(const Geo<T>& g, const T* us, const T* vs, const T* ws,
                                          T* u, T* v, T* w, const double* ph_in, double* ph_out,
                                          Scalars* sc, cudaStream_t s);
@@ -120,7 +135,7 @@ struct SorCfg { int tile; int kc; };   // tile < 0: two in-place half-sweep kern
 extern const SorTile kSorTiles[];
 extern const int kNumSorTiles;
 template <typename T> int launch_sor_fused(const Geo<T>& g, const T* din, T* dout, const T* r, int zero_start,
-                                           SorCfg cfg, cudaStream_t s);
+                                           const Scalars* sc, SorCfg cfg, cudaStream_t s);
 
 int max_reduce_blocks(const Dom& d);
 

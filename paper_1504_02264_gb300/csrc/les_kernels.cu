@@ -560,8 +560,9 @@ struct Poisson {
 // One half-sweep on the correction d (in place; a colour reads only the other
 // colour).  zero_start: first sweep of a batch, d = 0 everywhere before it.
 template <typename T>
-__global__ void k_sor_half(Geo<T> g, T* dl, const T* r, int nrd, int zero_start) {
+__global__ void k_sor_half(Geo<T> g, T* dl, const T* r, int nrd, int zero_arg, const Scalars* sc) {
     const Dom& d = g.d;
+    const bool zero_start = zero_arg == 1 || (zero_arg == 2 && sc->zflag);
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
     int k = blockIdx.z + 1;
@@ -593,11 +594,11 @@ __global__ void k_sor_half(Geo<T> g, T* dl, const T* r, int nrd, int zero_start)
 }
 
 template <typename T>
-int launch_sor_sweep(const Geo<T>& g, T* dl, const T* r, int zero_start, cudaStream_t s) {
+int launch_sor_sweep(const Geo<T>& g, T* dl, const T* r, int zero_start, const Scalars* sc, cudaStream_t s) {
     const Dom& d = g.d;
     dim3 grid(((d.nx + 1) / 2 + 31) / 32, (d.ny + 7) / 8, d.nz);
-    k_sor_half<T><<<grid, dim3(32, 8), 0, s>>>(g, dl, r, 0, zero_start);
-    k_sor_half<T><<<grid, dim3(32, 8), 0, s>>>(g, dl, r, 1, zero_start);
+    k_sor_half<T><<<grid, dim3(32, 8), 0, s>>>(g, dl, r, 0, zero_start, sc);
+    k_sor_half<T><<<grid, dim3(32, 8), 0, s>>>(g, dl, r, 1, zero_start, sc);
     return 2;
 }
 
@@ -620,18 +621,35 @@ int launch_accum(const Geo<T>& g, double* ph, const T* dl, cudaStream_t s) {
     return 1;
 }
 
+// Grid-stride reductions use at most kReduceBlocks blocks, so the last-block
+// completion counter sees few atomics.
+constexpr int kReduceBlocks = 1024;
+int reduce_blocks(const Dom& d) {
+    long long n = (long long)d.nx * d.ny * d.nz;
+    long long b = (n + 255) / 256;
+    return (int)(b < kReduceBlocks ? b : kReduceBlocks);
+}
+
+__device__ __forceinline__ void cell_of(const Dom& d, long long q, int& i, int& j, int& k) {
+    i = (int)(q % d.nx) + 1;
+    long long t = q / d.nx;
+    j = (int)(t % d.ny) + 1;
+    k = (int)(t / d.ny) + 1;
+}
+
 // r = (rhs - mean) - A ph formed in FP64 and stored in T; FP64 norms, the
-// stop test, the dz-weighted fluid mean of ph (for the gauge) and the
-// bookkeeping of the SOR loop (and its graph conditionals) in the last block.
+// true relative residual and stop test, the dz-weighted fluid mean of ph (for
+// the gauge) and the bookkeeping of the SOR loop in the last block.
 template <typename T>
-__global__ void k_residual64(Geo<T> g, const double* ph, const T* rhs, T* r, double tol, double vfluid,
-                             Reduce red, CondArgs ca) {
+__global__ void __launch_bounds__(256) k_residual64(Geo<T> g, const double* ph, const T* rhs, T* r, double vfluid,
+                                                    Reduce red, CondArgs ca) {
     const Dom& d = g.d;
-    int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
-    int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    int k = blockIdx.z + 1;
+    const long long n = (long long)d.nx * d.ny * d.nz;
+    const double mean = red.sc->rhs_mean;
     double x[3] = {0.0, 0.0, 0.0};
-    if (i <= d.nx && j <= d.ny) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        cell_of(d, q, i, j, k);
         long long c = d.at(i, j, k);
         const uint8_t f = g.flags[c];
         const double pc = ph[c];
@@ -639,23 +657,23 @@ __global__ void k_residual64(Geo<T> g, const double* ph, const T* rhs, T* r, dou
             Poisson<T> Q{g};
             double ae, aw, an, as, at, ab;
             Q.coefs(f, k, g.cx64, g.cy64, g.cT64, g.cB64, ae, aw, an, as, at, ab);
-            long long e, w, n, s_, t, b;
-            Q.nbr(i, j, k, e, w, n, s_, t, b);
+            long long e, w, nn, s_, t, b;
+            Q.nbr(i, j, k, e, w, nn, s_, t, b);
             double s = 0.0;
             s += ae * ph[e];
             s += aw * ph[w];
-            s += an * ph[n];
+            s += an * ph[nn];
             s += as * ph[s_];
             s += at * ph[t];
             s += ab * ph[b];
             const double diag = ae + aw + an + as + at + ab;
-            const double bb = (double)rhs[c] - red.sc->rhs_mean;
+            const double bb = (double)rhs[c] - mean;
             const double res = bb - (s - diag * pc);
             r[c] = (T)res;
-            x[0] = res * res;
-            x[1] = bb * bb;
+            x[0] += res * res;
+            x[1] += bb * bb;
         }
-        if (f & F_FLUID) x[2] = g.dz64[k] * pc;
+        if (f & F_FLUID) x[2] += g.dz64[k] * pc;
     }
     if (grid_sum<3>(x, red)) {
         if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -663,27 +681,32 @@ __global__ void k_residual64(Geo<T> g, const double* ph, const T* rhs, T* r, dou
             sc->res2 = x[0];
             sc->rhs2 = x[1];
             const double rel = x[1] == 0.0 ? sqrt(x[0]) : sqrt(x[0] / x[1]);
-            const bool conv = rel <= tol;
+            const bool conv = rel <= ca.tol;
             const bool bad = !isfinite(rel);
             sc->rel = rel;
             sc->converged = conv;
             sc->nonfinite = bad;
             sc->p_mean = vfluid > 0.0 ? x[2] / vfluid : 0.0;
+            sc->rho_ref = rel;
+            sc->since = 0;
+            sc->zflag = 1;
             bool go = false, tail = false, final_check = false;
             if (ca.mode == RES_INIT) {
                 sc->sweeps = 0;
                 sc->batches = 0;
-                go = ca.n_full > 0;
-                tail = ca.n_full == 0 && ca.rem > 0;
+                go = ca.limit > 0;
+                tail = ca.limit == 0 && ca.rem > 0;
             } else if (ca.mode == RES_LOOP) {
+                sc->batches += 1;
+                go = !conv && !bad && sc->sweeps < ca.limit;
+                tail = !conv && !bad && sc->sweeps >= ca.limit && ca.rem > 0;
+                final_check = !go && !tail;
+            } else if (ca.mode == RES_TAIL) {
                 sc->sweeps += ca.n;
                 sc->batches += 1;
-                go = !conv && !bad && sc->batches < ca.n_full;
-                tail = !conv && !bad && sc->batches == ca.n_full && ca.rem > 0;
-                final_check = !go && !tail;
+                final_check = true;
             } else {
-                sc->sweeps += ca.n;
-                final_check = ca.mode == RES_TAIL;
+                sc->batches += 1;
             }
             if (final_check && !conv) sc->noconv_any = 1;
             if (ca.use_cond) {
@@ -695,11 +718,67 @@ __global__ void k_residual64(Geo<T> g, const double* ph, const T* rhs, T* r, dou
 }
 
 template <typename T>
-int launch_residual64(const Geo<T>& g, const double* ph, const T* rhs, T* r, double tol, double vfluid,
-                      const Reduce& red, CondArgs ca, cudaStream_t s) {
+int launch_residual64(const Geo<T>& g, const double* ph, const T* rhs, T* r, double vfluid, const Reduce& red,
+                      CondArgs ca, cudaStream_t s) {
+    k_residual64<T><<<reduce_blocks(g.d), 256, 0, s>>>(g, ph, rhs, r, vfluid, red, ca);
+    return 1;
+}
+
+// Cheap convergence estimate after a batch of sweeps: e = r - A d in the field
+// type (difference form sum a_nb (d_nb - d_c), no cancellation against the
+// diagonal), |e| / |rhs| with FP64 sums.  b - A(p + d) = r - A d exactly, so
+// this is the residual of the current iterate up to rounding.  It only decides
+// when to take the FP64 refinement, which makes the stop decision.
+template <typename T>
+__global__ void __launch_bounds__(256) k_sor_est(Geo<T> g, const T* dl, const T* r, Reduce red, CondArgs ca) {
     const Dom& d = g.d;
-    k_residual64<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(
-        g, ph, rhs, r, tol, vfluid, red, ca);
+    const long long n = (long long)d.nx * d.ny * d.nz;
+    double x[1] = {0.0};
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        cell_of(d, q, i, j, k);
+        long long c = d.at(i, j, k);
+        const uint8_t f = g.flags[c];
+        if (!(f & F_UNK)) continue;
+        Poisson<T> Q{g};
+        T ae, aw, an, as, at, ab;
+        Q.coefs(f, k, g.cx, g.cy, g.cT, g.cB, ae, aw, an, as, at, ab);
+        long long e, w, nn, s_, t, b;
+        Q.nbr(i, j, k, e, w, nn, s_, t, b);
+        const T dc = dl[c];
+        T s = T(0);
+        s += ae * (dl[e] - dc);
+        s += aw * (dl[w] - dc);
+        s += an * (dl[nn] - dc);
+        s += as * (dl[s_] - dc);
+        s += at * (dl[t] - dc);
+        s += ab * (dl[b] - dc);
+        const T res = r[c] - s;
+        x[0] += (double)res * (double)res;
+    }
+    if (grid_sum<1>(x, red)) {
+        if (threadIdx.x == 0) {
+            Scalars* sc = red.sc;
+            const double rhs2 = sc->rhs2;
+            const double est = rhs2 == 0.0 ? sqrt(x[0]) : sqrt(x[0] / rhs2);
+            sc->est = est;
+            sc->sweeps += ca.n;
+            sc->since += ca.n;
+            sc->zflag = 0;
+            const bool need = !(est > ca.tol) || est <= kRefineDrop * sc->rho_ref || sc->since >= kRefineEvery ||
+                              sc->sweeps >= ca.limit;
+            sc->refine = need;
+            if (ca.use_cond) {
+                cudaGraphSetConditional(ca.refine, need ? 1u : 0u);
+                cudaGraphSetConditional(ca.loop, need ? 0u : 1u);
+            }
+        }
+    }
+}
+
+template <typename T>
+int launch_sor_est(const Geo<T>& g, const T* dl, const T* r, const Reduce& red, CondArgs ca, cudaStream_t s) {
+    k_sor_est<T><<<reduce_blocks(g.d), 256, 0, s>>>(g, dl, r, red, ca);
     return 1;
 }
 
@@ -816,10 +895,11 @@ int max_reduce_blocks(const Dom& d) { return ((d.nx + 31) / 32) * ((d.ny + 7) / 
     template int launch_rhs<T>(const Geo<T>&, const T*, const T*, const T*, T*, double, const Reduce&,  \
                                cudaStream_t);                                                           \
     template int launch_rhs_mean<T>(const Geo<T>&, T*, double, const Reduce&, cudaStream_t);            \
-    template int launch_sor_sweep<T>(const Geo<T>&, T*, const T*, int, cudaStream_t);                   \
+    template int launch_sor_sweep<T>(const Geo<T>&, T*, const T*, int, const Scalars*, cudaStream_t);   \
     template int launch_accum<T>(const Geo<T>&, double*, const T*, cudaStream_t);                      \
-    template int launch_residual64<T>(const Geo<T>&, const double*, const T*, T*, double, double,       \
-                                      const Reduce&, CondArgs, cudaStream_t);                           \
+    template int launch_residual64<T>(const Geo<T>&, const double*, const T*, T*, double, const Reduce&, \
+                                      CondArgs, cudaStream_t);                                          \
+    template int launch_sor_est<T>(const Geo<T>&, const T*, const T*, const Reduce&, CondArgs, cudaStream_t); \
     template int launch_project<T>(const Geo<T>&, const T*, const T*, const T*, T*, T*, T*,             \
                                    const double*, double*, Scalars*, cudaStream_t);                     \
     template int launch_rhs_eff<T>(const Geo<T>&, const T*, T*, const Scalars*, cudaStream_t);          \

@@ -20,7 +20,7 @@ namespace les {
 template <typename T, int TX, int TY>
 __global__ void __launch_bounds__(TX / 2 * TY)
 k_sor_fused(Geo<T> g, const T* __restrict__ din, T* __restrict__ dout, const T* __restrict__ r,
-            int zero_start, int kc_len) {
+            int zero_arg, const Scalars* __restrict__ sc, int kc_len) {
     constexpr int NT = TX / 2 * TY;
     constexpr int DX = TX + 4, DY = TY + 4;
     constexpr int RX = TX + 2, RY = TY + 2;
@@ -35,6 +35,7 @@ k_sor_fused(Geo<T> g, const T* __restrict__ din, T* __restrict__ dout, const T* 
     const int k0 = 1 + blockIdx.z * kc_len;
     const int k1 = min(k0 + kc_len, d.nz + 1);   // chunk is [k0, k1)
     const T omega = g.omega;
+    const bool zero_start = zero_arg == 1 || (zero_arg == 2 && sc->zflag);
 
     // padded index of (i, j, k) with periodic wrap; false outside the padded box
     auto src = [&](int i, int j, int k, long long& q) -> bool {
@@ -135,11 +136,11 @@ k_sor_fused(Geo<T> g, const T* __restrict__ din, T* __restrict__ dout, const T* 
 }
 
 template <typename T, int TX, int TY>
-static void launch_tile(const Geo<T>& g, const T* din, T* dout, const T* r, int zero_start, int kc,
-                        cudaStream_t s) {
+static void launch_tile(const Geo<T>& g, const T* din, T* dout, const T* r, int zero_start, const Scalars* sc,
+                        int kc, cudaStream_t s) {
     const Dom& d = g.d;
     dim3 grid((d.nx + TX - 1) / TX, (d.ny + TY - 1) / TY, (d.nz + kc - 1) / kc);
-    k_sor_fused<T, TX, TY><<<grid, TX / 2 * TY, 0, s>>>(g, din, dout, r, zero_start, kc);
+    k_sor_fused<T, TX, TY><<<grid, TX / 2 * TY, 0, s>>>(g, din, dout, r, zero_start, sc, kc);
 }
 
 // tile shapes the autotuner chooses from (TX, TY); the k-chunk is free
@@ -147,23 +148,23 @@ const SorTile kSorTiles[] = {{32, 4}, {32, 8}, {64, 4}, {64, 8}, {128, 2}, {128,
 const int kNumSorTiles = sizeof(kSorTiles) / sizeof(kSorTiles[0]);
 
 template <typename T>
-int launch_sor_fused(const Geo<T>& g, const T* din, T* dout, const T* r, int zero_start, SorCfg cfg,
-                     cudaStream_t s) {
+int launch_sor_fused(const Geo<T>& g, const T* din, T* dout, const T* r, int zero_start, const Scalars* sc,
+                     SorCfg cfg, cudaStream_t s) {
     const int kc = cfg.kc > 0 ? cfg.kc : g.d.nz;
     switch (cfg.tile) {
-        case 0: launch_tile<T, 32, 4>(g, din, dout, r, zero_start, kc, s); break;
-        case 1: launch_tile<T, 32, 8>(g, din, dout, r, zero_start, kc, s); break;
-        case 2: launch_tile<T, 64, 4>(g, din, dout, r, zero_start, kc, s); break;
-        case 3: launch_tile<T, 64, 8>(g, din, dout, r, zero_start, kc, s); break;
-        case 4: launch_tile<T, 128, 2>(g, din, dout, r, zero_start, kc, s); break;
-        default: launch_tile<T, 128, 4>(g, din, dout, r, zero_start, kc, s); break;
+        case 0: launch_tile<T, 32, 4>(g, din, dout, r, zero_start, sc, kc, s); break;
+        case 1: launch_tile<T, 32, 8>(g, din, dout, r, zero_start, sc, kc, s); break;
+        case 2: launch_tile<T, 64, 4>(g, din, dout, r, zero_start, sc, kc, s); break;
+        case 3: launch_tile<T, 64, 8>(g, din, dout, r, zero_start, sc, kc, s); break;
+        case 4: launch_tile<T, 128, 2>(g, din, dout, r, zero_start, sc, kc, s); break;
+        default: launch_tile<T, 128, 4>(g, din, dout, r, zero_start, sc, kc, s); break;
     }
     return 1;
 }
 
-template int launch_sor_fused<float>(const Geo<float>&, const float*, float*, const float*, int, SorCfg,
-                                     cudaStream_t);
-template int launch_sor_fused<double>(const Geo<double>&, const double*, double*, const double*, int, SorCfg,
-                                      cudaStream_t);
+template int launch_sor_fused<float>(const Geo<float>&, const float*, float*, const float*, int, const Scalars*,
+                                     SorCfg, cudaStream_t);
+template int launch_sor_fused<double>(const Geo<double>&, const double*, double*, const double*, int,
+                                      const Scalars*, SorCfg, cudaStream_t);
 
 }  // namespace les

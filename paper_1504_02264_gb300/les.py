@@ -83,6 +83,7 @@ def lib(build_if_missing: bool = False):
         L.les_get_aux.argtypes = [vp, i32, vp]
         L.les_get_state.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
         L.les_set_state.argtypes = [vp, vp, ctypes.c_size_t]
+        L.les_profiler_range.argtypes = [i32]
         L.les_set_graph.argtypes = [vp, i32]
         L.les_set_sor_config.argtypes = [vp, i32, i32]
         L.les_get_sor_config.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
@@ -90,7 +91,7 @@ def lib(build_if_missing: bool = False):
         L.les_autotune_sor.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
         L.les_set_timing.argtypes = [vp, i32]
         L.les_get_timing.argtypes = [vp, ctypes.POINTER(les_timing_t)]
-        for name in ("les_set_graph", "les_set_sor_config", "les_get_sor_config", "les_sor_tile", "les_autotune_sor",
+        for name in ("les_profiler_range", "les_set_graph", "les_set_sor_config", "les_get_sor_config", "les_sor_tile", "les_autotune_sor",
                      "les_set_timing", "les_get_timing", "les_create", "les_set_fields", "les_get_fields", "les_set_inflow", "les_step",
                      "les_pressure_solve", "les_get_aux", "les_get_state", "les_set_state"):
             getattr(L, name).restype = ctypes.c_int
@@ -171,6 +172,10 @@ def les_set_timing(h, enable):
 
 def les_get_timing(h, t: les_timing_t):
     return _check(lib().les_get_timing(h, ctypes.byref(t)), h)
+
+
+def les_profiler_range(start):
+    return _check(lib().les_profiler_range(1 if start else 0))
 
 
 def les_set_graph(h, enable):

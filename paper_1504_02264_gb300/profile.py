@@ -1,0 +1,70 @@
+"""Profiling driver: run LES steps through the C ABI only (no torch), so that
+an external profiler sees nothing but this library's kernels.
+
+    python -m paper_1504_02264_gb300.profile --workload random --warmup 3 --steps 2 [--range]
+
+--range brackets the measured steps with cudaProfilerStart/Stop (for
+``ncu --profile-from-start off``).  Prints one JSON line with host wall time
+per step and the solver statistics.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+from . import les, scene
+
+
+def make(workload: str, seed: int):
+    if workload == "lattice":
+        return scene.lattice_scene(seed)
+    if workload == "random":
+        return scene.random_scene(seed)
+    if workload == "large":
+        return scene.large_scene(seed)
+    raise ValueError(workload)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="random", choices=["lattice", "random", "large"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--graph", type=int, default=1)
+    ap.add_argument("--tile", type=int, default=None)
+    ap.add_argument("--kc", type=int, default=0)
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--fp64", action="store_true")
+    ap.add_argument("--range", action="store_true")
+    a = ap.parse_args()
+    sc = make(a.workload, a.seed)
+    d = les.Domain(sc, precision=les.LES_FP64 if a.fp64 else les.LES_FP32, stream=None)
+    d.set_graph(bool(a.graph))
+    if a.tile is not None:
+        d.set_sor_config(a.tile, a.kc)
+    for _ in range(a.warmup):
+        d.step(1)
+    tune = None
+    if a.autotune:
+        tune = d.autotune_sor(sweeps=20)
+    if a.range:
+        les.les_profiler_range(1)
+    t0 = time.perf_counter()
+    sweeps = []
+    for _ in range(a.steps):
+        st = d.step(1)
+        sweeps.append(st["sweeps"])
+    t1 = time.perf_counter()
+    if a.range:
+        les.les_profiler_range(0)
+    print(json.dumps({"workload": a.workload, "cells": sc.ncells, "steps": a.steps,
+                      "ms_per_step": (t1 - t0) * 1e3 / a.steps, "sweeps": sweeps,
+                      "rel_residual": st["rel_residual"], "sor_config": d.sor_config(), "autotune": tune,
+                      "graph": a.graph}))
+
+
+if __name__ == "__main__":
+    main()
