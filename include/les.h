@@ -205,17 +205,18 @@ int les_set_graph(les_handle h, int32_t enable);
 
 /*
  * SOR sweep kernel selection.  tile = -1 runs the two in-place half-sweep
- * kernels; tile = 0..LES_SOR_NTILES-1 runs the fused red-black kernel with
- * that column-tile shape (see les_sor_tile) marching kc planes per CTA
- * (kc <= 0: the whole column).  Every choice computes the same iterate.
+ * kernels; tile = 0..LES_SOR_NTILES-1 runs a fused red-black kernel: tiles
+ * whose les_sor_tile tz is 0 are column tiles marching kc planes per CTA
+ * (kc <= 0: the whole column), the others are tx x ty x tz blocks (kc
+ * ignored).  Every choice computes the same iterate.
  * les_autotune_sor times each tile shape with a few k-chunk lengths on this
  * handle's grid (sweeps per candidate), keeps the fastest and reports it;
  * the field state is saved and restored around the trial sweeps.
  */
-#define LES_SOR_NTILES 6
+#define LES_SOR_NTILES 12
 int les_set_sor_config(les_handle h, int32_t tile, int32_t kc);
 int les_get_sor_config(les_handle h, int32_t* tile, int32_t* kc);
-int les_sor_tile(int32_t tile, int32_t* tx, int32_t* ty);
+int les_sor_tile(int32_t tile, int32_t* tx, int32_t* ty, int32_t* tz);
 int les_autotune_sor(les_handle h, int32_t sweeps, double* best_ms_per_sweep);
 
 /* Bracket a region for a profiler started with capture off

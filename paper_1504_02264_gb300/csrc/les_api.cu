@@ -85,7 +85,7 @@ struct les_s {
     double* ph[2] = {nullptr, nullptr};   // FP64 pressure (velnw writes the gauged copy to the other)
     void* dl[2] = {nullptr, nullptr};     // SOR correction (ping-pong for the fused sweep)
     void* rr = nullptr;                   // its FP64-formed right-hand side
-    SorCfg sor = {3, 16};                 // fused kernel, 64 x 8 tiles, 16-plane chunks
+    SorCfg sor = {6, 0};                  // fused kernel, 32 x 8 x 4 blocks (les_autotune_sor refines)
     void* stage = nullptr;         // dense I/O staging
     size_t stage_elems = 0;
     uint8_t* flags = nullptr;
@@ -110,6 +110,7 @@ struct les_s {
     cudaStream_t cap[3] = {nullptr, nullptr, nullptr};
     cudaGraphConditionalHandle cond_loop = 0, cond_tail = 0, cond_refine = 0;
     int dcur = 0;                         // buffer holding the current SOR correction
+    bool graph_failed = false;            // graph build failed once; host-driven loop in use
     // phase timing
     bool timing = false;
     cudaEvent_t ev[8] = {};
@@ -370,6 +371,7 @@ int autotune_impl(les_s* h, int sweeps, double* best_ms) {
     for (int t = 0; t < kNumSorTiles; ++t)
         for (int kc : kcs) {
             if (kc > h->g.nz) continue;
+            if (kSorTiles[t].tz > 0 && kc != 0) continue;      // 3-D blocks ignore kc
             h->sor = SorCfg{t, kc};
             long long nl = 0;
             run_sweeps<T>(h, g, 2, 0, nl, h->stream);       // warm
@@ -464,8 +466,15 @@ int build_graph(les_s* h, int cur) {
     if (e != cudaSuccess) return fail(h, LES_ECUDA, "graph capture: %s", cudaGetErrorString(e));
     auto abort_capture = [&](cudaError_t err, const char* what) {
         cudaGraph_t junk = nullptr;
+        cudaStreamEndCapture(cb, &junk);
+        if (junk) cudaGraphDestroy(junk);
+        junk = nullptr;
+        cudaStreamEndCapture(cc, &junk);
+        if (junk) cudaGraphDestroy(junk);
+        junk = nullptr;
         cudaStreamEndCapture(cs, &junk);
         if (junk) cudaGraphDestroy(junk);
+        cudaGetLastError();    // do not leave the capture error for later calls
         h->cur = save_cur;
         h->dcur = save_dcur;
         h->launches = l0;
@@ -500,7 +509,6 @@ int build_graph(les_s* h, int cur) {
         if (e != cudaSuccess) return abort_capture(e, "capture info");
         e = cudaGraphConditionalHandleCreate(&h->cond_loop, graph, 0, 0);
         if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h->cond_tail, graph, 0, 0);
-        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h->cond_refine, graph, 0, 0);
         if (e != cudaSuccess) return abort_capture(e, "conditional handles");
         launch_residual64<T>(g, h->ph[cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h),
                              cond_args(h, RES_INIT, 0, true, limit, rem), cs);
@@ -510,7 +518,10 @@ int build_graph(les_s* h, int cur) {
         cudaGraph_t wbody, rbody;
         e = add_cond(graph, deps, ndeps, h->cond_loop, cudaGraphCondTypeWhile, &wnode, &wbody);
         if (e != cudaSuccess) return abort_capture(e, "while node");
-        // WHILE body: sweeps + estimate, then IF(refine) { accumulate + FP64 residual }
+        // WHILE body: sweeps + estimate, then IF(refine) { accumulate + FP64 residual };
+        // the nested node's handle belongs to the body graph that holds it
+        e = cudaGraphConditionalHandleCreate(&h->cond_refine, wbody, 0, 0);
+        if (e != cudaSuccess) return abort_capture(e, "refine handle");
         e = cudaStreamBeginCaptureToGraph(cb, wbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
         if (e != cudaSuccess) return abort_capture(e, "while body");
         long long nl = 0;
@@ -558,10 +569,17 @@ int build_graph(les_s* h, int cur) {
     h->cur = save_cur;
     h->dcur = save_dcur;
     h->launches = l0;          // capture launches nothing
-    if (e != cudaSuccess) return fail(h, LES_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, LES_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    }
     e = cudaGraphInstantiate(&h->gexec[cur], full, 0);
     cudaGraphDestroy(full);
-    if (e != cudaSuccess) return fail(h, LES_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->gexec[cur] = nullptr;
+        return fail(h, LES_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
     h->graph_ok[cur] = true;
     return LES_OK;
 }
@@ -583,7 +601,7 @@ int step_graph(les_s* h, int nsteps, les_stats_t* stats) {
     for (int c = 0; c < 2; ++c)
         if (!h->graph_ok[c]) {
             int rc = build_graph<T>(h, c);
-            if (rc) return rc;
+            if (rc) return rc;      // caller falls back to the host-driven loop
         }
     CK(cudaMemsetAsync(&h->sc->noconv_any, 0, sizeof(int), h->stream));
     for (int s = 0; s < nsteps; ++s) {
@@ -761,6 +779,7 @@ int create_impl(les_s* h, const uint8_t* solid) {
     CK(cudaMemcpyAsync(h->inflow64, h->inflow.data(), nt * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     rc = h->prec == LES_FP64 ? init_tables<double>(h) : init_tables<float>(h);
     if (rc) return rc;
+    CK(h->prec == LES_FP64 ? sor_prepare<double>() : sor_prepare<float>());
     CK(cudaStreamSynchronize(h->stream));
     return LES_OK;
 }
@@ -942,8 +961,14 @@ int les_step(les_handle h, int32_t nsteps, les_stats_t* stats) {
         return LES_OK;
     }
     const bool graph_ok = h->use_graph && !h->timing && (h->g.fixed_sweeps || h->sor.tile < 0 || h->g.check_every % 2 == 0);
-    if (graph_ok)
-        return h->prec == LES_FP64 ? step_graph<double>(h, nsteps, stats) : step_graph<float>(h, nsteps, stats);
+    if (graph_ok) {
+        int rc = h->prec == LES_FP64 ? step_graph<double>(h, nsteps, stats) : step_graph<float>(h, nsteps, stats);
+        if (rc != LES_ECUDA || h->graph_ok[0] && h->graph_ok[1]) return rc;
+        // the graph could not be built on this driver: keep the message, run
+        // the same kernels from the host-driven loop from now on
+        h->use_graph = false;
+        h->graph_failed = true;
+    }
     int worst = LES_OK;
     for (int s = 0; s < nsteps; ++s) {
         int rc = h->prec == LES_FP64 ? step_host<double>(h) : step_host<float>(h);
@@ -1044,10 +1069,11 @@ int les_get_sor_config(les_handle h, int32_t* tile, int32_t* kc) {
     return LES_OK;
 }
 
-int les_sor_tile(int32_t tile, int32_t* tx, int32_t* ty) {
+int les_sor_tile(int32_t tile, int32_t* tx, int32_t* ty, int32_t* tz) {
     if (tile < 0 || tile >= kNumSorTiles) return fail(nullptr, LES_EINVAL, "tile %d out of range", tile);
     if (tx) *tx = kSorTiles[tile].tx;
     if (ty) *ty = kSorTiles[tile].ty;
+    if (tz) *tz = kSorTiles[tile].tz;
     return LES_OK;
 }
 

@@ -130,12 +130,14 @@ template <typename T> int launch_gauge(const Geo<T>& g, const double* p_in, doub
                                        const Scalars* sc, cudaStream_t s);
 
 // fused SOR sweep (les_sor.cu): tile shape index into kSorTiles and k-chunk
-struct SorTile { int tx, ty; };
+struct SorTile { int tx, ty, tz; };   // tz = 0: k-marching column tile
 struct SorCfg { int tile; int kc; };   // tile < 0: two in-place half-sweep kernels
 extern const SorTile kSorTiles[];
 extern const int kNumSorTiles;
 template <typename T> int launch_sor_fused(const Geo<T>& g, const T* din, T* dout, const T* r, int zero_start,
                                            const Scalars* sc, SorCfg cfg, cudaStream_t s);
+
+template <typename T> cudaError_t sor_prepare();
 
 int max_reduce_blocks(const Dom& d);
 

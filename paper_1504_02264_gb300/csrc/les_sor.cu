@@ -135,6 +135,125 @@ k_sor_fused(Geo<T> g, const T* __restrict__ din, T* __restrict__ dout, const T* 
     }
 }
 
+// 3-D block variant for grids that fit in L2: no marching, so thousands of
+// independent CTAs hide the load latency.  One CTA loads d on its BX x BY x BZ
+// block plus a 2-cell halo and r/flags on block + 1, updates the red cells of
+// block + 1 ring, then the black cells of the block, and stores the block.
+template <typename T, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(256)
+k_sor_block(Geo<T> g, const T* __restrict__ din, T* __restrict__ dout, const T* __restrict__ r, int zero_arg,
+            const Scalars* __restrict__ sc) {
+    constexpr int NT = 256;
+    constexpr int DX = BX + 4, DY = BY + 4, DZ = BZ + 4;
+    constexpr int RX = BX + 2, RY = BY + 2, RZ = BZ + 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T(*sD)[DY][DX] = reinterpret_cast<T(*)[DY][DX]>(smem_raw);
+    T(*sR)[RY][RX] = reinterpret_cast<T(*)[RY][RX]>(smem_raw + sizeof(T) * DX * DY * DZ);
+    uint8_t(*sF)[RY][RX] = reinterpret_cast<uint8_t(*)[RY][RX]>(smem_raw + sizeof(T) * (DX * DY * DZ + RX * RY * RZ));
+    const Dom& d = g.d;
+    const int tid = threadIdx.x;
+    const int i0 = 1 + blockIdx.x * BX, j0 = 1 + blockIdx.y * BY, k0 = 1 + blockIdx.z * BZ;
+    const T omega = g.omega;
+    const bool zero_start = zero_arg == 1 || (zero_arg == 2 && sc->zflag);
+    auto src = [&](int i, int j, int k, long long& q) -> bool {
+        if (d.perx) { i = i < 1 ? i + d.nx : (i > d.nx ? i - d.nx : i); }
+        else if (i < 0 || i > d.nx + 1) return false;
+        if (d.pery) { j = j < 1 ? j + d.ny : (j > d.ny ? j - d.ny : j); }
+        else if (j < 0 || j > d.ny + 1) return false;
+        if (d.perz) { k = k < 1 ? k + d.nz : (k > d.nz ? k - d.nz : k); }
+        else if (k < 0 || k > d.nz + 1) return false;
+        q = d.at(i, j, k);
+        return true;
+    };
+    for (int q = tid; q < DX * DY * DZ; q += NT) {
+        const int ii = q % DX, t = q / DX, jj = t % DY, kk = t / DY;
+        long long s;
+        T v = T(0);
+        if (!zero_start && src(i0 - 2 + ii, j0 - 2 + jj, k0 - 2 + kk, s)) v = din[s];
+        sD[kk][jj][ii] = v;
+    }
+    for (int q = tid; q < RX * RY * RZ; q += NT) {
+        const int ii = q % RX, t = q / RX, jj = t % RY, kk = t / RY;
+        long long s;
+        T rv = T(0);
+        uint8_t fv = 0;
+        if (src(i0 - 1 + ii, j0 - 1 + jj, k0 - 1 + kk, s)) {
+            fv = g.flags[s];
+            if (fv & F_UNK) rv = r[s];
+        }
+        sR[kk][jj][ii] = rv;
+        sF[kk][jj][ii] = fv;
+    }
+    __syncthreads();
+    // the printed update at shared position (x, y, z) of the d tile
+    auto relax = [&](int x, int y, int z, int kglob, uint8_t f, T rhs) {
+        T ae = (f & F_E) ? g.cx : T(0);
+        T aw = (f & F_W) ? g.cx : T(0);
+        T an = (f & F_N) ? g.cy : T(0);
+        T as = (f & F_S) ? g.cy : T(0);
+        const int kl = d.perz ? (kglob < 1 ? kglob + d.nz : (kglob > d.nz ? kglob - d.nz : kglob))
+                              : min(max(kglob, 0), d.nz + 1);
+        T at = (f & F_T) ? g.cT[kl] : T(0);
+        T ab = (f & F_B) ? g.cB[kl] : T(0);
+        T cn1 = T(1) / (ae + aw + an + as + at + ab);
+        T s = T(0);
+        s += ae * sD[z][y][x + 1];
+        s += aw * sD[z][y][x - 1];
+        s += an * sD[z][y + 1][x];
+        s += as * sD[z][y - 1][x];
+        s += at * sD[z + 1][y][x];
+        s += ab * sD[z - 1][y][x];
+        T own = sD[z][y][x];
+        T reltmp = omega * (cn1 * (s - rhs) - own);
+        sD[z][y][x] = own + reltmp;
+    };
+    // red (i+j+k odd) on block + 1 ring
+    for (int q = tid; q < (RX / 2) * RY * RZ; q += NT) {
+        const int m = q % (RX / 2), t = q / (RX / 2), jj = t % RY, kk = t / RY;
+        const int par = (i0 + (j0 - 1 + jj) + (k0 - 1 + kk)) & 1;
+        const int ii = 2 * m + par;
+        const uint8_t f = sF[kk][jj][ii];
+        if (f & F_UNK) relax(ii + 1, jj + 1, kk + 1, k0 - 1 + kk, f, sR[kk][jj][ii]);
+    }
+    __syncthreads();
+    // black (i+j+k even) on the block
+    for (int q = tid; q < (BX / 2) * BY * BZ; q += NT) {
+        const int m = q % (BX / 2), t = q / (BX / 2), jj = t % BY, kk = t / BY;
+        const int par = (i0 + (j0 + jj) + (k0 + kk)) & 1;
+        const int ii = 2 * m + par;
+        const uint8_t f = sF[kk + 1][jj + 1][ii + 1];
+        if (f & F_UNK) relax(ii + 2, jj + 2, kk + 2, k0 + kk, f, sR[kk + 1][jj + 1][ii + 1]);
+    }
+    __syncthreads();
+    for (int q = tid; q < BX * BY * BZ; q += NT) {
+        const int ii = q % BX, t = q / BX, jj = t % BY, kk = t / BY;
+        const int i = i0 + ii, j = j0 + jj, k = k0 + kk;
+        if (i <= d.nx && j <= d.ny && k <= d.nz && (sF[kk + 1][jj + 1][ii + 1] & F_UNK))
+            dout[d.at(i, j, k)] = sD[kk + 2][jj + 2][ii + 2];
+    }
+}
+
+template <typename T, int BX, int BY, int BZ>
+constexpr size_t block_smem() {
+    return sizeof(T) * ((BX + 4) * (BY + 4) * (BZ + 4) + (BX + 2) * (BY + 2) * (BZ + 2)) +
+           (BX + 2) * (BY + 2) * (BZ + 2);
+}
+
+template <typename T, int BX, int BY, int BZ>
+static cudaError_t allow_block() {
+    return cudaFuncSetAttribute(k_sor_block<T, BX, BY, BZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)block_smem<T, BX, BY, BZ>());
+}
+
+template <typename T, int BX, int BY, int BZ>
+static void launch_block(const Geo<T>& g, const T* din, T* dout, const T* r, int zero_start, const Scalars* sc,
+                         cudaStream_t s) {
+    const Dom& d = g.d;
+    constexpr size_t bytes = block_smem<T, BX, BY, BZ>();
+    dim3 grid((d.nx + BX - 1) / BX, (d.ny + BY - 1) / BY, (d.nz + BZ - 1) / BZ);
+    k_sor_block<T, BX, BY, BZ><<<grid, 256, bytes, s>>>(g, din, dout, r, zero_start, sc);
+}
+
 template <typename T, int TX, int TY>
 static void launch_tile(const Geo<T>& g, const T* din, T* dout, const T* r, int zero_start, const Scalars* sc,
                         int kc, cudaStream_t s) {
@@ -143,8 +262,10 @@ static void launch_tile(const Geo<T>& g, const T* din, T* dout, const T* r, int 
     k_sor_fused<T, TX, TY><<<grid, TX / 2 * TY, 0, s>>>(g, din, dout, r, zero_start, sc, kc);
 }
 
-// tile shapes the autotuner chooses from (TX, TY); the k-chunk is free
-const SorTile kSorTiles[] = {{32, 4}, {32, 8}, {64, 4}, {64, 8}, {128, 2}, {128, 4}};
+// tile shapes the autotuner chooses from: (TX, TY, 0) k-marching column tiles
+// (the k-chunk is free), (BX, BY, BZ) 3-D blocks
+const SorTile kSorTiles[] = {{32, 4, 0},  {32, 8, 0}, {64, 4, 0}, {64, 8, 0}, {128, 2, 0}, {128, 4, 0},
+                             {32, 8, 4},  {32, 4, 8}, {64, 4, 4}, {32, 8, 8}, {16, 8, 8}, {64, 8, 2}};
 const int kNumSorTiles = sizeof(kSorTiles) / sizeof(kSorTiles[0]);
 
 template <typename T>
@@ -157,10 +278,32 @@ int launch_sor_fused(const Geo<T>& g, const T* din, T* dout, const T* r, int zer
         case 2: launch_tile<T, 64, 4>(g, din, dout, r, zero_start, sc, kc, s); break;
         case 3: launch_tile<T, 64, 8>(g, din, dout, r, zero_start, sc, kc, s); break;
         case 4: launch_tile<T, 128, 2>(g, din, dout, r, zero_start, sc, kc, s); break;
-        default: launch_tile<T, 128, 4>(g, din, dout, r, zero_start, sc, kc, s); break;
+        case 5: launch_tile<T, 128, 4>(g, din, dout, r, zero_start, sc, kc, s); break;
+        case 6: launch_block<T, 32, 8, 4>(g, din, dout, r, zero_start, sc, s); break;
+        case 7: launch_block<T, 32, 4, 8>(g, din, dout, r, zero_start, sc, s); break;
+        case 8: launch_block<T, 64, 4, 4>(g, din, dout, r, zero_start, sc, s); break;
+        case 9: launch_block<T, 32, 8, 8>(g, din, dout, r, zero_start, sc, s); break;
+        case 10: launch_block<T, 16, 8, 8>(g, din, dout, r, zero_start, sc, s); break;
+        default: launch_block<T, 64, 8, 2>(g, din, dout, r, zero_start, sc, s); break;
     }
     return 1;
 }
+
+// opt the 3-D block kernels in to their dynamic shared memory on the current
+// device (called when a handle is created, outside any stream capture)
+template <typename T>
+cudaError_t sor_prepare() {
+    cudaError_t e = cudaSuccess, x;
+    if ((x = allow_block<T, 32, 8, 4>()) != cudaSuccess) e = x;
+    if ((x = allow_block<T, 32, 4, 8>()) != cudaSuccess) e = x;
+    if ((x = allow_block<T, 64, 4, 4>()) != cudaSuccess) e = x;
+    if ((x = allow_block<T, 32, 8, 8>()) != cudaSuccess) e = x;
+    if ((x = allow_block<T, 16, 8, 8>()) != cudaSuccess) e = x;
+    if ((x = allow_block<T, 64, 8, 2>()) != cudaSuccess) e = x;
+    return e;
+}
+template cudaError_t sor_prepare<float>();
+template cudaError_t sor_prepare<double>();
 
 template int launch_sor_fused<float>(const Geo<float>&, const float*, float*, const float*, int, const Scalars*,
                                      SorCfg, cudaStream_t);

@@ -87,7 +87,7 @@ def lib(build_if_missing: bool = False):
         L.les_set_graph.argtypes = [vp, i32]
         L.les_set_sor_config.argtypes = [vp, i32, i32]
         L.les_get_sor_config.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
-        L.les_sor_tile.argtypes = [i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        L.les_sor_tile.argtypes = [i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
         L.les_autotune_sor.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
         L.les_set_timing.argtypes = [vp, i32]
         L.les_get_timing.argtypes = [vp, ctypes.POINTER(les_timing_t)]
@@ -193,9 +193,9 @@ def les_get_sor_config(h):
 
 
 def les_sor_tile(tile):
-    tx, ty = ctypes.c_int32(), ctypes.c_int32()
-    _check(lib().les_sor_tile(tile, ctypes.byref(tx), ctypes.byref(ty)))
-    return tx.value, ty.value
+    tx, ty, tz = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().les_sor_tile(tile, ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(tz)))
+    return tx.value, ty.value, tz.value
 
 
 def les_autotune_sor(h, sweeps):
