@@ -219,6 +219,7 @@ def run_ours(args):
         st = dom.step(1)
         ev[s][1].record(stream)
         sweeps.append(st["sweeps"])
+        graph_used = st["graph"]
         worst = max(worst, st["rel_residual"])
         if st["rc"] != 0:
             raise RuntimeError(f"step did not converge: {st}")
@@ -295,6 +296,7 @@ def run_ours(args):
                                   ("ms_momentum", "ms_sor", "ms_residual", "ms_project")},
             "sor_ms_per_sweep": sweep_ms,
             "gpu_launches": int(launches),
+            "step_mode": "cuda_graph" if graph_used else "host_loop",
             "sor_autotune": {"tile": tile, "kc": kc, "ms_per_sweep": tune_ms},
             "e2e": {"value": n * world / (e2e_ms * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": h2d, "ms_per_step": e2e_ms, "steps": e2e_steps},

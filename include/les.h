@@ -98,7 +98,9 @@ typedef struct {
     double q_in, q_out;          /* FP64 volume fluxes after the correction */
     double p_mean;               /* FP64 dz-weighted mean removed from p (gauge) */
     int64_t step;                /* step counter after the call */
-    int64_t launches;            /* kernels launched by the call */
+    int64_t launches;            /* kernels launched by the handle so far */
+    int32_t graph;               /* 1: the call ran its steps as CUDA graphs */
+    int32_t pad_;
 } les_stats_t;
 
 /*

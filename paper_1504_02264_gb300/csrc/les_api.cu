@@ -111,6 +111,7 @@ struct les_s {
     cudaGraphConditionalHandle cond_loop = 0, cond_tail = 0, cond_refine = 0;
     int dcur = 0;                         // buffer holding the current SOR correction
     bool graph_failed = false;            // graph build failed once; host-driven loop in use
+    bool last_graph = false;              // the last les_step ran as graphs
     // phase timing
     bool timing = false;
     cudaEvent_t ev[8] = {};
@@ -632,6 +633,7 @@ void fill_stats(les_s* h, les_stats_t* st, int status) {
     st->p_mean = s.p_mean;
     st->step = h->step;
     st->launches = h->launches;
+    st->graph = h->last_graph ? 1 : 0;
 }
 
 int validate(const les_grid_t* g) {
@@ -961,6 +963,7 @@ int les_step(les_handle h, int32_t nsteps, les_stats_t* stats) {
         return LES_OK;
     }
     const bool graph_ok = h->use_graph && !h->timing && (h->g.fixed_sweeps || h->sor.tile < 0 || h->g.check_every % 2 == 0);
+    h->last_graph = graph_ok;
     if (graph_ok) {
         int rc = h->prec == LES_FP64 ? step_graph<double>(h, nsteps, stats) : step_graph<float>(h, nsteps, stats);
         if (rc != LES_ECUDA || h->graph_ok[0] && h->graph_ok[1]) return rc;
@@ -968,6 +971,7 @@ int les_step(les_handle h, int32_t nsteps, les_stats_t* stats) {
         // the same kernels from the host-driven loop from now on
         h->use_graph = false;
         h->graph_failed = true;
+        h->last_graph = false;
     }
     int worst = LES_OK;
     for (int s = 0; s < nsteps; ++s) {

@@ -41,7 +41,7 @@ class les_stats_t(ctypes.Structure):
                 ("rhs_mean", ctypes.c_double), ("mass_factor", ctypes.c_double),
                 ("q_in", ctypes.c_double), ("q_out", ctypes.c_double),
                 ("p_mean", ctypes.c_double), ("step", ctypes.c_int64),
-                ("launches", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("graph", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 class les_timing_t(ctypes.Structure):
