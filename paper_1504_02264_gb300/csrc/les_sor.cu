@@ -165,24 +165,77 @@ k_sor_block(Geo<T> g, const T* __restrict__ din, T* __restrict__ dout, const T* 
         q = d.at(i, j, k);
         return true;
     };
-    for (int q = tid; q < DX * DY * DZ; q += NT) {
-        const int ii = q % DX, t = q / DX, jj = t % DY, kk = t / DY;
-        long long s;
-        T v = T(0);
-        if (!zero_start && src(i0 - 2 + ii, j0 - 2 + jj, k0 - 2 + kk, s)) v = din[s];
-        sD[kk][jj][ii] = v;
-    }
-    for (int q = tid; q < RX * RY * RZ; q += NT) {
-        const int ii = q % RX, t = q / RX, jj = t % RY, kk = t / RY;
-        long long s;
-        T rv = T(0);
-        uint8_t fv = 0;
-        if (src(i0 - 1 + ii, j0 - 1 + jj, k0 - 1 + kk, s)) {
-            fv = g.flags[s];
-            if (fv & F_UNK) rv = r[s];
+    // Every thread stages its share of the three tiles in registers first, so
+    // all of its loads are in flight together; blocks whose halo lies inside
+    // the padded box and needs no periodic wrap use plain address arithmetic.
+    constexpr int ND = DX * DY * DZ, NR = RX * RY * RZ;
+    constexpr int LD = (ND + NT - 1) / NT, LR = (NR + NT - 1) / NT;
+    // (halo strictly inside 1..n: periodic ghosts of d are never maintained)
+    const bool inner = i0 - 2 >= 1 && i0 + BX + 1 <= d.nx && j0 - 2 >= 1 && j0 + BY + 1 <= d.ny &&
+                       k0 - 2 >= 1 && k0 + BZ + 1 <= d.nz;
+    T* sDf = &sD[0][0][0];
+    T* sRf = &sR[0][0][0];
+    uint8_t* sFf = &sF[0][0][0];
+    if (inner) {
+        const long long bd = d.at(i0 - 2, j0 - 2, k0 - 2);
+        const long long br = d.at(i0 - 1, j0 - 1, k0 - 1);
+        T vd[LD];
+        T vr[LR];
+        uint8_t vf[LR];
+#pragma unroll
+        for (int n = 0; n < LD; ++n) {
+            const int q = tid + n * NT;
+            vd[n] = T(0);
+            if (q < ND && !zero_start) {
+                const int ii = q % DX, t = q / DX, jj = t % DY, kk = t / DY;
+                vd[n] = din[bd + ((long long)kk * d.py + jj) * d.px + ii];
+            }
         }
-        sR[kk][jj][ii] = rv;
-        sF[kk][jj][ii] = fv;
+#pragma unroll
+        for (int n = 0; n < LR; ++n) {
+            const int q = tid + n * NT;
+            vf[n] = 0;
+            vr[n] = T(0);
+            if (q < NR) {
+                const int ii = q % RX, t = q / RX, jj = t % RY, kk = t / RY;
+                const long long a = br + ((long long)kk * d.py + jj) * d.px + ii;
+                vf[n] = g.flags[a];
+                vr[n] = r[a];
+            }
+        }
+#pragma unroll
+        for (int n = 0; n < LD; ++n) {
+            const int q = tid + n * NT;
+            if (q < ND) sDf[q] = vd[n];
+        }
+#pragma unroll
+        for (int n = 0; n < LR; ++n) {
+            const int q = tid + n * NT;
+            if (q < NR) {
+                sRf[q] = (vf[n] & F_UNK) ? vr[n] : T(0);
+                sFf[q] = vf[n];
+            }
+        }
+    } else {
+        for (int q = tid; q < ND; q += NT) {
+            const int ii = q % DX, t = q / DX, jj = t % DY, kk = t / DY;
+            long long s;
+            T v = T(0);
+            if (!zero_start && src(i0 - 2 + ii, j0 - 2 + jj, k0 - 2 + kk, s)) v = din[s];
+            sDf[q] = v;
+        }
+        for (int q = tid; q < NR; q += NT) {
+            const int ii = q % RX, t = q / RX, jj = t % RY, kk = t / RY;
+            long long s;
+            T rv = T(0);
+            uint8_t fv = 0;
+            if (src(i0 - 1 + ii, j0 - 1 + jj, k0 - 1 + kk, s)) {
+                fv = g.flags[s];
+                if (fv & F_UNK) rv = r[s];
+            }
+            sRf[q] = rv;
+            sFf[q] = fv;
+        }
     }
     __syncthreads();
     // the printed update at shared position (x, y, z) of the d tile

@@ -60,7 +60,8 @@ def main():
     t1 = time.perf_counter()
     if a.range:
         les.les_profiler_range(0)
-    print(json.dumps({"workload": a.workload, "cells": sc.ncells, "steps": a.steps,
+    err = les.les_last_error(d.h)
+    print(json.dumps({"workload": a.workload, "graph_used": st["graph"], "last_error": err, "cells": sc.ncells, "steps": a.steps,
                       "ms_per_step": (t1 - t0) * 1e3 / a.steps, "sweeps": sweeps,
                       "rel_residual": st["rel_residual"], "sor_config": d.sor_config(), "autotune": tune,
                       "graph": a.graph}))
