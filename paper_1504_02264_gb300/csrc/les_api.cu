@@ -107,8 +107,10 @@ struct les_s {
     bool use_graph = true;
     bool graph_ok[2] = {false, false};
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    cudaStream_t cap[3] = {nullptr, nullptr, nullptr};
-    cudaGraphConditionalHandle cond_loop = 0, cond_tail = 0, cond_refine = 0;
+    cudaStream_t cap[1] = {nullptr};
+    cudaEvent_t chunk_ev[2] = {nullptr, nullptr};
+    int* done_host = nullptr;             // mapped pinned copy of the device `done` flag
+    int* done_dev = nullptr;              // its device address
     int dcur = 0;                         // buffer holding the current SOR correction
     bool graph_failed = false;            // graph build failed once; host-driven loop in use
     bool last_graph = false;              // the last les_step ran as graphs
@@ -273,23 +275,20 @@ int run_sweeps(les_s* h, const Geo<T>& g, int n, int zero, long long& launched, 
     return h->dcur;
 }
 
-CondArgs cond_args(const les_s* h, int mode, int n, bool use_cond, int limit, int rem) {
+CondArgs cond_args(const les_s* h, int mode, int n, int gate) {
     CondArgs ca{};
-    ca.loop = h->cond_loop;
-    ca.tail = h->cond_tail;
-    ca.refine = h->cond_refine;
-    ca.use_cond = use_cond ? 1 : 0;
     ca.mode = mode;
     ca.n = n;
-    ca.limit = limit;
-    ca.rem = rem;
+    ca.limit = h->g.max_sweeps;
+    ca.gate = gate;
     ca.tol = h->g.tol;
+    ca.done_host = h->done_dev;
     return ca;
 }
 
 template <typename T>
 void launch_refine(les_s* h, const Geo<T>& g, const CondArgs& ca, cudaStream_t st) {
-    h->launches += launch_accum<T>(g, h->ph[h->cur], (const T*)h->dl[h->dcur], st);
+    h->launches += launch_accum<T>(g, h->ph[h->cur], (const T*)h->dl[h->dcur], h->sc, ca.gate, st);
     h->launches += launch_residual64<T>(g, h->ph[h->cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h), ca, st);
 }
 
@@ -300,10 +299,9 @@ template <typename T>
 int sor_solve(les_s* h) {
     Geo<T> g = geo<T>(h);
     const les_grid_t& G = h->g;
-    const int limit = G.max_sweeps;
     rec(h, 2);
     h->launches += launch_residual64<T>(g, h->ph[h->cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h),
-                                        cond_args(h, RES_INIT, 0, false, limit, 0), h->stream);
+                                        cond_args(h, RES_INIT, 0, 0), h->stream);
     rec(h, 3);
     CK(cudaGetLastError());
     if (h->timing) {
@@ -324,7 +322,7 @@ int sor_solve(les_s* h) {
         bool need = true;
         if (!G.fixed_sweeps) {
             h->launches += launch_sor_est<T>(g, (const T*)h->dl[h->dcur], (const T*)h->rr, reducer(h),
-                                             cond_args(h, RES_HOST, n, false, limit, 0), h->stream);
+                                             cond_args(h, RES_LOOP, n, 0), h->stream);
             CK(cudaGetLastError());
             int rc = fetch_scalars(h);
             if (rc) return rc;
@@ -341,7 +339,7 @@ int sor_solve(les_s* h) {
         fresh = false;
         if (need) {
             rec(h, 3);
-            launch_refine<T>(h, g, cond_args(h, G.fixed_sweeps ? RES_TAIL : RES_HOST, n, false, limit, 0), h->stream);
+            launch_refine<T>(h, g, cond_args(h, G.fixed_sweeps ? RES_FIXED : RES_LOOP, n, 0), h->stream);
             rec(h, 4);
             CK(cudaGetLastError());
             int rc = fetch_scalars(h);
@@ -367,6 +365,9 @@ int autotune_impl(les_s* h, int sweeps, double* best_ms) {
     CK(cudaEventCreate(&a));
     CK(cudaEventCreate(&b));
     const int kcs[] = {4, 8, 16, 32, 0};
+    int done_save = 0;
+    CK(cudaMemcpyAsync(&done_save, &h->sc->done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemsetAsync(&h->sc->done, 0, sizeof(int), h->stream));
     SorCfg keep = h->sor, best = keep;
     double bms = 1e300;
     for (int t = 0; t < kNumSorTiles; ++t)
@@ -391,6 +392,8 @@ int autotune_impl(les_s* h, int sweeps, double* best_ms) {
         }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
+    CK(cudaMemcpyAsync(&h->sc->done, &done_save, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
     h->sor = bms < 1e299 ? best : keep;
     h->graph_ok[0] = h->graph_ok[1] = false;
     if (best_ms) *best_ms = bms;
@@ -443,177 +446,119 @@ int step_host(les_s* h) {
     return rc;
 }
 
-// The whole step as one CUDA graph: prefix kernels, the FP64 initial
-// residual, a conditional WHILE node whose body runs check_every sweeps and
-// the cheap estimate, with a nested IF node for the FP64 refinement, then a
-// conditional IF node for the remainder batch, then the projection.  The stop
-// test runs on the device (k_sor_est / k_residual64 set the conditions), so a
-// step needs no host round trip.  One graph per pressure-buffer parity
-// (velnw writes the gauged p to the other buffer).
+// Graph execution without device-side control flow.  A step launches the
+// prefix kernels and the first FP64 residual, then replays a captured "chunk"
+// of kChunkBatches batches (check_every sweeps, the estimate, a gated
+// refinement).  Every kernel of a chunk returns at once when the device flag
+// `done` is set, so the host can keep one chunk in flight and stop enqueueing
+// when it sees the mapped copy of the flag: the GPU never waits for the host.
+// With fixed_sweeps the whole step is one captured graph.
+constexpr int kChunkBatches = 10;
+
 template <typename T>
-int build_graph(les_s* h, int cur) {
-    Geo<T> g = geo<T>(h);
-    const les_grid_t& G = h->g;
-    if (h->gexec[cur]) {
-        cudaGraphExecDestroy(h->gexec[cur]);
-        h->gexec[cur] = nullptr;
-    }
-    cudaStream_t cs = h->cap[0], cb = h->cap[1], cc = h->cap[2];
-    const int save_cur = h->cur, save_dcur = h->dcur;
-    const long long l0 = h->launches;
-    h->cur = cur;
-    h->dcur = 0;
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
-    if (e != cudaSuccess) return fail(h, LES_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-    auto abort_capture = [&](cudaError_t err, const char* what) {
-        cudaGraph_t junk = nullptr;
-        cudaStreamEndCapture(cb, &junk);
-        if (junk) cudaGraphDestroy(junk);
-        junk = nullptr;
-        cudaStreamEndCapture(cc, &junk);
-        if (junk) cudaGraphDestroy(junk);
-        junk = nullptr;
-        cudaStreamEndCapture(cs, &junk);
-        if (junk) cudaGraphDestroy(junk);
-        cudaGetLastError();    // do not leave the capture error for later calls
-        h->cur = save_cur;
-        h->dcur = save_dcur;
-        h->launches = l0;
-        return fail(h, LES_ECUDA, "graph build (%s): %s", what, cudaGetErrorString(err));
-    };
-    launch_prefix<T>(h, g, cs);
-    cudaStreamCaptureStatus cst;
-    cudaGraph_t graph;
-    const cudaGraphNode_t* deps = nullptr;
-    size_t ndeps = 0;
-    auto add_cond = [&](cudaGraph_t gr, const cudaGraphNode_t* dp, size_t nd, cudaGraphConditionalHandle hd,
-                        cudaGraphConditionalNodeType type, cudaGraphNode_t* node, cudaGraph_t* body) -> cudaError_t {
-        cudaGraphNodeParams np = {};
-        np.type = cudaGraphNodeTypeConditional;
-        np.conditional.handle = hd;
-        np.conditional.type = type;
-        np.conditional.size = 1;
-        cudaError_t err = cudaGraphAddNode(node, gr, dp, nullptr, nd, &np);
-        if (err == cudaSuccess) *body = np.conditional.phGraph_out[0];
-        return err;
-    };
-    if (G.fixed_sweeps) {
-        launch_residual64<T>(g, h->ph[cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h),
-                             cond_args(h, RES_INIT, 0, false, 0, 0), cs);
-        long long nl = 0;
-        run_sweeps<T>(h, g, G.max_sweeps, 1, nl, cs);
-        launch_refine<T>(h, g, cond_args(h, RES_TAIL, G.max_sweeps, false, 0, 0), cs);
-    } else {
-        const int limit = (G.max_sweeps / G.check_every) * G.check_every;
-        const int rem = G.max_sweeps - limit;
-        e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph, nullptr, nullptr, nullptr);
-        if (e != cudaSuccess) return abort_capture(e, "capture info");
-        e = cudaGraphConditionalHandleCreate(&h->cond_loop, graph, 0, 0);
-        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h->cond_tail, graph, 0, 0);
-        if (e != cudaSuccess) return abort_capture(e, "conditional handles");
-        launch_residual64<T>(g, h->ph[cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h),
-                             cond_args(h, RES_INIT, 0, true, limit, rem), cs);
-        e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph, &deps, nullptr, &ndeps);
-        if (e != cudaSuccess) return abort_capture(e, "capture info");
-        cudaGraphNode_t wnode, rnode;
-        cudaGraph_t wbody, rbody;
-        e = add_cond(graph, deps, ndeps, h->cond_loop, cudaGraphCondTypeWhile, &wnode, &wbody);
-        if (e != cudaSuccess) return abort_capture(e, "while node");
-        // WHILE body: sweeps + estimate, then IF(refine) { accumulate + FP64 residual };
-        // the nested node's handle belongs to the body graph that holds it
-        e = cudaGraphConditionalHandleCreate(&h->cond_refine, wbody, 0, 0);
-        if (e != cudaSuccess) return abort_capture(e, "refine handle");
-        e = cudaStreamBeginCaptureToGraph(cb, wbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-        if (e != cudaSuccess) return abort_capture(e, "while body");
-        long long nl = 0;
-        h->dcur = 0;
-        run_sweeps<T>(h, g, G.check_every, 2, nl, cb);       // check_every even: d returns to dl[0]
-        h->launches += launch_sor_est<T>(g, (const T*)h->dl[h->dcur], (const T*)h->rr, reducer(h),
-                                         cond_args(h, RES_LOOP, G.check_every, true, limit, rem), cb);
-        const cudaGraphNode_t* bdeps = nullptr;
-        size_t nbdeps = 0;
-        cudaGraph_t bgraph;
-        e = cudaStreamGetCaptureInfo(cb, &cst, nullptr, &bgraph, &bdeps, nullptr, &nbdeps);
-        if (e != cudaSuccess) return abort_capture(e, "body capture info");
-        e = add_cond(bgraph, bdeps, nbdeps, h->cond_refine, cudaGraphCondTypeIf, &rnode, &rbody);
-        if (e != cudaSuccess) return abort_capture(e, "refine node");
-        e = cudaStreamUpdateCaptureDependencies(cb, &rnode, nullptr, 1, cudaStreamSetCaptureDependencies);
-        if (e != cudaSuccess) return abort_capture(e, "body dependencies");
-        e = cudaStreamEndCapture(cb, &wbody);
-        if (e != cudaSuccess) return abort_capture(e, "while body end");
-        e = cudaStreamBeginCaptureToGraph(cc, rbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-        if (e != cudaSuccess) return abort_capture(e, "refine body");
-        launch_refine<T>(h, g, cond_args(h, RES_LOOP, G.check_every, true, limit, rem), cc);
-        e = cudaStreamEndCapture(cc, &rbody);
-        if (e != cudaSuccess) return abort_capture(e, "refine body end");
-        cudaGraphNode_t last = wnode;
-        if (rem > 0) {
-            cudaGraphNode_t inode;
-            cudaGraph_t tbody;
-            e = add_cond(graph, &wnode, 1, h->cond_tail, cudaGraphCondTypeIf, &inode, &tbody);
-            if (e != cudaSuccess) return abort_capture(e, "tail node");
-            e = cudaStreamBeginCaptureToGraph(cb, tbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-            if (e != cudaSuccess) return abort_capture(e, "tail body");
-            h->dcur = 0;
-            run_sweeps<T>(h, g, rem, 1, nl, cb);
-            launch_refine<T>(h, g, cond_args(h, RES_TAIL, rem, true, limit, rem), cb);
-            e = cudaStreamEndCapture(cb, &tbody);
-            if (e != cudaSuccess) return abort_capture(e, "tail body end");
-            last = inode;
-        }
-        e = cudaStreamUpdateCaptureDependencies(cs, &last, nullptr, 1, cudaStreamSetCaptureDependencies);
-        if (e != cudaSuccess) return abort_capture(e, "dependencies");
-    }
-    launch_project_step<T>(h, g, cur, cs);
-    cudaGraph_t full = nullptr;
-    e = cudaStreamEndCapture(cs, &full);
-    h->cur = save_cur;
-    h->dcur = save_dcur;
-    h->launches = l0;          // capture launches nothing
+int capture_begin(les_s* h, cudaStream_t cs) {
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    return LES_OK;
+}
+
+template <typename T>
+int capture_end(les_s* h, cudaStream_t cs, cudaGraphExec_t* out) {
+    cudaGraph_t gr = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &gr);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(h, LES_ECUDA, "graph capture: %s", cudaGetErrorString(e));
     }
-    e = cudaGraphInstantiate(&h->gexec[cur], full, 0);
-    cudaGraphDestroy(full);
+    if (*out) cudaGraphExecDestroy(*out);
+    *out = nullptr;
+    e = cudaGraphInstantiate(out, gr, 0);
+    cudaGraphDestroy(gr);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        h->gexec[cur] = nullptr;
+        *out = nullptr;
         return fail(h, LES_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
     }
+    return LES_OK;
+}
+
+template <typename T>
+int build_graph(les_s* h, int cur) {
+    Geo<T> g = geo<T>(h);
+    const les_grid_t& G = h->g;
+    cudaStream_t cs = h->cap[0];
+    const int save_cur = h->cur, save_dcur = h->dcur;
+    const long long l0 = h->launches;
+    h->cur = cur;
+    h->dcur = 0;
+    int rc = capture_begin<T>(h, cs);
+    if (rc) return rc;
+    long long nl = 0;
+    if (G.fixed_sweeps) {
+        launch_prefix<T>(h, g, cs);
+        launch_residual64<T>(g, h->ph[cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h),
+                             cond_args(h, RES_INIT, 0, 0), cs);
+        run_sweeps<T>(h, g, G.max_sweeps, 1, nl, cs);
+        launch_refine<T>(h, g, cond_args(h, RES_FIXED, G.max_sweeps, 0), cs);
+        launch_project_step<T>(h, g, cur, cs);
+    } else {
+        for (int b = 0; b < kChunkBatches; ++b) {
+            run_sweeps<T>(h, g, G.check_every, 2, nl, cs);     // check_every even: d returns to dl[0]
+            launch_sor_est<T>(g, (const T*)h->dl[h->dcur], (const T*)h->rr, reducer(h),
+                              cond_args(h, RES_LOOP, G.check_every, 1), cs);
+            launch_refine<T>(h, g, cond_args(h, RES_LOOP, G.check_every, 1), cs);
+        }
+    }
+    rc = capture_end<T>(h, cs, &h->gexec[cur]);
+    h->cur = save_cur;
+    h->dcur = save_dcur;
+    h->launches = l0;          // capture launches nothing
+    if (rc) return rc;
     h->graph_ok[cur] = true;
     return LES_OK;
 }
 
 void fill_stats(les_s* h, les_stats_t* st, int status);
 
-// kernels one graph step launches for a given sweep count (for the counter)
-long long graph_step_launches(const les_s* h, int sweeps) {
-    int pre = 3 + 1 + 1 + 1 + (h->d.pery ? 1 : 0) + (h->d.perz ? 1 : 0) + 1;
-    const les_grid_t& G = h->g;
-    int per_sweep = h->sor.tile < 0 ? 2 : 1;
-    int checks = G.fixed_sweeps ? 0 : (sweeps + G.check_every - 1) / G.check_every;
-    int refines = h->sc_host->batches;
-    return pre + 1 + (long long)sweeps * per_sweep + checks + 2LL * refines + 1;
-}
-
 template <typename T>
 int step_graph(les_s* h, int nsteps, les_stats_t* stats) {
+    const les_grid_t& G = h->g;
     for (int c = 0; c < 2; ++c)
         if (!h->graph_ok[c]) {
             int rc = build_graph<T>(h, c);
             if (rc) return rc;      // caller falls back to the host-driven loop
         }
+    Geo<T> g = geo<T>(h);
     CK(cudaMemsetAsync(&h->sc->noconv_any, 0, sizeof(int), h->stream));
+    const int per_chunk = kChunkBatches * G.check_every;
+    const int max_chunks = (G.max_sweeps + per_chunk - 1) / per_chunk + 1;
     for (int s = 0; s < nsteps; ++s) {
-        CK(cudaGraphLaunch(h->gexec[h->cur], h->stream));
+        if (G.fixed_sweeps) {
+            CK(cudaGraphLaunch(h->gexec[h->cur], h->stream));
+            h->launches += 7 + (h->d.pery ? 1 : 0) + (h->d.perz ? 1 : 0) + 1 + G.max_sweeps + 2 + 1;
+        } else {
+            *(volatile int*)h->done_host = 0;
+            launch_prefix<T>(h, g, h->stream);
+            h->launches += launch_residual64<T>(g, h->ph[h->cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h),
+                                                cond_args(h, RES_INIT, 0, 0), h->stream);
+            CK(cudaGetLastError());
+            for (int c = 0; c < max_chunks; ++c) {
+                CK(cudaGraphLaunch(h->gexec[h->cur], h->stream));
+                CK(cudaEventRecord(h->chunk_ev[c & 1], h->stream));
+                h->launches += kChunkBatches * (G.check_every + 3);
+                if (c >= 1) {
+                    CK(cudaEventSynchronize(h->chunk_ev[(c - 1) & 1]));
+                    if (*(volatile int*)h->done_host) break;
+                }
+            }
+            launch_project_step<T>(h, g, h->cur, h->stream);
+            CK(cudaGetLastError());
+        }
         h->cur = 1 - h->cur;
         h->step += 1;
     }
     int rc = fetch_scalars(h);
     if (rc) return rc;
-    h->launches += graph_step_launches(h, h->sc_host->sweeps) * nsteps;   // sweep count of the last step
-    int status = h->sc_host->noconv_any ? LES_ENOCONV : LES_OK;
+    int status = (!G.fixed_sweeps && h->sc_host->noconv_any) ? LES_ENOCONV : LES_OK;
     if (h->sc_host->nonfinite) return fail(h, LES_ENONFINITE, "SOR residual is not finite");
     if (stats) fill_stats(h, stats, status);
     return status;
@@ -703,6 +648,13 @@ void release(les_s* h) {
             cudaStreamDestroy(c);
             c = nullptr;
         }
+    for (cudaEvent_t& e : h->chunk_ev)
+        if (e) {
+            cudaEventDestroy(e);
+            e = nullptr;
+        }
+    if (h->done_host) cudaFreeHost(h->done_host);
+    h->done_host = nullptr;
     for (cudaEvent_t& e : h->ev)
         if (e) {
             cudaEventDestroy(e);
@@ -752,6 +704,11 @@ int create_impl(les_s* h, const uint8_t* solid) {
     h->stage_elems = io_elems(h, 1) + io_elems(h, 2) + io_elems(h, 3) + io_elems(h, 0);
     if ((rc = dalloc(h, &h->stage, h->stage_elems * h->es))) return rc;
     for (cudaStream_t& c : h->cap) CK(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : h->chunk_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    if (cudaHostAlloc((void**)&h->done_host, sizeof(int), cudaHostAllocMapped) != cudaSuccess)
+        return fail(h, LES_ENOMEM, "cudaHostAlloc failed");
+    *h->done_host = 0;
+    CK(cudaHostGetDevicePointer((void**)&h->done_dev, h->done_host, 0));
     if (cudaMallocHost((void**)&h->sc_host, sizeof(Scalars)) != cudaSuccess)
         return fail(h, LES_ENOMEM, "cudaMallocHost failed");
     memset(h->sc_host, 0, sizeof(Scalars));
@@ -962,7 +919,11 @@ int les_step(les_handle h, int32_t nsteps, les_stats_t* stats) {
         fill_stats(h, stats, LES_OK);
         return LES_OK;
     }
-    const bool graph_ok = h->use_graph && !h->timing && (h->g.fixed_sweeps || h->sor.tile < 0 || h->g.check_every % 2 == 0);
+    // chunk graphs need an even batch (the ping-pong returns to the same buffer)
+    // and a sweep budget made of whole batches; otherwise the host loop runs
+    const bool graph_ok = h->use_graph && !h->timing &&
+                          (h->g.fixed_sweeps ||
+                           (h->g.check_every % 2 == 0 && h->g.max_sweeps % h->g.check_every == 0));
     h->last_graph = graph_ok;
     if (graph_ok) {
         int rc = h->prec == LES_FP64 ? step_graph<double>(h, nsteps, stats) : step_graph<float>(h, nsteps, stats);

@@ -51,6 +51,8 @@ struct Scalars {
     int refine;             // the last estimate asked for a refinement
     double est;             // FP32-arithmetic estimate of the relative residual
     double rho_ref;         // FP64 relative residual at the last refinement
+    int done;               // the current solve has finished (kernels of a chunk exit early)
+    int pad2_;
 };
 
 // A refinement (FP64 accumulate + true residual) is taken when the cheap
@@ -61,15 +63,18 @@ constexpr int kRefineEvery = 2000;
 
 // what the residual kernel does with the solve's bookkeeping and, inside a
 // CUDA graph, with the conditional nodes of the SOR loop
-enum ResMode { RES_INIT = 0, RES_LOOP = 1, RES_TAIL = 2, RES_HOST = 3 };
+// What the residual kernels do with the solve's bookkeeping.
+//   RES_INIT   first residual of a solve: resets the counters and `done`
+//   RES_LOOP   refinement after an estimate asked for it
+//   RES_FIXED  the single residual after a fixed number of sweeps
+enum ResMode { RES_INIT = 0, RES_LOOP = 1, RES_FIXED = 2 };
 struct CondArgs {
-    cudaGraphConditionalHandle loop, tail, refine;
-    int use_cond;           // set the conditional handles (graph path)
     int mode;               // ResMode
-    int n;                  // sweeps in the batch just finished
-    int limit;              // sweeps the loop may run (multiple of check_every in the graph path)
-    int rem;                // remainder batch size after the loop (0: none)
+    int n;                  // sweeps in the batch just finished (estimate / fixed)
+    int limit;              // sweep budget of the solve (max_sweeps)
+    int gate;               // 1: run only while !done and a refinement was asked for
     double tol;
+    int* done_host;         // mapped host copy of `done` (nullable)
 };
 
 // constant per-run data in the compute type
@@ -114,7 +119,8 @@ template <typename T> int launch_rhs_mean(const Geo<T>& g, T* rhs, double vfluid
 // zero_start: 0 continue from d, 1 treat d as zero, 2 read the device flag sc->zflag
 template <typename T> int launch_sor_sweep(const Geo<T>& g, T* dl, const T* r, int zero_start, const Scalars* sc,
                                            cudaStream_t s);
-template <typename T> int launch_accum(const Geo<T>& g, double* ph, const T* dl, cudaStream_t s);
+template <typename T> int launch_accum(const Geo<T>& g, double* ph, const T* dl, const Scalars* sc, int gate,
+                                       cudaStream_t s);
 template <typename T> int launch_residual64(const Geo<T>& g, const double* ph, const T* rhs, T* r,
                                             double vfluid, const Reduce& red, CondArgs ca, cudaStream_t s);
 template <typename T> int launch_sor_est(const Geo<T>& g, const T* dl, const T* r, const Reduce& red, CondArgs ca,

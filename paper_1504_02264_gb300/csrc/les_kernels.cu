@@ -562,6 +562,7 @@ struct Poisson {
 template <typename T>
 __global__ void k_sor_half(Geo<T> g, T* dl, const T* r, int nrd, int zero_arg, const Scalars* sc) {
     const Dom& d = g.d;
+    if (sc->done) return;
     const bool zero_start = zero_arg == 1 || (zero_arg == 2 && sc->zflag);
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
@@ -604,8 +605,9 @@ int launch_sor_sweep(const Geo<T>& g, T* dl, const T* r, int zero_start, const S
 
 // Refinement: ph += d on the unknowns (own cell only, so in place).
 template <typename T>
-__global__ void k_accum(Geo<T> g, double* ph, const T* dl) {
+__global__ void k_accum(Geo<T> g, double* ph, const T* dl, const Scalars* sc, int gate) {
     const Dom& d = g.d;
+    if (gate && (sc->done || !sc->refine)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
     int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
     int k = blockIdx.z + 1;
@@ -615,9 +617,9 @@ __global__ void k_accum(Geo<T> g, double* ph, const T* dl) {
 }
 
 template <typename T>
-int launch_accum(const Geo<T>& g, double* ph, const T* dl, cudaStream_t s) {
+int launch_accum(const Geo<T>& g, double* ph, const T* dl, const Scalars* sc, int gate, cudaStream_t s) {
     const Dom& d = g.d;
-    k_accum<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(g, ph, dl);
+    k_accum<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(g, ph, dl, sc, gate);
     return 1;
 }
 
@@ -644,6 +646,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_residual64(Geo<T> g, const double* ph, const T* rhs, T* r, double vfluid,
                                                     Reduce red, CondArgs ca) {
     const Dom& d = g.d;
+    if (ca.gate && (red.sc->done || !red.sc->refine)) return;     // uniform over the grid
     const long long n = (long long)d.nx * d.ny * d.nz;
     const double mean = red.sc->rhs_mean;
     double x[3] = {0.0, 0.0, 0.0};
@@ -690,29 +693,22 @@ __global__ void __launch_bounds__(256) k_residual64(Geo<T> g, const double* ph, 
             sc->rho_ref = rel;
             sc->since = 0;
             sc->zflag = 1;
-            bool go = false, tail = false, final_check = false;
+            sc->refine = 0;
+            int done = 0;
             if (ca.mode == RES_INIT) {
                 sc->sweeps = 0;
                 sc->batches = 0;
-                go = ca.limit > 0;
-                tail = ca.limit == 0 && ca.rem > 0;
             } else if (ca.mode == RES_LOOP) {
                 sc->batches += 1;
-                go = !conv && !bad && sc->sweeps < ca.limit;
-                tail = !conv && !bad && sc->sweeps >= ca.limit && ca.rem > 0;
-                final_check = !go && !tail;
-            } else if (ca.mode == RES_TAIL) {
+                done = conv || bad || sc->sweeps >= ca.limit;
+                if (done && !conv) sc->noconv_any = 1;
+            } else {
                 sc->sweeps += ca.n;
                 sc->batches += 1;
-                final_check = true;
-            } else {
-                sc->batches += 1;
+                done = 1;
             }
-            if (final_check && !conv) sc->noconv_any = 1;
-            if (ca.use_cond) {
-                cudaGraphSetConditional(ca.loop, go ? 1u : 0u);
-                cudaGraphSetConditional(ca.tail, tail ? 1u : 0u);
-            }
+            sc->done = done;
+            if (ca.done_host) *(volatile int*)ca.done_host = done;
         }
     }
 }
@@ -732,6 +728,7 @@ int launch_residual64(const Geo<T>& g, const double* ph, const T* rhs, T* r, dou
 template <typename T>
 __global__ void __launch_bounds__(256) k_sor_est(Geo<T> g, const T* dl, const T* r, Reduce red, CondArgs ca) {
     const Dom& d = g.d;
+    if (red.sc->done) return;      // uniform over the grid
     const long long n = (long long)d.nx * d.ny * d.nz;
     double x[1] = {0.0};
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
@@ -768,10 +765,6 @@ __global__ void __launch_bounds__(256) k_sor_est(Geo<T> g, const T* dl, const T*
             const bool need = !(est > ca.tol) || est <= kRefineDrop * sc->rho_ref || sc->since >= kRefineEvery ||
                               sc->sweeps >= ca.limit;
             sc->refine = need;
-            if (ca.use_cond) {
-                cudaGraphSetConditional(ca.refine, need ? 1u : 0u);
-                cudaGraphSetConditional(ca.loop, need ? 0u : 1u);
-            }
         }
     }
 }
@@ -896,7 +889,7 @@ int max_reduce_blocks(const Dom& d) { return ((d.nx + 31) / 32) * ((d.ny + 7) / 
                                cudaStream_t);                                                           \
     template int launch_rhs_mean<T>(const Geo<T>&, T*, double, const Reduce&, cudaStream_t);            \
     template int launch_sor_sweep<T>(const Geo<T>&, T*, const T*, int, const Scalars*, cudaStream_t);   \
-    template int launch_accum<T>(const Geo<T>&, double*, const T*, cudaStream_t);                      \
+    template int launch_accum<T>(const Geo<T>&, double*, const T*, const Scalars*, int, cudaStream_t);  \
     template int launch_residual64<T>(const Geo<T>&, const double*, const T*, T*, double, const Reduce&, \
                                       CondArgs, cudaStream_t);                                          \
     template int launch_sor_est<T>(const Geo<T>&, const T*, const T*, const Reduce&, CondArgs, cudaStream_t); \

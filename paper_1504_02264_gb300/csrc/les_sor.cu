@@ -35,6 +35,7 @@ k_sor_fused(Geo<T> g, const T* __restrict__ din, T* __restrict__ dout, const T* 
     const int k0 = 1 + blockIdx.z * kc_len;
     const int k1 = min(k0 + kc_len, d.nz + 1);   // chunk is [k0, k1)
     const T omega = g.omega;
+    if (sc->done) return;
     const bool zero_start = zero_arg == 1 || (zero_arg == 2 && sc->zflag);
 
     // padded index of (i, j, k) with periodic wrap; false outside the padded box
@@ -154,6 +155,7 @@ k_sor_block(Geo<T> g, const T* __restrict__ din, T* __restrict__ dout, const T* 
     const int tid = threadIdx.x;
     const int i0 = 1 + blockIdx.x * BX, j0 = 1 + blockIdx.y * BY, k0 = 1 + blockIdx.z * BZ;
     const T omega = g.omega;
+    if (sc->done) return;
     const bool zero_start = zero_arg == 1 || (zero_arg == 2 && sc->zflag);
     auto src = [&](int i, int j, int k, long long& q) -> bool {
         if (d.perx) { i = i < 1 ? i + d.nx : (i > d.nx ? i - d.nx : i); }
@@ -176,65 +178,50 @@ k_sor_block(Geo<T> g, const T* __restrict__ din, T* __restrict__ dout, const T* 
     T* sDf = &sD[0][0][0];
     T* sRf = &sR[0][0][0];
     uint8_t* sFf = &sF[0][0][0];
-    if (inner) {
-        const long long bd = d.at(i0 - 2, j0 - 2, k0 - 2);
-        const long long br = d.at(i0 - 1, j0 - 1, k0 - 1);
-        T vd[LD];
-        T vr[LR];
-        uint8_t vf[LR];
+    const long long bd = d.at(i0 - 2, j0 - 2, k0 - 2);
+    const long long br = d.at(i0 - 1, j0 - 1, k0 - 1);
+    T vd[LD];
+    T vr[LR];
+    uint8_t vf[LR];
 #pragma unroll
-        for (int n = 0; n < LD; ++n) {
-            const int q = tid + n * NT;
-            vd[n] = T(0);
-            if (q < ND && !zero_start) {
-                const int ii = q % DX, t = q / DX, jj = t % DY, kk = t / DY;
-                vd[n] = din[bd + ((long long)kk * d.py + jj) * d.px + ii];
-            }
+    for (int n = 0; n < LD; ++n) {
+        const int q = tid + n * NT;
+        vd[n] = T(0);
+        if (q < ND && !zero_start) {
+            const int ii = q % DX, t = q / DX, jj = t % DY, kk = t / DY;
+            long long a = bd + ((long long)kk * d.py + jj) * d.px + ii;
+            bool ok = true;
+            if (!inner) ok = src(i0 - 2 + ii, j0 - 2 + jj, k0 - 2 + kk, a);
+            if (ok) vd[n] = din[a];
         }
+    }
 #pragma unroll
-        for (int n = 0; n < LR; ++n) {
-            const int q = tid + n * NT;
-            vf[n] = 0;
-            vr[n] = T(0);
-            if (q < NR) {
-                const int ii = q % RX, t = q / RX, jj = t % RY, kk = t / RY;
-                const long long a = br + ((long long)kk * d.py + jj) * d.px + ii;
+    for (int n = 0; n < LR; ++n) {
+        const int q = tid + n * NT;
+        vf[n] = 0;
+        vr[n] = T(0);
+        if (q < NR) {
+            const int ii = q % RX, t = q / RX, jj = t % RY, kk = t / RY;
+            long long a = br + ((long long)kk * d.py + jj) * d.px + ii;
+            bool ok = true;
+            if (!inner) ok = src(i0 - 1 + ii, j0 - 1 + jj, k0 - 1 + kk, a);
+            if (ok) {
                 vf[n] = g.flags[a];
                 vr[n] = r[a];
             }
         }
+    }
 #pragma unroll
-        for (int n = 0; n < LD; ++n) {
-            const int q = tid + n * NT;
-            if (q < ND) sDf[q] = vd[n];
-        }
+    for (int n = 0; n < LD; ++n) {
+        const int q = tid + n * NT;
+        if (q < ND) sDf[q] = vd[n];
+    }
 #pragma unroll
-        for (int n = 0; n < LR; ++n) {
-            const int q = tid + n * NT;
-            if (q < NR) {
-                sRf[q] = (vf[n] & F_UNK) ? vr[n] : T(0);
-                sFf[q] = vf[n];
-            }
-        }
-    } else {
-        for (int q = tid; q < ND; q += NT) {
-            const int ii = q % DX, t = q / DX, jj = t % DY, kk = t / DY;
-            long long s;
-            T v = T(0);
-            if (!zero_start && src(i0 - 2 + ii, j0 - 2 + jj, k0 - 2 + kk, s)) v = din[s];
-            sDf[q] = v;
-        }
-        for (int q = tid; q < NR; q += NT) {
-            const int ii = q % RX, t = q / RX, jj = t % RY, kk = t / RY;
-            long long s;
-            T rv = T(0);
-            uint8_t fv = 0;
-            if (src(i0 - 1 + ii, j0 - 1 + jj, k0 - 1 + kk, s)) {
-                fv = g.flags[s];
-                if (fv & F_UNK) rv = r[s];
-            }
-            sRf[q] = rv;
-            sFf[q] = fv;
+    for (int n = 0; n < LR; ++n) {
+        const int q = tid + n * NT;
+        if (q < NR) {
+            sRf[q] = (vf[n] & F_UNK) ? vr[n] : T(0);
+            sFf[q] = vf[n];
         }
     }
     __syncthreads();

@@ -285,7 +285,8 @@ def test_graph_step_matches_host_loop(mode):
     for _ in range(3):
         sa = a.step(1)
         sb = b.step(1)
-        assert sb["graph"] == 1 and sa["graph"] == 0
+        # a sweep budget that is not a whole number of batches runs the host loop
+        assert sb["graph"] == (0 if mode == "tol_remainder" else 1) and sa["graph"] == 0
         assert sa["sweeps"] == sb["sweeps"] and sa["rc"] == sb["rc"], (sa, sb)
         assert sa["step"] == sb["step"]
     for x, y in zip(a.fields(), b.fields()):
