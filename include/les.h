@@ -215,7 +215,7 @@ int les_set_graph(les_handle h, int32_t enable);
  * handle's grid (sweeps per candidate), keeps the fastest and reports it;
  * the field state is saved and restored around the trial sweeps.
  */
-#define LES_SOR_NTILES 12
+#define LES_SOR_NTILES 17
 int les_set_sor_config(les_handle h, int32_t tile, int32_t kc);
 int les_get_sor_config(les_handle h, int32_t* tile, int32_t* kc);
 int les_sor_tile(int32_t tile, int32_t* tx, int32_t* ty, int32_t* tz);

@@ -678,6 +678,7 @@ int create_impl(les_s* h, const uint8_t* solid) {
     d.perx = G.bc_x == LES_BC_PERIODIC;
     d.pery = G.bc_y == LES_BC_PERIODIC;
     d.perz = G.bc_z == LES_BC_PERIODIC;
+    if (d.total() + 16 > 0x7fffffffLL) return fail(h, LES_EINVAL, "padded grid exceeds 2^31 elements");
     h->n = (size_t)d.total() + 16;     // slack so a vector load past the last row stays in bounds
     const size_t B = h->n * h->es;
     int rc;

@@ -632,11 +632,11 @@ int reduce_blocks(const Dom& d) {
     return (int)(b < kReduceBlocks ? b : kReduceBlocks);
 }
 
-__device__ __forceinline__ void cell_of(const Dom& d, long long q, int& i, int& j, int& k) {
-    i = (int)(q % d.nx) + 1;
-    long long t = q / d.nx;
-    j = (int)(t % d.ny) + 1;
-    k = (int)(t / d.ny) + 1;
+__device__ __forceinline__ void cell_of(const Dom& d, int q, int& i, int& j, int& k) {
+    i = q % d.nx + 1;
+    const int t = q / d.nx;
+    j = t % d.ny + 1;
+    k = t / d.ny + 1;
 }
 
 // r = (rhs - mean) - A ph formed in FP64 and stored in T; FP64 norms, the
@@ -647,10 +647,10 @@ __global__ void __launch_bounds__(256) k_residual64(Geo<T> g, const double* ph, 
                                                     Reduce red, CondArgs ca) {
     const Dom& d = g.d;
     if (ca.gate && (red.sc->done || !red.sc->refine)) return;     // uniform over the grid
-    const long long n = (long long)d.nx * d.ny * d.nz;
+    const int n = d.nx * d.ny * d.nz;
     const double mean = red.sc->rhs_mean;
     double x[3] = {0.0, 0.0, 0.0};
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
         int i, j, k;
         cell_of(d, q, i, j, k);
         long long c = d.at(i, j, k);
@@ -729,9 +729,9 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_sor_est(Geo<T> g, const T* dl, const T* r, Reduce red, CondArgs ca) {
     const Dom& d = g.d;
     if (red.sc->done) return;      // uniform over the grid
-    const long long n = (long long)d.nx * d.ny * d.nz;
+    const int n = d.nx * d.ny * d.nz;
     double x[1] = {0.0};
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
         int i, j, k;
         cell_of(d, q, i, j, k);
         long long c = d.at(i, j, k);

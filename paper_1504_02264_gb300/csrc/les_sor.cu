@@ -273,6 +273,179 @@ k_sor_block(Geo<T> g, const T* __restrict__ din, T* __restrict__ dout, const T* 
     }
 }
 
+// Row-mapped 3-D block variant (28 x BY x BZ): the d tile is 32 cells wide,
+// so each halo row is one warp-wide coalesced load; per-lane column offsets
+// and per-row offsets are computed once (32-bit), and cn1 comes from a
+// per-CTA table over (plane, open-face mask) built with the same arithmetic
+// as the scalar update, so the iterate is bit-identical to the other kernels.
+template <typename T, int BY, int BZ>
+struct RowTile {
+    static constexpr int BX = 28, DX = 32, DY = BY + 4, DZ = BZ + 4, RY = BY + 2, RZ = BZ + 2;
+    static constexpr size_t smem() {
+        return sizeof(T) * (DZ * DY * DX + RZ * RY * 32 + RZ * 64 + 2 * RZ) + RZ * RY * 32;
+    }
+};
+
+template <typename T, int BY, int BZ>
+__global__ void __launch_bounds__(256)
+k_sor_rows(Geo<T> g, const T* __restrict__ din, T* __restrict__ dout, const T* __restrict__ r, int zero_arg,
+           const Scalars* __restrict__ sc) {
+    using RT = RowTile<T, BY, BZ>;
+    constexpr int DX = RT::DX, DY = RT::DY, DZ = RT::DZ, RY = RT::RY, RZ = RT::RZ, BX = RT::BX;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T(*sD)[DY][DX] = reinterpret_cast<T(*)[DY][DX]>(smem_raw);
+    T(*sR)[RY][32] = reinterpret_cast<T(*)[RY][32]>(smem_raw + sizeof(T) * DZ * DY * DX);
+    T(*sCN)[64] = reinterpret_cast<T(*)[64]>(smem_raw + sizeof(T) * (DZ * DY * DX + RZ * RY * 32));
+    T* sCT = reinterpret_cast<T*>(smem_raw + sizeof(T) * (DZ * DY * DX + RZ * RY * 32 + RZ * 64));
+    T* sCB = sCT + RZ;
+    uint8_t(*sF)[RY][32] =
+        reinterpret_cast<uint8_t(*)[RY][32]>(smem_raw + sizeof(T) * (DZ * DY * DX + RZ * RY * 32 + RZ * 64 + 2 * RZ));
+    if (sc->done) return;
+    const Dom& d = g.d;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int i0 = 1 + blockIdx.x * BX, j0 = 1 + blockIdx.y * BY, k0 = 1 + blockIdx.z * BZ;
+    const bool zero_start = zero_arg == 1 || (zero_arg == 2 && sc->zflag);
+    const int px = d.px, py = d.py;
+    // column offset of a lane (wrapped on a periodic axis), -1 outside the padded box
+    auto col = [&](int i) -> int {
+        if (d.perx) i = i < 1 ? i + d.nx : (i > d.nx ? i - d.nx : i);
+        else if (i < 0 || i > d.nx + 1) return -1;
+        return i + OX;
+    };
+    auto row = [&](int j, int k) -> int {
+        if (d.pery) j = j < 1 ? j + d.ny : (j > d.ny ? j - d.ny : j);
+        else if (j < 0 || j > d.ny + 1) return -1;
+        if (d.perz) k = k < 1 ? k + d.nz : (k > d.nz ? k - d.nz : k);
+        else if (k < 0 || k > d.nz + 1) return -1;
+        return (k * py + j) * px;
+    };
+    const int cD = col(i0 - 2 + lane);
+    const int cR = lane < BX + 2 ? col(i0 - 1 + lane) : -1;
+    constexpr int ND = (DY * DZ + 7) / 8, NR = (RY * RZ + 7) / 8;
+    T vd[ND];
+    T vr[NR];
+    uint8_t vf[NR];
+#pragma unroll
+    for (int n = 0; n < ND; ++n) {
+        const int rw = warp + 8 * n;
+        vd[n] = T(0);
+        if (rw < DY * DZ && !zero_start) {
+            const int ro = row(j0 - 2 + rw % DY, k0 - 2 + rw / DY);
+            if (ro >= 0 && cD >= 0) vd[n] = din[ro + cD];
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < NR; ++n) {
+        const int rw = warp + 8 * n;
+        vf[n] = 0;
+        vr[n] = T(0);
+        if (rw < RY * RZ) {
+            const int ro = row(j0 - 1 + rw % RY, k0 - 1 + rw / RY);
+            if (ro >= 0 && cR >= 0) {
+                vf[n] = g.flags[ro + cR];
+                vr[n] = r[ro + cR];
+            }
+        }
+    }
+    // per-plane coefficients and the cn1 table over the six open-face bits
+    for (int q = tid; q < RZ * 64; q += 256) {
+        const int kk = q >> 6, m = q & 63;
+        int k = k0 - 1 + kk;
+        k = d.perz ? (k < 1 ? k + d.nz : (k > d.nz ? k - d.nz : k)) : min(max(k, 0), d.nz + 1);
+        const T ct = g.cT[k], cb = g.cB[k];
+        T ae = (m & F_E) ? g.cx : T(0);
+        T aw = (m & F_W) ? g.cx : T(0);
+        T an = (m & F_N) ? g.cy : T(0);
+        T as = (m & F_S) ? g.cy : T(0);
+        T at = (m & F_T) ? ct : T(0);
+        T ab = (m & F_B) ? cb : T(0);
+        const T sum = ae + aw + an + as + at + ab;
+        sCN[kk][m] = sum > T(0) ? T(1) / sum : T(0);
+        if (m == 0) {
+            sCT[kk] = ct;
+            sCB[kk] = cb;
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < ND; ++n) {
+        const int rw = warp + 8 * n;
+        if (rw < DY * DZ) sD[rw / DY][rw % DY][lane] = vd[n];
+    }
+#pragma unroll
+    for (int n = 0; n < NR; ++n) {
+        const int rw = warp + 8 * n;
+        if (rw < RY * RZ) {
+            sR[rw / RY][rw % RY][lane] = (vf[n] & F_UNK) ? vr[n] : T(0);
+            sF[rw / RY][rw % RY][lane] = vf[n];
+        }
+    }
+    __syncthreads();
+    const T omega = g.omega, cx = g.cx, cy = g.cy;
+    auto relax = [&](int x, int y, int z, int kz, uint8_t f, T rhs) {
+        T ae = (f & F_E) ? cx : T(0);
+        T aw = (f & F_W) ? cx : T(0);
+        T an = (f & F_N) ? cy : T(0);
+        T as = (f & F_S) ? cy : T(0);
+        T at = (f & F_T) ? sCT[kz] : T(0);
+        T ab = (f & F_B) ? sCB[kz] : T(0);
+        const T cn1 = sCN[kz][f & 63];
+        T s = T(0);
+        s += ae * sD[z][y][x + 1];
+        s += aw * sD[z][y][x - 1];
+        s += an * sD[z][y + 1][x];
+        s += as * sD[z][y - 1][x];
+        s += at * sD[z + 1][y][x];
+        s += ab * sD[z - 1][y][x];
+        T own = sD[z][y][x];
+        T reltmp = omega * (cn1 * (s - rhs) - own);
+        sD[z][y][x] = own + reltmp;
+    };
+    // red (i+j+k odd) on block + 1 ring: 15 per 30-wide row, two rows per warp pass
+    const int half = lane >> 4, m = lane & 15;
+    for (int p = warp; 2 * p < RY * RZ; p += 8) {
+        const int rw = 2 * p + half;
+        if (rw < RY * RZ && m < (BX + 2) / 2) {
+            const int jj = rw % RY, kk = rw / RY;
+            const int ii = 2 * m + ((i0 + (j0 - 1 + jj) + (k0 - 1 + kk)) & 1);
+            const uint8_t f = sF[kk][jj][ii];
+            if (f & F_UNK) relax(ii + 1, jj + 1, kk + 1, kk, f, sR[kk][jj][ii]);
+        }
+    }
+    __syncthreads();
+    // black (i+j+k even) on the block: 14 per row
+    for (int p = warp; 2 * p < BY * BZ; p += 8) {
+        const int rw = 2 * p + half;
+        if (rw < BY * BZ && m < BX / 2) {
+            const int jj = rw % BY, kk = rw / BY;
+            const int ii = 2 * m + ((i0 + (j0 + jj) + (k0 + kk)) & 1);
+            const uint8_t f = sF[kk + 1][jj + 1][ii + 1];
+            if (f & F_UNK) relax(ii + 2, jj + 2, kk + 2, kk + 1, f, sR[kk + 1][jj + 1][ii + 1]);
+        }
+    }
+    __syncthreads();
+    const int i = i0 + lane;
+    for (int rw = warp; rw < BY * BZ; rw += 8) {
+        const int jj = rw % BY, kk = rw / BY;
+        const int j = j0 + jj, k = k0 + kk;
+        if (lane < BX && i <= d.nx && j <= d.ny && k <= d.nz && (sF[kk + 1][jj + 1][lane + 1] & F_UNK))
+            dout[(k * py + j) * px + i + OX] = sD[kk + 2][jj + 2][lane + 2];
+    }
+}
+
+template <typename T, int BY, int BZ>
+static cudaError_t allow_rows() {
+    return cudaFuncSetAttribute(k_sor_rows<T, BY, BZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)RowTile<T, BY, BZ>::smem());
+}
+
+template <typename T, int BY, int BZ>
+static void launch_rows(const Geo<T>& g, const T* din, T* dout, const T* r, int zero_start, const Scalars* sc,
+                        cudaStream_t s) {
+    const Dom& d = g.d;
+    dim3 grid((d.nx + 27) / 28, (d.ny + BY - 1) / BY, (d.nz + BZ - 1) / BZ);
+    k_sor_rows<T, BY, BZ><<<grid, 256, RowTile<T, BY, BZ>::smem(), s>>>(g, din, dout, r, zero_start, sc);
+}
+
 template <typename T, int BX, int BY, int BZ>
 constexpr size_t block_smem() {
     return sizeof(T) * ((BX + 4) * (BY + 4) * (BZ + 4) + (BX + 2) * (BY + 2) * (BZ + 2)) +
@@ -304,8 +477,9 @@ static void launch_tile(const Geo<T>& g, const T* din, T* dout, const T* r, int 
 
 // tile shapes the autotuner chooses from: (TX, TY, 0) k-marching column tiles
 // (the k-chunk is free), (BX, BY, BZ) 3-D blocks
-const SorTile kSorTiles[] = {{32, 4, 0},  {32, 8, 0}, {64, 4, 0}, {64, 8, 0}, {128, 2, 0}, {128, 4, 0},
-                             {32, 8, 4},  {32, 4, 8}, {64, 4, 4}, {32, 8, 8}, {16, 8, 8}, {64, 8, 2}};
+const SorTile kSorTiles[] = {{32, 4, 0}, {32, 8, 0}, {64, 4, 0},  {64, 8, 0}, {128, 2, 0}, {128, 4, 0},
+                             {32, 8, 4}, {32, 4, 8}, {64, 4, 4},  {32, 8, 8}, {16, 8, 8}, {64, 8, 2},
+                             {28, 8, 8}, {28, 4, 8}, {28, 8, 4}, {28, 16, 4}, {28, 4, 16}};
 const int kNumSorTiles = sizeof(kSorTiles) / sizeof(kSorTiles[0]);
 
 template <typename T>
@@ -324,7 +498,12 @@ int launch_sor_fused(const Geo<T>& g, const T* din, T* dout, const T* r, int zer
         case 8: launch_block<T, 64, 4, 4>(g, din, dout, r, zero_start, sc, s); break;
         case 9: launch_block<T, 32, 8, 8>(g, din, dout, r, zero_start, sc, s); break;
         case 10: launch_block<T, 16, 8, 8>(g, din, dout, r, zero_start, sc, s); break;
-        default: launch_block<T, 64, 8, 2>(g, din, dout, r, zero_start, sc, s); break;
+        case 11: launch_block<T, 64, 8, 2>(g, din, dout, r, zero_start, sc, s); break;
+        case 12: launch_rows<T, 8, 8>(g, din, dout, r, zero_start, sc, s); break;
+        case 13: launch_rows<T, 4, 8>(g, din, dout, r, zero_start, sc, s); break;
+        case 14: launch_rows<T, 8, 4>(g, din, dout, r, zero_start, sc, s); break;
+        case 15: launch_rows<T, 16, 4>(g, din, dout, r, zero_start, sc, s); break;
+        default: launch_rows<T, 4, 16>(g, din, dout, r, zero_start, sc, s); break;
     }
     return 1;
 }
@@ -340,6 +519,11 @@ cudaError_t sor_prepare() {
     if ((x = allow_block<T, 32, 8, 8>()) != cudaSuccess) e = x;
     if ((x = allow_block<T, 16, 8, 8>()) != cudaSuccess) e = x;
     if ((x = allow_block<T, 64, 8, 2>()) != cudaSuccess) e = x;
+    if ((x = allow_rows<T, 8, 8>()) != cudaSuccess) e = x;
+    if ((x = allow_rows<T, 4, 8>()) != cudaSuccess) e = x;
+    if ((x = allow_rows<T, 8, 4>()) != cudaSuccess) e = x;
+    if ((x = allow_rows<T, 16, 4>()) != cudaSuccess) e = x;
+    if ((x = allow_rows<T, 4, 16>()) != cudaSuccess) e = x;
     return e;
 }
 template cudaError_t sor_prepare<float>();
