@@ -221,6 +221,44 @@ int les_get_sor_config(les_handle h, int32_t* tile, int32_t* kc);
 int les_sor_tile(int32_t tile, int32_t* tx, int32_t* ty, int32_t* tz);
 int les_autotune_sor(les_handle h, int32_t sweeps, double* best_ms_per_sweep);
 
+/*
+ * les_residual_noalloc: FP64 norms of the pressure Poisson residual for
+ * callers that cannot allocate device memory (code running inside another
+ * framework's memory pool, programs with a device-memory budget fixed at
+ * start-up, or callers that must not allocate while a stream capture is in
+ * progress elsewhere).  The paper has no counterpart: this is a service entry
+ * point next to the handle API, and it allocates nothing.
+ *
+ *   grid     nx, ny, nz, bc_x/y/z, dx, dy and precision are read (dz, the
+ *            SOR settings and the rest are ignored).
+ *   d_p      device array (nz, ny, nx) of pressure, element type per
+ *            precision (float for LES_FP32, double for LES_FP64).
+ *   d_rhs    device array (nz, ny, nx), same type: the right-hand side as is
+ *            (no mean is removed).
+ *   d_solid  device array (nz, ny, nx) of bytes, nonzero = building cell.
+ *   d_dz     device array [nz] of cell heights (double).
+ *   d_out    device array of 3 doubles written on completion:
+ *            [0] sum r^2, [1] sum rhs^2, [2] sqrt([0]/[1]) (sqrt([0]) when
+ *            [1] == 0), with r = rhs - A p over the fluid cells that have an
+ *            open face, A the operator of les_pressure_solve.
+ *   stream   cudaStream_t the work is ordered on (NULL = legacy default).
+ * The caller owns every buffer.  The only scratch is a fixed device array of
+ * about 64 KB in this library (4096 FP64 partial-sum pairs and a counter),
+ * present on every GPU that loads the library until the process exits; the
+ * entry point never calls cudaMalloc, cudaFree or any allocating routine.
+ * On its first call on a device (with that device current) it looks up the
+ * array's device address once; make that first call before any stream
+ * capture.  Each call clears the counter before use.  All calls share the
+ * array, so calls whose kernels overlap on the GPU (different streams, or
+ * different host threads) race and give wrong norms: order them.
+ * Grids above LES_NOALLOC_MAX_CELLS cells (the 32-bit index limit) and bad
+ * arguments give LES_EINVAL; CUDA failures LES_ECUDA.  Asynchronous: read
+ * d_out after synchronising the stream.
+ */
+#define LES_NOALLOC_MAX_CELLS 2147483647LL
+int les_residual_noalloc(const les_grid_t* grid, const void* d_p, const void* d_rhs, const uint8_t* d_solid,
+                         const double* d_dz, double* d_out, void* stream);
+
 /* Bracket a region for a profiler started with capture off
  * (cudaProfilerStart when start != 0, cudaProfilerStop otherwise). */
 int les_profiler_range(int32_t start);

@@ -84,6 +84,7 @@ def lib(build_if_missing: bool = False):
         L.les_get_state.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
         L.les_set_state.argtypes = [vp, vp, ctypes.c_size_t]
         L.les_profiler_range.argtypes = [i32]
+        L.les_residual_noalloc.argtypes = [ctypes.POINTER(les_grid_t), vp, vp, vp, vp, vp, vp]
         L.les_set_graph.argtypes = [vp, i32]
         L.les_set_sor_config.argtypes = [vp, i32, i32]
         L.les_get_sor_config.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
@@ -91,7 +92,7 @@ def lib(build_if_missing: bool = False):
         L.les_autotune_sor.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
         L.les_set_timing.argtypes = [vp, i32]
         L.les_get_timing.argtypes = [vp, ctypes.POINTER(les_timing_t)]
-        for name in ("les_profiler_range", "les_set_graph", "les_set_sor_config", "les_get_sor_config", "les_sor_tile", "les_autotune_sor",
+        for name in ("les_residual_noalloc", "les_profiler_range", "les_set_graph", "les_set_sor_config", "les_get_sor_config", "les_sor_tile", "les_autotune_sor",
                      "les_set_timing", "les_get_timing", "les_create", "les_set_fields", "les_get_fields", "les_set_inflow", "les_step",
                      "les_pressure_solve", "les_get_aux", "les_get_state", "les_set_state"):
             getattr(L, name).restype = ctypes.c_int
@@ -172,6 +173,11 @@ def les_set_timing(h, enable):
 
 def les_get_timing(h, t: les_timing_t):
     return _check(lib().les_get_timing(h, ctypes.byref(t)), h)
+
+
+def les_residual_noalloc(grid: les_grid_t, d_p, d_rhs, d_solid, d_dz, d_out, stream=None):
+    """Device pointers (ints) in, device pointer out; allocates nothing."""
+    return _check(lib().les_residual_noalloc(ctypes.byref(grid), d_p, d_rhs, d_solid, d_dz, d_out, stream))
 
 
 def les_profiler_range(start):
