@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include <cuda_profiler_api.h>
@@ -114,6 +115,8 @@ struct les_s {
     int dcur = 0;                         // buffer holding the current SOR correction
     bool graph_failed = false;            // graph build failed once; host-driven loop in use
     bool last_graph = false;              // the last les_step ran as graphs
+    TmaMaps tma[kNumTmaTiles];            // tensor maps of the TMA sweep (FP32, no periodic axis)
+    bool tma_ok = false;
     // phase timing
     bool timing = false;
     cudaEvent_t ev[8] = {};
@@ -268,6 +271,14 @@ int run_sweeps(les_s* h, const Geo<T>& g, int n, int zero, long long& launched, 
     }
     for (int s = 0; s < n; ++s) {
         const int in = h->dcur, out = 1 - h->dcur;
+        if constexpr (std::is_same<T, float>::value) {
+            if (h->sor.tile >= kFirstTmaTile) {
+                launched += launch_sor_tma(g, h->tma, h->sor.tile - kFirstTmaTile, in, (float*)h->dl[out],
+                                           s == 0 ? zero : 0, h->sc, st);
+                h->dcur = out;
+                continue;
+            }
+        }
         launched += launch_sor_fused<T>(g, (const T*)h->dl[in], (T*)h->dl[out], rr, s == 0 ? zero : 0, h->sc, h->sor,
                                         st);
         h->dcur = out;
@@ -351,6 +362,7 @@ int sor_solve(les_s* h) {
         }
     }
     h->sc_host->sweeps = sweeps;
+    if (h->sc_host->timeout) return fail(h, LES_ETIMEOUT, "a bounded device wait (TMA tile load) timed out");
     if (h->sc_host->nonfinite) return fail(h, LES_ENONFINITE, "SOR residual is not finite");
     return (!G.fixed_sweeps && !conv) ? LES_ENOCONV : LES_OK;
 }
@@ -370,10 +382,11 @@ int autotune_impl(les_s* h, int sweeps, double* best_ms) {
     CK(cudaMemsetAsync(&h->sc->done, 0, sizeof(int), h->stream));
     SorCfg keep = h->sor, best = keep;
     double bms = 1e300;
-    for (int t = 0; t < kNumSorTiles; ++t)
+    const int ntiles = kNumSorTiles + (h->tma_ok ? kNumTmaTiles : 0);
+    for (int t = 0; t < ntiles; ++t)
         for (int kc : kcs) {
             if (kc > h->g.nz) continue;
-            if (kSorTiles[t].tz > 0 && kc != 0) continue;      // 3-D blocks ignore kc
+            if ((t >= kNumSorTiles || kSorTiles[t].tz > 0) && kc != 0) continue;      // 3-D blocks ignore kc
             h->sor = SorCfg{t, kc};
             long long nl = 0;
             run_sweeps<T>(h, g, 2, 0, nl, h->stream);       // warm
@@ -559,6 +572,7 @@ int step_graph(les_s* h, int nsteps, les_stats_t* stats) {
     int rc = fetch_scalars(h);
     if (rc) return rc;
     int status = (!G.fixed_sweeps && h->sc_host->noconv_any) ? LES_ENOCONV : LES_OK;
+    if (h->sc_host->timeout) return fail(h, LES_ETIMEOUT, "a bounded device wait (TMA tile load) timed out");
     if (h->sc_host->nonfinite) return fail(h, LES_ENONFINITE, "SOR residual is not finite");
     if (stats) fill_stats(h, stats, status);
     return status;
@@ -740,6 +754,10 @@ int create_impl(les_s* h, const uint8_t* solid) {
     rc = h->prec == LES_FP64 ? init_tables<double>(h) : init_tables<float>(h);
     if (rc) return rc;
     CK(h->prec == LES_FP64 ? sor_prepare<double>() : sor_prepare<float>());
+    if (h->prec == LES_FP32 && tma_supported(d)) {
+        CK(tma_prepare());
+        h->tma_ok = tma_encode(d, (float*)h->dl[0], (float*)h->dl[1], (float*)h->rr, h->flags, h->tma);
+    }
     CK(cudaStreamSynchronize(h->stream));
     return LES_OK;
 }
@@ -1016,7 +1034,9 @@ int les_set_state(les_handle h, const void* buf, size_t len) {
 
 int les_set_sor_config(les_handle h, int32_t tile, int32_t kc) {
     if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
-    if (tile < -1 || tile >= kNumSorTiles) return fail(h, LES_EINVAL, "tile %d out of range", tile);
+    if (tile < -1 || tile >= kNumSorTiles + kNumTmaTiles) return fail(h, LES_EINVAL, "tile %d out of range", tile);
+    if (tile >= kNumSorTiles && !h->tma_ok)
+        return fail(h, LES_EINVAL, "TMA tiles need an FP32 grid without periodic axes");
     h->sor = SorCfg{tile, kc};
     h->graph_ok[0] = h->graph_ok[1] = false;
     return LES_OK;
@@ -1036,6 +1056,12 @@ int les_get_sor_config(les_handle h, int32_t* tile, int32_t* kc) {
 }
 
 int les_sor_tile(int32_t tile, int32_t* tx, int32_t* ty, int32_t* tz) {
+    if (tile >= kNumSorTiles && tile < kNumSorTiles + kNumTmaTiles) {
+        if (tx) *tx = 28;
+        if (ty) *ty = kTmaCfg[tile - kNumSorTiles][0];
+        if (tz) *tz = kTmaCfg[tile - kNumSorTiles][1];
+        return LES_OK;
+    }
     if (tile < 0 || tile >= kNumSorTiles) return fail(nullptr, LES_EINVAL, "tile %d out of range", tile);
     if (tx) *tx = kSorTiles[tile].tx;
     if (ty) *ty = kSorTiles[tile].ty;

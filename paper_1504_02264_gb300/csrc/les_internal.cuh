@@ -8,6 +8,8 @@
 // elements so every row starts 64-byte aligned.
 #pragma once
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -52,7 +54,7 @@ struct Scalars {
     double est;             // FP32-arithmetic estimate of the relative residual
     double rho_ref;         // FP64 relative residual at the last refinement
     int done;               // the current solve has finished (kernels of a chunk exit early)
-    int pad2_;
+    int timeout;            // a bounded device-side wait gave up (sticky until reported)
 };
 
 // A refinement (FP64 accumulate + true residual) is taken when the cheap
@@ -144,6 +146,18 @@ template <typename T> int launch_sor_fused(const Geo<T>& g, const T* din, T* dou
                                            const Scalars* sc, SorCfg cfg, cudaStream_t s);
 
 template <typename T> cudaError_t sor_prepare();
+
+// TMA variant (les_sor_tma.cu): FP32, no periodic axis; tile indices
+// kFirstTmaTile .. kFirstTmaTile + kNumTmaTiles - 1
+constexpr int kFirstTmaTile = 17;
+constexpr int kNumTmaTiles = 4;
+extern const int kTmaCfg[kNumTmaTiles][3];
+struct TmaMaps { CUtensorMap d[2], r, f; };
+bool tma_supported(const Dom& d);
+cudaError_t tma_prepare();
+bool tma_encode(const Dom& d, float* dl0, float* dl1, float* rr, uint8_t* flags, TmaMaps* maps);
+int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, int cfg, int in, float* dout, int zero, Scalars* sc,
+                   cudaStream_t s);
 
 int max_reduce_blocks(const Dom& d);
 

@@ -1,0 +1,279 @@
+// TMA variant of the fused red-black SOR sweep (Sec. 2.6) for FP32 domains
+// without periodic axes.
+//
+// A CTA owns a 28 x BY x BZ block.  One thread issues three tiled bulk-tensor
+// copies (cp.async.bulk.tensor) into shared memory on one mbarrier: the
+// correction d on the block plus a 2-cell halo, and r and the cell flags on
+// the block plus a 1-cell ring.  Cells outside the padded array arrive as
+// zeros (the copy's out-of-bounds fill), which is what the Neumann ghost
+// layer holds, so no per-element bounds logic is needed.  While the copies
+// are in flight the threads build the per-plane cn1 table.  Then red on the
+// block + ring, black on the block, and the block is stored (unknowns only),
+// exactly as in the other fused variants (bit-identical iterate).
+//
+// Alignment: the d and r tiles start at padded column 28*bx (a multiple of 4
+// floats = 16 bytes); the flag tile starts at the multiple of 16 bytes below it
+// and is 48 bytes wide.  The wait on the mbarrier is bounded by the global
+// timer; on a timeout the block records it in Scalars::timeout and returns
+// without touching the output.
+#include "les_internal.cuh"
+
+namespace les {
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+constexpr uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
+
+template <int BY, int BZ>
+struct TmaTile {
+    static constexpr int BX = 28, DXW = 36, FXW = 48;
+    static constexpr int DY = BY + 4, DZ = BZ + 4, RY = BY + 2, RZ = BZ + 2;
+    static constexpr uint32_t BYTES_D = DXW * DY * DZ * 4;
+    static constexpr uint32_t BYTES_R = DXW * RY * RZ * 4;
+    static constexpr uint32_t BYTES_F = FXW * RY * RZ;
+    static constexpr uint32_t OFF_R = align_up(BYTES_D, 128);
+    static constexpr uint32_t OFF_F = OFF_R + align_up(BYTES_R, 128);
+    static constexpr uint32_t OFF_CN = OFF_F + align_up(BYTES_F, 128);
+    static constexpr uint32_t OFF_CT = OFF_CN + RZ * 64 * 4;
+    static constexpr uint32_t OFF_BAR = align_up(OFF_CT + 2 * RZ * 4, 8);
+    static constexpr uint32_t SMEM = OFF_BAR + 8;
+};
+
+template <int BY, int BZ, int NT>
+__global__ void __launch_bounds__(NT)
+k_sor_tma(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtensorMap tr,
+          const __grid_constant__ CUtensorMap tf, Geo<float> g, float* __restrict__ dout, int zero_arg,
+          Scalars* __restrict__ sc) {
+    using TT = TmaTile<BY, BZ>;
+    constexpr int BX = TT::BX, DXW = TT::DXW, FXW = TT::FXW, DY = TT::DY, RY = TT::RY, RZ = TT::RZ;
+    extern __shared__ __align__(128) unsigned char sm[];
+    float(*sD)[DY][DXW] = reinterpret_cast<float(*)[DY][DXW]>(sm);
+    float(*sR)[RY][DXW] = reinterpret_cast<float(*)[RY][DXW]>(sm + TT::OFF_R);
+    uint8_t(*sF)[RY][FXW] = reinterpret_cast<uint8_t(*)[RY][FXW]>(sm + TT::OFF_F);
+    float(*sCN)[64] = reinterpret_cast<float(*)[64]>(sm + TT::OFF_CN);
+    float* sCT = reinterpret_cast<float*>(sm + TT::OFF_CT);
+    float* sCB = sCT + RZ;
+    if (sc->done) return;
+    const Dom& d = g.d;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = NT / 32;
+    const int i0 = 1 + blockIdx.x * BX, j0 = 1 + blockIdx.y * BY, k0 = 1 + blockIdx.z * BZ;
+    const int xd = blockIdx.x * BX;           // padded column of i0 - 4
+    const int xf = xd & ~15, off = xd - xf;
+    const bool zero_start = zero_arg == 1 || (zero_arg == 2 && sc->zflag);
+    const uint32_t bar = smem_u32(sm + TT::OFF_BAR);
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_fence_init();
+        mbar_expect_tx(bar, TT::BYTES_R + TT::BYTES_F + (zero_start ? 0u : TT::BYTES_D));
+        if (!zero_start) tma_load_3d(smem_u32(sD), &td, xd, j0 - 2, k0 - 2, bar);
+        tma_load_3d(smem_u32(sR), &tr, xd, j0 - 1, k0 - 1, bar);
+        tma_load_3d(smem_u32(sF), &tf, xf, j0 - 1, k0 - 1, bar);
+    }
+    // per-plane coefficients and the cn1 table while the copies fly
+    for (int q = tid; q < RZ * 64; q += NT) {
+        const int kk = q >> 6, m = q & 63;
+        const int k = min(max(k0 - 1 + kk, 0), d.nz + 1);
+        const float ct = g.cT[k], cb = g.cB[k];
+        float ae = (m & F_E) ? g.cx : 0.f;
+        float aw = (m & F_W) ? g.cx : 0.f;
+        float an = (m & F_N) ? g.cy : 0.f;
+        float as = (m & F_S) ? g.cy : 0.f;
+        float at = (m & F_T) ? ct : 0.f;
+        float ab = (m & F_B) ? cb : 0.f;
+        const float sum = ae + aw + an + as + at + ab;
+        sCN[kk][m] = sum > 0.f ? 1.f / sum : 0.f;
+        if (m == 0) {
+            sCT[kk] = ct;
+            sCB[kk] = cb;
+        }
+    }
+    if (zero_start) {
+        float* p = &sD[0][0][0];
+        for (int q = tid; q < DXW * DY * TT::DZ; q += NT) p[q] = 0.f;
+    }
+    __syncthreads();
+    bool ok = false;
+    const uint64_t t0 = global_ns();
+    while (!(ok = mbar_try_wait(bar, 0)))
+        if (global_ns() - t0 > 1000000000ull) break;
+    if (!__syncthreads_and(ok)) {
+        if (tid == 0) atomicExch(&sc->timeout, 1);
+        const uint64_t t1 = global_ns();     // give copies still in flight a bounded chance to land
+        while (!mbar_try_wait(bar, 0))
+            if (global_ns() - t1 > 1000000000ull) break;
+        return;
+    }
+    const float omega = g.omega, cx = g.cx, cy = g.cy;
+    auto relax = [&](int x, int y, int z, int kz, uint8_t f, float rhs) {
+        float ae = (f & F_E) ? cx : 0.f;
+        float aw = (f & F_W) ? cx : 0.f;
+        float an = (f & F_N) ? cy : 0.f;
+        float as = (f & F_S) ? cy : 0.f;
+        float at = (f & F_T) ? sCT[kz] : 0.f;
+        float ab = (f & F_B) ? sCB[kz] : 0.f;
+        const float cn1 = sCN[kz][f & 63];
+        float s = 0.f;
+        s += ae * sD[z][y][x + 1];
+        s += aw * sD[z][y][x - 1];
+        s += an * sD[z][y + 1][x];
+        s += as * sD[z][y - 1][x];
+        s += at * sD[z + 1][y][x];
+        s += ab * sD[z - 1][y][x];
+        float own = sD[z][y][x];
+        float reltmp = omega * (cn1 * (s - rhs) - own);
+        sD[z][y][x] = own + reltmp;
+    };
+    const int half = lane >> 4, m = lane & 15;
+    // red (i+j+k odd) on the block + 1 ring (i0-1 .. i0+28): 15 per row, two rows per warp pass
+    for (int p = warp; 2 * p < RY * RZ; p += NW) {
+        const int rw = 2 * p + half;
+        if (rw < RY * RZ && m < (BX + 2) / 2) {
+            const int jj = rw % RY, kk = rw / RY;
+            const int ii = 2 * m + ((i0 + (j0 - 1 + jj) + (k0 - 1 + kk)) & 1);   // i = i0 - 1 + ii
+            const uint8_t f = sF[kk][jj][ii + 3 + off];
+            if (f & F_UNK) relax(ii + 3, jj + 1, kk + 1, kk, f, sR[kk][jj][ii + 3]);
+        }
+    }
+    __syncthreads();
+    // black (i+j+k even) on the block (i0 .. i0+27): 14 per row
+    for (int p = warp; 2 * p < BY * BZ; p += NW) {
+        const int rw = 2 * p + half;
+        if (rw < BY * BZ && m < BX / 2) {
+            const int jj = rw % BY, kk = rw / BY;
+            const int ii = 2 * m + ((i0 + (j0 + jj) + (k0 + kk)) & 1);           // i = i0 + ii
+            const uint8_t f = sF[kk + 1][jj + 1][ii + 4 + off];
+            if (f & F_UNK) relax(ii + 4, jj + 2, kk + 2, kk + 1, f, sR[kk + 1][jj + 1][ii + 4]);
+        }
+    }
+    __syncthreads();
+    const int i = i0 + lane;
+    for (int rw = warp; rw < BY * BZ; rw += NW) {
+        const int jj = rw % BY, kk = rw / BY;
+        const int j = j0 + jj, k = k0 + kk;
+        if (lane < BX && i <= d.nx && j <= d.ny && k <= d.nz && (sF[kk + 1][jj + 1][lane + 4 + off] & F_UNK))
+            dout[(k * d.py + j) * d.px + i + OX] = sD[kk + 2][jj + 2][lane + 4];
+    }
+}
+
+template <int BY, int BZ, int NT>
+cudaError_t allow_tma() {
+    return cudaFuncSetAttribute(k_sor_tma<BY, BZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)TmaTile<BY, BZ>::SMEM);
+}
+
+template <int BY, int BZ, int NT>
+void launch_tma_cfg(const Geo<float>& g, const TmaMaps& m, int in, float* dout, int zero, Scalars* sc,
+                    cudaStream_t s) {
+    const Dom& d = g.d;
+    dim3 grid((d.nx + 27) / 28, (d.ny + BY - 1) / BY, (d.nz + BZ - 1) / BZ);
+    k_sor_tma<BY, BZ, NT><<<grid, NT, TmaTile<BY, BZ>::SMEM, s>>>(m.d[in], m.r, m.f, g, dout, zero, sc);
+}
+
+using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
+
+EncodeFn encoder() {
+    static EncodeFn fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeFn)p;
+    }
+    return fn;
+}
+
+bool encode3d(CUtensorMap* map, CUtensorMapDataType type, size_t es, void* base, const Dom& d, int bx, int by,
+              int bz) {
+    EncodeFn fn = encoder();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)d.px, (cuuint64_t)d.py, (cuuint64_t)(d.nz + 2)};
+    cuuint64_t strides[2] = {(cuuint64_t)d.px * es, (cuuint64_t)d.px * d.py * es};
+    cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return fn(map, type, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+// (BY, BZ, threads) of the TMA tiles, in the order of their tile indices
+const int kTmaCfg[kNumTmaTiles][3] = {{8, 8, 256}, {12, 12, 512}, {16, 12, 512}, {16, 16, 512}};
+
+bool tma_supported(const Dom& d) { return !d.perx && !d.pery && !d.perz; }
+
+cudaError_t tma_prepare() {
+    cudaError_t e = cudaSuccess, x;
+    if ((x = allow_tma<8, 8, 256>()) != cudaSuccess) e = x;
+    if ((x = allow_tma<12, 12, 512>()) != cudaSuccess) e = x;
+    if ((x = allow_tma<16, 12, 512>()) != cudaSuccess) e = x;
+    if ((x = allow_tma<16, 16, 512>()) != cudaSuccess) e = x;
+    return e;
+}
+
+bool tma_encode(const Dom& d, float* dl0, float* dl1, float* rr, uint8_t* flags, TmaMaps* maps) {
+    for (int c = 0; c < kNumTmaTiles; ++c) {
+        const int by = kTmaCfg[c][0], bz = kTmaCfg[c][1];
+        TmaMaps& m = maps[c];
+        if (!encode3d(&m.d[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, dl0, d, 36, by + 4, bz + 4)) return false;
+        if (!encode3d(&m.d[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, dl1, d, 36, by + 4, bz + 4)) return false;
+        if (!encode3d(&m.r, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, rr, d, 36, by + 2, bz + 2)) return false;
+        if (!encode3d(&m.f, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, flags, d, 48, by + 2, bz + 2)) return false;
+    }
+    return true;
+}
+
+int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, int cfg, int in, float* dout, int zero, Scalars* sc,
+                   cudaStream_t s) {
+    const TmaMaps& m = maps[cfg];
+    switch (cfg) {
+        case 0: launch_tma_cfg<8, 8, 256>(g, m, in, dout, zero, sc, s); break;
+        case 1: launch_tma_cfg<12, 12, 512>(g, m, in, dout, zero, sc, s); break;
+        case 2: launch_tma_cfg<16, 12, 512>(g, m, in, dout, zero, sc, s); break;
+        default: launch_tma_cfg<16, 16, 512>(g, m, in, dout, zero, sc, s); break;
+    }
+    return 1;
+}
+
+}  // namespace les
