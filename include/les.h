@@ -210,14 +210,15 @@ int les_set_graph(les_handle h, int32_t enable);
  * kernels; tile = 0..LES_SOR_NTILES-1 runs a fused red-black kernel: tiles
  * whose les_sor_tile tz is 0 are column tiles marching kc planes per CTA
  * (kc <= 0: the whole column), the others are tx x ty x tz blocks (kc
- * ignored); tiles 17-20 are 28 x ty x tz blocks loaded by the tensor-memory
- * accelerator (FP32 grids without periodic axes only, else LES_EINVAL).
+ * ignored); tiles 17-24 are 28 x ty x tz blocks loaded by the tensor-memory
+ * accelerator, 21-24 in persistent CTAs that prefetch their next block (FP32
+ * grids without periodic axes only, else LES_EINVAL).
  * Every choice computes the same iterate.
  * les_autotune_sor times each tile shape with a few k-chunk lengths on this
  * handle's grid (sweeps per candidate), keeps the fastest and reports it;
  * the field state is saved and restored around the trial sweeps.
  */
-#define LES_SOR_NTILES 21
+#define LES_SOR_NTILES 25
 int les_set_sor_config(les_handle h, int32_t tile, int32_t kc);
 int les_get_sor_config(les_handle h, int32_t* tile, int32_t* kc);
 int les_sor_tile(int32_t tile, int32_t* tx, int32_t* ty, int32_t* tz);

@@ -117,6 +117,7 @@ struct les_s {
     bool last_graph = false;              // the last les_step ran as graphs
     TmaMaps tma[kNumTmaTiles];            // tensor maps of the TMA sweep (FP32, no periodic axis)
     bool tma_ok = false;
+    float* cn1tab = nullptr;              // cn1 over (plane, open-face mask) for the pipelined sweep
     // phase timing
     bool timing = false;
     cudaEvent_t ev[8] = {};
@@ -273,8 +274,8 @@ int run_sweeps(les_s* h, const Geo<T>& g, int n, int zero, long long& launched, 
         const int in = h->dcur, out = 1 - h->dcur;
         if constexpr (std::is_same<T, float>::value) {
             if (h->sor.tile >= kFirstTmaTile) {
-                launched += launch_sor_tma(g, h->tma, h->sor.tile - kFirstTmaTile, in, (float*)h->dl[out],
-                                           s == 0 ? zero : 0, h->sc, st);
+                launched += launch_sor_tma(g, h->tma, h->cn1tab, h->sor.tile - kFirstTmaTile, in,
+                                           (float*)h->dl[out], s == 0 ? zero : 0, h->sc, st);
                 h->dcur = out;
                 continue;
             }
@@ -757,6 +758,10 @@ int create_impl(les_s* h, const uint8_t* solid) {
     if (h->prec == LES_FP32 && tma_supported(d)) {
         CK(tma_prepare());
         h->tma_ok = tma_encode(d, (float*)h->dl[0], (float*)h->dl[1], (float*)h->rr, h->flags, h->tma);
+        if ((rc = dalloc(h, (void**)&h->cn1tab, (size_t)(G.nz + 2) * 64 * sizeof(float)))) return rc;
+        launch_cn1_table(geo<float>(h), h->cn1tab, h->stream);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(h->stream));
     }
     CK(cudaStreamSynchronize(h->stream));
     return LES_OK;

@@ -150,14 +150,15 @@ template <typename T> cudaError_t sor_prepare();
 // TMA variant (les_sor_tma.cu): FP32, no periodic axis; tile indices
 // kFirstTmaTile .. kFirstTmaTile + kNumTmaTiles - 1
 constexpr int kFirstTmaTile = 17;
-constexpr int kNumTmaTiles = 4;
+constexpr int kNumTmaTiles = 8;
 extern const int kTmaCfg[kNumTmaTiles][3];
 struct TmaMaps { CUtensorMap d[2], r, f; };
 bool tma_supported(const Dom& d);
 cudaError_t tma_prepare();
 bool tma_encode(const Dom& d, float* dl0, float* dl1, float* rr, uint8_t* flags, TmaMaps* maps);
-int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, int cfg, int in, float* dout, int zero, Scalars* sc,
-                   cudaStream_t s);
+int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, const float* cn1tab, int cfg, int in, float* dout,
+                   int zero, Scalars* sc, cudaStream_t s);
+int launch_cn1_table(const Geo<float>& g, float* tab, cudaStream_t s);
 
 int max_reduce_blocks(const Dom& d);
 

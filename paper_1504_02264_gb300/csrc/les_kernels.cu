@@ -626,6 +626,7 @@ int launch_accum(const Geo<T>& g, double* ph, const T* dl, const Scalars* sc, in
 // Grid-stride reductions use at most kReduceBlocks blocks, so the last-block
 // completion counter sees few atomics.
 constexpr int kReduceBlocks = 1024;
+constexpr int kEstChunk = 16;      // planes per thread in the estimate kernel
 int reduce_blocks(const Dom& d) {
     long long n = (long long)d.nx * d.ny * d.nz;
     long long b = (n + 255) / 256;
@@ -729,32 +730,36 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_sor_est(Geo<T> g, const T* dl, const T* r, Reduce red, CondArgs ca) {
     const Dom& d = g.d;
     if (red.sc->done) return;      // uniform over the grid
-    const int n = d.nx * d.ny * d.nz;
-    double x[1] = {0.0};
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-        int i, j, k;
-        cell_of(d, q, i, j, k);
-        long long c = d.at(i, j, k);
-        const uint8_t f = g.flags[c];
-        if (!(f & F_UNK)) continue;
+    // a (32 x 8) column tile marching over a chunk of kEstChunk planes
+    const int i = blockIdx.x * 32 + threadIdx.x + 1;
+    const int j = blockIdx.y * 8 + threadIdx.y + 1;
+    const int kb = blockIdx.z * kEstChunk + 1, ke = min(kb + kEstChunk, d.nz + 1);
+    T acc = T(0);
+    if (i <= d.nx && j <= d.ny) {
         Poisson<T> Q{g};
-        T ae, aw, an, as, at, ab;
-        Q.coefs(f, k, g.cx, g.cy, g.cT, g.cB, ae, aw, an, as, at, ab);
-        long long e, w, nn, s_, t, b;
-        Q.nbr(i, j, k, e, w, nn, s_, t, b);
-        const T dc = dl[c];
-        T s = T(0);
-        s += ae * (dl[e] - dc);
-        s += aw * (dl[w] - dc);
-        s += an * (dl[nn] - dc);
-        s += as * (dl[s_] - dc);
-        s += at * (dl[t] - dc);
-        s += ab * (dl[b] - dc);
-        const T res = r[c] - s;
-        x[0] += (double)res * (double)res;
+        for (int k = kb; k < ke; ++k) {
+            const long long c = d.at(i, j, k);
+            const uint8_t f = g.flags[c];
+            if (!(f & F_UNK)) continue;
+            T ae, aw, an, as, at, ab;
+            Q.coefs(f, k, g.cx, g.cy, g.cT, g.cB, ae, aw, an, as, at, ab);
+            long long e, w, nn, s_, t, b;
+            Q.nbr(i, j, k, e, w, nn, s_, t, b);
+            const T dc = dl[c];
+            T s = T(0);
+            s += ae * (dl[e] - dc);
+            s += aw * (dl[w] - dc);
+            s += an * (dl[nn] - dc);
+            s += as * (dl[s_] - dc);
+            s += at * (dl[t] - dc);
+            s += ab * (dl[b] - dc);
+            const T res = r[c] - s;
+            acc += res * res;
+        }
     }
+    double x[1] = {(double)acc};
     if (grid_sum<1>(x, red)) {
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
             Scalars* sc = red.sc;
             const double rhs2 = sc->rhs2;
             const double est = rhs2 == 0.0 ? sqrt(x[0]) : sqrt(x[0] / rhs2);
@@ -771,7 +776,9 @@ __global__ void __launch_bounds__(256) k_sor_est(Geo<T> g, const T* dl, const T*
 
 template <typename T>
 int launch_sor_est(const Geo<T>& g, const T* dl, const T* r, const Reduce& red, CondArgs ca, cudaStream_t s) {
-    k_sor_est<T><<<reduce_blocks(g.d), 256, 0, s>>>(g, dl, r, red, ca);
+    const Dom& d = g.d;
+    dim3 grid((d.nx + 31) / 32, (d.ny + 7) / 8, (d.nz + kEstChunk - 1) / kEstChunk);
+    k_sor_est<T><<<grid, dim3(32, 8), 0, s>>>(g, dl, r, red, ca);
     return 1;
 }
 

@@ -194,6 +194,186 @@ k_sor_tma(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtens
     }
 }
 
+// Persistent, double-buffered variant: each CTA walks tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ... and issues the copies of its next tile into the
+// other shared-memory stage before computing the current one, so the copy
+// latency hides behind compute.  cn1 and the per-plane coefficients come
+// from a table over (plane, open-face mask) built once per handle with the
+// same arithmetic as the scalar update.
+template <int BY, int BZ>
+struct PipeTile {
+    using TT = TmaTile<BY, BZ>;
+    static constexpr uint32_t STAGE = align_up(TT::OFF_CN, 128);          // d, r, f of one tile
+    static constexpr uint32_t OFF_CN = 2 * STAGE;
+    static constexpr uint32_t OFF_CT = OFF_CN + TT::RZ * 64 * 4;
+    static constexpr uint32_t OFF_BAR = align_up(OFF_CT + 2 * TT::RZ * 4, 8);
+    static constexpr uint32_t SMEM = OFF_BAR + 16;
+};
+
+template <int BY, int BZ, int NT>
+__global__ void __launch_bounds__(NT)
+k_sor_pipe(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtensorMap tr,
+           const __grid_constant__ CUtensorMap tf, Geo<float> g, const float* __restrict__ cn1tab,
+           float* __restrict__ dout, int zero_arg, Scalars* __restrict__ sc) {
+    using TT = TmaTile<BY, BZ>;
+    using PT = PipeTile<BY, BZ>;
+    constexpr int BX = TT::BX, DXW = TT::DXW, FXW = TT::FXW, DY = TT::DY, DZ = TT::DZ, RY = TT::RY, RZ = TT::RZ;
+    constexpr int NW = NT / 32;
+    extern __shared__ __align__(128) unsigned char sm[];
+    float(*sCN)[64] = reinterpret_cast<float(*)[64]>(sm + PT::OFF_CN);
+    float* sCT = reinterpret_cast<float*>(sm + PT::OFF_CT);
+    float* sCB = sCT + RZ;
+    if (sc->done) return;
+    const Dom& d = g.d;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tx = (d.nx + BX - 1) / BX, ty = (d.ny + BY - 1) / BY, tz = (d.nz + BZ - 1) / BZ;
+    const int ntiles = tx * ty * tz;
+    const bool zero_start = zero_arg == 1 || (zero_arg == 2 && sc->zflag);
+    const uint32_t bar0 = smem_u32(sm + PT::OFF_BAR);
+    auto origin = [&](int t, int& i0, int& j0, int& k0) {
+        const int bx = t % tx, r_ = t / tx, by = r_ % ty, bz = r_ / ty;
+        i0 = 1 + bx * BX;
+        j0 = 1 + by * BY;
+        k0 = 1 + bz * BZ;
+    };
+    auto issue = [&](int t, int st) {     // thread 0 only
+        int i0, j0, k0;
+        origin(t, i0, j0, k0);
+        const int xd = i0 - 1, xf = xd & ~15;      // padded column of i0 - 4 (= 28 bx)
+        unsigned char* base = sm + st * PT::STAGE;
+        const uint32_t bar = bar0 + 8 * st;
+        mbar_expect_tx(bar, TT::BYTES_R + TT::BYTES_F + (zero_start ? 0u : TT::BYTES_D));
+        if (!zero_start) tma_load_3d(smem_u32(base), &td, xd, j0 - 2, k0 - 2, bar);
+        tma_load_3d(smem_u32(base + TT::OFF_R), &tr, xd, j0 - 1, k0 - 1, bar);
+        tma_load_3d(smem_u32(base + TT::OFF_F), &tf, xf, j0 - 1, k0 - 1, bar);
+    };
+    if (tid == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar0 + 8, 1);
+        mbar_fence_init();
+        if (blockIdx.x < ntiles) issue(blockIdx.x, 0);
+    }
+    __syncthreads();
+    uint32_t ph0 = 0u, ph1 = 0u;     // phase parity of each stage's barrier
+    int st = 0;
+    const float omega = g.omega, cx = g.cx, cy = g.cy;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int tn = t + gridDim.x;
+        if (tid == 0 && tn < ntiles) issue(tn, st ^ 1);
+        int i0, j0, k0;
+        origin(t, i0, j0, k0);
+        const int off = (i0 - 1) - ((i0 - 1) & ~15);  // flag tile offset, as in issue()
+        float(*sD)[DY][DXW] = reinterpret_cast<float(*)[DY][DXW]>(sm + st * PT::STAGE);
+        float(*sR)[RY][DXW] = reinterpret_cast<float(*)[RY][DXW]>(sm + st * PT::STAGE + TT::OFF_R);
+        uint8_t(*sF)[RY][FXW] = reinterpret_cast<uint8_t(*)[RY][FXW]>(sm + st * PT::STAGE + TT::OFF_F);
+        for (int q = tid; q < RZ * 64; q += NT) {
+            const int kk = q >> 6, m = q & 63;
+            const int k = min(max(k0 - 1 + kk, 0), d.nz + 1);
+            sCN[kk][m] = cn1tab[k * 64 + m];
+            if (m == 0) {
+                sCT[kk] = g.cT[k];
+                sCB[kk] = g.cB[k];
+            }
+        }
+        if (zero_start) {
+            float* p = &sD[0][0][0];
+            for (int q = tid; q < DXW * DY * DZ; q += NT) p[q] = 0.f;
+        }
+        bool ok = false;
+        const uint64_t t0 = global_ns();
+        const uint32_t par = st ? ph1 : ph0;
+        while (!(ok = mbar_try_wait(bar0 + 8 * st, par)))
+            if (global_ns() - t0 > 1000000000ull) break;
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) atomicExch(&sc->timeout, 1);
+            for (int s2 = 0; s2 < 2; ++s2) {          // bounded wait for copies still in flight
+                const uint64_t t1 = global_ns();
+                while (!mbar_try_wait(bar0 + 8 * s2, s2 ? ph1 : ph0))
+                    if (global_ns() - t1 > 1000000000ull) break;
+            }
+            return;
+        }
+        if (st) ph1 ^= 1u;
+        else ph0 ^= 1u;
+        auto relax = [&](int x, int y, int z, int kz, uint8_t f, float rhs) {
+            float ae = (f & F_E) ? cx : 0.f;
+            float aw = (f & F_W) ? cx : 0.f;
+            float an = (f & F_N) ? cy : 0.f;
+            float as = (f & F_S) ? cy : 0.f;
+            float at = (f & F_T) ? sCT[kz] : 0.f;
+            float ab = (f & F_B) ? sCB[kz] : 0.f;
+            const float cn1 = sCN[kz][f & 63];
+            float s = 0.f;
+            s += ae * sD[z][y][x + 1];
+            s += aw * sD[z][y][x - 1];
+            s += an * sD[z][y + 1][x];
+            s += as * sD[z][y - 1][x];
+            s += at * sD[z + 1][y][x];
+            s += ab * sD[z - 1][y][x];
+            float own = sD[z][y][x];
+            float reltmp = omega * (cn1 * (s - rhs) - own);
+            sD[z][y][x] = own + reltmp;
+        };
+        const int half = lane >> 4, m = lane & 15;
+        for (int p = warp; 2 * p < RY * RZ; p += NW) {
+            const int rw = 2 * p + half;
+            if (rw < RY * RZ && m < (BX + 2) / 2) {
+                const int jj = rw % RY, kk = rw / RY;
+                const int ii = 2 * m + ((i0 + (j0 - 1 + jj) + (k0 - 1 + kk)) & 1);
+                const uint8_t f = sF[kk][jj][ii + 3 + off];
+                if (f & F_UNK) relax(ii + 3, jj + 1, kk + 1, kk, f, sR[kk][jj][ii + 3]);
+            }
+        }
+        __syncthreads();
+        for (int p = warp; 2 * p < BY * BZ; p += NW) {
+            const int rw = 2 * p + half;
+            if (rw < BY * BZ && m < BX / 2) {
+                const int jj = rw % BY, kk = rw / BY;
+                const int ii = 2 * m + ((i0 + (j0 + jj) + (k0 + kk)) & 1);
+                const uint8_t f = sF[kk + 1][jj + 1][ii + 4 + off];
+                if (f & F_UNK) relax(ii + 4, jj + 2, kk + 2, kk + 1, f, sR[kk + 1][jj + 1][ii + 4]);
+            }
+        }
+        __syncthreads();
+        const int i = i0 + lane;
+        for (int rw = warp; rw < BY * BZ; rw += NW) {
+            const int jj = rw % BY, kk = rw / BY;
+            const int j = j0 + jj, k = k0 + kk;
+            if (lane < BX && i <= d.nx && j <= d.ny && k <= d.nz && (sF[kk + 1][jj + 1][lane + 4 + off] & F_UNK))
+                dout[(k * d.py + j) * d.px + i + OX] = sD[kk + 2][jj + 2][lane + 4];
+        }
+        __syncthreads();      // this stage is reloaded two tiles later
+        st ^= 1;
+    }
+}
+
+template <int BY, int BZ, int NT>
+cudaError_t allow_pipe() {
+    return cudaFuncSetAttribute(k_sor_pipe<BY, BZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)PipeTile<BY, BZ>::SMEM);
+}
+
+template <int BY, int BZ, int NT>
+int pipe_blocks() {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sor_pipe<BY, BZ, NT>, NT, PipeTile<BY, BZ>::SMEM);
+    return sms * (per > 0 ? per : 1);
+}
+
+int g_pipe_blocks[4] = {0, 0, 0, 0};    // resident CTAs of each persistent config (set at prepare)
+
+template <int BY, int BZ, int NT>
+void launch_pipe_cfg(const Geo<float>& g, const TmaMaps& m, const float* cn1tab, int in, float* dout, int zero,
+                     Scalars* sc, cudaStream_t s, int slot) {
+    const Dom& d = g.d;
+    const int blocks = g_pipe_blocks[slot] > 0 ? g_pipe_blocks[slot] : 152;
+    const int ntiles = ((d.nx + 27) / 28) * ((d.ny + BY - 1) / BY) * ((d.nz + BZ - 1) / BZ);
+    const int grid = ntiles < blocks ? ntiles : blocks;
+    k_sor_pipe<BY, BZ, NT><<<grid, NT, PipeTile<BY, BZ>::SMEM, s>>>(m.d[in], m.r, m.f, g, cn1tab, dout, zero, sc);
+}
+
 template <int BY, int BZ, int NT>
 cudaError_t allow_tma() {
     return cudaFuncSetAttribute(k_sor_tma<BY, BZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -239,7 +419,8 @@ bool encode3d(CUtensorMap* map, CUtensorMapDataType type, size_t es, void* base,
 }  // namespace
 
 // (BY, BZ, threads) of the TMA tiles, in the order of their tile indices
-const int kTmaCfg[kNumTmaTiles][3] = {{8, 8, 256}, {12, 12, 512}, {16, 12, 512}, {16, 16, 512}};
+const int kTmaCfg[kNumTmaTiles][3] = {{8, 8, 256}, {12, 12, 512}, {16, 12, 512}, {16, 16, 512},
+                                      {8, 8, 256}, {8, 8, 512}, {16, 8, 512}, {12, 12, 512}};
 
 bool tma_supported(const Dom& d) { return !d.perx && !d.pery && !d.perz; }
 
@@ -249,6 +430,14 @@ cudaError_t tma_prepare() {
     if ((x = allow_tma<12, 12, 512>()) != cudaSuccess) e = x;
     if ((x = allow_tma<16, 12, 512>()) != cudaSuccess) e = x;
     if ((x = allow_tma<16, 16, 512>()) != cudaSuccess) e = x;
+    if ((x = allow_pipe<8, 8, 256>()) != cudaSuccess) e = x;
+    if ((x = allow_pipe<8, 8, 512>()) != cudaSuccess) e = x;
+    if ((x = allow_pipe<16, 8, 512>()) != cudaSuccess) e = x;
+    if ((x = allow_pipe<12, 12, 512>()) != cudaSuccess) e = x;
+    g_pipe_blocks[0] = pipe_blocks<8, 8, 256>();
+    g_pipe_blocks[1] = pipe_blocks<8, 8, 512>();
+    g_pipe_blocks[2] = pipe_blocks<16, 8, 512>();
+    g_pipe_blocks[3] = pipe_blocks<12, 12, 512>();
     return e;
 }
 
@@ -264,15 +453,40 @@ bool tma_encode(const Dom& d, float* dl0, float* dl1, float* rr, uint8_t* flags,
     return true;
 }
 
-int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, int cfg, int in, float* dout, int zero, Scalars* sc,
-                   cudaStream_t s) {
+int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, const float* cn1tab, int cfg, int in, float* dout,
+                   int zero, Scalars* sc, cudaStream_t s) {
     const TmaMaps& m = maps[cfg];
     switch (cfg) {
         case 0: launch_tma_cfg<8, 8, 256>(g, m, in, dout, zero, sc, s); break;
         case 1: launch_tma_cfg<12, 12, 512>(g, m, in, dout, zero, sc, s); break;
         case 2: launch_tma_cfg<16, 12, 512>(g, m, in, dout, zero, sc, s); break;
-        default: launch_tma_cfg<16, 16, 512>(g, m, in, dout, zero, sc, s); break;
+        case 3: launch_tma_cfg<16, 16, 512>(g, m, in, dout, zero, sc, s); break;
+        case 4: launch_pipe_cfg<8, 8, 256>(g, m, cn1tab, in, dout, zero, sc, s, 0); break;
+        case 5: launch_pipe_cfg<8, 8, 512>(g, m, cn1tab, in, dout, zero, sc, s, 1); break;
+        case 6: launch_pipe_cfg<16, 8, 512>(g, m, cn1tab, in, dout, zero, sc, s, 2); break;
+        default: launch_pipe_cfg<12, 12, 512>(g, m, cn1tab, in, dout, zero, sc, s, 3); break;
     }
+    return 1;
+}
+
+// cn1 over (plane, open-face mask): the same sum and division as the update
+__global__ void k_cn1_table(Geo<float> g, float* tab) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (g.d.nz + 2) * 64) return;
+    const int k = q >> 6, m = q & 63;
+    float ae = (m & F_E) ? g.cx : 0.f;
+    float aw = (m & F_W) ? g.cx : 0.f;
+    float an = (m & F_N) ? g.cy : 0.f;
+    float as = (m & F_S) ? g.cy : 0.f;
+    float at = (m & F_T) ? g.cT[k] : 0.f;
+    float ab = (m & F_B) ? g.cB[k] : 0.f;
+    const float sum = ae + aw + an + as + at + ab;
+    tab[q] = sum > 0.f ? 1.f / sum : 0.f;
+}
+
+int launch_cn1_table(const Geo<float>& g, float* tab, cudaStream_t s) {
+    const int n = (g.d.nz + 2) * 64;
+    k_cn1_table<<<(n + 255) / 256, 256, 0, s>>>(g, tab);
     return 1;
 }
 

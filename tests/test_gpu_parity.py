@@ -243,7 +243,7 @@ def test_fused_sor_matches_two_pass(prec, case):
     ref.step(2)
     want = ref.fields()
     tol = 0.0 if prec == "fp64" else 1e-6
-    tiles = list(range(17)) + (list(range(17, 21)) if (case == "city" and prec == "fp32") else [])
+    tiles = list(range(17)) + (list(range(17, 25)) if (case == "city" and prec == "fp32") else [])
     for tile in tiles:
         for kc in ((0, 3, 5) if tile < 6 else (0,)):
             d = les.Domain(sc, precision=p)
@@ -260,7 +260,7 @@ def test_autotune_picks_a_valid_config():
     d = les.Domain(sc, precision=les.LES_FP32)
     d.step(1)
     (tile, kc), ms = d.autotune_sor(sweeps=5)
-    assert 0 <= tile < 21 and ms > 0
+    assert 0 <= tile < 25 and ms > 0
     before = d.fields()
     d2 = les.Domain(sc, precision=les.LES_FP32)
     d2.step(1)
