@@ -164,7 +164,15 @@ int les_pressure_solve(les_handle h, const void* rhs, les_stats_t* stats);
 #define LES_AUX_FU 5         /* Adams-Bashforth history F_u (u shape) */
 #define LES_AUX_FV 6
 #define LES_AUX_FW 7
+#define LES_AUX_R0 8         /* initial residual rhs - mean - A p_prev of the last solve (recording on) */
+#define LES_AUX_DELTA 9      /* correction p_solved - p_prev of the last solve, before the gauge (recording on) */
+#define LES_AUX_MASK 10      /* 1 on Poisson unknowns (fluid cells with an open face), else 0 */
 int les_get_aux(les_handle h, int32_t which, void* out);
+
+/* les_set_record: keep the initial residual and the total correction of every
+ * solve (LES_AUX_R0 / LES_AUX_DELTA), the training pairs of the warm-start
+ * network.  Costs two device copies per solve while on. */
+int les_set_record(les_handle h, int32_t enable);
 
 /*
  * Checkpoint / restart: the full state (velocities, p, AB2 history, step
@@ -261,6 +269,44 @@ int les_autotune_sor(les_handle h, int32_t sweeps, double* best_ms_per_sweep);
 #define LES_NOALLOC_MAX_CELLS 2147483647LL
 int les_residual_noalloc(const les_grid_t* grid, const void* d_p, const void* d_rhs, const uint8_t* d_solid,
                          const double* d_dz, double* d_out, void* stream);
+
+/*
+ * Learned SOR warm start (no counterpart in the paper, which warm-starts SOR
+ * from the previous step's pressure).  A 4-level 3-D U-Net (3x3x3 convs,
+ * 16/32/64/128 channels, bias-free, ReLU, 2x2x2 mean pooling, nearest
+ * upsampling, additive skips, 1x1x1 head) maps the solve's initial residual
+ * r0 = rhs - mean - A p_prev (scaled to unit RMS) and the unknown mask to a
+ * correction direction q.  The solver then takes p0 = p_prev + alpha q with
+ * alpha minimising ||r0 - alpha A q|| in FP64 (so p0 is never worse than
+ * p_prev) and runs the same red-black SOR to the same tolerance: plain SOR
+ * stays the stop test.  Activations are BF16, accumulation FP32, on the
+ * tensor cores (mma.sync m16n8k16).  Training runs on the GPU with the
+ * network's own backward kernels and Adam.
+ *
+ * Device arrays of the training / inference calls are dense float [b][nz][ny][nx]
+ * (b = batch index): d_r residuals, d_mask 1/0 unknown masks, d_t target
+ * corrections; the loss is the batch mean of mean_mask (y - t / rms_mask(t))^2.
+ * les_net_gradient writes the flat FP32 gradient (les_net_num_params floats:
+ * conv0..conv6 as [27][Cout][Cin], tap = (dz*3+dy)*3+dx, then the 16 head
+ * weights) without updating; les_net_train_step applies Adam (beta 0.9/0.999).
+ */
+typedef struct les_net_s* les_net;
+#define LES_WARM_PREV 0      /* p0 = p from the previous step (the paper's scheme) */
+#define LES_WARM_NET 1       /* p0 = p_prev + alpha * network(r0) */
+int les_net_create(uint64_t seed, void* stream, les_net* out);
+void les_net_destroy(les_net n);
+const char* les_net_last_error(les_net n);
+int les_net_num_params(les_net n, int64_t* count);
+int les_net_get_params(les_net n, float* host);
+int les_net_set_params(les_net n, const float* host);
+int les_net_forward(les_net n, const float* d_r, const float* d_mask, float* d_y, int32_t nx, int32_t ny, int32_t nz);
+int les_net_gradient(les_net n, const float* d_r, const float* d_mask, const float* d_t, int32_t batch, int32_t nx,
+                     int32_t ny, int32_t nz, float* d_grad, double* loss);
+int les_net_train_step(les_net n, const float* d_r, const float* d_mask, const float* d_t, int32_t batch, int32_t nx,
+                       int32_t ny, int32_t nz, float lr, double* loss);
+/* les_set_warmstart: LES_WARM_NET needs an FP32 grid; the handle keeps the
+ * network pointer (the caller keeps it alive). */
+int les_set_warmstart(les_handle h, int32_t mode, les_net net);
 
 /* Bracket a region for a profiler started with capture off
  * (cudaProfilerStart when start != 0, cudaProfilerStop otherwise). */

@@ -118,6 +118,16 @@ struct les_s {
     TmaMaps tma[kNumTmaTiles];            // tensor maps of the TMA sweep (FP32, no periodic axis)
     bool tma_ok = false;
     float* cn1tab = nullptr;              // cn1 over (plane, open-face mask) for the pipelined sweep
+    // learned warm start and training-pair recording
+    int warm = LES_WARM_PREV;
+    les_net_s* net = nullptr;
+    float* pred = nullptr;                // dense (nz, ny, nx) predicted correction
+    double* warm_scal = nullptr;          // [0] input scale, [1] line-search step
+    double n_unk = 0.0;                   // number of Poisson unknowns
+    bool record = false;
+    double* rec_p0 = nullptr;             // pressure before the last solve
+    void* rec_r0 = nullptr;               // initial residual of the last solve
+    void* rec_delta = nullptr;            // correction applied by the last solve
     // phase timing
     bool timing = false;
     cudaEvent_t ev[8] = {};
@@ -298,6 +308,41 @@ CondArgs cond_args(const les_s* h, int mode, int n, int gate) {
     return ca;
 }
 
+// After the first FP64 residual of a solve: optionally move p along the
+// network's predicted correction (FP64 line search, never worse than p_prev,
+// then the residual again), and record the training pair when asked.
+template <typename T>
+int solve_start(les_s* h, const Geo<T>& g, cudaStream_t st) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (h->warm == LES_WARM_NET && h->net) {
+            h->launches += launch_warm<T>(g, (const T*)h->rr, h->pred, h->ph[h->cur], h->warm_scal, h->n_unk,
+                                          reducer(h), 0, st);
+            int rc = net_predict(h->net, h->d, (const float*)h->rr, h->flags, h->warm_scal, h->pred, st);
+            if (rc) return fail(h, rc, "network prediction failed");
+            h->launches += 20;
+            h->launches += launch_warm<T>(g, (const T*)h->rr, h->pred, h->ph[h->cur], h->warm_scal, h->n_unk,
+                                          reducer(h), 1, st);
+            h->launches += launch_residual64<T>(g, h->ph[h->cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h),
+                                                cond_args(h, RES_INIT, 0, 0), st);
+        }
+    }
+    if (h->record) {
+        CK(cudaMemcpyAsync(h->rec_p0, h->ph[h->cur], h->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(h->rec_r0, h->rr, h->n * h->es, cudaMemcpyDeviceToDevice, st));
+    }
+    CK(cudaGetLastError());
+    return LES_OK;
+}
+
+template <typename T>
+int solve_end(les_s* h, const Geo<T>& g, cudaStream_t st) {
+    if (h->record) {
+        h->launches += launch_record<T>(g, h->ph[h->cur], h->rec_p0, (T*)h->rec_delta, 0, st);
+        CK(cudaGetLastError());
+    }
+    return LES_OK;
+}
+
 template <typename T>
 void launch_refine(les_s* h, const Geo<T>& g, const CondArgs& ca, cudaStream_t st) {
     h->launches += launch_accum<T>(g, h->ph[h->cur], (const T*)h->dl[h->dcur], h->sc, ca.gate, st);
@@ -319,6 +364,10 @@ int sor_solve(les_s* h) {
     if (h->timing) {
         CK(cudaEventSynchronize(h->ev[3]));
         h->tm.ms_residual += elapsed(h, 2, 3);
+    }
+    {
+        int rs = solve_start<T>(h, g, h->stream);
+        if (rs) return rs;
     }
     int sweeps = 0;
     bool fresh = true, conv = false;
@@ -363,6 +412,10 @@ int sor_solve(les_s* h) {
         }
     }
     h->sc_host->sweeps = sweeps;
+    {
+        int rs = solve_end<T>(h, g, h->stream);
+        if (rs) return rs;
+    }
     if (h->sc_host->timeout) return fail(h, LES_ETIMEOUT, "a bounded device wait (TMA tile load) timed out");
     if (h->sc_host->nonfinite) return fail(h, LES_ENONFINITE, "SOR residual is not finite");
     return (!G.fixed_sweeps && !conv) ? LES_ENOCONV : LES_OK;
@@ -555,6 +608,10 @@ int step_graph(les_s* h, int nsteps, les_stats_t* stats) {
             h->launches += launch_residual64<T>(g, h->ph[h->cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h),
                                                 cond_args(h, RES_INIT, 0, 0), h->stream);
             CK(cudaGetLastError());
+            {
+                int rs = solve_start<T>(h, g, h->stream);
+                if (rs) return rs;
+            }
             for (int c = 0; c < max_chunks; ++c) {
                 CK(cudaGraphLaunch(h->gexec[h->cur], h->stream));
                 CK(cudaEventRecord(h->chunk_ev[c & 1], h->stream));
@@ -563,6 +620,10 @@ int step_graph(les_s* h, int nsteps, les_stats_t* stats) {
                     CK(cudaEventSynchronize(h->chunk_ev[(c - 1) & 1]));
                     if (*(volatile int*)h->done_host) break;
                 }
+            }
+            {
+                int rs = solve_end<T>(h, g, h->stream);
+                if (rs) return rs;
             }
             launch_project_step<T>(h, g, h->cur, h->stream);
             CK(cudaGetLastError());
@@ -755,6 +816,15 @@ int create_impl(les_s* h, const uint8_t* solid) {
     rc = h->prec == LES_FP64 ? init_tables<double>(h) : init_tables<float>(h);
     if (rc) return rc;
     CK(h->prec == LES_FP64 ? sor_prepare<double>() : sor_prepare<float>());
+    {
+        unsigned long long* cnt = nullptr;
+        if ((rc = dalloc(h, (void**)&cnt, sizeof(unsigned long long)))) return rc;
+        launch_count_unknowns(d, h->flags, cnt, h->stream);
+        unsigned long long hc = 0;
+        CK(cudaMemcpyAsync(&hc, cnt, sizeof hc, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        h->n_unk = (double)hc;
+    }
     if (h->prec == LES_FP32 && tma_supported(d)) {
         CK(tma_prepare());
         h->tma_ok = tma_encode(d, (float*)h->dl[0], (float*)h->dl[1], (float*)h->rr, h->flags, h->tma);
@@ -815,6 +885,21 @@ int get_aux_impl(les_s* h, int which, void* out) {
         case LES_AUX_FU: src = h->fu; stag = 1; break;
         case LES_AUX_FV: src = h->fv; stag = 2; break;
         case LES_AUX_FW: src = h->fw; stag = 3; break;
+        case LES_AUX_R0:
+            if (!h->record) return fail(h, LES_EINVAL, "recording is off (les_set_record)");
+            src = h->rec_r0;
+            break;
+        case LES_AUX_DELTA:
+            if (!h->record) return fail(h, LES_EINVAL, "recording is off (les_set_record)");
+            src = h->rec_delta;
+            break;
+        case LES_AUX_MASK: {
+            Geo<T> g = geo<T>(h);
+            h->launches += launch_record<T>(g, nullptr, nullptr, (T*)h->tmp, 1, h->stream);
+            CK(cudaGetLastError());
+            src = h->tmp;
+            break;
+        }
         default: return fail(h, LES_EINVAL, "unknown aux array %d", which);
     }
     int rc = download<T>(h, src, stag, out, 0);
@@ -945,9 +1030,12 @@ int les_step(les_handle h, int32_t nsteps, les_stats_t* stats) {
     }
     // chunk graphs need an even batch (the ping-pong returns to the same buffer)
     // and a sweep budget made of whole batches; otherwise the host loop runs
+    // (a fixed-sweep graph captures the whole step, so it runs without the
+    // warm-start network and the recording; those use the chunked path)
+    const bool extras = h->record || h->warm == LES_WARM_NET;
     const bool graph_ok = h->use_graph && !h->timing &&
-                          (h->g.fixed_sweeps ||
-                           (h->g.check_every % 2 == 0 && h->g.max_sweeps % h->g.check_every == 0));
+                          ((h->g.fixed_sweeps && !extras) ||
+                           (!h->g.fixed_sweeps && h->g.check_every % 2 == 0 && h->g.max_sweeps % h->g.check_every == 0));
     h->last_graph = graph_ok;
     if (graph_ok) {
         int rc = h->prec == LES_FP64 ? step_graph<double>(h, nsteps, stats) : step_graph<float>(h, nsteps, stats);
@@ -1079,6 +1167,37 @@ int les_autotune_sor(les_handle h, int32_t sweeps, double* best_ms_per_sweep) {
     if (sweeps < 1) return fail(h, LES_EINVAL, "sweeps must be >= 1");
     return h->prec == LES_FP64 ? autotune_impl<double>(h, sweeps, best_ms_per_sweep)
                                : autotune_impl<float>(h, sweeps, best_ms_per_sweep);
+}
+
+int les_set_warmstart(les_handle h, int32_t mode, les_net net) {
+    if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
+    if (mode == LES_WARM_PREV) {
+        h->warm = LES_WARM_PREV;
+        h->net = nullptr;
+        return LES_OK;
+    }
+    if (mode != LES_WARM_NET || !net) return fail(h, LES_EINVAL, "bad warm-start mode or NULL network");
+    if (h->prec != LES_FP32) return fail(h, LES_EINVAL, "the learned warm start runs on FP32 grids");
+    if (!h->pred) {
+        int rc = dalloc(h, (void**)&h->pred, (size_t)h->g.nx * h->g.ny * h->g.nz * sizeof(float));
+        if (rc) return rc;
+        if ((rc = dalloc(h, (void**)&h->warm_scal, 4 * sizeof(double)))) return rc;
+    }
+    h->warm = LES_WARM_NET;
+    h->net = net;
+    return LES_OK;
+}
+
+int les_set_record(les_handle h, int32_t enable) {
+    if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
+    if (enable && !h->rec_p0) {
+        int rc = dalloc(h, (void**)&h->rec_p0, h->n * sizeof(double));
+        if (rc) return rc;
+        if ((rc = dalloc(h, &h->rec_r0, h->n * h->es))) return rc;
+        if ((rc = dalloc(h, &h->rec_delta, h->n * h->es))) return rc;
+    }
+    h->record = enable != 0;
+    return LES_OK;
 }
 
 int les_set_timing(les_handle h, int32_t enable) {

@@ -160,6 +160,21 @@ int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, const float* cn1tab
                    int zero, Scalars* sc, cudaStream_t s);
 int launch_cn1_table(const Geo<float>& g, float* tab, cudaStream_t s);
 
+// learned warm start (les_kernels.cu): stage 0 = input scale, 1 = line search + update
+template <typename T> int launch_warm(const Geo<T>& g, const T* r, const float* q, double* ph, double* scal,
+                                      double n_unk, const Reduce& red, int stage, cudaStream_t s);
+// training-pair recording: what 0 = ph - ph0 into out, 1 = unknown mask into out
+template <typename T> int launch_record(const Geo<T>& g, const double* ph, const double* ph0, T* out, int what,
+                                        cudaStream_t s);
+int launch_count_unknowns(const Dom& d, const uint8_t* flags, unsigned long long* out, cudaStream_t s);
+
 int max_reduce_blocks(const Dom& d);
 
+}  // namespace les
+
+struct les_net_s;
+namespace les {
+// network prediction on a solver grid (les_net.cu): dense (nz, ny, nx) output
+int net_predict(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, const double* rms,
+                float* out_dense, cudaStream_t s);
 }  // namespace les

@@ -883,6 +883,122 @@ int launch_rhs_eff(const Geo<T>& g, const T* rhs, T* out, const Scalars* sc, cud
     return 1;
 }
 
+// ---------------------------------------------------------------------------
+// learned warm start support: line search and update along a predicted
+// correction (dense (nz, ny, nx) array), plus recording of training pairs.
+
+// scale of the network input: rms of the initial residual over the unknowns
+__global__ void k_warm_scale(const Scalars* sc, double n_unk, double* out) {
+    out[0] = n_unk > 0.0 ? sqrt(sc->res2 / n_unk) : 0.0;
+}
+
+// alpha = <r, A q> / <A q, A q> over the unknowns (FP64), q the prediction
+template <typename T>
+__global__ void k_warm_ls(Geo<T> g, const T* r, const float* q, double* alpha, Reduce red) {
+    const Dom& d = g.d;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    const int k = blockIdx.z + 1;
+    double x[2] = {0.0, 0.0};
+    if (i <= d.nx && j <= d.ny) {
+        const long long c = d.at(i, j, k);
+        const uint8_t f = g.flags[c];
+        if (f & F_UNK) {
+            auto dense = [&](int a, int b, int cc) -> double {
+                if (d.perx) a = a < 1 ? a + d.nx : (a > d.nx ? a - d.nx : a);
+                if (d.pery) b = b < 1 ? b + d.ny : (b > d.ny ? b - d.ny : b);
+                if (d.perz) cc = cc < 1 ? cc + d.nz : (cc > d.nz ? cc - d.nz : cc);
+                return (double)q[((size_t)(cc - 1) * d.ny + (b - 1)) * d.nx + (a - 1)];
+            };
+            Poisson<T> P{g};
+            double ae, aw, an, as, at, ab;
+            P.coefs(f, k, g.cx64, g.cy64, g.cT64, g.cB64, ae, aw, an, as, at, ab);
+            const double qc = dense(i, j, k);
+            double aq = 0.0;
+            if (ae != 0.0) aq += ae * (dense(i + 1, j, k) - qc);
+            if (aw != 0.0) aq += aw * (dense(i - 1, j, k) - qc);
+            if (an != 0.0) aq += an * (dense(i, j + 1, k) - qc);
+            if (as != 0.0) aq += as * (dense(i, j - 1, k) - qc);
+            if (at != 0.0) aq += at * (dense(i, j, k + 1) - qc);
+            if (ab != 0.0) aq += ab * (dense(i, j, k - 1) - qc);
+            x[0] = (double)r[c] * aq;
+            x[1] = aq * aq;
+        }
+    }
+    if (grid_sum<2>(x, red)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) *alpha = (x[1] > 0.0 && isfinite(x[0] / x[1])) ? x[0] / x[1] : 0.0;
+    }
+}
+
+template <typename T>
+__global__ void k_warm_apply(Geo<T> g, double* ph, const float* q, const double* alpha) {
+    const Dom& d = g.d;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    const int k = blockIdx.z + 1;
+    if (i > d.nx || j > d.ny) return;
+    const long long c = d.at(i, j, k);
+    if (g.flags[c] & F_UNK) ph[c] += *alpha * (double)q[((size_t)(k - 1) * d.ny + (j - 1)) * d.nx + (i - 1)];
+}
+
+template <typename T>
+int launch_warm(const Geo<T>& g, const T* r, const float* q, double* ph, double* scal, double n_unk,
+                const Reduce& red, int stage, cudaStream_t s) {
+    const Dom& d = g.d;
+    const dim3 grid((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), blk(32, 8);
+    if (stage == 0) {
+        k_warm_scale<<<1, 1, 0, s>>>(red.sc, n_unk, scal);
+    } else {
+        k_warm_ls<T><<<grid, blk, 0, s>>>(g, r, q, scal + 1, red);
+        k_warm_apply<T><<<grid, blk, 0, s>>>(g, ph, q, scal + 1);
+    }
+    return stage == 0 ? 1 : 2;
+}
+
+// training pairs: delta = ph - ph0 (the correction a solve applied, before the gauge)
+template <typename T>
+__global__ void k_record_delta(Geo<T> g, const double* ph, const double* ph0, T* out) {
+    const Dom& d = g.d;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    const int k = blockIdx.z + 1;
+    if (i > d.nx || j > d.ny) return;
+    const long long c = d.at(i, j, k);
+    out[c] = (g.flags[c] & F_UNK) ? (T)(ph[c] - ph0[c]) : T(0);
+}
+template <typename T>
+__global__ void k_unknown_mask(Geo<T> g, T* out) {
+    const Dom& d = g.d;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    const int k = blockIdx.z + 1;
+    if (i > d.nx || j > d.ny) return;
+    const long long c = d.at(i, j, k);
+    out[c] = (g.flags[c] & F_UNK) ? T(1) : T(0);
+}
+template <typename T>
+int launch_record(const Geo<T>& g, const double* ph, const double* ph0, T* out, int what, cudaStream_t s) {
+    const Dom& d = g.d;
+    const dim3 grid((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), blk(32, 8);
+    if (what == 0) k_record_delta<T><<<grid, blk, 0, s>>>(g, ph, ph0, out);
+    else k_unknown_mask<T><<<grid, blk, 0, s>>>(g, out);
+    return 1;
+}
+
+__global__ void k_count_unknowns(Dom d, const uint8_t* flags, unsigned long long* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    const int k = blockIdx.z + 1;
+    unsigned v = 0;
+    if (i <= d.nx && j <= d.ny) v = (flags[d.at(i, j, k)] & F_UNK) ? 1u : 0u;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (((threadIdx.x + threadIdx.y * blockDim.x) & 31) == 0 && v) atomicAdd(out, (unsigned long long)v);
+}
+int launch_count_unknowns(const Dom& d, const uint8_t* flags, unsigned long long* out, cudaStream_t s) {
+    k_count_unknowns<<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(d, flags, out);
+    return 1;
+}
+
 int max_reduce_blocks(const Dom& d) { return ((d.nx + 31) / 32) * ((d.ny + 7) / 8) * d.nz; }
 
 #define LES_INSTANTIATE(T)                                                                              \
@@ -903,7 +1019,10 @@ int max_reduce_blocks(const Dom& d) { return ((d.nx + 31) / 32) * ((d.ny + 7) / 
     template int launch_project<T>(const Geo<T>&, const T*, const T*, const T*, T*, T*, T*,             \
                                    const double*, double*, Scalars*, cudaStream_t);                     \
     template int launch_rhs_eff<T>(const Geo<T>&, const T*, T*, const Scalars*, cudaStream_t);          \
-    template int launch_gauge<T>(const Geo<T>&, const double*, double*, const Scalars*, cudaStream_t);
+    template int launch_gauge<T>(const Geo<T>&, const double*, double*, const Scalars*, cudaStream_t);   \
+    template int launch_warm<T>(const Geo<T>&, const T*, const float*, double*, double*, double, const Reduce&, \
+                                int, cudaStream_t);                                                     \
+    template int launch_record<T>(const Geo<T>&, const double*, const double*, T*, int, cudaStream_t);
 
 LES_INSTANTIATE(float)
 LES_INSTANTIATE(double)

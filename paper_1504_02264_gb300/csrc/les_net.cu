@@ -1,0 +1,471 @@
+// The learned SOR warm start: a 4-level 3-D U-Net (16, 32, 64, 128
+// channels) on BF16 activations with FP32 accumulation (kernels in
+// les_nn_kernels.cu), trained on the GPU with its own forward / backward
+// kernels and Adam.  The paper has no learned component; this implements the
+// warm start described by the entry points in include/les.h.
+//
+// Network (bias-free, so it is positively homogeneous: scaling the input
+// scales the output):
+//   e0 = relu(c0(x))            16 @ level 0   x: residual / rms, fluid mask
+//   e1 = relu(c1(pool e0))      32 @ level 1
+//   e2 = relu(c2(pool e1))      64 @ level 2
+//   e3 = relu(c3(pool e2))     128 @ level 3
+//   d2 = relu(c4(up e3)) + e2   64 @ level 2
+//   d1 = relu(c5(up d2)) + e1   32 @ level 1
+//   d0 = relu(c6(up d1)) + e0   16 @ level 0
+//   y  = mask * (w_head . d0)    1 @ level 0  (FP32)
+// c* are 3x3x3 convolutions with zero padding; pool = 2x2x2 mean, up =
+// nearest.  Training minimises mean_fluid (y - t / rms(t))^2: the net
+// predicts the direction of the pressure correction, and the solver scales
+// it by an FP64 line search.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/les.h"
+#include "les_nn.cuh"
+
+using namespace les;
+
+namespace {
+
+constexpr int kConvs = 7;
+const int kCin[kConvs] = {16, 16, 32, 64, 128, 64, 32};
+const int kCout[kConvs] = {16, 32, 64, 128, 64, 32, 16};
+constexpr int kHeadC = 16;
+
+struct Level {
+    int X, Y, Z;
+    size_t v() const { return (size_t)X * Y * Z; }
+};
+
+// splitmix64 + Box-Muller, counter based (same construction as the inflow noise)
+uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+double normal_at(uint64_t seed, uint64_t c) {
+    auto u = [&](uint64_t k) {
+        return ((double)(mix64(seed + (k + 1) * 0x9E3779B97F4A7C15ull) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    };
+    return std::sqrt(-2.0 * std::log(u(2 * c))) * std::cos(6.283185307179586 * u(2 * c + 1));
+}
+
+// per-sample RMS over the mask: out[b] = sqrt(sum mask*a^2 / sum mask)
+__global__ void k_rms(const float* a, const float* mask, size_t n, double* out) {
+    const size_t base = (size_t)blockIdx.y * n;
+    double s = 0.0, m = 0.0;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        const double v = a[base + q], w = mask[base + q];
+        s += w * v * v;
+        m += w;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_down_sync(0xffffffffu, s, o);
+        m += __shfl_down_sync(0xffffffffu, m, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&out[2 * blockIdx.y], s);
+        atomicAdd(&out[2 * blockIdx.y + 1], m);
+    }
+}
+__global__ void k_rms_final(double* acc, int b) {
+    const int q = threadIdx.x;
+    if (q < b) {
+        const double m = acc[2 * q + 1];
+        acc[2 * q] = m > 0.0 ? sqrt(acc[2 * q] / m) : 0.0;
+    }
+}
+// dense input: channel 0 = r / scale, channel 1 = mask
+__global__ void k_pack_dense(const float* r, const float* mask, const double* scale, __nv_bfloat16* xin, size_t n) {
+    const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const float s = (float)(scale[0] > 0.0 ? 1.0 / scale[0] : 0.0);
+    __nv_bfloat16* o = xin + v * 16;
+    o[0] = __float2bfloat16(mask[v] * r[v] * s);
+    o[1] = __float2bfloat16(mask[v]);
+    for (int c = 2; c < 16; ++c) o[c] = __float2bfloat16(0.f);
+}
+__global__ void k_scale(const float* a, const double* scale, float* b, size_t n) {
+    const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    b[v] = (float)(scale[0] > 0.0 ? a[v] / scale[0] : 0.0);
+}
+
+}  // namespace
+
+struct les_net_s {
+    cudaStream_t stream = nullptr;
+    // FP32 master parameters (flat: conv0..conv6 [27][Cout][Cin], head [16]) and Adam state
+    size_t off[kConvs + 1];
+    size_t nparam = 0;
+    float *w32 = nullptr, *g32 = nullptr, *m32 = nullptr, *v32 = nullptr;
+    __nv_bfloat16* wb[kConvs] = {};     // BF16 copies
+    __nv_bfloat16* wt[kConvs] = {};     // flipped copies for the input gradient
+    long long adam_t = 0;
+    std::vector<void*> owned;
+    // activation workspace, sized per level for the largest volumes seen so far
+    size_t cap_v0 = 0;
+    size_t cap[4] = {0, 0, 0, 0};
+    std::vector<void*> ws;
+    __nv_bfloat16 *xin = nullptr, *e[4] = {}, *p[3] = {}, *u[3] = {}, *r[3] = {}, *dd[3] = {};
+    __nv_bfloat16 *ga = nullptr, *gb = nullptr, *gd0 = nullptr, *gd1 = nullptr, *gd2 = nullptr, *ge3 = nullptr,
+                  *gpb = nullptr;
+    float *y = nullptr, *gy = nullptr, *mask = nullptr, *tn = nullptr;
+    double* dscal = nullptr;            // [0..2B): per-sample rms and mask counts, [62]: loss
+    char err[256] = {0};
+};
+
+namespace {
+
+int nfail(les_net_s* n, int code, const char* msg, cudaError_t e = cudaSuccess) {
+    if (n)
+        snprintf(n->err, sizeof n->err, "%s%s%s", msg, e != cudaSuccess ? ": " : "",
+                 e != cudaSuccess ? cudaGetErrorString(e) : "");
+    return code;
+}
+#define NCK(call)                                                     \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return nfail(n, LES_ECUDA, #call, e_); \
+    } while (0)
+
+Level level(const Level& l0, int l) {
+    Level o = l0;
+    for (int i = 0; i < l; ++i) o = Level{(o.X + 1) / 2, (o.Y + 1) / 2, (o.Z + 1) / 2};
+    return o;
+}
+
+void free_ws(les_net_s* n) {
+    for (void* q : n->ws) cudaFree(q);
+    n->ws.clear();
+    n->cap_v0 = 0;
+    for (size_t& c : n->cap) c = 0;
+}
+
+// every buffer is sized from each level's volume (grown by 25% so nearby
+// shapes reuse the workspace); a shape that exceeds any level reallocates
+int ensure_ws(les_net_s* n, const Level& L0) {
+    Level Lb[4];
+    for (int l = 0; l < 4; ++l) Lb[l] = level(L0, l);
+    bool fits = n->cap_v0 > 0;
+    for (int l = 0; l < 4 && fits; ++l) fits = Lb[l].v() <= n->cap[l];
+    if (fits) return LES_OK;
+    NCK(cudaStreamSynchronize(n->stream));
+    size_t want[4];
+    for (int l = 0; l < 4; ++l) {
+        const size_t v = Lb[l].v() + Lb[l].v() / 4 + 64;
+        want[l] = v > n->cap[l] ? v : n->cap[l];
+    }
+    free_ws(n);
+    auto vol = [&](int l) { return want[l]; };
+    auto get = [&](size_t elems, size_t es, void** q) -> int {
+        cudaError_t e = cudaMalloc(q, elems * es);
+        if (e != cudaSuccess) return nfail(n, LES_ENOMEM, "network workspace", e);
+        n->ws.push_back(*q);
+        return LES_OK;
+    };
+    const size_t B = sizeof(__nv_bfloat16);
+    int rc;
+    const int ce[4] = {16, 32, 64, 128};
+    if ((rc = get(vol(0) * 16, B, (void**)&n->xin))) return rc;
+    for (int l = 0; l < 4; ++l)
+        if ((rc = get(vol(l) * ce[l], B, (void**)&n->e[l]))) return rc;
+    for (int l = 0; l < 3; ++l) {
+        if ((rc = get(vol(l + 1) * ce[l], B, (void**)&n->p[l]))) return rc;      // pool(e_l), level l+1
+        if ((rc = get(vol(l) * ce[l + 1], B, (void**)&n->u[l]))) return rc;      // up(d_{l+1} | e_3), level l
+        if ((rc = get(vol(l) * ce[l], B, (void**)&n->r[l]))) return rc;          // relu(conv), level l
+        if ((rc = get(vol(l) * ce[l], B, (void**)&n->dd[l]))) return rc;         // d_l
+    }
+    size_t gmax = 0;
+    for (int l = 0; l < 4; ++l) {
+        const size_t c = vol(l) * (size_t)(l < 3 ? ce[l + 1] : ce[3]);
+        gmax = c > gmax ? c : gmax;
+    }
+    if ((rc = get(gmax, B, (void**)&n->ga))) return rc;
+    if ((rc = get(gmax, B, (void**)&n->gb))) return rc;
+    if ((rc = get(vol(0) * 16, B, (void**)&n->gd0))) return rc;
+    if ((rc = get(vol(1) * 32, B, (void**)&n->gd1))) return rc;
+    if ((rc = get(vol(2) * 64, B, (void**)&n->gd2))) return rc;
+    if ((rc = get(vol(3) * 128, B, (void**)&n->ge3))) return rc;
+    if ((rc = get(vol(0) * 16, B, (void**)&n->gpb))) return rc;
+    if ((rc = get(vol(0), sizeof(float), (void**)&n->y))) return rc;
+    if ((rc = get(vol(0), sizeof(float), (void**)&n->gy))) return rc;
+    if ((rc = get(vol(0), sizeof(float), (void**)&n->mask))) return rc;
+    if ((rc = get(vol(0), sizeof(float), (void**)&n->tn))) return rc;
+    if ((rc = get(64, sizeof(double), (void**)&n->dscal))) return rc;
+    for (int l = 0; l < 4; ++l) n->cap[l] = want[l];
+    n->cap_v0 = want[0];
+    return LES_OK;
+}
+
+// forward on the packed input n->xin with mask n->mask; output n->y
+void forward(les_net_s* n, const Level& L0) {
+    cudaStream_t s = n->stream;
+    const Level L1 = level(L0, 1), L2 = level(L0, 2), L3 = level(L0, 3);
+    nn::conv3_fwd(n->xin, n->wb[0], n->e[0], nullptr, nullptr, L0.X, L0.Y, L0.Z, 16, 16, 1, s);
+    nn::pool(n->e[0], n->p[0], L0.X, L0.Y, L0.Z, 16, s);
+    nn::conv3_fwd(n->p[0], n->wb[1], n->e[1], nullptr, nullptr, L1.X, L1.Y, L1.Z, 16, 32, 1, s);
+    nn::pool(n->e[1], n->p[1], L1.X, L1.Y, L1.Z, 32, s);
+    nn::conv3_fwd(n->p[1], n->wb[2], n->e[2], nullptr, nullptr, L2.X, L2.Y, L2.Z, 32, 64, 1, s);
+    nn::pool(n->e[2], n->p[2], L2.X, L2.Y, L2.Z, 64, s);
+    nn::conv3_fwd(n->p[2], n->wb[3], n->e[3], nullptr, nullptr, L3.X, L3.Y, L3.Z, 64, 128, 1, s);
+    nn::up(n->e[3], n->u[2], L2.X, L2.Y, L2.Z, 128, s);
+    nn::conv3_fwd(n->u[2], n->wb[4], n->r[2], n->e[2], n->dd[2], L2.X, L2.Y, L2.Z, 128, 64, 1, s);
+    nn::up(n->dd[2], n->u[1], L1.X, L1.Y, L1.Z, 64, s);
+    nn::conv3_fwd(n->u[1], n->wb[5], n->r[1], n->e[1], n->dd[1], L1.X, L1.Y, L1.Z, 64, 32, 1, s);
+    nn::up(n->dd[1], n->u[0], L0.X, L0.Y, L0.Z, 32, s);
+    nn::conv3_fwd(n->u[0], n->wb[6], n->r[0], n->e[0], n->dd[0], L0.X, L0.Y, L0.Z, 32, 16, 1, s);
+    nn::head(n->dd[0], n->w32 + n->off[kConvs], n->mask, n->y, L0.v(), kHeadC, s);
+}
+
+// backward from n->gy; accumulates the parameter gradients into n->g32
+void backward(les_net_s* n, const Level& L0) {
+    cudaStream_t s = n->stream;
+    const Level L1 = level(L0, 1), L2 = level(L0, 2), L3 = level(L0, 3);
+    float* G = n->g32;
+    auto gw = [&](int c) { return G + n->off[c]; };
+    nn::head_bwd(n->dd[0], n->w32 + n->off[kConvs], n->mask, n->gy, n->gd0, G + n->off[kConvs], L0.v(), kHeadC, s);
+    // d0 = relu(c6(u0)) + e0
+    nn::relu_bwd(n->r[0], n->gd0, nullptr, n->ga, L0.v() * 16, s);
+    nn::conv3_wgrad(n->u[0], n->ga, gw(6), L0.X, L0.Y, L0.Z, 32, 16, s);
+    nn::conv3_fwd(n->ga, n->wt[6], n->gb, nullptr, nullptr, L0.X, L0.Y, L0.Z, 16, 32, 0, s);
+    nn::up_bwd(n->gb, n->gd1, L0.X, L0.Y, L0.Z, 32, s);
+    // d1 = relu(c5(u1)) + e1
+    nn::relu_bwd(n->r[1], n->gd1, nullptr, n->ga, L1.v() * 32, s);
+    nn::conv3_wgrad(n->u[1], n->ga, gw(5), L1.X, L1.Y, L1.Z, 64, 32, s);
+    nn::conv3_fwd(n->ga, n->wt[5], n->gb, nullptr, nullptr, L1.X, L1.Y, L1.Z, 32, 64, 0, s);
+    nn::up_bwd(n->gb, n->gd2, L1.X, L1.Y, L1.Z, 64, s);
+    // d2 = relu(c4(u2)) + e2
+    nn::relu_bwd(n->r[2], n->gd2, nullptr, n->ga, L2.v() * 64, s);
+    nn::conv3_wgrad(n->u[2], n->ga, gw(4), L2.X, L2.Y, L2.Z, 128, 64, s);
+    nn::conv3_fwd(n->ga, n->wt[4], n->gb, nullptr, nullptr, L2.X, L2.Y, L2.Z, 64, 128, 0, s);
+    nn::up_bwd(n->gb, n->ge3, L2.X, L2.Y, L2.Z, 128, s);
+    // e3 = relu(c3(p2))
+    nn::relu_bwd(n->e[3], n->ge3, nullptr, n->ga, L3.v() * 128, s);
+    nn::conv3_wgrad(n->p[2], n->ga, gw(3), L3.X, L3.Y, L3.Z, 64, 128, s);
+    nn::conv3_fwd(n->ga, n->wt[3], n->gb, nullptr, nullptr, L3.X, L3.Y, L3.Z, 128, 64, 0, s);
+    nn::pool_bwd(n->gb, n->gpb, L2.X, L2.Y, L2.Z, 64, s);
+    // e2 = relu(c2(p1)); dL/de2 = skip part + pooled part
+    nn::relu_bwd(n->e[2], n->gd2, n->gpb, n->ga, L2.v() * 64, s);
+    nn::conv3_wgrad(n->p[1], n->ga, gw(2), L2.X, L2.Y, L2.Z, 32, 64, s);
+    nn::conv3_fwd(n->ga, n->wt[2], n->gb, nullptr, nullptr, L2.X, L2.Y, L2.Z, 64, 32, 0, s);
+    nn::pool_bwd(n->gb, n->gpb, L1.X, L1.Y, L1.Z, 32, s);
+    // e1 = relu(c1(p0))
+    nn::relu_bwd(n->e[1], n->gd1, n->gpb, n->ga, L1.v() * 32, s);
+    nn::conv3_wgrad(n->p[0], n->ga, gw(1), L1.X, L1.Y, L1.Z, 16, 32, s);
+    nn::conv3_fwd(n->ga, n->wt[1], n->gb, nullptr, nullptr, L1.X, L1.Y, L1.Z, 32, 16, 0, s);
+    nn::pool_bwd(n->gb, n->gpb, L0.X, L0.Y, L0.Z, 16, s);
+    // e0 = relu(c0(xin))
+    nn::relu_bwd(n->e[0], n->gd0, n->gpb, n->ga, L0.v() * 16, s);
+    nn::conv3_wgrad(n->xin, n->ga, gw(0), L0.X, L0.Y, L0.Z, 16, 16, s);
+}
+
+void refresh_copies(les_net_s* n) {
+    for (int c = 0; c < kConvs; ++c) {
+        const size_t cnt = (size_t)27 * kCin[c] * kCout[c];
+        nn::to_bf16(n->w32 + n->off[c], n->wb[c], cnt, n->stream);
+        nn::wflip(n->wb[c], n->wt[c], kCin[c], kCout[c], n->stream);
+    }
+}
+
+// pack sample b of a dense batch and normalise its target (if any)
+int prepare_sample(les_net_s* n, const Level& L0, const float* r, const float* mask, const float* t, size_t b,
+                   double* nmask) {
+    const size_t v = L0.v();
+    cudaStream_t s = n->stream;
+    NCK(cudaMemsetAsync(n->dscal, 0, 4 * sizeof(double), s));
+    const unsigned blocks = (unsigned)((v + 255) / 256 < 1024 ? (v + 255) / 256 : 1024);
+    k_rms<<<dim3(blocks, 1), 256, 0, s>>>(r + b * v, mask + b * v, v, n->dscal);
+    if (t) k_rms<<<dim3(blocks, 1), 256, 0, s>>>(t + b * v, mask + b * v, v, n->dscal + 2);
+    k_rms_final<<<1, 32, 0, s>>>(n->dscal, t ? 2 : 1);
+    NCK(cudaMemcpyAsync(n->mask, mask + b * v, v * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    k_pack_dense<<<(unsigned)((v + 255) / 256), 256, 0, s>>>(r + b * v, n->mask, n->dscal, n->xin, v);
+    if (t) k_scale<<<(unsigned)((v + 255) / 256), 256, 0, s>>>(t + b * v, n->dscal + 2, n->tn, v);
+    NCK(cudaGetLastError());
+    if (nmask) {
+        double host[2];
+        NCK(cudaMemcpyAsync(host, n->dscal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        NCK(cudaStreamSynchronize(s));
+        *nmask = host[1];
+    }
+    return LES_OK;
+}
+
+// forward + loss + backward over a batch, gradients accumulated in g32
+int batch_grad(les_net_s* n, const Level& L0, const float* r, const float* mask, const float* t, int B, double* loss) {
+    int rc = ensure_ws(n, L0);
+    if (rc) return rc;
+    cudaStream_t s = n->stream;
+    NCK(cudaMemsetAsync(n->g32, 0, n->nparam * sizeof(float), s));
+    double* dl = n->dscal + 62;
+    NCK(cudaMemsetAsync(dl, 0, sizeof(double), s));
+    for (int b = 0; b < B; ++b) {
+        double nm = 0.0;
+        if ((rc = prepare_sample(n, L0, r, mask, t, b, &nm))) return rc;
+        forward(n, L0);
+        const double inv = nm > 0.0 ? 1.0 / (nm * B) : 0.0;
+        nn::mse(n->y, n->tn, n->mask, n->gy, dl, L0.v(), inv, s);
+        backward(n, L0);
+        NCK(cudaGetLastError());
+    }
+    NCK(cudaMemcpyAsync(loss, dl, sizeof(double), cudaMemcpyDeviceToHost, s));
+    NCK(cudaStreamSynchronize(s));
+    return LES_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// solver-side inference (les_api.cu): predicted correction direction on the
+// handle's grid from its padded residual (float) and flags
+namespace les {
+int net_predict(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, const double* rms,
+                float* out_dense, cudaStream_t s) {
+    const Level L0{d.nx, d.ny, d.nz};
+    cudaStream_t keep = n->stream;
+    n->stream = s;
+    int rc = ensure_ws(n, L0);
+    if (!rc) {
+        nn::pack_input(r_padded, flags, d, rms, n->xin, n->mask, s);
+        forward(n, L0);
+        cudaError_t e = cudaMemcpyAsync(out_dense, n->y, L0.v() * sizeof(float), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) rc = LES_ECUDA;
+    }
+    n->stream = keep;
+    return rc;
+}
+}  // namespace les
+
+extern "C" {
+
+int les_net_create(uint64_t seed, void* stream, les_net* out) {
+    if (!out) return LES_EINVAL;
+    *out = nullptr;
+    les_net_s* n = new (std::nothrow) les_net_s();
+    if (!n) return LES_ENOMEM;
+    n->stream = (cudaStream_t)stream;
+    size_t o = 0;
+    for (int c = 0; c < kConvs; ++c) {
+        n->off[c] = o;
+        o += (size_t)27 * kCin[c] * kCout[c];
+    }
+    n->off[kConvs] = o;
+    n->nparam = o + kHeadC;
+    // He-normal initialisation (conv0 sees 2 live input channels)
+    std::vector<float> w(n->nparam);
+    uint64_t ctr = 0;
+    for (int c = 0; c < kConvs; ++c) {
+        const double fan = 27.0 * (c == 0 ? 2 : kCin[c]);
+        const double sd = std::sqrt(2.0 / fan);
+        for (size_t q = n->off[c]; q < n->off[c + 1]; ++q) w[q] = (float)(sd * normal_at(seed, ctr++));
+    }
+    for (int q = 0; q < kHeadC; ++q) w[n->off[kConvs] + q] = (float)(std::sqrt(1.0 / kHeadC) * normal_at(seed, ctr++));
+    auto get = [&](size_t bytes, void** q) -> bool {
+        if (cudaMalloc(q, bytes) != cudaSuccess) return false;
+        n->owned.push_back(*q);
+        return cudaMemsetAsync(*q, 0, bytes, n->stream) == cudaSuccess;
+    };
+    bool ok = get(n->nparam * 4, (void**)&n->w32) && get(n->nparam * 4, (void**)&n->g32) &&
+              get(n->nparam * 4, (void**)&n->m32) && get(n->nparam * 4, (void**)&n->v32);
+    for (int c = 0; ok && c < kConvs; ++c) {
+        const size_t cnt = (size_t)27 * kCin[c] * kCout[c];
+        ok = get(cnt * 2, (void**)&n->wb[c]) && get(cnt * 2, (void**)&n->wt[c]);
+    }
+    if (ok) ok = cudaMemcpyAsync(n->w32, w.data(), n->nparam * 4, cudaMemcpyHostToDevice, n->stream) == cudaSuccess;
+    if (ok) {
+        refresh_copies(n);
+        ok = cudaStreamSynchronize(n->stream) == cudaSuccess && cudaGetLastError() == cudaSuccess;
+    }
+    if (!ok) {
+        for (void* q : n->owned) cudaFree(q);
+        delete n;
+        return LES_ENOMEM;
+    }
+    *out = n;
+    return LES_OK;
+}
+
+void les_net_destroy(les_net n) {
+    if (!n) return;
+    cudaStreamSynchronize(n->stream);
+    free_ws(n);
+    for (void* q : n->owned) cudaFree(q);
+    delete n;
+}
+
+const char* les_net_last_error(les_net n) { return n ? n->err : ""; }
+
+int les_net_num_params(les_net n, int64_t* count) {
+    if (!n || !count) return LES_EINVAL;
+    *count = (int64_t)n->nparam;
+    return LES_OK;
+}
+
+int les_net_get_params(les_net n, float* host) {
+    if (!n || !host) return LES_EINVAL;
+    NCK(cudaMemcpyAsync(host, n->w32, n->nparam * 4, cudaMemcpyDeviceToHost, n->stream));
+    NCK(cudaStreamSynchronize(n->stream));
+    return LES_OK;
+}
+
+int les_net_set_params(les_net n, const float* host) {
+    if (!n || !host) return LES_EINVAL;
+    NCK(cudaMemcpyAsync(n->w32, host, n->nparam * 4, cudaMemcpyHostToDevice, n->stream));
+    refresh_copies(n);
+    NCK(cudaGetLastError());
+    NCK(cudaStreamSynchronize(n->stream));
+    n->adam_t = 0;
+    NCK(cudaMemset(n->m32, 0, n->nparam * 4));
+    NCK(cudaMemset(n->v32, 0, n->nparam * 4));
+    return LES_OK;
+}
+
+int les_net_forward(les_net n, const float* d_r, const float* d_mask, float* d_y, int32_t nx, int32_t ny,
+                    int32_t nz) {
+    if (!n || !d_r || !d_mask || !d_y || nx < 1 || ny < 1 || nz < 1) return LES_EINVAL;
+    const Level L0{nx, ny, nz};
+    int rc = ensure_ws(n, L0);
+    if (rc) return rc;
+    if ((rc = prepare_sample(n, L0, d_r, d_mask, nullptr, 0, nullptr))) return rc;
+    forward(n, L0);
+    NCK(cudaMemcpyAsync(d_y, n->y, L0.v() * sizeof(float), cudaMemcpyDeviceToDevice, n->stream));
+    NCK(cudaGetLastError());
+    NCK(cudaStreamSynchronize(n->stream));
+    return LES_OK;
+}
+
+int les_net_gradient(les_net n, const float* d_r, const float* d_mask, const float* d_t, int32_t batch, int32_t nx,
+                     int32_t ny, int32_t nz, float* d_grad, double* loss) {
+    if (!n || !d_r || !d_mask || !d_t || !d_grad || !loss || batch < 1 || nx < 1 || ny < 1 || nz < 1)
+        return LES_EINVAL;
+    int rc = batch_grad(n, Level{nx, ny, nz}, d_r, d_mask, d_t, batch, loss);
+    if (rc) return rc;
+    NCK(cudaMemcpyAsync(d_grad, n->g32, n->nparam * 4, cudaMemcpyDeviceToDevice, n->stream));
+    NCK(cudaStreamSynchronize(n->stream));
+    return LES_OK;
+}
+
+int les_net_train_step(les_net n, const float* d_r, const float* d_mask, const float* d_t, int32_t batch, int32_t nx,
+                       int32_t ny, int32_t nz, float lr, double* loss) {
+    if (!n || !d_r || !d_mask || !d_t || !loss || batch < 1 || nx < 1 || ny < 1 || nz < 1 || !(lr > 0))
+        return LES_EINVAL;
+    int rc = batch_grad(n, Level{nx, ny, nz}, d_r, d_mask, d_t, batch, loss);
+    if (rc) return rc;
+    n->adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.f - std::pow(b1, (float)n->adam_t), c2 = 1.f - std::pow(b2, (float)n->adam_t);
+    for (int c = 0; c <= kConvs; ++c) {
+        const size_t o = n->off[c], cnt = (c < kConvs ? n->off[c + 1] : n->nparam) - o;
+        nn::adam(n->w32 + o, n->m32 + o, n->v32 + o, n->g32 + o, c < kConvs ? n->wb[c] : nullptr, cnt, lr, b1, b2,
+                 eps, c1, c2, n->stream);
+    }
+    for (int c = 0; c < kConvs; ++c) nn::wflip(n->wb[c], n->wt[c], kCin[c], kCout[c], n->stream);
+    NCK(cudaGetLastError());
+    NCK(cudaStreamSynchronize(n->stream));
+    return LES_OK;
+}
+
+}  // extern "C"

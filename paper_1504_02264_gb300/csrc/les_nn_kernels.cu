@@ -1,0 +1,452 @@
+// Kernels of the learned SOR warm start: a small 3-D U-Net on BF16
+// activations with FP32 accumulation on the tensor cores
+// (mma.sync.m16n8k16 bf16), plus the elementwise pieces of its forward and
+// backward pass and the Adam update.
+//
+// Activations are dense NDHWC: a[((z*Y + y)*X + x)*C + c], C a multiple of 16.
+// Conv weights are [27][Cout][Cin] (tap-major, input channel fastest), tap =
+// (dz*3 + dy)*3 + dx with offsets -1..1, zero padding outside the volume.
+#include <cuda_bf16.h>
+
+#include "les_nn.cuh"
+
+namespace les {
+namespace nn {
+
+// ---------------------------------------------------------------------------
+// 3x3x3 convolution, implicit GEMM on mma.sync.m16n8k16 (bf16 in, fp32 acc).
+// CTA: 16 x 4 x 2 output voxels, 8 warps; warp w owns the 16 voxels of row
+// (y = w % 4, z = w / 4) and CO output channels.  Per 16-channel input chunk
+// the input halo block (18 x 6 x 4 voxels) and the chunk's weights are staged
+// in shared memory; A fragments come from ldmatrix on the voxel rows, B
+// fragments from ldmatrix on the [co][ci] weight rows.
+// Epilogue: y = relu?(acc) (bf16), and optionally ysum = y + skip.
+
+constexpr int TX = 16, TY = 4, TZ = 2, HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2_t(uint32_t addr, uint32_t& r0, uint32_t& r1) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0, %1}, [%2];"
+                 : "=r"(r0), "=r"(r1)
+                 : "r"(addr));
+}
+__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+template <int CO>
+__global__ void __launch_bounds__(256)
+k_conv3(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ w, __nv_bfloat16* __restrict__ y,
+        const __nv_bfloat16* __restrict__ skip, __nv_bfloat16* __restrict__ ysum, int X, int Y, int Z, int Cin,
+        int Cout, int relu) {
+    __shared__ __align__(16) __nv_bfloat16 sIn[HZ][HY][HX][16];
+    __shared__ __align__(16) __nv_bfloat16 sW[27][CO][16];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ntz = (Z + TZ - 1) / TZ;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = (blockIdx.z % ntz) * TZ;
+    const int co0 = (blockIdx.z / ntz) * CO;
+    const int wy = warp % TY, wz = warp / TY;
+    float acc[CO / 8][4];
+#pragma unroll
+    for (int n = 0; n < CO / 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+    for (int c0 = 0; c0 < Cin; c0 += 16) {
+        // stage the halo block (two 16-byte halves per voxel) and the weights
+        for (int q = tid; q < HZ * HY * HX * 2; q += 256) {
+            const int h = q & 1, v = q >> 1;
+            const int hx = v % HX, hy = (v / HX) % HY, hz = v / (HX * HY);
+            const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = z0 - 1 + hz;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (gx >= 0 && gx < X && gy >= 0 && gy < Y && gz >= 0 && gz < Z)
+                val = *reinterpret_cast<const uint4*>(x + (((size_t)gz * Y + gy) * X + gx) * Cin + c0 + 8 * h);
+            *reinterpret_cast<uint4*>(&sIn[hz][hy][hx][8 * h]) = val;
+        }
+        for (int q = tid; q < 27 * CO * 2; q += 256) {
+            const int h = q & 1, r = q >> 1, co = r % CO, tap = r / CO;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (co0 + co < Cout)
+                val = *reinterpret_cast<const uint4*>(w + ((size_t)tap * Cout + co0 + co) * Cin + c0 + 8 * h);
+            *reinterpret_cast<uint4*>(&sW[tap][co][8 * h]) = val;
+        }
+        __syncthreads();
+        const int mat = lane >> 3, r8 = lane & 7;
+#pragma unroll 1
+        for (int tap = 0; tap < 27; ++tap) {
+            const int dx = tap % 3, dy = (tap / 3) % 3, dz = tap / 9;
+            // A: rows = 16 voxels of the warp's row shifted by the tap, k = 16 channels
+            const int vrow = r8 + 8 * (mat & 1), koff = 8 * (mat >> 1);
+            uint32_t a0, a1, a2, a3;
+            ldsm_x4(smem_addr(&sIn[wz + dz][wy + dy][vrow + dx][koff]), a0, a1, a2, a3);
+#pragma unroll
+            for (int n = 0; n < CO / 8; n += 2) {
+                // B: two n-tiles; matrices (co rows, ci 0-7 | 8-15) of tile n and n+1
+                const int co = 8 * (n + (mat >> 1)) + r8, ko = 8 * (mat & 1);
+                uint32_t b0, b1, b2, b3;
+                ldsm_x4(smem_addr(&sW[tap][co][ko]), b0, b1, b2, b3);
+                mma_bf16(acc[n], a0, a1, a2, a3, b0, b1);
+                mma_bf16(acc[n + 1], a0, a1, a2, a3, b2, b3);
+            }
+        }
+        __syncthreads();
+    }
+    // epilogue: thread holds rows g and g+8 (voxels), columns 2*(lane%4) + {0,1}
+    const int g = lane >> 2, cq = 2 * (lane & 3);
+    const int gy = y0 + wy, gz = z0 + wz;
+    if (gy >= Y || gz >= Z) return;
+#pragma unroll
+    for (int n = 0; n < CO / 8; ++n) {
+        const int co = co0 + 8 * n + cq;
+        if (co >= Cout) continue;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int gx = x0 + g + 8 * hh;
+            if (gx >= X) continue;
+            float v0 = acc[n][2 * hh], v1 = acc[n][2 * hh + 1];
+            if (relu) {
+                v0 = fmaxf(v0, 0.f);
+                v1 = fmaxf(v1, 0.f);
+            }
+            const size_t o = (((size_t)gz * Y + gy) * X + gx) * Cout + co;
+            __nv_bfloat162 r = __floats2bfloat162_rn(v0, v1);
+            *reinterpret_cast<__nv_bfloat162*>(y + o) = r;
+            if (skip) {
+                const __nv_bfloat162 s = *reinterpret_cast<const __nv_bfloat162*>(skip + o);
+                *reinterpret_cast<__nv_bfloat162*>(ysum + o) =
+                    __floats2bfloat162_rn(__bfloat162float(r.x) + __bfloat162float(s.x),
+                                          __bfloat162float(r.y) + __bfloat162float(s.y));
+            }
+        }
+    }
+}
+
+void conv3_fwd(const __nv_bfloat16* x, const __nv_bfloat16* w, __nv_bfloat16* y, const __nv_bfloat16* skip,
+               __nv_bfloat16* ysum, int X, int Y, int Z, int Cin, int Cout, int relu, cudaStream_t s) {
+    const int co = Cout >= 32 ? 32 : 16;
+    const int ntz = (Z + TZ - 1) / TZ;
+    dim3 grid((X + TX - 1) / TX, (Y + TY - 1) / TY, ntz * ((Cout + co - 1) / co));
+    if (co == 32)
+        k_conv3<32><<<grid, 256, 0, s>>>(x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu);
+    else
+        k_conv3<16><<<grid, 256, 0, s>>>(x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu);
+}
+
+// dgrad weights: W'[tap][ci][co] = W[26 - tap][co][ci] (flipped taps, swapped roles)
+__global__ void k_wflip(const __nv_bfloat16* w, __nv_bfloat16* wt, int Cin, int Cout) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= 27 * Cin * Cout) return;
+    const int co = q % Cout, ci = (q / Cout) % Cin, tap = q / (Cout * Cin);
+    wt[((size_t)tap * Cin + ci) * Cout + co] = w[((size_t)(26 - tap) * Cout + co) * Cin + ci];
+}
+
+void wflip(const __nv_bfloat16* w, __nv_bfloat16* wt, int Cin, int Cout, cudaStream_t s) {
+    const int n = 27 * Cin * Cout;
+    k_wflip<<<(n + 255) / 256, 256, 0, s>>>(w, wt, Cin, Cout);
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient: dW[tap][co][ci] += sum_v dY[v][co] * X[v + off(tap)][ci].
+// mma with M = co (16), N = ci (8), K = 16 voxels of one row; A = dY^T and
+// B = X_tap loaded with ldmatrix.trans from the [voxel][channel] tiles.  A CTA
+// walks `tiles` voxel blocks of one (co, ci) 16 x 16 pair; warp w owns taps
+// w, w+8, w+16, w+24.  Partial sums go to the FP32 gradient with atomics.
+__global__ void __launch_bounds__(256)
+k_conv3_wgrad(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ dy, float* __restrict__ dw,
+              int X, int Y, int Z, int Cin, int Cout, int tiles) {
+    __shared__ __align__(16) __nv_bfloat16 sIn[HZ][HY][HX][16];
+    __shared__ __align__(16) __nv_bfloat16 sG[TZ][TY][TX][16];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int co0 = blockIdx.y * 16, ci0 = blockIdx.z * 16;
+    const int nbx = (X + TX - 1) / TX, nby = (Y + TY - 1) / TY, nbz = (Z + TZ - 1) / TZ;
+    const int ntile = nbx * nby * nbz;
+    float acc[4][2][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int n = 0; n < 2; ++n) acc[a][n][0] = acc[a][n][1] = acc[a][n][2] = acc[a][n][3] = 0.f;
+    const int mat = lane >> 3, r8 = lane & 7;
+    for (int t = blockIdx.x * tiles; t < min(ntile, (blockIdx.x + 1) * tiles); ++t) {
+        const int bx = t % nbx, by = (t / nbx) % nby, bz = t / (nbx * nby);
+        const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
+        for (int q = tid; q < HZ * HY * HX * 2; q += 256) {
+            const int h = q & 1, v = q >> 1;
+            const int hx = v % HX, hy = (v / HX) % HY, hz = v / (HX * HY);
+            const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = z0 - 1 + hz;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (gx >= 0 && gx < X && gy >= 0 && gy < Y && gz >= 0 && gz < Z)
+                val = *reinterpret_cast<const uint4*>(x + (((size_t)gz * Y + gy) * X + gx) * Cin + ci0 + 8 * h);
+            *reinterpret_cast<uint4*>(&sIn[hz][hy][hx][8 * h]) = val;
+        }
+        for (int q = tid; q < TZ * TY * TX * 2; q += 256) {
+            const int h = q & 1, v = q >> 1;
+            const int lx = v % TX, ly = (v / TX) % TY, lz = v / (TX * TY);
+            const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (gx < X && gy < Y && gz < Z)
+                val = *reinterpret_cast<const uint4*>(dy + (((size_t)gz * Y + gy) * X + gx) * Cout + co0 + 8 * h);
+            *reinterpret_cast<uint4*>(&sG[lz][ly][lx][8 * h]) = val;
+        }
+        __syncthreads();
+        for (int row = 0; row < TY * TZ; ++row) {
+            const int ry = row % TY, rz = row / TY;
+            // A = dY^T (m = co 16, k = 16 voxels): transposed 8x8 blocks of sG[voxel][co]
+            // matrices: (co 0-7, v 0-7), (co 8-15, v 0-7), (co 0-7, v 8-15), (co 8-15, v 8-15)
+            uint32_t a0, a1, a2, a3;
+            {
+                const int v = r8 + 8 * (mat >> 1), c = 8 * (mat & 1);
+                ldsm_x4_t(smem_addr(&sG[rz][ry][v][c]), a0, a1, a2, a3);
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int tap = warp + 8 * a;
+                if (tap >= 27) break;
+                const int dx = tap % 3, dyy = (tap / 3) % 3, dz = tap / 9;
+                // B = X_tap (k = 16 voxels, n = 8 ci) per n-tile: transposed blocks of sIn[voxel][ci]
+#pragma unroll
+                for (int n = 0; n < 2; ++n) {
+                    uint32_t b0, b1;
+                    const int v = r8 + 8 * (mat & 1);
+                    ldsm_x2_t(smem_addr(&sIn[rz + dz][ry + dyy][v + dx][8 * n]), b0, b1);
+                    mma_bf16(acc[a][n], a0, a1, a2, a3, b0, b1);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // acc[a][n]: rows co = g, g+8 ; cols ci = 8n + 2(lane%4) + {0,1}
+    const int g = lane >> 2, cq = 2 * (lane & 3);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int tap = warp + 8 * a;
+        if (tap >= 27) break;
+#pragma unroll
+        for (int n = 0; n < 2; ++n)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int co = co0 + g + 8 * (e >> 1), ci = ci0 + 8 * n + cq + (e & 1);
+                atomicAdd(&dw[((size_t)tap * Cout + co) * Cin + ci], acc[a][n][e]);
+            }
+    }
+}
+
+void conv3_wgrad(const __nv_bfloat16* x, const __nv_bfloat16* dy, float* dw, int X, int Y, int Z, int Cin, int Cout,
+                 cudaStream_t s) {
+    const int ntile = ((X + TX - 1) / TX) * ((Y + TY - 1) / TY) * ((Z + TZ - 1) / TZ);
+    const int tiles = ntile < 32 ? 1 : 32;
+    dim3 grid((ntile + tiles - 1) / tiles, Cout / 16, Cin / 16);
+    k_conv3_wgrad<<<grid, 256, 0, s>>>(x, dy, dw, X, Y, Z, Cin, Cout, tiles);
+}
+
+// ---------------------------------------------------------------------------
+// elementwise pieces
+
+// 2x2x2 average pool (children outside the fine grid count as zero)
+__global__ void k_pool(const __nv_bfloat16* a, __nv_bfloat16* b, int X, int Y, int Z, int C) {
+    const int Xc = (X + 1) / 2, Yc = (Y + 1) / 2, Zc = (Z + 1) / 2;
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (size_t)Xc * Yc * Zc * C) return;
+    const int c = q % C;
+    size_t v = q / C;
+    const int x = v % Xc, yv = (v / Xc) % Yc, z = v / ((size_t)Xc * Yc);
+    float s = 0.f;
+    for (int e = 0; e < 8; ++e) {
+        const int fx = 2 * x + (e & 1), fy = 2 * yv + ((e >> 1) & 1), fz = 2 * z + (e >> 2);
+        if (fx < X && fy < Y && fz < Z) s += __bfloat162float(a[(((size_t)fz * Y + fy) * X + fx) * C + c]);
+    }
+    b[q] = __float2bfloat16(0.125f * s);
+}
+// adjoint: each fine voxel receives 1/8 of its parent's gradient
+__global__ void k_pool_bwd(const __nv_bfloat16* gb, __nv_bfloat16* ga, int X, int Y, int Z, int C) {
+    const int Xc = (X + 1) / 2, Yc = (Y + 1) / 2;
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (size_t)X * Y * Z * C) return;
+    const int c = q % C;
+    size_t v = q / C;
+    const int x = v % X, yv = (v / X) % Y, z = v / ((size_t)X * Y);
+    ga[q] = __float2bfloat16(0.125f * __bfloat162float(gb[(((size_t)(z / 2) * Yc + yv / 2) * Xc + x / 2) * C + c]));
+}
+// nearest upsample: fine voxel takes its parent's value
+__global__ void k_up(const __nv_bfloat16* b, __nv_bfloat16* a, int X, int Y, int Z, int C) {
+    const int Xc = (X + 1) / 2, Yc = (Y + 1) / 2;
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (size_t)X * Y * Z * C) return;
+    const int c = q % C;
+    size_t v = q / C;
+    const int x = v % X, yv = (v / X) % Y, z = v / ((size_t)X * Y);
+    a[q] = b[(((size_t)(z / 2) * Yc + yv / 2) * Xc + x / 2) * C + c];
+}
+// adjoint: parent sums its (existing) children
+__global__ void k_up_bwd(const __nv_bfloat16* ga, __nv_bfloat16* gb, int X, int Y, int Z, int C) {
+    const int Xc = (X + 1) / 2, Yc = (Y + 1) / 2, Zc = (Z + 1) / 2;
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (size_t)Xc * Yc * Zc * C) return;
+    const int c = q % C;
+    size_t v = q / C;
+    const int x = v % Xc, yv = (v / Xc) % Yc, z = v / ((size_t)Xc * Yc);
+    float s = 0.f;
+    for (int e = 0; e < 8; ++e) {
+        const int fx = 2 * x + (e & 1), fy = 2 * yv + ((e >> 1) & 1), fz = 2 * z + (e >> 2);
+        if (fx < X && fy < Y && fz < Z) s += __bfloat162float(ga[(((size_t)fz * Y + fy) * X + fx) * C + c]);
+    }
+    gb[q] = __float2bfloat16(s);
+}
+// g_pre = g_post * (post > 0); optional extra gradient added first (skip branch)
+__global__ void k_relu_bwd(const __nv_bfloat16* post, const __nv_bfloat16* g, const __nv_bfloat16* g2,
+                           __nv_bfloat16* out, size_t n) {
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    float v = __bfloat162float(g[q]) + (g2 ? __bfloat162float(g2[q]) : 0.f);
+    out[q] = __float2bfloat16(__bfloat162float(post[q]) > 0.f ? v : 0.f);
+}
+__global__ void k_add(const __nv_bfloat16* a, const __nv_bfloat16* b, __nv_bfloat16* out, size_t n) {
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    out[q] = __float2bfloat16(__bfloat162float(a[q]) + __bfloat162float(b[q]));
+}
+
+// head: y[v] = mask[v] * sum_c w1[c] * d[v][c]  (FP32 output)
+__global__ void k_head(const __nv_bfloat16* d, const float* w1, const float* mask, float* y, size_t nv, int C) {
+    const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    float s = 0.f;
+    for (int c = 0; c < C; ++c) s += w1[c] * __bfloat162float(d[v * C + c]);
+    y[v] = mask[v] * s;
+}
+// head backward: gd[v][c] = gy[v]*mask[v]*w1[c]; dw1[c] += sum_v gy[v]*mask[v]*d[v][c]
+__global__ void k_head_bwd(const __nv_bfloat16* d, const float* w1, const float* mask, const float* gy,
+                           __nv_bfloat16* gd, float* dw1, size_t nv, int C) {
+    __shared__ float part[16][17];
+    const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float loc[16];
+    for (int c = 0; c < 16; ++c) loc[c] = 0.f;
+    if (v < nv) {
+        const float gm = gy[v] * mask[v];
+        for (int c = 0; c < C; ++c) {
+            gd[v * C + c] = __float2bfloat16(gm * w1[c]);
+            loc[c] = gm * __bfloat162float(d[v * C + c]);
+        }
+    }
+    for (int c = 0; c < 16; ++c)
+        for (int o = 16; o > 0; o >>= 1) loc[c] += __shfl_down_sync(0xffffffffu, loc[c], o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int c = 0; c < 16; ++c) part[warp][c] = loc[c];
+    __syncthreads();
+    if (threadIdx.x < C) {
+        float s = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w][threadIdx.x];
+        atomicAdd(&dw1[threadIdx.x], s);
+    }
+}
+
+// network input: channel 0 = r / scale, channel 1 = fluid mask, 2..15 = 0;
+// from a padded cell array of the solver (field type float)
+__global__ void k_pack_input(const float* r, const uint8_t* flags, Dom d, const double* scale, __nv_bfloat16* xin,
+                             float* mask) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y, k = blockIdx.z;
+    if (i >= d.nx) return;
+    const long long c = d.at(i + 1, j + 1, k + 1);
+    const size_t v = ((size_t)k * d.ny + j) * d.nx + i;
+    const bool unk = flags[c] & F_UNK;
+    const float s = (float)(*scale > 0.0 ? 1.0 / *scale : 0.0);
+    __nv_bfloat16* o = xin + v * 16;
+    o[0] = __float2bfloat16(unk ? r[c] * s : 0.f);
+    o[1] = __float2bfloat16(unk ? 1.f : 0.f);
+    for (int ch = 2; ch < 16; ++ch) o[ch] = __float2bfloat16(0.f);
+    mask[v] = unk ? 1.f : 0.f;
+}
+
+// training loss 1/n * sum mask (y - t)^2 and its gradient
+__global__ void k_mse(const float* y, const float* t, const float* mask, float* g, double* loss, size_t n, double inv_n) {
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double e2 = 0.0;
+    if (q < n) {
+        const float e = mask[q] * (y[q] - t[q]);
+        g[q] = (float)(2.0 * inv_n) * e;
+        e2 = (double)e * e;
+    }
+    for (int o = 16; o > 0; o >>= 1) e2 += __shfl_down_sync(0xffffffffu, e2, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, e2 * inv_n);
+}
+
+// Adam on FP32 master weights, refreshing the BF16 copy
+__global__ void k_adam(float* w, float* m, float* v, const float* g, __nv_bfloat16* wb, size_t n, float lr, float b1,
+                       float b2, float eps, float c1, float c2) {
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const float gq = g[q];
+    const float mq = b1 * m[q] + (1.f - b1) * gq;
+    const float vq = b2 * v[q] + (1.f - b2) * gq * gq;
+    m[q] = mq;
+    v[q] = vq;
+    const float wq = w[q] - lr * (mq / c1) / (sqrtf(vq / c2) + eps);
+    w[q] = wq;
+    if (wb) wb[q] = __float2bfloat16(wq);
+}
+
+__global__ void k_to_bf16(const float* a, __nv_bfloat16* b, size_t n) {
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) b[q] = __float2bfloat16(a[q]);
+}
+
+static unsigned blocks_for(size_t n) { return (unsigned)((n + 255) / 256); }
+
+void pool(const __nv_bfloat16* a, __nv_bfloat16* b, int X, int Y, int Z, int C, cudaStream_t s) {
+    k_pool<<<blocks_for((size_t)((X + 1) / 2) * ((Y + 1) / 2) * ((Z + 1) / 2) * C), 256, 0, s>>>(a, b, X, Y, Z, C);
+}
+void pool_bwd(const __nv_bfloat16* gb, __nv_bfloat16* ga, int X, int Y, int Z, int C, cudaStream_t s) {
+    k_pool_bwd<<<blocks_for((size_t)X * Y * Z * C), 256, 0, s>>>(gb, ga, X, Y, Z, C);
+}
+void up(const __nv_bfloat16* b, __nv_bfloat16* a, int X, int Y, int Z, int C, cudaStream_t s) {
+    k_up<<<blocks_for((size_t)X * Y * Z * C), 256, 0, s>>>(b, a, X, Y, Z, C);
+}
+void up_bwd(const __nv_bfloat16* ga, __nv_bfloat16* gb, int X, int Y, int Z, int C, cudaStream_t s) {
+    k_up_bwd<<<blocks_for((size_t)((X + 1) / 2) * ((Y + 1) / 2) * ((Z + 1) / 2) * C), 256, 0, s>>>(ga, gb, X, Y, Z, C);
+}
+void relu_bwd(const __nv_bfloat16* post, const __nv_bfloat16* g, const __nv_bfloat16* g2, __nv_bfloat16* out,
+              size_t n, cudaStream_t s) {
+    k_relu_bwd<<<blocks_for(n), 256, 0, s>>>(post, g, g2, out, n);
+}
+void add(const __nv_bfloat16* a, const __nv_bfloat16* b, __nv_bfloat16* out, size_t n, cudaStream_t s) {
+    k_add<<<blocks_for(n), 256, 0, s>>>(a, b, out, n);
+}
+void head(const __nv_bfloat16* d, const float* w1, const float* mask, float* y, size_t nv, int C, cudaStream_t s) {
+    k_head<<<blocks_for(nv), 256, 0, s>>>(d, w1, mask, y, nv, C);
+}
+void head_bwd(const __nv_bfloat16* d, const float* w1, const float* mask, const float* gy, __nv_bfloat16* gd,
+              float* dw1, size_t nv, int C, cudaStream_t s) {
+    k_head_bwd<<<blocks_for(nv), 256, 0, s>>>(d, w1, mask, gy, gd, dw1, nv, C);
+}
+void pack_input(const float* r, const uint8_t* flags, const Dom& d, const double* scale, __nv_bfloat16* xin,
+                float* mask, cudaStream_t s) {
+    k_pack_input<<<dim3((d.nx + 127) / 128, d.ny, d.nz), 128, 0, s>>>(r, flags, d, scale, xin, mask);
+}
+void mse(const float* y, const float* t, const float* mask, float* g, double* loss, size_t n, double inv_n,
+         cudaStream_t s) {
+    k_mse<<<blocks_for(n), 256, 0, s>>>(y, t, mask, g, loss, n, inv_n);
+}
+void adam(float* w, float* m, float* v, const float* g, __nv_bfloat16* wb, size_t n, float lr, float b1, float b2,
+          float eps, float c1, float c2, cudaStream_t s) {
+    k_adam<<<blocks_for(n), 256, 0, s>>>(w, m, v, g, wb, n, lr, b1, b2, eps, c1, c2);
+}
+void to_bf16(const float* a, __nv_bfloat16* b, size_t n, cudaStream_t s) {
+    k_to_bf16<<<blocks_for(n), 256, 0, s>>>(a, b, n);
+}
+
+}  // namespace nn
+}  // namespace les

@@ -20,7 +20,8 @@ LES_EINVAL, LES_ENOMEM, LES_ECUDA, LES_ETIMEOUT, LES_ENONFINITE, LES_ESTATE = -1
 LES_BC_INOUT, LES_BC_FREESLIP, LES_BC_WALL, LES_BC_PERIODIC = 0, 1, 2, 3
 LES_FP32, LES_FP64 = 0, 1
 (LES_AUX_NUT, LES_AUX_RHS, LES_AUX_USTAR, LES_AUX_VSTAR, LES_AUX_WSTAR,
- LES_AUX_FU, LES_AUX_FV, LES_AUX_FW) = range(8)
+ LES_AUX_FU, LES_AUX_FV, LES_AUX_FW, LES_AUX_R0, LES_AUX_DELTA, LES_AUX_MASK) = range(11)
+LES_WARM_PREV, LES_WARM_NET = 0, 1
 
 
 class les_grid_t(ctypes.Structure):
@@ -85,6 +86,20 @@ def lib(build_if_missing: bool = False):
         L.les_set_state.argtypes = [vp, vp, ctypes.c_size_t]
         L.les_profiler_range.argtypes = [i32]
         L.les_residual_noalloc.argtypes = [ctypes.POINTER(les_grid_t), vp, vp, vp, vp, vp, vp]
+        L.les_set_record.argtypes = [vp, i32]
+        L.les_set_warmstart.argtypes = [vp, i32, vp]
+        L.les_net_create.argtypes = [ctypes.c_uint64, vp, ctypes.POINTER(vp)]
+        L.les_net_destroy.argtypes = [vp]
+        L.les_net_destroy.restype = None
+        L.les_net_last_error.argtypes = [vp]
+        L.les_net_last_error.restype = ctypes.c_char_p
+        L.les_net_num_params.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+        L.les_net_get_params.argtypes = [vp, vp]
+        L.les_net_set_params.argtypes = [vp, vp]
+        L.les_net_forward.argtypes = [vp, vp, vp, vp, i32, i32, i32]
+        L.les_net_gradient.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, vp, ctypes.POINTER(ctypes.c_double)]
+        L.les_net_train_step.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, ctypes.c_float,
+                                         ctypes.POINTER(ctypes.c_double)]
         L.les_set_graph.argtypes = [vp, i32]
         L.les_set_sor_config.argtypes = [vp, i32, i32]
         L.les_get_sor_config.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
@@ -92,7 +107,9 @@ def lib(build_if_missing: bool = False):
         L.les_autotune_sor.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
         L.les_set_timing.argtypes = [vp, i32]
         L.les_get_timing.argtypes = [vp, ctypes.POINTER(les_timing_t)]
-        for name in ("les_residual_noalloc", "les_profiler_range", "les_set_graph", "les_set_sor_config", "les_get_sor_config", "les_sor_tile", "les_autotune_sor",
+        for name in ("les_set_record", "les_set_warmstart", "les_net_create", "les_net_num_params",
+                     "les_net_get_params", "les_net_set_params", "les_net_forward", "les_net_gradient",
+                     "les_net_train_step", "les_residual_noalloc", "les_profiler_range", "les_set_graph", "les_set_sor_config", "les_get_sor_config", "les_sor_tile", "les_autotune_sor",
                      "les_set_timing", "les_get_timing", "les_create", "les_set_fields", "les_get_fields", "les_set_inflow", "les_step",
                      "les_pressure_solve", "les_get_aux", "les_get_state", "les_set_state"):
             getattr(L, name).restype = ctypes.c_int
@@ -178,6 +195,91 @@ def les_get_timing(h, t: les_timing_t):
 def les_residual_noalloc(grid: les_grid_t, d_p, d_rhs, d_solid, d_dz, d_out, stream=None):
     """Device pointers (ints) in, device pointer out; allocates nothing."""
     return _check(lib().les_residual_noalloc(ctypes.byref(grid), d_p, d_rhs, d_solid, d_dz, d_out, stream))
+
+
+def les_set_record(h, enable):
+    return _check(lib().les_set_record(h, 1 if enable else 0), h)
+
+
+def les_set_warmstart(h, mode, net):
+    return _check(lib().les_set_warmstart(h, mode, net), h)
+
+
+def _ncheck(rc, n):
+    if rc < 0:
+        m = lib().les_net_last_error(n)
+        raise LesError(rc, m.decode() if m else "")
+    return rc
+
+
+def les_net_create(seed, stream=None):
+    h = ctypes.c_void_p()
+    rc = lib().les_net_create(seed, stream, ctypes.byref(h))
+    if rc < 0:
+        raise LesError(rc, "les_net_create failed")
+    return h.value
+
+
+def les_net_destroy(n):
+    lib().les_net_destroy(n)
+
+
+def les_net_num_params(n):
+    c = ctypes.c_int64()
+    _ncheck(lib().les_net_num_params(n, ctypes.byref(c)), n)
+    return c.value
+
+
+def les_net_get_params(n, out):
+    return _ncheck(lib().les_net_get_params(n, _ptr(out)), n)
+
+
+def les_net_set_params(n, params):
+    return _ncheck(lib().les_net_set_params(n, _ptr(params)), n)
+
+
+def les_net_forward(n, d_r, d_mask, d_y, nx, ny, nz):
+    return _ncheck(lib().les_net_forward(n, d_r, d_mask, d_y, nx, ny, nz), n)
+
+
+def les_net_gradient(n, d_r, d_mask, d_t, batch, nx, ny, nz, d_grad):
+    loss = ctypes.c_double()
+    _ncheck(lib().les_net_gradient(n, d_r, d_mask, d_t, batch, nx, ny, nz, d_grad, ctypes.byref(loss)), n)
+    return loss.value
+
+
+def les_net_train_step(n, d_r, d_mask, d_t, batch, nx, ny, nz, lr):
+    loss = ctypes.c_double()
+    _ncheck(lib().les_net_train_step(n, d_r, d_mask, d_t, batch, nx, ny, nz, lr, ctypes.byref(loss)), n)
+    return loss.value
+
+
+class Net:
+    """The warm-start network (device weights owned by the library)."""
+
+    def __init__(self, seed=0, stream="torch"):
+        st = current_stream() if stream == "torch" else stream
+        self.h = les_net_create(seed, st)
+        self.nparam = les_net_num_params(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            les_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.nparam, np.float32)
+        les_net_get_params(self.h, out)
+        return out
+
+    def set_params(self, p):
+        les_net_set_params(self.h, np.ascontiguousarray(p, np.float32))
 
 
 def les_profiler_range(start):
@@ -294,7 +396,8 @@ class Domain:
 
     def aux(self, which) -> np.ndarray:
         nx, ny, nz = self.nx, self.ny, self.nz
-        shape = {LES_AUX_NUT: (nz, ny, nx), LES_AUX_RHS: (nz, ny, nx),
+        shape = {LES_AUX_NUT: (nz, ny, nx), LES_AUX_RHS: (nz, ny, nx), LES_AUX_R0: (nz, ny, nx),
+                 LES_AUX_DELTA: (nz, ny, nx), LES_AUX_MASK: (nz, ny, nx),
                  LES_AUX_USTAR: (nz, ny, nx + 1), LES_AUX_FU: (nz, ny, nx + 1),
                  LES_AUX_VSTAR: (nz, ny + 1, nx), LES_AUX_FV: (nz, ny + 1, nx),
                  LES_AUX_WSTAR: (nz + 1, ny, nx), LES_AUX_FW: (nz + 1, ny, nx)}[which]
@@ -312,6 +415,16 @@ class Domain:
     def set_state(self, blob: bytes):
         buf = ctypes.create_string_buffer(blob, len(blob))
         les_set_state(self.h, buf, len(blob))
+
+    def set_record(self, enable=True):
+        les_set_record(self.h, enable)
+
+    def set_warmstart(self, net=None):
+        if net is None:
+            les_set_warmstart(self.h, LES_WARM_PREV, None)
+        else:
+            les_set_warmstart(self.h, LES_WARM_NET, net.h)
+        self._net = net          # keep the network alive while the handle uses it
 
     def set_graph(self, enable=True):
         les_set_graph(self.h, enable)
