@@ -293,6 +293,7 @@ int les_residual_noalloc(const les_grid_t* grid, const void* d_p, const void* d_
 typedef struct les_net_s* les_net;
 #define LES_WARM_PREV 0      /* p0 = p from the previous step (the paper's scheme) */
 #define LES_WARM_NET 1       /* p0 = p_prev + alpha * network(r0) */
+#define LES_WARM_ZERO 2      /* p0 = 0 (cold start every step; a reference point for the two above) */
 int les_net_create(uint64_t seed, void* stream, les_net* out);
 void les_net_destroy(les_net n);
 const char* les_net_last_error(les_net n);

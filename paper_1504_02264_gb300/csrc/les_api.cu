@@ -313,13 +313,18 @@ CondArgs cond_args(const les_s* h, int mode, int n, int gate) {
 // then the residual again), and record the training pair when asked.
 template <typename T>
 int solve_start(les_s* h, const Geo<T>& g, cudaStream_t st) {
+    if (h->warm == LES_WARM_ZERO) {
+        CK(cudaMemsetAsync(h->ph[h->cur], 0, h->n * sizeof(double), st));
+        h->launches += launch_residual64<T>(g, h->ph[h->cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h),
+                                            cond_args(h, RES_INIT, 0, 0), st);
+    }
     if constexpr (std::is_same<T, float>::value) {
         if (h->warm == LES_WARM_NET && h->net) {
             h->launches += launch_warm<T>(g, (const T*)h->rr, h->pred, h->ph[h->cur], h->warm_scal, h->n_unk,
                                           reducer(h), 0, st);
             int rc = net_predict(h->net, h->d, (const float*)h->rr, h->flags, h->warm_scal, h->pred, st);
             if (rc) return fail(h, rc, "network prediction failed");
-            h->launches += 20;
+            h->launches += 15;      // pack, 7 convolutions, 3 pools, 3 upsamplings, head
             h->launches += launch_warm<T>(g, (const T*)h->rr, h->pred, h->ph[h->cur], h->warm_scal, h->n_unk,
                                           reducer(h), 1, st);
             h->launches += launch_residual64<T>(g, h->ph[h->cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h),
@@ -1032,7 +1037,7 @@ int les_step(les_handle h, int32_t nsteps, les_stats_t* stats) {
     // and a sweep budget made of whole batches; otherwise the host loop runs
     // (a fixed-sweep graph captures the whole step, so it runs without the
     // warm-start network and the recording; those use the chunked path)
-    const bool extras = h->record || h->warm == LES_WARM_NET;
+    const bool extras = h->record || h->warm != LES_WARM_PREV;
     const bool graph_ok = h->use_graph && !h->timing &&
                           ((h->g.fixed_sweeps && !extras) ||
                            (!h->g.fixed_sweeps && h->g.check_every % 2 == 0 && h->g.max_sweeps % h->g.check_every == 0));
@@ -1171,8 +1176,8 @@ int les_autotune_sor(les_handle h, int32_t sweeps, double* best_ms_per_sweep) {
 
 int les_set_warmstart(les_handle h, int32_t mode, les_net net) {
     if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
-    if (mode == LES_WARM_PREV) {
-        h->warm = LES_WARM_PREV;
+    if (mode == LES_WARM_PREV || mode == LES_WARM_ZERO) {
+        h->warm = mode;
         h->net = nullptr;
         return LES_OK;
     }

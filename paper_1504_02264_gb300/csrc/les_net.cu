@@ -190,7 +190,10 @@ int ensure_ws(les_net_s* n, const Level& L0) {
     if ((rc = get(vol(1) * 32, B, (void**)&n->gd1))) return rc;
     if ((rc = get(vol(2) * 64, B, (void**)&n->gd2))) return rc;
     if ((rc = get(vol(3) * 128, B, (void**)&n->ge3))) return rc;
-    if ((rc = get(vol(0) * 16, B, (void**)&n->gpb))) return rc;
+    // pooled-branch gradient: level l (l = 0..2) with ce[l] channels
+    size_t pmax = 0;
+    for (int l = 0; l < 3; ++l) pmax = vol(l) * ce[l] > pmax ? vol(l) * ce[l] : pmax;
+    if ((rc = get(pmax, B, (void**)&n->gpb))) return rc;
     if ((rc = get(vol(0), sizeof(float), (void**)&n->y))) return rc;
     if ((rc = get(vol(0), sizeof(float), (void**)&n->gy))) return rc;
     if ((rc = get(vol(0), sizeof(float), (void**)&n->mask))) return rc;

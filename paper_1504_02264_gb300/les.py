@@ -21,7 +21,7 @@ LES_BC_INOUT, LES_BC_FREESLIP, LES_BC_WALL, LES_BC_PERIODIC = 0, 1, 2, 3
 LES_FP32, LES_FP64 = 0, 1
 (LES_AUX_NUT, LES_AUX_RHS, LES_AUX_USTAR, LES_AUX_VSTAR, LES_AUX_WSTAR,
  LES_AUX_FU, LES_AUX_FV, LES_AUX_FW, LES_AUX_R0, LES_AUX_DELTA, LES_AUX_MASK) = range(11)
-LES_WARM_PREV, LES_WARM_NET = 0, 1
+LES_WARM_PREV, LES_WARM_NET, LES_WARM_ZERO = 0, 1, 2
 
 
 class les_grid_t(ctypes.Structure):
@@ -419,11 +419,12 @@ class Domain:
     def set_record(self, enable=True):
         les_set_record(self.h, enable)
 
-    def set_warmstart(self, net=None):
-        if net is None:
-            les_set_warmstart(self.h, LES_WARM_PREV, None)
-        else:
+    def set_warmstart(self, net=None, mode=None):
+        """net given: learned warm start; else mode LES_WARM_PREV (default) or LES_WARM_ZERO."""
+        if net is not None:
             les_set_warmstart(self.h, LES_WARM_NET, net.h)
+        else:
+            les_set_warmstart(self.h, LES_WARM_PREV if mode is None else mode, None)
         self._net = net          # keep the network alive while the handle uses it
 
     def set_graph(self, enable=True):

@@ -1,0 +1,242 @@
+"""GPU tests of the learned SOR warm start: the BF16 tensor-core network
+against the FP64 NumPy network oracle (forward and gradient), its training
+step, the recording of training pairs, and the warm start inside the solver.
+
+Tolerances.  The GPU network stores activations and activation gradients in
+BF16 (unit roundoff u = 2^-9) and accumulates in FP32.  The longest forward
+chain rounds about 14 times (input, 7 convolution outputs, 3 pools, 3 skip
+sums), so the worst-case relative error is ~14u = 2.7% and the random-walk
+estimate sqrt(14)u = 0.7%; the forward bar is 2% in relative L2 norm.  The
+backward pass adds about as many roundings again: 5% per layer gradient, with
+the direction (cosine) within 0.998.  The oracle uses the same BF16-rounded
+convolution weights, so weight rounding is not part of the comparison."""
+
+import numpy as np
+import pytest
+
+from oracle import net_oracle
+from oracle.oracle import Oracle
+from paper_1504_02264_gb300 import scene
+
+pytestmark = pytest.mark.gpu
+
+les = pytest.importorskip("paper_1504_02264_gb300.les")
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    les.lib()
+    yield
+
+
+def bf16_round(a):
+    """Round float32 values to the nearest bfloat16 (ties to even), kept as float32."""
+    u = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def oracle_theta(theta32):
+    """The parameters the GPU computes with: BF16 convolution weights, FP32 head."""
+    t = theta32.astype(np.float32).copy()
+    nh = net_oracle.HEAD
+    t[:-nh] = bf16_round(t[:-nh])
+    return t.astype(np.float64)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def sample(rng, shape, fluid=0.8):
+    r = rng.standard_normal(shape)
+    # smooth-ish residual plus noise, like an SOR residual
+    mask = (rng.random(shape) < fluid).astype(np.float64)
+    return r * mask, mask
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+@pytest.fixture()
+def net():
+    n = les.Net(seed=11)
+    yield n
+    torch.cuda.synchronize()
+    n.close()
+
+
+def test_param_count_and_roundtrip(net):
+    ws = [27 * ci * co for ci, co in zip(net_oracle.CIN, net_oracle.COUT)]
+    assert net.nparam == sum(ws) + net_oracle.HEAD
+    theta = net_oracle.init_params(5).astype(np.float32)
+    net.set_params(theta)
+    assert np.array_equal(net.params(), theta)
+    assert np.all(np.isfinite(net.params()))
+
+
+@pytest.mark.parametrize("shape", [(7, 11, 37), (1, 1, 1), (5, 9, 16), (3, 4, 17)])
+def test_forward_matches_oracle(net, shape):
+    """(nz, ny, nx) = 7x11x37 spans 3x3x4 tiles with ragged tails on every level."""
+    rng = np.random.default_rng(sum(shape))
+    theta = net_oracle.init_params(7).astype(np.float32)
+    net.set_params(theta)
+    r, mask = sample(rng, shape)
+    if mask.sum() == 0:
+        mask.flat[0] = 1.0
+    y = torch.empty(shape, dtype=torch.float32, device="cuda")
+    dr, dm = dev(r), dev(mask)
+    nz, ny, nx = shape
+    les.les_net_forward(net.h, dr.data_ptr(), dm.data_ptr(), y.data_ptr(), nx, ny, nz)
+    yg = y.cpu().numpy().astype(np.float64)
+    yo, _ = net_oracle.forward(oracle_theta(theta), r.astype(np.float32).astype(np.float64), mask)
+    assert np.all(yg[mask == 0] == 0.0)
+    err = rel_l2(yg, yo)
+    assert err <= 2e-2, err
+    assert np.abs(yg - yo).max() <= 5e-2 * np.abs(yo).max()
+
+
+def test_forward_scale_invariant(net):
+    """The input is normalised by its RMS: r and 2r give bit-identical outputs."""
+    rng = np.random.default_rng(1)
+    shape = (6, 10, 20)
+    r, mask = sample(rng, shape)
+    nz, ny, nx = shape
+    ys = []
+    for s in (1.0, 2.0):
+        y = torch.empty(shape, dtype=torch.float32, device="cuda")
+        dr, dm = dev(r * s), dev(mask)
+        les.les_net_forward(net.h, dr.data_ptr(), dm.data_ptr(), y.data_ptr(), nx, ny, nz)
+        ys.append(y.cpu().numpy())
+    assert np.array_equal(ys[0], ys[1])
+
+
+def test_gradient_matches_oracle(net):
+    rng = np.random.default_rng(2)
+    shape, B = (5, 9, 21), 2
+    theta = net_oracle.init_params(9).astype(np.float32)
+    net.set_params(theta)
+    rs, ms, ts = [], [], []
+    for _ in range(B):
+        r, m = sample(rng, shape)
+        t = rng.standard_normal(shape) * m
+        rs.append(r.astype(np.float32)); ms.append(m); ts.append(t.astype(np.float32))
+    nz, ny, nx = shape
+    dr, dm, dt = dev(np.stack(rs)), dev(np.stack(ms)), dev(np.stack(ts))
+    g = torch.empty(net.nparam, dtype=torch.float32, device="cuda")
+    L = les.les_net_gradient(net.h, dr.data_ptr(), dm.data_ptr(), dt.data_ptr(), B, nx, ny, nz, g.data_ptr())
+    Lo, go = net_oracle.loss_and_grad(oracle_theta(theta), [x.astype(np.float64) for x in rs], ms,
+                                      [x.astype(np.float64) for x in ts])
+    assert abs(L - Lo) <= 2e-2 * abs(Lo), (L, Lo)
+    gg = g.cpu().numpy().astype(np.float64)
+    o = 0
+    for k, (ci, co) in enumerate(zip(net_oracle.CIN, net_oracle.COUT)):
+        n = 27 * ci * co
+        a, b = gg[o:o + n], go[o:o + n]
+        cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
+        assert rel_l2(a, b) <= 5e-2 and cos >= 0.998, (k, rel_l2(a, b), cos)
+        o += n
+    assert rel_l2(gg[o:], go[o:]) <= 5e-2
+
+
+def test_train_step_reduces_loss(net):
+    rng = np.random.default_rng(3)
+    shape, B = (8, 12, 24), 4
+    nz, ny, nx = shape
+    rs, ms, ts = [], [], []
+    for _ in range(B):
+        m = (rng.random(shape) < 0.85).astype(np.float32)
+        t = rng.standard_normal(shape).astype(np.float32)
+        # a target the network can fit: a smoothed version of the input
+        r = t.copy()
+        for ax in range(3):
+            r = 0.5 * r + 0.25 * (np.roll(r, 1, ax) + np.roll(r, -1, ax))
+        rs.append(r * m); ms.append(m); ts.append(t * m)
+    dr, dm, dt = dev(np.stack(rs)), dev(np.stack(ms)), dev(np.stack(ts))
+    losses = [les.les_net_train_step(net.h, dr.data_ptr(), dm.data_ptr(), dt.data_ptr(), B, nx, ny, nz, 1e-3)
+              for _ in range(40)]
+    assert np.all(np.isfinite(losses))
+    assert losses[-1] < 0.8 * losses[0], losses[::8]
+
+
+def city(nx=48, ny=32, nz=16, seed=4, **kw):
+    rng = np.random.default_rng(seed)
+    solid = np.zeros((nz, ny, nx), np.uint8)
+    for _ in range(5):
+        x0 = int(rng.integers(8, nx - 12))
+        y0 = int(rng.integers(1, ny - 7))
+        h = int(rng.integers(3, nz - 3))
+        solid[:h, y0:y0 + 6, x0:x0 + 6] = 1
+    bc = (scene.BC_INOUT, scene.BC_FREESLIP, scene.BC_WALL)
+    return scene.box_scene(nx, ny, nz, dz=scene.stretched_dz(nz), solid=solid, bc=bc, turb=0.1, seed=seed,
+                           **kw)
+
+
+def test_recorded_pair_solves_the_system():
+    """The recorded correction delta of a converged solve satisfies A delta = r0
+    to the solve's tolerance (FP64 grid, checked with the oracle's operator)."""
+    sc = city(tol=1e-8, max_sweeps=40000, check_every=20)
+    dom = les.Domain(sc, precision=les.LES_FP64)
+    dom.set_record(True)
+    for _ in range(3):
+        st = dom.step()
+        assert st["rc"] == 0 and st["rel_residual"] <= 1e-8
+    r0 = dom.aux(les.LES_AUX_R0)
+    delta = dom.aux(les.LES_AUX_DELTA)
+    mask = dom.aux(les.LES_AUX_MASK)
+    o = Oracle(sc)
+    Ad = o.apply_A(delta)
+    assert np.all(delta[mask == 0] == 0) and np.all(r0[mask == 0] == 0)
+    err = np.linalg.norm((Ad - r0)[mask == 1])
+    assert err <= 1.01e-8 * st["rhs_norm"] + 1e-12 * np.linalg.norm(r0), (err, st["rhs_norm"])
+    assert np.linalg.norm(r0) > 10 * err          # the pair is not trivial
+    dom.close()
+
+
+def test_warm_start_never_worse_and_converges(net):
+    """With an (untrained) network the line search keeps p0 no worse than
+    p_prev, every step still converges to the same tolerance, and the cold
+    start needs more sweeps than either warm start."""
+    sc = city(tol=1e-6, max_sweeps=40000, check_every=20)
+    doms = {m: les.Domain(sc) for m in ("prev", "net", "zero")}
+    doms["net"].set_warmstart(net)
+    doms["zero"].set_warmstart(mode=les.LES_WARM_ZERO)
+    for d in doms.values():
+        d.set_record(True)
+    sweeps = {m: [] for m in doms}
+    for _ in range(4):
+        for m, d in doms.items():
+            st = d.step()
+            assert st["rc"] == 0 and st["rel_residual"] <= 1e-6, (m, st)
+            sweeps[m].append(st["sweeps"])
+    # one pressure solve from the same state: the recorded initial residual of
+    # the network start is no larger than that of the previous-step start
+    state = doms["prev"].get_state()
+    doms["net"].set_state(state)
+    rhs = doms["prev"].aux(les.LES_AUX_RHS)
+    doms["prev"].pressure_solve(rhs)
+    doms["net"].pressure_solve(rhs)
+    r_prev = np.linalg.norm(doms["prev"].aux(les.LES_AUX_R0))
+    r_net = np.linalg.norm(doms["net"].aux(les.LES_AUX_R0))
+    assert r_net <= r_prev * (1 + 1e-5), (r_net, r_prev)
+    assert sum(sweeps["zero"]) > sum(sweeps["prev"])
+    for d in doms.values():
+        d.close()
+
+
+def test_warm_start_rejects_bad_use(net):
+    sc = city()
+    d64 = les.Domain(sc, precision=les.LES_FP64)
+    with pytest.raises(les.LesError):
+        d64.set_warmstart(net)
+    d32 = les.Domain(sc)
+    with pytest.raises(les.LesError):
+        d32.aux(les.LES_AUX_R0)                 # recording is off
+    with pytest.raises(les.LesError):
+        les.les_set_warmstart(d32.h, 7, None)
+    d64.close()
+    d32.close()
