@@ -173,6 +173,14 @@ int les_get_aux(les_handle h, int32_t which, void* out);
  * solve (LES_AUX_R0 / LES_AUX_DELTA), the training pairs of the warm-start
  * network.  Costs two device copies per solve while on. */
 int les_set_record(les_handle h, int32_t enable);
+/* les_set_record_at: take the recorded pair at the first FP64 refinement at
+ * or after `after_sweeps` sweeps instead of at the start of the solve: the
+ * residual r_k of the iterate p_k there and the remaining correction
+ * p_solved - p_k (the pairs a network applied inside the solve sees).
+ * 0 = at the start (default).  A value > 0 runs solves from the host loop.
+ * A solve that passes the stop test before the record point records no
+ * pair: LES_AUX_R0 / LES_AUX_DELTA then return LES_ESTATE until one does. */
+int les_set_record_at(les_handle h, int32_t after_sweeps);
 
 /*
  * Checkpoint / restart: the full state (velocities, p, AB2 history, step
@@ -277,9 +285,10 @@ int les_residual_noalloc(const les_grid_t* grid, const void* d_p, const void* d_
  * upsampling, additive skips, 1x1x1 head) maps the solve's initial residual
  * r0 = rhs - mean - A p_prev (scaled to unit RMS) and the unknown mask to a
  * correction direction q.  The solver then takes p0 = p_prev + alpha q with
- * alpha minimising ||r0 - alpha A q|| in FP64 (so p0 is never worse than
- * p_prev) and runs the same red-black SOR to the same tolerance: plain SOR
- * stays the stop test.  Activations are BF16, accumulation FP32, on the
+ * alpha = <q, V r0> / <q, V A q> in FP64 (V = diag(dz_k); V A is symmetric),
+ * the minimiser of the energy norm of the error along q, so p0 is never
+ * further from the solution than p_prev in that norm, and runs the same
+ * red-black SOR to the same tolerance: plain SOR stays the stop test.  Activations are BF16, accumulation FP32, on the
  * tensor cores (mma.sync m16n8k16).  Training runs on the GPU with the
  * network's own backward kernels and Adam.
  *
@@ -308,6 +317,13 @@ int les_net_train_step(les_net n, const float* d_r, const float* d_mask, const f
 /* les_set_warmstart: LES_WARM_NET needs an FP32 grid; the handle keeps the
  * network pointer (the caller keeps it alive). */
 int les_set_warmstart(les_handle h, int32_t mode, les_net net);
+/* les_set_net_schedule: with LES_WARM_NET, also apply the network inside the
+ * solve every `every_sweeps` sweeps (at an FP64 refinement: q = Net(r_k),
+ * p += alpha q with the energy-norm step, residual formed again), i.e. the
+ * network as a coarse correction between SOR batches.  0 = only at the
+ * start (default).  A value > 0 runs solves from the host loop.  The stop
+ * test is unchanged. */
+int les_set_net_schedule(les_handle h, int32_t every_sweeps);
 
 /* Bracket a region for a profiler started with capture off
  * (cudaProfilerStart when start != 0, cudaProfilerStop otherwise). */

@@ -124,7 +124,11 @@ struct les_s {
     float* pred = nullptr;                // dense (nz, ny, nx) predicted correction
     double* warm_scal = nullptr;          // [0] input scale, [1] line-search step
     double n_unk = 0.0;                   // number of Poisson unknowns
+    int net_every = 0;                    // sweeps between network corrections inside a solve (0: start only)
     bool record = false;
+    int rec_after = 0;                    // record at the first refinement after this many sweeps
+    bool rec_taken = false;               // the current solve has taken its pair's input
+    bool rec_valid = false;               // the last solve recorded a complete pair
     double* rec_p0 = nullptr;             // pressure before the last solve
     void* rec_r0 = nullptr;               // initial residual of the last solve
     void* rec_delta = nullptr;            // correction applied by the last solve
@@ -308,9 +312,34 @@ CondArgs cond_args(const les_s* h, int mode, int n, int gate) {
     return ca;
 }
 
-// After the first FP64 residual of a solve: optionally move p along the
-// network's predicted correction (FP64 line search, never worse than p_prev,
-// then the residual again), and record the training pair when asked.
+// Move p along the network's predicted correction q = Net(r / rms(r)) with
+// the energy-norm line search, then form the FP64 residual again (`mode` is
+// RES_INIT at the start of a solve, RES_LOOP inside it, where the new
+// residual may already pass the stop test).
+template <typename T>
+int net_correct(les_s* h, const Geo<T>& g, int mode, cudaStream_t st) {
+    h->launches += launch_warm<T>(g, (const T*)h->rr, h->pred, h->ph[h->cur], h->warm_scal, h->n_unk, reducer(h), 0,
+                                  st);
+    int rc = net_predict(h->net, h->d, (const float*)h->rr, h->flags, h->warm_scal, h->pred, st);
+    if (rc) return fail(h, rc, "network prediction failed");
+    h->launches += 15;      // pack, 7 convolutions, 3 pools, 3 upsamplings, head
+    h->launches += launch_warm<T>(g, (const T*)h->rr, h->pred, h->ph[h->cur], h->warm_scal, h->n_unk, reducer(h), 1,
+                                  st);
+    h->launches += launch_residual64<T>(g, h->ph[h->cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h),
+                                        cond_args(h, mode, 0, 0), st);
+    CK(cudaGetLastError());
+    return LES_OK;
+}
+
+void record_start(les_s* h, cudaStream_t st) {
+    cudaMemcpyAsync(h->rec_p0, h->ph[h->cur], h->n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(h->rec_r0, h->rr, h->n * h->es, cudaMemcpyDeviceToDevice, st);
+    h->rec_taken = true;
+}
+
+// After the first FP64 residual of a solve: the cold start (p = 0) or the
+// learned warm start, then the recording of the training pair's input when
+// it is taken at the start.
 template <typename T>
 int solve_start(les_s* h, const Geo<T>& g, cudaStream_t st) {
     if (h->warm == LES_WARM_ZERO) {
@@ -320,28 +349,20 @@ int solve_start(les_s* h, const Geo<T>& g, cudaStream_t st) {
     }
     if constexpr (std::is_same<T, float>::value) {
         if (h->warm == LES_WARM_NET && h->net) {
-            h->launches += launch_warm<T>(g, (const T*)h->rr, h->pred, h->ph[h->cur], h->warm_scal, h->n_unk,
-                                          reducer(h), 0, st);
-            int rc = net_predict(h->net, h->d, (const float*)h->rr, h->flags, h->warm_scal, h->pred, st);
-            if (rc) return fail(h, rc, "network prediction failed");
-            h->launches += 15;      // pack, 7 convolutions, 3 pools, 3 upsamplings, head
-            h->launches += launch_warm<T>(g, (const T*)h->rr, h->pred, h->ph[h->cur], h->warm_scal, h->n_unk,
-                                          reducer(h), 1, st);
-            h->launches += launch_residual64<T>(g, h->ph[h->cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h),
-                                                cond_args(h, RES_INIT, 0, 0), st);
+            int rc = net_correct<T>(h, g, RES_INIT, st);
+            if (rc) return rc;
         }
     }
-    if (h->record) {
-        CK(cudaMemcpyAsync(h->rec_p0, h->ph[h->cur], h->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        CK(cudaMemcpyAsync(h->rec_r0, h->rr, h->n * h->es, cudaMemcpyDeviceToDevice, st));
-    }
+    h->rec_taken = false;
+    if (h->record && h->rec_after == 0) record_start(h, st);
     CK(cudaGetLastError());
     return LES_OK;
 }
 
 template <typename T>
 int solve_end(les_s* h, const Geo<T>& g, cudaStream_t st) {
-    if (h->record) {
+    h->rec_valid = h->record && h->rec_taken;
+    if (h->rec_valid) {
         h->launches += launch_record<T>(g, h->ph[h->cur], h->rec_p0, (T*)h->rec_delta, 0, st);
         CK(cudaGetLastError());
     }
@@ -374,9 +395,17 @@ int sor_solve(les_s* h) {
         int rs = solve_start<T>(h, g, h->stream);
         if (rs) return rs;
     }
-    int sweeps = 0;
+    int sweeps = 0, last_net = 0;
     bool fresh = true, conv = false;
-    while (sweeps < G.max_sweeps) {
+    bool recorded = !h->record || h->rec_taken;
+    const bool net_loop = std::is_same<T, float>::value && h->warm == LES_WARM_NET && h->net && h->net_every > 0;
+    if (!G.fixed_sweeps && h->warm != LES_WARM_PREV) {
+        // the start of the solve moved p: its residual may already pass the test
+        int rc = fetch_scalars(h);
+        if (rc) return rc;
+        conv = h->sc_host->converged != 0;
+    }
+    while (sweeps < G.max_sweeps && !conv) {
         const int n = G.fixed_sweeps ? G.max_sweeps
                                      : (G.check_every < G.max_sweeps - sweeps ? G.check_every : G.max_sweeps - sweeps);
         rec(h, 2);
@@ -403,7 +432,9 @@ int sor_solve(les_s* h) {
             h->tm.sor_launches += nl;
         }
         fresh = false;
-        if (need) {
+        const bool net_due = net_loop && sweeps - last_net >= h->net_every && sweeps < G.max_sweeps;
+        const bool rec_due = !recorded && sweeps >= h->rec_after;
+        if (need || net_due || rec_due) {
             rec(h, 3);
             launch_refine<T>(h, g, cond_args(h, G.fixed_sweeps ? RES_FIXED : RES_LOOP, n, 0), h->stream);
             rec(h, 4);
@@ -414,6 +445,19 @@ int sor_solve(les_s* h) {
             fresh = true;
             conv = h->sc_host->converged != 0;
             if (conv || h->sc_host->nonfinite) break;
+            if (rec_due) {
+                record_start(h, h->stream);
+                recorded = true;
+            }
+            if constexpr (std::is_same<T, float>::value) {
+                if (net_due) {
+                    last_net = sweeps;
+                    if ((rc = net_correct<T>(h, g, RES_LOOP, h->stream))) return rc;
+                    if ((rc = fetch_scalars(h))) return rc;
+                    conv = h->sc_host->converged != 0;
+                    if (conv || h->sc_host->nonfinite) break;
+                }
+            }
         }
     }
     h->sc_host->sweeps = sweeps;
@@ -891,12 +935,11 @@ int get_aux_impl(les_s* h, int which, void* out) {
         case LES_AUX_FV: src = h->fv; stag = 2; break;
         case LES_AUX_FW: src = h->fw; stag = 3; break;
         case LES_AUX_R0:
-            if (!h->record) return fail(h, LES_EINVAL, "recording is off (les_set_record)");
-            src = h->rec_r0;
-            break;
         case LES_AUX_DELTA:
             if (!h->record) return fail(h, LES_EINVAL, "recording is off (les_set_record)");
-            src = h->rec_delta;
+            if (!h->rec_valid)
+                return fail(h, LES_ESTATE, "the last solve recorded no pair (it ended before the record point)");
+            src = which == LES_AUX_R0 ? h->rec_r0 : h->rec_delta;
             break;
         case LES_AUX_MASK: {
             Geo<T> g = geo<T>(h);
@@ -1037,8 +1080,11 @@ int les_step(les_handle h, int32_t nsteps, les_stats_t* stats) {
     // and a sweep budget made of whole batches; otherwise the host loop runs
     // (a fixed-sweep graph captures the whole step, so it runs without the
     // warm-start network and the recording; those use the chunked path)
+    // network corrections inside a solve and recording after the start run
+    // from the host loop
     const bool extras = h->record || h->warm != LES_WARM_PREV;
-    const bool graph_ok = h->use_graph && !h->timing &&
+    const bool host_only = (h->warm == LES_WARM_NET && h->net_every > 0) || (h->record && h->rec_after > 0);
+    const bool graph_ok = h->use_graph && !h->timing && !host_only &&
                           ((h->g.fixed_sweeps && !extras) ||
                            (!h->g.fixed_sweeps && h->g.check_every % 2 == 0 && h->g.max_sweeps % h->g.check_every == 0));
     h->last_graph = graph_ok;
@@ -1190,6 +1236,20 @@ int les_set_warmstart(les_handle h, int32_t mode, les_net net) {
     }
     h->warm = LES_WARM_NET;
     h->net = net;
+    return LES_OK;
+}
+
+int les_set_net_schedule(les_handle h, int32_t every_sweeps) {
+    if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
+    if (every_sweeps < 0) return fail(h, LES_EINVAL, "every_sweeps must be >= 0");
+    h->net_every = every_sweeps;
+    return LES_OK;
+}
+
+int les_set_record_at(les_handle h, int32_t after_sweeps) {
+    if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
+    if (after_sweeps < 0) return fail(h, LES_EINVAL, "after_sweeps must be >= 0");
+    h->rec_after = after_sweeps;
     return LES_OK;
 }
 

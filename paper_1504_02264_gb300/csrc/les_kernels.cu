@@ -892,7 +892,12 @@ __global__ void k_warm_scale(const Scalars* sc, double n_unk, double* out) {
     out[0] = n_unk > 0.0 ? sqrt(sc->res2 / n_unk) : 0.0;
 }
 
-// alpha = <r, A q> / <A q, A q> over the unknowns (FP64), q the prediction
+// alpha minimising the energy norm of the error along q (FP64):
+//   alpha = <q, V r> / <q, V A q>,  V = diag(dz_k) (the cell volumes up to dx dy),
+// which makes V A symmetric, so this is the exact minimiser of
+// (e - alpha q)^T (-V A) (e - alpha q) with A e = r.  Smooth predictions with
+// some high-frequency noise keep a useful step (the residual-norm minimiser
+// <r, A q> / <A q, A q> would be dominated by A's amplified noise).
 template <typename T>
 __global__ void k_warm_ls(Geo<T> g, const T* r, const float* q, double* alpha, Reduce red) {
     const Dom& d = g.d;
@@ -904,6 +909,8 @@ __global__ void k_warm_ls(Geo<T> g, const T* r, const float* q, double* alpha, R
         const long long c = d.at(i, j, k);
         const uint8_t f = g.flags[c];
         if (f & F_UNK) {
+            // flags never open a face across a non-periodic domain boundary,
+            // so every neighbour read below stays inside the dense array
             auto dense = [&](int a, int b, int cc) -> double {
                 if (d.perx) a = a < 1 ? a + d.nx : (a > d.nx ? a - d.nx : a);
                 if (d.pery) b = b < 1 ? b + d.ny : (b > d.ny ? b - d.ny : b);
@@ -921,12 +928,16 @@ __global__ void k_warm_ls(Geo<T> g, const T* r, const float* q, double* alpha, R
             if (as != 0.0) aq += as * (dense(i, j - 1, k) - qc);
             if (at != 0.0) aq += at * (dense(i, j, k + 1) - qc);
             if (ab != 0.0) aq += ab * (dense(i, j, k - 1) - qc);
-            x[0] = (double)r[c] * aq;
-            x[1] = aq * aq;
+            const double vol = g.dz64[k];
+            x[0] = vol * qc * (double)r[c];
+            x[1] = vol * qc * aq;
         }
     }
     if (grid_sum<2>(x, red)) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) *alpha = (x[1] > 0.0 && isfinite(x[0] / x[1])) ? x[0] / x[1] : 0.0;
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            const double a = x[0] / x[1];
+            *alpha = (x[1] != 0.0 && isfinite(a)) ? a : 0.0;
+        }
     }
 }
 

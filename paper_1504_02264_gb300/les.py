@@ -87,6 +87,8 @@ def lib(build_if_missing: bool = False):
         L.les_profiler_range.argtypes = [i32]
         L.les_residual_noalloc.argtypes = [ctypes.POINTER(les_grid_t), vp, vp, vp, vp, vp, vp]
         L.les_set_record.argtypes = [vp, i32]
+        L.les_set_record_at.argtypes = [vp, i32]
+        L.les_set_net_schedule.argtypes = [vp, i32]
         L.les_set_warmstart.argtypes = [vp, i32, vp]
         L.les_net_create.argtypes = [ctypes.c_uint64, vp, ctypes.POINTER(vp)]
         L.les_net_destroy.argtypes = [vp]
@@ -107,7 +109,7 @@ def lib(build_if_missing: bool = False):
         L.les_autotune_sor.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
         L.les_set_timing.argtypes = [vp, i32]
         L.les_get_timing.argtypes = [vp, ctypes.POINTER(les_timing_t)]
-        for name in ("les_set_record", "les_set_warmstart", "les_net_create", "les_net_num_params",
+        for name in ("les_set_record", "les_set_record_at", "les_set_net_schedule", "les_set_warmstart", "les_net_create", "les_net_num_params",
                      "les_net_get_params", "les_net_set_params", "les_net_forward", "les_net_gradient",
                      "les_net_train_step", "les_residual_noalloc", "les_profiler_range", "les_set_graph", "les_set_sor_config", "les_get_sor_config", "les_sor_tile", "les_autotune_sor",
                      "les_set_timing", "les_get_timing", "les_create", "les_set_fields", "les_get_fields", "les_set_inflow", "les_step",
@@ -199,6 +201,14 @@ def les_residual_noalloc(grid: les_grid_t, d_p, d_rhs, d_solid, d_dz, d_out, str
 
 def les_set_record(h, enable):
     return _check(lib().les_set_record(h, 1 if enable else 0), h)
+
+
+def les_set_record_at(h, after_sweeps):
+    return _check(lib().les_set_record_at(h, after_sweeps), h)
+
+
+def les_set_net_schedule(h, every_sweeps):
+    return _check(lib().les_set_net_schedule(h, every_sweeps), h)
 
 
 def les_set_warmstart(h, mode, net):
@@ -416,8 +426,12 @@ class Domain:
         buf = ctypes.create_string_buffer(blob, len(blob))
         les_set_state(self.h, buf, len(blob))
 
-    def set_record(self, enable=True):
+    def set_record(self, enable=True, after_sweeps=0):
         les_set_record(self.h, enable)
+        les_set_record_at(self.h, after_sweeps)
+
+    def set_net_schedule(self, every_sweeps):
+        les_set_net_schedule(self.h, every_sweeps)
 
     def set_warmstart(self, net=None, mode=None):
         """net given: learned warm start; else mode LES_WARM_PREV (default) or LES_WARM_ZERO."""
