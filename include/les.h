@@ -309,6 +309,16 @@ const char* les_net_last_error(les_net n);
 int les_net_num_params(les_net n, int64_t* count);
 int les_net_get_params(les_net n, float* host);
 int les_net_set_params(les_net n, const float* host);
+/* les_net_set_stride: run the network on the grid coarsened `stride` times per
+ * axis (1, 2, 4 or 8; default 1).  Inputs are pooled (block sums / stride^3,
+ * cells outside the grid count as zero: the pooled mask is the unknown
+ * fraction), the network runs at the coarse level and its output is
+ * prolongated to the fine cells by trilinear interpolation between coarse
+ * cell centres (clamped at the boundary) and masked: a learned coarse-grid
+ * correction.  Training calls take fine arrays and train at the coarse level
+ * against the pooled target. */
+int les_net_set_stride(les_net n, int32_t stride);
+int les_net_get_stride(les_net n, int32_t* stride);
 int les_net_forward(les_net n, const float* d_r, const float* d_mask, float* d_y, int32_t nx, int32_t ny, int32_t nz);
 int les_net_gradient(les_net n, const float* d_r, const float* d_mask, const float* d_t, int32_t batch, int32_t nx,
                      int32_t ny, int32_t nz, float* d_grad, double* loss);

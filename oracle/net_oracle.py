@@ -13,9 +13,17 @@ nearest-neighbour copy.  Input x: channel 0 = mask * r / rms_mask(r), channel 1
 = mask, channels 2..15 zero.  Loss: mean over the batch of
 mean_mask (y - t / rms_mask(t))^2.
 
+With an input stride s the sample is first pooled s times per axis (block
+means, cells outside the grid counting as zero), the network runs on the coarse
+grid, and its output is prolongated to the fine cells by trilinear
+interpolation between coarse cell centres and masked.
+
 Pins (tests/test_oracle_net.py): the convolution equals scipy.signal's
 correlation channel by channel, pool/up are adjoint to their backward
-maps, and the full gradient matches central finite differences.
+maps, the full gradient matches central finite differences, strided pooling
+reduces to the 2x2x2 pool and preserves block means, and the prolongation
+reproduces constants everywhere and linear functions away from the clamped
+boundary cells.
 """
 
 from __future__ import annotations
@@ -198,6 +206,55 @@ def loss(theta, rs, masks, ts):
         e = mask * (y - tn)
         L += (e * e).sum() / (mask.sum() * B)
     return L
+
+
+# ---------------------------------------------------------------------------
+# input stride: the network runs on the grid coarsened s times per axis
+
+def pool_s(a, s):
+    """Block sums over s x s x s fine cells / s^3 (cells outside the grid count as zero)."""
+    Z, Y, X = a.shape
+    ap = np.pad(a, ((0, -Z % s), (0, -Y % s), (0, -X % s)))
+    Zc, Yc, Xc = ap.shape[0] // s, ap.shape[1] // s, ap.shape[2] // s
+    return ap.reshape(Zc, s, Yc, s, Xc, s).sum(axis=(1, 3, 5)) / float(s ** 3)
+
+
+def interp_matrix(n_fine, s):
+    """1-D linear interpolation from coarse cell centres to fine cell centres:
+    fine centre f is at coarse coordinate (f + 1/2)/s - 1/2, clamped to the
+    first / last coarse centre."""
+    C = -(-n_fine // s)
+    P = np.zeros((n_fine, C))
+    for f in range(n_fine):
+        x = (f + 0.5) / s - 0.5
+        c0 = int(np.floor(x))
+        w = x - c0
+        if c0 < 0:
+            c0, w = 0, 0.0
+        if c0 >= C - 1:
+            c0, w = C - 1, 0.0
+        P[f, c0] += 1.0 - w
+        if w > 0.0:
+            P[f, c0 + 1] += w
+    return P
+
+
+def prolong(yc, shape, s):
+    """Trilinear prolongation of a coarse [Zc, Yc, Xc] field to the fine shape."""
+    Pz, Py, Px = (interp_matrix(n, s) for n in shape)
+    return np.einsum("zc,yb,xa,cba->zyx", Pz, Py, Px, yc)
+
+
+def forward_strided(theta, r, mask, s):
+    """The network on the pooled sample, prolongated and masked on the fine grid."""
+    yc, _ = forward(theta, pool_s(r, s), pool_s(mask, s))
+    return mask * prolong(yc, r.shape, s)
+
+
+def loss_and_grad_strided(theta, rs, masks, ts, s):
+    """Training at the coarse level against the pooled targets."""
+    return loss_and_grad(theta, [pool_s(r, s) for r in rs], [pool_s(m, s) for m in masks],
+                         [pool_s(t, s) for t in ts])
 
 
 def init_params(seed):

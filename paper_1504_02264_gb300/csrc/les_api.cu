@@ -318,13 +318,10 @@ CondArgs cond_args(const les_s* h, int mode, int n, int gate) {
 // residual may already pass the stop test).
 template <typename T>
 int net_correct(les_s* h, const Geo<T>& g, int mode, cudaStream_t st) {
-    h->launches += launch_warm<T>(g, (const T*)h->rr, h->pred, h->ph[h->cur], h->warm_scal, h->n_unk, reducer(h), 0,
-                                  st);
-    int rc = net_predict(h->net, h->d, (const float*)h->rr, h->flags, h->warm_scal, h->pred, st);
+    int rc = net_predict(h->net, h->d, (const float*)h->rr, h->flags, h->pred, st);
     if (rc) return fail(h, rc, "network prediction failed");
-    h->launches += 15;      // pack, 7 convolutions, 3 pools, 3 upsamplings, head
-    h->launches += launch_warm<T>(g, (const T*)h->rr, h->pred, h->ph[h->cur], h->warm_scal, h->n_unk, reducer(h), 1,
-                                  st);
+    h->launches += net_launches(h->net);
+    h->launches += launch_warm<T>(g, (const T*)h->rr, h->pred, h->ph[h->cur], h->warm_scal + 1, reducer(h), st);
     h->launches += launch_residual64<T>(g, h->ph[h->cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h),
                                         cond_args(h, mode, 0, 0), st);
     CK(cudaGetLastError());

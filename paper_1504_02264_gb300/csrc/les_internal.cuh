@@ -160,9 +160,9 @@ int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, const float* cn1tab
                    int zero, Scalars* sc, cudaStream_t s);
 int launch_cn1_table(const Geo<float>& g, float* tab, cudaStream_t s);
 
-// learned warm start (les_kernels.cu): stage 0 = input scale, 1 = line search + update
-template <typename T> int launch_warm(const Geo<T>& g, const T* r, const float* q, double* ph, double* scal,
-                                      double n_unk, const Reduce& red, int stage, cudaStream_t s);
+// learned warm start (les_kernels.cu): energy-norm line search along q and p += alpha q
+template <typename T> int launch_warm(const Geo<T>& g, const T* r, const float* q, double* ph, double* alpha,
+                                      const Reduce& red, cudaStream_t s);
 // training-pair recording: what 0 = ph - ph0 into out, 1 = unknown mask into out
 template <typename T> int launch_record(const Geo<T>& g, const double* ph, const double* ph0, T* out, int what,
                                         cudaStream_t s);
@@ -174,7 +174,10 @@ int max_reduce_blocks(const Dom& d);
 
 struct les_net_s;
 namespace les {
-// network prediction on a solver grid (les_net.cu): dense (nz, ny, nx) output
-int net_predict(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, const double* rms,
-                float* out_dense, cudaStream_t s);
+// network prediction on a solver grid (les_net.cu): the padded residual and
+// the unknown flags in, the correction direction as a dense (nz, ny, nx)
+// array out (zero off the unknowns)
+int net_predict(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, float* out_dense,
+                cudaStream_t s);
+int net_launches(const les_net_s* n);
 }  // namespace les

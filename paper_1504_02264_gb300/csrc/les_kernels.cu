@@ -887,11 +887,6 @@ int launch_rhs_eff(const Geo<T>& g, const T* rhs, T* out, const Scalars* sc, cud
 // learned warm start support: line search and update along a predicted
 // correction (dense (nz, ny, nx) array), plus recording of training pairs.
 
-// scale of the network input: rms of the initial residual over the unknowns
-__global__ void k_warm_scale(const Scalars* sc, double n_unk, double* out) {
-    out[0] = n_unk > 0.0 ? sqrt(sc->res2 / n_unk) : 0.0;
-}
-
 // alpha minimising the energy norm of the error along q (FP64):
 //   alpha = <q, V r> / <q, V A q>,  V = diag(dz_k) (the cell volumes up to dx dy),
 // which makes V A symmetric, so this is the exact minimiser of
@@ -953,17 +948,13 @@ __global__ void k_warm_apply(Geo<T> g, double* ph, const float* q, const double*
 }
 
 template <typename T>
-int launch_warm(const Geo<T>& g, const T* r, const float* q, double* ph, double* scal, double n_unk,
-                const Reduce& red, int stage, cudaStream_t s) {
+int launch_warm(const Geo<T>& g, const T* r, const float* q, double* ph, double* alpha, const Reduce& red,
+                cudaStream_t s) {
     const Dom& d = g.d;
     const dim3 grid((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), blk(32, 8);
-    if (stage == 0) {
-        k_warm_scale<<<1, 1, 0, s>>>(red.sc, n_unk, scal);
-    } else {
-        k_warm_ls<T><<<grid, blk, 0, s>>>(g, r, q, scal + 1, red);
-        k_warm_apply<T><<<grid, blk, 0, s>>>(g, ph, q, scal + 1);
-    }
-    return stage == 0 ? 1 : 2;
+    k_warm_ls<T><<<grid, blk, 0, s>>>(g, r, q, alpha, red);
+    k_warm_apply<T><<<grid, blk, 0, s>>>(g, ph, q, alpha);
+    return 2;
 }
 
 // training pairs: delta = ph - ph0 (the correction a solve applied, before the gauge)
@@ -1031,8 +1022,8 @@ int max_reduce_blocks(const Dom& d) { return ((d.nx + 31) / 32) * ((d.ny + 7) / 
                                    const double*, double*, Scalars*, cudaStream_t);                     \
     template int launch_rhs_eff<T>(const Geo<T>&, const T*, T*, const Scalars*, cudaStream_t);          \
     template int launch_gauge<T>(const Geo<T>&, const double*, double*, const Scalars*, cudaStream_t);   \
-    template int launch_warm<T>(const Geo<T>&, const T*, const float*, double*, double*, double, const Reduce&, \
-                                int, cudaStream_t);                                                     \
+    template int launch_warm<T>(const Geo<T>&, const T*, const float*, double*, double*, const Reduce&,         \
+                                cudaStream_t);                                                          \
     template int launch_record<T>(const Geo<T>&, const double*, const double*, T*, int, cudaStream_t);
 
 LES_INSTANTIATE(float)

@@ -114,6 +114,8 @@ struct les_net_s {
     __nv_bfloat16 *ga = nullptr, *gb = nullptr, *gd0 = nullptr, *gd1 = nullptr, *gd2 = nullptr, *ge3 = nullptr,
                   *gpb = nullptr;
     float *y = nullptr, *gy = nullptr, *mask = nullptr, *tn = nullptr;
+    int stride = 1;                     // the network runs on the grid coarsened stride times per axis
+    float *rc = nullptr, *mc = nullptr, *tc = nullptr;     // pooled sample (coarse level 0)
     double* dscal = nullptr;            // [0..2B): per-sample rms and mask counts, [62]: loss
     char err[256] = {0};
 };
@@ -136,6 +138,12 @@ Level level(const Level& l0, int l) {
     Level o = l0;
     for (int i = 0; i < l; ++i) o = Level{(o.X + 1) / 2, (o.Y + 1) / 2, (o.Z + 1) / 2};
     return o;
+}
+
+// the network's level 0 for a fine grid
+Level coarse(const les_net_s* n, const Level& f) {
+    const int s = n->stride;
+    return Level{(f.X + s - 1) / s, (f.Y + s - 1) / s, (f.Z + s - 1) / s};
 }
 
 void free_ws(les_net_s* n) {
@@ -198,6 +206,9 @@ int ensure_ws(les_net_s* n, const Level& L0) {
     if ((rc = get(vol(0), sizeof(float), (void**)&n->gy))) return rc;
     if ((rc = get(vol(0), sizeof(float), (void**)&n->mask))) return rc;
     if ((rc = get(vol(0), sizeof(float), (void**)&n->tn))) return rc;
+    if ((rc = get(vol(0), sizeof(float), (void**)&n->rc))) return rc;
+    if ((rc = get(vol(0), sizeof(float), (void**)&n->mc))) return rc;
+    if ((rc = get(vol(0), sizeof(float), (void**)&n->tc))) return rc;
     if ((rc = get(64, sizeof(double), (void**)&n->dscal))) return rc;
     for (int l = 0; l < 4; ++l) n->cap[l] = want[l];
     n->cap_v0 = want[0];
@@ -274,19 +285,19 @@ void refresh_copies(les_net_s* n) {
     }
 }
 
-// pack sample b of a dense batch and normalise its target (if any)
-int prepare_sample(les_net_s* n, const Level& L0, const float* r, const float* mask, const float* t, size_t b,
-                   double* nmask) {
+// pack a dense coarse sample (r, mask, optional target t) into the network
+// input and normalise the target; nmask receives sum(mask) when asked
+int pack_sample(les_net_s* n, const Level& L0, const float* r, const float* mask, const float* t, double* nmask) {
     const size_t v = L0.v();
     cudaStream_t s = n->stream;
     NCK(cudaMemsetAsync(n->dscal, 0, 4 * sizeof(double), s));
     const unsigned blocks = (unsigned)((v + 255) / 256 < 1024 ? (v + 255) / 256 : 1024);
-    k_rms<<<dim3(blocks, 1), 256, 0, s>>>(r + b * v, mask + b * v, v, n->dscal);
-    if (t) k_rms<<<dim3(blocks, 1), 256, 0, s>>>(t + b * v, mask + b * v, v, n->dscal + 2);
+    k_rms<<<dim3(blocks, 1), 256, 0, s>>>(r, mask, v, n->dscal);
+    if (t) k_rms<<<dim3(blocks, 1), 256, 0, s>>>(t, mask, v, n->dscal + 2);
     k_rms_final<<<1, 32, 0, s>>>(n->dscal, t ? 2 : 1);
-    NCK(cudaMemcpyAsync(n->mask, mask + b * v, v * sizeof(float), cudaMemcpyDeviceToDevice, s));
-    k_pack_dense<<<(unsigned)((v + 255) / 256), 256, 0, s>>>(r + b * v, n->mask, n->dscal, n->xin, v);
-    if (t) k_scale<<<(unsigned)((v + 255) / 256), 256, 0, s>>>(t + b * v, n->dscal + 2, n->tn, v);
+    if (mask != n->mask) NCK(cudaMemcpyAsync(n->mask, mask, v * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    k_pack_dense<<<(unsigned)((v + 255) / 256), 256, 0, s>>>(r, n->mask, n->dscal, n->xin, v);
+    if (t) k_scale<<<(unsigned)((v + 255) / 256), 256, 0, s>>>(t, n->dscal + 2, n->tn, v);
     NCK(cudaGetLastError());
     if (nmask) {
         double host[2];
@@ -297,8 +308,27 @@ int prepare_sample(les_net_s* n, const Level& L0, const float* r, const float* m
     return LES_OK;
 }
 
+// sample b of a dense fine batch: pooled to the network's level 0 when the
+// stride is above 1, then packed
+int prepare_sample(les_net_s* n, const Level& Lf, const float* r, const float* mask, const float* t, size_t b,
+                   double* nmask) {
+    const size_t vf = Lf.v();
+    const float *pr = r + b * vf, *pm = mask + b * vf, *pt = t ? t + b * vf : nullptr;
+    if (n->stride > 1) {
+        const int st = n->stride;
+        nn::pool_dense_s(pr, n->rc, Lf.X, Lf.Y, Lf.Z, st, n->stream);
+        nn::pool_dense_s(pm, n->mc, Lf.X, Lf.Y, Lf.Z, st, n->stream);
+        if (pt) nn::pool_dense_s(pt, n->tc, Lf.X, Lf.Y, Lf.Z, st, n->stream);
+        pr = n->rc;
+        pm = n->mc;
+        pt = pt ? n->tc : nullptr;
+    }
+    return pack_sample(n, coarse(n, Lf), pr, pm, pt, nmask);
+}
+
 // forward + loss + backward over a batch, gradients accumulated in g32
-int batch_grad(les_net_s* n, const Level& L0, const float* r, const float* mask, const float* t, int B, double* loss) {
+int batch_grad(les_net_s* n, const Level& Lf, const float* r, const float* mask, const float* t, int B, double* loss) {
+    const Level L0 = coarse(n, Lf);
     int rc = ensure_ws(n, L0);
     if (rc) return rc;
     cudaStream_t s = n->stream;
@@ -307,7 +337,7 @@ int batch_grad(les_net_s* n, const Level& L0, const float* r, const float* mask,
     NCK(cudaMemsetAsync(dl, 0, sizeof(double), s));
     for (int b = 0; b < B; ++b) {
         double nm = 0.0;
-        if ((rc = prepare_sample(n, L0, r, mask, t, b, &nm))) return rc;
+        if ((rc = prepare_sample(n, Lf, r, mask, t, b, &nm))) return rc;
         forward(n, L0);
         const double inv = nm > 0.0 ? 1.0 / (nm * B) : 0.0;
         nn::mse(n->y, n->tn, n->mask, n->gy, dl, L0.v(), inv, s);
@@ -325,21 +355,26 @@ int batch_grad(les_net_s* n, const Level& L0, const float* r, const float* mask,
 // solver-side inference (les_api.cu): predicted correction direction on the
 // handle's grid from its padded residual (float) and flags
 namespace les {
-int net_predict(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, const double* rms,
-                float* out_dense, cudaStream_t s) {
-    const Level L0{d.nx, d.ny, d.nz};
+int net_predict(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, float* out_dense,
+                cudaStream_t s) {
+    const Level Lf{d.nx, d.ny, d.nz};
+    const Level L0 = coarse(n, Lf);
     cudaStream_t keep = n->stream;
     n->stream = s;
     int rc = ensure_ws(n, L0);
     if (!rc) {
-        nn::pack_input(r_padded, flags, d, rms, n->xin, n->mask, s);
+        nn::pool_padded_s(r_padded, flags, d, n->stride, n->rc, n->mc, s);
+        rc = pack_sample(n, L0, n->rc, n->mc, nullptr, nullptr);
+    }
+    if (!rc) {
         forward(n, L0);
-        cudaError_t e = cudaMemcpyAsync(out_dense, n->y, L0.v() * sizeof(float), cudaMemcpyDeviceToDevice, s);
-        if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) rc = LES_ECUDA;
+        nn::prolong_flags(n->y, flags, d, n->stride, out_dense, s);
+        if (cudaGetLastError() != cudaSuccess) rc = LES_ECUDA;
     }
     n->stream = keep;
     return rc;
 }
+int net_launches(const les_net_s* n) { return 2 + 3 + 15 + 1; }     // pool, rms + pack, network, prolongation
 }  // namespace les
 
 extern "C" {
@@ -426,15 +461,28 @@ int les_net_set_params(les_net n, const float* host) {
     return LES_OK;
 }
 
+int les_net_set_stride(les_net n, int32_t stride) {
+    if (!n || (stride != 1 && stride != 2 && stride != 4 && stride != 8)) return LES_EINVAL;
+    n->stride = stride;
+    return LES_OK;
+}
+
+int les_net_get_stride(les_net n, int32_t* stride) {
+    if (!n || !stride) return LES_EINVAL;
+    *stride = n->stride;
+    return LES_OK;
+}
+
 int les_net_forward(les_net n, const float* d_r, const float* d_mask, float* d_y, int32_t nx, int32_t ny,
                     int32_t nz) {
     if (!n || !d_r || !d_mask || !d_y || nx < 1 || ny < 1 || nz < 1) return LES_EINVAL;
-    const Level L0{nx, ny, nz};
+    const Level Lf{nx, ny, nz};
+    const Level L0 = coarse(n, Lf);
     int rc = ensure_ws(n, L0);
     if (rc) return rc;
-    if ((rc = prepare_sample(n, L0, d_r, d_mask, nullptr, 0, nullptr))) return rc;
+    if ((rc = prepare_sample(n, Lf, d_r, d_mask, nullptr, 0, nullptr))) return rc;
     forward(n, L0);
-    NCK(cudaMemcpyAsync(d_y, n->y, L0.v() * sizeof(float), cudaMemcpyDeviceToDevice, n->stream));
+    nn::prolong_dense(n->y, d_mask, d_y, nx, ny, nz, n->stride, n->stream);
     NCK(cudaGetLastError());
     NCK(cudaStreamSynchronize(n->stream));
     return LES_OK;

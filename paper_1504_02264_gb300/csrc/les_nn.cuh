@@ -23,8 +23,10 @@ void add(const __nv_bfloat16* a, const __nv_bfloat16* b, __nv_bfloat16* out, siz
 void head(const __nv_bfloat16* d, const float* w1, const float* mask, float* y, size_t nv, int C, cudaStream_t s);
 void head_bwd(const __nv_bfloat16* d, const float* w1, const float* mask, const float* gy, __nv_bfloat16* gd,
               float* dw1, size_t nv, int C, cudaStream_t s);
-void pack_input(const float* r, const uint8_t* flags, const Dom& d, const double* scale, __nv_bfloat16* xin,
-                float* mask, cudaStream_t s);
+void pool_dense_s(const float* a, float* b, int Xf, int Yf, int Zf, int st, cudaStream_t s);
+void pool_padded_s(const float* r, const uint8_t* flags, const Dom& d, int st, float* rc, float* mc, cudaStream_t s);
+void prolong_dense(const float* yc, const float* mask, float* out, int Xf, int Yf, int Zf, int st, cudaStream_t s);
+void prolong_flags(const float* yc, const uint8_t* flags, const Dom& d, int st, float* out, cudaStream_t s);
 void mse(const float* y, const float* t, const float* mask, float* g, double* loss, size_t n, double inv_n,
          cudaStream_t s);
 void adam(float* w, float* m, float* v, const float* g, __nv_bfloat16* wb, size_t n, float lr, float b1, float b2,

@@ -353,22 +353,97 @@ __global__ void k_head_bwd(const __nv_bfloat16* d, const float* w1, const float*
     }
 }
 
-// network input: channel 0 = r / scale, channel 1 = fluid mask, 2..15 = 0;
-// from a padded cell array of the solver (field type float)
-__global__ void k_pack_input(const float* r, const uint8_t* flags, Dom d, const double* scale, __nv_bfloat16* xin,
-                             float* mask) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y, k = blockIdx.z;
-    if (i >= d.nx) return;
-    const long long c = d.at(i + 1, j + 1, k + 1);
-    const size_t v = ((size_t)k * d.ny + j) * d.nx + i;
-    const bool unk = flags[c] & F_UNK;
-    const float s = (float)(*scale > 0.0 ? 1.0 / *scale : 0.0);
-    __nv_bfloat16* o = xin + v * 16;
-    o[0] = __float2bfloat16(unk ? r[c] * s : 0.f);
-    o[1] = __float2bfloat16(unk ? 1.f : 0.f);
-    for (int ch = 2; ch < 16; ++ch) o[ch] = __float2bfloat16(0.f);
-    mask[v] = unk ? 1.f : 0.f;
+// ---------------------------------------------------------------------------
+// input stride s (the network runs on the grid coarsened s times per axis):
+// coarse value = sum of the existing fine children / s^3
+
+// dense fine [Zf][Yf][Xf] -> dense coarse
+__global__ void k_pool_dense_s(const float* a, float* b, int Xf, int Yf, int Zf, int s) {
+    const int Xc = (Xf + s - 1) / s, Yc = (Yf + s - 1) / s, Zc = (Zf + s - 1) / s;
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (size_t)Xc * Yc * Zc) return;
+    const int x = q % Xc, y = (q / Xc) % Yc, z = q / ((size_t)Xc * Yc);
+    float acc = 0.f;
+    for (int dz = 0; dz < s; ++dz)
+        for (int dy = 0; dy < s; ++dy)
+            for (int dx = 0; dx < s; ++dx) {
+                const int fx = x * s + dx, fy = y * s + dy, fz = z * s + dz;
+                if (fx < Xf && fy < Yf && fz < Zf) acc += a[((size_t)fz * Yf + fy) * Xf + fx];
+            }
+    b[q] = acc / (float)(s * s * s);
+}
+
+// the solver's padded residual (unknowns only) and unknown mask -> dense coarse
+__global__ void k_pool_padded_s(const float* r, const uint8_t* flags, Dom d, int s, float* rc, float* mc) {
+    const int Xc = (d.nx + s - 1) / s, Yc = (d.ny + s - 1) / s, Zc = (d.nz + s - 1) / s;
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (size_t)Xc * Yc * Zc) return;
+    const int x = q % Xc, y = (q / Xc) % Yc, z = q / ((size_t)Xc * Yc);
+    float ar = 0.f, am = 0.f;
+    for (int dz = 0; dz < s; ++dz)
+        for (int dy = 0; dy < s; ++dy)
+            for (int dx = 0; dx < s; ++dx) {
+                const int fx = x * s + dx, fy = y * s + dy, fz = z * s + dz;
+                if (fx < d.nx && fy < d.ny && fz < d.nz) {
+                    const long long c = d.at(fx + 1, fy + 1, fz + 1);
+                    if (flags[c] & F_UNK) {
+                        ar += r[c];
+                        am += 1.f;
+                    }
+                }
+            }
+    const float inv = 1.f / (float)(s * s * s);
+    rc[q] = ar * inv;
+    mc[q] = am * inv;
+}
+
+// trilinear prolongation of a coarse cell-centred field to the fine cells,
+// times the fine mask: fine centre f sits at coarse coordinate (f + 1/2)/s - 1/2
+// on each axis, clamped to the first / last coarse centre
+__device__ __forceinline__ void lin_w(int f, int s, int C, int& c0, float& w) {
+    const float x = ((float)f + 0.5f) / (float)s - 0.5f;
+    c0 = (int)floorf(x);
+    w = x - (float)c0;
+    if (c0 < 0) {
+        c0 = 0;
+        w = 0.f;
+    }
+    if (c0 >= C - 1) {
+        c0 = C - 1;
+        w = 0.f;
+    }
+}
+__device__ __forceinline__ float trilinear(const float* y, int Xc, int Yc, int Zc, int s, int fx, int fy, int fz) {
+    int x0, y0, z0;
+    float wx, wy, wz;
+    lin_w(fx, s, Xc, x0, wx);
+    lin_w(fy, s, Yc, y0, wy);
+    lin_w(fz, s, Zc, z0, wz);
+    const int x1 = min(x0 + 1, Xc - 1), y1 = min(y0 + 1, Yc - 1), z1 = min(z0 + 1, Zc - 1);
+    auto at = [&](int a, int b, int c) { return y[((size_t)c * Yc + b) * Xc + a]; };
+    const float c00 = (1.f - wx) * at(x0, y0, z0) + wx * at(x1, y0, z0);
+    const float c10 = (1.f - wx) * at(x0, y1, z0) + wx * at(x1, y1, z0);
+    const float c01 = (1.f - wx) * at(x0, y0, z1) + wx * at(x1, y0, z1);
+    const float c11 = (1.f - wx) * at(x0, y1, z1) + wx * at(x1, y1, z1);
+    const float c0 = (1.f - wy) * c00 + wy * c10, c1 = (1.f - wy) * c01 + wy * c11;
+    return (1.f - wz) * c0 + wz * c1;
+}
+// dense fine output with a dense fine mask
+__global__ void k_prolong_dense(const float* yc, const float* mask, float* out, int Xf, int Yf, int Zf, int s) {
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (size_t)Xf * Yf * Zf) return;
+    const int x = q % Xf, y = (q / Xf) % Yf, z = q / ((size_t)Xf * Yf);
+    const int Xc = (Xf + s - 1) / s, Yc = (Yf + s - 1) / s, Zc = (Zf + s - 1) / s;
+    out[q] = mask[q] * trilinear(yc, Xc, Yc, Zc, s, x, y, z);
+}
+// dense fine output on the solver's unknowns
+__global__ void k_prolong_flags(const float* yc, const uint8_t* flags, Dom d, int s, float* out) {
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (size_t)d.nx * d.ny * d.nz) return;
+    const int x = q % d.nx, y = (q / d.nx) % d.ny, z = q / ((size_t)d.nx * d.ny);
+    const int Xc = (d.nx + s - 1) / s, Yc = (d.ny + s - 1) / s, Zc = (d.nz + s - 1) / s;
+    const bool unk = flags[d.at(x + 1, y + 1, z + 1)] & F_UNK;
+    out[q] = unk ? trilinear(yc, Xc, Yc, Zc, s, x, y, z) : 0.f;
 }
 
 // training loss 1/n * sum mask (y - t)^2 and its gradient
@@ -432,9 +507,19 @@ void head_bwd(const __nv_bfloat16* d, const float* w1, const float* mask, const 
               float* dw1, size_t nv, int C, cudaStream_t s) {
     k_head_bwd<<<blocks_for(nv), 256, 0, s>>>(d, w1, mask, gy, gd, dw1, nv, C);
 }
-void pack_input(const float* r, const uint8_t* flags, const Dom& d, const double* scale, __nv_bfloat16* xin,
-                float* mask, cudaStream_t s) {
-    k_pack_input<<<dim3((d.nx + 127) / 128, d.ny, d.nz), 128, 0, s>>>(r, flags, d, scale, xin, mask);
+void pool_dense_s(const float* a, float* b, int Xf, int Yf, int Zf, int st, cudaStream_t s) {
+    const size_t n = (size_t)((Xf + st - 1) / st) * ((Yf + st - 1) / st) * ((Zf + st - 1) / st);
+    k_pool_dense_s<<<blocks_for(n), 256, 0, s>>>(a, b, Xf, Yf, Zf, st);
+}
+void pool_padded_s(const float* r, const uint8_t* flags, const Dom& d, int st, float* rc, float* mc, cudaStream_t s) {
+    const size_t n = (size_t)((d.nx + st - 1) / st) * ((d.ny + st - 1) / st) * ((d.nz + st - 1) / st);
+    k_pool_padded_s<<<blocks_for(n), 256, 0, s>>>(r, flags, d, st, rc, mc);
+}
+void prolong_dense(const float* yc, const float* mask, float* out, int Xf, int Yf, int Zf, int st, cudaStream_t s) {
+    k_prolong_dense<<<blocks_for((size_t)Xf * Yf * Zf), 256, 0, s>>>(yc, mask, out, Xf, Yf, Zf, st);
+}
+void prolong_flags(const float* yc, const uint8_t* flags, const Dom& d, int st, float* out, cudaStream_t s) {
+    k_prolong_flags<<<blocks_for((size_t)d.nx * d.ny * d.nz), 256, 0, s>>>(yc, flags, d, st, out);
 }
 void mse(const float* y, const float* t, const float* mask, float* g, double* loss, size_t n, double inv_n,
          cudaStream_t s) {

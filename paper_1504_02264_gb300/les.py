@@ -96,6 +96,8 @@ def lib(build_if_missing: bool = False):
         L.les_net_last_error.argtypes = [vp]
         L.les_net_last_error.restype = ctypes.c_char_p
         L.les_net_num_params.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+        L.les_net_set_stride.argtypes = [vp, i32]
+        L.les_net_get_stride.argtypes = [vp, ctypes.POINTER(i32)]
         L.les_net_get_params.argtypes = [vp, vp]
         L.les_net_set_params.argtypes = [vp, vp]
         L.les_net_forward.argtypes = [vp, vp, vp, vp, i32, i32, i32]
@@ -110,6 +112,7 @@ def lib(build_if_missing: bool = False):
         L.les_set_timing.argtypes = [vp, i32]
         L.les_get_timing.argtypes = [vp, ctypes.POINTER(les_timing_t)]
         for name in ("les_set_record", "les_set_record_at", "les_set_net_schedule", "les_set_warmstart", "les_net_create", "les_net_num_params",
+                     "les_net_set_stride", "les_net_get_stride",
                      "les_net_get_params", "les_net_set_params", "les_net_forward", "les_net_gradient",
                      "les_net_train_step", "les_residual_noalloc", "les_profiler_range", "les_set_graph", "les_set_sor_config", "les_get_sor_config", "les_sor_tile", "les_autotune_sor",
                      "les_set_timing", "les_get_timing", "les_create", "les_set_fields", "les_get_fields", "les_set_inflow", "les_step",
@@ -240,6 +243,16 @@ def les_net_num_params(n):
     return c.value
 
 
+def les_net_set_stride(n, stride):
+    return _ncheck(lib().les_net_set_stride(n, stride), n)
+
+
+def les_net_get_stride(n):
+    s = ctypes.c_int32()
+    _ncheck(lib().les_net_get_stride(n, ctypes.byref(s)), n)
+    return s.value
+
+
 def les_net_get_params(n, out):
     return _ncheck(lib().les_net_get_params(n, _ptr(out)), n)
 
@@ -267,10 +280,19 @@ def les_net_train_step(n, d_r, d_mask, d_t, batch, nx, ny, nz, lr):
 class Net:
     """The warm-start network (device weights owned by the library)."""
 
-    def __init__(self, seed=0, stream="torch"):
+    def __init__(self, seed=0, stream="torch", stride=1):
         st = current_stream() if stream == "torch" else stream
         self.h = les_net_create(seed, st)
         self.nparam = les_net_num_params(self.h)
+        les_net_set_stride(self.h, stride)
+
+    @property
+    def stride(self):
+        return les_net_get_stride(self.h)
+
+    @stride.setter
+    def stride(self, s):
+        les_net_set_stride(self.h, s)
 
     def close(self):
         if getattr(self, "h", None):

@@ -36,6 +36,18 @@ def _require_torch():
     return torch
 
 
+def save(net: les.Net, path: str):
+    """Parameters and input stride of a trained network (.npz)."""
+    np.savez(path, params=net.params(), stride=np.int32(net.stride))
+
+
+def load(path: str, seed: int = 0) -> les.Net:
+    z = np.load(path)
+    net = les.Net(seed=seed, stride=int(z["stride"]))
+    net.set_params(z["params"])
+    return net
+
+
 def training_scenes(n_lattice: int, n_city: int, seed: int, city_shape=(96, 96, 48)):
     """Lattice scenes (turbulent inflow for variety) and small random cities."""
     out = []
@@ -130,12 +142,14 @@ def evaluate(net: les.Net | None, sc, steps: int, spinup: int, schedules=(0,), l
     for _ in range(spinup):
         base.step()
     state = base.get_state()
+    (tile, kc), _ = base.autotune_sor(sweeps=20)
     base.close()
     modes = [("prev", None)] + ([(f"net_every_{m}", m) for m in schedules] if net is not None else [])
     res = {}
     for name, m in modes:
         dom = les.Domain(sc)
         dom.set_state(state)
+        dom.set_sor_config(tile, kc)
         if m is not None:
             dom.set_warmstart(net)
             dom.set_net_schedule(m)
@@ -150,15 +164,17 @@ def evaluate(net: les.Net | None, sc, steps: int, spinup: int, schedules=(0,), l
             ok &= st["rc"] == 0 and st["rel_residual"] <= sc.tol
         dom.close()
         res[name] = {"sweeps_per_step": float(np.mean(sweeps)), "ms_per_step": float(np.mean(ms)),
-                     "converged": bool(ok)}
+                     "converged": bool(ok), "sor_tile": [tile, kc]}
         log(f"  {name}: {res[name]}")
     return res
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("--out", default="warmstart.npy")
-    ap.add_argument("--init", default=None, help="start from these parameters (.npy)")
+    ap.add_argument("--out", default="warmstart.npz")
+    ap.add_argument("--init", default=None, help="start from this network (.npz)")
+    ap.add_argument("--stride", type=int, default=4, help="input stride of the network")
+    ap.add_argument("--city-size", default="96x96x48")
     ap.add_argument("--lattice", type=int, default=16, help="lattice scenes (seeds)")
     ap.add_argument("--cities", type=int, default=8, help="random-city scenes")
     ap.add_argument("--steps", type=int, default=40, help="recorded steps per scene")
@@ -178,14 +194,14 @@ def main(argv=None):
     t0 = time.time()
     pts = [int(x) for x in a.record_points.split(",")]
     print(f"generating pairs: {a.lattice} lattice + {a.cities} city scenes x {a.steps} steps", flush=True)
-    data = generate(training_scenes(a.lattice, a.cities, a.seed), a.steps, a.spinup, pts, a.seed)
+    cs = tuple(int(x) for x in a.city_size.split("x"))
+    data = generate(training_scenes(a.lattice, a.cities, a.seed, cs), a.steps, a.spinup, pts, a.seed)
     npairs = sum(v[0].shape[0] for v in data.values())
     print(f"{npairs} pairs in {time.time() - t0:.0f} s", flush=True)
-    net = les.Net(seed=a.seed)
-    if a.init:
-        net.set_params(np.load(a.init))
+    net = load(a.init, a.seed) if a.init else les.Net(seed=a.seed)
+    net.stride = a.stride
     hist = train(net, data, a.iters, a.batch, a.lr, a.seed)
-    np.save(a.out, net.params())
+    save(net, a.out)
     print(f"trained {a.iters} iterations, final loss {np.mean(hist[-100:]):.4f}; saved {a.out}", flush=True)
     nx, ny, nz = (int(x) for x in a.eval_size.split("x"))
     ev_sc = scene.random_scene(seed=a.seed + 7777, nx=nx, ny=ny, nz=nz, max_sweeps=60000, check_every=20)

@@ -70,6 +70,14 @@ def net():
     n.close()
 
 
+def test_stride_setting(net):
+    assert net.stride == 1
+    net.stride = 4
+    assert net.stride == 4
+    with pytest.raises(les.LesError):
+        net.stride = 3
+
+
 def test_param_count_and_roundtrip(net):
     ws = [27 * ci * co for ci, co in zip(net_oracle.CIN, net_oracle.COUT)]
     assert net.nparam == sum(ws) + net_oracle.HEAD
@@ -79,12 +87,15 @@ def test_param_count_and_roundtrip(net):
     assert np.all(np.isfinite(net.params()))
 
 
-@pytest.mark.parametrize("shape", [(7, 11, 37), (1, 1, 1), (5, 9, 16), (3, 4, 17)])
-def test_forward_matches_oracle(net, shape):
-    """(nz, ny, nx) = 7x11x37 spans 3x3x4 tiles with ragged tails on every level."""
+@pytest.mark.parametrize("shape,stride", [((7, 11, 37), 1), ((1, 1, 1), 1), ((5, 9, 16), 1), ((3, 4, 17), 1),
+                                          ((13, 22, 70), 2), ((17, 30, 61), 4), ((3, 5, 6), 4)])
+def test_forward_matches_oracle(net, shape, stride):
+    """(nz, ny, nx) = 7x11x37 spans 3x3x4 tiles with ragged tails on every
+    level; the strided cases pool to ragged coarse grids and prolongate back."""
     rng = np.random.default_rng(sum(shape))
     theta = net_oracle.init_params(7).astype(np.float32)
     net.set_params(theta)
+    net.stride = stride
     r, mask = sample(rng, shape)
     if mask.sum() == 0:
         mask.flat[0] = 1.0
@@ -93,7 +104,7 @@ def test_forward_matches_oracle(net, shape):
     nz, ny, nx = shape
     les.les_net_forward(net.h, dr.data_ptr(), dm.data_ptr(), y.data_ptr(), nx, ny, nz)
     yg = y.cpu().numpy().astype(np.float64)
-    yo, _ = net_oracle.forward(oracle_theta(theta), r.astype(np.float32).astype(np.float64), mask)
+    yo = net_oracle.forward_strided(oracle_theta(theta), r.astype(np.float32).astype(np.float64), mask, stride)
     assert np.all(yg[mask == 0] == 0.0)
     err = rel_l2(yg, yo)
     assert err <= 2e-2, err
@@ -115,11 +126,13 @@ def test_forward_scale_invariant(net):
     assert np.array_equal(ys[0], ys[1])
 
 
-def test_gradient_matches_oracle(net):
+@pytest.mark.parametrize("shape,stride", [((5, 9, 21), 1), ((10, 17, 40), 2)])
+def test_gradient_matches_oracle(net, shape, stride):
     rng = np.random.default_rng(2)
-    shape, B = (5, 9, 21), 2
+    B = 2
     theta = net_oracle.init_params(9).astype(np.float32)
     net.set_params(theta)
+    net.stride = stride
     rs, ms, ts = [], [], []
     for _ in range(B):
         r, m = sample(rng, shape)
@@ -129,8 +142,8 @@ def test_gradient_matches_oracle(net):
     dr, dm, dt = dev(np.stack(rs)), dev(np.stack(ms)), dev(np.stack(ts))
     g = torch.empty(net.nparam, dtype=torch.float32, device="cuda")
     L = les.les_net_gradient(net.h, dr.data_ptr(), dm.data_ptr(), dt.data_ptr(), B, nx, ny, nz, g.data_ptr())
-    Lo, go = net_oracle.loss_and_grad(oracle_theta(theta), [x.astype(np.float64) for x in rs], ms,
-                                      [x.astype(np.float64) for x in ts])
+    Lo, go = net_oracle.loss_and_grad_strided(oracle_theta(theta), [x.astype(np.float64) for x in rs], ms,
+                                              [x.astype(np.float64) for x in ts], stride)
     assert abs(L - Lo) <= 2e-2 * abs(Lo), (L, Lo)
     gg = g.cpu().numpy().astype(np.float64)
     o = 0

@@ -65,3 +65,32 @@ def test_gradient_matches_finite_differences():
     d = rng.standard_normal(len(theta))
     fd = (net.loss(theta + h * d, rs, masks, ts) - net.loss(theta - h * d, rs, masks, ts)) / (2 * h)
     assert np.isclose(fd, g @ d, rtol=1e-5)
+
+
+def test_strided_pool_matches_pool_and_block_means():
+    rng = np.random.default_rng(5)
+    a = rng.standard_normal((6, 7, 9))
+    np.testing.assert_allclose(net.pool_s(a, 2), net.pool(a[..., None])[..., 0], rtol=1e-14, atol=1e-14)
+    np.testing.assert_allclose(net.pool_s(a, 4), net.pool_s(net.pool_s(a, 2), 2), rtol=1e-14, atol=1e-14)
+    b = rng.standard_normal((8, 8, 12))
+    assert np.isclose(net.pool_s(b, 4)[1, 0, 2], b[4:8, 0:4, 8:12].mean())
+    assert np.array_equal(net.pool_s(b, 1), b)
+
+
+@pytest.mark.parametrize("s", [1, 2, 4])
+def test_prolong_reproduces_constants_and_linear_functions(s):
+    shape = (9, 13, 17)
+    C = [-(-n // s) for n in shape]
+    yc = np.full(C, 3.25)
+    np.testing.assert_allclose(net.prolong(yc, shape, s), 3.25, rtol=1e-15)
+    # a linear function of the cell-centre coordinates is reproduced wherever
+    # the fine centre lies between two coarse centres
+    zc, ycc, xc = np.meshgrid(*[(np.arange(c) + 0.5) * s for c in C], indexing="ij")
+    lin = 0.3 * xc - 1.1 * ycc + 0.7 * zc
+    out = net.prolong(lin, shape, s)
+    zf, yf, xf = np.meshgrid(*[np.arange(n) + 0.5 for n in shape], indexing="ij")
+    ref = 0.3 * xf - 1.1 * yf + 0.7 * zf
+    inner = tuple(slice(s // 2 + 1, (c - 1) * s + s // 2 - 1 if s > 1 else n) for c, n in zip(C, shape))
+    np.testing.assert_allclose(out[inner], ref[inner], rtol=1e-12, atol=1e-12)
+    if s == 1:
+        np.testing.assert_allclose(out, ref, rtol=1e-14, atol=1e-14)
