@@ -173,7 +173,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--out", default="warmstart.npz")
     ap.add_argument("--init", default=None, help="start from this network (.npz)")
-    ap.add_argument("--stride", type=int, default=4, help="input stride of the network")
+    ap.add_argument("--stride", default="4", help="input stride(s) of the network, e.g. 2,4 (one net each)")
     ap.add_argument("--city-size", default="96x96x48")
     ap.add_argument("--lattice", type=int, default=16, help="lattice scenes (seeds)")
     ap.add_argument("--cities", type=int, default=8, help="random-city scenes")
@@ -198,22 +198,26 @@ def main(argv=None):
     data = generate(training_scenes(a.lattice, a.cities, a.seed, cs), a.steps, a.spinup, pts, a.seed)
     npairs = sum(v[0].shape[0] for v in data.values())
     print(f"{npairs} pairs in {time.time() - t0:.0f} s", flush=True)
-    net = load(a.init, a.seed) if a.init else les.Net(seed=a.seed)
-    net.stride = a.stride
-    hist = train(net, data, a.iters, a.batch, a.lr, a.seed)
-    save(net, a.out)
-    print(f"trained {a.iters} iterations, final loss {np.mean(hist[-100:]):.4f}; saved {a.out}", flush=True)
     nx, ny, nz = (int(x) for x in a.eval_size.split("x"))
     ev_sc = scene.random_scene(seed=a.seed + 7777, nx=nx, ny=ny, nz=nz, max_sweeps=60000, check_every=20)
-    print(f"evaluation on {ev_sc.name} seed {ev_sc.seed}:", flush=True)
-    res = evaluate(net, ev_sc, a.eval_steps, a.eval_spinup, [int(x) for x in a.schedules.split(",")])
-    out = {"pairs": npairs, "iters": a.iters, "final_loss": float(np.mean(hist[-100:])),
-           "loss_first": float(np.mean(hist[:100])), "eval_scene": ev_sc.name, "eval": res}
-    print(json.dumps(out), flush=True)
+    report = {"pairs": npairs, "iters": a.iters, "eval_scene": ev_sc.name, "nets": {}}
+    for st in (int(x) for x in a.stride.split(",")):
+        net = load(a.init, a.seed) if a.init else les.Net(seed=a.seed)
+        net.stride = st
+        hist = train(net, data, a.iters, a.batch, a.lr, a.seed)
+        out = a.out if "," not in a.stride else a.out.replace(".npz", f"_s{st}.npz")
+        save(net, out)
+        print(f"stride {st}: trained {a.iters} iterations, final loss {np.mean(hist[-100:]):.4f}; saved {out}",
+              flush=True)
+        print(f"evaluation on {ev_sc.name} seed {ev_sc.seed}:", flush=True)
+        res = evaluate(net, ev_sc, a.eval_steps, a.eval_spinup, [int(x) for x in a.schedules.split(",")])
+        report["nets"][st] = {"final_loss": float(np.mean(hist[-100:])), "loss_first": float(np.mean(hist[:100])),
+                              "file": out, "eval": res}
+        net.close()
+    print(json.dumps(report), flush=True)
     if a.json:
         with open(a.json, "w") as f:
-            json.dump(out, f, indent=1)
-    net.close()
+            json.dump(report, f, indent=1)
 
 
 if __name__ == "__main__":
