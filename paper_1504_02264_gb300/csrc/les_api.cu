@@ -1,5 +1,6 @@
 // Host side of the C ABI declared in include/les.h: handle, validation,
 // device allocation, host <-> device staging and the per-step launch order.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -125,6 +126,7 @@ struct les_s {
     double* warm_scal = nullptr;          // [0] input scale, [1] line-search step
     double n_unk = 0.0;                   // number of Poisson unknowns
     int net_every = 0;                    // sweeps between network corrections inside a solve (0: start only)
+    long long net_gen = -1;               // network workspace generation the chunk graphs were captured with
     bool record = false;
     int rec_after = 0;                    // record at the first refinement after this many sweeps
     bool rec_taken = false;               // the current solve has taken its pair's input
@@ -316,14 +318,16 @@ CondArgs cond_args(const les_s* h, int mode, int n, int gate) {
 // the energy-norm line search, then form the FP64 residual again (`mode` is
 // RES_INIT at the start of a solve, RES_LOOP inside it, where the new
 // residual may already pass the stop test).
+// `gated`: captured inside a chunk graph, every kernel returns at once once
+// the solve is done.
 template <typename T>
-int net_correct(les_s* h, const Geo<T>& g, int mode, cudaStream_t st) {
-    int rc = net_predict(h->net, h->d, (const float*)h->rr, h->flags, h->pred, st);
+int net_correct(les_s* h, const Geo<T>& g, int mode, cudaStream_t st, bool gated = false) {
+    int rc = net_predict(h->net, h->d, (const float*)h->rr, h->flags, h->pred, st, gated ? &h->sc->done : nullptr);
     if (rc) return fail(h, rc, "network prediction failed");
     h->launches += net_launches(h->net);
     h->launches += launch_warm<T>(g, (const T*)h->rr, h->pred, h->ph[h->cur], h->warm_scal + 1, reducer(h), st);
     h->launches += launch_residual64<T>(g, h->ph[h->cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h),
-                                        cond_args(h, mode, 0, 0), st);
+                                        cond_args(h, mode, 0, gated ? 2 : 0), st);
     CK(cudaGetLastError());
     return LES_OK;
 }
@@ -403,8 +407,9 @@ int sor_solve(les_s* h) {
         conv = h->sc_host->converged != 0;
     }
     while (sweeps < G.max_sweeps && !conv) {
-        const int n = G.fixed_sweeps ? G.max_sweeps
-                                     : (G.check_every < G.max_sweeps - sweeps ? G.check_every : G.max_sweeps - sweeps);
+        int n = G.fixed_sweeps ? G.max_sweeps
+                               : (G.check_every < G.max_sweeps - sweeps ? G.check_every : G.max_sweeps - sweeps);
+        if (net_loop && !G.fixed_sweeps) n = std::min(n, std::max(1, h->net_every - (sweeps - last_net)));
         rec(h, 2);
         long long nl = 0;
         run_sweeps<T>(h, g, n, fresh ? 1 : 0, nl, h->stream);
@@ -594,6 +599,11 @@ int capture_end(les_s* h, cudaStream_t cs, cudaGraphExec_t* out) {
     return LES_OK;
 }
 
+// the network correction runs inside the solve loop (FP32 grids)
+bool net_in_loop(const les_s* h) {
+    return h->prec == LES_FP32 && h->warm == LES_WARM_NET && h->net && h->net_every > 0;
+}
+
 template <typename T>
 int build_graph(les_s* h, int cur) {
     Geo<T> g = geo<T>(h);
@@ -603,6 +613,15 @@ int build_graph(les_s* h, int cur) {
     const long long l0 = h->launches;
     h->cur = cur;
     h->dcur = 0;
+    if (net_in_loop(h)) {
+        // allocate the network's workspace before the capture
+        int rp = net_prepare(h->net, h->d, &h->net_gen);
+        if (rp) {
+            h->cur = save_cur;
+            h->dcur = save_dcur;
+            return fail(h, rp, "network workspace");
+        }
+    }
     int rc = capture_begin<T>(h, cs);
     if (rc) return rc;
     long long nl = 0;
@@ -613,6 +632,20 @@ int build_graph(les_s* h, int cur) {
         run_sweeps<T>(h, g, G.max_sweeps, 1, nl, cs);
         launch_refine<T>(h, g, cond_args(h, RES_FIXED, G.max_sweeps, 0), cs);
         launch_project_step<T>(h, g, cur, cs);
+    } else if (net_in_loop(h)) {
+        // cycles of net_every sweeps, a forced refinement, the network
+        // correction and the residual again, all gated on `done`
+        if constexpr (std::is_same<T, float>::value) {
+            for (int b = 0; b < kChunkBatches; ++b) {
+                run_sweeps<T>(h, g, h->net_every, 2, nl, cs);     // net_every even: d returns to dl[0]
+                CondArgs ca = cond_args(h, RES_LOOP, h->net_every, 1);
+                ca.force = 1;
+                launch_sor_est<T>(g, (const T*)h->dl[h->dcur], (const T*)h->rr, reducer(h), ca, cs);
+                launch_refine<T>(h, g, cond_args(h, RES_LOOP, h->net_every, 1), cs);
+                rc = net_correct<T>(h, g, RES_LOOP, cs, true);
+                if (rc) break;
+            }
+        }
     } else {
         for (int b = 0; b < kChunkBatches; ++b) {
             run_sweeps<T>(h, g, G.check_every, 2, nl, cs);     // check_every even: d returns to dl[0]
@@ -621,7 +654,10 @@ int build_graph(les_s* h, int cur) {
             launch_refine<T>(h, g, cond_args(h, RES_LOOP, G.check_every, 1), cs);
         }
     }
-    rc = capture_end<T>(h, cs, &h->gexec[cur]);
+    {
+        const int rc2 = capture_end<T>(h, cs, &h->gexec[cur]);
+        if (!rc) rc = rc2;
+    }
     h->cur = save_cur;
     h->dcur = save_dcur;
     h->launches = l0;          // capture launches nothing
@@ -635,6 +671,7 @@ void fill_stats(les_s* h, les_stats_t* st, int status);
 template <typename T>
 int step_graph(les_s* h, int nsteps, les_stats_t* stats) {
     const les_grid_t& G = h->g;
+    if (net_in_loop(h) && net_generation(h->net) != h->net_gen) h->graph_ok[0] = h->graph_ok[1] = false;
     for (int c = 0; c < 2; ++c)
         if (!h->graph_ok[c]) {
             int rc = build_graph<T>(h, c);
@@ -642,7 +679,7 @@ int step_graph(les_s* h, int nsteps, les_stats_t* stats) {
         }
     Geo<T> g = geo<T>(h);
     CK(cudaMemsetAsync(&h->sc->noconv_any, 0, sizeof(int), h->stream));
-    const int per_chunk = kChunkBatches * G.check_every;
+    const int per_chunk = kChunkBatches * (net_in_loop(h) ? h->net_every : G.check_every);
     const int max_chunks = (G.max_sweeps + per_chunk - 1) / per_chunk + 1;
     for (int s = 0; s < nsteps; ++s) {
         if (G.fixed_sweeps) {
@@ -658,10 +695,12 @@ int step_graph(les_s* h, int nsteps, les_stats_t* stats) {
                 int rs = solve_start<T>(h, g, h->stream);
                 if (rs) return rs;
             }
+            const long long per_batch = net_in_loop(h) ? h->net_every + 3 + net_launches(h->net) + 3
+                                                       : G.check_every + 3;
             for (int c = 0; c < max_chunks; ++c) {
                 CK(cudaGraphLaunch(h->gexec[h->cur], h->stream));
                 CK(cudaEventRecord(h->chunk_ev[c & 1], h->stream));
-                h->launches += kChunkBatches * (G.check_every + 3);
+                h->launches += kChunkBatches * per_batch;
                 if (c >= 1) {
                     CK(cudaEventSynchronize(h->chunk_ev[(c - 1) & 1]));
                     if (*(volatile int*)h->done_host) break;
@@ -1080,10 +1119,11 @@ int les_step(les_handle h, int32_t nsteps, les_stats_t* stats) {
     // network corrections inside a solve and recording after the start run
     // from the host loop
     const bool extras = h->record || h->warm != LES_WARM_PREV;
-    const bool host_only = (h->warm == LES_WARM_NET && h->net_every > 0) || (h->record && h->rec_after > 0);
+    const bool host_only = h->record && h->rec_after > 0;
+    const int cycle = net_in_loop(h) ? h->net_every : h->g.check_every;
     const bool graph_ok = h->use_graph && !h->timing && !host_only &&
                           ((h->g.fixed_sweeps && !extras) ||
-                           (!h->g.fixed_sweeps && h->g.check_every % 2 == 0 && h->g.max_sweeps % h->g.check_every == 0));
+                           (!h->g.fixed_sweeps && cycle % 2 == 0 && h->g.max_sweeps % cycle == 0));
     h->last_graph = graph_ok;
     if (graph_ok) {
         int rc = h->prec == LES_FP64 ? step_graph<double>(h, nsteps, stats) : step_graph<float>(h, nsteps, stats);
@@ -1222,6 +1262,7 @@ int les_set_warmstart(les_handle h, int32_t mode, les_net net) {
     if (mode == LES_WARM_PREV || mode == LES_WARM_ZERO) {
         h->warm = mode;
         h->net = nullptr;
+        h->graph_ok[0] = h->graph_ok[1] = false;
         return LES_OK;
     }
     if (mode != LES_WARM_NET || !net) return fail(h, LES_EINVAL, "bad warm-start mode or NULL network");
@@ -1233,6 +1274,7 @@ int les_set_warmstart(les_handle h, int32_t mode, les_net net) {
     }
     h->warm = LES_WARM_NET;
     h->net = net;
+    h->graph_ok[0] = h->graph_ok[1] = false;
     return LES_OK;
 }
 
@@ -1240,6 +1282,7 @@ int les_set_net_schedule(les_handle h, int32_t every_sweeps) {
     if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
     if (every_sweeps < 0) return fail(h, LES_EINVAL, "every_sweeps must be >= 0");
     h->net_every = every_sweeps;
+    h->graph_ok[0] = h->graph_ok[1] = false;
     return LES_OK;
 }
 

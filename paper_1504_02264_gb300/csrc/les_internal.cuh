@@ -74,7 +74,8 @@ struct CondArgs {
     int mode;               // ResMode
     int n;                  // sweeps in the batch just finished (estimate / fixed)
     int limit;              // sweep budget of the solve (max_sweeps)
-    int gate;               // 1: run only while !done and a refinement was asked for
+    int gate;               // 1: run only while !done and a refinement was asked for; 2: only while !done
+    int force;              // estimate: ask for a refinement whatever the estimate says
     double tol;
     int* done_host;         // mapped host copy of `done` (nullable)
 };
@@ -177,7 +178,13 @@ namespace les {
 // network prediction on a solver grid (les_net.cu): the padded residual and
 // the unknown flags in, the correction direction as a dense (nz, ny, nx)
 // array out (zero off the unknowns)
+// (`gate` nullable: every kernel returns at once while *gate != 0)
 int net_predict(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, float* out_dense,
-                cudaStream_t s);
+                cudaStream_t s, const int* gate = nullptr);
 int net_launches(const les_net_s* n);
+// size the network's workspace for a solver grid ahead of a graph capture; the
+// generation changes whenever the workspace is reallocated (captured graphs
+// holding the old buffers must then be rebuilt)
+int net_prepare(les_net_s* n, const Dom& d, long long* generation);
+long long net_generation(const les_net_s* n);
 }  // namespace les

@@ -647,7 +647,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_residual64(Geo<T> g, const double* ph, const T* rhs, T* r, double vfluid,
                                                     Reduce red, CondArgs ca) {
     const Dom& d = g.d;
-    if (ca.gate && (red.sc->done || !red.sc->refine)) return;     // uniform over the grid
+    if (ca.gate == 1 && (red.sc->done || !red.sc->refine)) return;     // uniform over the grid
+    if (ca.gate == 2 && red.sc->done) return;
     const int n = d.nx * d.ny * d.nz;
     const double mean = red.sc->rhs_mean;
     double x[3] = {0.0, 0.0, 0.0};
@@ -767,8 +768,8 @@ __global__ void __launch_bounds__(256) k_sor_est(Geo<T> g, const T* dl, const T*
             sc->sweeps += ca.n;
             sc->since += ca.n;
             sc->zflag = 0;
-            const bool need = !(est > ca.tol) || est <= kRefineDrop * sc->rho_ref || sc->since >= kRefineEvery ||
-                              sc->sweeps >= ca.limit;
+            const bool need = ca.force || !(est > ca.tol) || est <= kRefineDrop * sc->rho_ref ||
+                              sc->since >= kRefineEvery || sc->sweeps >= ca.limit;
             sc->refine = need;
         }
     }
@@ -896,6 +897,7 @@ int launch_rhs_eff(const Geo<T>& g, const T* rhs, T* out, const Scalars* sc, cud
 template <typename T>
 __global__ void k_warm_ls(Geo<T> g, const T* r, const float* q, double* alpha, Reduce red) {
     const Dom& d = g.d;
+    if (red.sc->done) return;      // uniform over the grid
     const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
     const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
     const int k = blockIdx.z + 1;
@@ -937,8 +939,9 @@ __global__ void k_warm_ls(Geo<T> g, const T* r, const float* q, double* alpha, R
 }
 
 template <typename T>
-__global__ void k_warm_apply(Geo<T> g, double* ph, const float* q, const double* alpha) {
+__global__ void k_warm_apply(Geo<T> g, double* ph, const float* q, const double* alpha, const Scalars* sc) {
     const Dom& d = g.d;
+    if (sc->done) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
     const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
     const int k = blockIdx.z + 1;
@@ -953,7 +956,7 @@ int launch_warm(const Geo<T>& g, const T* r, const float* q, double* ph, double*
     const Dom& d = g.d;
     const dim3 grid((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), blk(32, 8);
     k_warm_ls<T><<<grid, blk, 0, s>>>(g, r, q, alpha, red);
-    k_warm_apply<T><<<grid, blk, 0, s>>>(g, ph, q, alpha);
+    k_warm_apply<T><<<grid, blk, 0, s>>>(g, ph, q, alpha, red.sc);
     return 2;
 }
 

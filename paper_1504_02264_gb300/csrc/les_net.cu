@@ -54,7 +54,8 @@ double normal_at(uint64_t seed, uint64_t c) {
 }
 
 // per-sample RMS over the mask: out[b] = sqrt(sum mask*a^2 / sum mask)
-__global__ void k_rms(const float* a, const float* mask, size_t n, double* out) {
+__global__ void k_rms(const float* a, const float* mask, size_t n, double* out, const int* gate) {
+    if (gate && *(volatile const int*)gate) return;
     const size_t base = (size_t)blockIdx.y * n;
     double s = 0.0, m = 0.0;
     for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
@@ -71,7 +72,8 @@ __global__ void k_rms(const float* a, const float* mask, size_t n, double* out) 
         atomicAdd(&out[2 * blockIdx.y + 1], m);
     }
 }
-__global__ void k_rms_final(double* acc, int b) {
+__global__ void k_rms_final(double* acc, int b, const int* gate) {
+    if (gate && *(volatile const int*)gate) return;
     const int q = threadIdx.x;
     if (q < b) {
         const double m = acc[2 * q + 1];
@@ -79,7 +81,9 @@ __global__ void k_rms_final(double* acc, int b) {
     }
 }
 // dense input: channel 0 = r / scale, channel 1 = mask
-__global__ void k_pack_dense(const float* r, const float* mask, const double* scale, __nv_bfloat16* xin, size_t n) {
+__global__ void k_pack_dense(const float* r, const float* mask, const double* scale, __nv_bfloat16* xin, size_t n,
+                             const int* gate) {
+    if (gate && *(volatile const int*)gate) return;
     const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
     const float s = (float)(scale[0] > 0.0 ? 1.0 / scale[0] : 0.0);
@@ -117,6 +121,7 @@ struct les_net_s {
     int stride = 1;                     // the network runs on the grid coarsened stride times per axis
     float *rc = nullptr, *mc = nullptr, *tc = nullptr;     // pooled sample (coarse level 0)
     double* dscal = nullptr;            // [0..2B): per-sample rms and mask counts, [62]: loss
+    long long ws_gen = 0;               // bumped whenever the workspace is reallocated
     char err[256] = {0};
 };
 
@@ -212,27 +217,29 @@ int ensure_ws(les_net_s* n, const Level& L0) {
     if ((rc = get(64, sizeof(double), (void**)&n->dscal))) return rc;
     for (int l = 0; l < 4; ++l) n->cap[l] = want[l];
     n->cap_v0 = want[0];
+    n->ws_gen += 1;
     return LES_OK;
 }
 
 // forward on the packed input n->xin with mask n->mask; output n->y
-void forward(les_net_s* n, const Level& L0) {
+// (every kernel returns at once while *gate != 0; gate may be null)
+void forward(les_net_s* n, const Level& L0, const int* gate = nullptr) {
     cudaStream_t s = n->stream;
     const Level L1 = level(L0, 1), L2 = level(L0, 2), L3 = level(L0, 3);
-    nn::conv3_fwd(n->xin, n->wb[0], n->e[0], nullptr, nullptr, L0.X, L0.Y, L0.Z, 16, 16, 1, s);
-    nn::pool(n->e[0], n->p[0], L0.X, L0.Y, L0.Z, 16, s);
-    nn::conv3_fwd(n->p[0], n->wb[1], n->e[1], nullptr, nullptr, L1.X, L1.Y, L1.Z, 16, 32, 1, s);
-    nn::pool(n->e[1], n->p[1], L1.X, L1.Y, L1.Z, 32, s);
-    nn::conv3_fwd(n->p[1], n->wb[2], n->e[2], nullptr, nullptr, L2.X, L2.Y, L2.Z, 32, 64, 1, s);
-    nn::pool(n->e[2], n->p[2], L2.X, L2.Y, L2.Z, 64, s);
-    nn::conv3_fwd(n->p[2], n->wb[3], n->e[3], nullptr, nullptr, L3.X, L3.Y, L3.Z, 64, 128, 1, s);
-    nn::up(n->e[3], n->u[2], L2.X, L2.Y, L2.Z, 128, s);
-    nn::conv3_fwd(n->u[2], n->wb[4], n->r[2], n->e[2], n->dd[2], L2.X, L2.Y, L2.Z, 128, 64, 1, s);
-    nn::up(n->dd[2], n->u[1], L1.X, L1.Y, L1.Z, 64, s);
-    nn::conv3_fwd(n->u[1], n->wb[5], n->r[1], n->e[1], n->dd[1], L1.X, L1.Y, L1.Z, 64, 32, 1, s);
-    nn::up(n->dd[1], n->u[0], L0.X, L0.Y, L0.Z, 32, s);
-    nn::conv3_fwd(n->u[0], n->wb[6], n->r[0], n->e[0], n->dd[0], L0.X, L0.Y, L0.Z, 32, 16, 1, s);
-    nn::head(n->dd[0], n->w32 + n->off[kConvs], n->mask, n->y, L0.v(), kHeadC, s);
+    nn::conv3_fwd(n->xin, n->wb[0], n->e[0], nullptr, nullptr, L0.X, L0.Y, L0.Z, 16, 16, 1, s, gate);
+    nn::pool(n->e[0], n->p[0], L0.X, L0.Y, L0.Z, 16, s, gate);
+    nn::conv3_fwd(n->p[0], n->wb[1], n->e[1], nullptr, nullptr, L1.X, L1.Y, L1.Z, 16, 32, 1, s, gate);
+    nn::pool(n->e[1], n->p[1], L1.X, L1.Y, L1.Z, 32, s, gate);
+    nn::conv3_fwd(n->p[1], n->wb[2], n->e[2], nullptr, nullptr, L2.X, L2.Y, L2.Z, 32, 64, 1, s, gate);
+    nn::pool(n->e[2], n->p[2], L2.X, L2.Y, L2.Z, 64, s, gate);
+    nn::conv3_fwd(n->p[2], n->wb[3], n->e[3], nullptr, nullptr, L3.X, L3.Y, L3.Z, 64, 128, 1, s, gate);
+    nn::up(n->e[3], n->u[2], L2.X, L2.Y, L2.Z, 128, s, gate);
+    nn::conv3_fwd(n->u[2], n->wb[4], n->r[2], n->e[2], n->dd[2], L2.X, L2.Y, L2.Z, 128, 64, 1, s, gate);
+    nn::up(n->dd[2], n->u[1], L1.X, L1.Y, L1.Z, 64, s, gate);
+    nn::conv3_fwd(n->u[1], n->wb[5], n->r[1], n->e[1], n->dd[1], L1.X, L1.Y, L1.Z, 64, 32, 1, s, gate);
+    nn::up(n->dd[1], n->u[0], L0.X, L0.Y, L0.Z, 32, s, gate);
+    nn::conv3_fwd(n->u[0], n->wb[6], n->r[0], n->e[0], n->dd[0], L0.X, L0.Y, L0.Z, 32, 16, 1, s, gate);
+    nn::head(n->dd[0], n->w32 + n->off[kConvs], n->mask, n->y, L0.v(), kHeadC, s, gate);
 }
 
 // backward from n->gy; accumulates the parameter gradients into n->g32
@@ -287,16 +294,17 @@ void refresh_copies(les_net_s* n) {
 
 // pack a dense coarse sample (r, mask, optional target t) into the network
 // input and normalise the target; nmask receives sum(mask) when asked
-int pack_sample(les_net_s* n, const Level& L0, const float* r, const float* mask, const float* t, double* nmask) {
+int pack_sample(les_net_s* n, const Level& L0, const float* r, const float* mask, const float* t, double* nmask,
+                const int* gate = nullptr) {
     const size_t v = L0.v();
     cudaStream_t s = n->stream;
     NCK(cudaMemsetAsync(n->dscal, 0, 4 * sizeof(double), s));
     const unsigned blocks = (unsigned)((v + 255) / 256 < 1024 ? (v + 255) / 256 : 1024);
-    k_rms<<<dim3(blocks, 1), 256, 0, s>>>(r, mask, v, n->dscal);
-    if (t) k_rms<<<dim3(blocks, 1), 256, 0, s>>>(t, mask, v, n->dscal + 2);
-    k_rms_final<<<1, 32, 0, s>>>(n->dscal, t ? 2 : 1);
+    k_rms<<<dim3(blocks, 1), 256, 0, s>>>(r, mask, v, n->dscal, gate);
+    if (t) k_rms<<<dim3(blocks, 1), 256, 0, s>>>(t, mask, v, n->dscal + 2, gate);
+    k_rms_final<<<1, 32, 0, s>>>(n->dscal, t ? 2 : 1, gate);
     if (mask != n->mask) NCK(cudaMemcpyAsync(n->mask, mask, v * sizeof(float), cudaMemcpyDeviceToDevice, s));
-    k_pack_dense<<<(unsigned)((v + 255) / 256), 256, 0, s>>>(r, n->mask, n->dscal, n->xin, v);
+    k_pack_dense<<<(unsigned)((v + 255) / 256), 256, 0, s>>>(r, n->mask, n->dscal, n->xin, v, gate);
     if (t) k_scale<<<(unsigned)((v + 255) / 256), 256, 0, s>>>(t, n->dscal + 2, n->tn, v);
     NCK(cudaGetLastError());
     if (nmask) {
@@ -355,20 +363,26 @@ int batch_grad(les_net_s* n, const Level& Lf, const float* r, const float* mask,
 // solver-side inference (les_api.cu): predicted correction direction on the
 // handle's grid from its padded residual (float) and flags
 namespace les {
+int net_prepare(les_net_s* n, const Dom& d, long long* generation) {
+    int rc = ensure_ws(n, coarse(n, Level{d.nx, d.ny, d.nz}));
+    if (generation) *generation = n->ws_gen;
+    return rc;
+}
+long long net_generation(const les_net_s* n) { return n->ws_gen; }
 int net_predict(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, float* out_dense,
-                cudaStream_t s) {
+                cudaStream_t s, const int* gate) {
     const Level Lf{d.nx, d.ny, d.nz};
     const Level L0 = coarse(n, Lf);
     cudaStream_t keep = n->stream;
     n->stream = s;
     int rc = ensure_ws(n, L0);
     if (!rc) {
-        nn::pool_padded_s(r_padded, flags, d, n->stride, n->rc, n->mc, s);
-        rc = pack_sample(n, L0, n->rc, n->mc, nullptr, nullptr);
+        nn::pool_padded_s(r_padded, flags, d, n->stride, n->rc, n->mc, s, gate);
+        rc = pack_sample(n, L0, n->rc, n->mc, nullptr, nullptr, gate);
     }
     if (!rc) {
-        forward(n, L0);
-        nn::prolong_flags(n->y, flags, d, n->stride, out_dense, s);
+        forward(n, L0, gate);
+        nn::prolong_flags(n->y, flags, d, n->stride, out_dense, s, gate);
         if (cudaGetLastError() != cudaSuccess) rc = LES_ECUDA;
     }
     n->stream = keep;

@@ -9,24 +9,32 @@ namespace les {
 namespace nn {
 
 void conv3_fwd(const __nv_bfloat16* x, const __nv_bfloat16* w, __nv_bfloat16* y, const __nv_bfloat16* skip,
-               __nv_bfloat16* ysum, int X, int Y, int Z, int Cin, int Cout, int relu, cudaStream_t s);
+               __nv_bfloat16* ysum, int X, int Y, int Z, int Cin, int Cout, int relu, cudaStream_t s,
+               const int* gate = nullptr);
 void wflip(const __nv_bfloat16* w, __nv_bfloat16* wt, int Cin, int Cout, cudaStream_t s);
 void conv3_wgrad(const __nv_bfloat16* x, const __nv_bfloat16* dy, float* dw, int X, int Y, int Z, int Cin, int Cout,
                  cudaStream_t s);
-void pool(const __nv_bfloat16* a, __nv_bfloat16* b, int X, int Y, int Z, int C, cudaStream_t s);
+// `gate` (nullable): the kernels return at once while *gate != 0 (a solve's
+// done flag when the inference is captured inside a CUDA graph)
+void pool(const __nv_bfloat16* a, __nv_bfloat16* b, int X, int Y, int Z, int C, cudaStream_t s,
+          const int* gate = nullptr);
 void pool_bwd(const __nv_bfloat16* gb, __nv_bfloat16* ga, int X, int Y, int Z, int C, cudaStream_t s);
-void up(const __nv_bfloat16* b, __nv_bfloat16* a, int X, int Y, int Z, int C, cudaStream_t s);
+void up(const __nv_bfloat16* b, __nv_bfloat16* a, int X, int Y, int Z, int C, cudaStream_t s,
+        const int* gate = nullptr);
 void up_bwd(const __nv_bfloat16* ga, __nv_bfloat16* gb, int X, int Y, int Z, int C, cudaStream_t s);
 void relu_bwd(const __nv_bfloat16* post, const __nv_bfloat16* g, const __nv_bfloat16* g2, __nv_bfloat16* out,
               size_t n, cudaStream_t s);
 void add(const __nv_bfloat16* a, const __nv_bfloat16* b, __nv_bfloat16* out, size_t n, cudaStream_t s);
-void head(const __nv_bfloat16* d, const float* w1, const float* mask, float* y, size_t nv, int C, cudaStream_t s);
+void head(const __nv_bfloat16* d, const float* w1, const float* mask, float* y, size_t nv, int C, cudaStream_t s,
+          const int* gate = nullptr);
 void head_bwd(const __nv_bfloat16* d, const float* w1, const float* mask, const float* gy, __nv_bfloat16* gd,
               float* dw1, size_t nv, int C, cudaStream_t s);
 void pool_dense_s(const float* a, float* b, int Xf, int Yf, int Zf, int st, cudaStream_t s);
-void pool_padded_s(const float* r, const uint8_t* flags, const Dom& d, int st, float* rc, float* mc, cudaStream_t s);
+void pool_padded_s(const float* r, const uint8_t* flags, const Dom& d, int st, float* rc, float* mc, cudaStream_t s,
+                   const int* gate = nullptr);
 void prolong_dense(const float* yc, const float* mask, float* out, int Xf, int Yf, int Zf, int st, cudaStream_t s);
-void prolong_flags(const float* yc, const uint8_t* flags, const Dom& d, int st, float* out, cudaStream_t s);
+void prolong_flags(const float* yc, const uint8_t* flags, const Dom& d, int st, float* out, cudaStream_t s,
+                   const int* gate = nullptr);
 void mse(const float* y, const float* t, const float* mask, float* g, double* loss, size_t n, double inv_n,
          cudaStream_t s);
 void adam(float* w, float* m, float* v, const float* g, __nv_bfloat16* wb, size_t n, float lr, float b1, float b2,

@@ -54,7 +54,8 @@ template <int CO>
 __global__ void __launch_bounds__(256)
 k_conv3(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ w, __nv_bfloat16* __restrict__ y,
         const __nv_bfloat16* __restrict__ skip, __nv_bfloat16* __restrict__ ysum, int X, int Y, int Z, int Cin,
-        int Cout, int relu) {
+        int Cout, int relu, const int* gate) {
+    if (gate && *(volatile const int*)gate) return;      // the solve this inference serves has ended
     __shared__ __align__(16) __nv_bfloat16 sIn[HZ][HY][HX][16];
     __shared__ __align__(16) __nv_bfloat16 sW[27][CO][16];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -135,14 +136,15 @@ k_conv3(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ w
 }
 
 void conv3_fwd(const __nv_bfloat16* x, const __nv_bfloat16* w, __nv_bfloat16* y, const __nv_bfloat16* skip,
-               __nv_bfloat16* ysum, int X, int Y, int Z, int Cin, int Cout, int relu, cudaStream_t s) {
+               __nv_bfloat16* ysum, int X, int Y, int Z, int Cin, int Cout, int relu, cudaStream_t s,
+               const int* gate) {
     const int co = Cout >= 32 ? 32 : 16;
     const int ntz = (Z + TZ - 1) / TZ;
     dim3 grid((X + TX - 1) / TX, (Y + TY - 1) / TY, ntz * ((Cout + co - 1) / co));
     if (co == 32)
-        k_conv3<32><<<grid, 256, 0, s>>>(x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu);
+        k_conv3<32><<<grid, 256, 0, s>>>(x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu, gate);
     else
-        k_conv3<16><<<grid, 256, 0, s>>>(x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu);
+        k_conv3<16><<<grid, 256, 0, s>>>(x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu, gate);
 }
 
 // dgrad weights: W'[tap][ci][co] = W[26 - tap][co][ci] (flipped taps, swapped roles)
@@ -255,7 +257,8 @@ void conv3_wgrad(const __nv_bfloat16* x, const __nv_bfloat16* dy, float* dw, int
 // elementwise pieces
 
 // 2x2x2 average pool (children outside the fine grid count as zero)
-__global__ void k_pool(const __nv_bfloat16* a, __nv_bfloat16* b, int X, int Y, int Z, int C) {
+__global__ void k_pool(const __nv_bfloat16* a, __nv_bfloat16* b, int X, int Y, int Z, int C, const int* gate) {
+    if (gate && *(volatile const int*)gate) return;
     const int Xc = (X + 1) / 2, Yc = (Y + 1) / 2, Zc = (Z + 1) / 2;
     const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= (size_t)Xc * Yc * Zc * C) return;
@@ -280,7 +283,8 @@ __global__ void k_pool_bwd(const __nv_bfloat16* gb, __nv_bfloat16* ga, int X, in
     ga[q] = __float2bfloat16(0.125f * __bfloat162float(gb[(((size_t)(z / 2) * Yc + yv / 2) * Xc + x / 2) * C + c]));
 }
 // nearest upsample: fine voxel takes its parent's value
-__global__ void k_up(const __nv_bfloat16* b, __nv_bfloat16* a, int X, int Y, int Z, int C) {
+__global__ void k_up(const __nv_bfloat16* b, __nv_bfloat16* a, int X, int Y, int Z, int C, const int* gate) {
+    if (gate && *(volatile const int*)gate) return;
     const int Xc = (X + 1) / 2, Yc = (Y + 1) / 2;
     const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= (size_t)X * Y * Z * C) return;
@@ -319,7 +323,9 @@ __global__ void k_add(const __nv_bfloat16* a, const __nv_bfloat16* b, __nv_bfloa
 }
 
 // head: y[v] = mask[v] * sum_c w1[c] * d[v][c]  (FP32 output)
-__global__ void k_head(const __nv_bfloat16* d, const float* w1, const float* mask, float* y, size_t nv, int C) {
+__global__ void k_head(const __nv_bfloat16* d, const float* w1, const float* mask, float* y, size_t nv, int C,
+                       const int* gate) {
+    if (gate && *(volatile const int*)gate) return;
     const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
     float s = 0.f;
@@ -374,7 +380,9 @@ __global__ void k_pool_dense_s(const float* a, float* b, int Xf, int Yf, int Zf,
 }
 
 // the solver's padded residual (unknowns only) and unknown mask -> dense coarse
-__global__ void k_pool_padded_s(const float* r, const uint8_t* flags, Dom d, int s, float* rc, float* mc) {
+__global__ void k_pool_padded_s(const float* r, const uint8_t* flags, Dom d, int s, float* rc, float* mc,
+                                const int* gate) {
+    if (gate && *(volatile const int*)gate) return;
     const int Xc = (d.nx + s - 1) / s, Yc = (d.ny + s - 1) / s, Zc = (d.nz + s - 1) / s;
     const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= (size_t)Xc * Yc * Zc) return;
@@ -437,7 +445,8 @@ __global__ void k_prolong_dense(const float* yc, const float* mask, float* out, 
     out[q] = mask[q] * trilinear(yc, Xc, Yc, Zc, s, x, y, z);
 }
 // dense fine output on the solver's unknowns
-__global__ void k_prolong_flags(const float* yc, const uint8_t* flags, Dom d, int s, float* out) {
+__global__ void k_prolong_flags(const float* yc, const uint8_t* flags, Dom d, int s, float* out, const int* gate) {
+    if (gate && *(volatile const int*)gate) return;
     const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= (size_t)d.nx * d.ny * d.nz) return;
     const int x = q % d.nx, y = (q / d.nx) % d.ny, z = q / ((size_t)d.nx * d.ny);
@@ -481,14 +490,15 @@ __global__ void k_to_bf16(const float* a, __nv_bfloat16* b, size_t n) {
 
 static unsigned blocks_for(size_t n) { return (unsigned)((n + 255) / 256); }
 
-void pool(const __nv_bfloat16* a, __nv_bfloat16* b, int X, int Y, int Z, int C, cudaStream_t s) {
-    k_pool<<<blocks_for((size_t)((X + 1) / 2) * ((Y + 1) / 2) * ((Z + 1) / 2) * C), 256, 0, s>>>(a, b, X, Y, Z, C);
+void pool(const __nv_bfloat16* a, __nv_bfloat16* b, int X, int Y, int Z, int C, cudaStream_t s, const int* gate) {
+    k_pool<<<blocks_for((size_t)((X + 1) / 2) * ((Y + 1) / 2) * ((Z + 1) / 2) * C), 256, 0, s>>>(a, b, X, Y, Z, C,
+                                                                                                  gate);
 }
 void pool_bwd(const __nv_bfloat16* gb, __nv_bfloat16* ga, int X, int Y, int Z, int C, cudaStream_t s) {
     k_pool_bwd<<<blocks_for((size_t)X * Y * Z * C), 256, 0, s>>>(gb, ga, X, Y, Z, C);
 }
-void up(const __nv_bfloat16* b, __nv_bfloat16* a, int X, int Y, int Z, int C, cudaStream_t s) {
-    k_up<<<blocks_for((size_t)X * Y * Z * C), 256, 0, s>>>(b, a, X, Y, Z, C);
+void up(const __nv_bfloat16* b, __nv_bfloat16* a, int X, int Y, int Z, int C, cudaStream_t s, const int* gate) {
+    k_up<<<blocks_for((size_t)X * Y * Z * C), 256, 0, s>>>(b, a, X, Y, Z, C, gate);
 }
 void up_bwd(const __nv_bfloat16* ga, __nv_bfloat16* gb, int X, int Y, int Z, int C, cudaStream_t s) {
     k_up_bwd<<<blocks_for((size_t)((X + 1) / 2) * ((Y + 1) / 2) * ((Z + 1) / 2) * C), 256, 0, s>>>(ga, gb, X, Y, Z, C);
@@ -500,8 +510,9 @@ void relu_bwd(const __nv_bfloat16* post, const __nv_bfloat16* g, const __nv_bflo
 void add(const __nv_bfloat16* a, const __nv_bfloat16* b, __nv_bfloat16* out, size_t n, cudaStream_t s) {
     k_add<<<blocks_for(n), 256, 0, s>>>(a, b, out, n);
 }
-void head(const __nv_bfloat16* d, const float* w1, const float* mask, float* y, size_t nv, int C, cudaStream_t s) {
-    k_head<<<blocks_for(nv), 256, 0, s>>>(d, w1, mask, y, nv, C);
+void head(const __nv_bfloat16* d, const float* w1, const float* mask, float* y, size_t nv, int C, cudaStream_t s,
+          const int* gate) {
+    k_head<<<blocks_for(nv), 256, 0, s>>>(d, w1, mask, y, nv, C, gate);
 }
 void head_bwd(const __nv_bfloat16* d, const float* w1, const float* mask, const float* gy, __nv_bfloat16* gd,
               float* dw1, size_t nv, int C, cudaStream_t s) {
@@ -511,15 +522,17 @@ void pool_dense_s(const float* a, float* b, int Xf, int Yf, int Zf, int st, cuda
     const size_t n = (size_t)((Xf + st - 1) / st) * ((Yf + st - 1) / st) * ((Zf + st - 1) / st);
     k_pool_dense_s<<<blocks_for(n), 256, 0, s>>>(a, b, Xf, Yf, Zf, st);
 }
-void pool_padded_s(const float* r, const uint8_t* flags, const Dom& d, int st, float* rc, float* mc, cudaStream_t s) {
+void pool_padded_s(const float* r, const uint8_t* flags, const Dom& d, int st, float* rc, float* mc, cudaStream_t s,
+                   const int* gate) {
     const size_t n = (size_t)((d.nx + st - 1) / st) * ((d.ny + st - 1) / st) * ((d.nz + st - 1) / st);
-    k_pool_padded_s<<<blocks_for(n), 256, 0, s>>>(r, flags, d, st, rc, mc);
+    k_pool_padded_s<<<blocks_for(n), 256, 0, s>>>(r, flags, d, st, rc, mc, gate);
 }
 void prolong_dense(const float* yc, const float* mask, float* out, int Xf, int Yf, int Zf, int st, cudaStream_t s) {
     k_prolong_dense<<<blocks_for((size_t)Xf * Yf * Zf), 256, 0, s>>>(yc, mask, out, Xf, Yf, Zf, st);
 }
-void prolong_flags(const float* yc, const uint8_t* flags, const Dom& d, int st, float* out, cudaStream_t s) {
-    k_prolong_flags<<<blocks_for((size_t)d.nx * d.ny * d.nz), 256, 0, s>>>(yc, flags, d, st, out);
+void prolong_flags(const float* yc, const uint8_t* flags, const Dom& d, int st, float* out, cudaStream_t s,
+                   const int* gate) {
+    k_prolong_flags<<<blocks_for((size_t)d.nx * d.ny * d.nz), 256, 0, s>>>(yc, flags, d, st, out, gate);
 }
 void mse(const float* y, const float* t, const float* mask, float* g, double* loss, size_t n, double inv_n,
          cudaStream_t s) {

@@ -275,6 +275,30 @@ def test_warm_start_schedules_converge(net):
         d.close()
 
 
+@pytest.mark.parametrize("stride", [1, 4])
+def test_net_cycle_graph_matches_host_loop(net, stride):
+    """The network correction every 20 sweeps captured in the chunk graphs
+    (device-side early exit) runs exactly the host loop's kernels: identical
+    sweeps and bit-identical fields."""
+    net.stride = stride
+    sc = city(tol=1e-6, max_sweeps=40000, check_every=20)
+    doms = []
+    for graph in (True, False):
+        d = les.Domain(sc)
+        d.set_graph(graph)
+        d.set_warmstart(net)
+        d.set_net_schedule(20)
+        doms.append(d)
+    for _ in range(2):
+        a, b = doms[0].step(), doms[1].step()
+        assert a["graph"] == 1 and b["graph"] == 0
+        assert a["rc"] == b["rc"] == 0 and a["sweeps"] == b["sweeps"], (a, b)
+    for fa, fb in zip(doms[0].fields(), doms[1].fields()):
+        assert np.array_equal(fa, fb)
+    for d in doms:
+        d.close()
+
+
 def test_warm_start_rejects_bad_use(net):
     sc = city()
     d64 = les.Domain(sc, precision=les.LES_FP64)
