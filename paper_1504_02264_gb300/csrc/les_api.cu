@@ -123,6 +123,7 @@ struct les_s {
     int warm = LES_WARM_PREV;
     les_net_s* net = nullptr;
     float* pred = nullptr;                // dense (nz, ny, nx) predicted correction
+    void* rcur = nullptr;                 // current residual written by the estimate (network input in the loop)
     double* warm_scal = nullptr;          // [0] input scale, [1] line-search step
     double n_unk = 0.0;                   // number of Poisson unknowns
     int net_every = 0;                    // sweeps between network corrections inside a solve (0: start only)
@@ -318,16 +319,30 @@ CondArgs cond_args(const les_s* h, int mode, int n, int gate) {
 // the energy-norm line search, then form the FP64 residual again (`mode` is
 // RES_INIT at the start of a solve, RES_LOOP inside it, where the new
 // residual may already pass the stop test).
-// `gated`: captured inside a chunk graph, every kernel returns at once once
-// the solve is done.
 template <typename T>
-int net_correct(les_s* h, const Geo<T>& g, int mode, cudaStream_t st, bool gated = false) {
-    int rc = net_predict(h->net, h->d, (const float*)h->rr, h->flags, h->pred, st, gated ? &h->sc->done : nullptr);
+int net_correct(les_s* h, const Geo<T>& g, cudaStream_t st) {
+    int rc = net_predict(h->net, h->d, (const float*)h->rr, h->flags, h->pred, st);
     if (rc) return fail(h, rc, "network prediction failed");
     h->launches += net_launches(h->net);
-    h->launches += launch_warm<T>(g, (const T*)h->rr, h->pred, h->ph[h->cur], h->warm_scal + 1, reducer(h), st);
+    h->launches += launch_warm<T>(g, (const T*)h->rr, h->pred, h->ph[h->cur], (T*)nullptr, h->warm_scal + 1,
+                                  reducer(h), st);
     h->launches += launch_residual64<T>(g, h->ph[h->cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h),
-                                        cond_args(h, mode, 0, gated ? 2 : 0), st);
+                                        cond_args(h, RES_INIT, 0, 0), st);
+    CK(cudaGetLastError());
+    return LES_OK;
+}
+
+// The network correction inside the solve loop: q = Net(r) from the residual
+// the last estimate stored, the energy-norm step into the FP32 SOR correction
+// (no FP64 pass: the next refinement folds it into p).  `gated`: captured in a
+// chunk graph, every kernel returns at once when the solve is done.
+template <typename T>
+int net_correct_loop(les_s* h, const Geo<T>& g, cudaStream_t st, bool gated) {
+    int rc = net_predict(h->net, h->d, (const float*)h->rcur, h->flags, h->pred, st, gated ? &h->sc->done : nullptr);
+    if (rc) return fail(h, rc, "network prediction failed");
+    h->launches += net_launches(h->net);
+    h->launches += launch_warm<T>(g, (const T*)h->rcur, h->pred, nullptr, (T*)h->dl[h->dcur], h->warm_scal + 1,
+                                  reducer(h), st);
     CK(cudaGetLastError());
     return LES_OK;
 }
@@ -350,7 +365,7 @@ int solve_start(les_s* h, const Geo<T>& g, cudaStream_t st) {
     }
     if constexpr (std::is_same<T, float>::value) {
         if (h->warm == LES_WARM_NET && h->net) {
-            int rc = net_correct<T>(h, g, RES_INIT, st);
+            int rc = net_correct<T>(h, g, st);
             if (rc) return rc;
         }
     }
@@ -418,7 +433,8 @@ int sor_solve(les_s* h) {
         sweeps += n;
         bool need = true;
         if (!G.fixed_sweeps) {
-            h->launches += launch_sor_est<T>(g, (const T*)h->dl[h->dcur], (const T*)h->rr, reducer(h),
+            h->launches += launch_sor_est<T>(g, (const T*)h->dl[h->dcur], (const T*)h->rr,
+                                             net_loop ? (T*)h->rcur : nullptr, reducer(h),
                                              cond_args(h, RES_LOOP, n, 0), h->stream);
             CK(cudaGetLastError());
             int rc = fetch_scalars(h);
@@ -436,7 +452,7 @@ int sor_solve(les_s* h) {
         fresh = false;
         const bool net_due = net_loop && sweeps - last_net >= h->net_every && sweeps < G.max_sweeps;
         const bool rec_due = !recorded && sweeps >= h->rec_after;
-        if (need || net_due || rec_due) {
+        if (need || rec_due) {
             rec(h, 3);
             launch_refine<T>(h, g, cond_args(h, G.fixed_sweeps ? RES_FIXED : RES_LOOP, n, 0), h->stream);
             rec(h, 4);
@@ -451,14 +467,13 @@ int sor_solve(les_s* h) {
                 record_start(h, h->stream);
                 recorded = true;
             }
-            if constexpr (std::is_same<T, float>::value) {
-                if (net_due) {
-                    last_net = sweeps;
-                    if ((rc = net_correct<T>(h, g, RES_LOOP, h->stream))) return rc;
-                    if ((rc = fetch_scalars(h))) return rc;
-                    conv = h->sc_host->converged != 0;
-                    if (conv || h->sc_host->nonfinite) break;
-                }
+        }
+        if constexpr (std::is_same<T, float>::value) {
+            if (net_due) {
+                last_net = sweeps;
+                int rc = net_correct_loop<T>(h, g, h->stream, false);
+                if (rc) return rc;
+                fresh = false;      // the correction now holds the network's step
             }
         }
     }
@@ -638,18 +653,17 @@ int build_graph(les_s* h, int cur) {
         if constexpr (std::is_same<T, float>::value) {
             for (int b = 0; b < kChunkBatches; ++b) {
                 run_sweeps<T>(h, g, h->net_every, 2, nl, cs);     // net_every even: d returns to dl[0]
-                CondArgs ca = cond_args(h, RES_LOOP, h->net_every, 1);
-                ca.force = 1;
-                launch_sor_est<T>(g, (const T*)h->dl[h->dcur], (const T*)h->rr, reducer(h), ca, cs);
+                launch_sor_est<T>(g, (const T*)h->dl[h->dcur], (const T*)h->rr, (T*)h->rcur, reducer(h),
+                                  cond_args(h, RES_LOOP, h->net_every, 1), cs);
                 launch_refine<T>(h, g, cond_args(h, RES_LOOP, h->net_every, 1), cs);
-                rc = net_correct<T>(h, g, RES_LOOP, cs, true);
+                rc = net_correct_loop<T>(h, g, cs, true);
                 if (rc) break;
             }
         }
     } else {
         for (int b = 0; b < kChunkBatches; ++b) {
             run_sweeps<T>(h, g, G.check_every, 2, nl, cs);     // check_every even: d returns to dl[0]
-            launch_sor_est<T>(g, (const T*)h->dl[h->dcur], (const T*)h->rr, reducer(h),
+            launch_sor_est<T>(g, (const T*)h->dl[h->dcur], (const T*)h->rr, (T*)nullptr, reducer(h),
                               cond_args(h, RES_LOOP, G.check_every, 1), cs);
             launch_refine<T>(h, g, cond_args(h, RES_LOOP, G.check_every, 1), cs);
         }
@@ -695,7 +709,7 @@ int step_graph(les_s* h, int nsteps, les_stats_t* stats) {
                 int rs = solve_start<T>(h, g, h->stream);
                 if (rs) return rs;
             }
-            const long long per_batch = net_in_loop(h) ? h->net_every + 3 + net_launches(h->net) + 3
+            const long long per_batch = net_in_loop(h) ? h->net_every + 3 + net_launches(h->net) + 2
                                                        : G.check_every + 3;
             for (int c = 0; c < max_chunks; ++c) {
                 CK(cudaGraphLaunch(h->gexec[h->cur], h->stream));
@@ -1271,6 +1285,7 @@ int les_set_warmstart(les_handle h, int32_t mode, les_net net) {
         int rc = dalloc(h, (void**)&h->pred, (size_t)h->g.nx * h->g.ny * h->g.nz * sizeof(float));
         if (rc) return rc;
         if ((rc = dalloc(h, (void**)&h->warm_scal, 4 * sizeof(double)))) return rc;
+        if ((rc = dalloc(h, &h->rcur, h->n * h->es))) return rc;
     }
     h->warm = LES_WARM_NET;
     h->net = net;

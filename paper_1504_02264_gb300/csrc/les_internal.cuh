@@ -54,6 +54,7 @@ struct Scalars {
     double est;             // FP32-arithmetic estimate of the relative residual
     double rho_ref;         // FP64 relative residual at the last refinement
     int done;               // the current solve has finished (kernels of a chunk exit early)
+    int zcopy;              // zflag as it was before a network step wrote into the correction
     int timeout;            // a bounded device-side wait gave up (sticky until reported)
 };
 
@@ -126,7 +127,7 @@ template <typename T> int launch_accum(const Geo<T>& g, double* ph, const T* dl,
                                        cudaStream_t s);
 template <typename T> int launch_residual64(const Geo<T>& g, const double* ph, const T* rhs, T* r,
                                             double vfluid, const Reduce& red, CondArgs ca, cudaStream_t s);
-template <typename T> int launch_sor_est(const Geo<T>& g, const T* dl, const T* r, const Reduce& red, CondArgs ca,
+template <typename T> int launch_sor_est(const Geo<T>& g, const T* dl, const T* r, T* rout, const Reduce& red, CondArgs ca,
                                          cudaStream_t s);
 int reduce_blocks(const Dom& d);
 template <typename T> int launch_project(const Geo<T>& g, const T* us, const T* vs, const T* ws,
@@ -162,7 +163,9 @@ int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, const float* cn1tab
 int launch_cn1_table(const Geo<float>& g, float* tab, cudaStream_t s);
 
 // learned warm start (les_kernels.cu): energy-norm line search along q and p += alpha q
-template <typename T> int launch_warm(const Geo<T>& g, const T* r, const float* q, double* ph, double* alpha,
+// (dl null: p_h += alpha q at the start of a solve; dl set: inside the loop the
+// SOR correction takes the step)
+template <typename T> int launch_warm(const Geo<T>& g, const T* r, const float* q, double* ph, T* dl, double* alpha,
                                       const Reduce& red, cudaStream_t s);
 // training-pair recording: what 0 = ph - ph0 into out, 1 = unknown mask into out
 template <typename T> int launch_record(const Geo<T>& g, const double* ph, const double* ph0, T* out, int what,

@@ -728,7 +728,8 @@ int launch_residual64(const Geo<T>& g, const double* ph, const T* rhs, T* r, dou
 // this is the residual of the current iterate up to rounding.  It only decides
 // when to take the FP64 refinement, which makes the stop decision.
 template <typename T>
-__global__ void __launch_bounds__(256) k_sor_est(Geo<T> g, const T* dl, const T* r, Reduce red, CondArgs ca) {
+__global__ void __launch_bounds__(256) k_sor_est(Geo<T> g, const T* dl, const T* r, T* rout, Reduce red,
+                                                 CondArgs ca) {
     const Dom& d = g.d;
     if (red.sc->done) return;      // uniform over the grid
     // a (32 x 8) column tile marching over a chunk of kEstChunk planes
@@ -755,6 +756,7 @@ __global__ void __launch_bounds__(256) k_sor_est(Geo<T> g, const T* dl, const T*
             s += at * (dl[t] - dc);
             s += ab * (dl[b] - dc);
             const T res = r[c] - s;
+            if (rout) rout[c] = res;        // the current residual, input of the network correction
             acc += res * res;
         }
     }
@@ -776,10 +778,11 @@ __global__ void __launch_bounds__(256) k_sor_est(Geo<T> g, const T* dl, const T*
 }
 
 template <typename T>
-int launch_sor_est(const Geo<T>& g, const T* dl, const T* r, const Reduce& red, CondArgs ca, cudaStream_t s) {
+int launch_sor_est(const Geo<T>& g, const T* dl, const T* r, T* rout, const Reduce& red, CondArgs ca,
+                   cudaStream_t s) {
     const Dom& d = g.d;
     dim3 grid((d.nx + 31) / 32, (d.ny + 7) / 8, (d.nz + kEstChunk - 1) / kEstChunk);
-    k_sor_est<T><<<grid, dim3(32, 8), 0, s>>>(g, dl, r, red, ca);
+    k_sor_est<T><<<grid, dim3(32, 8), 0, s>>>(g, dl, r, rout, red, ca);
     return 1;
 }
 
@@ -895,7 +898,7 @@ int launch_rhs_eff(const Geo<T>& g, const T* rhs, T* out, const Scalars* sc, cud
 // some high-frequency noise keep a useful step (the residual-norm minimiser
 // <r, A q> / <A q, A q> would be dominated by A's amplified noise).
 template <typename T>
-__global__ void k_warm_ls(Geo<T> g, const T* r, const float* q, double* alpha, Reduce red) {
+__global__ void k_warm_ls(Geo<T> g, const T* r, const float* q, double* alpha, Reduce red, int in_loop) {
     const Dom& d = g.d;
     if (red.sc->done) return;      // uniform over the grid
     const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
@@ -934,6 +937,12 @@ __global__ void k_warm_ls(Geo<T> g, const T* r, const float* q, double* alpha, R
         if (threadIdx.x == 0 && threadIdx.y == 0) {
             const double a = x[0] / x[1];
             *alpha = (x[1] != 0.0 && isfinite(a)) ? a : 0.0;
+            if (in_loop) {
+                // the update goes into the SOR correction: hand its "correction
+                // is zero" state to k_warm_apply_dl and mark it live for the sweeps
+                red.sc->zcopy = red.sc->zflag;
+                red.sc->zflag = 0;
+            }
         }
     }
 }
@@ -950,13 +959,33 @@ __global__ void k_warm_apply(Geo<T> g, double* ph, const float* q, const double*
     if (g.flags[c] & F_UNK) ph[c] += *alpha * (double)q[((size_t)(k - 1) * d.ny + (j - 1)) * d.nx + (i - 1)];
 }
 
+// inside the solve loop: the SOR correction d (field type) takes the step,
+// d = (zero ? 0 : d) + alpha q, so the FP64 pressure is only touched by the
+// next refinement
 template <typename T>
-int launch_warm(const Geo<T>& g, const T* r, const float* q, double* ph, double* alpha, const Reduce& red,
+__global__ void k_warm_apply_dl(Geo<T> g, T* dl, const float* q, const double* alpha, const Scalars* sc) {
+    const Dom& d = g.d;
+    if (sc->done) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    const int k = blockIdx.z + 1;
+    if (i > d.nx || j > d.ny) return;
+    const long long c = d.at(i, j, k);
+    if (!(g.flags[c] & F_UNK)) return;
+    const T base = sc->zcopy ? T(0) : dl[c];
+    dl[c] = base + (T)(*alpha * (double)q[((size_t)(k - 1) * d.ny + (j - 1)) * d.nx + (i - 1)]);
+}
+
+template <typename T>
+int launch_warm(const Geo<T>& g, const T* r, const float* q, double* ph, T* dl, double* alpha, const Reduce& red,
                 cudaStream_t s) {
     const Dom& d = g.d;
     const dim3 grid((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), blk(32, 8);
-    k_warm_ls<T><<<grid, blk, 0, s>>>(g, r, q, alpha, red);
-    k_warm_apply<T><<<grid, blk, 0, s>>>(g, ph, q, alpha, red.sc);
+    k_warm_ls<T><<<grid, blk, 0, s>>>(g, r, q, alpha, red, dl ? 1 : 0);
+    if (dl)
+        k_warm_apply_dl<T><<<grid, blk, 0, s>>>(g, dl, q, alpha, red.sc);
+    else
+        k_warm_apply<T><<<grid, blk, 0, s>>>(g, ph, q, alpha, red.sc);
     return 2;
 }
 
@@ -1020,12 +1049,12 @@ int max_reduce_blocks(const Dom& d) { return ((d.nx + 31) / 32) * ((d.ny + 7) / 
     template int launch_accum<T>(const Geo<T>&, double*, const T*, const Scalars*, int, cudaStream_t);  \
     template int launch_residual64<T>(const Geo<T>&, const double*, const T*, T*, double, const Reduce&, \
                                       CondArgs, cudaStream_t);                                          \
-    template int launch_sor_est<T>(const Geo<T>&, const T*, const T*, const Reduce&, CondArgs, cudaStream_t); \
+    template int launch_sor_est<T>(const Geo<T>&, const T*, const T*, T*, const Reduce&, CondArgs, cudaStream_t); \
     template int launch_project<T>(const Geo<T>&, const T*, const T*, const T*, T*, T*, T*,             \
                                    const double*, double*, Scalars*, cudaStream_t);                     \
     template int launch_rhs_eff<T>(const Geo<T>&, const T*, T*, const Scalars*, cudaStream_t);          \
     template int launch_gauge<T>(const Geo<T>&, const double*, double*, const Scalars*, cudaStream_t);   \
-    template int launch_warm<T>(const Geo<T>&, const T*, const float*, double*, double*, const Reduce&,         \
+    template int launch_warm<T>(const Geo<T>&, const T*, const float*, double*, T*, double*, const Reduce&,     \
                                 cudaStream_t);                                                          \
     template int launch_record<T>(const Geo<T>&, const double*, const double*, T*, int, cudaStream_t);
 

@@ -189,8 +189,24 @@ def main(argv=None):
     ap.add_argument("--eval-size", default="150x150x90")
     ap.add_argument("--schedules", default="0,50,100,200")
     ap.add_argument("--json", default=None, help="write the evaluation here")
+    ap.add_argument("--eval-only", default=None, help="evaluate these trained networks (.npz, comma separated)")
     a = ap.parse_args(argv)
     les.lib()
+    if a.eval_only:
+        nx, ny, nz = (int(x) for x in a.eval_size.split("x"))
+        ev_sc = scene.random_scene(seed=a.seed + 7777, nx=nx, ny=ny, nz=nz, max_sweeps=60000, check_every=20)
+        report = {"eval_scene": ev_sc.name, "nets": {}}
+        for path in a.eval_only.split(","):
+            net = load(path)
+            print(f"{path} (stride {net.stride}) on {ev_sc.name} seed {ev_sc.seed}:", flush=True)
+            report["nets"][path] = evaluate(net, ev_sc, a.eval_steps, a.eval_spinup,
+                                            [int(x) for x in a.schedules.split(",")])
+            net.close()
+        print(json.dumps(report), flush=True)
+        if a.json:
+            with open(a.json, "w") as f:
+                json.dump(report, f, indent=1)
+        return
     t0 = time.time()
     pts = [int(x) for x in a.record_points.split(",")]
     print(f"generating pairs: {a.lattice} lattice + {a.cities} city scenes x {a.steps} steps", flush=True)
