@@ -897,42 +897,51 @@ int launch_rhs_eff(const Geo<T>& g, const T* rhs, T* out, const Scalars* sc, cud
 // (e - alpha q)^T (-V A) (e - alpha q) with A e = r.  Smooth predictions with
 // some high-frequency noise keep a useful step (the residual-norm minimiser
 // <r, A q> / <A q, A q> would be dominated by A's amplified noise).
+// The step needs only moderate precision (it decides the efficiency of the
+// correction, not the solution), so A q and the per-thread sums are formed in
+// the field type and the grid sums in FP64.  Tiles of (32 x 8) columns march
+// over kEstChunk planes, like the estimate.
 template <typename T>
-__global__ void k_warm_ls(Geo<T> g, const T* r, const float* q, double* alpha, Reduce red, int in_loop) {
+__global__ void __launch_bounds__(256) k_warm_ls(Geo<T> g, const T* r, const float* q, double* alpha, Reduce red,
+                                                 int in_loop) {
     const Dom& d = g.d;
     if (red.sc->done) return;      // uniform over the grid
-    const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    const int k = blockIdx.z + 1;
-    double x[2] = {0.0, 0.0};
+    const int i = blockIdx.x * 32 + threadIdx.x + 1;
+    const int j = blockIdx.y * 8 + threadIdx.y + 1;
+    const int kb = blockIdx.z * kEstChunk + 1, ke = min(kb + kEstChunk, d.nz + 1);
+    const int sx = 1, sy = d.nx, sz = d.nx * d.ny;      // dense strides (the grid has < 2^31 cells)
+    T s0 = T(0), s1 = T(0);
     if (i <= d.nx && j <= d.ny) {
-        const long long c = d.at(i, j, k);
-        const uint8_t f = g.flags[c];
-        if (f & F_UNK) {
-            // flags never open a face across a non-periodic domain boundary,
-            // so every neighbour read below stays inside the dense array
-            auto dense = [&](int a, int b, int cc) -> double {
-                if (d.perx) a = a < 1 ? a + d.nx : (a > d.nx ? a - d.nx : a);
-                if (d.pery) b = b < 1 ? b + d.ny : (b > d.ny ? b - d.ny : b);
-                if (d.perz) cc = cc < 1 ? cc + d.nz : (cc > d.nz ? cc - d.nz : cc);
-                return (double)q[((size_t)(cc - 1) * d.ny + (b - 1)) * d.nx + (a - 1)];
-            };
+        // flags never open a face across a non-periodic domain boundary, so
+        // every neighbour read below stays inside the dense array
+        const int oe = (d.perx && i == d.nx) ? -(d.nx - 1) * sx : sx;
+        const int ow = (d.perx && i == 1) ? (d.nx - 1) * sx : -sx;
+        const int on = (d.pery && j == d.ny) ? -(d.ny - 1) * sy : sy;
+        const int os = (d.pery && j == 1) ? (d.ny - 1) * sy : -sy;
+        for (int k = kb; k < ke; ++k) {
+            const long long c = d.at(i, j, k);
+            const uint8_t f = g.flags[c];
+            if (!(f & F_UNK)) continue;
+            const int v = ((k - 1) * d.ny + (j - 1)) * d.nx + (i - 1);
+            const int ot = (d.perz && k == d.nz) ? -(d.nz - 1) * sz : sz;
+            const int ob = (d.perz && k == 1) ? (d.nz - 1) * sz : -sz;
             Poisson<T> P{g};
-            double ae, aw, an, as, at, ab;
-            P.coefs(f, k, g.cx64, g.cy64, g.cT64, g.cB64, ae, aw, an, as, at, ab);
-            const double qc = dense(i, j, k);
-            double aq = 0.0;
-            if (ae != 0.0) aq += ae * (dense(i + 1, j, k) - qc);
-            if (aw != 0.0) aq += aw * (dense(i - 1, j, k) - qc);
-            if (an != 0.0) aq += an * (dense(i, j + 1, k) - qc);
-            if (as != 0.0) aq += as * (dense(i, j - 1, k) - qc);
-            if (at != 0.0) aq += at * (dense(i, j, k + 1) - qc);
-            if (ab != 0.0) aq += ab * (dense(i, j, k - 1) - qc);
-            const double vol = g.dz64[k];
-            x[0] = vol * qc * (double)r[c];
-            x[1] = vol * qc * aq;
+            T ae, aw, an, as, at, ab;
+            P.coefs(f, k, g.cx, g.cy, g.cT, g.cB, ae, aw, an, as, at, ab);
+            const T qc = (T)q[v];
+            T aq = T(0);
+            if (f & F_E) aq += ae * ((T)q[v + oe] - qc);
+            if (f & F_W) aq += aw * ((T)q[v + ow] - qc);
+            if (f & F_N) aq += an * ((T)q[v + on] - qc);
+            if (f & F_S) aq += as * ((T)q[v + os] - qc);
+            if (f & F_T) aq += at * ((T)q[v + ot] - qc);
+            if (f & F_B) aq += ab * ((T)q[v + ob] - qc);
+            const T vq = g.dz[k] * qc;
+            s0 += vq * r[c];
+            s1 += vq * aq;
         }
     }
+    double x[2] = {(double)s0, (double)s1};
     if (grid_sum<2>(x, red)) {
         if (threadIdx.x == 0 && threadIdx.y == 0) {
             const double a = x[0] / x[1];
@@ -956,7 +965,7 @@ __global__ void k_warm_apply(Geo<T> g, double* ph, const float* q, const double*
     const int k = blockIdx.z + 1;
     if (i > d.nx || j > d.ny) return;
     const long long c = d.at(i, j, k);
-    if (g.flags[c] & F_UNK) ph[c] += *alpha * (double)q[((size_t)(k - 1) * d.ny + (j - 1)) * d.nx + (i - 1)];
+    if (g.flags[c] & F_UNK) ph[c] += *alpha * (double)q[((k - 1) * d.ny + (j - 1)) * d.nx + (i - 1)];
 }
 
 // inside the solve loop: the SOR correction d (field type) takes the step,
@@ -972,8 +981,9 @@ __global__ void k_warm_apply_dl(Geo<T> g, T* dl, const float* q, const double* a
     if (i > d.nx || j > d.ny) return;
     const long long c = d.at(i, j, k);
     if (!(g.flags[c] & F_UNK)) return;
+    const T a = (T)*alpha;
     const T base = sc->zcopy ? T(0) : dl[c];
-    dl[c] = base + (T)(*alpha * (double)q[((size_t)(k - 1) * d.ny + (j - 1)) * d.nx + (i - 1)]);
+    dl[c] = base + a * (T)q[((k - 1) * d.ny + (j - 1)) * d.nx + (i - 1)];
 }
 
 template <typename T>
@@ -981,7 +991,8 @@ int launch_warm(const Geo<T>& g, const T* r, const float* q, double* ph, T* dl, 
                 cudaStream_t s) {
     const Dom& d = g.d;
     const dim3 grid((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), blk(32, 8);
-    k_warm_ls<T><<<grid, blk, 0, s>>>(g, r, q, alpha, red, dl ? 1 : 0);
+    const dim3 grid_ls((d.nx + 31) / 32, (d.ny + 7) / 8, (d.nz + kEstChunk - 1) / kEstChunk);
+    k_warm_ls<T><<<grid_ls, blk, 0, s>>>(g, r, q, alpha, red, dl ? 1 : 0);
     if (dl)
         k_warm_apply_dl<T><<<grid, blk, 0, s>>>(g, dl, q, alpha, red.sc);
     else

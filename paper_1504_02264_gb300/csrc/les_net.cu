@@ -399,6 +399,10 @@ int les_net_create(uint64_t seed, void* stream, les_net* out) {
     les_net_s* n = new (std::nothrow) les_net_s();
     if (!n) return LES_ENOMEM;
     n->stream = (cudaStream_t)stream;
+    if (nn::conv3_prepare() != 0) {
+        delete n;
+        return LES_ECUDA;
+    }
     size_t o = 0;
     for (int c = 0; c < kConvs; ++c) {
         n->off[c] = o;

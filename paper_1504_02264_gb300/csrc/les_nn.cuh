@@ -8,6 +8,8 @@
 namespace les {
 namespace nn {
 
+// set the convolution kernels' dynamic shared memory limit on the current device (0 = ok)
+int conv3_prepare();
 void conv3_fwd(const __nv_bfloat16* x, const __nv_bfloat16* w, __nv_bfloat16* y, const __nv_bfloat16* skip,
                __nv_bfloat16* ysum, int X, int Y, int Z, int Cin, int Cout, int relu, cudaStream_t s,
                const int* gate = nullptr);

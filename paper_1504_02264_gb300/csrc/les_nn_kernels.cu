@@ -50,55 +50,83 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int bytes) {
+    // bytes = 0 fills the 16 destination bytes with zeros (src is not read)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N));
+}
+
+template <int CO>
+struct ConvStage {
+    __nv_bfloat16 in[HZ][HY][HX][16];
+    __nv_bfloat16 w[27][CO][16];
+};
+
+// Two stages in dynamic shared memory: the next 16-channel chunk (halo block
+// and weights) is copied with cp.async while the tensor cores work on the
+// current one; the 27 taps are unrolled.
 template <int CO>
 __global__ void __launch_bounds__(256)
 k_conv3(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ w, __nv_bfloat16* __restrict__ y,
         const __nv_bfloat16* __restrict__ skip, __nv_bfloat16* __restrict__ ysum, int X, int Y, int Z, int Cin,
         int Cout, int relu, const int* gate) {
     if (gate && *(volatile const int*)gate) return;      // the solve this inference serves has ended
-    __shared__ __align__(16) __nv_bfloat16 sIn[HZ][HY][HX][16];
-    __shared__ __align__(16) __nv_bfloat16 sW[27][CO][16];
+    extern __shared__ __align__(16) unsigned char conv_smem[];
+    ConvStage<CO>* st = reinterpret_cast<ConvStage<CO>*>(conv_smem);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ntz = (Z + TZ - 1) / TZ;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = (blockIdx.z % ntz) * TZ;
     const int co0 = (blockIdx.z / ntz) * CO;
     const int wy = warp % TY, wz = warp / TY;
-    float acc[CO / 8][4];
-#pragma unroll
-    for (int n = 0; n < CO / 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-    for (int c0 = 0; c0 < Cin; c0 += 16) {
-        // stage the halo block (two 16-byte halves per voxel) and the weights
+    auto stage = [&](int c0, ConvStage<CO>& S) {
         for (int q = tid; q < HZ * HY * HX * 2; q += 256) {
             const int h = q & 1, v = q >> 1;
             const int hx = v % HX, hy = (v / HX) % HY, hz = v / (HX * HY);
             const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = z0 - 1 + hz;
-            uint4 val = make_uint4(0, 0, 0, 0);
-            if (gx >= 0 && gx < X && gy >= 0 && gy < Y && gz >= 0 && gz < Z)
-                val = *reinterpret_cast<const uint4*>(x + (((size_t)gz * Y + gy) * X + gx) * Cin + c0 + 8 * h);
-            *reinterpret_cast<uint4*>(&sIn[hz][hy][hx][8 * h]) = val;
+            const bool ok = gx >= 0 && gx < X && gy >= 0 && gy < Y && gz >= 0 && gz < Z;
+            const __nv_bfloat16* src = ok ? x + (((size_t)gz * Y + gy) * X + gx) * Cin + c0 + 8 * h : x;
+            cp_async16(smem_addr(&S.in[hz][hy][hx][8 * h]), src, ok ? 16 : 0);
         }
         for (int q = tid; q < 27 * CO * 2; q += 256) {
             const int h = q & 1, r = q >> 1, co = r % CO, tap = r / CO;
-            uint4 val = make_uint4(0, 0, 0, 0);
-            if (co0 + co < Cout)
-                val = *reinterpret_cast<const uint4*>(w + ((size_t)tap * Cout + co0 + co) * Cin + c0 + 8 * h);
-            *reinterpret_cast<uint4*>(&sW[tap][co][8 * h]) = val;
+            const bool ok = co0 + co < Cout;
+            const __nv_bfloat16* src = ok ? w + ((size_t)tap * Cout + co0 + co) * Cin + c0 + 8 * h : w;
+            cp_async16(smem_addr(&S.w[tap][co][8 * h]), src, ok ? 16 : 0);
+        }
+        cp_async_commit();
+    };
+    float acc[CO / 8][4];
+#pragma unroll
+    for (int n = 0; n < CO / 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+    const int nch = Cin / 16;
+    const int mat = lane >> 3, r8 = lane & 7;
+    const int vrow = r8 + 8 * (mat & 1), koff = 8 * (mat >> 1);
+    stage(0, st[0]);
+    for (int c = 0; c < nch; ++c) {
+        if (c + 1 < nch) {
+            stage(16 * (c + 1), st[(c + 1) & 1]);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
-        const int mat = lane >> 3, r8 = lane & 7;
-#pragma unroll 1
+        const ConvStage<CO>& S = st[c & 1];
+#pragma unroll
         for (int tap = 0; tap < 27; ++tap) {
             const int dx = tap % 3, dy = (tap / 3) % 3, dz = tap / 9;
             // A: rows = 16 voxels of the warp's row shifted by the tap, k = 16 channels
-            const int vrow = r8 + 8 * (mat & 1), koff = 8 * (mat >> 1);
             uint32_t a0, a1, a2, a3;
-            ldsm_x4(smem_addr(&sIn[wz + dz][wy + dy][vrow + dx][koff]), a0, a1, a2, a3);
+            ldsm_x4(smem_addr(&S.in[wz + dz][wy + dy][vrow + dx][koff]), a0, a1, a2, a3);
 #pragma unroll
             for (int n = 0; n < CO / 8; n += 2) {
                 // B: two n-tiles; matrices (co rows, ci 0-7 | 8-15) of tile n and n+1
                 const int co = 8 * (n + (mat >> 1)) + r8, ko = 8 * (mat & 1);
                 uint32_t b0, b1, b2, b3;
-                ldsm_x4(smem_addr(&sW[tap][co][ko]), b0, b1, b2, b3);
+                ldsm_x4(smem_addr(&S.w[tap][co][ko]), b0, b1, b2, b3);
                 mma_bf16(acc[n], a0, a1, a2, a3, b0, b1);
                 mma_bf16(acc[n + 1], a0, a1, a2, a3, b2, b3);
             }
@@ -135,6 +163,15 @@ k_conv3(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ w
     }
 }
 
+int conv3_prepare() {
+    cudaError_t e = cudaFuncSetAttribute(k_conv3<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(2 * sizeof(ConvStage<32>)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_conv3<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(2 * sizeof(ConvStage<16>)));
+    return e == cudaSuccess ? 0 : -1;
+}
+
 void conv3_fwd(const __nv_bfloat16* x, const __nv_bfloat16* w, __nv_bfloat16* y, const __nv_bfloat16* skip,
                __nv_bfloat16* ysum, int X, int Y, int Z, int Cin, int Cout, int relu, cudaStream_t s,
                const int* gate) {
@@ -142,9 +179,9 @@ void conv3_fwd(const __nv_bfloat16* x, const __nv_bfloat16* w, __nv_bfloat16* y,
     const int ntz = (Z + TZ - 1) / TZ;
     dim3 grid((X + TX - 1) / TX, (Y + TY - 1) / TY, ntz * ((Cout + co - 1) / co));
     if (co == 32)
-        k_conv3<32><<<grid, 256, 0, s>>>(x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu, gate);
+        k_conv3<32><<<grid, 256, 2 * sizeof(ConvStage<32>), s>>>(x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu, gate);
     else
-        k_conv3<16><<<grid, 256, 0, s>>>(x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu, gate);
+        k_conv3<16><<<grid, 256, 2 * sizeof(ConvStage<16>), s>>>(x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu, gate);
 }
 
 // dgrad weights: W'[tap][ci][co] = W[26 - tap][co][ci] (flipped taps, swapped roles)
@@ -379,28 +416,33 @@ __global__ void k_pool_dense_s(const float* a, float* b, int Xf, int Yf, int Zf,
     b[q] = acc / (float)(s * s * s);
 }
 
-// the solver's padded residual (unknowns only) and unknown mask -> dense coarse
-__global__ void k_pool_padded_s(const float* r, const uint8_t* flags, Dom d, int s, float* rc, float* mc,
-                                const int* gate) {
+// the solver's padded residual (unknowns only) and unknown mask -> dense
+// coarse; a thread per coarse cell, the S^3 children unrolled
+template <int S>
+__global__ void k_pool_padded_s(const float* r, const uint8_t* flags, Dom d, float* rc, float* mc, const int* gate) {
     if (gate && *(volatile const int*)gate) return;
-    const int Xc = (d.nx + s - 1) / s, Yc = (d.ny + s - 1) / s, Zc = (d.nz + s - 1) / s;
-    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= (size_t)Xc * Yc * Zc) return;
-    const int x = q % Xc, y = (q / Xc) % Yc, z = q / ((size_t)Xc * Yc);
+    const int Xc = (d.nx + S - 1) / S, Yc = (d.ny + S - 1) / S;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= Xc) return;
     float ar = 0.f, am = 0.f;
-    for (int dz = 0; dz < s; ++dz)
-        for (int dy = 0; dy < s; ++dy)
-            for (int dx = 0; dx < s; ++dx) {
-                const int fx = x * s + dx, fy = y * s + dy, fz = z * s + dz;
-                if (fx < d.nx && fy < d.ny && fz < d.nz) {
-                    const long long c = d.at(fx + 1, fy + 1, fz + 1);
-                    if (flags[c] & F_UNK) {
-                        ar += r[c];
-                        am += 1.f;
-                    }
+#pragma unroll
+    for (int dz = 0; dz < S; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < S; ++dy) {
+            const int fy = y * S + dy, fz = z * S + dz;
+            if (fy >= d.ny || fz >= d.nz) continue;
+            const long long row = d.at(1, fy + 1, fz + 1);
+#pragma unroll
+            for (int dx = 0; dx < S; ++dx) {
+                const int fx = x * S + dx;
+                if (fx < d.nx && (flags[row + fx] & F_UNK)) {
+                    ar += r[row + fx];
+                    am += 1.f;
                 }
             }
-    const float inv = 1.f / (float)(s * s * s);
+        }
+    const float inv = 1.f / (float)(S * S * S);
+    const int q = (z * Yc + y) * Xc + x;
     rc[q] = ar * inv;
     mc[q] = am * inv;
 }
@@ -444,15 +486,14 @@ __global__ void k_prolong_dense(const float* yc, const float* mask, float* out, 
     const int Xc = (Xf + s - 1) / s, Yc = (Yf + s - 1) / s, Zc = (Zf + s - 1) / s;
     out[q] = mask[q] * trilinear(yc, Xc, Yc, Zc, s, x, y, z);
 }
-// dense fine output on the solver's unknowns
+// dense fine output on the solver's unknowns (3-D grid, 32-bit indices)
 __global__ void k_prolong_flags(const float* yc, const uint8_t* flags, Dom d, int s, float* out, const int* gate) {
     if (gate && *(volatile const int*)gate) return;
-    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= (size_t)d.nx * d.ny * d.nz) return;
-    const int x = q % d.nx, y = (q / d.nx) % d.ny, z = q / ((size_t)d.nx * d.ny);
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= d.nx) return;
     const int Xc = (d.nx + s - 1) / s, Yc = (d.ny + s - 1) / s, Zc = (d.nz + s - 1) / s;
     const bool unk = flags[d.at(x + 1, y + 1, z + 1)] & F_UNK;
-    out[q] = unk ? trilinear(yc, Xc, Yc, Zc, s, x, y, z) : 0.f;
+    out[(z * d.ny + y) * d.nx + x] = unk ? trilinear(yc, Xc, Yc, Zc, s, x, y, z) : 0.f;
 }
 
 // training loss 1/n * sum mask (y - t)^2 and its gradient
@@ -524,15 +565,21 @@ void pool_dense_s(const float* a, float* b, int Xf, int Yf, int Zf, int st, cuda
 }
 void pool_padded_s(const float* r, const uint8_t* flags, const Dom& d, int st, float* rc, float* mc, cudaStream_t s,
                    const int* gate) {
-    const size_t n = (size_t)((d.nx + st - 1) / st) * ((d.ny + st - 1) / st) * ((d.nz + st - 1) / st);
-    k_pool_padded_s<<<blocks_for(n), 256, 0, s>>>(r, flags, d, st, rc, mc, gate);
+    const int Xc = (d.nx + st - 1) / st, Yc = (d.ny + st - 1) / st, Zc = (d.nz + st - 1) / st;
+    const dim3 grid((Xc + 63) / 64, Yc, Zc);
+    switch (st) {
+        case 1: k_pool_padded_s<1><<<grid, 64, 0, s>>>(r, flags, d, rc, mc, gate); break;
+        case 2: k_pool_padded_s<2><<<grid, 64, 0, s>>>(r, flags, d, rc, mc, gate); break;
+        case 4: k_pool_padded_s<4><<<grid, 64, 0, s>>>(r, flags, d, rc, mc, gate); break;
+        default: k_pool_padded_s<8><<<grid, 64, 0, s>>>(r, flags, d, rc, mc, gate); break;
+    }
 }
 void prolong_dense(const float* yc, const float* mask, float* out, int Xf, int Yf, int Zf, int st, cudaStream_t s) {
     k_prolong_dense<<<blocks_for((size_t)Xf * Yf * Zf), 256, 0, s>>>(yc, mask, out, Xf, Yf, Zf, st);
 }
 void prolong_flags(const float* yc, const uint8_t* flags, const Dom& d, int st, float* out, cudaStream_t s,
                    const int* gate) {
-    k_prolong_flags<<<blocks_for((size_t)d.nx * d.ny * d.nz), 256, 0, s>>>(yc, flags, d, st, out, gate);
+    k_prolong_flags<<<dim3((d.nx + 127) / 128, d.ny, d.nz), 128, 0, s>>>(yc, flags, d, st, out, gate);
 }
 void mse(const float* y, const float* t, const float* mask, float* g, double* loss, size_t n, double inv_n,
          cudaStream_t s) {

@@ -39,17 +39,29 @@ def main():
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--fp64", action="store_true")
     ap.add_argument("--range", action="store_true")
+    ap.add_argument("--net", default=None, help="trained warm-start network (.npz: params, stride)")
+    ap.add_argument("--net-every", type=int, default=0, help="network correction every n sweeps")
     a = ap.parse_args()
     sc = make(a.workload, a.seed)
     d = les.Domain(sc, precision=les.LES_FP64 if a.fp64 else les.LES_FP32, stream=None)
     d.set_graph(bool(a.graph))
     if a.tile is not None:
         d.set_sor_config(a.tile, a.kc)
+    net = None
+    if a.net:
+        import numpy as np
+        z = np.load(a.net)
+        net = les.Net(seed=0, stream=None, stride=int(z["stride"]))
+        net.set_params(z["params"])
     for _ in range(a.warmup):
         d.step(1)
     tune = None
     if a.autotune:
         tune = d.autotune_sor(sweeps=20)
+    if net is not None:
+        d.set_warmstart(net)
+        d.set_net_schedule(a.net_every)
+        d.step(1)
     if a.range:
         les.les_profiler_range(1)
     t0 = time.perf_counter()
@@ -64,7 +76,7 @@ def main():
     print(json.dumps({"workload": a.workload, "graph_used": st["graph"], "last_error": err, "cells": sc.ncells, "steps": a.steps,
                       "ms_per_step": (t1 - t0) * 1e3 / a.steps, "sweeps": sweeps,
                       "rel_residual": st["rel_residual"], "sor_config": d.sor_config(), "autotune": tune,
-                      "graph": a.graph}))
+                      "graph": a.graph, "net": a.net, "net_every": a.net_every}))
 
 
 if __name__ == "__main__":
