@@ -65,19 +65,26 @@ def training_scenes(n_lattice: int, n_city: int, seed: int, city_shape=(96, 96, 
     return out
 
 
-def generate(scenes, steps: int, spinup: int, record_points, seed: int = 0, log=print):
+def generate(scenes, steps: int, spinup: int, record_points, seed: int = 0, log=print, net=None, net_every=0,
+             groups=None):
     """Run each scene and record one (r_k, remaining correction) pair per step.
 
-    Returns {shape: (R, T, M)} with R, T float32 device tensors [n, nz, ny, nx]
-    (residuals, targets) and M the unknown mask [nz, ny, nx] of each pair."""
+    With `net`, the solves run with that network correction every `net_every`
+    sweeps, so the recorded residuals are the ones the network meets in its
+    own loop.  Returns (and extends) {shape: (R, T, M)} with R, T float32
+    device tensor lists [nz, ny, nx] (residuals, targets) and M the unknown
+    mask of each pair."""
     torch = _require_torch()
     rng = np.random.default_rng(seed)
-    groups = {}
+    groups = {} if groups is None else groups
     for sc in scenes:
         dom = les.Domain(sc)
         dom.set_graph(True)
         for _ in range(spinup):
             dom.step()
+        if net is not None:
+            dom.set_warmstart(net)
+            dom.set_net_schedule(net_every)
         dom.set_record(True)
         mask = torch.from_numpy(dom.aux(les.LES_AUX_MASK)).cuda()
         rs, ts = [], []
@@ -105,6 +112,11 @@ def generate(scenes, steps: int, spinup: int, record_points, seed: int = 0, log=
         groups[shape] = (R, T, M)
         log(f"  {sc.name} seed {sc.seed}: {len(rs)} pairs, {sw / max(1, steps):.0f} sweeps/step, "
             f"{time.time() - t0:.1f} s")
+    return groups
+
+
+def stack(groups):
+    torch = _require_torch()
     return {s: (torch.stack(R), torch.stack(T), torch.stack(M)) for s, (R, T, M) in groups.items()}
 
 
@@ -190,6 +202,9 @@ def main(argv=None):
     ap.add_argument("--schedules", default="0,50,100,200")
     ap.add_argument("--json", default=None, help="write the evaluation here")
     ap.add_argument("--eval-only", default=None, help="evaluate these trained networks (.npz, comma separated)")
+    ap.add_argument("--dagger", default=None, help="also record pairs with this network in the loop (.npz)")
+    ap.add_argument("--dagger-every", type=int, default=10)
+    ap.add_argument("--dagger-points", default="0,10,20,30,50,80,120,200")
     a = ap.parse_args(argv)
     les.lib()
     if a.eval_only:
@@ -211,7 +226,16 @@ def main(argv=None):
     pts = [int(x) for x in a.record_points.split(",")]
     print(f"generating pairs: {a.lattice} lattice + {a.cities} city scenes x {a.steps} steps", flush=True)
     cs = tuple(int(x) for x in a.city_size.split("x"))
-    data = generate(training_scenes(a.lattice, a.cities, a.seed, cs), a.steps, a.spinup, pts, a.seed)
+    scenes = training_scenes(a.lattice, a.cities, a.seed, cs)
+    groups = generate(scenes, a.steps, a.spinup, pts, a.seed)
+    if a.dagger:
+        # pairs from solves that run with a network in the loop
+        dnet = load(a.dagger)
+        dpts = [int(x) for x in a.dagger_points.split(",")]
+        print(f"pairs with {a.dagger} every {a.dagger_every} sweeps in the loop", flush=True)
+        generate(scenes, a.steps, a.spinup, dpts, a.seed + 1, net=dnet, net_every=a.dagger_every, groups=groups)
+        dnet.close()
+    data = stack(groups)
     npairs = sum(v[0].shape[0] for v in data.values())
     print(f"{npairs} pairs in {time.time() - t0:.0f} s", flush=True)
     nx, ny, nz = (int(x) for x in a.eval_size.split("x"))
