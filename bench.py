@@ -35,6 +35,8 @@ if ROOT not in sys.path:
 from paper_1504_02264_gb300 import scene  # noqa: E402
 
 METRIC = "LES Mcell-steps/s to |div|<=1e-6 (150x150x90, 100 buildings)"
+WEIGHTS = os.path.join(ROOT, "paper_1504_02264_gb300", "weights", "warmstart_s4.npz")
+NET_EVERY = 10                  # sweeps between learned corrections (trained schedule)
 UNIT = "Mcell-steps/s"
 SOR_BYTES_PER_CELL = 13.0       # per sweep: read p, rhs (4+4), flags (1), write p (4)
 L2_FLUSH_BYTES = 256 << 20
@@ -49,6 +51,19 @@ def workload(seed=0):
     sc.check_every = 10
     sc.max_sweeps = 20000
     return sc
+
+
+def sor_kernel_name(tile):
+    """The sweep kernel a tile index of les_set_sor_config runs."""
+    if tile >= 21:
+        return "k_sor_pipe"
+    if tile >= 17:
+        return "k_sor_tma"
+    if tile >= 12:
+        return "k_sor_rows"
+    if tile >= 6:
+        return "k_sor_block"
+    return "k_sor_fused" if tile >= 0 else "k_sor_half"
 
 
 def peaks():
@@ -200,39 +215,73 @@ def run_ours(args):
             raise RuntimeError(st)
     # set-up, not timed: pick the SOR tile shape and k-chunk for this grid
     (tile, kc), tune_ms = dom.autotune_sor(sweeps=20)
+    net = None
+    if not args.no_learned:
+        from paper_1504_02264_gb300 import train
+        net = train.load(WEIGHTS)
+    state0 = dom.get_state()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
 
-    # timed region 1: the library's default step (one CUDA graph per step)
-    l0 = dom.timing()["launches"]
-    clocks = Clocks(local) if (rank == 0 and not args.ncu_range) else None
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    sweeps = []
-    worst = 0.0
-    torch.cuda.synchronize()
-    if args.ncu_range:
-        torch.cuda.profiler.start()
-    for s in range(args.steps):
-        flush.zero_()
-        ev[s][0].record(stream)
-        st = dom.step(1)
-        ev[s][1].record(stream)
-        sweeps.append(st["sweeps"])
-        graph_used = st["graph"]
-        worst = max(worst, st["rel_residual"])
-        if st["rc"] != 0:
-            raise RuntimeError(f"step did not converge: {st}")
-    torch.cuda.synchronize()
-    if args.ncu_range:
-        torch.cuda.profiler.stop()
-    clk = clocks.stop() if clocks else None
-    launches = dom.timing()["launches"] - l0
-    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    def timed(label, clocks_on):
+        """K steps from state0, each bracketed by CUDA events on the library's
+        stream after an L2 flush; max over ranks."""
+        dom.set_state(state0)
+        l0 = dom.timing()["launches"]
+        clocks = Clocks(local) if (clocks_on and rank == 0 and not args.ncu_range) else None
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        sweeps, worst, graph_used = [], 0.0, 0
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        if args.ncu_range:
+            torch.cuda.profiler.start()
+        for s in range(args.steps):
+            flush.zero_()
+            ev[s][0].record(stream)
+            st = dom.step(1)
+            ev[s][1].record(stream)
+            sweeps.append(st["sweeps"])
+            graph_used = st["graph"]
+            worst = max(worst, st["rel_residual"])
+            if st["rc"] != 0:
+                raise RuntimeError(f"{label} step did not converge: {st}")
+        torch.cuda.synchronize()
+        if args.ncu_range:
+            torch.cuda.profiler.stop()
+        clk = clocks.stop() if clocks else None
+        launches = dom.timing()["launches"] - l0
+        ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return {"ms": ms, "sweeps": sweeps, "worst": worst, "graph": graph_used, "clocks": clk,
+                "launches": launches}
+
+    # timed region 1: the plain step (red-black SOR from the previous
+    # pressure, one chunked CUDA graph per step)
+    plain = timed("plain", net is None)
+    if net is not None:
+        # timed region 1b: the full hot path with the learned correction
+        # (stride-4 network every NET_EVERY sweeps), same start state, same
+        # stop test; one untimed step first builds its graphs
+        dom.set_warmstart(net)
+        dom.set_net_schedule(NET_EVERY)
+        dom.set_state(state0)
+        dom.step(1)
+        learned = timed("learned", True)
+        head = learned
+    else:
+        head = plain
+    ms, sweeps, worst, graph_used, clk, launches = (head["ms"], head["sweeps"], head["worst"], head["graph"],
+                                                    head["clocks"], head["launches"])
+    if net is not None:
+        # the SOR kernel roofline and the CPU baseline use the plain step
+        dom.set_warmstart(None)
+        dom.set_state(state0)
 
     # timed region 2: same steps, host-driven, with CUDA events around every
     # batch of SOR sweep launches on the library's stream (kernel roofline)
@@ -244,7 +293,12 @@ def run_ours(args):
     tm = dom.timing()
     dom.set_timing(False)
 
-    # end to end through the C ABI with pinned host buffers
+    # end to end through the C ABI with pinned host buffers (the configuration
+    # of the headline value)
+    if net is not None:
+        dom.set_warmstart(net)
+        dom.set_net_schedule(NET_EVERY)
+    dom.set_state(state0)
     shapes = dom.shapes()
     host = [torch.empty(s, dtype=torch.float32, pin_memory=True).numpy() for s in shapes]
     for h, f in zip(host, dom.fields()):
@@ -277,6 +331,7 @@ def run_ours(args):
         bytes_per_launch = SOR_BYTES_PER_CELL * n / launches_per_sweep
         achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
         mean_sweeps = float(np.mean(sweeps))
+        plain_sweeps = float(np.mean(plain["sweeps"]))
         line = {
             "metric": METRIC, "value": n * world / (ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -285,8 +340,21 @@ def run_ours(args):
             "config": {"workload": "random_150x150x90", "nx": 150, "ny": 150, "nz": 90, "buildings": 100,
                        "tol": 1e-6, "check_every": sc.check_every, "mean_sweeps_per_step": mean_sweeps,
                        "max_rel_residual": worst, "parallelism": f"replicas x{world}",
+                       "sor_start": ("previous-step pressure + learned correction (stride-4 U-Net every "
+                                     f"{NET_EVERY} sweeps)" if net is not None else "previous-step pressure"),
                        "l2": "flushed (256 MiB write) before every timed step"},
-            "roofline": {"kernel": f"k_sor_fused (red-black SOR sweep, tile {les.les_sor_tile(tile) if tile >= 0 else 'two-pass'}, kc {kc})",
+            "plain_sor": {"value": n * world / (plain["ms"] * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": plain["ms"],
+                          "mean_sweeps_per_step": plain_sweeps, "max_rel_residual": plain["worst"],
+                          "step_mode": "cuda_graph" if plain["graph"] else "host_loop",
+                          "gpu_launches": int(plain["launches"])},
+            "learned": None if net is None else {
+                "ms_per_step": ms, "mean_sweeps_per_step": mean_sweeps,
+                "speedup_vs_plain_sor": plain["ms"] / ms, "sweeps_ratio": plain_sweeps / max(mean_sweeps, 1.0),
+                "net_every_sweeps": NET_EVERY, "stride": 4,
+                "weights": os.path.relpath(WEIGHTS, ROOT),
+                "note": "same start state and stop test (FP64 relative residual <= 1e-6 every step); "
+                        "network time included"},
+            "roofline": {"kernel": f"{sor_kernel_name(tile)} (red-black SOR sweep, tile {les.les_sor_tile(tile) if tile >= 0 else 'two-pass'}, kc {kc})",
                          "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "traffic": None,
@@ -306,12 +374,13 @@ def run_ours(args):
             state = {"fields": [f.astype(np.float64) for f in dom.fields()],
                      "F": [dom.aux(a).astype(np.float64) for a in (les.LES_AUX_FU, les.LES_AUX_FV, les.LES_AUX_FW)],
                      "step": dom.step(0)["step"]}
-            t_step, det = oracle_sample(sc, mean_sweeps, n_sample_sweeps=40, state=state)
+            t_step, det = oracle_sample(sc, plain_sweeps, n_sample_sweeps=40, state=state)
             line["cpu_baseline"] = {
                 "value": n / t_step / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
                 "sample": (f"one single-threaded FP64 oracle step of the same 150x150x90 state with 40 "
                            f"SOR sweeps, timed phase by phase (wall {det['sample_wall_s']:.1f} s), SOR "
-                           f"part scaled to the GPU run's {mean_sweeps:.0f} sweeps/step"),
+                           f"part scaled to the plain GPU step's {plain_sweeps:.0f} sweeps/step (the oracle "
+                           f"runs plain SOR)"),
                 "detail": det}
         print(json.dumps(line))
     if world > 1:
@@ -327,6 +396,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="time the plain SOR step only")
     ap.add_argument("--ncu-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     args = ap.parse_args()

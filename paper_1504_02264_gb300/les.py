@@ -111,12 +111,14 @@ def lib(build_if_missing: bool = False):
         L.les_autotune_sor.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
         L.les_set_timing.argtypes = [vp, i32]
         L.les_get_timing.argtypes = [vp, ctypes.POINTER(les_timing_t)]
-        for name in ("les_set_record", "les_set_record_at", "les_set_net_schedule", "les_set_warmstart", "les_net_create", "les_net_num_params",
-                     "les_net_set_stride", "les_net_get_stride",
+        for name in ("les_set_record", "les_set_record_at", "les_set_net_schedule", "les_set_warmstart",
+                     "les_net_create", "les_net_num_params", "les_net_set_stride", "les_net_get_stride",
                      "les_net_get_params", "les_net_set_params", "les_net_forward", "les_net_gradient",
-                     "les_net_train_step", "les_residual_noalloc", "les_profiler_range", "les_set_graph", "les_set_sor_config", "les_get_sor_config", "les_sor_tile", "les_autotune_sor",
-                     "les_set_timing", "les_get_timing", "les_create", "les_set_fields", "les_get_fields", "les_set_inflow", "les_step",
-                     "les_pressure_solve", "les_get_aux", "les_get_state", "les_set_state"):
+                     "les_net_train_step", "les_residual_noalloc", "les_profiler_range", "les_set_graph",
+                     "les_set_sor_config", "les_get_sor_config", "les_sor_tile", "les_autotune_sor",
+                     "les_set_timing", "les_get_timing", "les_create", "les_set_fields", "les_get_fields",
+                     "les_set_inflow", "les_step", "les_pressure_solve", "les_get_aux", "les_get_state",
+                     "les_set_state"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib

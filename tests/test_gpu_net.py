@@ -311,3 +311,45 @@ def test_warm_start_rejects_bad_use(net):
         les.les_set_warmstart(d32.h, 7, None)
     d64.close()
     d32.close()
+
+
+def test_trained_network_gain():
+    """What the trained network (the package's weights, stride 4) gains over
+    plain SOR on an unseen random city: the same tolerance every step with far
+    fewer sweeps and less time per step, network time included."""
+    import os
+    import time
+    from paper_1504_02264_gb300 import train
+    path = os.path.join(os.path.dirname(les.__file__), "weights", "warmstart_s4.npz")
+    net = train.load(path)
+    sc = scene.random_scene(seed=4242, nx=96, ny=96, nz=48, n_buildings=40, x_margin=12, max_sweeps=60000,
+                            check_every=20)
+    base = les.Domain(sc)
+    for _ in range(4):
+        base.step()
+    state = base.get_state()
+    base.close()
+    res = {}
+    for mode in ("plain", "learned"):
+        d = les.Domain(sc)
+        d.set_state(state)
+        if mode == "learned":
+            d.set_warmstart(net)
+            d.set_net_schedule(10)
+            d.step()                      # builds its graphs
+            d.set_state(state)
+        sw, ms = [], []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = d.step()
+            torch.cuda.synchronize()
+            ms.append(1e3 * (time.perf_counter() - t0))
+            assert st["rc"] == 0 and st["rel_residual"] <= 1e-6, (mode, st)
+            sw.append(st["sweeps"])
+        res[mode] = (np.mean(sw), np.median(ms))
+        d.close()
+    net.close()
+    print("plain vs learned (sweeps, ms per step):", res)
+    assert res["learned"][0] * 3 <= res["plain"][0], res
+    assert res["learned"][1] < res["plain"][1], res
