@@ -626,7 +626,7 @@ int launch_accum(const Geo<T>& g, double* ph, const T* dl, const Scalars* sc, in
 // Grid-stride reductions use at most kReduceBlocks blocks, so the last-block
 // completion counter sees few atomics.
 constexpr int kReduceBlocks = 1024;
-constexpr int kEstChunk = 16;      // planes per thread in the estimate kernel
+constexpr int kEstChunk = 8;       // planes per thread in the estimate and line-search kernels
 int reduce_blocks(const Dom& d) {
     long long n = (long long)d.nx * d.ny * d.nz;
     long long b = (n + 255) / 256;
@@ -732,29 +732,32 @@ __global__ void __launch_bounds__(256) k_sor_est(Geo<T> g, const T* dl, const T*
                                                  CondArgs ca) {
     const Dom& d = g.d;
     if (red.sc->done) return;      // uniform over the grid
-    // a (32 x 8) column tile marching over a chunk of kEstChunk planes
+    // a (32 x 8) column tile marching over a chunk of kEstChunk planes; the
+    // cell index advances by one plane per step, neighbour offsets are 32-bit
     const int i = blockIdx.x * 32 + threadIdx.x + 1;
     const int j = blockIdx.y * 8 + threadIdx.y + 1;
     const int kb = blockIdx.z * kEstChunk + 1, ke = min(kb + kEstChunk, d.nz + 1);
     T acc = T(0);
     if (i <= d.nx && j <= d.ny) {
-        Poisson<T> Q{g};
-        for (int k = kb; k < ke; ++k) {
-            const long long c = d.at(i, j, k);
+        const int pl = (int)d.plane;
+        const int oe = (d.perx && i == d.nx) ? -(d.nx - 1) : 1;
+        const int ow = (d.perx && i == 1) ? (d.nx - 1) : -1;
+        const int on = (d.pery && j == d.ny) ? -(d.ny - 1) * d.px : d.px;
+        const int os = (d.pery && j == 1) ? (d.ny - 1) * d.px : -d.px;
+        long long c = d.at(i, j, kb);
+        for (int k = kb; k < ke; ++k, c += pl) {
             const uint8_t f = g.flags[c];
             if (!(f & F_UNK)) continue;
-            T ae, aw, an, as, at, ab;
-            Q.coefs(f, k, g.cx, g.cy, g.cT, g.cB, ae, aw, an, as, at, ab);
-            long long e, w, nn, s_, t, b;
-            Q.nbr(i, j, k, e, w, nn, s_, t, b);
+            const int ot = (d.perz && k == d.nz) ? -(d.nz - 1) * pl : pl;
+            const int ob = (d.perz && k == 1) ? (d.nz - 1) * pl : -pl;
             const T dc = dl[c];
             T s = T(0);
-            s += ae * (dl[e] - dc);
-            s += aw * (dl[w] - dc);
-            s += an * (dl[nn] - dc);
-            s += as * (dl[s_] - dc);
-            s += at * (dl[t] - dc);
-            s += ab * (dl[b] - dc);
+            if (f & F_E) s += g.cx * (dl[c + oe] - dc);
+            if (f & F_W) s += g.cx * (dl[c + ow] - dc);
+            if (f & F_N) s += g.cy * (dl[c + on] - dc);
+            if (f & F_S) s += g.cy * (dl[c + os] - dc);
+            if (f & F_T) s += g.cT[k] * (dl[c + ot] - dc);
+            if (f & F_B) s += g.cB[k] * (dl[c + ob] - dc);
             const T res = r[c] - s;
             if (rout) rout[c] = res;        // the current residual, input of the network correction
             acc += res * res;
@@ -909,33 +912,32 @@ __global__ void __launch_bounds__(256) k_warm_ls(Geo<T> g, const T* r, const flo
     const int i = blockIdx.x * 32 + threadIdx.x + 1;
     const int j = blockIdx.y * 8 + threadIdx.y + 1;
     const int kb = blockIdx.z * kEstChunk + 1, ke = min(kb + kEstChunk, d.nz + 1);
-    const int sx = 1, sy = d.nx, sz = d.nx * d.ny;      // dense strides (the grid has < 2^31 cells)
     T s0 = T(0), s1 = T(0);
     if (i <= d.nx && j <= d.ny) {
-        // flags never open a face across a non-periodic domain boundary, so
-        // every neighbour read below stays inside the dense array
-        const int oe = (d.perx && i == d.nx) ? -(d.nx - 1) * sx : sx;
-        const int ow = (d.perx && i == 1) ? (d.nx - 1) * sx : -sx;
+        // dense offsets (the grid has < 2^31 cells); flags never open a face
+        // across a non-periodic domain boundary, so every neighbour read
+        // stays inside the dense array
+        const int sy = d.nx, sz = d.nx * d.ny;
+        const int oe = (d.perx && i == d.nx) ? -(d.nx - 1) : 1;
+        const int ow = (d.perx && i == 1) ? (d.nx - 1) : -1;
         const int on = (d.pery && j == d.ny) ? -(d.ny - 1) * sy : sy;
         const int os = (d.pery && j == 1) ? (d.ny - 1) * sy : -sy;
-        for (int k = kb; k < ke; ++k) {
-            const long long c = d.at(i, j, k);
+        const int pl = (int)d.plane;
+        long long c = d.at(i, j, kb);
+        int v = ((kb - 1) * d.ny + (j - 1)) * d.nx + (i - 1);
+        for (int k = kb; k < ke; ++k, c += pl, v += sz) {
             const uint8_t f = g.flags[c];
             if (!(f & F_UNK)) continue;
-            const int v = ((k - 1) * d.ny + (j - 1)) * d.nx + (i - 1);
             const int ot = (d.perz && k == d.nz) ? -(d.nz - 1) * sz : sz;
             const int ob = (d.perz && k == 1) ? (d.nz - 1) * sz : -sz;
-            Poisson<T> P{g};
-            T ae, aw, an, as, at, ab;
-            P.coefs(f, k, g.cx, g.cy, g.cT, g.cB, ae, aw, an, as, at, ab);
             const T qc = (T)q[v];
             T aq = T(0);
-            if (f & F_E) aq += ae * ((T)q[v + oe] - qc);
-            if (f & F_W) aq += aw * ((T)q[v + ow] - qc);
-            if (f & F_N) aq += an * ((T)q[v + on] - qc);
-            if (f & F_S) aq += as * ((T)q[v + os] - qc);
-            if (f & F_T) aq += at * ((T)q[v + ot] - qc);
-            if (f & F_B) aq += ab * ((T)q[v + ob] - qc);
+            if (f & F_E) aq += g.cx * ((T)q[v + oe] - qc);
+            if (f & F_W) aq += g.cx * ((T)q[v + ow] - qc);
+            if (f & F_N) aq += g.cy * ((T)q[v + on] - qc);
+            if (f & F_S) aq += g.cy * ((T)q[v + os] - qc);
+            if (f & F_T) aq += g.cT[k] * ((T)q[v + ot] - qc);
+            if (f & F_B) aq += g.cB[k] * ((T)q[v + ob] - qc);
             const T vq = g.dz[k] * qc;
             s0 += vq * r[c];
             s1 += vq * aq;
@@ -980,9 +982,10 @@ __global__ void k_warm_apply_dl(Geo<T> g, T* dl, const float* q, const double* a
     const int k = blockIdx.z + 1;
     if (i > d.nx || j > d.ny) return;
     const long long c = d.at(i, j, k);
-    if (!(g.flags[c] & F_UNK)) return;
     const T a = (T)*alpha;
-    const T base = sc->zcopy ? T(0) : dl[c];
+    const bool zero = sc->zcopy != 0;
+    if (!(g.flags[c] & F_UNK)) return;
+    const T base = zero ? T(0) : dl[c];
     dl[c] = base + a * (T)q[((k - 1) * d.ny + (j - 1)) * d.nx + (i - 1)];
 }
 

@@ -26,6 +26,12 @@ constexpr int TX = 16, TY = 4, TZ = 2, HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// Shared tiles hold 16 channels (32 bytes) per row; ldmatrix reads 8
+// consecutive rows, and rows r and r+4 would fall on the same banks.  The two
+// 16-byte halves of a row are swapped when bit 2 of the row index is set, so
+// any 8 consecutive rows hit 8 distinct bank groups.
+__device__ __forceinline__ int swz(int row) { return (row >> 2) & 1; }
+
 __device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
                  : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
@@ -89,13 +95,13 @@ k_conv3(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ w
             const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = z0 - 1 + hz;
             const bool ok = gx >= 0 && gx < X && gy >= 0 && gy < Y && gz >= 0 && gz < Z;
             const __nv_bfloat16* src = ok ? x + (((size_t)gz * Y + gy) * X + gx) * Cin + c0 + 8 * h : x;
-            cp_async16(smem_addr(&S.in[hz][hy][hx][8 * h]), src, ok ? 16 : 0);
+            cp_async16(smem_addr(&S.in[hz][hy][hx][8 * (h ^ swz(hx))]), src, ok ? 16 : 0);
         }
         for (int q = tid; q < 27 * CO * 2; q += 256) {
             const int h = q & 1, r = q >> 1, co = r % CO, tap = r / CO;
             const bool ok = co0 + co < Cout;
             const __nv_bfloat16* src = ok ? w + ((size_t)tap * Cout + co0 + co) * Cin + c0 + 8 * h : w;
-            cp_async16(smem_addr(&S.w[tap][co][8 * h]), src, ok ? 16 : 0);
+            cp_async16(smem_addr(&S.w[tap][co][8 * (h ^ swz(co))]), src, ok ? 16 : 0);
         }
         cp_async_commit();
     };
@@ -104,7 +110,7 @@ k_conv3(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ w
     for (int n = 0; n < CO / 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
     const int nch = Cin / 16;
     const int mat = lane >> 3, r8 = lane & 7;
-    const int vrow = r8 + 8 * (mat & 1), koff = 8 * (mat >> 1);
+    const int vrow = r8 + 8 * (mat & 1), khalf = mat >> 1;
     stage(0, st[0]);
     for (int c = 0; c < nch; ++c) {
         if (c + 1 < nch) {
@@ -120,11 +126,11 @@ k_conv3(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ w
             const int dx = tap % 3, dy = (tap / 3) % 3, dz = tap / 9;
             // A: rows = 16 voxels of the warp's row shifted by the tap, k = 16 channels
             uint32_t a0, a1, a2, a3;
-            ldsm_x4(smem_addr(&S.in[wz + dz][wy + dy][vrow + dx][koff]), a0, a1, a2, a3);
+            ldsm_x4(smem_addr(&S.in[wz + dz][wy + dy][vrow + dx][8 * (khalf ^ swz(vrow + dx))]), a0, a1, a2, a3);
 #pragma unroll
             for (int n = 0; n < CO / 8; n += 2) {
                 // B: two n-tiles; matrices (co rows, ci 0-7 | 8-15) of tile n and n+1
-                const int co = 8 * (n + (mat >> 1)) + r8, ko = 8 * (mat & 1);
+                const int co = 8 * (n + (mat >> 1)) + r8, ko = 8 * ((mat & 1) ^ swz(co));
                 uint32_t b0, b1, b2, b3;
                 ldsm_x4(smem_addr(&S.w[tap][co][ko]), b0, b1, b2, b3);
                 mma_bf16(acc[n], a0, a1, a2, a3, b0, b1);
@@ -175,8 +181,11 @@ int conv3_prepare() {
 void conv3_fwd(const __nv_bfloat16* x, const __nv_bfloat16* w, __nv_bfloat16* y, const __nv_bfloat16* skip,
                __nv_bfloat16* ysum, int X, int Y, int Z, int Cin, int Cout, int relu, cudaStream_t s,
                const int* gate) {
-    const int co = Cout >= 32 ? 32 : 16;
+    // 32 output channels per CTA when the grid fills the GPU, else 16 (twice
+    // the CTAs, half the weights staged per CTA: small levels are latency-bound)
     const int ntz = (Z + TZ - 1) / TZ;
+    const long long tiles = (long long)((X + TX - 1) / TX) * ((Y + TY - 1) / TY) * ntz;
+    const int co = (Cout >= 32 && tiles * (Cout / 32) >= 2 * 152) ? 32 : 16;
     dim3 grid((X + TX - 1) / TX, (Y + TY - 1) / TY, ntz * ((Cout + co - 1) / co));
     if (co == 32)
         k_conv3<32><<<grid, 256, 2 * sizeof(ConvStage<32>), s>>>(x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu, gate);
@@ -228,7 +237,7 @@ k_conv3_wgrad(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restri
             uint4 val = make_uint4(0, 0, 0, 0);
             if (gx >= 0 && gx < X && gy >= 0 && gy < Y && gz >= 0 && gz < Z)
                 val = *reinterpret_cast<const uint4*>(x + (((size_t)gz * Y + gy) * X + gx) * Cin + ci0 + 8 * h);
-            *reinterpret_cast<uint4*>(&sIn[hz][hy][hx][8 * h]) = val;
+            *reinterpret_cast<uint4*>(&sIn[hz][hy][hx][8 * (h ^ swz(hx))]) = val;
         }
         for (int q = tid; q < TZ * TY * TX * 2; q += 256) {
             const int h = q & 1, v = q >> 1;
@@ -237,7 +246,7 @@ k_conv3_wgrad(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restri
             uint4 val = make_uint4(0, 0, 0, 0);
             if (gx < X && gy < Y && gz < Z)
                 val = *reinterpret_cast<const uint4*>(dy + (((size_t)gz * Y + gy) * X + gx) * Cout + co0 + 8 * h);
-            *reinterpret_cast<uint4*>(&sG[lz][ly][lx][8 * h]) = val;
+            *reinterpret_cast<uint4*>(&sG[lz][ly][lx][8 * (h ^ swz(lx))]) = val;
         }
         __syncthreads();
         for (int row = 0; row < TY * TZ; ++row) {
@@ -246,7 +255,7 @@ k_conv3_wgrad(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restri
             // matrices: (co 0-7, v 0-7), (co 8-15, v 0-7), (co 0-7, v 8-15), (co 8-15, v 8-15)
             uint32_t a0, a1, a2, a3;
             {
-                const int v = r8 + 8 * (mat >> 1), c = 8 * (mat & 1);
+                const int v = r8 + 8 * (mat >> 1), c = 8 * ((mat & 1) ^ swz(v));
                 ldsm_x4_t(smem_addr(&sG[rz][ry][v][c]), a0, a1, a2, a3);
             }
 #pragma unroll
@@ -259,7 +268,7 @@ k_conv3_wgrad(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restri
                 for (int n = 0; n < 2; ++n) {
                     uint32_t b0, b1;
                     const int v = r8 + 8 * (mat & 1);
-                    ldsm_x2_t(smem_addr(&sIn[rz + dz][ry + dyy][v + dx][8 * n]), b0, b1);
+                    ldsm_x2_t(smem_addr(&sIn[rz + dz][ry + dyy][v + dx][8 * (n ^ swz(v + dx))]), b0, b1);
                     mma_bf16(acc[a][n], a0, a1, a2, a3, b0, b1);
                 }
             }
@@ -417,34 +426,51 @@ __global__ void k_pool_dense_s(const float* a, float* b, int Xf, int Yf, int Zf,
 }
 
 // the solver's padded residual (unknowns only) and unknown mask -> dense
-// coarse; a thread per coarse cell, the S^3 children unrolled
+// coarse.  Block (32, S, SZ): thread (tx, ty, tz) sums the S fine cells of
+// one fine row (y = cy*S + ty, z = cz*S + tz [+ SZ ...]) under coarse cell
+// cx = blockIdx.x*32 + tx, then the block adds the rows in shared memory
+// (fixed order: deterministic).
 template <int S>
 __global__ void k_pool_padded_s(const float* r, const uint8_t* flags, Dom d, float* rc, float* mc, const int* gate) {
+    constexpr int SZ = S < 4 ? S : 4;
+    __shared__ float sr[SZ][S][32], sm[SZ][S][32];
     if (gate && *(volatile const int*)gate) return;
     const int Xc = (d.nx + S - 1) / S, Yc = (d.ny + S - 1) / S;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
-    if (x >= Xc) return;
+    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+    const int cx = blockIdx.x * 32 + tx, cy = blockIdx.y, cz = blockIdx.z;
     float ar = 0.f, am = 0.f;
+    const int fy = cy * S + ty;
+    if (cx < Xc && fy < d.ny) {
 #pragma unroll
-    for (int dz = 0; dz < S; ++dz)
+        for (int zz = 0; zz < S; zz += SZ) {
+            const int fz = cz * S + tz + zz;
+            if (fz >= d.nz) break;
+            const long long row = d.at(1, fy + 1, fz + 1) + (long long)cx * S;
 #pragma unroll
-        for (int dy = 0; dy < S; ++dy) {
-            const int fy = y * S + dy, fz = z * S + dz;
-            if (fy >= d.ny || fz >= d.nz) continue;
-            const long long row = d.at(1, fy + 1, fz + 1);
-#pragma unroll
-            for (int dx = 0; dx < S; ++dx) {
-                const int fx = x * S + dx;
-                if (fx < d.nx && (flags[row + fx] & F_UNK)) {
-                    ar += r[row + fx];
+            for (int dx = 0; dx < S; ++dx)
+                if (cx * S + dx < d.nx && (flags[row + dx] & F_UNK)) {
+                    ar += r[row + dx];
                     am += 1.f;
                 }
-            }
         }
-    const float inv = 1.f / (float)(S * S * S);
-    const int q = (z * Yc + y) * Xc + x;
-    rc[q] = ar * inv;
-    mc[q] = am * inv;
+    }
+    sr[tz][ty][tx] = ar;
+    sm[tz][ty][tx] = am;
+    __syncthreads();
+    if (ty == 0 && tz == 0 && cx < Xc) {
+        float tr = 0.f, tm = 0.f;
+#pragma unroll
+        for (int a = 0; a < SZ; ++a)
+#pragma unroll
+            for (int b = 0; b < S; ++b) {
+                tr += sr[a][b][tx];
+                tm += sm[a][b][tx];
+            }
+        const float inv = 1.f / (float)(S * S * S);
+        const int q = (cz * Yc + cy) * Xc + cx;
+        rc[q] = tr * inv;
+        mc[q] = tm * inv;
+    }
 }
 
 // trilinear prolongation of a coarse cell-centred field to the fine cells,
@@ -486,14 +512,42 @@ __global__ void k_prolong_dense(const float* yc, const float* mask, float* out, 
     const int Xc = (Xf + s - 1) / s, Yc = (Yf + s - 1) / s, Zc = (Zf + s - 1) / s;
     out[q] = mask[q] * trilinear(yc, Xc, Yc, Zc, s, x, y, z);
 }
-// dense fine output on the solver's unknowns (3-D grid, 32-bit indices)
-__global__ void k_prolong_flags(const float* yc, const uint8_t* flags, Dom d, int s, float* out, const int* gate) {
+// dense fine output on the solver's unknowns: a thread takes the S fine
+// cells of one fine row under coarse column cx, interpolating between the
+// (y, z)-interpolated coarse columns cx-1, cx, cx+1
+template <int S>
+__global__ void k_prolong_flags(const float* yc, const uint8_t* flags, Dom d, float* out, const int* gate) {
     if (gate && *(volatile const int*)gate) return;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
-    if (x >= d.nx) return;
-    const int Xc = (d.nx + s - 1) / s, Yc = (d.ny + s - 1) / s, Zc = (d.nz + s - 1) / s;
-    const bool unk = flags[d.at(x + 1, y + 1, z + 1)] & F_UNK;
-    out[(z * d.ny + y) * d.nx + x] = unk ? trilinear(yc, Xc, Yc, Zc, s, x, y, z) : 0.f;
+    const int Xc = (d.nx + S - 1) / S, Yc = (d.ny + S - 1) / S, Zc = (d.nz + S - 1) / S;
+    const int cx = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (cx >= Xc) return;
+    int y0, z0;
+    float wy, wz;
+    lin_w(y, S, Yc, y0, wy);
+    lin_w(z, S, Zc, z0, wz);
+    const int y1 = min(y0 + 1, Yc - 1), z1 = min(z0 + 1, Zc - 1);
+    auto col = [&](int c) {
+        c = max(0, min(c, Xc - 1));
+        auto at = [&](int b, int cc) { return yc[((size_t)cc * Yc + b) * Xc + c]; };
+        const float a0 = (1.f - wy) * at(y0, z0) + wy * at(y1, z0);
+        const float a1 = (1.f - wy) * at(y0, z1) + wy * at(y1, z1);
+        return (1.f - wz) * a0 + wz * a1;
+    };
+    const float cm = col(cx - 1), c0v = col(cx), cp = col(cx + 1);
+    const long long row = d.at(1, y + 1, z + 1);
+    float* o = out + ((size_t)z * d.ny + y) * d.nx;
+#pragma unroll
+    for (int m = 0; m < S; ++m) {
+        const int x = cx * S + m;
+        if (x >= d.nx) break;
+        int x0;
+        float wx;
+        lin_w(x, S, Xc, x0, wx);
+        const int x1 = min(x0 + 1, Xc - 1);
+        const float v0 = x0 < cx ? cm : (x0 == cx ? c0v : cp);
+        const float v1 = x1 < cx ? cm : (x1 == cx ? c0v : cp);
+        o[x] = (flags[row + x] & F_UNK) ? (1.f - wx) * v0 + wx * v1 : 0.f;
+    }
 }
 
 // training loss 1/n * sum mask (y - t)^2 and its gradient
@@ -566,12 +620,12 @@ void pool_dense_s(const float* a, float* b, int Xf, int Yf, int Zf, int st, cuda
 void pool_padded_s(const float* r, const uint8_t* flags, const Dom& d, int st, float* rc, float* mc, cudaStream_t s,
                    const int* gate) {
     const int Xc = (d.nx + st - 1) / st, Yc = (d.ny + st - 1) / st, Zc = (d.nz + st - 1) / st;
-    const dim3 grid((Xc + 63) / 64, Yc, Zc);
+    const dim3 grid((Xc + 31) / 32, Yc, Zc);
     switch (st) {
-        case 1: k_pool_padded_s<1><<<grid, 64, 0, s>>>(r, flags, d, rc, mc, gate); break;
-        case 2: k_pool_padded_s<2><<<grid, 64, 0, s>>>(r, flags, d, rc, mc, gate); break;
-        case 4: k_pool_padded_s<4><<<grid, 64, 0, s>>>(r, flags, d, rc, mc, gate); break;
-        default: k_pool_padded_s<8><<<grid, 64, 0, s>>>(r, flags, d, rc, mc, gate); break;
+        case 1: k_pool_padded_s<1><<<grid, dim3(32, 1, 1), 0, s>>>(r, flags, d, rc, mc, gate); break;
+        case 2: k_pool_padded_s<2><<<grid, dim3(32, 2, 2), 0, s>>>(r, flags, d, rc, mc, gate); break;
+        case 4: k_pool_padded_s<4><<<grid, dim3(32, 4, 4), 0, s>>>(r, flags, d, rc, mc, gate); break;
+        default: k_pool_padded_s<8><<<grid, dim3(32, 8, 4), 0, s>>>(r, flags, d, rc, mc, gate); break;
     }
 }
 void prolong_dense(const float* yc, const float* mask, float* out, int Xf, int Yf, int Zf, int st, cudaStream_t s) {
@@ -579,7 +633,14 @@ void prolong_dense(const float* yc, const float* mask, float* out, int Xf, int Y
 }
 void prolong_flags(const float* yc, const uint8_t* flags, const Dom& d, int st, float* out, cudaStream_t s,
                    const int* gate) {
-    k_prolong_flags<<<dim3((d.nx + 127) / 128, d.ny, d.nz), 128, 0, s>>>(yc, flags, d, st, out, gate);
+    const int Xc = (d.nx + st - 1) / st;
+    const dim3 grid((Xc + 63) / 64, d.ny, d.nz);
+    switch (st) {
+        case 1: k_prolong_flags<1><<<grid, 64, 0, s>>>(yc, flags, d, out, gate); break;
+        case 2: k_prolong_flags<2><<<grid, 64, 0, s>>>(yc, flags, d, out, gate); break;
+        case 4: k_prolong_flags<4><<<grid, 64, 0, s>>>(yc, flags, d, out, gate); break;
+        default: k_prolong_flags<8><<<grid, 64, 0, s>>>(yc, flags, d, out, gate); break;
+    }
 }
 void mse(const float* y, const float* t, const float* mask, float* g, double* loss, size_t n, double inv_n,
          cudaStream_t s) {
