@@ -39,6 +39,10 @@ WEIGHTS = os.path.join(ROOT, "paper_1504_02264_gb300", "weights", "warmstart_s4.
 NET_EVERY = 10                  # sweeps between learned corrections (trained schedule)
 UNIT = "Mcell-steps/s"
 SOR_BYTES_PER_CELL = 13.0       # per sweep: read p, rhs (4+4), flags (1), write p (4)
+# DRAM bytes (read + write) of one k_sor_tma launch on this workload from one
+# ncu capture (cold L2; profiles/sor_tma_28x8x8_random150x150x90.md); reported
+# only while that kernel is the one timed
+SOR_TMA_TILE, SOR_TMA_DRAM_BYTES = 17, 20.147968e6 + 2.048e3
 L2_FLUSH_BYTES = 256 << 20
 # mean SOR sweeps per step of this workload after the default warm-up, from the
 # GPU arm (the FP64 path takes the same sweeps as the oracle); used only to scale
@@ -357,7 +361,8 @@ def run_ours(args):
             "roofline": {"kernel": f"{sor_kernel_name(tile)} (red-black SOR sweep, tile {les.les_sor_tile(tile) if tile >= 0 else 'two-pass'}, kc {kc})",
                          "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "peak_kind": peak_kind, "traffic": None,
+                         "peak_kind": peak_kind,
+                         "traffic": SOR_TMA_DRAM_BYTES if tile == SOR_TMA_TILE else None,
                          "bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms,
                          "note": "150x150x90 SOR state (p, rhs, flags ~18 MB) is L2-resident"},
             "phase_ms_per_step": {k: tm[k] / max(tm["steps"], 1) for k in
