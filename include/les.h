@@ -335,6 +335,45 @@ int les_set_warmstart(les_handle h, int32_t mode, les_net net);
  * test is unchanged. */
 int les_set_net_schedule(les_handle h, int32_t every_sweeps);
 
+/*
+ * Ensembles: n domains of uneven size, each with its own buildings, inflow
+ * and state, stepped together.  Every member is an ordinary FP32 domain
+ * handle created from grids[i], solid[i], inflow[i] exactly as by
+ * les_create, on the ensemble's stream; les_ensemble_member gives the
+ * handle for les_set_fields / les_get_fields / les_get_aux / les_get_state
+ * (the ensemble owns it: do not destroy it, and step members only through
+ * les_ensemble_step, else the next ensemble step returns LES_ESTATE).
+ * The SOR solves of all members run as batched launches over a flattened
+ * (member, tile) work list: one persistent sweep launch per sweep for the
+ * whole ensemble (28 x BY x BZ row tiles, `tile` 0..4 = 8x8, 4x8, 8x4,
+ * 16x4, 4x16; ctas_per_sm CTAs per SM walk the list), one estimate and one
+ * refinement launch per batch of check_every sweeps, chunks of batches in
+ * CUDA graphs; each member stops at its own tolerance and sweep count.  A
+ * member evolves bit-identically to the same domain stepped alone with the
+ * same row tile (les_set_sor_config(h, 12 + tile, 0)).
+ * Requirements (else LES_EINVAL): 1 <= n <= 64; every member FP32, tolerance
+ * mode (fixed_sweeps = 0), the same even check_every, and max_sweeps a
+ * multiple of it.  The ensemble keeps no pointer to the caller's arrays.
+ * les_ensemble_step fills stats[i] for member i after the last step when
+ * stats is not NULL (n entries); returns LES_ENOCONV if any member ended
+ * above its tolerance.  les_ensemble_autotune times `sweeps` batched sweeps
+ * per (tile, CTAs per SM) candidate on the members' scratch correction
+ * buffers (the state is not changed) and keeps the fastest.
+ */
+typedef struct les_ensemble_s* les_ensemble;
+int les_ensemble_create(int32_t n, const les_grid_t* grids, const uint8_t* const* solid, const double* const* inflow,
+                        void* stream, les_ensemble* out);
+void les_ensemble_destroy(les_ensemble e);
+const char* les_ensemble_last_error(les_ensemble e);
+int les_ensemble_size(les_ensemble e, int32_t* n);
+int les_ensemble_member(les_ensemble e, int32_t i, les_handle* out);
+int les_ensemble_step(les_ensemble e, int32_t nsteps, les_stats_t* stats);
+int les_ensemble_set_graph(les_ensemble e, int32_t enable);
+int les_ensemble_set_tile(les_ensemble e, int32_t tile, int32_t ctas_per_sm);
+int les_ensemble_get_tile(les_ensemble e, int32_t* tile, int32_t* ctas);
+int les_ensemble_autotune(les_ensemble e, int32_t sweeps, double* best_ms_per_sweep);
+int les_ensemble_launches(les_ensemble e, int64_t* launches);
+
 /* Bracket a region for a profiler started with capture off
  * (cudaProfilerStart when start != 0, cudaProfilerStop otherwise). */
 int les_profiler_range(int32_t start);

@@ -1338,3 +1338,84 @@ int les_get_timing(les_handle h, les_timing_t* t) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// ensemble support: a member is an ordinary FP32 domain handle
+namespace les {
+
+int member_check(les_s* h, char* why, size_t n) {
+    if (!h) {
+        snprintf(why, n, "member handle is NULL");
+        return LES_EINVAL;
+    }
+    if (h->prec != LES_FP32) {
+        snprintf(why, n, "ensemble members run in FP32");
+        return LES_EINVAL;
+    }
+    return LES_OK;
+}
+
+void member_fill(les_s* h, EnsMember<float>& M, int ens_tile, int parity) {
+    const Dom& d = h->d;
+    M.g = geo<float>(h);
+    M.dl[0] = (float*)h->dl[0];
+    M.dl[1] = (float*)h->dl[1];
+    M.rr = (float*)h->rr;
+    M.rhs = (const float*)h->rhs;
+    M.ph = h->ph[parity];
+    M.vfluid = h->vfluid;
+    M.tol = h->g.tol;
+    M.limit = h->g.max_sweeps;
+    M.red = reducer(h);
+    const SorTile t = ens_tile_shape(ens_tile);
+    M.sgrid[0] = (d.nx + t.tx - 1) / t.tx;
+    M.sgrid[1] = (d.ny + t.ty - 1) / t.ty;
+    M.sgrid[2] = (d.nz + t.tz - 1) / t.tz;
+    M.egrid[0] = (d.nx + 31) / 32;
+    M.egrid[1] = (d.ny + 7) / 8;
+    M.egrid[2] = (d.nz + 7) / 8;      // the estimate's plane chunk
+    M.agrid[0] = (d.nx + 31) / 32;
+    M.agrid[1] = (d.ny + 7) / 8;
+    M.agrid[2] = d.nz;
+    M.rblocks = reduce_blocks(d);
+}
+
+int member_check_every(const les_s* h) { return h->g.check_every; }
+int member_max_sweeps(const les_s* h) { return h->g.max_sweeps; }
+cudaStream_t member_stream(const les_s* h) { return h->stream; }
+
+int member_prefix(les_s* h, cudaStream_t s) {
+    Geo<float> g = geo<float>(h);
+    launch_prefix<float>(h, g, s);
+    CK(cudaGetLastError());
+    return LES_OK;
+}
+
+int member_finish(les_s* h, cudaStream_t s) {
+    Geo<float> g = geo<float>(h);
+    launch_project_step<float>(h, g, h->cur, s);
+    CK(cudaGetLastError());
+    h->cur = 1 - h->cur;
+    h->step += 1;
+    return LES_OK;
+}
+
+int member_stats(les_s* h, les_stats_t* st) {
+    int rc = fetch_scalars(h);
+    if (rc) return rc;
+    int status = (!h->g.fixed_sweeps && h->sc_host->noconv_any) ? LES_ENOCONV : LES_OK;
+    if (h->sc_host->nonfinite) status = fail(h, LES_ENONFINITE, "SOR residual is not finite");
+    if (st) fill_stats(h, st, status);
+    return status;
+}
+
+void member_set_dcur(les_s* h, int dcur) { h->dcur = dcur; }
+int member_parity(const les_s* h) { return h->cur; }
+int member_begin(les_s* h, cudaStream_t s) {
+    CK(cudaMemsetAsync(&h->sc->noconv_any, 0, sizeof(int), s));
+    return LES_OK;
+}
+int* member_done_flag(les_s* h) { return &h->sc->done; }
+
+}  // namespace les
+

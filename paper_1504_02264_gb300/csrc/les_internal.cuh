@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/les.h"
+
 namespace les {
 
 constexpr int OX = 3;
@@ -140,10 +142,52 @@ template <typename T> int launch_gauge(const Geo<T>& g, const double* p_in, doub
                                        const Scalars* sc, cudaStream_t s);
 
 // fused SOR sweep (les_sor.cu): tile shape index into kSorTiles and k-chunk
+// ---------------------------------------------------------------------------
+// ensembles: the per-member arguments of the batched kernels, passed as one
+// __grid_constant__ kernel parameter (< 32 KB)
+constexpr int kMaxMembers = 64;
+template <typename T>
+struct EnsMember {
+    Geo<T> g;
+    T* dl[2];               // SOR correction (ping-pong)
+    T* rr;                  // residual of the FP64 pressure (field type)
+    const T* rhs;
+    double* ph;             // FP64 pressure of the current step
+    double vfluid;
+    double tol;
+    int limit;              // sweep budget of the member's solve
+    Reduce red;             // the member's partials, counter and scalars
+    int sgrid[3];           // sweep tiles of the ensemble tile shape
+    int egrid[3];           // estimate blocks
+    int agrid[3];           // accumulate blocks (32 x 8 threads, one plane per block)
+    int rblocks;            // residual blocks (grid-stride)
+};
+template <typename T>
+struct EnsTab {
+    int n;
+    int tile;                       // ensemble row tile 0..kNumEnsTiles-1
+    int sbeg[kMaxMembers + 1];      // first flattened item of each member, per kernel kind
+    int ebeg[kMaxMembers + 1];
+    int abeg[kMaxMembers + 1];
+    int rbeg[kMaxMembers + 1];
+    int* ndone;                     // members whose solve has ended (device counter)
+    int* all_done_host;             // mapped host flag set when ndone reaches n
+    EnsMember<T> m[kMaxMembers];
+};
+static_assert(sizeof(EnsTab<float>) < 32000, "ensemble table must fit in the kernel parameter space");
+constexpr int kFirstRowTile = 12, kNumEnsTiles = 5;
+
 struct SorTile { int tx, ty, tz; };   // tz = 0: k-marching column tile
 struct SorCfg { int tile; int kc; };   // tile < 0: two in-place half-sweep kernels
 extern const SorTile kSorTiles[];
 extern const int kNumSorTiles;
+// ensemble launchers: the batched sweep (les_sor.cu) and the batched estimate /
+// refinement (les_kernels.cu); one launch each covers every member
+SorTile ens_tile_shape(int t);
+int ens_rows_smem(int t);
+int launch_sor_ens(const EnsTab<float>& tab, int in, int zero, int ctas, cudaStream_t s);
+int launch_est_ens(const EnsTab<float>& tab, int dcur, const CondArgs& ca, cudaStream_t s);
+int launch_refine_ens(const EnsTab<float>& tab, int dcur, const CondArgs& ca, cudaStream_t s);
 template <typename T> int launch_sor_fused(const Geo<T>& g, const T* din, T* dout, const T* r, int zero_start,
                                            const Scalars* sc, SorCfg cfg, cudaStream_t s);
 
@@ -174,6 +218,23 @@ int launch_count_unknowns(const Dom& d, const uint8_t* flags, unsigned long long
 
 int max_reduce_blocks(const Dom& d);
 
+}  // namespace les
+
+struct les_s;
+namespace les {
+// ensemble support (les_api.cu): the members are ordinary domain handles
+int member_check(les_s* h, char* why, size_t n);          // 0 if h can join an ensemble
+void member_fill(les_s* h, EnsMember<float>& M, int ens_tile, int parity);
+int member_parity(const les_s* h);                        // which pressure buffer is current
+int member_begin(les_s* h, cudaStream_t s);               // clears the sticky non-convergence flag
+int member_check_every(const les_s* h);
+int member_max_sweeps(const les_s* h);
+cudaStream_t member_stream(const les_s* h);
+int member_prefix(les_s* h, cudaStream_t s);              // bondv1 .. rhs of the step, first residual
+int member_finish(les_s* h, cudaStream_t s);              // velnw, buffer flip, step counter
+int member_stats(les_s* h, les_stats_t* st);              // reads the scalars back; returns the status
+void member_set_dcur(les_s* h, int dcur);
+int* member_done_flag(les_s* h);                           // device address of the member's `done`
 }  // namespace les
 
 struct les_net_s;

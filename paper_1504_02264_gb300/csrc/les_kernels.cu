@@ -363,10 +363,8 @@ __device__ __forceinline__ void block_sum(double (&x)[NV]) {
 // Each block stores its partial sums; the last block to finish adds all the
 // partials in block order and returns true (with the totals in x on thread 0).
 template <int NV>
-__device__ bool grid_sum(double (&x)[NV], const Reduce& r) {
+__device__ bool grid_sum_at(double (&x)[NV], const Reduce& r, unsigned nb, unsigned b) {
     block_sum<NV>(x);
-    const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
-    const unsigned b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     __shared__ bool last;
     if (tid == 0) {
@@ -389,6 +387,12 @@ __device__ bool grid_sum(double (&x)[NV], const Reduce& r) {
     block_sum<NV>(x);
     if (tid == 0) *r.counter = 0u;
     return true;
+}
+
+template <int NV>
+__device__ bool grid_sum(double (&x)[NV], const Reduce& r) {
+    return grid_sum_at<NV>(x, r, gridDim.x * gridDim.y * gridDim.z,
+                           blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
 }
 
 // ---------------------------------------------------------------------------
@@ -605,15 +609,20 @@ int launch_sor_sweep(const Geo<T>& g, T* dl, const T* r, int zero_start, const S
 
 // Refinement: ph += d on the unknowns (own cell only, so in place).
 template <typename T>
-__global__ void k_accum(Geo<T> g, double* ph, const T* dl, const Scalars* sc, int gate) {
+__device__ __forceinline__ void accum_body(const Geo<T>& g, double* ph, const T* dl, int bx, int by, int bz) {
     const Dom& d = g.d;
-    if (gate && (sc->done || !sc->refine)) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
-    int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    int k = blockIdx.z + 1;
+    int i = bx * blockDim.x + threadIdx.x + 1;
+    int j = by * blockDim.y + threadIdx.y + 1;
+    int k = bz + 1;
     if (i > d.nx || j > d.ny) return;
     long long c = d.at(i, j, k);
     if (g.flags[c] & F_UNK) ph[c] += (double)dl[c];
+}
+
+template <typename T>
+__global__ void k_accum(Geo<T> g, double* ph, const T* dl, const Scalars* sc, int gate) {
+    if (gate && (sc->done || !sc->refine)) return;
+    accum_body<T>(g, ph, dl, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 template <typename T>
@@ -643,16 +652,17 @@ __device__ __forceinline__ void cell_of(const Dom& d, int q, int& i, int& j, int
 // r = (rhs - mean) - A ph formed in FP64 and stored in T; FP64 norms, the
 // true relative residual and stop test, the dz-weighted fluid mean of ph (for
 // the gauge) and the bookkeeping of the SOR loop in the last block.
+// block b of nb (grid-stride over the cells); returns, on thread 0 of the
+// last block, 1 if this residual ended the solve, else 0 (-1 elsewhere)
 template <typename T>
-__global__ void __launch_bounds__(256) k_residual64(Geo<T> g, const double* ph, const T* rhs, T* r, double vfluid,
-                                                    Reduce red, CondArgs ca) {
+__device__ __forceinline__ int residual64_body(const Geo<T>& g, const double* ph, const T* rhs, T* r,
+                                               double vfluid, const Reduce& red, const CondArgs& ca, unsigned b,
+                                               unsigned nb) {
     const Dom& d = g.d;
-    if (ca.gate == 1 && (red.sc->done || !red.sc->refine)) return;     // uniform over the grid
-    if (ca.gate == 2 && red.sc->done) return;
     const int n = d.nx * d.ny * d.nz;
     const double mean = red.sc->rhs_mean;
     double x[3] = {0.0, 0.0, 0.0};
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    for (int q = b * blockDim.x + threadIdx.x; q < n; q += nb * blockDim.x) {
         int i, j, k;
         cell_of(d, q, i, j, k);
         long long c = d.at(i, j, k);
@@ -680,7 +690,7 @@ __global__ void __launch_bounds__(256) k_residual64(Geo<T> g, const double* ph, 
         }
         if (f & F_FLUID) x[2] += g.dz64[k] * pc;
     }
-    if (grid_sum<3>(x, red)) {
+    if (grid_sum_at<3>(x, red, nb, b)) {
         if (threadIdx.x == 0 && threadIdx.y == 0) {
             Scalars* sc = red.sc;
             sc->res2 = x[0];
@@ -711,8 +721,18 @@ __global__ void __launch_bounds__(256) k_residual64(Geo<T> g, const double* ph, 
             }
             sc->done = done;
             if (ca.done_host) *(volatile int*)ca.done_host = done;
+            return done;
         }
     }
+    return -1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_residual64(Geo<T> g, const double* ph, const T* rhs, T* r, double vfluid,
+                                                    Reduce red, CondArgs ca) {
+    if (ca.gate == 1 && (red.sc->done || !red.sc->refine)) return;     // uniform over the grid
+    if (ca.gate == 2 && red.sc->done) return;
+    residual64_body<T>(g, ph, rhs, r, vfluid, red, ca, blockIdx.x, gridDim.x);
 }
 
 template <typename T>
@@ -728,15 +748,14 @@ int launch_residual64(const Geo<T>& g, const double* ph, const T* rhs, T* r, dou
 // this is the residual of the current iterate up to rounding.  It only decides
 // when to take the FP64 refinement, which makes the stop decision.
 template <typename T>
-__global__ void __launch_bounds__(256) k_sor_est(Geo<T> g, const T* dl, const T* r, T* rout, Reduce red,
-                                                 CondArgs ca) {
+__device__ __forceinline__ void sor_est_body(const Geo<T>& g, const T* dl, const T* r, T* rout, const Reduce& red,
+                                             const CondArgs& ca, int bx, int by, int bz, unsigned nb, unsigned b) {
     const Dom& d = g.d;
-    if (red.sc->done) return;      // uniform over the grid
     // a (32 x 8) column tile marching over a chunk of kEstChunk planes; the
     // cell index advances by one plane per step, neighbour offsets are 32-bit
-    const int i = blockIdx.x * 32 + threadIdx.x + 1;
-    const int j = blockIdx.y * 8 + threadIdx.y + 1;
-    const int kb = blockIdx.z * kEstChunk + 1, ke = min(kb + kEstChunk, d.nz + 1);
+    const int i = bx * 32 + threadIdx.x + 1;
+    const int j = by * 8 + threadIdx.y + 1;
+    const int kb = bz * kEstChunk + 1, ke = min(kb + kEstChunk, d.nz + 1);
     T acc = T(0);
     if (i <= d.nx && j <= d.ny) {
         const int pl = (int)d.plane;
@@ -764,7 +783,7 @@ __global__ void __launch_bounds__(256) k_sor_est(Geo<T> g, const T* dl, const T*
         }
     }
     double x[1] = {(double)acc};
-    if (grid_sum<1>(x, red)) {
+    if (grid_sum_at<1>(x, red, nb, b)) {
         if (threadIdx.x == 0 && threadIdx.y == 0) {
             Scalars* sc = red.sc;
             const double rhs2 = sc->rhs2;
@@ -778,6 +797,14 @@ __global__ void __launch_bounds__(256) k_sor_est(Geo<T> g, const T* dl, const T*
             sc->refine = need;
         }
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sor_est(Geo<T> g, const T* dl, const T* r, T* rout, Reduce red,
+                                                 CondArgs ca) {
+    if (red.sc->done) return;      // uniform over the grid
+    sor_est_body<T>(g, dl, r, rout, red, ca, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x * gridDim.y * gridDim.z,
+                    blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
 }
 
 template <typename T>
@@ -1048,6 +1075,66 @@ int launch_count_unknowns(const Dom& d, const uint8_t* flags, unsigned long long
 }
 
 int max_reduce_blocks(const Dom& d) { return ((d.nx + 31) / 32) * ((d.ny + 7) / 8) * d.nz; }
+
+// ---------------------------------------------------------------------------
+// ensembles: the estimate and the refinement of every member in one launch
+// each, block by block the same geometry as the member's own launch (so the
+// sums, the decisions and the iterates are bit-identical)
+
+__device__ __forceinline__ int ens_member(const int* beg, int n, int t) {
+    int m = 0;
+    while (m + 1 < n && t >= beg[m + 1]) ++m;
+    return m;
+}
+
+__global__ void __launch_bounds__(256) k_sor_est_ens(const __grid_constant__ EnsTab<float> tab, int dcur, CondArgs ca) {
+    const int t = blockIdx.x, m = ens_member(tab.ebeg, tab.n, t);
+    const EnsMember<float>& M = tab.m[m];
+    if (M.red.sc->done) return;
+    CondArgs c = ca;
+    c.tol = M.tol;
+    c.limit = M.limit;
+    const int lt = t - tab.ebeg[m], ex = M.egrid[0], ey = M.egrid[1];
+    sor_est_body<float>(M.g, M.dl[dcur], M.rr, nullptr, M.red, c, lt % ex, (lt / ex) % ey, lt / (ex * ey),
+                        ex * ey * M.egrid[2], lt);
+}
+
+__global__ void k_accum_ens(const __grid_constant__ EnsTab<float> tab, int dcur) {
+    const int t = blockIdx.x, m = ens_member(tab.abeg, tab.n, t);
+    const EnsMember<float>& M = tab.m[m];
+    if (M.red.sc->done || !M.red.sc->refine) return;
+    const int lt = t - tab.abeg[m], ax = M.agrid[0], ay = M.agrid[1];
+    accum_body<float>(M.g, M.ph, M.dl[dcur], lt % ax, (lt / ax) % ay, lt / (ax * ay));
+}
+
+__global__ void __launch_bounds__(256) k_residual64_ens(const __grid_constant__ EnsTab<float> tab, CondArgs ca) {
+    const int t = blockIdx.x, m = ens_member(tab.rbeg, tab.n, t);
+    const EnsMember<float>& M = tab.m[m];
+    if (ca.gate == 1 && (M.red.sc->done || !M.red.sc->refine)) return;
+    if (ca.gate == 2 && M.red.sc->done) return;
+    CondArgs c = ca;
+    c.tol = M.tol;
+    c.limit = M.limit;
+    c.done_host = nullptr;
+    const int done = residual64_body<float>(M.g, M.ph, M.rhs, M.rr, M.vfluid, M.red, c, t - tab.rbeg[m],
+                                            M.rblocks);
+    if (done == 1 && tab.ndone) {
+        // this member's solve ended: the last member to end raises the host flag
+        const int v = atomicAdd(tab.ndone, 1) + 1;
+        if (v == tab.n && tab.all_done_host) *(volatile int*)tab.all_done_host = 1;
+    }
+}
+
+int launch_est_ens(const EnsTab<float>& tab, int dcur, const CondArgs& ca, cudaStream_t s) {
+    k_sor_est_ens<<<tab.ebeg[tab.n], dim3(32, 8), 0, s>>>(tab, dcur, ca);
+    return 1;
+}
+
+int launch_refine_ens(const EnsTab<float>& tab, int dcur, const CondArgs& ca, cudaStream_t s) {
+    if (ca.mode != RES_INIT) k_accum_ens<<<tab.abeg[tab.n], dim3(32, 8), 0, s>>>(tab, dcur);
+    k_residual64_ens<<<tab.rbeg[tab.n], 256, 0, s>>>(tab, ca);
+    return ca.mode != RES_INIT ? 2 : 1;
+}
 
 #define LES_INSTANTIATE(T)                                                                              \
     template int launch_bc<T>(const Geo<T>&, T*, T*, T*, const double*, double, uint64_t,               \

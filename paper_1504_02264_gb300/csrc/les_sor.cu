@@ -13,6 +13,8 @@
 // black-old inputs as in the neighbouring CTA, so every CTA sees the same red
 // iterate and no inter-CTA synchronisation is needed.  The halo re-reads hit
 // L2; DRAM traffic per sweep is ~ d in, r in, flags in, d out = 13 B/cell.
+#include <type_traits>
+
 #include "les_internal.cuh"
 
 namespace les {
@@ -286,13 +288,13 @@ struct RowTile {
     }
 };
 
+// one 28 x BY x BZ tile (bx, by, bz) of the sweep; the caller has checked `done`
 template <typename T, int BY, int BZ>
-__global__ void __launch_bounds__(256)
-k_sor_rows(Geo<T> g, const T* __restrict__ din, T* __restrict__ dout, const T* __restrict__ r, int zero_arg,
-           const Scalars* __restrict__ sc) {
+__device__ __forceinline__ void sor_rows_tile(const Geo<T>& g, const T* __restrict__ din, T* __restrict__ dout,
+                                              const T* __restrict__ r, bool zero_start, int bx, int by, int bz,
+                                              unsigned char* smem_raw) {
     using RT = RowTile<T, BY, BZ>;
     constexpr int DX = RT::DX, DY = RT::DY, DZ = RT::DZ, RY = RT::RY, RZ = RT::RZ, BX = RT::BX;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T(*sD)[DY][DX] = reinterpret_cast<T(*)[DY][DX]>(smem_raw);
     T(*sR)[RY][32] = reinterpret_cast<T(*)[RY][32]>(smem_raw + sizeof(T) * DZ * DY * DX);
     T(*sCN)[64] = reinterpret_cast<T(*)[64]>(smem_raw + sizeof(T) * (DZ * DY * DX + RZ * RY * 32));
@@ -300,11 +302,9 @@ k_sor_rows(Geo<T> g, const T* __restrict__ din, T* __restrict__ dout, const T* _
     T* sCB = sCT + RZ;
     uint8_t(*sF)[RY][32] =
         reinterpret_cast<uint8_t(*)[RY][32]>(smem_raw + sizeof(T) * (DZ * DY * DX + RZ * RY * 32 + RZ * 64 + 2 * RZ));
-    if (sc->done) return;
     const Dom& d = g.d;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int i0 = 1 + blockIdx.x * BX, j0 = 1 + blockIdx.y * BY, k0 = 1 + blockIdx.z * BZ;
-    const bool zero_start = zero_arg == 1 || (zero_arg == 2 && sc->zflag);
+    const int i0 = 1 + bx * BX, j0 = 1 + by * BY, k0 = 1 + bz * BZ;
     const int px = d.px, py = d.py;
     // column offset of a lane (wrapped on a periodic axis), -1 outside the padded box
     auto col = [&](int i) -> int {
@@ -433,9 +433,70 @@ k_sor_rows(Geo<T> g, const T* __restrict__ din, T* __restrict__ dout, const T* _
 }
 
 template <typename T, int BY, int BZ>
+__global__ void __launch_bounds__(256)
+k_sor_rows(Geo<T> g, const T* __restrict__ din, T* __restrict__ dout, const T* __restrict__ r, int zero_arg,
+           const Scalars* __restrict__ sc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (sc->done) return;
+    const bool zero_start = zero_arg == 1 || (zero_arg == 2 && sc->zflag);
+    sor_rows_tile<T, BY, BZ>(g, din, dout, r, zero_start, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+}
+
+// The ensemble sweep: one persistent launch over the tiles of every member
+// (flattened in member order); each CTA walks its share of the list, skips
+// the tiles of members whose solve is done, and relaxes the others with the
+// same tile code as the single-domain launch (bit-identical iterates).
+template <typename T, int BY, int BZ>
+__global__ void __launch_bounds__(256) k_sor_rows_ens(const __grid_constant__ EnsTab<T> tab, int in, int zero_arg) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int total = tab.sbeg[tab.n];
+    int m = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        while (t >= tab.sbeg[m + 1]) ++m;
+        const EnsMember<T>& M = tab.m[m];
+        if (M.red.sc->done) continue;                     // uniform over the CTA
+        const bool zero_start = zero_arg == 1 || (zero_arg == 2 && M.red.sc->zflag);
+        const int lt = t - tab.sbeg[m], sx = M.sgrid[0], sy = M.sgrid[1];
+        sor_rows_tile<T, BY, BZ>(M.g, M.dl[in], M.dl[1 - in], M.rr, zero_start, lt % sx, (lt / sx) % sy,
+                                 lt / (sx * sy), smem_raw);
+        __syncthreads();                                  // shared tiles are reused by the next item
+    }
+}
+
+template <typename T, int BY, int BZ>
 static cudaError_t allow_rows() {
-    return cudaFuncSetAttribute(k_sor_rows<T, BY, BZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)RowTile<T, BY, BZ>::smem());
+    cudaError_t e = cudaFuncSetAttribute(k_sor_rows<T, BY, BZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)RowTile<T, BY, BZ>::smem());
+    if (e == cudaSuccess && std::is_same<T, float>::value)
+        e = cudaFuncSetAttribute(k_sor_rows_ens<T, BY, BZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)RowTile<T, BY, BZ>::smem());
+    return e;
+}
+
+template <int BY, int BZ>
+static void launch_rows_ens(const EnsTab<float>& tab, int in, int zero, int ctas, cudaStream_t s) {
+    k_sor_rows_ens<float, BY, BZ><<<ctas, 256, RowTile<float, BY, BZ>::smem(), s>>>(tab, in, zero);
+}
+
+int launch_sor_ens(const EnsTab<float>& tab, int in, int zero, int ctas, cudaStream_t s) {
+    switch (tab.tile) {
+        case 0: launch_rows_ens<8, 8>(tab, in, zero, ctas, s); break;
+        case 1: launch_rows_ens<4, 8>(tab, in, zero, ctas, s); break;
+        case 2: launch_rows_ens<8, 4>(tab, in, zero, ctas, s); break;
+        case 3: launch_rows_ens<16, 4>(tab, in, zero, ctas, s); break;
+        default: launch_rows_ens<4, 16>(tab, in, zero, ctas, s); break;
+    }
+    return 1;
+}
+
+int ens_rows_smem(int t) {
+    switch (t) {
+        case 0: return (int)RowTile<float, 8, 8>::smem();
+        case 1: return (int)RowTile<float, 4, 8>::smem();
+        case 2: return (int)RowTile<float, 8, 4>::smem();
+        case 3: return (int)RowTile<float, 16, 4>::smem();
+        default: return (int)RowTile<float, 4, 16>::smem();
+    }
 }
 
 template <typename T, int BY, int BZ>
@@ -481,6 +542,9 @@ const SorTile kSorTiles[] = {{32, 4, 0}, {32, 8, 0}, {64, 4, 0},  {64, 8, 0}, {1
                              {32, 8, 4}, {32, 4, 8}, {64, 4, 4},  {32, 8, 8}, {16, 8, 8}, {64, 8, 2},
                              {28, 8, 8}, {28, 4, 8}, {28, 8, 4}, {28, 16, 4}, {28, 4, 16}};
 const int kNumSorTiles = sizeof(kSorTiles) / sizeof(kSorTiles[0]);
+
+// row-tile shape of ensemble tile index t (the row tiles of kSorTiles)
+SorTile ens_tile_shape(int t) { return kSorTiles[kFirstRowTile + t]; }
 
 template <typename T>
 int launch_sor_fused(const Geo<T>& g, const T* din, T* dout, const T* r, int zero_start, const Scalars* sc,

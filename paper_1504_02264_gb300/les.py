@@ -86,6 +86,19 @@ def lib(build_if_missing: bool = False):
         L.les_set_state.argtypes = [vp, vp, ctypes.c_size_t]
         L.les_profiler_range.argtypes = [i32]
         L.les_residual_noalloc.argtypes = [ctypes.POINTER(les_grid_t), vp, vp, vp, vp, vp, vp]
+        L.les_ensemble_create.argtypes = [i32, vp, vp, vp, vp, ctypes.POINTER(vp)]
+        L.les_ensemble_destroy.argtypes = [vp]
+        L.les_ensemble_destroy.restype = None
+        L.les_ensemble_last_error.argtypes = [vp]
+        L.les_ensemble_last_error.restype = ctypes.c_char_p
+        L.les_ensemble_size.argtypes = [vp, ctypes.POINTER(i32)]
+        L.les_ensemble_member.argtypes = [vp, i32, ctypes.POINTER(vp)]
+        L.les_ensemble_step.argtypes = [vp, i32, vp]
+        L.les_ensemble_set_graph.argtypes = [vp, i32]
+        L.les_ensemble_set_tile.argtypes = [vp, i32, i32]
+        L.les_ensemble_get_tile.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        L.les_ensemble_autotune.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
+        L.les_ensemble_launches.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
         L.les_set_record.argtypes = [vp, i32]
         L.les_set_record_at.argtypes = [vp, i32]
         L.les_set_net_schedule.argtypes = [vp, i32]
@@ -111,7 +124,9 @@ def lib(build_if_missing: bool = False):
         L.les_autotune_sor.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
         L.les_set_timing.argtypes = [vp, i32]
         L.les_get_timing.argtypes = [vp, ctypes.POINTER(les_timing_t)]
-        for name in ("les_set_record", "les_set_record_at", "les_set_net_schedule", "les_set_warmstart",
+        for name in ("les_ensemble_create", "les_ensemble_size", "les_ensemble_member", "les_ensemble_step",
+                     "les_ensemble_set_graph", "les_ensemble_set_tile", "les_ensemble_get_tile",
+                     "les_ensemble_autotune", "les_ensemble_launches", "les_set_record", "les_set_record_at", "les_set_net_schedule", "les_set_warmstart",
                      "les_net_create", "les_net_num_params", "les_net_set_stride", "les_net_get_stride",
                      "les_net_get_params", "les_net_set_params", "les_net_forward", "les_net_gradient",
                      "les_net_train_step", "les_residual_noalloc", "les_profiler_range", "les_set_graph",
@@ -316,6 +331,89 @@ class Net:
         les_net_set_params(self.h, np.ascontiguousarray(p, np.float32))
 
 
+def _echeck(rc, e):
+    if rc < 0:
+        m = lib().les_ensemble_last_error(e)
+        raise LesError(rc, m.decode() if m else "")
+    return rc
+
+
+class Ensemble:
+    """Uneven domains stepped together (batched SOR launches over all members)."""
+
+    def __init__(self, scenes, stream="torch"):
+        n = len(scenes)
+        grids = (les_grid_t * n)()
+        self._keep = []
+        solid_p = (ctypes.c_void_p * n)()
+        inflow_p = (ctypes.c_void_p * n)()
+        for i, sc in enumerate(scenes):
+            g, dz, solid, inflow = grid_of(sc, LES_FP32)
+            grids[i] = g
+            self._keep += [dz, solid, inflow]
+            solid_p[i] = solid.ctypes.data
+            inflow_p[i] = inflow.ctypes.data
+        st = current_stream() if stream == "torch" else stream
+        h = ctypes.c_void_p()
+        rc = lib().les_ensemble_create(n, grids, solid_p, inflow_p, st, ctypes.byref(h))
+        if rc < 0:
+            raise LesError(rc, "les_ensemble_create failed")
+        self.h = h.value
+        self.n = n
+        self.members = []
+        for i, sc in enumerate(scenes):
+            mh = ctypes.c_void_p()
+            _echeck(lib().les_ensemble_member(self.h, i, ctypes.byref(mh)), self.h)
+            d = Domain(sc, handle=mh.value)
+            if sc.u0 is not None:
+                d.set_fields(sc.u0, sc.v0, sc.w0, sc.p0)
+            self.members.append(d)
+
+    def close(self):
+        if getattr(self, "h", None):
+            for d in self.members:
+                d.close()
+            lib().les_ensemble_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1):
+        st = (les_stats_t * self.n)()
+        rc = _echeck(lib().les_ensemble_step(self.h, n, st), self.h)
+        out = []
+        for i in range(self.n):
+            d = {f: getattr(st[i], f) for f, _ in les_stats_t._fields_}
+            d["rc"] = rc
+            out.append(d)
+        return out
+
+    def set_graph(self, enable=True):
+        _echeck(lib().les_ensemble_set_graph(self.h, 1 if enable else 0), self.h)
+
+    def set_tile(self, tile, ctas_per_sm=4):
+        _echeck(lib().les_ensemble_set_tile(self.h, tile, ctas_per_sm), self.h)
+
+    def tile(self):
+        t, c = ctypes.c_int32(), ctypes.c_int32()
+        _echeck(lib().les_ensemble_get_tile(self.h, ctypes.byref(t), ctypes.byref(c)), self.h)
+        return t.value, c.value
+
+    def autotune(self, sweeps=10):
+        ms = ctypes.c_double()
+        _echeck(lib().les_ensemble_autotune(self.h, sweeps, ctypes.byref(ms)), self.h)
+        return self.tile(), ms.value
+
+    def launches(self):
+        v = ctypes.c_int64()
+        _echeck(lib().les_ensemble_launches(self.h, ctypes.byref(v)), self.h)
+        return v.value
+
+
 def les_profiler_range(start):
     return _check(lib().les_profiler_range(1 if start else 0))
 
@@ -365,32 +463,43 @@ def current_stream():
     return None
 
 
+def grid_of(sc, precision=LES_FP32, **override):
+    """The les_grid_t of a scene (the returned dz array backs its dz pointer)."""
+    prm = sc.params()
+    prm.update(override)
+    dz = np.ascontiguousarray(sc.dz, dtype=np.float64)
+    g = les_grid_t(nx=prm["nx"], ny=prm["ny"], nz=prm["nz"], bc_x=prm["bc_x"], bc_y=prm["bc_y"],
+                   bc_z=prm["bc_z"], dx=prm["dx"], dy=prm["dy"],
+                   dz=dz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                   dt=prm["dt"], cs=prm["cs"], nu=prm["nu"], omega=prm["omega"], tol=prm["tol"],
+                   max_sweeps=prm["max_sweeps"], check_every=prm["check_every"],
+                   fixed_sweeps=prm["fixed_sweeps"], precision=precision, turb=prm["turb"],
+                   seed=prm["seed"])
+    solid = np.ascontiguousarray(sc.solid, dtype=np.uint8)
+    inflow = np.ascontiguousarray(sc.inflow_u, dtype=np.float64)
+    return g, dz, solid, inflow
+
+
 class Domain:
     """One LES domain on the GPU, built from a ``scene.Scene``."""
 
-    def __init__(self, sc, precision=LES_FP32, stream="torch", **override):
-        prm = sc.params()
-        prm.update(override)
-        self.nx, self.ny, self.nz = prm["nx"], prm["ny"], prm["nz"]
+    def __init__(self, sc, precision=LES_FP32, stream="torch", handle=None, **override):
+        g, self._dz, solid, inflow = grid_of(sc, precision, **override)
+        self.nx, self.ny, self.nz = g.nx, g.ny, g.nz
         self.dtype = np.float64 if precision == LES_FP64 else np.float32
-        self._dz = np.ascontiguousarray(sc.dz, dtype=np.float64)
-        g = les_grid_t(nx=prm["nx"], ny=prm["ny"], nz=prm["nz"], bc_x=prm["bc_x"], bc_y=prm["bc_y"],
-                       bc_z=prm["bc_z"], dx=prm["dx"], dy=prm["dy"],
-                       dz=self._dz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                       dt=prm["dt"], cs=prm["cs"], nu=prm["nu"], omega=prm["omega"], tol=prm["tol"],
-                       max_sweeps=prm["max_sweeps"], check_every=prm["check_every"],
-                       fixed_sweeps=prm["fixed_sweeps"], precision=precision, turb=prm["turb"],
-                       seed=prm["seed"])
-        solid = np.ascontiguousarray(sc.solid, dtype=np.uint8)
-        inflow = np.ascontiguousarray(sc.inflow_u, dtype=np.float64)
-        st = current_stream() if stream == "torch" else stream
-        self.h = les_create(g, solid, inflow, st)
-        if sc.u0 is not None:
+        self._owned = handle is None
+        if handle is None:
+            st = current_stream() if stream == "torch" else stream
+            self.h = les_create(g, solid, inflow, st)
+        else:
+            self.h = handle
+        if sc.u0 is not None and handle is None:
             self.set_fields(sc.u0, sc.v0, sc.w0, sc.p0)
 
     def close(self):
         if getattr(self, "h", None):
-            les_destroy(self.h)
+            if self._owned:
+                les_destroy(self.h)
             self.h = None
 
     def __del__(self):

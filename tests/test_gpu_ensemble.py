@@ -1,0 +1,111 @@
+"""GPU tests of ensembles: uneven domains stepped together with batched SOR
+launches must evolve every member bit-identically to the same domain stepped
+alone with the same row tile, in graph and host-loop execution, and every
+member must end every step at its own tolerance."""
+
+import numpy as np
+import pytest
+
+from paper_1504_02264_gb300 import scene
+
+pytestmark = pytest.mark.gpu
+
+les = pytest.importorskip("paper_1504_02264_gb300.les")
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    les.lib()
+    yield
+
+
+def city(nx, ny, nz, seed, periodic_y=False, **kw):
+    rng = np.random.default_rng(seed)
+    solid = np.zeros((nz, ny, nx), np.uint8)
+    for _ in range(4):
+        x0 = int(rng.integers(6, nx - 10))
+        y0 = int(rng.integers(1, ny - 7))
+        h = int(rng.integers(2, nz - 2))
+        solid[:h, y0:y0 + 5, x0:x0 + 6] = 1
+    bc = (scene.BC_INOUT, scene.BC_PERIODIC if periodic_y else scene.BC_FREESLIP, scene.BC_WALL)
+    ustar = float(rng.uniform(0.2, 0.6))
+    z0 = float(rng.uniform(0.05, 0.5))
+    dz = scene.stretched_dz(nz)
+    inflow = scene.log_law(scene.centre_heights(dz), ustar, z0)
+    params = dict(turb=0.1, seed=seed, fixed_sweeps=0, tol=1e-6, max_sweeps=20000, check_every=10)
+    params.update(kw)
+    return scene.box_scene(nx, ny, nz, dz=dz, solid=solid, bc=bc, inflow=inflow, **params)
+
+
+def scenes():
+    return [city(40, 24, 12, 1), city(33, 22, 10, 2), city(48, 32, 16, 3, periodic_y=True), city(29, 40, 14, 4)]
+
+
+@pytest.mark.parametrize("tile", [0, 3])
+def test_members_match_single_domains(tile):
+    scs = scenes()
+    ens = les.Ensemble(scs)
+    ens.set_tile(tile, 4)
+    singles = []
+    for sc in scs:
+        d = les.Domain(sc)
+        d.set_sor_config(12 + tile, 0)
+        singles.append(d)
+    for _ in range(3):
+        est = ens.step()
+        sst = [d.step() for d in singles]
+        for a, b in zip(est, sst):
+            assert a["rc"] == 0 and b["rc"] == 0
+            assert a["sweeps"] == b["sweeps"], (a, b)
+            assert a["rel_residual"] <= 1e-6
+    assert len({s["sweeps"] for s in est}) > 1          # members stop at their own sweep counts
+    for m, d in zip(ens.members, singles):
+        for fa, fb in zip(m.fields(), d.fields()):
+            assert np.array_equal(fa, fb)
+        d.close()
+    ens.close()
+
+
+def test_graph_matches_host_loop():
+    scs = scenes()
+    out = []
+    for graph in (True, False):
+        ens = les.Ensemble(scs)
+        ens.set_graph(graph)
+        for _ in range(2):
+            st = ens.step()
+        out.append(([m.fields() for m in ens.members], [s["sweeps"] for s in st]))
+        ens.close()
+    assert out[0][1] == out[1][1]
+    for fa, fb in zip(out[0][0], out[1][0]):
+        for a, b in zip(fa, fb):
+            assert np.array_equal(a, b)
+
+
+def test_autotune_and_converge():
+    scs = scenes()
+    ens = les.Ensemble(scs)
+    (tile, ctas), ms = ens.autotune(sweeps=5)
+    assert 0 <= tile < 5 and ctas >= 1 and ms > 0
+    st = ens.step(2)
+    assert all(s["rc"] == 0 and s["rel_residual"] <= 1e-6 for s in st)
+    assert ens.launches() > 0
+    ens.close()
+
+
+def test_ensemble_rejects_bad_use():
+    scs = scenes()
+    bad = scs[:1] + [city(30, 20, 10, 9, check_every=20)]
+    with pytest.raises(les.LesError):
+        les.Ensemble(bad)
+    ens = les.Ensemble(scs[:2])
+    ens.step()
+    ens.members[0].step()               # a member stepped on its own
+    with pytest.raises(les.LesError):
+        ens.step()
+    with pytest.raises(les.LesError):
+        ens.set_tile(7)
+    ens.close()
