@@ -17,6 +17,39 @@ import time
 from . import les, scene
 
 
+def run_ensemble(a):
+    """Batched ensemble of uneven random cities (96^2-256^2 x 64-128)."""
+    scs = scene.ensemble_scenes(seed=a.seed, n=a.members)
+    for sc in scs:
+        sc.max_sweeps = a.max_sweeps
+    cells = sum(sc.ncells for sc in scs)
+    ens = les.Ensemble(scs, stream=None)
+    ens.set_graph(bool(a.graph))
+    for _ in range(a.warmup):
+        ens.step(1)
+    tune = ens.autotune(sweeps=10) if a.autotune else None
+    if a.range:
+        les.les_profiler_range(1)
+    t0 = time.perf_counter()
+    sweeps, worst, rcs = [], 0.0, []
+    for _ in range(a.steps):
+        st = ens.step(1)
+        sweeps.append([s["sweeps"] for s in st])
+        worst = max(worst, max(s["rel_residual"] for s in st))
+        rcs.append(st[0]["rc"])
+    t1 = time.perf_counter()
+    if a.range:
+        les.les_profiler_range(0)
+    ms = (t1 - t0) * 1e3 / a.steps
+    print(json.dumps({"workload": "ensemble", "members": a.members, "cells": cells, "steps": a.steps,
+                      "ms_per_step": ms, "mcell_steps_per_s": cells / (ms * 1e-3) / 1e6,
+                      "max_sweeps_per_step": [max(x) for x in sweeps],
+                      "mean_member_sweeps": [sum(x) / len(x) for x in sweeps], "max_rel_residual": worst,
+                      "rc": rcs, "tile": ens.tile(), "autotune": tune, "graph": a.graph,
+                      "shapes": [[sc.nx, sc.ny, sc.nz] for sc in scs]}))
+    ens.close()
+
+
 def make(workload: str, seed: int):
     if workload == "lattice":
         return scene.lattice_scene(seed)
@@ -29,7 +62,9 @@ def make(workload: str, seed: int):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="random", choices=["lattice", "random", "large"])
+    ap.add_argument("--workload", default="random", choices=["lattice", "random", "large", "ensemble"])
+    ap.add_argument("--members", type=int, default=32, help="ensemble members")
+    ap.add_argument("--max-sweeps", type=int, default=60000, help="ensemble members' sweep budget")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--steps", type=int, default=2)
@@ -42,6 +77,8 @@ def main():
     ap.add_argument("--net", default=None, help="trained warm-start network (.npz: params, stride)")
     ap.add_argument("--net-every", type=int, default=0, help="network correction every n sweeps")
     a = ap.parse_args()
+    if a.workload == "ensemble":
+        return run_ensemble(a)
     sc = make(a.workload, a.seed)
     d = les.Domain(sc, precision=les.LES_FP64 if a.fp64 else les.LES_FP32, stream=None)
     d.set_graph(bool(a.graph))
