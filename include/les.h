@@ -373,6 +373,12 @@ int les_ensemble_set_tile(les_ensemble e, int32_t tile, int32_t ctas_per_sm);
 int les_ensemble_get_tile(les_ensemble e, int32_t* tile, int32_t* ctas);
 int les_ensemble_autotune(les_ensemble e, int32_t sweeps, double* best_ms_per_sweep);
 int les_ensemble_launches(les_ensemble e, int64_t* launches);
+/* les_ensemble_set_warmstart: every member applies the learned correction
+ * `net` at the start of its solve and every `every_sweeps` sweeps inside it
+ * (even, dividing each member's max_sweeps; the batch size of the ensemble's
+ * loop becomes every_sweeps); net = NULL returns to the previous-step start.
+ * The members share the network (its workspace is sized for the largest). */
+int les_ensemble_set_warmstart(les_ensemble e, les_net net, int32_t every_sweeps);
 
 /* Bracket a region for a profiler started with capture off
  * (cudaProfilerStart when start != 0, cudaProfilerStop otherwise). */

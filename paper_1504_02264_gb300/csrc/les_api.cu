@@ -1378,6 +1378,7 @@ void member_fill(les_s* h, EnsMember<float>& M, int ens_tile, int parity) {
     M.agrid[1] = (d.ny + 7) / 8;
     M.agrid[2] = d.nz;
     M.rblocks = reduce_blocks(d);
+    M.rcur = net_in_loop(h) ? (float*)h->rcur : nullptr;
 }
 
 int member_check_every(const les_s* h) { return h->g.check_every; }
@@ -1410,6 +1411,25 @@ int member_stats(les_s* h, les_stats_t* st) {
 }
 
 void member_set_dcur(les_s* h, int dcur) { h->dcur = dcur; }
+bool member_net_on(const les_s* h) { return net_in_loop(h); }
+int member_net_every(const les_s* h) { return h->net_every; }
+void* member_rcur(les_s* h) { return net_in_loop(h) ? h->rcur : nullptr; }
+int member_net_prepare(les_s* h) {
+    if (!net_in_loop(h)) return LES_OK;
+    return net_prepare(h->net, h->d, &h->net_gen);
+}
+long long member_net_generation(const les_s* h) { return net_in_loop(h) ? net_generation(h->net) : -1; }
+int member_net_start(les_s* h, cudaStream_t s) {
+    if (!(h->warm == LES_WARM_NET && h->net && h->prec == LES_FP32)) return LES_OK;
+    Geo<float> g = geo<float>(h);
+    return net_correct<float>(h, g, s);
+}
+int member_net_loop(les_s* h, cudaStream_t s) {
+    if (!net_in_loop(h)) return LES_OK;
+    Geo<float> g = geo<float>(h);
+    h->dcur = 0;
+    return net_correct_loop<float>(h, g, s, true);
+}
 int member_parity(const les_s* h) { return h->cur; }
 int member_begin(les_s* h, cudaStream_t s) {
     CK(cudaMemsetAsync(&h->sc->noconv_any, 0, sizeof(int), s));

@@ -34,6 +34,9 @@ struct les_ensemble_s {
     int tile = 0;                                // ensemble row tile (0 .. kNumEnsTiles-1)
     int ctas = 0;                                // CTAs of the persistent sweep launch
     int check_every = 10;
+    int cycle = 10;                              // sweeps per batch (check_every, or the network's interval)
+    bool net = false;                            // members apply the learned correction in the loop
+    std::vector<long long> net_gen;              // network workspace generation at capture
     int max_sweeps = 0;                          // largest member budget
     int cur = 0;                                 // parity of the members' pressure buffers
     int* ndone = nullptr;                        // device counter of members whose solve ended
@@ -103,22 +106,35 @@ CondArgs eargs(const les_ensemble_s* e, int mode, int n, int gate) {
     return ca;
 }
 
-// one chunk: kEnsChunkBatches x (check_every sweeps, estimate, gated refinement)
+// one chunk: kEnsChunkBatches x (cycle sweeps, estimate, gated refinement
+// [, each member's network correction, done-gated])
 int launch_chunk(les_ensemble_s* e, const EnsTab<float>& T, cudaStream_t s) {
     int dcur = 0;
     for (int b = 0; b < kEnsChunkBatches; ++b) {
-        for (int q = 0; q < e->check_every; ++q) {
+        for (int q = 0; q < e->cycle; ++q) {
             e->launches += launch_sor_ens(T, dcur, q == 0 ? 2 : 0, e->ctas, s);
             dcur = 1 - dcur;
         }
-        e->launches += launch_est_ens(T, dcur, eargs(e, RES_LOOP, e->check_every, 1), s);
-        e->launches += launch_refine_ens(T, dcur, eargs(e, RES_LOOP, e->check_every, 1), s);
+        e->launches += launch_est_ens(T, dcur, eargs(e, RES_LOOP, e->cycle, 1), s);
+        e->launches += launch_refine_ens(T, dcur, eargs(e, RES_LOOP, e->cycle, 1), s);
+        if (e->net)
+            for (les_handle h : e->mem) {
+                int rc = member_net_loop(h, s);
+                if (rc) return efail(e, rc, "member network correction: %s", les_last_error(h));
+            }
     }
     ECK(cudaGetLastError());
     return LES_OK;
 }
 
 int build_chunk(les_ensemble_s* e, int par) {
+    if (e->net)
+        for (size_t i = 0; i < e->mem.size(); ++i) {
+            // network workspaces are allocated before the capture
+            int rc = member_net_prepare(e->mem[i]);
+            if (rc) return efail(e, rc, "member network workspace: %s", les_last_error(e->mem[i]));
+            e->net_gen[i] = member_net_generation(e->mem[i]);
+        }
     ECK(cudaStreamBeginCapture(e->cap, cudaStreamCaptureModeRelaxed));
     const long long l0 = e->launches;
     int rc = launch_chunk(e, *e->tab[par], e->cap);
@@ -220,6 +236,8 @@ int les_ensemble_create(int32_t n, const les_grid_t* grids, const uint8_t* const
         return rc;
     }
     *e->all_done_host = 0;
+    e->cycle = e->check_every;
+    e->net_gen.assign(n, -1);
     e->tile = 0;
     fill_tables(e);
     choose_ctas(e, 4);
@@ -284,10 +302,13 @@ int les_ensemble_step(les_ensemble e, int32_t nsteps, les_stats_t* stats) {
         int rc = member_begin(h, s);
         if (rc) return efail(e, rc, "member: %s", les_last_error(h));
     }
-    const int per_chunk = kEnsChunkBatches * e->check_every;
+    const int per_chunk = kEnsChunkBatches * e->cycle;
     const int max_chunks = (e->max_sweeps + per_chunk - 1) / per_chunk + 1;
     for (int st = 0; st < nsteps; ++st) {
         const int par = e->cur;
+        if (e->net)
+            for (size_t i = 0; i < e->mem.size(); ++i)
+                if (member_net_generation(e->mem[i]) != e->net_gen[i]) invalidate(e);
         if (e->use_graph && !e->graph_ok[par]) {
             if (build_chunk(e, par)) {
                 e->use_graph = false;      // the same launches from the host from now on
@@ -303,10 +324,15 @@ int les_ensemble_step(les_ensemble e, int32_t nsteps, les_stats_t* stats) {
         e->launches += 6 * e->n;
         const EnsTab<float>& T = *e->tab[par];
         e->launches += launch_refine_ens(T, 0, eargs(e, RES_INIT, 0, 0), s);
+        if (e->net)
+            for (les_handle h : e->mem) {
+                int rc = member_net_start(h, s);
+                if (rc) return efail(e, rc, "member network start: %s", les_last_error(h));
+            }
         for (int c = 0; c < max_chunks; ++c) {
             if (e->use_graph) {
                 ECK(cudaGraphLaunch(e->chunk[par], s));
-                e->launches += kEnsChunkBatches * (e->check_every + 3);
+                e->launches += kEnsChunkBatches * (e->cycle + 3 + (e->net ? 22 * e->n : 0));
             } else {
                 int rc = launch_chunk(e, T, s);
                 if (rc) return rc;
@@ -385,6 +411,26 @@ int les_ensemble_autotune(les_ensemble e, int32_t sweeps, double* best_ms_per_sw
     choose_ctas(e, best_per_sm);
     invalidate(e);
     if (best_ms_per_sweep) *best_ms_per_sweep = best;
+    return LES_OK;
+}
+
+int les_ensemble_set_warmstart(les_ensemble e, les_net net, int32_t every_sweeps) {
+    if (!e) return LES_EINVAL;
+    if (net && (every_sweeps < 2 || every_sweeps % 2))
+        return efail(e, LES_EINVAL, "every_sweeps must be even and >= 2");
+    for (les_handle h : e->mem)
+        if (net && member_max_sweeps(h) % every_sweeps)
+            return efail(e, LES_EINVAL, "every_sweeps must divide each member's max_sweeps");
+    for (les_handle h : e->mem) {
+        int rc = net ? les_set_warmstart(h, LES_WARM_NET, net) : les_set_warmstart(h, LES_WARM_PREV, nullptr);
+        if (!rc) rc = les_set_net_schedule(h, net ? every_sweeps : 0);
+        if (rc) return efail(e, rc, "member: %s", les_last_error(h));
+    }
+    e->net = net != nullptr;
+    e->cycle = net ? every_sweeps : e->check_every;
+    e->net_gen.assign(e->mem.size(), -1);
+    fill_tables(e);
+    invalidate(e);
     return LES_OK;
 }
 

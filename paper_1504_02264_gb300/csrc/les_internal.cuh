@@ -161,6 +161,7 @@ struct EnsMember {
     int egrid[3];           // estimate blocks
     int agrid[3];           // accumulate blocks (32 x 8 threads, one plane per block)
     int rblocks;            // residual blocks (grid-stride)
+    T* rcur;                // residual copy for the network correction (null without one)
 };
 template <typename T>
 struct EnsTab {
@@ -235,6 +236,13 @@ int member_finish(les_s* h, cudaStream_t s);              // velnw, buffer flip,
 int member_stats(les_s* h, les_stats_t* st);              // reads the scalars back; returns the status
 void member_set_dcur(les_s* h, int dcur);
 int* member_done_flag(les_s* h);                           // device address of the member's `done`
+// the learned correction of a member (set with les_set_warmstart / les_set_net_schedule)
+bool member_net_on(const les_s* h);                        // network inside the solve loop
+int member_net_every(const les_s* h);
+int member_net_prepare(les_s* h);                          // workspace, before a capture
+long long member_net_generation(const les_s* h);
+int member_net_start(les_s* h, cudaStream_t s);           // step at the start of the solve
+int member_net_loop(les_s* h, cudaStream_t s);            // step inside the loop (done-gated)
 }  // namespace les
 
 struct les_net_s;

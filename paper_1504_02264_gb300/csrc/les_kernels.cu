@@ -1095,7 +1095,7 @@ __global__ void __launch_bounds__(256) k_sor_est_ens(const __grid_constant__ Ens
     c.tol = M.tol;
     c.limit = M.limit;
     const int lt = t - tab.ebeg[m], ex = M.egrid[0], ey = M.egrid[1];
-    sor_est_body<float>(M.g, M.dl[dcur], M.rr, nullptr, M.red, c, lt % ex, (lt / ex) % ey, lt / (ex * ey),
+    sor_est_body<float>(M.g, M.dl[dcur], M.rr, M.rcur, M.red, c, lt % ex, (lt / ex) % ey, lt / (ex * ey),
                         ex * ey * M.egrid[2], lt);
 }
 

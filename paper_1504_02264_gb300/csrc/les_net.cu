@@ -53,13 +53,18 @@ double normal_at(uint64_t seed, uint64_t c) {
     return std::sqrt(-2.0 * std::log(u(2 * c))) * std::cos(6.283185307179586 * u(2 * c + 1));
 }
 
-// per-sample RMS over the mask: out[b] = sqrt(sum mask*a^2 / sum mask)
-__global__ void k_rms(const float* a, const float* mask, size_t n, double* out, const int* gate) {
+// per-sample RMS over the mask, rms = sqrt(sum mask*a^2 / sum mask), in a
+// fixed summation order (the result must not depend on scheduling): each
+// block writes its two partial sums to part[2*block], k_rms_final adds the
+// partials in block order into out[0] (rms) and out[1] (sum of the mask)
+constexpr int kRmsBlocks = 256;
+__global__ void __launch_bounds__(256) k_rms(const float* a, const float* mask, size_t n, double* part,
+                                             const int* gate) {
     if (gate && *(volatile const int*)gate) return;
-    const size_t base = (size_t)blockIdx.y * n;
+    __shared__ double sh[2][8];
     double s = 0.0, m = 0.0;
     for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
-        const double v = a[base + q], w = mask[base + q];
+        const double v = a[q], w = mask[q];
         s += w * v * v;
         m += w;
     }
@@ -67,18 +72,32 @@ __global__ void k_rms(const float* a, const float* mask, size_t n, double* out, 
         s += __shfl_down_sync(0xffffffffu, s, o);
         m += __shfl_down_sync(0xffffffffu, m, o);
     }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&out[2 * blockIdx.y], s);
-        atomicAdd(&out[2 * blockIdx.y + 1], m);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh[0][warp] = s;
+        sh[1][warp] = m;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ts = 0.0, tm = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            ts += sh[0][w];
+            tm += sh[1][w];
+        }
+        part[2 * blockIdx.x] = ts;
+        part[2 * blockIdx.x + 1] = tm;
     }
 }
-__global__ void k_rms_final(double* acc, int b, const int* gate) {
+__global__ void k_rms_final(const double* part, int nblocks, double* out, const int* gate) {
     if (gate && *(volatile const int*)gate) return;
-    const int q = threadIdx.x;
-    if (q < b) {
-        const double m = acc[2 * q + 1];
-        acc[2 * q] = m > 0.0 ? sqrt(acc[2 * q] / m) : 0.0;
+    if (threadIdx.x != 0) return;
+    double s = 0.0, m = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        s += part[2 * b];
+        m += part[2 * b + 1];
     }
+    out[0] = m > 0.0 ? sqrt(s / m) : 0.0;
+    out[1] = m;
 }
 // dense input: channel 0 = r / scale, channel 1 = mask
 __global__ void k_pack_dense(const float* r, const float* mask, const double* scale, __nv_bfloat16* xin, size_t n,
@@ -120,7 +139,7 @@ struct les_net_s {
     float *y = nullptr, *gy = nullptr, *mask = nullptr, *tn = nullptr;
     int stride = 1;                     // the network runs on the grid coarsened stride times per axis
     float *rc = nullptr, *mc = nullptr, *tc = nullptr;     // pooled sample (coarse level 0)
-    double* dscal = nullptr;            // [0..2B): per-sample rms and mask counts, [62]: loss
+    double* dscal = nullptr;            // [0,1] rms / mask sum of r, [2,3] of t, [62] loss, [64..) partials
     long long ws_gen = 0;               // bumped whenever the workspace is reallocated
     char err[256] = {0};
 };
@@ -214,7 +233,7 @@ int ensure_ws(les_net_s* n, const Level& L0) {
     if ((rc = get(vol(0), sizeof(float), (void**)&n->rc))) return rc;
     if ((rc = get(vol(0), sizeof(float), (void**)&n->mc))) return rc;
     if ((rc = get(vol(0), sizeof(float), (void**)&n->tc))) return rc;
-    if ((rc = get(64, sizeof(double), (void**)&n->dscal))) return rc;
+    if ((rc = get(64 + 4 * kRmsBlocks, sizeof(double), (void**)&n->dscal))) return rc;
     for (int l = 0; l < 4; ++l) n->cap[l] = want[l];
     n->cap_v0 = want[0];
     n->ws_gen += 1;
@@ -298,11 +317,14 @@ int pack_sample(les_net_s* n, const Level& L0, const float* r, const float* mask
                 const int* gate = nullptr) {
     const size_t v = L0.v();
     cudaStream_t s = n->stream;
-    NCK(cudaMemsetAsync(n->dscal, 0, 4 * sizeof(double), s));
-    const unsigned blocks = (unsigned)((v + 255) / 256 < 1024 ? (v + 255) / 256 : 1024);
-    k_rms<<<dim3(blocks, 1), 256, 0, s>>>(r, mask, v, n->dscal, gate);
-    if (t) k_rms<<<dim3(blocks, 1), 256, 0, s>>>(t, mask, v, n->dscal + 2, gate);
-    k_rms_final<<<1, 32, 0, s>>>(n->dscal, t ? 2 : 1, gate);
+    const int blocks = (int)((v + 255) / 256 < (size_t)kRmsBlocks ? (v + 255) / 256 : kRmsBlocks);
+    double* part = n->dscal + 64;
+    k_rms<<<blocks, 256, 0, s>>>(r, mask, v, part, gate);
+    k_rms_final<<<1, 32, 0, s>>>(part, blocks, n->dscal, gate);
+    if (t) {
+        k_rms<<<blocks, 256, 0, s>>>(t, mask, v, part + 2 * kRmsBlocks, gate);
+        k_rms_final<<<1, 32, 0, s>>>(part + 2 * kRmsBlocks, blocks, n->dscal + 2, gate);
+    }
     if (mask != n->mask) NCK(cudaMemcpyAsync(n->mask, mask, v * sizeof(float), cudaMemcpyDeviceToDevice, s));
     k_pack_dense<<<(unsigned)((v + 255) / 256), 256, 0, s>>>(r, n->mask, n->dscal, n->xin, v, gate);
     if (t) k_scale<<<(unsigned)((v + 255) / 256), 256, 0, s>>>(t, n->dscal + 2, n->tn, v);
@@ -388,7 +410,7 @@ int net_predict(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t
     n->stream = keep;
     return rc;
 }
-int net_launches(const les_net_s* n) { return 2 + 3 + 15 + 1; }     // pool, rms + pack, network, prolongation
+int net_launches(const les_net_s*) { return 1 + 3 + 15 + 1; }     // pool, rms + pack, network, prolongation
 }  // namespace les
 
 extern "C" {

@@ -99,6 +99,7 @@ def lib(build_if_missing: bool = False):
         L.les_ensemble_get_tile.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
         L.les_ensemble_autotune.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
         L.les_ensemble_launches.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+        L.les_ensemble_set_warmstart.argtypes = [vp, vp, i32]
         L.les_set_record.argtypes = [vp, i32]
         L.les_set_record_at.argtypes = [vp, i32]
         L.les_set_net_schedule.argtypes = [vp, i32]
@@ -126,7 +127,7 @@ def lib(build_if_missing: bool = False):
         L.les_get_timing.argtypes = [vp, ctypes.POINTER(les_timing_t)]
         for name in ("les_ensemble_create", "les_ensemble_size", "les_ensemble_member", "les_ensemble_step",
                      "les_ensemble_set_graph", "les_ensemble_set_tile", "les_ensemble_get_tile",
-                     "les_ensemble_autotune", "les_ensemble_launches", "les_set_record", "les_set_record_at", "les_set_net_schedule", "les_set_warmstart",
+                     "les_ensemble_autotune", "les_ensemble_launches", "les_ensemble_set_warmstart", "les_set_record", "les_set_record_at", "les_set_net_schedule", "les_set_warmstart",
                      "les_net_create", "les_net_num_params", "les_net_set_stride", "les_net_get_stride",
                      "les_net_get_params", "les_net_set_params", "les_net_forward", "les_net_gradient",
                      "les_net_train_step", "les_residual_noalloc", "les_profiler_range", "les_set_graph",
@@ -412,6 +413,12 @@ class Ensemble:
         v = ctypes.c_int64()
         _echeck(lib().les_ensemble_launches(self.h, ctypes.byref(v)), self.h)
         return v.value
+
+    def set_warmstart(self, net=None, every_sweeps=10):
+        """Learned correction in every member's solve (net None: previous-step start)."""
+        _echeck(lib().les_ensemble_set_warmstart(self.h, net.h if net is not None else None, every_sweeps),
+                self.h)
+        self._net = net
 
 
 def les_profiler_range(start):

@@ -25,6 +25,13 @@ def run_ensemble(a):
     cells = sum(sc.ncells for sc in scs)
     ens = les.Ensemble(scs, stream=None)
     ens.set_graph(bool(a.graph))
+    net = None
+    if a.net:
+        import numpy as np
+        z = np.load(a.net)
+        net = les.Net(seed=0, stream=None, stride=int(z["stride"]))
+        net.set_params(z["params"])
+        ens.set_warmstart(net, a.net_every)
     for _ in range(a.warmup):
         ens.step(1)
     tune = ens.autotune(sweeps=10) if a.autotune else None
@@ -45,7 +52,8 @@ def run_ensemble(a):
                       "ms_per_step": ms, "mcell_steps_per_s": cells / (ms * 1e-3) / 1e6,
                       "max_sweeps_per_step": [max(x) for x in sweeps],
                       "mean_member_sweeps": [sum(x) / len(x) for x in sweeps], "max_rel_residual": worst,
-                      "rc": rcs, "tile": ens.tile(), "autotune": tune, "graph": a.graph,
+                      "rc": rcs, "tile": ens.tile(), "autotune": tune, "graph": a.graph, "net": a.net,
+                      "net_every": a.net_every if a.net else None,
                       "shapes": [[sc.nx, sc.ny, sc.nz] for sc in scs]}))
     ens.close()
 

@@ -109,3 +109,34 @@ def test_ensemble_rejects_bad_use():
     with pytest.raises(les.LesError):
         ens.set_tile(7)
     ens.close()
+
+
+def test_members_match_single_domains_with_learned_correction():
+    """Ensemble and single domains with the trained network every 10 sweeps:
+    bit-identical members (the network inference is deterministic)."""
+    import os
+    from paper_1504_02264_gb300 import train
+    net = train.load(os.path.join(os.path.dirname(les.__file__), "weights", "warmstart_s4.npz"))
+    scs = scenes()
+    ens = les.Ensemble(scs)
+    ens.set_tile(0, 4)
+    ens.set_warmstart(net, 10)
+    singles = []
+    for sc in scs:
+        d = les.Domain(sc)
+        d.set_sor_config(12, 0)
+        d.set_warmstart(net)
+        d.set_net_schedule(10)
+        singles.append(d)
+    for _ in range(2):
+        est = ens.step()
+        sst = [d.step() for d in singles]
+        for a, b in zip(est, sst):
+            assert a["rc"] == 0 and a["rel_residual"] <= 1e-6
+            assert a["sweeps"] == b["sweeps"], (a, b)
+    for m, d in zip(ens.members, singles):
+        for fa, fb in zip(m.fields(), d.fields()):
+            assert np.array_equal(fa, fb)
+        d.close()
+    ens.close()
+    net.close()
