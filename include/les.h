@@ -380,6 +380,15 @@ int les_ensemble_launches(les_ensemble e, int64_t* launches);
  * The members share the network (its workspace is sized for the largest). */
 int les_ensemble_set_warmstart(les_ensemble e, les_net net, int32_t every_sweeps);
 
+/* Failure-detection self-test: launches one block whose bounded device wait
+ * (the one the TMA sweeps use: an mbarrier polled against the global timer)
+ * waits for a transaction that never arrives.  It must give up after
+ * limit_ns (1e3..2e9) and report it: returns LES_ETIMEOUT (the expected
+ * result; les_last_error(NULL) says so), LES_OK if the wait completed,
+ * LES_ECUDA/LES_ENOMEM on CUDA errors.  Nothing is left in flight; the CUDA
+ * context stays usable. */
+int les_selftest_wait_timeout(int64_t limit_ns, void* stream);
+
 /* Bracket a region for a profiler started with capture off
  * (cudaProfilerStart when start != 0, cudaProfilerStop otherwise). */
 int les_profiler_range(int32_t start);

@@ -1050,6 +1050,23 @@ extern "C" {
 
 const char* les_version(void) { return kVersion; }
 
+int les_selftest_wait_timeout(int64_t limit_ns, void* stream) {
+    if (limit_ns < 1000 || limit_ns > 2000000000LL) return fail(nullptr, LES_EINVAL, "limit_ns must be 1e3..2e9");
+    int* d = nullptr;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return fail(nullptr, LES_ENOMEM, "self-test flag");
+    cudaStream_t s = (cudaStream_t)stream;
+    int host = -1;
+    launch_wait_selftest((unsigned long long)limit_ns, d, s);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&host, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(nullptr, LES_ECUDA, "wait self-test: %s", cudaGetErrorString(e));
+    if (host == 1) return fail(nullptr, LES_ETIMEOUT, "bounded wait gave up after %lld ns (expected)",
+                               (long long)limit_ns);
+    return LES_OK;
+}
+
 int les_profiler_range(int32_t start) {
     cudaError_t e = start ? cudaProfilerStart() : cudaProfilerStop();
     return e == cudaSuccess ? LES_OK : fail(nullptr, LES_ECUDA, "profiler range: %s", cudaGetErrorString(e));

@@ -206,6 +206,7 @@ bool tma_encode(const Dom& d, float* dl0, float* dl1, float* rr, uint8_t* flags,
 int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, const float* cn1tab, int cfg, int in, float* dout,
                    int zero, Scalars* sc, cudaStream_t s);
 int launch_cn1_table(const Geo<float>& g, float* tab, cudaStream_t s);
+int launch_wait_selftest(unsigned long long limit_ns, int* status, cudaStream_t s);
 
 // learned warm start (les_kernels.cu): energy-norm line search along q and p += alpha q
 // (dl null: p_h += alpha q at the start of a solve; dl set: inside the loop the

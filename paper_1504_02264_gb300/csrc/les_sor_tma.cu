@@ -490,4 +490,35 @@ int launch_cn1_table(const Geo<float>& g, float* tab, cudaStream_t s) {
     return 1;
 }
 
+// Self-test of the bounded device wait used by the TMA sweeps: an mbarrier
+// armed for 16 bytes of transaction that no copy will ever deliver.  The wait
+// gives up after limit_ns (global timer), every thread agrees, and the block
+// reports the timeout and returns; nothing is in flight, so the context stays
+// usable.  status: 1 = timed out (expected), 0 = the barrier completed.
+__global__ void k_wait_selftest(unsigned long long limit_ns, int* status) {
+    __shared__ __align__(8) uint64_t bar_word;
+    const uint32_t bar = smem_u32(&bar_word);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_expect_tx(bar, 16);
+    __syncthreads();
+    bool ok = false;
+    const uint64_t t0 = global_ns();
+    while (!(ok = mbar_try_wait(bar, 0)))
+        if (global_ns() - t0 > limit_ns) break;
+    const bool all = __syncthreads_and(ok);
+    if (threadIdx.x == 0) {
+        *status = all ? 0 : 1;
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+    }
+}
+
+int launch_wait_selftest(unsigned long long limit_ns, int* status, cudaStream_t s) {
+    k_wait_selftest<<<1, 128, 0, s>>>(limit_ns, status);
+    return 1;
+}
+
 }  // namespace les

@@ -100,6 +100,7 @@ def lib(build_if_missing: bool = False):
         L.les_ensemble_autotune.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
         L.les_ensemble_launches.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
         L.les_ensemble_set_warmstart.argtypes = [vp, vp, i32]
+        L.les_selftest_wait_timeout.argtypes = [ctypes.c_int64, vp]
         L.les_set_record.argtypes = [vp, i32]
         L.les_set_record_at.argtypes = [vp, i32]
         L.les_set_net_schedule.argtypes = [vp, i32]
@@ -127,7 +128,7 @@ def lib(build_if_missing: bool = False):
         L.les_get_timing.argtypes = [vp, ctypes.POINTER(les_timing_t)]
         for name in ("les_ensemble_create", "les_ensemble_size", "les_ensemble_member", "les_ensemble_step",
                      "les_ensemble_set_graph", "les_ensemble_set_tile", "les_ensemble_get_tile",
-                     "les_ensemble_autotune", "les_ensemble_launches", "les_ensemble_set_warmstart", "les_set_record", "les_set_record_at", "les_set_net_schedule", "les_set_warmstart",
+                     "les_ensemble_autotune", "les_ensemble_launches", "les_ensemble_set_warmstart", "les_selftest_wait_timeout", "les_set_record", "les_set_record_at", "les_set_net_schedule", "les_set_warmstart",
                      "les_net_create", "les_net_num_params", "les_net_set_stride", "les_net_get_stride",
                      "les_net_get_params", "les_net_set_params", "les_net_forward", "les_net_gradient",
                      "les_net_train_step", "les_residual_noalloc", "les_profiler_range", "les_set_graph",
@@ -419,6 +420,14 @@ class Ensemble:
         _echeck(lib().les_ensemble_set_warmstart(self.h, net.h if net is not None else None, every_sweeps),
                 self.h)
         self._net = net
+
+
+def les_selftest_wait_timeout(limit_ns, stream=None):
+    """Returns the C status (LES_ETIMEOUT expected) without raising on it."""
+    rc = lib().les_selftest_wait_timeout(int(limit_ns), stream)
+    if rc < 0 and rc != LES_ETIMEOUT:
+        raise LesError(rc, lib().les_last_error(None).decode())
+    return rc
 
 
 def les_profiler_range(start):
