@@ -239,6 +239,11 @@ int les_set_sor_config(les_handle h, int32_t tile, int32_t kc);
 int les_get_sor_config(les_handle h, int32_t* tile, int32_t* kc);
 int les_sor_tile(int32_t tile, int32_t* tx, int32_t* ty, int32_t* tz);
 int les_autotune_sor(les_handle h, int32_t sweeps, double* best_ms_per_sweep);
+/* les_time_sor: milliseconds per sweep of one configuration (tile index of
+ * les_set_sor_config, kc) timed over `sweeps` sweeps on the scratch
+ * correction buffers (state untouched, configuration kept).  LES_EINVAL for
+ * a tile this grid cannot use. */
+int les_time_sor(les_handle h, int32_t tile, int32_t kc, int32_t sweeps, double* ms_per_sweep);
 
 /*
  * les_residual_noalloc: FP64 norms of the pressure Poisson residual for

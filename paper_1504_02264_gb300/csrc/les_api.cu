@@ -491,7 +491,19 @@ int sor_solve(les_s* h) {
 // correction right-hand side; the sweeps touch only the scratch correction
 // buffers, never the state.
 template <typename T>
-int autotune_impl(les_s* h, int sweeps, double* best_ms) {
+int autotune_impl(les_s* h, int sweeps, double* best_ms, int only_tile = -2, int only_kc = 0);
+
+// time one configuration (the state is untouched; the current configuration is kept)
+template <typename T>
+int time_config_impl(les_s* h, int tile, int kc, int sweeps, double* ms) {
+    const SorCfg keep = h->sor;
+    int rc = autotune_impl<T>(h, sweeps, ms, tile, kc);
+    h->sor = keep;
+    return rc;
+}
+
+template <typename T>
+int autotune_impl(les_s* h, int sweeps, double* best_ms, int only_tile, int only_kc) {
     Geo<T> g = geo<T>(h);
     cudaEvent_t a, b;
     CK(cudaEventCreate(&a));
@@ -507,6 +519,7 @@ int autotune_impl(les_s* h, int sweeps, double* best_ms) {
         for (int kc : kcs) {
             if (kc > h->g.nz) continue;
             if ((t >= kNumSorTiles || kSorTiles[t].tz > 0) && kc != 0) continue;      // 3-D blocks ignore kc
+            if (only_tile >= -1 && (t != only_tile || kc != only_kc)) continue;
             h->sor = SorCfg{t, kc};
             long long nl = 0;
             run_sweeps<T>(h, g, 2, 0, nl, h->stream);       // warm
@@ -1279,6 +1292,18 @@ int les_sor_tile(int32_t tile, int32_t* tx, int32_t* ty, int32_t* tz) {
     if (ty) *ty = kSorTiles[tile].ty;
     if (tz) *tz = kSorTiles[tile].tz;
     return LES_OK;
+}
+
+int les_time_sor(les_handle h, int32_t tile, int32_t kc, int32_t sweeps, double* ms_per_sweep) {
+    if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
+    if (sweeps < 1 || !ms_per_sweep) return fail(h, LES_EINVAL, "sweeps must be >= 1 and ms_per_sweep set");
+    const int ntiles = kNumSorTiles + (h->tma_ok ? kNumTmaTiles : 0);
+    if (tile < 0 || tile >= ntiles) return fail(h, LES_EINVAL, "tile %d not available on this grid", tile);
+    *ms_per_sweep = -1.0;
+    int rc = h->prec == LES_FP64 ? time_config_impl<double>(h, tile, kc, sweeps, ms_per_sweep)
+                                 : time_config_impl<float>(h, tile, kc, sweeps, ms_per_sweep);
+    if (!rc && *ms_per_sweep > 1e299) return fail(h, LES_EINVAL, "configuration (%d, %d) not valid", tile, kc);
+    return rc;
 }
 
 int les_autotune_sor(les_handle h, int32_t sweeps, double* best_ms_per_sweep) {

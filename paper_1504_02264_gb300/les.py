@@ -101,6 +101,7 @@ def lib(build_if_missing: bool = False):
         L.les_ensemble_launches.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
         L.les_ensemble_set_warmstart.argtypes = [vp, vp, i32]
         L.les_selftest_wait_timeout.argtypes = [ctypes.c_int64, vp]
+        L.les_time_sor.argtypes = [vp, i32, i32, i32, ctypes.POINTER(ctypes.c_double)]
         L.les_set_record.argtypes = [vp, i32]
         L.les_set_record_at.argtypes = [vp, i32]
         L.les_set_net_schedule.argtypes = [vp, i32]
@@ -128,7 +129,7 @@ def lib(build_if_missing: bool = False):
         L.les_get_timing.argtypes = [vp, ctypes.POINTER(les_timing_t)]
         for name in ("les_ensemble_create", "les_ensemble_size", "les_ensemble_member", "les_ensemble_step",
                      "les_ensemble_set_graph", "les_ensemble_set_tile", "les_ensemble_get_tile",
-                     "les_ensemble_autotune", "les_ensemble_launches", "les_ensemble_set_warmstart", "les_selftest_wait_timeout", "les_set_record", "les_set_record_at", "les_set_net_schedule", "les_set_warmstart",
+                     "les_ensemble_autotune", "les_ensemble_launches", "les_ensemble_set_warmstart", "les_selftest_wait_timeout", "les_time_sor", "les_set_record", "les_set_record_at", "les_set_net_schedule", "les_set_warmstart",
                      "les_net_create", "les_net_num_params", "les_net_set_stride", "les_net_get_stride",
                      "les_net_get_params", "les_net_set_params", "les_net_forward", "les_net_gradient",
                      "les_net_train_step", "les_residual_noalloc", "les_profiler_range", "les_set_graph",
@@ -598,6 +599,11 @@ class Domain:
 
     def sor_config(self):
         return les_get_sor_config(self.h)
+
+    def time_sor(self, tile, kc=0, sweeps=20):
+        ms = ctypes.c_double()
+        _check(lib().les_time_sor(self.h, tile, kc, sweeps, ctypes.byref(ms)), self.h)
+        return ms.value
 
     def autotune_sor(self, sweeps=20):
         ms = les_autotune_sor(self.h, sweeps)

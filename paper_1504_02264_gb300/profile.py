@@ -82,6 +82,8 @@ def main():
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--fp64", action="store_true")
     ap.add_argument("--range", action="store_true")
+    ap.add_argument("--sweep-table", action="store_true",
+                    help="time every SOR sweep configuration on the workload after the warm-up steps")
     ap.add_argument("--net", default=None, help="trained warm-start network (.npz: params, stride)")
     ap.add_argument("--net-every", type=int, default=0, help="network correction every n sweeps")
     a = ap.parse_args()
@@ -101,6 +103,18 @@ def main():
     for _ in range(a.warmup):
         d.step(1)
     tune = None
+    if a.sweep_table:
+        rows = []
+        for t in range(-1, 25):
+            for kc in ((0, 8, 16) if 0 <= t <= 5 else (0,)):
+                try:
+                    ms = d.time_sor(t, kc, sweeps=20)
+                except les.LesError:
+                    continue
+                rows.append({"tile": t, "kc": kc, "shape": les.les_sor_tile(t) if t >= 0 else "two-pass",
+                             "ms_per_sweep": ms, "alg_gbs": 13.0 * sc.ncells / (ms * 1e-3) / 1e9})
+        print(json.dumps({"workload": a.workload, "cells": sc.ncells, "sweep_table": rows}))
+        return
     if a.autotune:
         tune = d.autotune_sor(sweeps=20)
     if net is not None:
