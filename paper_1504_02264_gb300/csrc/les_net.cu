@@ -88,16 +88,27 @@ __global__ void __launch_bounds__(256) k_rms(const float* a, const float* mask, 
         part[2 * blockIdx.x + 1] = tm;
     }
 }
-__global__ void k_rms_final(const double* part, int nblocks, double* out, const int* gate) {
+// one block of kRmsBlocks threads: thread b takes partial b, then a fixed
+// shared-memory tree (deterministic)
+__global__ void __launch_bounds__(kRmsBlocks) k_rms_final(const double* part, int nblocks, double* out,
+                                                          const int* gate) {
     if (gate && *(volatile const int*)gate) return;
-    if (threadIdx.x != 0) return;
-    double s = 0.0, m = 0.0;
-    for (int b = 0; b < nblocks; ++b) {
-        s += part[2 * b];
-        m += part[2 * b + 1];
+    __shared__ double ss[kRmsBlocks], sm[kRmsBlocks];
+    const int t = threadIdx.x;
+    ss[t] = t < nblocks ? part[2 * t] : 0.0;
+    sm[t] = t < nblocks ? part[2 * t + 1] : 0.0;
+    __syncthreads();
+    for (int o = kRmsBlocks / 2; o > 0; o >>= 1) {
+        if (t < o) {
+            ss[t] += ss[t + o];
+            sm[t] += sm[t + o];
+        }
+        __syncthreads();
     }
-    out[0] = m > 0.0 ? sqrt(s / m) : 0.0;
-    out[1] = m;
+    if (t == 0) {
+        out[0] = sm[0] > 0.0 ? sqrt(ss[0] / sm[0]) : 0.0;
+        out[1] = sm[0];
+    }
 }
 // dense input: channel 0 = r / scale, channel 1 = mask
 __global__ void k_pack_dense(const float* r, const float* mask, const double* scale, __nv_bfloat16* xin, size_t n,
@@ -240,6 +251,23 @@ int ensure_ws(les_net_s* n, const Level& L0) {
     return LES_OK;
 }
 
+// inference forward: pooling and upsampling folded into the convolutions'
+// input staging (bit-identical to forward(), which keeps the pooled and
+// upsampled tensors for the backward pass); every kernel returns at once
+// while *gate != 0 (gate may be null)
+void forward_fused(les_net_s* n, const Level& L0, const int* gate) {
+    cudaStream_t s = n->stream;
+    const Level L1 = level(L0, 1), L2 = level(L0, 2), L3 = level(L0, 3);
+    nn::conv3_fwd(n->xin, n->wb[0], n->e[0], nullptr, nullptr, L0.X, L0.Y, L0.Z, 16, 16, 1, s, gate);
+    nn::conv3_fwd_pool(n->e[0], n->wb[1], n->e[1], L0.X, L0.Y, L0.Z, 16, 32, 1, s, gate);
+    nn::conv3_fwd_pool(n->e[1], n->wb[2], n->e[2], L1.X, L1.Y, L1.Z, 32, 64, 1, s, gate);
+    nn::conv3_fwd_pool(n->e[2], n->wb[3], n->e[3], L2.X, L2.Y, L2.Z, 64, 128, 1, s, gate);
+    nn::conv3_fwd_up(n->e[3], n->wb[4], n->r[2], n->e[2], n->dd[2], L2.X, L2.Y, L2.Z, 128, 64, 1, s, gate);
+    nn::conv3_fwd_up(n->dd[2], n->wb[5], n->r[1], n->e[1], n->dd[1], L1.X, L1.Y, L1.Z, 64, 32, 1, s, gate);
+    nn::conv3_fwd_up(n->dd[1], n->wb[6], n->r[0], n->e[0], n->dd[0], L0.X, L0.Y, L0.Z, 32, 16, 1, s, gate);
+    nn::head(n->dd[0], n->w32 + n->off[kConvs], n->mask, n->y, L0.v(), kHeadC, s, gate);
+}
+
 // forward on the packed input n->xin with mask n->mask; output n->y
 // (every kernel returns at once while *gate != 0; gate may be null)
 void forward(les_net_s* n, const Level& L0, const int* gate = nullptr) {
@@ -320,10 +348,10 @@ int pack_sample(les_net_s* n, const Level& L0, const float* r, const float* mask
     const int blocks = (int)((v + 255) / 256 < (size_t)kRmsBlocks ? (v + 255) / 256 : kRmsBlocks);
     double* part = n->dscal + 64;
     k_rms<<<blocks, 256, 0, s>>>(r, mask, v, part, gate);
-    k_rms_final<<<1, 32, 0, s>>>(part, blocks, n->dscal, gate);
+    k_rms_final<<<1, kRmsBlocks, 0, s>>>(part, blocks, n->dscal, gate);
     if (t) {
         k_rms<<<blocks, 256, 0, s>>>(t, mask, v, part + 2 * kRmsBlocks, gate);
-        k_rms_final<<<1, 32, 0, s>>>(part + 2 * kRmsBlocks, blocks, n->dscal + 2, gate);
+        k_rms_final<<<1, kRmsBlocks, 0, s>>>(part + 2 * kRmsBlocks, blocks, n->dscal + 2, gate);
     }
     if (mask != n->mask) NCK(cudaMemcpyAsync(n->mask, mask, v * sizeof(float), cudaMemcpyDeviceToDevice, s));
     k_pack_dense<<<(unsigned)((v + 255) / 256), 256, 0, s>>>(r, n->mask, n->dscal, n->xin, v, gate);
@@ -403,14 +431,14 @@ int net_predict(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t
         rc = pack_sample(n, L0, n->rc, n->mc, nullptr, nullptr, gate);
     }
     if (!rc) {
-        forward(n, L0, gate);
+        forward_fused(n, L0, gate);
         nn::prolong_flags(n->y, flags, d, n->stride, out_dense, s, gate);
         if (cudaGetLastError() != cudaSuccess) rc = LES_ECUDA;
     }
     n->stream = keep;
     return rc;
 }
-int net_launches(const les_net_s*) { return 1 + 3 + 15 + 1; }     // pool, rms + pack, network, prolongation
+int net_launches(const les_net_s*) { return 1 + 4 + 8 + 1; }     // pool, rms + pack, network, prolongation
 }  // namespace les
 
 extern "C" {
@@ -521,7 +549,7 @@ int les_net_forward(les_net n, const float* d_r, const float* d_mask, float* d_y
     int rc = ensure_ws(n, L0);
     if (rc) return rc;
     if ((rc = prepare_sample(n, Lf, d_r, d_mask, nullptr, 0, nullptr))) return rc;
-    forward(n, L0);
+    forward_fused(n, L0, nullptr);
     nn::prolong_dense(n->y, d_mask, d_y, nx, ny, nz, n->stride, n->stream);
     NCK(cudaGetLastError());
     NCK(cudaStreamSynchronize(n->stream));

@@ -75,11 +75,19 @@ struct ConvStage {
 // Two stages in dynamic shared memory: the next 16-channel chunk (halo block
 // and weights) is copied with cp.async while the tensor cores work on the
 // current one; the 27 taps are unrolled.
-template <int CO>
+// IN selects how the input voxel (gx, gy, gz) of the X x Y x Z output grid is
+// read from the source tensor x (Xs x Ys x Zs):
+//   IN_DIRECT  x[gz][gy][gx]                     (Xs = X ...)
+//   IN_UP      x[gz/2][gy/2][gx/2]               nearest upsampling of a coarser tensor
+//   IN_POOL    mean of the 8 children x[2gz+c][2gy+b][2gx+a] (missing children count as
+//              zero; summed in the order of the stand-alone pooling kernel, so the
+//              staged values are bit-identical to pooling first)
+enum { IN_DIRECT = 0, IN_UP = 1, IN_POOL = 2 };
+template <int CO, int IN>
 __global__ void __launch_bounds__(256)
 k_conv3(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ w, __nv_bfloat16* __restrict__ y,
         const __nv_bfloat16* __restrict__ skip, __nv_bfloat16* __restrict__ ysum, int X, int Y, int Z, int Cin,
-        int Cout, int relu, const int* gate) {
+        int Cout, int relu, const int* gate, int Xs, int Ys, int Zs) {
     if (gate && *(volatile const int*)gate) return;      // the solve this inference serves has ended
     extern __shared__ __align__(16) unsigned char conv_smem[];
     ConvStage<CO>* st = reinterpret_cast<ConvStage<CO>*>(conv_smem);
@@ -94,8 +102,31 @@ k_conv3(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ w
             const int hx = v % HX, hy = (v / HX) % HY, hz = v / (HX * HY);
             const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = z0 - 1 + hz;
             const bool ok = gx >= 0 && gx < X && gy >= 0 && gy < Y && gz >= 0 && gz < Z;
-            const __nv_bfloat16* src = ok ? x + (((size_t)gz * Y + gy) * X + gx) * Cin + c0 + 8 * h : x;
-            cp_async16(smem_addr(&S.in[hz][hy][hx][8 * (h ^ swz(hx))]), src, ok ? 16 : 0);
+            __nv_bfloat16* dst = &S.in[hz][hy][hx][8 * (h ^ swz(hx))];
+            if constexpr (IN == IN_POOL) {
+                float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (ok)
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int fx = 2 * gx + (e & 1), fy = 2 * gy + ((e >> 1) & 1), fz = 2 * gz + (e >> 2);
+                        if (fx < Xs && fy < Ys && fz < Zs) {
+                            const uint4 v = *reinterpret_cast<const uint4*>(
+                                x + (((size_t)fz * Ys + fy) * Xs + fx) * Cin + c0 + 8 * h);
+                            const __nv_bfloat16* b = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) a[c] += __bfloat162float(b[c]);
+                        }
+                    }
+                __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) o[c] = __float2bfloat16(0.125f * a[c]);
+                *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(o);
+            } else {
+                const int sx = IN == IN_UP ? gx >> 1 : gx, sy = IN == IN_UP ? gy >> 1 : gy,
+                          sz = IN == IN_UP ? gz >> 1 : gz;
+                const __nv_bfloat16* src = ok ? x + (((size_t)sz * Ys + sy) * Xs + sx) * Cin + c0 + 8 * h : x;
+                cp_async16(smem_addr(dst), src, ok ? 16 : 0);
+            }
         }
         for (int q = tid; q < 27 * CO * 2; q += 256) {
             const int h = q & 1, r = q >> 1, co = r % CO, tap = r / CO;
@@ -119,7 +150,7 @@ k_conv3(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ w
         } else {
             cp_async_wait<0>();
         }
-        __syncthreads();
+        __syncthreads();      // (also orders the plain shared stores of IN_POOL staging)
         const ConvStage<CO>& S = st[c & 1];
 #pragma unroll
         for (int tap = 0; tap < 27; ++tap) {
@@ -169,18 +200,27 @@ k_conv3(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ w
     }
 }
 
+template <int CO, int IN>
+static cudaError_t allow_conv() {
+    return cudaFuncSetAttribute(k_conv3<CO, IN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(2 * sizeof(ConvStage<CO>)));
+}
+
 int conv3_prepare() {
-    cudaError_t e = cudaFuncSetAttribute(k_conv3<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(2 * sizeof(ConvStage<32>)));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_conv3<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(2 * sizeof(ConvStage<16>)));
+    cudaError_t e = cudaSuccess, x;
+    if ((x = allow_conv<32, IN_DIRECT>()) != cudaSuccess) e = x;
+    if ((x = allow_conv<16, IN_DIRECT>()) != cudaSuccess) e = x;
+    if ((x = allow_conv<32, IN_UP>()) != cudaSuccess) e = x;
+    if ((x = allow_conv<16, IN_UP>()) != cudaSuccess) e = x;
+    if ((x = allow_conv<32, IN_POOL>()) != cudaSuccess) e = x;
+    if ((x = allow_conv<16, IN_POOL>()) != cudaSuccess) e = x;
     return e == cudaSuccess ? 0 : -1;
 }
 
-void conv3_fwd(const __nv_bfloat16* x, const __nv_bfloat16* w, __nv_bfloat16* y, const __nv_bfloat16* skip,
-               __nv_bfloat16* ysum, int X, int Y, int Z, int Cin, int Cout, int relu, cudaStream_t s,
-               const int* gate) {
+template <int IN>
+static void conv3_launch(const __nv_bfloat16* x, const __nv_bfloat16* w, __nv_bfloat16* y, const __nv_bfloat16* skip,
+                         __nv_bfloat16* ysum, int X, int Y, int Z, int Cin, int Cout, int relu, cudaStream_t s,
+                         const int* gate, int Xs, int Ys, int Zs) {
     // 32 output channels per CTA when the grid fills the GPU, else 16 (twice
     // the CTAs, half the weights staged per CTA: small levels are latency-bound)
     const int ntz = (Z + TZ - 1) / TZ;
@@ -188,9 +228,30 @@ void conv3_fwd(const __nv_bfloat16* x, const __nv_bfloat16* w, __nv_bfloat16* y,
     const int co = (Cout >= 32 && tiles * (Cout / 32) >= 2 * 152) ? 32 : 16;
     dim3 grid((X + TX - 1) / TX, (Y + TY - 1) / TY, ntz * ((Cout + co - 1) / co));
     if (co == 32)
-        k_conv3<32><<<grid, 256, 2 * sizeof(ConvStage<32>), s>>>(x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu, gate);
+        k_conv3<32, IN><<<grid, 256, 2 * sizeof(ConvStage<32>), s>>>(x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu,
+                                                                     gate, Xs, Ys, Zs);
     else
-        k_conv3<16><<<grid, 256, 2 * sizeof(ConvStage<16>), s>>>(x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu, gate);
+        k_conv3<16, IN><<<grid, 256, 2 * sizeof(ConvStage<16>), s>>>(x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu,
+                                                                     gate, Xs, Ys, Zs);
+}
+
+void conv3_fwd(const __nv_bfloat16* x, const __nv_bfloat16* w, __nv_bfloat16* y, const __nv_bfloat16* skip,
+               __nv_bfloat16* ysum, int X, int Y, int Z, int Cin, int Cout, int relu, cudaStream_t s,
+               const int* gate) {
+    conv3_launch<IN_DIRECT>(x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu, s, gate, X, Y, Z);
+}
+
+void conv3_fwd_up(const __nv_bfloat16* xc, const __nv_bfloat16* w, __nv_bfloat16* y, const __nv_bfloat16* skip,
+                  __nv_bfloat16* ysum, int X, int Y, int Z, int Cin, int Cout, int relu, cudaStream_t s,
+                  const int* gate) {
+    conv3_launch<IN_UP>(xc, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu, s, gate, (X + 1) / 2, (Y + 1) / 2,
+                        (Z + 1) / 2);
+}
+
+void conv3_fwd_pool(const __nv_bfloat16* xf, const __nv_bfloat16* w, __nv_bfloat16* y, int Xf, int Yf, int Zf,
+                    int Cin, int Cout, int relu, cudaStream_t s, const int* gate) {
+    conv3_launch<IN_POOL>(xf, w, y, nullptr, nullptr, (Xf + 1) / 2, (Yf + 1) / 2, (Zf + 1) / 2, Cin, Cout, relu, s,
+                          gate, Xf, Yf, Zf);
 }
 
 // dgrad weights: W'[tap][ci][co] = W[26 - tap][co][ci] (flipped taps, swapped roles)
