@@ -1415,7 +1415,7 @@ void member_fill(les_s* h, EnsMember<float>& M, int ens_tile, int parity) {
     M.sgrid[2] = (d.nz + t.tz - 1) / t.tz;
     M.egrid[0] = (d.nx + 31) / 32;
     M.egrid[1] = (d.ny + 7) / 8;
-    M.egrid[2] = (d.nz + 3) / 4;      // the estimate's plane chunk (kEstChunk)
+    M.egrid[2] = (d.nz + kEstChunk - 1) / kEstChunk;
     M.agrid[0] = (d.nx + 31) / 32;
     M.agrid[1] = (d.ny + 7) / 8;
     M.agrid[2] = d.nz;

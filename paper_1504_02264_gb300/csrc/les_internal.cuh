@@ -177,6 +177,7 @@ struct EnsTab {
 };
 static_assert(sizeof(EnsTab<float>) < 32000, "ensemble table must fit in the kernel parameter space");
 constexpr int kFirstRowTile = 12, kNumEnsTiles = 5;
+constexpr int kEstChunk = 4;       // planes per thread in the estimate and line-search kernels
 
 struct SorTile { int tx, ty, tz; };   // tz = 0: k-marching column tile
 struct SorCfg { int tile; int kc; };   // tile < 0: two in-place half-sweep kernels

@@ -635,7 +635,6 @@ int launch_accum(const Geo<T>& g, double* ph, const T* dl, const Scalars* sc, in
 // Grid-stride reductions use at most kReduceBlocks blocks, so the last-block
 // completion counter sees few atomics.
 constexpr int kReduceBlocks = 1024;
-constexpr int kEstChunk = 4;       // planes per thread in the estimate and line-search kernels
 int reduce_blocks(const Dom& d) {
     long long n = (long long)d.nx * d.ny * d.nz;
     long long b = (n + 255) / 256;
