@@ -242,6 +242,7 @@ Geo<T> geo(les_s* h) {
     g.cT64 = h->cT64;
     g.cB64 = h->cB64;
     g.flags = h->flags;
+    g.cn1 = std::is_same<T, float>::value ? (const T*)h->cn1tab : nullptr;
     return g;
 }
 
@@ -937,12 +938,15 @@ int create_impl(les_s* h, const uint8_t* solid) {
         CK(cudaStreamSynchronize(h->stream));
         h->n_unk = (double)hc;
     }
-    if (h->prec == LES_FP32 && tma_supported(d)) {
-        CK(tma_prepare());
-        h->tma_ok = tma_encode(d, (float*)h->dl[0], (float*)h->dl[1], (float*)h->rr, h->flags, h->tma);
+    if (h->prec == LES_FP32) {
+        // cn1 over (plane, open-face mask), read by the FP32 sweep kernels
         if ((rc = dalloc(h, (void**)&h->cn1tab, (size_t)(G.nz + 2) * 64 * sizeof(float)))) return rc;
         launch_cn1_table(geo<float>(h), h->cn1tab, h->stream);
         CK(cudaGetLastError());
+        if (tma_supported(d)) {
+            CK(tma_prepare());
+            h->tma_ok = tma_encode(d, (float*)h->dl[0], (float*)h->dl[1], (float*)h->rr, h->flags, h->tma);
+        }
         CK(cudaStreamSynchronize(h->stream));
     }
     CK(cudaStreamSynchronize(h->stream));

@@ -100,6 +100,7 @@ struct Geo {
     const double* cT64;     // [nz+2]
     const double* cB64;     // [nz+2]
     const uint8_t* flags;   // padded cell flags
+    const T* cn1;           // [nz+2][64] cn1 over (plane, open-face mask); FP32 grids only (else null)
 };
 
 struct Reduce {

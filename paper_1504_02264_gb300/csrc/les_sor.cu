@@ -348,19 +348,24 @@ __device__ __forceinline__ void sor_rows_tile(const Geo<T>& g, const T* __restri
         }
     }
     // per-plane coefficients and the cn1 table over the six open-face bits
+    // (from the handle's table on FP32 grids, else the same arithmetic here)
     for (int q = tid; q < RZ * 64; q += 256) {
         const int kk = q >> 6, m = q & 63;
         int k = k0 - 1 + kk;
         k = d.perz ? (k < 1 ? k + d.nz : (k > d.nz ? k - d.nz : k)) : min(max(k, 0), d.nz + 1);
         const T ct = g.cT[k], cb = g.cB[k];
-        T ae = (m & F_E) ? g.cx : T(0);
-        T aw = (m & F_W) ? g.cx : T(0);
-        T an = (m & F_N) ? g.cy : T(0);
-        T as = (m & F_S) ? g.cy : T(0);
-        T at = (m & F_T) ? ct : T(0);
-        T ab = (m & F_B) ? cb : T(0);
-        const T sum = ae + aw + an + as + at + ab;
-        sCN[kk][m] = sum > T(0) ? T(1) / sum : T(0);
+        if (g.cn1) {
+            sCN[kk][m] = g.cn1[k * 64 + m];
+        } else {
+            T ae = (m & F_E) ? g.cx : T(0);
+            T aw = (m & F_W) ? g.cx : T(0);
+            T an = (m & F_N) ? g.cy : T(0);
+            T as = (m & F_S) ? g.cy : T(0);
+            T at = (m & F_T) ? ct : T(0);
+            T ab = (m & F_B) ? cb : T(0);
+            const T sum = ae + aw + an + as + at + ab;
+            sCN[kk][m] = sum > T(0) ? T(1) / sum : T(0);
+        }
         if (m == 0) {
             sCT[kk] = ct;
             sCB[kk] = cb;
@@ -382,20 +387,28 @@ __device__ __forceinline__ void sor_rows_tile(const Geo<T>& g, const T* __restri
     __syncthreads();
     const T omega = g.omega, cx = g.cx, cy = g.cy;
     auto relax = [&](int x, int y, int z, int kz, uint8_t f, T rhs) {
-        T ae = (f & F_E) ? cx : T(0);
-        T aw = (f & F_W) ? cx : T(0);
-        T an = (f & F_N) ? cy : T(0);
-        T as = (f & F_S) ? cy : T(0);
-        T at = (f & F_T) ? sCT[kz] : T(0);
-        T ab = (f & F_B) ? sCB[kz] : T(0);
+        const T ct = sCT[kz], cb = sCB[kz];
         const T cn1 = sCN[kz][f & 63];
         T s = T(0);
-        s += ae * sD[z][y][x + 1];
-        s += aw * sD[z][y][x - 1];
-        s += an * sD[z][y + 1][x];
-        s += as * sD[z][y - 1][x];
-        s += at * sD[z + 1][y][x];
-        s += ab * sD[z - 1][y][x];
+        if ((f & 63) == 63) {
+            // all six faces open: the same sum without the selects
+            s += cx * sD[z][y][x + 1];
+            s += cx * sD[z][y][x - 1];
+            s += cy * sD[z][y + 1][x];
+            s += cy * sD[z][y - 1][x];
+            s += ct * sD[z + 1][y][x];
+            s += cb * sD[z - 1][y][x];
+        } else {
+            const T ae = (f & F_E) ? cx : T(0), aw = (f & F_W) ? cx : T(0);
+            const T an = (f & F_N) ? cy : T(0), as = (f & F_S) ? cy : T(0);
+            const T at = (f & F_T) ? ct : T(0), ab = (f & F_B) ? cb : T(0);
+            s += ae * sD[z][y][x + 1];
+            s += aw * sD[z][y][x - 1];
+            s += an * sD[z][y + 1][x];
+            s += as * sD[z][y - 1][x];
+            s += at * sD[z + 1][y][x];
+            s += ab * sD[z - 1][y][x];
+        }
         T own = sD[z][y][x];
         T reltmp = omega * (cn1 * (s - rhs) - own);
         sD[z][y][x] = own + reltmp;
@@ -423,12 +436,14 @@ __device__ __forceinline__ void sor_rows_tile(const Geo<T>& g, const T* __restri
         }
     }
     __syncthreads();
+    // store the block (cells that are not unknowns hold 0 in d and in the tile)
     const int i = i0 + lane;
-    for (int rw = warp; rw < BY * BZ; rw += 8) {
-        const int jj = rw % BY, kk = rw / BY;
-        const int j = j0 + jj, k = k0 + kk;
-        if (lane < BX && i <= d.nx && j <= d.ny && k <= d.nz && (sF[kk + 1][jj + 1][lane + 1] & F_UNK))
-            dout[(k * py + j) * px + i + OX] = sD[kk + 2][jj + 2][lane + 2];
+    if (lane < BX && i <= d.nx) {
+        const int kend = min(BZ, d.nz + 1 - k0), jend = min(BY, d.ny + 1 - j0);
+        for (int rw = warp; rw < BY * BZ; rw += 8) {
+            const int jj = rw % BY, kk = rw / BY;
+            if (jj < jend && kk < kend) dout[((k0 + kk) * py + j0 + jj) * px + i + OX] = sD[kk + 2][jj + 2][lane + 2];
+        }
     }
 }
 

@@ -108,20 +108,13 @@ k_sor_tma(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtens
         tma_load_3d(smem_u32(sR), &tr, xd, j0 - 1, k0 - 1, bar);
         tma_load_3d(smem_u32(sF), &tf, xf, j0 - 1, k0 - 1, bar);
     }
-    // per-plane coefficients and the cn1 table while the copies fly
+    // per-plane coefficients and the block's rows of the cn1 table while the copies fly
     for (int q = tid; q < RZ * 64; q += NT) {
         const int kk = q >> 6, m = q & 63;
         const int k = min(max(k0 - 1 + kk, 0), d.nz + 1);
-        const float ct = g.cT[k], cb = g.cB[k];
-        float ae = (m & F_E) ? g.cx : 0.f;
-        float aw = (m & F_W) ? g.cx : 0.f;
-        float an = (m & F_N) ? g.cy : 0.f;
-        float as = (m & F_S) ? g.cy : 0.f;
-        float at = (m & F_T) ? ct : 0.f;
-        float ab = (m & F_B) ? cb : 0.f;
-        const float sum = ae + aw + an + as + at + ab;
-        sCN[kk][m] = sum > 0.f ? 1.f / sum : 0.f;
+        sCN[kk][m] = g.cn1[k * 64 + m];
         if (m == 0) {
+            const float ct = g.cT[k], cb = g.cB[k];
             sCT[kk] = ct;
             sCB[kk] = cb;
         }
@@ -144,20 +137,28 @@ k_sor_tma(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtens
     }
     const float omega = g.omega, cx = g.cx, cy = g.cy;
     auto relax = [&](int x, int y, int z, int kz, uint8_t f, float rhs) {
-        float ae = (f & F_E) ? cx : 0.f;
-        float aw = (f & F_W) ? cx : 0.f;
-        float an = (f & F_N) ? cy : 0.f;
-        float as = (f & F_S) ? cy : 0.f;
-        float at = (f & F_T) ? sCT[kz] : 0.f;
-        float ab = (f & F_B) ? sCB[kz] : 0.f;
+        const float ct = sCT[kz], cb = sCB[kz];
         const float cn1 = sCN[kz][f & 63];
         float s = 0.f;
-        s += ae * sD[z][y][x + 1];
-        s += aw * sD[z][y][x - 1];
-        s += an * sD[z][y + 1][x];
-        s += as * sD[z][y - 1][x];
-        s += at * sD[z + 1][y][x];
-        s += ab * sD[z - 1][y][x];
+        if ((f & 63) == 63) {
+            // all six faces open (most fluid cells): the same sum without the selects
+            s += cx * sD[z][y][x + 1];
+            s += cx * sD[z][y][x - 1];
+            s += cy * sD[z][y + 1][x];
+            s += cy * sD[z][y - 1][x];
+            s += ct * sD[z + 1][y][x];
+            s += cb * sD[z - 1][y][x];
+        } else {
+            const float ae = (f & F_E) ? cx : 0.f, aw = (f & F_W) ? cx : 0.f;
+            const float an = (f & F_N) ? cy : 0.f, as = (f & F_S) ? cy : 0.f;
+            const float at = (f & F_T) ? ct : 0.f, ab = (f & F_B) ? cb : 0.f;
+            s += ae * sD[z][y][x + 1];
+            s += aw * sD[z][y][x - 1];
+            s += an * sD[z][y + 1][x];
+            s += as * sD[z][y - 1][x];
+            s += at * sD[z + 1][y][x];
+            s += ab * sD[z - 1][y][x];
+        }
         float own = sD[z][y][x];
         float reltmp = omega * (cn1 * (s - rhs) - own);
         sD[z][y][x] = own + reltmp;
@@ -185,12 +186,14 @@ k_sor_tma(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtens
         }
     }
     __syncthreads();
+    // store the block (cells that are not unknowns hold 0 in d and in the tile)
     const int i = i0 + lane;
-    for (int rw = warp; rw < BY * BZ; rw += NW) {
-        const int jj = rw % BY, kk = rw / BY;
-        const int j = j0 + jj, k = k0 + kk;
-        if (lane < BX && i <= d.nx && j <= d.ny && k <= d.nz && (sF[kk + 1][jj + 1][lane + 4 + off] & F_UNK))
-            dout[(k * d.py + j) * d.px + i + OX] = sD[kk + 2][jj + 2][lane + 4];
+    if (lane < BX && i <= d.nx) {
+        const int kend = min(BZ, d.nz + 1 - k0), jend = min(BY, d.ny + 1 - j0);
+        for (int rw = warp; rw < BY * BZ; rw += NW) {
+            const int jj = rw % BY, kk = rw / BY;
+            if (jj < jend && kk < kend) dout[((k0 + kk) * d.py + j0 + jj) * d.px + i + OX] = sD[kk + 2][jj + 2][lane + 4];
+        }
     }
 }
 
