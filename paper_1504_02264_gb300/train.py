@@ -48,20 +48,22 @@ def load(path: str, seed: int = 0) -> les.Net:
     return net
 
 
-def training_scenes(n_lattice: int, n_city: int, seed: int, city_shape=(96, 96, 48)):
-    """Lattice scenes (turbulent inflow for variety) and small random cities."""
+def training_scenes(n_lattice: int, n_city: int, seed: int, city_shape=(96, 96, 48), n_city2: int = 0,
+                    city_shape2=(150, 150, 90)):
+    """Lattice scenes (turbulent inflow for variety) and random cities of two
+    sizes (seeds 1000+ and 2000+, disjoint from the evaluation and bench cities)."""
     out = []
     for s in range(n_lattice):
         sc = scene.lattice_scene(seed=seed + s)
         sc.turb, sc.fixed_sweeps, sc.tol = 0.1, 0, 1e-7
         sc.max_sweeps, sc.check_every = 60000, 20
         out.append(sc)
-    nx, ny, nz = city_shape
-    for s in range(n_city):
-        sc = scene.random_scene(seed=seed + 1000 + s, nx=nx, ny=ny, nz=nz,
-                                n_buildings=max(8, int(100 * nx * ny / (150 * 150))), x_margin=12,
-                                tol=1e-7, max_sweeps=60000, check_every=20)
-        out.append(sc)
+    for base, n, (nx, ny, nz) in ((1000, n_city, city_shape), (2000, n_city2, city_shape2)):
+        for s in range(n):
+            sc = scene.random_scene(seed=seed + base + s, nx=nx, ny=ny, nz=nz,
+                                    n_buildings=max(8, int(100 * nx * ny / (150 * 150))),
+                                    x_margin=min(16, nx // 8), tol=1e-7, max_sweeps=60000, check_every=20)
+            out.append(sc)
     return out
 
 
@@ -187,6 +189,8 @@ def main(argv=None):
     ap.add_argument("--init", default=None, help="start from this network (.npz)")
     ap.add_argument("--stride", default="4", help="input stride(s) of the network, e.g. 2,4 (one net each)")
     ap.add_argument("--city-size", default="96x96x48")
+    ap.add_argument("--cities2", type=int, default=0, help="random-city scenes of the second size")
+    ap.add_argument("--city-size2", default="150x150x90")
     ap.add_argument("--lattice", type=int, default=16, help="lattice scenes (seeds)")
     ap.add_argument("--cities", type=int, default=8, help="random-city scenes")
     ap.add_argument("--steps", type=int, default=40, help="recorded steps per scene")
@@ -226,7 +230,8 @@ def main(argv=None):
     pts = [int(x) for x in a.record_points.split(",")]
     print(f"generating pairs: {a.lattice} lattice + {a.cities} city scenes x {a.steps} steps", flush=True)
     cs = tuple(int(x) for x in a.city_size.split("x"))
-    scenes = training_scenes(a.lattice, a.cities, a.seed, cs)
+    cs2 = tuple(int(x) for x in a.city_size2.split("x"))
+    scenes = training_scenes(a.lattice, a.cities, a.seed, cs, a.cities2, cs2)
     groups = generate(scenes, a.steps, a.spinup, pts, a.seed)
     if a.dagger:
         # pairs from solves that run with a network in the loop
