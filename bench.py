@@ -35,7 +35,7 @@ if ROOT not in sys.path:
 from paper_1504_02264_gb300 import scene  # noqa: E402
 
 METRIC = "LES Mcell-steps/s to |div|<=1e-6 (150x150x90, 100 buildings)"
-WEIGHTS = os.path.join(ROOT, "paper_1504_02264_gb300", "weights", "warmstart_s4.npz")
+WEIGHTS = os.path.join(ROOT, "paper_1504_02264_gb300", "weights", "warmstart.npz")
 NET_EVERY = 10                  # sweeps between learned corrections (trained schedule)
 UNIT = "Mcell-steps/s"
 SOR_BYTES_PER_CELL = 13.0       # per sweep: read p, rhs (4+4), flags (1), write p (4)
@@ -270,7 +270,7 @@ def run_ours(args):
     plain = timed("plain", net is None)
     if net is not None:
         # timed region 1b: the full hot path with the learned correction
-        # (stride-4 network every NET_EVERY sweeps), same start state, same
+        # (the package's network every NET_EVERY sweeps), same start state, same
         # stop test; one untimed step first builds its graphs
         dom.set_warmstart(net)
         dom.set_net_schedule(NET_EVERY)
@@ -344,8 +344,8 @@ def run_ours(args):
             "config": {"workload": "random_150x150x90", "nx": 150, "ny": 150, "nz": 90, "buildings": 100,
                        "tol": 1e-6, "check_every": sc.check_every, "mean_sweeps_per_step": mean_sweeps,
                        "max_rel_residual": worst, "parallelism": f"replicas x{world}",
-                       "sor_start": ("previous-step pressure + learned correction (stride-4 U-Net every "
-                                     f"{NET_EVERY} sweeps)" if net is not None else "previous-step pressure"),
+                       "sor_start": (f"previous-step pressure + learned correction (U-Net at stride {net.stride} "
+                                     f"every {NET_EVERY} sweeps)" if net is not None else "previous-step pressure"),
                        "l2": "flushed (256 MiB write) before every timed step"},
             "plain_sor": {"value": n * world / (plain["ms"] * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": plain["ms"],
                           "mean_sweeps_per_step": plain_sweeps, "max_rel_residual": plain["worst"],
@@ -354,7 +354,7 @@ def run_ours(args):
             "learned": None if net is None else {
                 "ms_per_step": ms, "mean_sweeps_per_step": mean_sweeps,
                 "speedup_vs_plain_sor": plain["ms"] / ms, "sweeps_ratio": plain_sweeps / max(mean_sweeps, 1.0),
-                "net_every_sweeps": NET_EVERY, "stride": 4,
+                "net_every_sweeps": NET_EVERY, "stride": net.stride,
                 "weights": os.path.relpath(WEIGHTS, ROOT),
                 "note": "same start state and stop test (FP64 relative residual <= 1e-6 every step); "
                         "network time included"},

@@ -116,7 +116,7 @@ def test_members_match_single_domains_with_learned_correction():
     bit-identical members (the network inference is deterministic)."""
     import os
     from paper_1504_02264_gb300 import train
-    net = train.load(os.path.join(os.path.dirname(les.__file__), "weights", "warmstart_s4.npz"))
+    net = train.load(os.path.join(os.path.dirname(les.__file__), "weights", "warmstart.npz"))
     scs = scenes()
     ens = les.Ensemble(scs)
     ens.set_tile(0, 4)

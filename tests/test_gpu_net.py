@@ -314,13 +314,13 @@ def test_warm_start_rejects_bad_use(net):
 
 
 def test_trained_network_gain():
-    """What the trained network (the package's weights, stride 4) gains over
+    """What the trained network (the package's weights) gains over
     plain SOR on an unseen random city: the same tolerance every step with far
     fewer sweeps and less time per step, network time included."""
     import os
     import time
     from paper_1504_02264_gb300 import train
-    path = os.path.join(os.path.dirname(les.__file__), "weights", "warmstart_s4.npz")
+    path = os.path.join(os.path.dirname(les.__file__), "weights", "warmstart.npz")
     net = train.load(path)
     sc = scene.random_scene(seed=4242, nx=96, ny=96, nz=48, n_buildings=40, x_margin=12, max_sweeps=60000,
                             check_every=20)
