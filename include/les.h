@@ -339,6 +339,13 @@ int les_set_warmstart(les_handle h, int32_t mode, les_net net);
  * start (default).  A value > 0 runs solves from the host loop.  The stop
  * test is unchanged. */
 int les_set_net_schedule(les_handle h, int32_t every_sweeps);
+/* les_set_net_kernels: 1 (default) runs each network correction as one
+ * cooperative persistent launch (pooling, network, prolongation, line search
+ * and step, phases separated by a grid barrier with a bounded wait) when the
+ * device supports cooperative launches; 0 uses one launch per layer.  Both
+ * compute the same correction up to the summation order of the RMS and the
+ * line search. */
+int les_set_net_kernels(les_handle h, int32_t persistent);
 
 /*
  * Ensembles: n domains of uneven size, each with its own buildings, inflow

@@ -128,6 +128,7 @@ struct les_s {
     double n_unk = 0.0;                   // number of Poisson unknowns
     int net_every = 0;                    // sweeps between network corrections inside a solve (0: start only)
     long long net_gen = -1;               // network workspace generation the chunk graphs were captured with
+    bool net_persistent = true;           // run the correction as one cooperative launch when the device can
     bool record = false;
     int rec_after = 0;                    // record at the first refinement after this many sweeps
     bool rec_taken = false;               // the current solve has taken its pair's input
@@ -322,11 +323,21 @@ CondArgs cond_args(const les_s* h, int mode, int n, int gate) {
 // residual may already pass the stop test).
 template <typename T>
 int net_correct(les_s* h, const Geo<T>& g, cudaStream_t st) {
-    int rc = net_predict(h->net, h->d, (const float*)h->rr, h->flags, h->pred, st);
-    if (rc) return fail(h, rc, "network prediction failed");
-    h->launches += net_launches(h->net);
-    h->launches += launch_warm<T>(g, (const T*)h->rr, h->pred, h->ph[h->cur], (T*)nullptr, h->warm_scal + 1,
-                                  reducer(h), st);
+    int rc = LES_EINVAL;
+    if constexpr (std::is_same<T, float>::value)
+        if (h->net_persistent)
+            rc = net_correct_persistent(h->net, g, (const float*)h->rr, nullptr, h->ph[h->cur], h->sc, h->pred,
+                                        h->warm_scal + 1, 1, st);
+    if (rc == LES_OK) {
+        h->launches += 1;
+    } else {
+        if (rc != LES_EINVAL) return fail(h, rc, "persistent network correction failed");
+        rc = net_predict(h->net, h->d, (const float*)h->rr, h->flags, h->pred, st);
+        if (rc) return fail(h, rc, "network prediction failed");
+        h->launches += net_launches(h->net);
+        h->launches += launch_warm<T>(g, (const T*)h->rr, h->pred, h->ph[h->cur], (T*)nullptr, h->warm_scal + 1,
+                                      reducer(h), st);
+    }
     h->launches += launch_residual64<T>(g, h->ph[h->cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h),
                                         cond_args(h, RES_INIT, 0, 0), st);
     CK(cudaGetLastError());
@@ -339,6 +350,17 @@ int net_correct(les_s* h, const Geo<T>& g, cudaStream_t st) {
 // chunk graph, every kernel returns at once when the solve is done.
 template <typename T>
 int net_correct_loop(les_s* h, const Geo<T>& g, cudaStream_t st, bool gated) {
+    if constexpr (std::is_same<T, float>::value)
+        if (h->net_persistent) {
+            // one cooperative launch; it returns at once when the solve is done
+            int rc = net_correct_persistent(h->net, g, (const float*)h->rcur, (float*)h->dl[h->dcur], nullptr, h->sc,
+                                            h->pred, h->warm_scal + 1, 0, st);
+            if (rc == LES_OK) {
+                h->launches += 1;
+                return LES_OK;
+            }
+            if (rc != LES_EINVAL) return fail(h, rc, "persistent network correction failed");
+        }
     int rc = net_predict(h->net, h->d, (const float*)h->rcur, h->flags, h->pred, st, gated ? &h->sc->done : nullptr);
     if (rc) return fail(h, rc, "network prediction failed");
     h->launches += net_launches(h->net);
@@ -1335,6 +1357,13 @@ int les_set_warmstart(les_handle h, int32_t mode, les_net net) {
     }
     h->warm = LES_WARM_NET;
     h->net = net;
+    h->graph_ok[0] = h->graph_ok[1] = false;
+    return LES_OK;
+}
+
+int les_set_net_kernels(les_handle h, int32_t persistent) {
+    if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
+    h->net_persistent = persistent != 0;
     h->graph_ok[0] = h->graph_ok[1] = false;
     return LES_OK;
 }

@@ -152,10 +152,17 @@ struct les_net_s {
     float *rc = nullptr, *mc = nullptr, *tc = nullptr;     // pooled sample (coarse level 0)
     double* dscal = nullptr;            // [0,1] rms / mask sum of r, [2,3] of t, [62] loss, [64..) partials
     long long ws_gen = 0;               // bumped whenever the workspace is reallocated
+    // persistent inference: pooling partials, per-CTA sums, grid barrier state
+    float* part = nullptr;
+    size_t part_cap = 0;
+    double* cta = nullptr;              // [4 * kMaxInferGrid]
+    unsigned* bar = nullptr;            // [2]: count, generation
     char err[256] = {0};
 };
 
 namespace {
+
+constexpr int kMaxInferGrid = 1024;
 
 int nfail(les_net_s* n, int code, const char* msg, cudaError_t e = cudaSuccess) {
     if (n)
@@ -412,11 +419,85 @@ int batch_grad(les_net_s* n, const Level& Lf, const float* r, const float* mask,
 // ===========================================================================
 // solver-side inference (les_api.cu): predicted correction direction on the
 // handle's grid from its padded residual (float) and flags
+namespace {
+// pooling partials of the persistent inference: 2 floats per (coarse cell, dz, dy)
+int ensure_part(les_net_s* n, const Level& L0) {
+    const size_t want = 2 * L0.v() * (size_t)n->stride * n->stride;
+    if (want <= n->part_cap) return LES_OK;
+    NCK(cudaStreamSynchronize(n->stream));
+    if (n->part) cudaFree(n->part);
+    n->part = nullptr;
+    n->part_cap = 0;
+    const size_t cap = want + want / 4 + 64;
+    cudaError_t e = cudaMalloc(&n->part, cap * sizeof(float));
+    if (e != cudaSuccess) return nfail(n, LES_ENOMEM, "inference partials", e);
+    n->part_cap = cap;
+    n->ws_gen += 1;
+    return LES_OK;
+}
+}  // namespace
+
 namespace les {
 int net_prepare(les_net_s* n, const Dom& d, long long* generation) {
-    int rc = ensure_ws(n, coarse(n, Level{d.nx, d.ny, d.nz}));
+    const Level L0 = coarse(n, Level{d.nx, d.ny, d.nz});
+    int rc = ensure_ws(n, L0);
+    if (!rc && nn::net_infer_grid() > 0) rc = ensure_part(n, L0);
     if (generation) *generation = n->ws_gen;
     return rc;
+}
+
+// the whole correction in one cooperative launch; LES_EINVAL when this device
+// cannot run it (the caller then uses the separate kernels)
+int net_correct_persistent(les_net_s* n, const Geo<float>& g, const float* r_padded, float* dl, double* ph,
+                           Scalars* sc, float* q_dense, double* alpha, int mode, cudaStream_t s) {
+    const int grid = nn::net_infer_grid();
+    if (grid <= 0 || grid > kMaxInferGrid) return LES_EINVAL;
+    const Dom& d = g.d;
+    const Level Lf{d.nx, d.ny, d.nz};
+    const Level L0 = coarse(n, Lf);
+    cudaStream_t keep = n->stream;
+    n->stream = s;
+    int rc = ensure_ws(n, L0);
+    if (!rc) rc = ensure_part(n, L0);
+    n->stream = keep;
+    if (rc) return rc;
+    nn::NetInferArgs A{};
+    A.g = g;
+    A.r = r_padded;
+    A.dl = dl;
+    A.ph = ph;
+    A.sc = sc;
+    A.mode = mode;
+    A.S = n->stride;
+    for (int l = 0; l < 4; ++l) {
+        const Level Ll = level(L0, l);
+        A.L[l][0] = Ll.X;
+        A.L[l][1] = Ll.Y;
+        A.L[l][2] = Ll.Z;
+    }
+    A.part = n->part;
+    A.cta = n->cta;
+    A.rc = n->rc;
+    A.mask = n->mask;
+    A.xin = n->xin;
+    for (int l = 0; l < 4; ++l) A.e[l] = n->e[l];
+    for (int l = 0; l < 3; ++l) {
+        A.rr[l] = n->r[l];
+        A.dd[l] = n->dd[l];
+    }
+    for (int c = 0; c < kConvs; ++c) A.wb[c] = n->wb[c];
+    A.head_w = n->w32 + n->off[kConvs];
+    A.y = n->y;
+    A.q = q_dense;
+    A.alpha = alpha;
+    A.bar_count = n->bar;
+    A.bar_gen = n->bar + 1;
+    cudaError_t e = nn::net_infer_launch(A, grid, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return nfail(n, LES_ECUDA, "persistent network correction", e);
+    }
+    return LES_OK;
 }
 long long net_generation(const les_net_s* n) { return n->ws_gen; }
 int net_predict(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, float* out_dense,
@@ -475,7 +556,8 @@ int les_net_create(uint64_t seed, void* stream, les_net* out) {
         return cudaMemsetAsync(*q, 0, bytes, n->stream) == cudaSuccess;
     };
     bool ok = get(n->nparam * 4, (void**)&n->w32) && get(n->nparam * 4, (void**)&n->g32) &&
-              get(n->nparam * 4, (void**)&n->m32) && get(n->nparam * 4, (void**)&n->v32);
+              get(n->nparam * 4, (void**)&n->m32) && get(n->nparam * 4, (void**)&n->v32) &&
+              get(4 * kMaxInferGrid * sizeof(double), (void**)&n->cta) && get(2 * sizeof(unsigned), (void**)&n->bar);
     for (int c = 0; ok && c < kConvs; ++c) {
         const size_t cnt = (size_t)27 * kCin[c] * kCout[c];
         ok = get(cnt * 2, (void**)&n->wb[c]) && get(cnt * 2, (void**)&n->wt[c]);
@@ -498,6 +580,7 @@ void les_net_destroy(les_net n) {
     if (!n) return;
     cudaStreamSynchronize(n->stream);
     free_ws(n);
+    if (n->part) cudaFree(n->part);
     for (void* q : n->owned) cudaFree(q);
     delete n;
 }

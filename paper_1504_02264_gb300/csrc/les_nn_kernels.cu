@@ -83,18 +83,29 @@ struct ConvStage {
 //              zero; summed in the order of the stand-alone pooling kernel, so the
 //              staged values are bit-identical to pooling first)
 enum { IN_DIRECT = 0, IN_UP = 1, IN_POOL = 2 };
+struct ConvArgs {
+    const __nv_bfloat16* x;
+    const __nv_bfloat16* w;
+    __nv_bfloat16* y;
+    const __nv_bfloat16* skip;
+    __nv_bfloat16* ysum;
+    int X, Y, Z, Cin, Cout, relu, Xs, Ys, Zs;
+};
+
+// one output tile: (bx, by) and bz = z tile + ntz * output-channel tile
 template <int CO, int IN>
-__global__ void __launch_bounds__(256)
-k_conv3(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ w, __nv_bfloat16* __restrict__ y,
-        const __nv_bfloat16* __restrict__ skip, __nv_bfloat16* __restrict__ ysum, int X, int Y, int Z, int Cin,
-        int Cout, int relu, const int* gate, int Xs, int Ys, int Zs) {
-    if (gate && *(volatile const int*)gate) return;      // the solve this inference serves has ended
-    extern __shared__ __align__(16) unsigned char conv_smem[];
-    ConvStage<CO>* st = reinterpret_cast<ConvStage<CO>*>(conv_smem);
+__device__ __forceinline__ void conv_tile(const ConvArgs& A, int bx, int by, int bz, ConvStage<CO>* st) {
+    const __nv_bfloat16* __restrict__ x = A.x;
+    const __nv_bfloat16* __restrict__ w = A.w;
+    __nv_bfloat16* __restrict__ y = A.y;
+    const __nv_bfloat16* __restrict__ skip = A.skip;
+    __nv_bfloat16* __restrict__ ysum = A.ysum;
+    const int X = A.X, Y = A.Y, Z = A.Z, Cin = A.Cin, Cout = A.Cout, relu = A.relu;
+    const int Xs = A.Xs, Ys = A.Ys, Zs = A.Zs;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ntz = (Z + TZ - 1) / TZ;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = (blockIdx.z % ntz) * TZ;
-    const int co0 = (blockIdx.z / ntz) * CO;
+    const int x0 = bx * TX, y0 = by * TY, z0 = (bz % ntz) * TZ;
+    const int co0 = (bz / ntz) * CO;
     const int wy = warp % TY, wz = warp / TY;
     auto stage = [&](int c0, ConvStage<CO>& S) {
         for (int q = tid; q < HZ * HY * HX * 2; q += 256) {
@@ -201,6 +212,13 @@ k_conv3(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ w
 }
 
 template <int CO, int IN>
+__global__ void __launch_bounds__(256) k_conv3(ConvArgs A, const int* gate) {
+    if (gate && *(volatile const int*)gate) return;      // the solve this inference serves has ended
+    extern __shared__ __align__(16) unsigned char conv_smem[];
+    conv_tile<CO, IN>(A, blockIdx.x, blockIdx.y, blockIdx.z, reinterpret_cast<ConvStage<CO>*>(conv_smem));
+}
+
+template <int CO, int IN>
 static cudaError_t allow_conv() {
     return cudaFuncSetAttribute(k_conv3<CO, IN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(2 * sizeof(ConvStage<CO>)));
@@ -227,12 +245,11 @@ static void conv3_launch(const __nv_bfloat16* x, const __nv_bfloat16* w, __nv_bf
     const long long tiles = (long long)((X + TX - 1) / TX) * ((Y + TY - 1) / TY) * ntz;
     const int co = (Cout >= 32 && tiles * (Cout / 32) >= 2 * 152) ? 32 : 16;
     dim3 grid((X + TX - 1) / TX, (Y + TY - 1) / TY, ntz * ((Cout + co - 1) / co));
+    const ConvArgs A{x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu, Xs, Ys, Zs};
     if (co == 32)
-        k_conv3<32, IN><<<grid, 256, 2 * sizeof(ConvStage<32>), s>>>(x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu,
-                                                                     gate, Xs, Ys, Zs);
+        k_conv3<32, IN><<<grid, 256, 2 * sizeof(ConvStage<32>), s>>>(A, gate);
     else
-        k_conv3<16, IN><<<grid, 256, 2 * sizeof(ConvStage<16>), s>>>(x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu,
-                                                                     gate, Xs, Ys, Zs);
+        k_conv3<16, IN><<<grid, 256, 2 * sizeof(ConvStage<16>), s>>>(A, gate);
 }
 
 void conv3_fwd(const __nv_bfloat16* x, const __nv_bfloat16* w, __nv_bfloat16* y, const __nv_bfloat16* skip,
@@ -713,6 +730,325 @@ void adam(float* w, float* m, float* v, const float* g, __nv_bfloat16* wb, size_
 }
 void to_bf16(const float* a, __nv_bfloat16* b, size_t n, cudaStream_t s) {
     k_to_bf16<<<blocks_for(n), 256, 0, s>>>(a, b, n);
+}
+
+// ---------------------------------------------------------------------------
+// persistent network correction (one cooperative launch)
+
+__device__ __forceinline__ uint64_t nn_global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// sense-counting grid barrier with a bounded wait (1 s); returns false (and
+// records a timeout) if the other CTAs did not arrive in time
+__device__ bool grid_barrier(unsigned* count, unsigned* gen, Scalars* sc) {
+    __shared__ int ok_sh;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned g0 = *(volatile unsigned*)gen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(count, 1u) == gridDim.x - 1) {
+            *(volatile unsigned*)count = 0u;
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            const uint64_t t0 = nn_global_ns();
+            while (*(volatile unsigned*)gen == g0)
+                if (nn_global_ns() - t0 > 1000000000ull) {
+                    ok = 0;
+                    atomicExch(&sc->timeout, 1);
+                    break;
+                }
+        }
+        __threadfence();
+        ok_sh = ok;
+    }
+    __syncthreads();
+    return ok_sh != 0;
+}
+
+// block sum of NV doubles (fixed order), result on thread 0
+template <int NV>
+__device__ __forceinline__ void nn_block_sum(double (&x)[NV]) {
+    __shared__ double sh[NV][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+        for (int o = 16; o > 0; o >>= 1) x[q] += __shfl_down_sync(0xffffffffu, x[q], o);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) sh[q][warp] = x[q];
+    __syncthreads();
+    if (warp == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            x[q] = lane < nw ? sh[q][lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) x[q] += __shfl_down_sync(0xffffffffu, x[q], o);
+        }
+}
+
+template <int IN>
+__device__ void conv_phase(const ConvArgs& A, ConvStage<16>* st) {
+    const int ntx = (A.X + TX - 1) / TX, nty = (A.Y + TY - 1) / TY, ntz = (A.Z + TZ - 1) / TZ;
+    const int tiles = ntx * nty * ntz * (A.Cout / 16);
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+        conv_tile<16, IN>(A, t % ntx, (t / ntx) % nty, t / (ntx * nty), st);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_net_infer(const __grid_constant__ NetInferArgs A) {
+    extern __shared__ __align__(16) unsigned char infer_smem[];
+    ConvStage<16>* st = reinterpret_cast<ConvStage<16>*>(infer_smem);
+    Scalars* sc = A.sc;
+    if (sc->done) return;                                  // uniform: the solve has ended
+    const Dom& d = A.g.d;
+    const int S = A.S;
+    const int Xc = A.L[0][0], Yc = A.L[0][1], Zc = A.L[0][2];
+    const int nc = Xc * Yc * Zc;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+    const bool zero_before = sc->zflag != 0;               // read once, before anyone changes it
+    // 1. pooling partials: item = (coarse cell, dz, dy), S fine cells in x
+    for (int it = gt; it < nc * S * S; it += gs) {
+        const int c = it / (S * S), dz = (it / S) % S, dy = it % S;
+        const int cx = c % Xc, cy = (c / Xc) % Yc, cz = c / (Xc * Yc);
+        const int fy = cy * S + dy, fz = cz * S + dz;
+        float ar = 0.f, am = 0.f;
+        if (fy < d.ny && fz < d.nz) {
+            const long long row = d.at(1, fy + 1, fz + 1) + (long long)cx * S;
+            for (int dx = 0; dx < S; ++dx)
+                if (cx * S + dx < d.nx && (A.g.flags[row + dx] & F_UNK)) {
+                    ar += A.r[row + dx];
+                    am += 1.f;
+                }
+        }
+        A.part[2 * it] = ar;
+        A.part[2 * it + 1] = am;
+    }
+    if (!grid_barrier(A.bar_count, A.bar_gen, sc)) return;
+    // 2. coarse residual and mask (partials added in a fixed order), RMS partials per CTA
+    double rs[2] = {0.0, 0.0};
+    const float inv = 1.f / (float)(S * S * S);
+    for (int c = gt; c < nc; c += gs) {
+        float ar = 0.f, am = 0.f;
+        for (int q = 0; q < S * S; ++q) {
+            ar += A.part[2 * (c * S * S + q)];
+            am += A.part[2 * (c * S * S + q) + 1];
+        }
+        const float rv = ar * inv, mv = am * inv;
+        A.rc[c] = rv;
+        A.mask[c] = mv;
+        rs[0] += (double)mv * (double)rv * (double)rv;
+        rs[1] += (double)mv;
+    }
+    nn_block_sum<2>(rs);
+    if (threadIdx.x == 0) {
+        A.cta[2 * blockIdx.x] = rs[0];
+        A.cta[2 * blockIdx.x + 1] = rs[1];
+    }
+    if (!grid_barrier(A.bar_count, A.bar_gen, sc)) return;
+    // 3. RMS (every CTA adds the CTA partials in the same order) and the packed input
+    double ts = 0.0, tm = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+        ts += A.cta[2 * b];
+        tm += A.cta[2 * b + 1];
+    }
+    const double rms = tm > 0.0 ? sqrt(ts / tm) : 0.0;
+    const float scale = (float)(rms > 0.0 ? 1.0 / rms : 0.0);
+    for (int c = gt; c < nc; c += gs) {
+        __align__(16) __nv_bfloat16 o[16];
+        o[0] = __float2bfloat16(A.mask[c] * A.rc[c] * scale);
+        o[1] = __float2bfloat16(A.mask[c]);
+#pragma unroll
+        for (int ch = 2; ch < 16; ++ch) o[ch] = __float2bfloat16(0.f);
+        uint4* dst = reinterpret_cast<uint4*>(A.xin + (size_t)c * 16);
+        dst[0] = reinterpret_cast<const uint4*>(o)[0];
+        dst[1] = reinterpret_cast<const uint4*>(o)[1];
+    }
+    if (!grid_barrier(A.bar_count, A.bar_gen, sc)) return;
+    // 4. the U-Net
+    const int(*L)[3] = A.L;
+    {
+        const ConvArgs c0{A.xin, A.wb[0], A.e[0], nullptr, nullptr, L[0][0], L[0][1], L[0][2], 16, 16, 1,
+                          L[0][0], L[0][1], L[0][2]};
+        conv_phase<IN_DIRECT>(c0, st);
+    }
+    if (!grid_barrier(A.bar_count, A.bar_gen, sc)) return;
+    {
+        const ConvArgs c1{A.e[0], A.wb[1], A.e[1], nullptr, nullptr, L[1][0], L[1][1], L[1][2], 16, 32, 1,
+                          L[0][0], L[0][1], L[0][2]};
+        conv_phase<IN_POOL>(c1, st);
+    }
+    if (!grid_barrier(A.bar_count, A.bar_gen, sc)) return;
+    {
+        const ConvArgs c2{A.e[1], A.wb[2], A.e[2], nullptr, nullptr, L[2][0], L[2][1], L[2][2], 32, 64, 1,
+                          L[1][0], L[1][1], L[1][2]};
+        conv_phase<IN_POOL>(c2, st);
+    }
+    if (!grid_barrier(A.bar_count, A.bar_gen, sc)) return;
+    {
+        const ConvArgs c3{A.e[2], A.wb[3], A.e[3], nullptr, nullptr, L[3][0], L[3][1], L[3][2], 64, 128, 1,
+                          L[2][0], L[2][1], L[2][2]};
+        conv_phase<IN_POOL>(c3, st);
+    }
+    if (!grid_barrier(A.bar_count, A.bar_gen, sc)) return;
+    {
+        const ConvArgs c4{A.e[3], A.wb[4], A.rr[2], A.e[2], A.dd[2], L[2][0], L[2][1], L[2][2], 128, 64, 1,
+                          L[3][0], L[3][1], L[3][2]};
+        conv_phase<IN_UP>(c4, st);
+    }
+    if (!grid_barrier(A.bar_count, A.bar_gen, sc)) return;
+    {
+        const ConvArgs c5{A.dd[2], A.wb[5], A.rr[1], A.e[1], A.dd[1], L[1][0], L[1][1], L[1][2], 64, 32, 1,
+                          L[2][0], L[2][1], L[2][2]};
+        conv_phase<IN_UP>(c5, st);
+    }
+    if (!grid_barrier(A.bar_count, A.bar_gen, sc)) return;
+    {
+        const ConvArgs c6{A.dd[1], A.wb[6], A.rr[0], A.e[0], A.dd[0], L[0][0], L[0][1], L[0][2], 32, 16, 1,
+                          L[1][0], L[1][1], L[1][2]};
+        conv_phase<IN_UP>(c6, st);
+    }
+    if (!grid_barrier(A.bar_count, A.bar_gen, sc)) return;
+    // 5. head
+    for (int c = gt; c < nc; c += gs) {
+        float sacc = 0.f;
+        for (int ch = 0; ch < 16; ++ch) sacc += A.head_w[ch] * __bfloat162float(A.dd[0][(size_t)c * 16 + ch]);
+        A.y[c] = A.mask[c] * sacc;
+    }
+    if (!grid_barrier(A.bar_count, A.bar_gen, sc)) return;
+    // 6. trilinear prolongation on the unknowns: item = S fine cells of a row
+    for (int it = gt; it < Xc * d.ny * d.nz; it += gs) {
+        const int cx = it % Xc, yz = it / Xc, fy = yz % d.ny, fz = yz / d.ny;
+        int y0, z0;
+        float wy, wz;
+        lin_w(fy, S, Yc, y0, wy);
+        lin_w(fz, S, Zc, z0, wz);
+        const int y1 = min(y0 + 1, Yc - 1), z1 = min(z0 + 1, Zc - 1);
+        auto col = [&](int c) {
+            c = max(0, min(c, Xc - 1));
+            auto at = [&](int b, int cc) { return A.y[((size_t)cc * Yc + b) * Xc + c]; };
+            const float a0 = (1.f - wy) * at(y0, z0) + wy * at(y1, z0);
+            const float a1 = (1.f - wy) * at(y0, z1) + wy * at(y1, z1);
+            return (1.f - wz) * a0 + wz * a1;
+        };
+        const float cm = col(cx - 1), c0v = col(cx), cp = col(cx + 1);
+        const long long row = d.at(1, fy + 1, fz + 1);
+        float* o = A.q + ((size_t)fz * d.ny + fy) * d.nx;
+        for (int m = 0; m < S; ++m) {
+            const int x = cx * S + m;
+            if (x >= d.nx) break;
+            int x0;
+            float wx;
+            lin_w(x, S, Xc, x0, wx);
+            const int x1 = min(x0 + 1, Xc - 1);
+            const float v0 = x0 < cx ? cm : (x0 == cx ? c0v : cp);
+            const float v1 = x1 < cx ? cm : (x1 == cx ? c0v : cp);
+            o[x] = (A.g.flags[row + x] & F_UNK) ? (1.f - wx) * v0 + wx * v1 : 0.f;
+        }
+    }
+    if (!grid_barrier(A.bar_count, A.bar_gen, sc)) return;
+    // 7. energy-norm line search: <q, V r> / <q, V A q> (CTA partials, fixed order)
+    const Geo<float>& g = A.g;
+    const int n = d.nx * d.ny * d.nz, sy = d.nx, sz = d.nx * d.ny;
+    float l0 = 0.f, l1 = 0.f;
+    for (int v = gt; v < n; v += gs) {
+        const int i = v % d.nx + 1, j = (v / d.nx) % d.ny + 1, k = v / sz + 1;
+        const long long c = d.at(i, j, k);
+        const uint8_t f = g.flags[c];
+        if (!(f & F_UNK)) continue;
+        const int oe = (d.perx && i == d.nx) ? -(d.nx - 1) : 1;
+        const int ow = (d.perx && i == 1) ? (d.nx - 1) : -1;
+        const int on = (d.pery && j == d.ny) ? -(d.ny - 1) * sy : sy;
+        const int os = (d.pery && j == 1) ? (d.ny - 1) * sy : -sy;
+        const int ot = (d.perz && k == d.nz) ? -(d.nz - 1) * sz : sz;
+        const int ob = (d.perz && k == 1) ? (d.nz - 1) * sz : -sz;
+        const float qc = A.q[v];
+        float aq = 0.f;
+        if (f & F_E) aq += g.cx * (A.q[v + oe] - qc);
+        if (f & F_W) aq += g.cx * (A.q[v + ow] - qc);
+        if (f & F_N) aq += g.cy * (A.q[v + on] - qc);
+        if (f & F_S) aq += g.cy * (A.q[v + os] - qc);
+        if (f & F_T) aq += g.cT[k] * (A.q[v + ot] - qc);
+        if (f & F_B) aq += g.cB[k] * (A.q[v + ob] - qc);
+        const float vq = g.dz[k] * qc;
+        l0 += vq * A.r[c];
+        l1 += vq * aq;
+    }
+    double ls[2] = {(double)l0, (double)l1};
+    nn_block_sum<2>(ls);
+    if (threadIdx.x == 0) {
+        A.cta[2 * gridDim.x + 2 * blockIdx.x] = ls[0];
+        A.cta[2 * gridDim.x + 2 * blockIdx.x + 1] = ls[1];
+    }
+    if (!grid_barrier(A.bar_count, A.bar_gen, sc)) return;
+    // 8. the step (every CTA forms alpha from the same partials in the same order)
+    double s0 = 0.0, s1 = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+        s0 += A.cta[2 * gridDim.x + 2 * b];
+        s1 += A.cta[2 * gridDim.x + 2 * b + 1];
+    }
+    const double ad = s0 / s1;
+    const double alpha = (s1 != 0.0 && isfinite(ad)) ? ad : 0.0;
+    if (gt == 0) *A.alpha = alpha;
+    const float af = (float)alpha;
+    for (int v = gt; v < n; v += gs) {
+        const int i = v % d.nx + 1, j = (v / d.nx) % d.ny + 1, k = v / sz + 1;
+        const long long c = d.at(i, j, k);
+        if (!(g.flags[c] & F_UNK)) continue;
+        if (A.mode == 0) {
+            const float base = zero_before ? 0.f : A.dl[c];
+            A.dl[c] = base + af * A.q[v];
+        } else {
+            A.ph[c] += alpha * (double)A.q[v];
+        }
+    }
+    if (A.mode == 0 && gt == 0) {
+        // the correction now holds the step: the next sweeps must read it
+        sc->zcopy = zero_before ? 1 : 0;
+        sc->zflag = 0;
+    }
+}
+
+int net_infer_grid() {
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 0;
+    if (cached[dev]) return cached[dev] > 0 ? cached[dev] : 0;
+    int coop = 0, sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int smem = (int)(2 * sizeof(ConvStage<16>));
+    if (cudaFuncSetAttribute(k_net_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_net_infer, 256, smem) != cudaSuccess || !coop ||
+        per_sm < 1) {
+        cudaGetLastError();
+        cached[dev] = -1;
+        return 0;
+    }
+    cached[dev] = sms;          // one CTA per SM: cheap barriers, enough for the coarse grid
+    return sms;
+}
+
+cudaError_t net_infer_launch(const NetInferArgs& a, int grid, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 2 * sizeof(ConvStage<16>);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaMemsetAsync(a.bar_count, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernelEx(&cfg, k_net_infer, a);
 }
 
 }  // namespace nn

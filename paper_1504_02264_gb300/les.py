@@ -104,6 +104,7 @@ def lib(build_if_missing: bool = False):
         L.les_time_sor.argtypes = [vp, i32, i32, i32, ctypes.POINTER(ctypes.c_double)]
         L.les_set_record.argtypes = [vp, i32]
         L.les_set_record_at.argtypes = [vp, i32]
+        L.les_set_net_kernels.argtypes = [vp, i32]
         L.les_set_net_schedule.argtypes = [vp, i32]
         L.les_set_warmstart.argtypes = [vp, i32, vp]
         L.les_net_create.argtypes = [ctypes.c_uint64, vp, ctypes.POINTER(vp)]
@@ -129,7 +130,7 @@ def lib(build_if_missing: bool = False):
         L.les_get_timing.argtypes = [vp, ctypes.POINTER(les_timing_t)]
         for name in ("les_ensemble_create", "les_ensemble_size", "les_ensemble_member", "les_ensemble_step",
                      "les_ensemble_set_graph", "les_ensemble_set_tile", "les_ensemble_get_tile",
-                     "les_ensemble_autotune", "les_ensemble_launches", "les_ensemble_set_warmstart", "les_selftest_wait_timeout", "les_time_sor", "les_set_record", "les_set_record_at", "les_set_net_schedule", "les_set_warmstart",
+                     "les_ensemble_autotune", "les_ensemble_launches", "les_ensemble_set_warmstart", "les_selftest_wait_timeout", "les_time_sor", "les_set_net_kernels", "les_set_record", "les_set_record_at", "les_set_net_schedule", "les_set_warmstart",
                      "les_net_create", "les_net_num_params", "les_net_set_stride", "les_net_get_stride",
                      "les_net_get_params", "les_net_set_params", "les_net_forward", "les_net_gradient",
                      "les_net_train_step", "les_residual_noalloc", "les_profiler_range", "les_set_graph",
@@ -582,6 +583,9 @@ class Domain:
 
     def set_net_schedule(self, every_sweeps):
         les_set_net_schedule(self.h, every_sweeps)
+
+    def set_net_kernels(self, persistent=True):
+        _check(lib().les_set_net_kernels(self.h, 1 if persistent else 0), self.h)
 
     def set_warmstart(self, net=None, mode=None):
         """net given: learned warm start; else mode LES_WARM_PREV (default) or LES_WARM_ZERO."""

@@ -146,7 +146,7 @@ def train(net: les.Net, data, iters: int, batch: int, lr: float, seed: int = 0, 
     return hist
 
 
-def evaluate(net: les.Net | None, sc, steps: int, spinup: int, schedules=(0,), log=print):
+def evaluate(net: les.Net | None, sc, steps: int, spinup: int, schedules=(0,), log=print, persistent=True):
     """Sweeps and milliseconds per step to the scene's tolerance for the
     previous-step start and, with a network, for each correction schedule
     (0 = one-shot warm start; m > 0 = also every m sweeps).  All runs start
@@ -167,6 +167,7 @@ def evaluate(net: les.Net | None, sc, steps: int, spinup: int, schedules=(0,), l
         if m is not None:
             dom.set_warmstart(net)
             dom.set_net_schedule(m)
+            dom.set_net_kernels(persistent)
         sweeps, ms, ok = [], [], True
         for _ in range(steps):
             torch.cuda.synchronize()
@@ -206,6 +207,7 @@ def main(argv=None):
     ap.add_argument("--schedules", default="0,50,100,200")
     ap.add_argument("--json", default=None, help="write the evaluation here")
     ap.add_argument("--eval-only", default=None, help="evaluate these trained networks (.npz, comma separated)")
+    ap.add_argument("--layer-kernels", action="store_true", help="evaluate with one launch per network layer")
     ap.add_argument("--dagger", default=None, help="also record pairs with this network in the loop (.npz)")
     ap.add_argument("--dagger-every", type=int, default=10)
     ap.add_argument("--dagger-points", default="0,10,20,30,50,80,120,200")
@@ -219,7 +221,8 @@ def main(argv=None):
             net = load(path)
             print(f"{path} (stride {net.stride}) on {ev_sc.name} seed {ev_sc.seed}:", flush=True)
             report["nets"][path] = evaluate(net, ev_sc, a.eval_steps, a.eval_spinup,
-                                            [int(x) for x in a.schedules.split(",")])
+                                            [int(x) for x in a.schedules.split(",")],
+                                            persistent=not a.layer_kernels)
             net.close()
         print(json.dumps(report), flush=True)
         if a.json:

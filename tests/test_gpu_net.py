@@ -299,6 +299,31 @@ def test_net_cycle_graph_matches_host_loop(net, stride):
         d.close()
 
 
+def test_persistent_and_layer_kernels_agree(net):
+    """The one-launch network correction and the per-layer launches compute
+    the same correction (up to summation order): both converge every step with
+    sweep counts within a few batches of each other."""
+    net.stride = 4
+    sc = city(tol=1e-6, max_sweeps=40000, check_every=20)
+    out = {}
+    for persistent in (True, False):
+        d = les.Domain(sc)
+        d.set_warmstart(net)
+        d.set_net_schedule(20)
+        d.set_net_kernels(persistent)
+        sw = []
+        for _ in range(3):
+            st = d.step()
+            assert st["rc"] == 0 and st["rel_residual"] <= 1e-6
+            sw.append(st["sweeps"])
+        out[persistent] = (sw, d.fields()[0])
+        d.close()
+    for a, b in zip(out[True][0], out[False][0]):
+        assert abs(a - b) <= 60, out
+    u1, u2 = out[True][1], out[False][1]
+    assert np.abs(u1 - u2).max() <= 1e-3 * np.abs(u2).max()
+
+
 def test_warm_start_rejects_bad_use(net):
     sc = city()
     d64 = les.Domain(sc, precision=les.LES_FP64)
