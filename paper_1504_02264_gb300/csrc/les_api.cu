@@ -321,23 +321,29 @@ CondArgs cond_args(const les_s* h, int mode, int n, int gate) {
 // the energy-norm line search, then form the FP64 residual again (`mode` is
 // RES_INIT at the start of a solve, RES_LOOP inside it, where the new
 // residual may already pass the stop test).
+// the network's prediction q of the correction for residual r: the coarse
+// network as one cooperative launch when the device can, else per layer
+int predict(les_s* h, const float* r, cudaStream_t st, const int* gate) {
+    if (h->net_persistent) {
+        int rc = net_predict_persistent(h->net, h->d, r, h->flags, h->pred, h->sc, gate, st);
+        if (rc == LES_OK) {
+            h->launches += net_persistent_launches();
+            return LES_OK;
+        }
+        if (rc != LES_EINVAL) return fail(h, rc, "persistent network prediction failed");
+    }
+    int rc = net_predict(h->net, h->d, r, h->flags, h->pred, st, gate);
+    if (rc) return fail(h, rc, "network prediction failed");
+    h->launches += net_launches(h->net);
+    return LES_OK;
+}
+
 template <typename T>
 int net_correct(les_s* h, const Geo<T>& g, cudaStream_t st) {
-    int rc = LES_EINVAL;
-    if constexpr (std::is_same<T, float>::value)
-        if (h->net_persistent)
-            rc = net_correct_persistent(h->net, g, (const float*)h->rr, nullptr, h->ph[h->cur], h->sc, h->pred,
-                                        h->warm_scal + 1, 1, st);
-    if (rc == LES_OK) {
-        h->launches += 1;
-    } else {
-        if (rc != LES_EINVAL) return fail(h, rc, "persistent network correction failed");
-        rc = net_predict(h->net, h->d, (const float*)h->rr, h->flags, h->pred, st);
-        if (rc) return fail(h, rc, "network prediction failed");
-        h->launches += net_launches(h->net);
-        h->launches += launch_warm<T>(g, (const T*)h->rr, h->pred, h->ph[h->cur], (T*)nullptr, h->warm_scal + 1,
-                                      reducer(h), st);
-    }
+    int rc = predict(h, (const float*)h->rr, st, nullptr);
+    if (rc) return rc;
+    h->launches += launch_warm<T>(g, (const T*)h->rr, h->pred, h->ph[h->cur], (T*)nullptr, h->warm_scal + 1,
+                                  reducer(h), st);
     h->launches += launch_residual64<T>(g, h->ph[h->cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h),
                                         cond_args(h, RES_INIT, 0, 0), st);
     CK(cudaGetLastError());
@@ -350,20 +356,8 @@ int net_correct(les_s* h, const Geo<T>& g, cudaStream_t st) {
 // chunk graph, every kernel returns at once when the solve is done.
 template <typename T>
 int net_correct_loop(les_s* h, const Geo<T>& g, cudaStream_t st, bool gated) {
-    if constexpr (std::is_same<T, float>::value)
-        if (h->net_persistent) {
-            // one cooperative launch; it returns at once when the solve is done
-            int rc = net_correct_persistent(h->net, g, (const float*)h->rcur, (float*)h->dl[h->dcur], nullptr, h->sc,
-                                            h->pred, h->warm_scal + 1, 0, st);
-            if (rc == LES_OK) {
-                h->launches += 1;
-                return LES_OK;
-            }
-            if (rc != LES_EINVAL) return fail(h, rc, "persistent network correction failed");
-        }
-    int rc = net_predict(h->net, h->d, (const float*)h->rcur, h->flags, h->pred, st, gated ? &h->sc->done : nullptr);
-    if (rc) return fail(h, rc, "network prediction failed");
-    h->launches += net_launches(h->net);
+    int rc = predict(h, (const float*)h->rcur, st, gated ? &h->sc->done : nullptr);
+    if (rc) return rc;
     h->launches += launch_warm<T>(g, (const T*)h->rcur, h->pred, nullptr, (T*)h->dl[h->dcur], h->warm_scal + 1,
                                   reducer(h), st);
     CK(cudaGetLastError());

@@ -262,9 +262,10 @@ int net_launches(const les_net_s* n);
 // holding the old buffers must then be rebuilt)
 int net_prepare(les_net_s* n, const Dom& d, long long* generation);
 long long net_generation(const les_net_s* n);
-// the whole correction (pool, network, prolongation, line search, step) in one
-// cooperative persistent launch; mode 0 steps the SOR correction dl (inside the
-// loop), mode 1 the FP64 pressure ph; LES_EINVAL if the device cannot run it
-int net_correct_persistent(les_net_s* n, const Geo<float>& g, const float* r_padded, float* dl, double* ph,
-                           Scalars* sc, float* q_dense, double* alpha, int mode, cudaStream_t s);
+// the prediction with the coarse network as one cooperative persistent launch
+// (pool and prolongation as full-grid kernels around it); LES_EINVAL if the
+// device cannot run it
+int net_predict_persistent(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, float* q_dense,
+                           Scalars* sc, const int* gate, cudaStream_t s);
+int net_persistent_launches();
 }  // namespace les

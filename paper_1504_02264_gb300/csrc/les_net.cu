@@ -152,9 +152,7 @@ struct les_net_s {
     float *rc = nullptr, *mc = nullptr, *tc = nullptr;     // pooled sample (coarse level 0)
     double* dscal = nullptr;            // [0,1] rms / mask sum of r, [2,3] of t, [62] loss, [64..) partials
     long long ws_gen = 0;               // bumped whenever the workspace is reallocated
-    // persistent inference: pooling partials, per-CTA sums, grid barrier state
-    float* part = nullptr;
-    size_t part_cap = 0;
+    // persistent inference: per-CTA sums, grid barrier state
     double* cta = nullptr;              // [4 * kMaxInferGrid]
     unsigned* bar = nullptr;            // [2]: count, generation
     char err[256] = {0};
@@ -419,66 +417,43 @@ int batch_grad(les_net_s* n, const Level& Lf, const float* r, const float* mask,
 // ===========================================================================
 // solver-side inference (les_api.cu): predicted correction direction on the
 // handle's grid from its padded residual (float) and flags
-namespace {
-// pooling partials of the persistent inference: 2 floats per (coarse cell, dz, dy)
-int ensure_part(les_net_s* n, const Level& L0) {
-    const size_t want = 2 * L0.v() * (size_t)n->stride * n->stride;
-    if (want <= n->part_cap) return LES_OK;
-    NCK(cudaStreamSynchronize(n->stream));
-    if (n->part) cudaFree(n->part);
-    n->part = nullptr;
-    n->part_cap = 0;
-    const size_t cap = want + want / 4 + 64;
-    cudaError_t e = cudaMalloc(&n->part, cap * sizeof(float));
-    if (e != cudaSuccess) return nfail(n, LES_ENOMEM, "inference partials", e);
-    n->part_cap = cap;
-    n->ws_gen += 1;
-    return LES_OK;
-}
-}  // namespace
 
 namespace les {
 int net_prepare(les_net_s* n, const Dom& d, long long* generation) {
     const Level L0 = coarse(n, Level{d.nx, d.ny, d.nz});
     int rc = ensure_ws(n, L0);
-    if (!rc && nn::net_infer_grid() > 0) rc = ensure_part(n, L0);
     if (generation) *generation = n->ws_gen;
     return rc;
 }
 
-// the whole correction in one cooperative launch; LES_EINVAL when this device
-// cannot run it (the caller then uses the separate kernels)
-int net_correct_persistent(les_net_s* n, const Geo<float>& g, const float* r_padded, float* dl, double* ph,
-                           Scalars* sc, float* q_dense, double* alpha, int mode, cudaStream_t s) {
+// the network prediction with the coarse network as one cooperative launch:
+// pool (full grid) -> network (persistent) -> prolongation (full grid); the
+// caller adds the line search and step.  LES_EINVAL when this device cannot
+// run the cooperative launch (the caller then uses the per-layer launches).
+int net_predict_persistent(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, float* q_dense,
+                           Scalars* sc, const int* gate, cudaStream_t s) {
     const int grid = nn::net_infer_grid();
     if (grid <= 0 || grid > kMaxInferGrid) return LES_EINVAL;
-    const Dom& d = g.d;
     const Level Lf{d.nx, d.ny, d.nz};
     const Level L0 = coarse(n, Lf);
     cudaStream_t keep = n->stream;
     n->stream = s;
     int rc = ensure_ws(n, L0);
-    if (!rc) rc = ensure_part(n, L0);
     n->stream = keep;
     if (rc) return rc;
+    nn::pool_padded_s(r_padded, flags, d, n->stride, n->rc, n->mc, s, gate);
     nn::NetInferArgs A{};
-    A.g = g;
-    A.r = r_padded;
-    A.dl = dl;
-    A.ph = ph;
+    A.gate = gate;
     A.sc = sc;
-    A.mode = mode;
-    A.S = n->stride;
     for (int l = 0; l < 4; ++l) {
         const Level Ll = level(L0, l);
         A.L[l][0] = Ll.X;
         A.L[l][1] = Ll.Y;
         A.L[l][2] = Ll.Z;
     }
-    A.part = n->part;
     A.cta = n->cta;
     A.rc = n->rc;
-    A.mask = n->mask;
+    A.mask = n->mc;
     A.xin = n->xin;
     for (int l = 0; l < 4; ++l) A.e[l] = n->e[l];
     for (int l = 0; l < 3; ++l) {
@@ -488,17 +463,21 @@ int net_correct_persistent(les_net_s* n, const Geo<float>& g, const float* r_pad
     for (int c = 0; c < kConvs; ++c) A.wb[c] = n->wb[c];
     A.head_w = n->w32 + n->off[kConvs];
     A.y = n->y;
-    A.q = q_dense;
-    A.alpha = alpha;
     A.bar_count = n->bar;
     A.bar_gen = n->bar + 1;
     cudaError_t e = nn::net_infer_launch(A, grid, s);
+    if (e == cudaSuccess) {
+        nn::prolong_flags(n->y, flags, d, n->stride, q_dense, s, gate);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return nfail(n, LES_ECUDA, "persistent network correction", e);
+        return nfail(n, LES_ECUDA, "persistent network prediction", e);
     }
     return LES_OK;
 }
+int net_persistent_launches() { return 4; }     // pool, barrier reset, network, prolongation
+
 long long net_generation(const les_net_s* n) { return n->ws_gen; }
 int net_predict(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, float* out_dense,
                 cudaStream_t s, const int* gate) {
@@ -580,7 +559,6 @@ void les_net_destroy(les_net n) {
     if (!n) return;
     cudaStreamSynchronize(n->stream);
     free_ws(n);
-    if (n->part) cudaFree(n->part);
     for (void* q : n->owned) cudaFree(q);
     delete n;
 }

@@ -51,24 +51,18 @@ void adam(float* w, float* m, float* v, const float* g, __nv_bfloat16* wb, size_
           float eps, float c1, float c2, cudaStream_t s);
 void to_bf16(const float* a, __nv_bfloat16* b, size_t n, cudaStream_t s);
 
-// The whole network correction of the solver in one cooperative persistent
-// launch: pooling of the residual, RMS, packing, the seven convolutions (pooling
-// and upsampling folded into their staging), head, prolongation, the
-// energy-norm line search and the step, phases separated by a bounded grid
-// barrier.  mode 0: the step goes into the SOR correction dl (inside the
-// loop, with the zero-flag hand-off); mode 1: into the FP64 pressure ph.
+// The coarse network of the solver's correction in one cooperative persistent
+// launch: RMS of the pooled residual, packing, the seven convolutions (pooling
+// and upsampling folded into their staging) and the head, phases separated by
+// a bounded grid barrier.  Pooling before it and prolongation, line search and
+// step after it are ordinary full-grid kernels.
 struct NetInferArgs {
-    Geo<float> g;                   // the solver grid (flags, coefficients, Dom)
-    const float* r;                 // padded residual
-    float* dl;                      // mode 0 target
-    double* ph;                     // mode 1 target
-    Scalars* sc;
-    int mode, S;
+    const int* gate;                // the solve's done flag (kernel returns at once when set; nullable)
+    Scalars* sc;                    // timeout record of the grid barrier
     int L[4][3];                    // level dims (X, Y, Z); level 0 = coarse grid of the network
-    float* part;                    // [2 * Xc*Yc*Zc*S*S] pooling partials
-    double* cta;                    // [4 * grid] per-CTA partial sums
-    float* rc;                      // coarse residual
-    float* mask;                    // coarse unknown fraction
+    double* cta;                    // [2 * grid] per-CTA partial sums
+    const float* rc;                // pooled residual
+    const float* mask;              // pooled unknown fraction
     __nv_bfloat16* xin;
     __nv_bfloat16* e[4];
     __nv_bfloat16* rr[3];
@@ -76,8 +70,6 @@ struct NetInferArgs {
     const __nv_bfloat16* wb[7];
     const float* head_w;
     float* y;                       // coarse output
-    float* q;                       // dense fine prediction
-    double* alpha;
     unsigned* bar_count;            // grid barrier state (count zeroed before each launch)
     unsigned* bar_gen;
 };

@@ -801,49 +801,25 @@ __device__ void conv_phase(const ConvArgs& A, ConvStage<16>* st) {
     }
 }
 
+// the coarse network in one launch: RMS of the pooled residual, packing, the
+// seven convolutions (pooling / upsampling folded into their staging) and the
+// head, phases separated by the grid barrier.  The pooled residual and mask
+// come from the pooling kernel; prolongation, line search and step follow as
+// ordinary full-grid kernels.
 __global__ void __launch_bounds__(256) k_net_infer(const __grid_constant__ NetInferArgs A) {
     extern __shared__ __align__(16) unsigned char infer_smem[];
     ConvStage<16>* st = reinterpret_cast<ConvStage<16>*>(infer_smem);
     Scalars* sc = A.sc;
-    if (sc->done) return;                                  // uniform: the solve has ended
-    const Dom& d = A.g.d;
-    const int S = A.S;
+    if (A.gate && *(volatile const int*)A.gate) return;      // uniform: the solve has ended
     const int Xc = A.L[0][0], Yc = A.L[0][1], Zc = A.L[0][2];
     const int nc = Xc * Yc * Zc;
     const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
-    const bool zero_before = sc->zflag != 0;               // read once, before anyone changes it
-    // 1. pooling partials: item = (coarse cell, dz, dy), S fine cells in x
-    for (int it = gt; it < nc * S * S; it += gs) {
-        const int c = it / (S * S), dz = (it / S) % S, dy = it % S;
-        const int cx = c % Xc, cy = (c / Xc) % Yc, cz = c / (Xc * Yc);
-        const int fy = cy * S + dy, fz = cz * S + dz;
-        float ar = 0.f, am = 0.f;
-        if (fy < d.ny && fz < d.nz) {
-            const long long row = d.at(1, fy + 1, fz + 1) + (long long)cx * S;
-            for (int dx = 0; dx < S; ++dx)
-                if (cx * S + dx < d.nx && (A.g.flags[row + dx] & F_UNK)) {
-                    ar += A.r[row + dx];
-                    am += 1.f;
-                }
-        }
-        A.part[2 * it] = ar;
-        A.part[2 * it + 1] = am;
-    }
-    if (!grid_barrier(A.bar_count, A.bar_gen, sc)) return;
-    // 2. coarse residual and mask (partials added in a fixed order), RMS partials per CTA
+    // 1. RMS partials per CTA: sum mask r^2 and sum mask
     double rs[2] = {0.0, 0.0};
-    const float inv = 1.f / (float)(S * S * S);
     for (int c = gt; c < nc; c += gs) {
-        float ar = 0.f, am = 0.f;
-        for (int q = 0; q < S * S; ++q) {
-            ar += A.part[2 * (c * S * S + q)];
-            am += A.part[2 * (c * S * S + q) + 1];
-        }
-        const float rv = ar * inv, mv = am * inv;
-        A.rc[c] = rv;
-        A.mask[c] = mv;
-        rs[0] += (double)mv * (double)rv * (double)rv;
-        rs[1] += (double)mv;
+        const double rv = A.rc[c], mv = A.mask[c];
+        rs[0] += mv * rv * rv;
+        rs[1] += mv;
     }
     nn_block_sum<2>(rs);
     if (threadIdx.x == 0) {
@@ -851,7 +827,7 @@ __global__ void __launch_bounds__(256) k_net_infer(const __grid_constant__ NetIn
         A.cta[2 * blockIdx.x + 1] = rs[1];
     }
     if (!grid_barrier(A.bar_count, A.bar_gen, sc)) return;
-    // 3. RMS (every CTA adds the CTA partials in the same order) and the packed input
+    // 2. RMS (every CTA adds the CTA partials in the same order) and the packed input
     double ts = 0.0, tm = 0.0;
     for (int b = 0; b < (int)gridDim.x; ++b) {
         ts += A.cta[2 * b];
@@ -870,7 +846,7 @@ __global__ void __launch_bounds__(256) k_net_infer(const __grid_constant__ NetIn
         dst[1] = reinterpret_cast<const uint4*>(o)[1];
     }
     if (!grid_barrier(A.bar_count, A.bar_gen, sc)) return;
-    // 4. the U-Net
+    // 3. the U-Net
     const int(*L)[3] = A.L;
     {
         const ConvArgs c0{A.xin, A.wb[0], A.e[0], nullptr, nullptr, L[0][0], L[0][1], L[0][2], 16, 16, 1,
@@ -914,103 +890,11 @@ __global__ void __launch_bounds__(256) k_net_infer(const __grid_constant__ NetIn
         conv_phase<IN_UP>(c6, st);
     }
     if (!grid_barrier(A.bar_count, A.bar_gen, sc)) return;
-    // 5. head
+    // 4. head
     for (int c = gt; c < nc; c += gs) {
         float sacc = 0.f;
         for (int ch = 0; ch < 16; ++ch) sacc += A.head_w[ch] * __bfloat162float(A.dd[0][(size_t)c * 16 + ch]);
         A.y[c] = A.mask[c] * sacc;
-    }
-    if (!grid_barrier(A.bar_count, A.bar_gen, sc)) return;
-    // 6. trilinear prolongation on the unknowns: item = S fine cells of a row
-    for (int it = gt; it < Xc * d.ny * d.nz; it += gs) {
-        const int cx = it % Xc, yz = it / Xc, fy = yz % d.ny, fz = yz / d.ny;
-        int y0, z0;
-        float wy, wz;
-        lin_w(fy, S, Yc, y0, wy);
-        lin_w(fz, S, Zc, z0, wz);
-        const int y1 = min(y0 + 1, Yc - 1), z1 = min(z0 + 1, Zc - 1);
-        auto col = [&](int c) {
-            c = max(0, min(c, Xc - 1));
-            auto at = [&](int b, int cc) { return A.y[((size_t)cc * Yc + b) * Xc + c]; };
-            const float a0 = (1.f - wy) * at(y0, z0) + wy * at(y1, z0);
-            const float a1 = (1.f - wy) * at(y0, z1) + wy * at(y1, z1);
-            return (1.f - wz) * a0 + wz * a1;
-        };
-        const float cm = col(cx - 1), c0v = col(cx), cp = col(cx + 1);
-        const long long row = d.at(1, fy + 1, fz + 1);
-        float* o = A.q + ((size_t)fz * d.ny + fy) * d.nx;
-        for (int m = 0; m < S; ++m) {
-            const int x = cx * S + m;
-            if (x >= d.nx) break;
-            int x0;
-            float wx;
-            lin_w(x, S, Xc, x0, wx);
-            const int x1 = min(x0 + 1, Xc - 1);
-            const float v0 = x0 < cx ? cm : (x0 == cx ? c0v : cp);
-            const float v1 = x1 < cx ? cm : (x1 == cx ? c0v : cp);
-            o[x] = (A.g.flags[row + x] & F_UNK) ? (1.f - wx) * v0 + wx * v1 : 0.f;
-        }
-    }
-    if (!grid_barrier(A.bar_count, A.bar_gen, sc)) return;
-    // 7. energy-norm line search: <q, V r> / <q, V A q> (CTA partials, fixed order)
-    const Geo<float>& g = A.g;
-    const int n = d.nx * d.ny * d.nz, sy = d.nx, sz = d.nx * d.ny;
-    float l0 = 0.f, l1 = 0.f;
-    for (int v = gt; v < n; v += gs) {
-        const int i = v % d.nx + 1, j = (v / d.nx) % d.ny + 1, k = v / sz + 1;
-        const long long c = d.at(i, j, k);
-        const uint8_t f = g.flags[c];
-        if (!(f & F_UNK)) continue;
-        const int oe = (d.perx && i == d.nx) ? -(d.nx - 1) : 1;
-        const int ow = (d.perx && i == 1) ? (d.nx - 1) : -1;
-        const int on = (d.pery && j == d.ny) ? -(d.ny - 1) * sy : sy;
-        const int os = (d.pery && j == 1) ? (d.ny - 1) * sy : -sy;
-        const int ot = (d.perz && k == d.nz) ? -(d.nz - 1) * sz : sz;
-        const int ob = (d.perz && k == 1) ? (d.nz - 1) * sz : -sz;
-        const float qc = A.q[v];
-        float aq = 0.f;
-        if (f & F_E) aq += g.cx * (A.q[v + oe] - qc);
-        if (f & F_W) aq += g.cx * (A.q[v + ow] - qc);
-        if (f & F_N) aq += g.cy * (A.q[v + on] - qc);
-        if (f & F_S) aq += g.cy * (A.q[v + os] - qc);
-        if (f & F_T) aq += g.cT[k] * (A.q[v + ot] - qc);
-        if (f & F_B) aq += g.cB[k] * (A.q[v + ob] - qc);
-        const float vq = g.dz[k] * qc;
-        l0 += vq * A.r[c];
-        l1 += vq * aq;
-    }
-    double ls[2] = {(double)l0, (double)l1};
-    nn_block_sum<2>(ls);
-    if (threadIdx.x == 0) {
-        A.cta[2 * gridDim.x + 2 * blockIdx.x] = ls[0];
-        A.cta[2 * gridDim.x + 2 * blockIdx.x + 1] = ls[1];
-    }
-    if (!grid_barrier(A.bar_count, A.bar_gen, sc)) return;
-    // 8. the step (every CTA forms alpha from the same partials in the same order)
-    double s0 = 0.0, s1 = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) {
-        s0 += A.cta[2 * gridDim.x + 2 * b];
-        s1 += A.cta[2 * gridDim.x + 2 * b + 1];
-    }
-    const double ad = s0 / s1;
-    const double alpha = (s1 != 0.0 && isfinite(ad)) ? ad : 0.0;
-    if (gt == 0) *A.alpha = alpha;
-    const float af = (float)alpha;
-    for (int v = gt; v < n; v += gs) {
-        const int i = v % d.nx + 1, j = (v / d.nx) % d.ny + 1, k = v / sz + 1;
-        const long long c = d.at(i, j, k);
-        if (!(g.flags[c] & F_UNK)) continue;
-        if (A.mode == 0) {
-            const float base = zero_before ? 0.f : A.dl[c];
-            A.dl[c] = base + af * A.q[v];
-        } else {
-            A.ph[c] += alpha * (double)A.q[v];
-        }
-    }
-    if (A.mode == 0 && gt == 0) {
-        // the correction now holds the step: the next sweeps must read it
-        sc->zcopy = zero_before ? 1 : 0;
-        sc->zflag = 0;
     }
 }
 
