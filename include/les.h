@@ -339,12 +339,12 @@ int les_set_warmstart(les_handle h, int32_t mode, les_net net);
  * start (default).  A value > 0 runs solves from the host loop.  The stop
  * test is unchanged. */
 int les_set_net_schedule(les_handle h, int32_t every_sweeps);
-/* les_set_net_kernels: 1 (default) runs each network correction as one
- * cooperative persistent launch (pooling, network, prolongation, line search
- * and step, phases separated by a grid barrier with a bounded wait) when the
- * device supports cooperative launches; 0 uses one launch per layer.  Both
- * compute the same correction up to the summation order of the RMS and the
- * line search. */
+/* les_set_net_kernels: 1 runs the coarse network of each correction (RMS,
+ * packing, the seven convolutions, head) as one cooperative persistent launch
+ * with a bounded grid barrier between layers, when the device supports
+ * cooperative launches; 0 (default, faster inside the CUDA graphs on GB300)
+ * uses one launch per layer.  Both compute the same correction up to the
+ * summation order of the RMS. */
 int les_set_net_kernels(les_handle h, int32_t persistent);
 
 /*

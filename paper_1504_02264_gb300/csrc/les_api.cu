@@ -128,7 +128,7 @@ struct les_s {
     double n_unk = 0.0;                   // number of Poisson unknowns
     int net_every = 0;                    // sweeps between network corrections inside a solve (0: start only)
     long long net_gen = -1;               // network workspace generation the chunk graphs were captured with
-    bool net_persistent = true;           // run the correction as one cooperative launch when the device can
+    bool net_persistent = false;          // coarse network as one cooperative launch (les_set_net_kernels)
     bool record = false;
     int rec_after = 0;                    // record at the first refinement after this many sweeps
     bool rec_taken = false;               // the current solve has taken its pair's input
