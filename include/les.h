@@ -136,6 +136,15 @@ int les_get_fields(les_handle h, void* u, void* v, void* w, void* p);
 
 /* les_set_inflow: replace the inflow profile [nz] (m/s), intensity and seed. */
 int les_set_inflow(les_handle h, const double* inflow_u, double turb, uint64_t seed);
+/* les_set_inflow_series: inflow profiles that change in time (the LES side of
+ * the coupling to a mesoscale model, Sec. 4, fed here by a synthetic series):
+ * n profiles [n][nz] (m/s, level k fastest) at increasing times [n] (s).  Each
+ * step takes at t = step * dt the linear interpolation between the two
+ * bracketing profiles, held at the first / last profile outside the series;
+ * the turbulence of les_set_inflow still applies on top.  n = 0 returns to
+ * the fixed profile.  The series is configuration: les_get_state does not
+ * store it.  Non-increasing times give LES_EINVAL. */
+int les_set_inflow_series(les_handle h, int32_t n, const double* times, const double* profiles);
 
 /*
  * les_step: advance nsteps time steps (Sec. 2.1 routine sequence, velnw last).

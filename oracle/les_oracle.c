@@ -65,6 +65,10 @@ typedef struct {
     double *fu, *fv, *fw;     /* F_old: previous tendency (AB2 history) */
     int64_t step;
     orc_stats st;
+    /* inflow profile series in time (the LES side of the coupling to a
+     * mesoscale model, Sec. 4): n profiles U_m(z_k) at times t_m */
+    int nseries;
+    double *series_t, *series_p;   /* [n], [n][nz+2] */
 } orc_t;
 
 #define IX(o, i, j, k) (((size_t)(k) * (o)->sy + (size_t)(j)) * (o)->sx + (size_t)(i))
@@ -140,6 +144,21 @@ static int face_hi(int bc, int n) { return bc == BC_PERIODIC ? n : n - 1; }
  *  periodic: a(0) = a(n), a(n+1) = a(1) for every array.
  * The passes run x, then y over all i, then z over all i and j, so corner
  * ghosts take the composition of the rules in that order.                   */
+/* inflow profile at level k for the current step: the fixed profile, or the
+ * series interpolated linearly in time t = step * dt between the two
+ * bracketing profiles (held constant before the first and after the last) */
+static double inflow_at(const orc_t* o, int k) {
+    if (o->nseries <= 0) return o->inflow[k];
+    const int n = o->nseries, sk = o->P.nz + 2;
+    const double t = (double)o->step * o->P.dt;
+    if (n == 1 || t <= o->series_t[0]) return o->series_p[k];
+    if (t >= o->series_t[n - 1]) return o->series_p[(size_t)(n - 1) * sk + k];
+    int m = 0;
+    while (m + 1 < n - 1 && o->series_t[m + 1] <= t) ++m;
+    const double w = (t - o->series_t[m]) / (o->series_t[m + 1] - o->series_t[m]);
+    return (1.0 - w) * o->series_p[(size_t)m * sk + k] + w * o->series_p[(size_t)(m + 1) * sk + k];
+}
+
 static void bc_fill(orc_t* o) {
     const orc_params* P = &o->P;
     const int nx = P->nx, ny = P->ny, nz = P->nz;
@@ -152,7 +171,7 @@ static void bc_fill(orc_t* o) {
                     A[a][IX(o, nx + 1, j, k)] = A[a][IX(o, 1, j, k)];
                 }
             } else {
-                double U = o->inflow[k];
+                double U = inflow_at(o, k);
                 double xu = 0.0, xv = 0.0, xw = 0.0;
                 if (P->turb != 0.0) {
                     xu = inflow_noise(o, 0, j, k);
@@ -753,8 +772,37 @@ void orc_destroy(orc_t* o) {
     double* arrs[] = {o->u, o->v, o->w, o->p, o->rhs, o->nut, o->us, o->vs, o->ws,
                       o->fu, o->fv, o->fw, o->dz, o->dzs, o->inflow};
     for (size_t a = 0; a < sizeof(arrs) / sizeof(arrs[0]); ++a) free(arrs[a]);
+    free(o->series_t);
+    free(o->series_p);
     free(o->solid);
     free(o);
+}
+
+/* n profiles [n][nz] at increasing times [n]; n = 0 returns to the fixed profile */
+int orc_set_inflow_series(orc_t* o, int n, const double* times, const double* profiles) {
+    if (n < 0) return -1;
+    for (int m = 1; m < n; ++m)
+        if (!(times[m] > times[m - 1])) return -1;
+    free(o->series_t);
+    free(o->series_p);
+    o->series_t = NULL;
+    o->series_p = NULL;
+    o->nseries = 0;
+    if (n == 0) return 0;
+    const int sk = o->P.nz + 2;
+    o->series_t = (double*)calloc((size_t)n, sizeof(double));
+    o->series_p = (double*)calloc((size_t)n * sk, sizeof(double));
+    for (int m = 0; m < n; ++m) {
+        o->series_t[m] = times[m];
+        for (int k = 1; k <= o->P.nz; ++k) o->series_p[(size_t)m * sk + k] = profiles[(size_t)m * o->P.nz + k - 1];
+    }
+    o->nseries = n;
+    return 0;
+}
+
+/* the inflow profile the next step will use (for pinning the interpolation) */
+void orc_inflow_profile(const orc_t* o, double* out) {
+    for (int k = 1; k <= o->P.nz; ++k) out[k - 1] = inflow_at(o, k);
 }
 
 /* I/O layout: u (nz, ny, nx+1) faces i=0..nx; v (nz, ny+1, nx) faces j=0..ny;

@@ -105,6 +105,9 @@ def lib():
         L.orc_gauss.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
         L.orc_splitmix64.restype = ctypes.c_uint64
         L.orc_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+        L.orc_set_inflow_series.restype = ctypes.c_int
+        L.orc_set_inflow_series.argtypes = [vp, ctypes.c_int, dp, dp]
+        L.orc_inflow_profile.argtypes = [vp, dp]
         _lib = L
     return _lib
 
@@ -211,6 +214,19 @@ class Oracle:
     def gauge(self): lib().orc_gauge(self.h)
     def project(self): lib().orc_project(self.h)
     def tendency(self, with_sgs=True): lib().orc_tendency(self.h, 1 if with_sgs else 0)
+
+    def set_inflow_series(self, times, profiles):
+        """Inflow profiles [n][nz] at increasing times [n] (n = 0: the fixed profile)."""
+        self._st = np.ascontiguousarray(times, dtype=np.float64)
+        self._sp = np.ascontiguousarray(profiles, dtype=np.float64)
+        n = len(self._st)
+        if lib().orc_set_inflow_series(self.h, n, _dp(self._st) if n else None, _dp(self._sp) if n else None):
+            raise ValueError("inflow series: times must increase")
+
+    def inflow_profile(self) -> np.ndarray:
+        out = np.empty(self.nz)
+        lib().orc_inflow_profile(self.h, _dp(out))
+        return out
 
     def apply_A(self, p) -> np.ndarray:
         p = np.ascontiguousarray(p, dtype=np.float64)

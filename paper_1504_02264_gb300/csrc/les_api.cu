@@ -127,6 +127,10 @@ struct les_s {
     double* warm_scal = nullptr;          // [0] input scale, [1] line-search step
     double n_unk = 0.0;                   // number of Poisson unknowns
     int net_every = 0;                    // sweeps between network corrections inside a solve (0: start only)
+    // inflow profile series in time (device; nseries = 0: the fixed profile)
+    double* series_p = nullptr;
+    double* series_t = nullptr;
+    int nseries = 0, series_cap = 0;
     long long net_gen = -1;               // network workspace generation the chunk graphs were captured with
     bool net_persistent = false;          // coarse network as one cooperative launch (les_set_net_kernels)
     bool record = false;
@@ -575,7 +579,8 @@ void launch_prefix(les_s* h, const Geo<T>& g, cudaStream_t s) {
     T* u = (T*)h->u;
     T* v = (T*)h->v;
     T* w = (T*)h->w;
-    h->launches += launch_bc<T>(g, u, v, w, h->inflow64, h->g.turb, h->g.seed, h->sc, s);
+    const InflowSeries ser{h->series_p, h->series_t, h->nseries, h->g.dt};
+    h->launches += launch_bc<T>(g, u, v, w, h->inflow64, ser, h->g.turb, h->g.seed, h->sc, s);
     h->launches += launch_nut<T>(g, u, v, w, (T*)h->nut, s);
     h->launches += launch_momentum<T>(g, u, v, w, (const T*)h->nut, (T*)h->fu, (T*)h->fv, (T*)h->fw, (T*)h->us,
                                       (T*)h->vs, (T*)h->ws, h->sc, s);
@@ -843,6 +848,9 @@ int init_tables(les_s* h) {
 }
 
 void release(les_s* h) {
+    if (h->series_p) cudaFree(h->series_p);
+    if (h->series_t) cudaFree(h->series_t);
+    h->series_p = h->series_t = nullptr;
     for (cudaGraphExec_t& x : h->gexec)
         if (x) {
             cudaGraphExecDestroy(x);
@@ -1164,6 +1172,35 @@ int les_set_inflow(les_handle h, const double* inflow_u, double turb, uint64_t s
     CK(cudaMemcpyAsync(h->inflow64, h->inflow.data(), h->inflow.size() * sizeof(double), cudaMemcpyHostToDevice,
                        h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    return LES_OK;
+}
+
+int les_set_inflow_series(les_handle h, int32_t n, const double* times, const double* profiles) {
+    if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
+    if (n < 0 || (n > 0 && (!times || !profiles))) return fail(h, LES_EINVAL, "bad inflow series");
+    for (int m = 1; m < n; ++m)
+        if (!(times[m] > times[m - 1])) return fail(h, LES_EINVAL, "inflow series times must increase");
+    CK(cudaStreamSynchronize(h->stream));
+    const int sk = h->g.nz + 2;
+    if (n > h->series_cap) {
+        if (h->series_p) cudaFree(h->series_p);
+        if (h->series_t) cudaFree(h->series_t);
+        h->series_p = h->series_t = nullptr;
+        h->series_cap = 0;
+        if (cudaMalloc(&h->series_p, (size_t)n * sk * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&h->series_t, (size_t)n * sizeof(double)) != cudaSuccess)
+            return fail(h, LES_ENOMEM, "inflow series");
+        h->series_cap = n;
+    }
+    if (n > 0) {
+        std::vector<double> p((size_t)n * sk, 0.0);
+        for (int m = 0; m < n; ++m)
+            for (int k = 1; k <= h->g.nz; ++k) p[(size_t)m * sk + k] = profiles[(size_t)m * h->g.nz + k - 1];
+        CK(cudaMemcpy(h->series_p, p.data(), p.size() * sizeof(double), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->series_t, times, (size_t)n * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    h->nseries = n;
+    h->graph_ok[0] = h->graph_ok[1] = false;      // a fixed-sweep graph holds the bondv1 arguments
     return LES_OK;
 }
 

@@ -109,9 +109,18 @@ struct Reduce {
     Scalars* sc;
 };
 
+// inflow profile series in time (n = 0: the fixed profile is used)
+struct InflowSeries {
+    const double* p;        // [n][nz+2] profiles (level k at index k)
+    const double* t;        // [n] increasing times (s)
+    int n;
+    double dt;
+};
+
 // launchers (les_kernels.cu); each returns the number of kernels launched
 template <typename T> int launch_bc(const Geo<T>& g, T* u, T* v, T* w, const double* inflow,
-                                    double turb, uint64_t seed, const Scalars* sc, cudaStream_t s);
+                                    const InflowSeries& ser, double turb, uint64_t seed, const Scalars* sc,
+                                    cudaStream_t s);
 template <typename T> int launch_nut(const Geo<T>& g, const T* u, const T* v, const T* w, T* nut,
                                      cudaStream_t s);
 template <typename T> int launch_momentum(const Geo<T>& g, const T* u, const T* v, const T* w,

@@ -31,8 +31,24 @@ __device__ double gauss_at(uint64_t seed, uint64_t c) {
 // bondv1, three passes (x over interior j,k; y over all i; z over all i,j) so
 // corner ghosts take the rules in that order.
 
+// inflow profile at level k of the current step: the fixed profile, or the
+// series interpolated linearly in t = step * dt between the two bracketing
+// profiles (held constant before the first and after the last)
+__device__ __forceinline__ double inflow_at(const double* inflow, const InflowSeries& ser, long long step, int k,
+                                            int nz) {
+    if (ser.n <= 0) return inflow[k];
+    const int sk = nz + 2, n = ser.n;
+    const double t = (double)step * ser.dt;
+    if (n == 1 || t <= ser.t[0]) return ser.p[k];
+    if (t >= ser.t[n - 1]) return ser.p[(size_t)(n - 1) * sk + k];
+    int m = 0;
+    while (m + 1 < n - 1 && ser.t[m + 1] <= t) ++m;
+    const double wgt = (t - ser.t[m]) / (ser.t[m + 1] - ser.t[m]);
+    return (1.0 - wgt) * ser.p[(size_t)m * sk + k] + wgt * ser.p[(size_t)(m + 1) * sk + k];
+}
+
 template <typename T>
-__global__ void k_bc_x(Dom d, T* u, T* v, T* w, const double* inflow, double turb, uint64_t seed,
+__global__ void k_bc_x(Dom d, T* u, T* v, T* w, const double* inflow, InflowSeries ser, double turb, uint64_t seed,
                        const Scalars* sc) {
     int j = blockIdx.x * blockDim.x + threadIdx.x + 1;
     int k = blockIdx.y + 1;
@@ -47,7 +63,7 @@ __global__ void k_bc_x(Dom d, T* u, T* v, T* w, const double* inflow, double tur
         w[d.at(nx + 1, j, k)] = w[d.at(1, j, k)];
         return;
     }
-    double U = inflow[k];
+    const double U = inflow_at(inflow, ser, sc->step, k, d.nz);
     double xu = 0.0, xv = 0.0, xw = 0.0;
     if (turb != 0.0) {
         const uint64_t sy = (uint64_t)(d.ny + 2), sz = (uint64_t)(d.nz + 2);
@@ -115,10 +131,10 @@ __global__ void k_bc_z(Dom d, T* u, T* v, T* w) {
 }
 
 template <typename T>
-int launch_bc(const Geo<T>& g, T* u, T* v, T* w, const double* inflow, double turb, uint64_t seed,
-              const Scalars* sc, cudaStream_t s) {
+int launch_bc(const Geo<T>& g, T* u, T* v, T* w, const double* inflow, const InflowSeries& ser, double turb,
+              uint64_t seed, const Scalars* sc, cudaStream_t s) {
     const Dom& d = g.d;
-    k_bc_x<T><<<dim3((d.ny + 127) / 128, d.nz), 128, 0, s>>>(d, u, v, w, inflow, turb, seed, sc);
+    k_bc_x<T><<<dim3((d.ny + 127) / 128, d.nz), 128, 0, s>>>(d, u, v, w, inflow, ser, turb, seed, sc);
     k_bc_y<T><<<dim3((d.nx + 2 + 127) / 128, d.nz), 128, 0, s>>>(d, u, v, w);
     k_bc_z<T><<<dim3((d.nx + 2 + 127) / 128, d.ny + 2), 128, 0, s>>>(d, u, v, w);
     return 3;
@@ -1136,8 +1152,8 @@ int launch_refine_ens(const EnsTab<float>& tab, int dcur, const CondArgs& ca, cu
 }
 
 #define LES_INSTANTIATE(T)                                                                              \
-    template int launch_bc<T>(const Geo<T>&, T*, T*, T*, const double*, double, uint64_t,               \
-                              const Scalars*, cudaStream_t);                                            \
+    template int launch_bc<T>(const Geo<T>&, T*, T*, T*, const double*, const InflowSeries&, double,      \
+                              uint64_t, const Scalars*, cudaStream_t);                                  \
     template int launch_nut<T>(const Geo<T>&, const T*, const T*, const T*, T*, cudaStream_t);          \
     template int launch_momentum<T>(const Geo<T>&, const T*, const T*, const T*, const T*, T*, T*, T*,  \
                                     T*, T*, T*, const Scalars*, cudaStream_t);                          \

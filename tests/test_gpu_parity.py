@@ -306,3 +306,20 @@ def test_graph_multi_step_call_matches_single_steps():
     assert st["step"] == 4 and st["rc"] == 0
     for x, y in zip(a.fields(), b.fields()):
         assert np.array_equal(x, y)
+
+
+def test_fp64_inflow_series_matches_oracle():
+    """A time-varying inflow series (interpolated in time, turbulence on top)
+    gives the oracle's step to FP64 rounding over several steps."""
+    sc = city(turb=0.1)
+    z = scene.centre_heights(sc.dz)
+    times = np.array([0.0, 0.08, 0.2, 0.3])
+    prof = np.stack([sc.inflow_u * (1.0 + 0.3 * np.sin(3.0 * t)) + 0.01 * t * z for t in times])
+    o = Oracle(sc)
+    o.set_inflow_series(times, prof)
+    d = les.Domain(sc, precision=les.LES_FP64)
+    d.set_inflow_series(times, prof)
+    o.step(6)
+    d.step(6)
+    compare_fields(d, o, 1e-11)
+    d.close()
