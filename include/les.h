@@ -355,6 +355,10 @@ int les_set_net_schedule(les_handle h, int32_t every_sweeps);
  * uses one launch per layer.  Both compute the same correction up to the
  * summation order of the RMS. */
 int les_set_net_kernels(les_handle h, int32_t persistent);
+/* les_set_net_start: with a schedule (every_sweeps > 0), whether the network
+ * also corrects p at the start of each solve (default 1); without a schedule
+ * the start correction is the warm start and always runs. */
+int les_set_net_start(les_handle h, int32_t enable);
 
 /*
  * Ensembles: n domains of uneven size, each with its own buildings, inflow

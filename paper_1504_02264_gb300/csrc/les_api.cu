@@ -133,6 +133,7 @@ struct les_s {
     int nseries = 0, series_cap = 0;
     long long net_gen = -1;               // network workspace generation the chunk graphs were captured with
     bool net_persistent = false;          // coarse network as one cooperative launch (les_set_net_kernels)
+    bool net_start = true;                // also correct at the start of each solve
     bool record = false;
     int rec_after = 0;                    // record at the first refinement after this many sweeps
     bool rec_taken = false;               // the current solve has taken its pair's input
@@ -385,7 +386,7 @@ int solve_start(les_s* h, const Geo<T>& g, cudaStream_t st) {
                                             cond_args(h, RES_INIT, 0, 0), st);
     }
     if constexpr (std::is_same<T, float>::value) {
-        if (h->warm == LES_WARM_NET && h->net) {
+        if (h->warm == LES_WARM_NET && h->net && (h->net_start || h->net_every == 0)) {
             int rc = net_correct<T>(h, g, st);
             if (rc) return rc;
         }
@@ -621,7 +622,17 @@ int step_host(les_s* h) {
 // `done` is set, so the host can keep one chunk in flight and stop enqueueing
 // when it sees the mapped copy of the flag: the GPU never waits for the host.
 // With fixed_sweeps the whole step is one captured graph.
+// the network correction runs inside the solve loop (FP32 grids)
+bool net_in_loop(const les_s* h) {
+    return h->prec == LES_FP32 && h->warm == LES_WARM_NET && h->net && h->net_every > 0;
+}
+
 constexpr int kChunkBatches = 10;
+// with the network correction a batch is a whole cycle (sweeps, estimate,
+// network, step): shorter chunks waste fewer done-gated launches after the
+// stop test has passed
+constexpr int kChunkCycles = 4;
+int chunk_batches(const les_s* h) { return net_in_loop(h) ? kChunkCycles : kChunkBatches; }
 
 template <typename T>
 int capture_begin(les_s* h, cudaStream_t cs) {
@@ -649,10 +660,6 @@ int capture_end(les_s* h, cudaStream_t cs, cudaGraphExec_t* out) {
     return LES_OK;
 }
 
-// the network correction runs inside the solve loop (FP32 grids)
-bool net_in_loop(const les_s* h) {
-    return h->prec == LES_FP32 && h->warm == LES_WARM_NET && h->net && h->net_every > 0;
-}
 
 template <typename T>
 int build_graph(les_s* h, int cur) {
@@ -686,7 +693,7 @@ int build_graph(les_s* h, int cur) {
         // cycles of net_every sweeps, a forced refinement, the network
         // correction and the residual again, all gated on `done`
         if constexpr (std::is_same<T, float>::value) {
-            for (int b = 0; b < kChunkBatches; ++b) {
+            for (int b = 0; b < chunk_batches(h); ++b) {
                 run_sweeps<T>(h, g, h->net_every, 2, nl, cs);     // net_every even: d returns to dl[0]
                 launch_sor_est<T>(g, (const T*)h->dl[h->dcur], (const T*)h->rr, (T*)h->rcur, reducer(h),
                                   cond_args(h, RES_LOOP, h->net_every, 1), cs);
@@ -728,7 +735,7 @@ int step_graph(les_s* h, int nsteps, les_stats_t* stats) {
         }
     Geo<T> g = geo<T>(h);
     CK(cudaMemsetAsync(&h->sc->noconv_any, 0, sizeof(int), h->stream));
-    const int per_chunk = kChunkBatches * (net_in_loop(h) ? h->net_every : G.check_every);
+    const int per_chunk = chunk_batches(h) * (net_in_loop(h) ? h->net_every : G.check_every);
     const int max_chunks = (G.max_sweeps + per_chunk - 1) / per_chunk + 1;
     for (int s = 0; s < nsteps; ++s) {
         if (G.fixed_sweeps) {
@@ -749,7 +756,7 @@ int step_graph(les_s* h, int nsteps, les_stats_t* stats) {
             for (int c = 0; c < max_chunks; ++c) {
                 CK(cudaGraphLaunch(h->gexec[h->cur], h->stream));
                 CK(cudaEventRecord(h->chunk_ev[c & 1], h->stream));
-                h->launches += kChunkBatches * per_batch;
+                h->launches += chunk_batches(h) * per_batch;
                 if (c >= 1) {
                     CK(cudaEventSynchronize(h->chunk_ev[(c - 1) & 1]));
                     if (*(volatile int*)h->done_host) break;
@@ -1392,6 +1399,12 @@ int les_set_warmstart(les_handle h, int32_t mode, les_net net) {
     return LES_OK;
 }
 
+int les_set_net_start(les_handle h, int32_t enable) {
+    if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
+    h->net_start = enable != 0;
+    return LES_OK;
+}
+
 int les_set_net_kernels(les_handle h, int32_t persistent) {
     if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
     h->net_persistent = persistent != 0;
@@ -1527,6 +1540,7 @@ int member_net_prepare(les_s* h) {
 long long member_net_generation(const les_s* h) { return net_in_loop(h) ? net_generation(h->net) : -1; }
 int member_net_start(les_s* h, cudaStream_t s) {
     if (!(h->warm == LES_WARM_NET && h->net && h->prec == LES_FP32)) return LES_OK;
+    if (!h->net_start && h->net_every > 0) return LES_OK;
     Geo<float> g = geo<float>(h);
     return net_correct<float>(h, g, s);
 }

@@ -146,7 +146,8 @@ def train(net: les.Net, data, iters: int, batch: int, lr: float, seed: int = 0, 
     return hist
 
 
-def evaluate(net: les.Net | None, sc, steps: int, spinup: int, schedules=(0,), log=print, persistent=True):
+def evaluate(net: les.Net | None, sc, steps: int, spinup: int, schedules=(0,), log=print, persistent=False,
+             start=True):
     """Sweeps and milliseconds per step to the scene's tolerance for the
     previous-step start and, with a network, for each correction schedule
     (0 = one-shot warm start; m > 0 = also every m sweeps).  All runs start
@@ -168,6 +169,7 @@ def evaluate(net: les.Net | None, sc, steps: int, spinup: int, schedules=(0,), l
             dom.set_warmstart(net)
             dom.set_net_schedule(m)
             dom.set_net_kernels(persistent)
+            dom.set_net_start(start)
         sweeps, ms, ok = [], [], True
         for _ in range(steps):
             torch.cuda.synchronize()
@@ -207,7 +209,8 @@ def main(argv=None):
     ap.add_argument("--schedules", default="0,50,100,200")
     ap.add_argument("--json", default=None, help="write the evaluation here")
     ap.add_argument("--eval-only", default=None, help="evaluate these trained networks (.npz, comma separated)")
-    ap.add_argument("--layer-kernels", action="store_true", help="evaluate with one launch per network layer")
+    ap.add_argument("--persistent", action="store_true", help="evaluate with the persistent coarse network")
+    ap.add_argument("--no-start", action="store_true", help="no network correction at the start of a solve")
     ap.add_argument("--dagger", default=None, help="also record pairs with this network in the loop (.npz)")
     ap.add_argument("--dagger-every", type=int, default=10)
     ap.add_argument("--dagger-points", default="0,10,20,30,50,80,120,200")
@@ -222,7 +225,7 @@ def main(argv=None):
             print(f"{path} (stride {net.stride}) on {ev_sc.name} seed {ev_sc.seed}:", flush=True)
             report["nets"][path] = evaluate(net, ev_sc, a.eval_steps, a.eval_spinup,
                                             [int(x) for x in a.schedules.split(",")],
-                                            persistent=not a.layer_kernels)
+                                            persistent=a.persistent, start=not a.no_start)
             net.close()
         print(json.dumps(report), flush=True)
         if a.json:
