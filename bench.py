@@ -47,7 +47,7 @@ L2_FLUSH_BYTES = 256 << 20
 # mean SOR sweeps per step of this workload after the default warm-up, from the
 # GPU arm (the FP64 path takes the same sweeps as the oracle); used only to scale
 # the bounded oracle sample to a full step when no GPU run is available
-REF_SWEEPS_PER_STEP = 13600
+REF_SWEEPS_PER_STEP = 12600
 
 
 def workload(seed=0):
