@@ -282,7 +282,23 @@ def run_ours(args):
         head = plain
     ms, sweeps, worst, graph_used, clk, launches = (head["ms"], head["sweeps"], head["worst"], head["graph"],
                                                     head["clocks"], head["launches"])
+    net_phases = None
     if net is not None:
+        # phase times of the learned step (host loop with CUDA events around
+        # each phase; not the timed region)
+        dom.set_state(state0)
+        dom.set_timing(True)
+        for s in range(min(args.steps, 3)):
+            flush.zero_()
+            dom.step(1)
+        torch.cuda.synchronize()
+        tn = dom.timing()
+        dom.set_timing(False)
+        net_phases = {k: tn[k] / max(tn["steps"], 1) for k in
+                      ("ms_momentum", "ms_sor", "ms_residual", "ms_project", "ms_net")}
+        net_phases["net_cycles_per_step"] = tn["net_cycles"] / max(tn["steps"], 1)
+        net_phases["sweeps_per_step"] = tn["sor_sweeps"] / max(tn["steps"], 1)
+        net_phases["note"] = "host loop with an event pair around every phase; sums exceed the graph step time"
         # the SOR kernel roofline and the CPU baseline use the plain step
         dom.set_warmstart(None)
         dom.set_state(state0)
@@ -357,7 +373,8 @@ def run_ours(args):
                 "net_every_sweeps": NET_EVERY, "stride": net.stride,
                 "weights": os.path.relpath(WEIGHTS, ROOT),
                 "note": "same start state and stop test (FP64 relative residual <= 1e-6 every step); "
-                        "network time included"},
+                        "network time included",
+                "phase_ms_per_step": net_phases},
             "roofline": {"kernel": f"{sor_kernel_name(tile)} (red-black SOR sweep, tile {les.les_sor_tile(tile) if tile >= 0 else 'two-pass'}, kc {kc})",
                          "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

@@ -216,6 +216,8 @@ typedef struct {
     int64_t sor_sweeps;          /* SOR sweeps timed */
     int64_t sor_launches;        /* SOR kernel launches timed */
     int64_t launches;            /* all kernels launched by the handle so far */
+    double ms_net;               /* learned correction: prediction, line search, step */
+    int64_t net_cycles;          /* learned corrections timed inside the solve loop */
 } les_timing_t;
 int les_set_timing(les_handle h, int32_t enable);
 int les_get_timing(les_handle h, les_timing_t* t);

@@ -430,8 +430,14 @@ int sor_solve(les_s* h) {
         h->tm.ms_residual += elapsed(h, 2, 3);
     }
     {
+        rec(h, 2);
         int rs = solve_start<T>(h, g, h->stream);
         if (rs) return rs;
+        rec(h, 3);
+        if (h->timing && h->warm == LES_WARM_NET) {
+            CK(cudaEventSynchronize(h->ev[3]));
+            h->tm.ms_net += elapsed(h, 2, 3);
+        }
     }
     int sweeps = 0, last_net = 0;
     bool fresh = true, conv = false;
@@ -493,8 +499,15 @@ int sor_solve(les_s* h) {
         if constexpr (std::is_same<T, float>::value) {
             if (net_due) {
                 last_net = sweeps;
+                rec(h, 2);
                 int rc = net_correct_loop<T>(h, g, h->stream, false);
                 if (rc) return rc;
+                rec(h, 3);
+                if (h->timing) {
+                    CK(cudaEventSynchronize(h->ev[3]));
+                    h->tm.ms_net += elapsed(h, 2, 3);
+                    h->tm.net_cycles += 1;
+                }
                 fresh = false;      // the correction now holds the network's step
             }
         }

@@ -49,7 +49,8 @@ class les_timing_t(ctypes.Structure):
     _fields_ = [("ms_momentum", ctypes.c_double), ("ms_sor", ctypes.c_double),
                 ("ms_residual", ctypes.c_double), ("ms_project", ctypes.c_double),
                 ("steps", ctypes.c_int64), ("sor_sweeps", ctypes.c_int64),
-                ("sor_launches", ctypes.c_int64), ("launches", ctypes.c_int64)]
+                ("sor_launches", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("ms_net", ctypes.c_double), ("net_cycles", ctypes.c_int64)]
 
 
 _lib = None
