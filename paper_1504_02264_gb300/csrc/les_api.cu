@@ -753,7 +753,7 @@ int step_graph(les_s* h, int nsteps, les_stats_t* stats) {
     for (int s = 0; s < nsteps; ++s) {
         if (G.fixed_sweeps) {
             CK(cudaGraphLaunch(h->gexec[h->cur], h->stream));
-            h->launches += 7 + (h->d.pery ? 1 : 0) + (h->d.perz ? 1 : 0) + 1 + G.max_sweeps + 2 + 1;
+            h->launches += 10 + (h->d.pery ? 1 : 0) + (h->d.perz ? 1 : 0) + 1 + G.max_sweeps + 2 + 1;
         } else {
             *(volatile int*)h->done_host = 0;
             launch_prefix<T>(h, g, h->stream);

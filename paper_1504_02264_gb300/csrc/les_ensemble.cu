@@ -321,7 +321,7 @@ int les_ensemble_step(les_ensemble e, int32_t nsteps, les_stats_t* stats) {
             int rc = member_prefix(h, s);
             if (rc) return efail(e, rc, "member prefix: %s", les_last_error(h));
         }
-        e->launches += 6 * e->n;
+        e->launches += 9 * e->n;
         const EnsTab<float>& T = *e->tab[par];
         e->launches += launch_refine_ens(T, 0, eargs(e, RES_INIT, 0, 0), s);
         if (e->net)

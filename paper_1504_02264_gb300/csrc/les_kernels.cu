@@ -143,15 +143,25 @@ int launch_bc(const Geo<T>& g, T* u, T* v, T* w, const double* inflow, const Inf
 // ---------------------------------------------------------------------------
 // les: Smagorinsky eddy viscosity at cell centres
 
+// velocity reads around the cell (i0, j0, k0): the padded index of the cell
+// once, neighbours by 32-bit offsets (rows and planes are < 2^31 elements)
 template <typename T>
 struct Stencil {
     const Geo<T>& g;
     const T* u;
     const T* v;
     const T* w;
-    __device__ __forceinline__ T U(int i, int j, int k) const { return u[g.d.at(i, j, k)]; }
-    __device__ __forceinline__ T V(int i, int j, int k) const { return v[g.d.at(i, j, k)]; }
-    __device__ __forceinline__ T W(int i, int j, int k) const { return w[g.d.at(i, j, k)]; }
+    long long c0;
+    int i0, j0, k0, px, pl;
+    __device__ __forceinline__ Stencil(const Geo<T>& g_, const T* u_, const T* v_, const T* w_, int i, int j, int k)
+        : g(g_), u(u_), v(v_), w(w_), c0(g_.d.at(i, j, k)), i0(i), j0(j), k0(k), px(g_.d.px),
+          pl((int)g_.d.plane) {}
+    __device__ __forceinline__ long long at(int i, int j, int k) const {
+        return c0 + ((i - i0) + (j - j0) * px + (k - k0) * pl);
+    }
+    __device__ __forceinline__ T U(int i, int j, int k) const { return u[at(i, j, k)]; }
+    __device__ __forceinline__ T V(int i, int j, int k) const { return v[at(i, j, k)]; }
+    __device__ __forceinline__ T W(int i, int j, int k) const { return w[at(i, j, k)]; }
     // shear rates on cell edges
     __device__ __forceinline__ T s12(int i, int j, int k) const {
         return T(0.5) * ((U(i, j + 1, k) - U(i, j, k)) / g.dy + (V(i + 1, j, k) - V(i, j, k)) / g.dx);
@@ -173,7 +183,7 @@ __global__ void k_nut(Geo<T> g, const T* u, const T* v, const T* w, T* nut) {
     if (i > d.nx || j > d.ny) return;
     long long c = d.at(i, j, k);
     if (!(g.flags[c] & F_FLUID)) { nut[c] = T(0); return; }
-    Stencil<T> S{g, u, v, w};
+    const Stencil<T> S(g, u, v, w, i, j, k);
     T s11 = (u[c] - S.U(i - 1, j, k)) / g.dx;
     T s22 = (v[c] - S.V(i, j - 1, k)) / g.dy;
     T s33 = (w[c] - S.W(i, j, k - 1)) / g.dz[k];
@@ -184,25 +194,54 @@ __global__ void k_nut(Geo<T> g, const T* u, const T* v, const T* w, T* nut) {
     nut[c] = g.delta2[k] * smag;
 }
 
+// nu_t ghost layer: zero gradient (the adjacent interior value) or periodic
+// wrap, axis by axis (x over interior j, k; y over all i; z over all i, j), so
+// a ghost read equals the read of the index clamped / wrapped on each axis
+template <typename T>
+__global__ void k_nut_ghost(Dom d, T* nut, int axis) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (axis == 0) {
+        const int j = a + 1, k = b + 1;
+        if (j > d.ny) return;
+        nut[d.at(0, j, k)] = nut[d.at(d.perx ? d.nx : 1, j, k)];
+        nut[d.at(d.nx + 1, j, k)] = nut[d.at(d.perx ? 1 : d.nx, j, k)];
+    } else if (axis == 1) {
+        const int i = a, k = b + 1;
+        if (i > d.nx + 1) return;
+        nut[d.at(i, 0, k)] = nut[d.at(i, d.pery ? d.ny : 1, k)];
+        nut[d.at(i, d.ny + 1, k)] = nut[d.at(i, d.pery ? 1 : d.ny, k)];
+    } else {
+        const int i = a, j = b;
+        if (i > d.nx + 1) return;
+        nut[d.at(i, j, 0)] = nut[d.at(i, j, d.perz ? d.nz : 1)];
+        nut[d.at(i, j, d.nz + 1)] = nut[d.at(i, j, d.perz ? 1 : d.nz)];
+    }
+}
+
 template <typename T>
 int launch_nut(const Geo<T>& g, const T* u, const T* v, const T* w, T* nut, cudaStream_t s) {
     const Dom& d = g.d;
     k_nut<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(g, u, v, w, nut);
-    return 1;
+    k_nut_ghost<T><<<dim3((d.ny + 127) / 128, d.nz), 128, 0, s>>>(d, nut, 0);
+    k_nut_ghost<T><<<dim3((d.nx + 2 + 127) / 128, d.nz), 128, 0, s>>>(d, nut, 1);
+    k_nut_ghost<T><<<dim3((d.nx + 2 + 127) / 128, d.ny + 2), 128, 0, s>>>(d, nut, 2);
+    return 4;
 }
 
 // ---------------------------------------------------------------------------
-// velfg + les (SGS) + adam + feedbf.  nu_t is read with its ghost rule applied
-// to the index (zero gradient = clamp, periodic = wrap), so no ghost pass.
+// velfg + les (SGS) + adam + feedbf.  nu_t ghosts hold the clamped / wrapped
+// values (k_nut_ghost), so the edge averages read it directly.
 
 template <typename T>
 struct Nut {
-    const Dom& d;
     const T* nut;
-    __device__ __forceinline__ int cx(int i) const { return d.perx ? (i < 1 ? i + d.nx : (i > d.nx ? i - d.nx : i)) : min(max(i, 1), d.nx); }
-    __device__ __forceinline__ int cy(int j) const { return d.pery ? (j < 1 ? j + d.ny : (j > d.ny ? j - d.ny : j)) : min(max(j, 1), d.ny); }
-    __device__ __forceinline__ int cz(int k) const { return d.perz ? (k < 1 ? k + d.nz : (k > d.nz ? k - d.nz : k)) : min(max(k, 1), d.nz); }
-    __device__ __forceinline__ T operator()(int i, int j, int k) const { return nut[d.at(cx(i), cy(j), cz(k))]; }
+    long long c0;
+    int i0, j0, k0, px, pl;
+    __device__ __forceinline__ Nut(const Dom& d, const T* nut_, int i, int j, int k)
+        : nut(nut_), c0(d.at(i, j, k)), i0(i), j0(j), k0(k), px(d.px), pl((int)d.plane) {}
+    __device__ __forceinline__ T operator()(int i, int j, int k) const {
+        return nut[c0 + ((i - i0) + (j - j0) * px + (k - k0) * pl)];
+    }
     __device__ __forceinline__ T xy(int i, int j, int k) const {
         return T(0.25) * ((*this)(i, j, k) + (*this)(i + 1, j, k) + (*this)(i, j + 1, k) + (*this)(i + 1, j + 1, k));
     }
@@ -318,8 +357,8 @@ __global__ void k_momentum(Geo<T> g, const T* u, const T* v, const T* w, const T
     if (i > d.nx || j > d.ny) return;
     long long c = d.at(i, j, k);
     const uint8_t f = g.flags[c];
-    Stencil<T> S{g, u, v, w};
-    Nut<T> N{d, nut};
+    const Stencil<T> S(g, u, v, w, i, j, k);
+    const Nut<T> N(d, nut, i, j, k);
     if (i <= (d.perx ? d.nx : d.nx - 1)) {
         T F = velfg_u(g, S, i, j, k) + sgs_u(g, S, N, i, j, k);
         T Fh = first ? F : T(1.5) * F - T(0.5) * fu[c];
