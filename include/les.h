@@ -373,7 +373,10 @@ int les_set_net_start(les_handle h, int32_t enable);
  * The SOR solves of all members run as batched launches over a flattened
  * (member, tile) work list: one persistent sweep launch per sweep for the
  * whole ensemble (28 x BY x BZ row tiles, `tile` 0..4 = 8x8, 4x8, 8x4,
- * 16x4, 4x16; ctas_per_sm CTAs per SM walk the list), one estimate and one
+ * 16x4, 4x16; ctas_per_sm CTAs per SM walk the list) -- or, with `tile` 5,
+ * one launch per member per sweep with the member's own kernel and tile
+ * (les_set_sor_config / les_autotune_sor of the member; TMA where its grid
+ * allows) -- one estimate and one
  * refinement launch per batch of check_every sweeps, chunks of batches in
  * CUDA graphs; each member stops at its own tolerance and sweep count.  A
  * member evolves bit-identically to the same domain stepped alone with the
@@ -384,8 +387,9 @@ int les_set_net_start(les_handle h, int32_t enable);
  * les_ensemble_step fills stats[i] for member i after the last step when
  * stats is not NULL (n entries); returns LES_ENOCONV if any member ended
  * above its tolerance.  les_ensemble_autotune times `sweeps` batched sweeps
- * per (tile, CTAs per SM) candidate on the members' scratch correction
- * buffers (the state is not changed) and keeps the fastest.
+ * per (tile, CTAs per SM) candidate and the per-member mode (after
+ * autotuning every member) on the members' scratch correction buffers (the
+ * state is not changed) and keeps the fastest.
  */
 typedef struct les_ensemble_s* les_ensemble;
 int les_ensemble_create(int32_t n, const les_grid_t* grids, const uint8_t* const* solid, const double* const* inflow,

@@ -1543,6 +1543,21 @@ int member_stats(les_s* h, les_stats_t* st) {
 }
 
 void member_set_dcur(les_s* h, int dcur) { h->dcur = dcur; }
+int member_sweep(les_s* h, int in, int zero, cudaStream_t s) {
+    if (h->sor.tile < 0) h->sor = SorCfg{6, 0};      // the ping-pong kernels only
+    Geo<float> g = geo<float>(h);
+    h->dcur = in;
+    long long nl = 0;
+    run_sweeps<float>(h, g, 1, zero, nl, s);
+    h->launches += nl;
+    return LES_OK;
+}
+int member_autotune(les_s* h, int sweeps) {
+    double ms = 0.0;
+    int rc = autotune_impl<float>(h, sweeps, &ms);
+    if (h->sor.tile < 0) h->sor = SorCfg{6, 0};
+    return rc;
+}
 bool member_net_on(const les_s* h) { return net_in_loop(h); }
 int member_net_every(const les_s* h) { return h->net_every; }
 void* member_rcur(les_s* h) { return net_in_loop(h) ? h->rcur : nullptr; }

@@ -23,6 +23,9 @@ using namespace les;
 
 namespace {
 constexpr int kEnsChunkBatches = 10;
+// tile index of the per-member mode: every member sweeps with its own kernel
+// and tile (TMA where its grid allows), one launch per member per sweep
+constexpr int kPerMember = kNumEnsTiles;
 }
 
 struct les_ensemble_s {
@@ -86,7 +89,7 @@ void fill_tables(les_ensemble_s* e) {
         T.all_done_host = e->all_done_dev;
         for (int i = 0; i < e->n; ++i) {
             les_handle h = e->mem[i];
-            member_fill(h, T.m[i], e->tile, par);
+            member_fill(h, T.m[i], e->tile == kPerMember ? 0 : e->tile, par);
             T.sbeg[i + 1] = T.sbeg[i] + T.m[i].sgrid[0] * T.m[i].sgrid[1] * T.m[i].sgrid[2];
             T.ebeg[i + 1] = T.ebeg[i] + T.m[i].egrid[0] * T.m[i].egrid[1] * T.m[i].egrid[2];
             T.abeg[i + 1] = T.abeg[i] + T.m[i].agrid[0] * T.m[i].agrid[1] * T.m[i].agrid[2];
@@ -112,7 +115,12 @@ int launch_chunk(les_ensemble_s* e, const EnsTab<float>& T, cudaStream_t s) {
     int dcur = 0;
     for (int b = 0; b < kEnsChunkBatches; ++b) {
         for (int q = 0; q < e->cycle; ++q) {
-            e->launches += launch_sor_ens(T, dcur, q == 0 ? 2 : 0, e->ctas, s);
+            if (e->tile == kPerMember) {
+                for (les_handle h : e->mem) member_sweep(h, dcur, q == 0 ? 2 : 0, s);
+                e->launches += e->n;
+            } else {
+                e->launches += launch_sor_ens(T, dcur, q == 0 ? 2 : 0, e->ctas, s);
+            }
             dcur = 1 - dcur;
         }
         e->launches += launch_est_ens(T, dcur, eargs(e, RES_LOOP, e->cycle, 1), s);
@@ -162,6 +170,10 @@ int build_chunk(les_ensemble_s* e, int par) {
 void invalidate(les_ensemble_s* e) { e->graph_ok[0] = e->graph_ok[1] = false; }
 
 int choose_ctas(les_ensemble_s* e, int per_sm) {
+    if (e->tile == kPerMember) {
+        e->ctas = 0;
+        return LES_OK;
+    }
     int occ = 0;
     // the sweep kernels are opted in to their shared memory at member creation
     const int smem = ens_rows_smem(e->tile);
@@ -275,7 +287,7 @@ int les_ensemble_set_graph(les_ensemble e, int32_t enable) {
 
 int les_ensemble_set_tile(les_ensemble e, int32_t tile, int32_t ctas_per_sm) {
     if (!e) return LES_EINVAL;
-    if (tile < 0 || tile >= kNumEnsTiles) return efail(e, LES_EINVAL, "tile must be 0..%d", kNumEnsTiles - 1);
+    if (tile < 0 || tile > kPerMember) return efail(e, LES_EINVAL, "tile must be 0..%d", kPerMember);
     if (ctas_per_sm < 1 || ctas_per_sm > 8) return efail(e, LES_EINVAL, "ctas_per_sm must be 1..8");
     e->tile = tile;
     fill_tables(e);
@@ -400,6 +412,31 @@ int les_ensemble_autotune(les_ensemble e, int32_t sweeps, double* best_ms_per_sw
                 best_per_sm = per_sm;
             }
         }
+    {
+        // the per-member mode: each member first picks its own kernel and tile
+        for (les_handle h : e->mem) {
+            int rc = member_autotune(h, std::max(2, sweeps / 2));
+            if (rc) return efail(e, rc, "member autotune: %s", les_last_error(h));
+        }
+        for (int i = 0; i < e->n; ++i) ECK(cudaMemsetAsync(member_done_flag(e->mem[i]), 0, sizeof(int), s));
+        for (les_handle h : e->mem) {
+            member_sweep(h, 0, 0, s);
+            member_sweep(h, 1, 0, s);
+        }
+        ECK(cudaEventRecord(a, s));
+        for (int q = 0; q < sweeps; ++q)
+            for (les_handle h : e->mem) member_sweep(h, q & 1, 0, s);
+        ECK(cudaEventRecord(b, s));
+        ECK(cudaEventSynchronize(b));
+        ECK(cudaGetLastError());
+        float ms = 0.f;
+        ECK(cudaEventElapsedTime(&ms, a, b));
+        for (les_handle h : e->mem) member_set_dcur(h, 0);
+        if (ms / sweeps < best) {
+            best = ms / sweeps;
+            best_tile = kPerMember;
+        }
+    }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     for (int i = 0; i < e->n; ++i)

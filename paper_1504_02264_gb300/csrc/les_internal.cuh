@@ -247,6 +247,8 @@ int member_prefix(les_s* h, cudaStream_t s);              // bondv1 .. rhs of th
 int member_finish(les_s* h, cudaStream_t s);              // velnw, buffer flip, step counter
 int member_stats(les_s* h, les_stats_t* st);              // reads the scalars back; returns the status
 void member_set_dcur(les_s* h, int dcur);
+int member_sweep(les_s* h, int in, int zero, cudaStream_t s);   // one sweep d[in] -> d[1-in], own kernel
+int member_autotune(les_s* h, int sweeps);                       // the member's own sweep configuration
 int* member_done_flag(les_s* h);                           // device address of the member's `done`
 // the learned correction of a member (set with les_set_warmstart / les_set_net_schedule)
 bool member_net_on(const les_s* h);                        // network inside the solve loop

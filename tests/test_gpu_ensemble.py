@@ -44,15 +44,18 @@ def scenes():
     return [city(40, 24, 12, 1), city(33, 22, 10, 2), city(48, 32, 16, 3, periodic_y=True), city(29, 40, 14, 4)]
 
 
-@pytest.mark.parametrize("tile", [0, 3])
+@pytest.mark.parametrize("tile", [0, 3, 5])
 def test_members_match_single_domains(tile):
+    """Tiles 0-4: the batched row-tile sweep; 5: each member's own kernel
+    (here the default configuration, the same as the single domains')."""
     scs = scenes()
     ens = les.Ensemble(scs)
     ens.set_tile(tile, 4)
     singles = []
     for sc in scs:
         d = les.Domain(sc)
-        d.set_sor_config(12 + tile, 0)
+        if tile < 5:
+            d.set_sor_config(12 + tile, 0)
         singles.append(d)
     for _ in range(3):
         est = ens.step()
@@ -89,7 +92,7 @@ def test_autotune_and_converge():
     scs = scenes()
     ens = les.Ensemble(scs)
     (tile, ctas), ms = ens.autotune(sweeps=5)
-    assert 0 <= tile < 5 and ctas >= 1 and ms > 0
+    assert 0 <= tile <= 5 and (ctas >= 1 or tile == 5) and ms > 0
     st = ens.step(2)
     assert all(s["rc"] == 0 and s["rel_residual"] <= 1e-6 for s in st)
     assert ens.launches() > 0
