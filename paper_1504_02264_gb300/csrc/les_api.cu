@@ -92,6 +92,7 @@ struct les_s {
     size_t stage_elems = 0;
     uint8_t* flags = nullptr;
     void *kdz = nullptr, *kdzs = nullptr, *kcT = nullptr, *kcB = nullptr, *kdel = nullptr;
+    void *krdz = nullptr, *krdzs = nullptr;   // reciprocals of dz and dzs
     double* dz64 = nullptr;
     double *dzs64 = nullptr, *cT64 = nullptr, *cB64 = nullptr;
     double* inflow64 = nullptr;
@@ -239,6 +240,8 @@ Geo<T> geo(les_s* h) {
     g.cT = (const T*)h->kcT;
     g.cB = (const T*)h->kcB;
     g.delta2 = (const T*)h->kdel;
+    g.rdz = (const T*)h->krdz;
+    g.rdzs = (const T*)h->krdzs;
     g.dz64 = h->dz64;
     g.dx64 = h->g.dx;
     g.dy64 = h->g.dy;
@@ -854,7 +857,14 @@ int init_tables(les_s* h) {
         double l = h->g.cs * std::cbrt(h->g.dx * h->g.dy * dzp[k]);
         del[k] = l * l;
     }
+    std::vector<double> rdz(nz + 2), rdzs(nz + 2);
+    for (int k = 0; k <= nz + 1; ++k) {
+        rdz[k] = 1.0 / dzp[k];
+        rdzs[k] = 1.0 / dzs[k];
+    }
     int rc;
+    if ((rc = upload_table<T>(h, h->krdz, rdz))) return rc;
+    if ((rc = upload_table<T>(h, h->krdzs, rdzs))) return rc;
     if ((rc = upload_table<T>(h, h->kdz, dzp))) return rc;
     if ((rc = upload_table<T>(h, h->kdzs, dzs))) return rc;
     if ((rc = upload_table<T>(h, h->kcT, cT))) return rc;
@@ -923,7 +933,7 @@ int create_impl(les_s* h, const uint8_t* solid) {
         if ((rc = dalloc(h, (void**)&f, h->n * sizeof(double)))) return rc;
     if ((rc = dalloc(h, (void**)&h->flags, h->n))) return rc;
     const size_t nt = (size_t)G.nz + 2;
-    void** tabs[] = {&h->kdz, &h->kdzs, &h->kcT, &h->kcB, &h->kdel};
+    void** tabs[] = {&h->kdz, &h->kdzs, &h->kcT, &h->kcB, &h->kdel, &h->krdz, &h->krdzs};
     for (void** t : tabs)
         if ((rc = dalloc(h, t, nt * h->es))) return rc;
     if ((rc = dalloc(h, (void**)&h->dz64, nt * sizeof(double)))) return rc;

@@ -94,6 +94,8 @@ struct Geo {
     const T* cT;            // [nz+2] 1/(dz_k dzs_k)
     const T* cB;            // [nz+2] 1/(dz_k dzs_{k-1})
     const T* delta2;        // [nz+2] (Cs Delta_k)^2
+    const T* rdz;           // [nz+2] 1 / dz_k
+    const T* rdzs;          // [nz+2] 1 / dzs_k
     const double* dz64;     // [nz+2]
     double dx64, dy64, cx64, cy64;
     const double* dzs64;    // [nz+2]

@@ -164,13 +164,13 @@ struct Stencil {
     __device__ __forceinline__ T W(int i, int j, int k) const { return w[at(i, j, k)]; }
     // shear rates on cell edges
     __device__ __forceinline__ T s12(int i, int j, int k) const {
-        return T(0.5) * ((U(i, j + 1, k) - U(i, j, k)) / g.dy + (V(i + 1, j, k) - V(i, j, k)) / g.dx);
+        return T(0.5) * ((U(i, j + 1, k) - U(i, j, k)) * g.rdy + (V(i + 1, j, k) - V(i, j, k)) * g.rdx);
     }
     __device__ __forceinline__ T s13(int i, int j, int k) const {
-        return T(0.5) * ((U(i, j, k + 1) - U(i, j, k)) / g.dzs[k] + (W(i + 1, j, k) - W(i, j, k)) / g.dx);
+        return T(0.5) * ((U(i, j, k + 1) - U(i, j, k)) * g.rdzs[k] + (W(i + 1, j, k) - W(i, j, k)) * g.rdx);
     }
     __device__ __forceinline__ T s23(int i, int j, int k) const {
-        return T(0.5) * ((V(i, j, k + 1) - V(i, j, k)) / g.dzs[k] + (W(i, j + 1, k) - W(i, j, k)) / g.dy);
+        return T(0.5) * ((V(i, j, k + 1) - V(i, j, k)) * g.rdzs[k] + (W(i, j + 1, k) - W(i, j, k)) * g.rdy);
     }
 };
 
@@ -184,9 +184,9 @@ __global__ void k_nut(Geo<T> g, const T* u, const T* v, const T* w, T* nut) {
     long long c = d.at(i, j, k);
     if (!(g.flags[c] & F_FLUID)) { nut[c] = T(0); return; }
     const Stencil<T> S(g, u, v, w, i, j, k);
-    T s11 = (u[c] - S.U(i - 1, j, k)) / g.dx;
-    T s22 = (v[c] - S.V(i, j - 1, k)) / g.dy;
-    T s33 = (w[c] - S.W(i, j, k - 1)) / g.dz[k];
+    T s11 = (u[c] - S.U(i - 1, j, k)) * g.rdx;
+    T s22 = (v[c] - S.V(i, j - 1, k)) * g.rdy;
+    T s33 = (w[c] - S.W(i, j, k - 1)) * g.rdz[k];
     T s12 = T(0.25) * (S.s12(i - 1, j - 1, k) + S.s12(i, j - 1, k) + S.s12(i - 1, j, k) + S.s12(i, j, k));
     T s13 = T(0.25) * (S.s13(i - 1, j, k - 1) + S.s13(i, j, k - 1) + S.s13(i - 1, j, k) + S.s13(i, j, k));
     T s23 = T(0.25) * (S.s23(i, j - 1, k - 1) + S.s23(i, j, k - 1) + S.s23(i, j - 1, k) + S.s23(i, j, k));
@@ -255,95 +255,96 @@ struct Nut {
 
 template <typename T>
 __device__ __forceinline__ T velfg_u(const Geo<T>& g, const Stencil<T>& S, int i, int j, int k) {
-    const T dx = g.dx, dy = g.dy;
+    const T dx = g.dx, dy = g.dy, rdx = g.rdx, rdy = g.rdy;
     T um = S.U(i - 1, j, k), uc = S.U(i, j, k), up = S.U(i + 1, j, k);
-    T cov1_i = T(0.5) * (um + uc) * (uc - um) / dx;
-    T cov1_ip = T(0.5) * (uc + up) * (up - uc) / dx;
-    T covx = (dx * cov1_i + dx * cov1_ip) / (dx + dx);
+    T cov1_i = T(0.5) * (um + uc) * (uc - um) * rdx;
+    T cov1_ip = T(0.5) * (uc + up) * (up - uc) * rdx;
+    T covx = (dx * cov1_i + dx * cov1_ip) * (T(0.5) * rdx);
     T vn = T(0.5) * (S.V(i, j, k) + S.V(i + 1, j, k));
     T vs = T(0.5) * (S.V(i, j - 1, k) + S.V(i + 1, j - 1, k));
     T un = S.U(i, j + 1, k), us = S.U(i, j - 1, k);
-    T covy = (vs * (uc - us) / dy + vn * (un - uc) / dy) / T(2);
+    T covy = (vs * (uc - us) * rdy + vn * (un - uc) * rdy) * T(0.5);
     T wt = T(0.5) * (S.W(i, j, k) + S.W(i + 1, j, k));
     T wb = T(0.5) * (S.W(i, j, k - 1) + S.W(i + 1, j, k - 1));
     T ut = S.U(i, j, k + 1), ub = S.U(i, j, k - 1);
-    T covz = (wb * (uc - ub) / g.dzs[k - 1] + wt * (ut - uc) / g.dzs[k]) / T(2);
-    T diu1_i = (uc - um) / dx, diu1_ip = (up - uc) / dx;
-    T dfu = T(2) * (diu1_ip - diu1_i) / (dx + dx) + ((un - uc) / dy - (uc - us) / dy) / dy +
-            ((ut - uc) / g.dzs[k] - (uc - ub) / g.dzs[k - 1]) / g.dz[k];
+    T covz = (wb * (uc - ub) * g.rdzs[k - 1] + wt * (ut - uc) * g.rdzs[k]) * T(0.5);
+    T diu1_i = (uc - um) * rdx, diu1_ip = (up - uc) * rdx;
+    T dfu = T(2) * (diu1_ip - diu1_i) * (T(0.5) * rdx) + ((un - uc) * rdy - (uc - us) * rdy) * rdy +
+            ((ut - uc) * g.rdzs[k] - (uc - ub) * g.rdzs[k - 1]) * g.rdz[k];
     return -(covx + covy + covz) + g.nu * dfu;
 }
 
 template <typename T>
 __device__ __forceinline__ T velfg_v(const Geo<T>& g, const Stencil<T>& S, int i, int j, int k) {
-    const T dx = g.dx, dy = g.dy;
+    const T dx = g.dx, dy = g.dy, rdx = g.rdx, rdy = g.rdy;
     T vm = S.V(i, j - 1, k), vc = S.V(i, j, k), vp = S.V(i, j + 1, k);
-    T cov_j = T(0.5) * (vm + vc) * (vc - vm) / dy;
-    T cov_jp = T(0.5) * (vc + vp) * (vp - vc) / dy;
-    T covy = (dy * cov_j + dy * cov_jp) / (dy + dy);
+    T cov_j = T(0.5) * (vm + vc) * (vc - vm) * rdy;
+    T cov_jp = T(0.5) * (vc + vp) * (vp - vc) * rdy;
+    T covy = (dy * cov_j + dy * cov_jp) * (T(0.5) * rdy);
     T ue = T(0.5) * (S.U(i, j, k) + S.U(i, j + 1, k));
     T uw = T(0.5) * (S.U(i - 1, j, k) + S.U(i - 1, j + 1, k));
     T ve = S.V(i + 1, j, k), vw = S.V(i - 1, j, k);
-    T covx = (uw * (vc - vw) / dx + ue * (ve - vc) / dx) / T(2);
+    T covx = (uw * (vc - vw) * rdx + ue * (ve - vc) * rdx) * T(0.5);
     T wt = T(0.5) * (S.W(i, j, k) + S.W(i, j + 1, k));
     T wb = T(0.5) * (S.W(i, j, k - 1) + S.W(i, j + 1, k - 1));
     T vt = S.V(i, j, k + 1), vb = S.V(i, j, k - 1);
-    T covz = (wb * (vc - vb) / g.dzs[k - 1] + wt * (vt - vc) / g.dzs[k]) / T(2);
-    T dfv = ((ve - vc) / dx - (vc - vw) / dx) / dx + T(2) * ((vp - vc) / dy - (vc - vm) / dy) / (dy + dy) +
-            ((vt - vc) / g.dzs[k] - (vc - vb) / g.dzs[k - 1]) / g.dz[k];
+    T covz = (wb * (vc - vb) * g.rdzs[k - 1] + wt * (vt - vc) * g.rdzs[k]) * T(0.5);
+    T dfv = ((ve - vc) * rdx - (vc - vw) * rdx) * rdx + T(2) * ((vp - vc) * rdy - (vc - vm) * rdy) * (T(0.5) * rdy) +
+            ((vt - vc) * g.rdzs[k] - (vc - vb) * g.rdzs[k - 1]) * g.rdz[k];
     return -(covx + covy + covz) + g.nu * dfv;
 }
 
 template <typename T>
 __device__ __forceinline__ T velfg_w(const Geo<T>& g, const Stencil<T>& S, int i, int j, int k) {
-    const T dx = g.dx, dy = g.dy;
-    const T dzk = g.dz[k], dzp = g.dz[k + 1];
+    const T dx = g.dx, dy = g.dy, rdx = g.rdx, rdy = g.rdy;
+    const T dzk = g.dz[k], dzp = g.dz[k + 1], rdzk = g.rdz[k], rdzp = g.rdz[k + 1];
+    const T rsum = T(1) * rsum;
     T wm = S.W(i, j, k - 1), wc = S.W(i, j, k), wp = S.W(i, j, k + 1);
-    T cov_k = T(0.5) * (wm + wc) * (wc - wm) / dzk;
-    T cov_kp = T(0.5) * (wc + wp) * (wp - wc) / dzp;
-    T covz = (dzp * cov_k + dzk * cov_kp) / (dzk + dzp);
-    T ue = (dzp * S.U(i, j, k) + dzk * S.U(i, j, k + 1)) / (dzk + dzp);
-    T uw = (dzp * S.U(i - 1, j, k) + dzk * S.U(i - 1, j, k + 1)) / (dzk + dzp);
+    T cov_k = T(0.5) * (wm + wc) * (wc - wm) * rdzk;
+    T cov_kp = T(0.5) * (wc + wp) * (wp - wc) * rdzp;
+    T covz = (dzp * cov_k + dzk * cov_kp) * rsum;
+    T ue = (dzp * S.U(i, j, k) + dzk * S.U(i, j, k + 1)) * rsum;
+    T uw = (dzp * S.U(i - 1, j, k) + dzk * S.U(i - 1, j, k + 1)) * rsum;
     T we = S.W(i + 1, j, k), ww = S.W(i - 1, j, k);
-    T covx = (uw * (wc - ww) / dx + ue * (we - wc) / dx) / T(2);
-    T vn = (dzp * S.V(i, j, k) + dzk * S.V(i, j, k + 1)) / (dzk + dzp);
-    T vs = (dzp * S.V(i, j - 1, k) + dzk * S.V(i, j - 1, k + 1)) / (dzk + dzp);
+    T covx = (uw * (wc - ww) * rdx + ue * (we - wc) * rdx) * T(0.5);
+    T vn = (dzp * S.V(i, j, k) + dzk * S.V(i, j, k + 1)) * rsum;
+    T vs = (dzp * S.V(i, j - 1, k) + dzk * S.V(i, j - 1, k + 1)) * rsum;
     T wn = S.W(i, j + 1, k), wsv = S.W(i, j - 1, k);
-    T covy = (vs * (wc - wsv) / dy + vn * (wn - wc) / dy) / T(2);
-    T dfw = ((we - wc) / dx - (wc - ww) / dx) / dx + ((wn - wc) / dy - (wc - wsv) / dy) / dy +
-            T(2) * ((wp - wc) / dzp - (wc - wm) / dzk) / (dzk + dzp);
+    T covy = (vs * (wc - wsv) * rdy + vn * (wn - wc) * rdy) * T(0.5);
+    T dfw = ((we - wc) * rdx - (wc - ww) * rdx) * rdx + ((wn - wc) * rdy - (wc - wsv) * rdy) * rdy +
+            T(2) * ((wp - wc) * rdzp - (wc - wm) * rdzk) * rsum;
     return -(covx + covy + covz) + g.nu * dfw;
 }
 
 template <typename T>
 __device__ __forceinline__ T sgs_u(const Geo<T>& g, const Stencil<T>& S, const Nut<T>& N, int i, int j, int k) {
-    T t11_i = T(2) * N(i, j, k) * (S.U(i, j, k) - S.U(i - 1, j, k)) / g.dx;
-    T t11_ip = T(2) * N(i + 1, j, k) * (S.U(i + 1, j, k) - S.U(i, j, k)) / g.dx;
+    T t11_i = T(2) * N(i, j, k) * (S.U(i, j, k) - S.U(i - 1, j, k)) * g.rdx;
+    T t11_ip = T(2) * N(i + 1, j, k) * (S.U(i + 1, j, k) - S.U(i, j, k)) * g.rdx;
     T t12_n = T(2) * N.xy(i, j, k) * S.s12(i, j, k);
     T t12_s = T(2) * N.xy(i, j - 1, k) * S.s12(i, j - 1, k);
     T t13_t = T(2) * N.xz(i, j, k) * S.s13(i, j, k);
     T t13_b = T(2) * N.xz(i, j, k - 1) * S.s13(i, j, k - 1);
-    return (t11_ip - t11_i) / g.dx + (t12_n - t12_s) / g.dy + (t13_t - t13_b) / g.dz[k];
+    return (t11_ip - t11_i) * g.rdx + (t12_n - t12_s) * g.rdy + (t13_t - t13_b) * g.rdz[k];
 }
 template <typename T>
 __device__ __forceinline__ T sgs_v(const Geo<T>& g, const Stencil<T>& S, const Nut<T>& N, int i, int j, int k) {
-    T t22_j = T(2) * N(i, j, k) * (S.V(i, j, k) - S.V(i, j - 1, k)) / g.dy;
-    T t22_jp = T(2) * N(i, j + 1, k) * (S.V(i, j + 1, k) - S.V(i, j, k)) / g.dy;
+    T t22_j = T(2) * N(i, j, k) * (S.V(i, j, k) - S.V(i, j - 1, k)) * g.rdy;
+    T t22_jp = T(2) * N(i, j + 1, k) * (S.V(i, j + 1, k) - S.V(i, j, k)) * g.rdy;
     T t12_e = T(2) * N.xy(i, j, k) * S.s12(i, j, k);
     T t12_w = T(2) * N.xy(i - 1, j, k) * S.s12(i - 1, j, k);
     T t23_t = T(2) * N.yz(i, j, k) * S.s23(i, j, k);
     T t23_b = T(2) * N.yz(i, j, k - 1) * S.s23(i, j, k - 1);
-    return (t12_e - t12_w) / g.dx + (t22_jp - t22_j) / g.dy + (t23_t - t23_b) / g.dz[k];
+    return (t12_e - t12_w) * g.rdx + (t22_jp - t22_j) * g.rdy + (t23_t - t23_b) * g.rdz[k];
 }
 template <typename T>
 __device__ __forceinline__ T sgs_w(const Geo<T>& g, const Stencil<T>& S, const Nut<T>& N, int i, int j, int k) {
-    T t33_k = T(2) * N(i, j, k) * (S.W(i, j, k) - S.W(i, j, k - 1)) / g.dz[k];
-    T t33_kp = T(2) * N(i, j, k + 1) * (S.W(i, j, k + 1) - S.W(i, j, k)) / g.dz[k + 1];
+    T t33_k = T(2) * N(i, j, k) * (S.W(i, j, k) - S.W(i, j, k - 1)) * g.rdz[k];
+    T t33_kp = T(2) * N(i, j, k + 1) * (S.W(i, j, k + 1) - S.W(i, j, k)) * g.rdz[k + 1];
     T t13_e = T(2) * N.xz(i, j, k) * S.s13(i, j, k);
     T t13_w = T(2) * N.xz(i - 1, j, k) * S.s13(i - 1, j, k);
     T t23_n = T(2) * N.yz(i, j, k) * S.s23(i, j, k);
     T t23_s = T(2) * N.yz(i, j - 1, k) * S.s23(i, j - 1, k);
-    return (t13_e - t13_w) / g.dx + (t23_n - t23_s) / g.dy + (t33_kp - t33_k) / g.dzs[k];
+    return (t13_e - t13_w) * g.rdx + (t23_n - t23_s) * g.rdy + (t33_kp - t33_k) * g.rdzs[k];
 }
 
 template <typename T>
