@@ -298,7 +298,7 @@ template <typename T>
 __device__ __forceinline__ T velfg_w(const Geo<T>& g, const Stencil<T>& S, int i, int j, int k) {
     const T dx = g.dx, dy = g.dy, rdx = g.rdx, rdy = g.rdy;
     const T dzk = g.dz[k], dzp = g.dz[k + 1], rdzk = g.rdz[k], rdzp = g.rdz[k + 1];
-    const T rsum = T(1) * rsum;
+    const T rsum = T(1) / (dzk + dzp);
     T wm = S.W(i, j, k - 1), wc = S.W(i, j, k), wp = S.W(i, j, k + 1);
     T cov_k = T(0.5) * (wm + wc) * (wc - wm) * rdzk;
     T cov_kp = T(0.5) * (wc + wp) * (wp - wc) * rdzp;
