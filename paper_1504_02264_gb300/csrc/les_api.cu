@@ -109,6 +109,7 @@ struct les_s {
     // CUDA graph of one step per pressure-buffer parity
     bool use_graph = true;
     bool graph_ok[2] = {false, false};
+    long long graph_launches[2] = {0, 0};  // kernels in each fixed-sweep step graph
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     cudaStream_t cap[1] = {nullptr};
     cudaEvent_t chunk_ev[2] = {nullptr, nullptr};
@@ -119,6 +120,7 @@ struct les_s {
     bool last_graph = false;              // the last les_step ran as graphs
     TmaMaps tma[kNumTmaTiles];            // tensor maps of the TMA sweep (FP32, no periodic axis)
     bool tma_ok = false;
+    bool pipe_ok = false;                 // persistent TMA tiles (no periodic axis)
     float* cn1tab = nullptr;              // cn1 over (plane, open-face mask) for the pipelined sweep
     // learned warm start and training-pair recording
     int warm = LES_WARM_PREV;
@@ -525,6 +527,14 @@ int sor_solve(les_s* h) {
     return (!G.fixed_sweeps && !conv) ? LES_ENOCONV : LES_OK;
 }
 
+// sweep configurations this handle can run: the plain tiles always, the TMA
+// block tiles on FP32 grids, the persistent TMA tiles without periodic axes
+bool tile_available(const les_s* h, int t) {
+    if (t < 0 || t >= kNumSorTiles + kNumTmaTiles) return false;
+    if (t < kNumSorTiles) return true;
+    return h->tma_ok && (t < kNumSorTiles + kNumTmaBlockTiles || h->pipe_ok);
+}
+
 // Time `sweeps` sweeps per candidate (tile shape x k-chunk) on the current
 // correction right-hand side; the sweeps touch only the scratch correction
 // buffers, never the state.
@@ -552,9 +562,9 @@ int autotune_impl(les_s* h, int sweeps, double* best_ms, int only_tile, int only
     CK(cudaMemsetAsync(&h->sc->done, 0, sizeof(int), h->stream));
     SorCfg keep = h->sor, best = keep;
     double bms = 1e300;
-    const int ntiles = kNumSorTiles + (h->tma_ok ? kNumTmaTiles : 0);
-    for (int t = 0; t < ntiles; ++t)
+    for (int t = 0; t < kNumSorTiles + kNumTmaTiles; ++t)
         for (int kc : kcs) {
+            if (!tile_available(h, t)) continue;
             if (kc > h->g.nz) continue;
             if ((t >= kNumSorTiles || kSorTiles[t].tz > 0) && kc != 0) continue;      // 3-D blocks ignore kc
             if (only_tile >= -1 && (t != only_tile || kc != only_kc)) continue;
@@ -601,7 +611,7 @@ void launch_prefix(les_s* h, const Geo<T>& g, cudaStream_t s) {
     h->launches += launch_nut<T>(g, u, v, w, (T*)h->nut, s);
     h->launches += launch_momentum<T>(g, u, v, w, (const T*)h->nut, (T*)h->fu, (T*)h->fv, (T*)h->fw, (T*)h->us,
                                       (T*)h->vs, (T*)h->ws, h->sc, s);
-    h->launches += launch_outflow<T>(g, u, (T*)h->us, (T*)h->vs, (T*)h->ws, h->sc, s);
+    h->launches += launch_outflow<T>(g, u, (T*)h->us, (T*)h->vs, (T*)h->ws, reducer(h), s);
     h->launches += launch_rhs<T>(g, (const T*)h->us, (const T*)h->vs, (const T*)h->ws, (T*)h->rhs, h->vfluid,
                                  reducer(h), s);
 }
@@ -700,11 +710,12 @@ int build_graph(les_s* h, int cur) {
     long long nl = 0;
     if (G.fixed_sweeps) {
         launch_prefix<T>(h, g, cs);
-        launch_residual64<T>(g, h->ph[cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h),
-                             cond_args(h, RES_INIT, 0, 0), cs);
+        nl += launch_residual64<T>(g, h->ph[cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h),
+                                   cond_args(h, RES_INIT, 0, 0), cs);
         run_sweeps<T>(h, g, G.max_sweeps, 1, nl, cs);
         launch_refine<T>(h, g, cond_args(h, RES_FIXED, G.max_sweeps, 0), cs);
         launch_project_step<T>(h, g, cur, cs);
+        h->graph_launches[cur] = h->launches - l0 + nl;
     } else if (net_in_loop(h)) {
         // cycles of net_every sweeps, a forced refinement, the network
         // correction and the residual again, all gated on `done`
@@ -756,7 +767,7 @@ int step_graph(les_s* h, int nsteps, les_stats_t* stats) {
     for (int s = 0; s < nsteps; ++s) {
         if (G.fixed_sweeps) {
             CK(cudaGraphLaunch(h->gexec[h->cur], h->stream));
-            h->launches += 10 + (h->d.pery ? 1 : 0) + (h->d.perz ? 1 : 0) + 1 + G.max_sweeps + 2 + 1;
+            h->launches += h->graph_launches[h->cur];
         } else {
             *(volatile int*)h->done_host = 0;
             launch_prefix<T>(h, g, h->stream);
@@ -1000,6 +1011,7 @@ int create_impl(les_s* h, const uint8_t* solid) {
         if (tma_supported(d)) {
             CK(tma_prepare());
             h->tma_ok = tma_encode(d, (float*)h->dl[0], (float*)h->dl[1], (float*)h->rr, h->flags, h->tma);
+            h->pipe_ok = h->tma_ok && pipe_supported(d);
         }
         CK(cudaStreamSynchronize(h->stream));
     }
@@ -1347,8 +1359,8 @@ int les_set_state(les_handle h, const void* buf, size_t len) {
 int les_set_sor_config(les_handle h, int32_t tile, int32_t kc) {
     if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
     if (tile < -1 || tile >= kNumSorTiles + kNumTmaTiles) return fail(h, LES_EINVAL, "tile %d out of range", tile);
-    if (tile >= kNumSorTiles && !h->tma_ok)
-        return fail(h, LES_EINVAL, "TMA tiles need an FP32 grid without periodic axes");
+    if (tile >= 0 && !tile_available(h, tile))
+        return fail(h, LES_EINVAL, "tile %d needs an FP32 grid (persistent TMA tiles: no periodic axis)", tile);
     h->sor = SorCfg{tile, kc};
     h->graph_ok[0] = h->graph_ok[1] = false;
     return LES_OK;
@@ -1384,8 +1396,7 @@ int les_sor_tile(int32_t tile, int32_t* tx, int32_t* ty, int32_t* tz) {
 int les_time_sor(les_handle h, int32_t tile, int32_t kc, int32_t sweeps, double* ms_per_sweep) {
     if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
     if (sweeps < 1 || !ms_per_sweep) return fail(h, LES_EINVAL, "sweeps must be >= 1 and ms_per_sweep set");
-    const int ntiles = kNumSorTiles + (h->tma_ok ? kNumTmaTiles : 0);
-    if (tile < 0 || tile >= ntiles) return fail(h, LES_EINVAL, "tile %d not available on this grid", tile);
+    if (!tile_available(h, tile)) return fail(h, LES_EINVAL, "tile %d not available on this grid", tile);
     *ms_per_sweep = -1.0;
     int rc = h->prec == LES_FP64 ? time_config_impl<double>(h, tile, kc, sweeps, ms_per_sweep)
                                  : time_config_impl<float>(h, tile, kc, sweeps, ms_per_sweep);
@@ -1529,9 +1540,10 @@ cudaStream_t member_stream(const les_s* h) { return h->stream; }
 
 int member_prefix(les_s* h, cudaStream_t s) {
     Geo<float> g = geo<float>(h);
+    const long long l0 = h->launches;
     launch_prefix<float>(h, g, s);
     CK(cudaGetLastError());
-    return LES_OK;
+    return (int)(h->launches - l0);
 }
 
 int member_finish(les_s* h, cudaStream_t s) {

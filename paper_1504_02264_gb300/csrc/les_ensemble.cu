@@ -330,10 +330,10 @@ int les_ensemble_step(les_ensemble e, int32_t nsteps, les_stats_t* stats) {
         ECK(cudaMemsetAsync(e->ndone, 0, sizeof(int), s));
         *(volatile int*)e->all_done_host = 0;
         for (les_handle h : e->mem) {
-            int rc = member_prefix(h, s);
-            if (rc) return efail(e, rc, "member prefix: %s", les_last_error(h));
+            const int rc = member_prefix(h, s);
+            if (rc < 0) return efail(e, rc, "member prefix: %s", les_last_error(h));
+            e->launches += rc;
         }
-        e->launches += 9 * e->n;
         const EnsTab<float>& T = *e->tab[par];
         e->launches += launch_refine_ens(T, 0, eargs(e, RES_INIT, 0, 0), s);
         if (e->net)

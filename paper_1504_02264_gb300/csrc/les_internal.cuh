@@ -128,8 +128,8 @@ template <typename T> int launch_nut(const Geo<T>& g, const T* u, const T* v, co
 template <typename T> int launch_momentum(const Geo<T>& g, const T* u, const T* v, const T* w,
                                           const T* nut, T* fu, T* fv, T* fw, T* us, T* vs, T* ws,
                                           const Scalars* sc, cudaStream_t s);
-template <typename T> int launch_outflow(const Geo<T>& g, const T* u, T* us, T* vs, T* ws,
-                                         Scalars* sc, cudaStream_t s);
+template <typename T> int launch_outflow(const Geo<T>& g, const T* u, T* us, T* vs, T* ws, const Reduce& red,
+                                         cudaStream_t s);
 template <typename T> int launch_rhs(const Geo<T>& g, const T* us, const T* vs, const T* ws, T* rhs,
                                      double vfluid, const Reduce& r, cudaStream_t s);
 template <typename T> int launch_rhs_mean(const Geo<T>& g, T* rhs, double vfluid, const Reduce& r,
@@ -207,13 +207,21 @@ template <typename T> int launch_sor_fused(const Geo<T>& g, const T* din, T* dou
 
 template <typename T> cudaError_t sor_prepare();
 
-// TMA variant (les_sor_tma.cu): FP32, no periodic axis; tile indices
-// kFirstTmaTile .. kFirstTmaTile + kNumTmaTiles - 1
+// TMA variants (les_sor_tma.cu), FP32; tile indices kFirstTmaTile ..
+// kFirstTmaTile + kNumTmaTiles - 1: the first kNumTmaBlockTiles are one CTA
+// per block (any boundary conditions), the rest persistent double-buffered
+// (no periodic axis)
 constexpr int kFirstTmaTile = 17;
 constexpr int kNumTmaTiles = 8;
+constexpr int kNumTmaBlockTiles = 4;
 extern const int kTmaCfg[kNumTmaTiles][3];
-struct TmaMaps { CUtensorMap d[2], r, f; };
+struct TmaMaps {
+    CUtensorMap d[2], r, f;
+    const float* dptr[2];       // the arrays behind the maps (periodic halo images)
+    const float* rptr;
+};
 bool tma_supported(const Dom& d);
+bool pipe_supported(const Dom& d);
 cudaError_t tma_prepare();
 bool tma_encode(const Dom& d, float* dl0, float* dl1, float* rr, uint8_t* flags, TmaMaps* maps);
 int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, const float* cn1tab, int cfg, int in, float* dout,
@@ -245,7 +253,7 @@ int member_begin(les_s* h, cudaStream_t s);               // clears the sticky n
 int member_check_every(const les_s* h);
 int member_max_sweeps(const les_s* h);
 cudaStream_t member_stream(const les_s* h);
-int member_prefix(les_s* h, cudaStream_t s);              // bondv1 .. rhs of the step, first residual
+int member_prefix(les_s* h, cudaStream_t s);              // bondv1 .. rhs of the step; launches, or < 0 on error
 int member_finish(les_s* h, cudaStream_t s);              // velnw, buffer flip, step counter
 int member_stats(les_s* h, les_stats_t* st);              // reads the scalars back; returns the status
 void member_set_dcur(les_s* h, int dcur);

@@ -5,6 +5,8 @@
 // viscosity), k_momentum = velfg + les (SGS divergence) + adam + feedbf,
 // k_outflow = bondv1 outflow and mass-flux correction, k_rhs / k_sor_half /
 // k_accum / k_residual64 = press (Sec. 2.6), k_project = velnw.
+#include <type_traits>
+
 #include "les_internal.cuh"
 
 namespace les {
@@ -145,8 +147,26 @@ int launch_bc(const Geo<T>& g, T* u, T* v, T* w, const double* inflow, const Inf
 
 // velocity reads around the cell (i0, j0, k0): the padded index of the cell
 // once, neighbours by 32-bit offsets (rows and planes are < 2^31 elements)
+// shear rates on cell edges, over any accessor D with U/V/W(i, j, k) and g
+template <typename T, typename D>
+struct StrainOps {
+    __device__ __forceinline__ const D& self() const { return static_cast<const D&>(*this); }
+    __device__ __forceinline__ T s12(int i, int j, int k) const {
+        const D& S = self();
+        return T(0.5) * ((S.U(i, j + 1, k) - S.U(i, j, k)) * S.g.rdy + (S.V(i + 1, j, k) - S.V(i, j, k)) * S.g.rdx);
+    }
+    __device__ __forceinline__ T s13(int i, int j, int k) const {
+        const D& S = self();
+        return T(0.5) * ((S.U(i, j, k + 1) - S.U(i, j, k)) * S.g.rdzs[k] + (S.W(i + 1, j, k) - S.W(i, j, k)) * S.g.rdx);
+    }
+    __device__ __forceinline__ T s23(int i, int j, int k) const {
+        const D& S = self();
+        return T(0.5) * ((S.V(i, j, k + 1) - S.V(i, j, k)) * S.g.rdzs[k] + (S.W(i, j + 1, k) - S.W(i, j, k)) * S.g.rdy);
+    }
+};
+
 template <typename T>
-struct Stencil {
+struct Stencil : StrainOps<T, Stencil<T>> {
     const Geo<T>& g;
     const T* u;
     const T* v;
@@ -162,37 +182,7 @@ struct Stencil {
     __device__ __forceinline__ T U(int i, int j, int k) const { return u[at(i, j, k)]; }
     __device__ __forceinline__ T V(int i, int j, int k) const { return v[at(i, j, k)]; }
     __device__ __forceinline__ T W(int i, int j, int k) const { return w[at(i, j, k)]; }
-    // shear rates on cell edges
-    __device__ __forceinline__ T s12(int i, int j, int k) const {
-        return T(0.5) * ((U(i, j + 1, k) - U(i, j, k)) * g.rdy + (V(i + 1, j, k) - V(i, j, k)) * g.rdx);
-    }
-    __device__ __forceinline__ T s13(int i, int j, int k) const {
-        return T(0.5) * ((U(i, j, k + 1) - U(i, j, k)) * g.rdzs[k] + (W(i + 1, j, k) - W(i, j, k)) * g.rdx);
-    }
-    __device__ __forceinline__ T s23(int i, int j, int k) const {
-        return T(0.5) * ((V(i, j, k + 1) - V(i, j, k)) * g.rdzs[k] + (W(i, j + 1, k) - W(i, j, k)) * g.rdy);
-    }
 };
-
-template <typename T>
-__global__ void k_nut(Geo<T> g, const T* u, const T* v, const T* w, T* nut) {
-    const Dom& d = g.d;
-    int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
-    int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    int k = blockIdx.z + 1;
-    if (i > d.nx || j > d.ny) return;
-    long long c = d.at(i, j, k);
-    if (!(g.flags[c] & F_FLUID)) { nut[c] = T(0); return; }
-    const Stencil<T> S(g, u, v, w, i, j, k);
-    T s11 = (u[c] - S.U(i - 1, j, k)) * g.rdx;
-    T s22 = (v[c] - S.V(i, j - 1, k)) * g.rdy;
-    T s33 = (w[c] - S.W(i, j, k - 1)) * g.rdz[k];
-    T s12 = T(0.25) * (S.s12(i - 1, j - 1, k) + S.s12(i, j - 1, k) + S.s12(i - 1, j, k) + S.s12(i, j, k));
-    T s13 = T(0.25) * (S.s13(i - 1, j, k - 1) + S.s13(i, j, k - 1) + S.s13(i - 1, j, k) + S.s13(i, j, k));
-    T s23 = T(0.25) * (S.s23(i, j - 1, k - 1) + S.s23(i, j, k - 1) + S.s23(i, j - 1, k) + S.s23(i, j, k));
-    T smag = sqrt(T(2) * (s11 * s11 + s22 * s22 + s33 * s33) + T(4) * (s12 * s12 + s13 * s13 + s23 * s23));
-    nut[c] = g.delta2[k] * smag;
-}
 
 // nu_t ghost layer: zero gradient (the adjacent interior value) or periodic
 // wrap, axis by axis (x over interior j, k; y over all i; z over all i, j), so
@@ -218,22 +208,30 @@ __global__ void k_nut_ghost(Dom d, T* nut, int axis) {
     }
 }
 
-template <typename T>
-int launch_nut(const Geo<T>& g, const T* u, const T* v, const T* w, T* nut, cudaStream_t s) {
-    const Dom& d = g.d;
-    k_nut<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(g, u, v, w, nut);
-    k_nut_ghost<T><<<dim3((d.ny + 127) / 128, d.nz), 128, 0, s>>>(d, nut, 0);
-    k_nut_ghost<T><<<dim3((d.nx + 2 + 127) / 128, d.nz), 128, 0, s>>>(d, nut, 1);
-    k_nut_ghost<T><<<dim3((d.nx + 2 + 127) / 128, d.ny + 2), 128, 0, s>>>(d, nut, 2);
-    return 4;
-}
-
 // ---------------------------------------------------------------------------
 // velfg + les (SGS) + adam + feedbf.  nu_t ghosts hold the clamped / wrapped
 // values (k_nut_ghost), so the edge averages read it directly.
 
+// nu_t averaged onto cell edges, over any accessor D with operator()(i, j, k)
+template <typename T, typename D>
+struct NutOps {
+    __device__ __forceinline__ const D& self() const { return static_cast<const D&>(*this); }
+    __device__ __forceinline__ T xy(int i, int j, int k) const {
+        const D& N = self();
+        return T(0.25) * (N(i, j, k) + N(i + 1, j, k) + N(i, j + 1, k) + N(i + 1, j + 1, k));
+    }
+    __device__ __forceinline__ T xz(int i, int j, int k) const {
+        const D& N = self();
+        return T(0.25) * (N(i, j, k) + N(i + 1, j, k) + N(i, j, k + 1) + N(i + 1, j, k + 1));
+    }
+    __device__ __forceinline__ T yz(int i, int j, int k) const {
+        const D& N = self();
+        return T(0.25) * (N(i, j, k) + N(i, j + 1, k) + N(i, j, k + 1) + N(i, j + 1, k + 1));
+    }
+};
+
 template <typename T>
-struct Nut {
+struct Nut : NutOps<T, Nut<T>> {
     const T* nut;
     long long c0;
     int i0, j0, k0, px, pl;
@@ -242,19 +240,38 @@ struct Nut {
     __device__ __forceinline__ T operator()(int i, int j, int k) const {
         return nut[c0 + ((i - i0) + (j - j0) * px + (k - k0) * pl)];
     }
-    __device__ __forceinline__ T xy(int i, int j, int k) const {
-        return T(0.25) * ((*this)(i, j, k) + (*this)(i + 1, j, k) + (*this)(i, j + 1, k) + (*this)(i + 1, j + 1, k));
-    }
-    __device__ __forceinline__ T xz(int i, int j, int k) const {
-        return T(0.25) * ((*this)(i, j, k) + (*this)(i + 1, j, k) + (*this)(i, j, k + 1) + (*this)(i + 1, j, k + 1));
-    }
-    __device__ __forceinline__ T yz(int i, int j, int k) const {
-        return T(0.25) * ((*this)(i, j, k) + (*this)(i, j + 1, k) + (*this)(i, j, k + 1) + (*this)(i, j + 1, k + 1));
+};
+
+// the same reads from a shared-memory window: planes in 4 rolling slots
+// (plane k in slot k & 3), each MY rows of MX cells, the window's first cell
+// being (ib, jb)
+template <typename T, int MX, int MY>
+struct SmemStencil : StrainOps<T, SmemStencil<T, MX, MY>> {
+    const Geo<T>& g;
+    const T* su;
+    const T* sv;
+    const T* sw;
+    int ib, jb;
+    __device__ __forceinline__ SmemStencil(const Geo<T>& g_, const T* su_, const T* sv_, const T* sw_, int ib_, int jb_)
+        : g(g_), su(su_), sv(sv_), sw(sw_), ib(ib_), jb(jb_) {}
+    __device__ __forceinline__ int at(int i, int j, int k) const { return ((k & 3) * MY + (j - jb)) * MX + (i - ib); }
+    __device__ __forceinline__ T U(int i, int j, int k) const { return su[at(i, j, k)]; }
+    __device__ __forceinline__ T V(int i, int j, int k) const { return sv[at(i, j, k)]; }
+    __device__ __forceinline__ T W(int i, int j, int k) const { return sw[at(i, j, k)]; }
+};
+
+template <typename T, int MX, int MY>
+struct SmemNut : NutOps<T, SmemNut<T, MX, MY>> {
+    const T* sn;
+    int ib, jb;
+    __device__ __forceinline__ SmemNut(const T* sn_, int ib_, int jb_) : sn(sn_), ib(ib_), jb(jb_) {}
+    __device__ __forceinline__ T operator()(int i, int j, int k) const {
+        return sn[((k & 3) * MY + (j - jb)) * MX + (i - ib)];
     }
 };
 
-template <typename T>
-__device__ __forceinline__ T velfg_u(const Geo<T>& g, const Stencil<T>& S, int i, int j, int k) {
+template <typename T, typename SA>
+__device__ __forceinline__ T velfg_u(const Geo<T>& g, const SA& S, int i, int j, int k) {
     const T dx = g.dx, dy = g.dy, rdx = g.rdx, rdy = g.rdy;
     T um = S.U(i - 1, j, k), uc = S.U(i, j, k), up = S.U(i + 1, j, k);
     T cov1_i = T(0.5) * (um + uc) * (uc - um) * rdx;
@@ -274,8 +291,8 @@ __device__ __forceinline__ T velfg_u(const Geo<T>& g, const Stencil<T>& S, int i
     return -(covx + covy + covz) + g.nu * dfu;
 }
 
-template <typename T>
-__device__ __forceinline__ T velfg_v(const Geo<T>& g, const Stencil<T>& S, int i, int j, int k) {
+template <typename T, typename SA>
+__device__ __forceinline__ T velfg_v(const Geo<T>& g, const SA& S, int i, int j, int k) {
     const T dx = g.dx, dy = g.dy, rdx = g.rdx, rdy = g.rdy;
     T vm = S.V(i, j - 1, k), vc = S.V(i, j, k), vp = S.V(i, j + 1, k);
     T cov_j = T(0.5) * (vm + vc) * (vc - vm) * rdy;
@@ -294,8 +311,8 @@ __device__ __forceinline__ T velfg_v(const Geo<T>& g, const Stencil<T>& S, int i
     return -(covx + covy + covz) + g.nu * dfv;
 }
 
-template <typename T>
-__device__ __forceinline__ T velfg_w(const Geo<T>& g, const Stencil<T>& S, int i, int j, int k) {
+template <typename T, typename SA>
+__device__ __forceinline__ T velfg_w(const Geo<T>& g, const SA& S, int i, int j, int k) {
     const T dx = g.dx, dy = g.dy, rdx = g.rdx, rdy = g.rdy;
     const T dzk = g.dz[k], dzp = g.dz[k + 1], rdzk = g.rdz[k], rdzp = g.rdz[k + 1];
     const T rsum = T(1) / (dzk + dzp);
@@ -316,8 +333,9 @@ __device__ __forceinline__ T velfg_w(const Geo<T>& g, const Stencil<T>& S, int i
     return -(covx + covy + covz) + g.nu * dfw;
 }
 
-template <typename T>
-__device__ __forceinline__ T sgs_u(const Geo<T>& g, const Stencil<T>& S, const Nut<T>& N, int i, int j, int k) {
+template <typename T, typename SA, typename NA>
+__device__ __forceinline__ T sgs_u(const Geo<T>& g, const SA& S, const NA& N, int i,
+                                        int j, int k) {
     T t11_i = T(2) * N(i, j, k) * (S.U(i, j, k) - S.U(i - 1, j, k)) * g.rdx;
     T t11_ip = T(2) * N(i + 1, j, k) * (S.U(i + 1, j, k) - S.U(i, j, k)) * g.rdx;
     T t12_n = T(2) * N.xy(i, j, k) * S.s12(i, j, k);
@@ -326,8 +344,9 @@ __device__ __forceinline__ T sgs_u(const Geo<T>& g, const Stencil<T>& S, const N
     T t13_b = T(2) * N.xz(i, j, k - 1) * S.s13(i, j, k - 1);
     return (t11_ip - t11_i) * g.rdx + (t12_n - t12_s) * g.rdy + (t13_t - t13_b) * g.rdz[k];
 }
-template <typename T>
-__device__ __forceinline__ T sgs_v(const Geo<T>& g, const Stencil<T>& S, const Nut<T>& N, int i, int j, int k) {
+template <typename T, typename SA, typename NA>
+__device__ __forceinline__ T sgs_v(const Geo<T>& g, const SA& S, const NA& N, int i,
+                                        int j, int k) {
     T t22_j = T(2) * N(i, j, k) * (S.V(i, j, k) - S.V(i, j - 1, k)) * g.rdy;
     T t22_jp = T(2) * N(i, j + 1, k) * (S.V(i, j + 1, k) - S.V(i, j, k)) * g.rdy;
     T t12_e = T(2) * N.xy(i, j, k) * S.s12(i, j, k);
@@ -336,8 +355,9 @@ __device__ __forceinline__ T sgs_v(const Geo<T>& g, const Stencil<T>& S, const N
     T t23_b = T(2) * N.yz(i, j, k - 1) * S.s23(i, j, k - 1);
     return (t12_e - t12_w) * g.rdx + (t22_jp - t22_j) * g.rdy + (t23_t - t23_b) * g.rdz[k];
 }
-template <typename T>
-__device__ __forceinline__ T sgs_w(const Geo<T>& g, const Stencil<T>& S, const Nut<T>& N, int i, int j, int k) {
+template <typename T, typename SA, typename NA>
+__device__ __forceinline__ T sgs_w(const Geo<T>& g, const SA& S, const NA& N, int i,
+                                        int j, int k) {
     T t33_k = T(2) * N(i, j, k) * (S.W(i, j, k) - S.W(i, j, k - 1)) * g.rdz[k];
     T t33_kp = T(2) * N(i, j, k + 1) * (S.W(i, j, k + 1) - S.W(i, j, k)) * g.rdz[k + 1];
     T t13_e = T(2) * N.xz(i, j, k) * S.s13(i, j, k);
@@ -347,45 +367,171 @@ __device__ __forceinline__ T sgs_w(const Geo<T>& g, const Stencil<T>& S, const N
     return (t13_e - t13_w) * g.rdx + (t23_n - t23_s) * g.rdy + (t33_kp - t33_k) * g.rdzs[k];
 }
 
+// Plane kk of NF fields into slot kk & 3 of their shared-memory windows
+// (MY rows of MX cells from padded cell (ib, jb); zeros outside the padded box).
+// The trip count is fixed, so every load of a plane is in flight before the
+// first store to shared memory.
+template <typename T, int NF, int MX, int MY, int NT>
+__device__ __forceinline__ void window_load(const Dom& d, const T* const (&src)[NF], T* const (&dst)[NF], int ib,
+                                            int jb, int kk, int tid) {
+    constexpr int NP = MX * MY;
+    const int o = (kk & 3) * NP;
+#pragma unroll
+    for (int rep = 0; rep < (NP + NT - 1) / NT; ++rep) {
+        const int q = tid + rep * NT;
+        if (q >= NP) break;
+        const int gi = ib + q % MX, gj = jb + q / MX;
+        T val[NF];
+        const bool in = gi <= d.nx + 1 && gj <= d.ny + 1;
+        const long long x = in ? d.at(gi, gj, kk) : 0;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) val[f] = in ? src[f][x] : T(0);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) dst[f][o + q] = val[f];
+    }
+}
+
+// A CTA owns a 32 x 8 column of cells and marches up kc planes.  The planes
+// k-1 .. k+1 of u, v, w and nu_t, each with a 1-cell ring, sit in shared
+// memory in 4 rolling slots: the loads of plane k+1 go to the slot that plane
+// k-3 held, which no thread reads any more, so one barrier per plane
+// suffices.  Every read of the per-cell formulas then hits shared memory
+// (the previous one-thread-per-cell version waited on ~150 dependent global
+// loads per cell).  The arithmetic is the per-cell formulas above, unchanged.
+constexpr int kMomTX = 32, kMomTY = 8;
+
 template <typename T>
-__global__ void k_momentum(Geo<T> g, const T* u, const T* v, const T* w, const T* nut, T* fu, T* fv,
-                           T* fw, T* us, T* vs, T* ws, const Scalars* sc) {
+__global__ void __launch_bounds__(kMomTX * kMomTY)
+k_momentum(Geo<T> g, const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ w,
+           const T* __restrict__ nut, T* __restrict__ fu, T* __restrict__ fv, T* __restrict__ fw, T* __restrict__ us,
+           T* __restrict__ vs, T* __restrict__ ws, const Scalars* __restrict__ sc, int kc) {
+    constexpr int MX = kMomTX + 2, MY = kMomTY + 2, NP = MX * MY, NT = kMomTX * kMomTY;
+    __shared__ T sU[4 * NP], sV[4 * NP], sW[4 * NP], sN[4 * NP];
     const Dom& d = g.d;
     const bool first = sc->step == 0;
-    int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
-    int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    int k = blockIdx.z + 1;
-    if (i > d.nx || j > d.ny) return;
-    long long c = d.at(i, j, k);
-    const uint8_t f = g.flags[c];
-    const Stencil<T> S(g, u, v, w, i, j, k);
-    const Nut<T> N(d, nut, i, j, k);
-    if (i <= (d.perx ? d.nx : d.nx - 1)) {
-        T F = velfg_u(g, S, i, j, k) + sgs_u(g, S, N, i, j, k);
-        T Fh = first ? F : T(1.5) * F - T(0.5) * fu[c];
-        fu[c] = F;
-        us[c] = (f & F_E) ? u[c] + g.dt * Fh : T(0);
+    const int tid = threadIdx.x + kMomTX * threadIdx.y;
+    const int ib = blockIdx.x * kMomTX, jb = blockIdx.y * kMomTY;    // window corner (ring included)
+    const int i = ib + 1 + threadIdx.x, j = jb + 1 + threadIdx.y;
+    const int k0 = 1 + blockIdx.z * kc, k1 = min(k0 + kc, d.nz + 1);
+    const T* const src[4] = {u, v, w, nut};
+    T* const dst[4] = {sU, sV, sW, sN};
+    auto load = [&](int kk) { window_load<T, 4, MX, MY, NT>(d, src, dst, ib, jb, kk, tid); };
+    const SmemStencil<T, MX, MY> S(g, sU, sV, sW, ib, jb);
+    const SmemNut<T, MX, MY> N(sN, ib, jb);
+    load(k0 - 1);
+    load(k0);
+    const bool own = i <= d.nx && j <= d.ny;
+    for (int k = k0; k < k1; ++k) {
+        // the cell's own flags and previous tendencies, issued before the
+        // window loads and the barrier so that their latency overlaps them
+        const long long c = own ? d.at(i, j, k) : 0;
+        uint8_t f = 0;
+        T fu0 = T(0), fv0 = T(0), fw0 = T(0);
+        if (own) {
+            f = g.flags[c];
+            if (!first) {
+                fu0 = fu[c];
+                fv0 = fv[c];
+                fw0 = fw[c];
+            }
+        }
+        load(k + 1);
+        __syncthreads();
+        if (!own) continue;
+        if (i <= (d.perx ? d.nx : d.nx - 1)) {
+            T F = velfg_u(g, S, i, j, k) + sgs_u(g, S, N, i, j, k);
+            T Fh = first ? F : T(1.5) * F - T(0.5) * fu0;
+            fu[c] = F;
+            us[c] = (f & F_E) ? S.U(i, j, k) + g.dt * Fh : T(0);
+        }
+        if (j <= (d.pery ? d.ny : d.ny - 1)) {
+            T F = velfg_v(g, S, i, j, k) + sgs_v(g, S, N, i, j, k);
+            T Fh = first ? F : T(1.5) * F - T(0.5) * fv0;
+            fv[c] = F;
+            vs[c] = (f & F_N) ? S.V(i, j, k) + g.dt * Fh : T(0);
+        }
+        if (k <= (d.perz ? d.nz : d.nz - 1)) {
+            T F = velfg_w(g, S, i, j, k) + sgs_w(g, S, N, i, j, k);
+            T Fh = first ? F : T(1.5) * F - T(0.5) * fw0;
+            fw[c] = F;
+            ws[c] = (f & F_T) ? S.W(i, j, k) + g.dt * Fh : T(0);
+        }
     }
-    if (j <= (d.pery ? d.ny : d.ny - 1)) {
-        T F = velfg_v(g, S, i, j, k) + sgs_v(g, S, N, i, j, k);
-        T Fh = first ? F : T(1.5) * F - T(0.5) * fv[c];
-        fv[c] = F;
-        vs[c] = (f & F_N) ? v[c] + g.dt * Fh : T(0);
+}
+
+// les (Smagorinsky eddy viscosity at cell centres) on the same staged
+// window: u, v, w planes k-1 .. k+1 with a 1-cell ring
+template <typename T>
+__global__ void __launch_bounds__(kMomTX * kMomTY)
+k_nut(Geo<T> g, const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ w, T* __restrict__ nut,
+      int kc) {
+    constexpr int MX = kMomTX + 2, MY = kMomTY + 2, NP = MX * MY, NT = kMomTX * kMomTY;
+    __shared__ T sU[4 * NP], sV[4 * NP], sW[4 * NP];
+    const Dom& d = g.d;
+    const int tid = threadIdx.x + kMomTX * threadIdx.y;
+    const int ib = blockIdx.x * kMomTX, jb = blockIdx.y * kMomTY;
+    const int i = ib + 1 + threadIdx.x, j = jb + 1 + threadIdx.y;
+    const int k0 = 1 + blockIdx.z * kc, k1 = min(k0 + kc, d.nz + 1);
+    const T* const src[3] = {u, v, w};
+    T* const dst[3] = {sU, sV, sW};
+    const SmemStencil<T, MX, MY> S(g, sU, sV, sW, ib, jb);
+    const bool own = i <= d.nx && j <= d.ny;
+    window_load<T, 3, MX, MY, NT>(d, src, dst, ib, jb, k0 - 1, tid);
+    window_load<T, 3, MX, MY, NT>(d, src, dst, ib, jb, k0, tid);
+    for (int k = k0; k < k1; ++k) {
+        const long long c = own ? d.at(i, j, k) : 0;
+        const uint8_t f = own ? g.flags[c] : 0;
+        window_load<T, 3, MX, MY, NT>(d, src, dst, ib, jb, k + 1, tid);
+        __syncthreads();
+        if (!own) continue;
+        if (!(f & F_FLUID)) {
+            nut[c] = T(0);
+            continue;
+        }
+        T s11 = (S.U(i, j, k) - S.U(i - 1, j, k)) * g.rdx;
+        T s22 = (S.V(i, j, k) - S.V(i, j - 1, k)) * g.rdy;
+        T s33 = (S.W(i, j, k) - S.W(i, j, k - 1)) * g.rdz[k];
+        T s12 = T(0.25) * (S.s12(i - 1, j - 1, k) + S.s12(i, j - 1, k) + S.s12(i - 1, j, k) + S.s12(i, j, k));
+        T s13 = T(0.25) * (S.s13(i - 1, j, k - 1) + S.s13(i, j, k - 1) + S.s13(i - 1, j, k) + S.s13(i, j, k));
+        T s23 = T(0.25) * (S.s23(i, j - 1, k - 1) + S.s23(i, j, k - 1) + S.s23(i, j - 1, k) + S.s23(i, j, k));
+        T smag = sqrt(T(2) * (s11 * s11 + s22 * s22 + s33 * s33) + T(4) * (s12 * s12 + s13 * s13 + s23 * s23));
+        nut[c] = g.delta2[k] * smag;
     }
-    if (k <= (d.perz ? d.nz : d.nz - 1)) {
-        T F = velfg_w(g, S, i, j, k) + sgs_w(g, S, N, i, j, k);
-        T Fh = first ? F : T(1.5) * F - T(0.5) * fw[c];
-        fw[c] = F;
-        ws[c] = (f & F_T) ? w[c] + g.dt * Fh : T(0);
+}
+
+// planes per CTA: enough CTAs for a few waves on every SM, few ring planes
+int momentum_kc(const Dom& d) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 132;
     }
+    const long long cols = (long long)((d.nx + kMomTX - 1) / kMomTX) * ((d.ny + kMomTY - 1) / kMomTY);
+    const long long target = (long long)sms * 24;
+    const long long kc = (cols * d.nz + target - 1) / target;
+    return (int)(kc < 4 ? 4 : (kc > 32 ? 32 : kc));
+}
+
+template <typename T>
+int launch_nut(const Geo<T>& g, const T* u, const T* v, const T* w, T* nut, cudaStream_t s) {
+    const Dom& d = g.d;
+    const int kc = momentum_kc(d);
+    k_nut<T><<<dim3((d.nx + kMomTX - 1) / kMomTX, (d.ny + kMomTY - 1) / kMomTY, (d.nz + kc - 1) / kc),
+               dim3(kMomTX, kMomTY), 0, s>>>(g, u, v, w, nut, kc);
+    k_nut_ghost<T><<<dim3((d.ny + 127) / 128, d.nz), 128, 0, s>>>(d, nut, 0);
+    k_nut_ghost<T><<<dim3((d.nx + 2 + 127) / 128, d.nz), 128, 0, s>>>(d, nut, 1);
+    k_nut_ghost<T><<<dim3((d.nx + 2 + 127) / 128, d.ny + 2), 128, 0, s>>>(d, nut, 2);
+    return 4;
 }
 
 template <typename T>
 int launch_momentum(const Geo<T>& g, const T* u, const T* v, const T* w, const T* nut, T* fu, T* fv,
                     T* fw, T* us, T* vs, T* ws, const Scalars* sc, cudaStream_t s) {
     const Dom& d = g.d;
-    k_momentum<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(
-        g, u, v, w, nut, fu, fv, fw, us, vs, ws, sc);
+    const int kc = momentum_kc(d);
+    k_momentum<T><<<dim3((d.nx + kMomTX - 1) / kMomTX, (d.ny + kMomTY - 1) / kMomTY, (d.nz + kc - 1) / kc),
+                    dim3(kMomTX, kMomTY), 0, s>>>(g, u, v, w, nut, fu, fv, fw, us, vs, ws, sc, kc);
     return 1;
 }
 
@@ -455,40 +601,51 @@ __device__ bool grid_sum(double (&x)[NV], const Reduce& r) {
 // bondv1 on u*: inflow face copied, zero-gradient outflow, FP64 mass-flux
 // correction (one block; the plane is small), periodic face copies.
 
+// inflow face copied into u*, inflow and outflow fluxes summed (FP64, last
+// block), the correction factor stored; periodic x: the face copy only
 template <typename T>
-__global__ void k_outflow(Geo<T> g, const T* u, T* us, T* vs, T* ws, Scalars* sc) {
+__global__ void k_outflow_sum(Geo<T> g, const T* u, T* us, Reduce red) {
     const Dom& d = g.d;
     const int n = d.ny * d.nz;
-    if (d.perx) {
-        for (int q = threadIdx.x; q < n; q += blockDim.x) {
-            int j = q % d.ny + 1, k = q / d.ny + 1;
+    const int q0 = blockIdx.x * blockDim.x + threadIdx.x, qs = gridDim.x * blockDim.x;
+    if (d.perx) {        // uniform over the grid
+        for (int q = q0; q < n; q += qs) {
+            const int j = q % d.ny + 1, k = q / d.ny + 1;
             us[d.at(0, j, k)] = us[d.at(d.nx, j, k)];
         }
-        if (threadIdx.x == 0) { sc->mass_factor = 1.0; sc->q_in = sc->q_out = 0.0; }
+        if (q0 == 0) {
+            red.sc->mass_factor = 1.0;
+            red.sc->q_in = red.sc->q_out = 0.0;
+        }
         return;
     }
     double x[2] = {0.0, 0.0};
-    for (int q = threadIdx.x; q < n; q += blockDim.x) {
-        int j = q % d.ny + 1, k = q / d.ny + 1;
-        T ui = u[d.at(0, j, k)];
-        T uo = us[d.at(d.nx - 1, j, k)];
+    for (int q = q0; q < n; q += qs) {
+        const int j = q % d.ny + 1, k = q / d.ny + 1;
+        const T ui = u[d.at(0, j, k)];
+        const T uo = us[d.at(d.nx - 1, j, k)];
         us[d.at(0, j, k)] = ui;
         x[0] += (double)ui * (double)g.dy * g.dz64[k];
         x[1] += (double)uo * (double)g.dy * g.dz64[k];
     }
-    block_sum<2>(x);
-    __shared__ double fac;
-    if (threadIdx.x == 0) {
-        double f = fabs(x[1]) > 1e-300 ? x[0] / x[1] : 1.0;
-        fac = f;
+    if (grid_sum<2>(x, red) && threadIdx.x == 0) {
+        Scalars* sc = red.sc;
+        const double f = fabs(x[1]) > 1e-300 ? x[0] / x[1] : 1.0;
         sc->mass_factor = f;
         sc->q_in = x[0];
         sc->q_out = x[1] * f;
     }
-    __syncthreads();
-    const double f = fac;
-    for (int q = threadIdx.x; q < n; q += blockDim.x) {
-        int j = q % d.ny + 1, k = q / d.ny + 1;
+}
+
+// zero-gradient outflow scaled by the mass-flux correction
+template <typename T>
+__global__ void k_outflow_apply(Geo<T> g, T* us, const Scalars* sc) {
+    const Dom& d = g.d;
+    if (d.perx) return;
+    const int n = d.ny * d.nz;
+    const double f = sc->mass_factor;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        const int j = q % d.ny + 1, k = q / d.ny + 1;
         us[d.at(d.nx, j, k)] = (T)((double)us[d.at(d.nx - 1, j, k)] * f);
     }
 }
@@ -503,10 +660,13 @@ __global__ void k_wrap_faces(Dom d, T* vs, T* ws, int zaxis) {
 }
 
 template <typename T>
-int launch_outflow(const Geo<T>& g, const T* u, T* us, T* vs, T* ws, Scalars* sc, cudaStream_t s) {
+int launch_outflow(const Geo<T>& g, const T* u, T* us, T* vs, T* ws, const Reduce& red, cudaStream_t s) {
     const Dom& d = g.d;
-    k_outflow<T><<<1, 1024, 0, s>>>(g, u, us, vs, ws, sc);
-    int n = 1;
+    const int n_face = d.ny * d.nz;
+    const int nb = n_face < 64 * 256 ? (n_face + 255) / 256 : 64;
+    k_outflow_sum<T><<<nb, 256, 0, s>>>(g, u, us, red);
+    k_outflow_apply<T><<<nb, 256, 0, s>>>(g, us, red.sc);
+    int n = 2;
     if (d.pery) {
         k_wrap_faces<T><<<dim3((d.nx + 127) / 128, d.nz), 128, 0, s>>>(d, vs, ws, 0);
         n++;
@@ -521,22 +681,35 @@ int launch_outflow(const Geo<T>& g, const T* u, T* us, T* vs, T* ws, Scalars* sc
 // ---------------------------------------------------------------------------
 // press: rhs = div(u*)/dt on fluid cells; FP64 dz-weighted mean (last block)
 
+// Column kernels with a grid reduction: each thread walks kc planes of its
+// (i, j) column, kc chosen so that at most ~2048 CTAs leave partial sums for
+// the last block to add (one CTA per plane left it ~10^5 partials on large
+// grids, added serially).
+int column_kc(const Dom& d) {
+    const long long cols = (long long)((d.nx + 31) / 32) * ((d.ny + 7) / 8);
+    const long long kc = (cols * d.nz + 2047) / 2048;
+    return (int)(kc < 1 ? 1 : (kc > d.nz ? d.nz : kc));
+}
+
 template <typename T>
-__global__ void k_rhs(Geo<T> g, const T* us, const T* vs, const T* ws, T* rhs, double vfluid, Reduce r) {
+__global__ void k_rhs(Geo<T> g, const T* us, const T* vs, const T* ws, T* rhs, double vfluid, Reduce r, int kc) {
     const Dom& d = g.d;
-    int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
-    int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    int k = blockIdx.z + 1;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    const int kb = blockIdx.z * kc + 1, ke = min(kb + kc, d.nz + 1);
     double x[1] = {0.0};
     if (i <= d.nx && j <= d.ny) {
-        long long c = d.at(i, j, k);
-        T val = T(0);
-        if (g.flags[c] & F_FLUID) {
-            T div = (us[c] - us[c - 1]) / g.dx + (vs[c] - vs[c - d.px]) / g.dy + (ws[c] - ws[c - d.plane]) / g.dz[k];
-            val = div / g.dt;
-            x[0] = g.dz64[k] * (double)val;
+        long long c = d.at(i, j, kb);
+        for (int k = kb; k < ke; ++k, c += d.plane) {
+            T val = T(0);
+            if (g.flags[c] & F_FLUID) {
+                T div = (us[c] - us[c - 1]) / g.dx + (vs[c] - vs[c - d.px]) / g.dy +
+                        (ws[c] - ws[c - d.plane]) / g.dz[k];
+                val = div / g.dt;
+                x[0] += g.dz64[k] * (double)val;
+            }
+            rhs[c] = val;
         }
-        rhs[c] = val;
     }
     if (grid_sum<1>(x, r)) {
         if (threadIdx.x == 0 && threadIdx.y == 0) r.sc->rhs_mean = vfluid > 0.0 ? x[0] / vfluid : 0.0;
@@ -547,22 +720,26 @@ template <typename T>
 int launch_rhs(const Geo<T>& g, const T* us, const T* vs, const T* ws, T* rhs, double vfluid,
                const Reduce& r, cudaStream_t s) {
     const Dom& d = g.d;
-    k_rhs<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(g, us, vs, ws, rhs, vfluid, r);
+    const int kc = column_kc(d);
+    k_rhs<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, (d.nz + kc - 1) / kc), dim3(32, 8), 0, s>>>(
+        g, us, vs, ws, rhs, vfluid, r, kc);
     return 1;
 }
 
 // caller-supplied rhs: zero non-fluid cells and compute the mean
 template <typename T>
-__global__ void k_rhs_mean(Geo<T> g, T* rhs, double vfluid, Reduce r) {
+__global__ void k_rhs_mean(Geo<T> g, T* rhs, double vfluid, Reduce r, int kc) {
     const Dom& d = g.d;
-    int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
-    int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    int k = blockIdx.z + 1;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    const int kb = blockIdx.z * kc + 1, ke = min(kb + kc, d.nz + 1);
     double x[1] = {0.0};
     if (i <= d.nx && j <= d.ny) {
-        long long c = d.at(i, j, k);
-        if (g.flags[c] & F_FLUID) x[0] = g.dz64[k] * (double)rhs[c];
-        else rhs[c] = T(0);
+        long long c = d.at(i, j, kb);
+        for (int k = kb; k < ke; ++k, c += d.plane) {
+            if (g.flags[c] & F_FLUID) x[0] += g.dz64[k] * (double)rhs[c];
+            else rhs[c] = T(0);
+        }
     }
     if (grid_sum<1>(x, r)) {
         if (threadIdx.x == 0 && threadIdx.y == 0) r.sc->rhs_mean = vfluid > 0.0 ? x[0] / vfluid : 0.0;
@@ -572,7 +749,9 @@ __global__ void k_rhs_mean(Geo<T> g, T* rhs, double vfluid, Reduce r) {
 template <typename T>
 int launch_rhs_mean(const Geo<T>& g, T* rhs, double vfluid, const Reduce& r, cudaStream_t s) {
     const Dom& d = g.d;
-    k_rhs_mean<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(g, rhs, vfluid, r);
+    const int kc = column_kc(d);
+    k_rhs_mean<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, (d.nz + kc - 1) / kc), dim3(32, 8), 0, s>>>(
+        g, rhs, vfluid, r, kc);
     return 1;
 }
 
@@ -889,6 +1068,42 @@ __global__ void k_project(Geo<T> g, const T* us, const T* vs, const T* ws, T* u,
     long long c = d.at(i, j, k);
     const uint8_t f = g.flags[c];
     const double pm = sc->p_mean;
+    if constexpr (std::is_same<T, float>::value) {
+        // FP32 fields: an open face joins two fluid cells, so the gauge cancels
+        // in the pressure difference; the difference is taken in FP64 (no
+        // cancellation error) and the rest of the update in FP32, which keeps
+        // this kernel off GB300's narrow FP64 pipe (no FP64 division)
+        const double praw = ph_in[c];
+        ph_out[c] = (f & F_FLUID) ? praw - pm : praw;
+        if (i <= (d.perx ? d.nx : d.nx - 1)) {
+            const int ie = (d.perx && i == d.nx) ? 1 : i + 1;
+            const float val = (f & F_E) ? us[c] - (g.dt * g.rdx) * (float)(ph_in[d.at(ie, j, k)] - praw) : 0.f;
+            u[c] = val;
+            if (d.perx && i == d.nx) u[d.at(0, j, k)] = val;
+        } else {
+            u[c] = us[c];
+        }
+        if (!d.perx && i == 1) u[d.at(0, j, k)] = us[d.at(0, j, k)];
+        if (j <= (d.pery ? d.ny : d.ny - 1)) {
+            const int jn = (d.pery && j == d.ny) ? 1 : j + 1;
+            const float val = (f & F_N) ? vs[c] - (g.dt * g.rdy) * (float)(ph_in[d.at(i, jn, k)] - praw) : 0.f;
+            v[c] = val;
+            if (d.pery && j == d.ny) v[d.at(i, 0, k)] = val;
+        } else {
+            v[c] = vs[c];
+        }
+        if (!d.pery && j == 1) v[d.at(i, 0, k)] = vs[d.at(i, 0, k)];
+        if (k <= (d.perz ? d.nz : d.nz - 1)) {
+            const int kt = (d.perz && k == d.nz) ? 1 : k + 1;
+            const float val = (f & F_T) ? ws[c] - (g.dt * g.rdzs[k]) * (float)(ph_in[d.at(i, j, kt)] - praw) : 0.f;
+            w[c] = val;
+            if (d.perz && k == d.nz) w[d.at(i, j, 0)] = val;
+        } else {
+            w[c] = ws[c];
+        }
+        if (!d.perz && k == 1) w[d.at(i, j, 0)] = ws[d.at(i, j, 0)];
+        return;
+    }
     const double dt = (double)g.dt;
     auto gp = [&](long long q) -> double { return (g.flags[q] & F_FLUID) ? ph_in[q] - pm : ph_in[q]; };
     const double pc = gp(c);
@@ -1197,7 +1412,7 @@ int launch_refine_ens(const EnsTab<float>& tab, int dcur, const CondArgs& ca, cu
     template int launch_nut<T>(const Geo<T>&, const T*, const T*, const T*, T*, cudaStream_t);          \
     template int launch_momentum<T>(const Geo<T>&, const T*, const T*, const T*, const T*, T*, T*, T*,  \
                                     T*, T*, T*, const Scalars*, cudaStream_t);                          \
-    template int launch_outflow<T>(const Geo<T>&, const T*, T*, T*, T*, Scalars*, cudaStream_t);        \
+    template int launch_outflow<T>(const Geo<T>&, const T*, T*, T*, T*, const Reduce&, cudaStream_t);   \
     template int launch_rhs<T>(const Geo<T>&, const T*, const T*, const T*, T*, double, const Reduce&,  \
                                cudaStream_t);                                                           \
     template int launch_rhs_mean<T>(const Geo<T>&, T*, double, const Reduce&, cudaStream_t);            \

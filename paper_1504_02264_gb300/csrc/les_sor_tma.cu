@@ -1,5 +1,4 @@
-// TMA variant of the fused red-black SOR sweep (Sec. 2.6) for FP32 domains
-// without periodic axes.
+// TMA variant of the fused red-black SOR sweep (Sec. 2.6) for FP32 domains.
 //
 // A CTA owns a 28 x BY x BZ block.  One thread issues three tiled bulk-tensor
 // copies (cp.async.bulk.tensor) into shared memory on one mbarrier: the
@@ -10,6 +9,13 @@
 // are in flight the threads build the per-plane cn1 table.  Then red on the
 // block + ring, black on the block, and the block is stored (unknowns only),
 // exactly as in the other fused variants (bit-identical iterate).
+//
+// Periodic axes: a copy cannot wrap, so after the copies land the blocks
+// whose halo crosses a periodic face overwrite the out-of-range cells of the
+// tiles with plain loads of their periodic images (d, r and flags), and the
+// ring planes take the coefficients of the wrapped plane.  Interior blocks
+// skip this step.  The persistent double-buffered variant (k_sor_pipe) stays
+// restricted to domains without periodic axes.
 //
 // Alignment: the d and r tiles start at padded column 28*bx (a multiple of 4
 // floats = 16 bytes); the flag tile starts at the multiple of 16 bytes below it
@@ -62,6 +68,26 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
 
 constexpr uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
+// periodic image of (i, j, k): false when no periodic axis wraps; otherwise
+// q = padded index of the image, or -1 when a non-periodic coordinate lies
+// outside the padded box (the copy's zero fill)
+__device__ __forceinline__ bool periodic_image(const Dom& d, int i, int j, int k, long long& q) {
+    bool w = false;
+    if (d.perx && (i < 1 || i > d.nx)) { i = ((i - 1) % d.nx + d.nx) % d.nx + 1; w = true; }
+    if (d.pery && (j < 1 || j > d.ny)) { j = ((j - 1) % d.ny + d.ny) % d.ny + 1; w = true; }
+    if (d.perz && (k < 1 || k > d.nz)) { k = ((k - 1) % d.nz + d.nz) % d.nz + 1; w = true; }
+    if (!w) return false;
+    q = (i < 0 || i > d.nx + 1 || j < 0 || j > d.ny + 1 || k < 0 || k > d.nz + 1) ? -1ll : d.at(i, j, k);
+    return true;
+}
+
+// plane whose coefficients a ring plane takes: wrapped on a periodic z axis,
+// else clamped to the padded range
+__device__ __forceinline__ int coef_plane(const Dom& d, int k) {
+    if (d.perz && (k < 1 || k > d.nz)) return ((k - 1) % d.nz + d.nz) % d.nz + 1;
+    return min(max(k, 0), d.nz + 1);
+}
+
 template <int BY, int BZ>
 struct TmaTile {
     static constexpr int BX = 28, DXW = 36, FXW = 48;
@@ -80,8 +106,8 @@ struct TmaTile {
 template <int BY, int BZ, int NT>
 __global__ void __launch_bounds__(NT)
 k_sor_tma(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtensorMap tr,
-          const __grid_constant__ CUtensorMap tf, Geo<float> g, float* __restrict__ dout, int zero_arg,
-          Scalars* __restrict__ sc) {
+          const __grid_constant__ CUtensorMap tf, Geo<float> g, const float* __restrict__ din,
+          const float* __restrict__ rin, float* __restrict__ dout, int zero_arg, Scalars* __restrict__ sc) {
     using TT = TmaTile<BY, BZ>;
     constexpr int BX = TT::BX, DXW = TT::DXW, FXW = TT::FXW, DY = TT::DY, RY = TT::RY, RZ = TT::RZ;
     extern __shared__ __align__(128) unsigned char sm[];
@@ -111,7 +137,7 @@ k_sor_tma(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtens
     // per-plane coefficients and the block's rows of the cn1 table while the copies fly
     for (int q = tid; q < RZ * 64; q += NT) {
         const int kk = q >> 6, m = q & 63;
-        const int k = min(max(k0 - 1 + kk, 0), d.nz + 1);
+        const int k = coef_plane(d, k0 - 1 + kk);
         sCN[kk][m] = g.cn1[k * 64 + m];
         if (m == 0) {
             const float ct = g.cT[k], cb = g.cB[k];
@@ -134,6 +160,27 @@ k_sor_tma(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtens
         while (!mbar_try_wait(bar, 0))
             if (global_ns() - t1 > 1000000000ull) break;
         return;
+    }
+    if ((d.perx && (i0 - 2 < 1 || i0 + BX + 1 > d.nx)) || (d.pery && (j0 - 2 < 1 || j0 + BY + 1 > d.ny)) ||
+        (d.perz && (k0 - 2 < 1 || k0 + BZ + 1 > d.nz))) {
+        // halo across a periodic face: the images of the cells the sweep reads
+        // (d on i0-2 .. i0+BX+1 with a 2-cell halo in j, k; r and flags on the
+        // block + 1 ring)
+        if (!zero_start)
+            for (int q = tid; q < TT::DZ * DY * (BX + 4); q += NT) {
+                const int x = 2 + q % (BX + 4), y = (q / (BX + 4)) % DY, z = q / ((BX + 4) * DY);
+                long long s;
+                if (periodic_image(d, i0 - 4 + x, j0 - 2 + y, k0 - 2 + z, s)) sD[z][y][x] = s >= 0 ? din[s] : 0.f;
+            }
+        for (int q = tid; q < RZ * RY * (BX + 2); q += NT) {
+            const int x = q % (BX + 2), y = (q / (BX + 2)) % RY, z = q / ((BX + 2) * RY);
+            long long s;
+            if (periodic_image(d, i0 - 1 + x, j0 - 1 + y, k0 - 1 + z, s)) {
+                sR[z][y][x + 3] = s >= 0 ? rin[s] : 0.f;
+                sF[z][y][x + 3 + off] = s >= 0 ? g.flags[s] : (uint8_t)0;
+            }
+        }
+        __syncthreads();
     }
     const float omega = g.omega, cx = g.cx, cy = g.cy;
     auto relax = [&](int x, int y, int z, int kz, uint8_t f, float rhs) {
@@ -388,7 +435,8 @@ void launch_tma_cfg(const Geo<float>& g, const TmaMaps& m, int in, float* dout, 
                     cudaStream_t s) {
     const Dom& d = g.d;
     dim3 grid((d.nx + 27) / 28, (d.ny + BY - 1) / BY, (d.nz + BZ - 1) / BZ);
-    k_sor_tma<BY, BZ, NT><<<grid, NT, TmaTile<BY, BZ>::SMEM, s>>>(m.d[in], m.r, m.f, g, dout, zero, sc);
+    k_sor_tma<BY, BZ, NT><<<grid, NT, TmaTile<BY, BZ>::SMEM, s>>>(m.d[in], m.r, m.f, g, m.dptr[in], m.rptr, dout,
+                                                                  zero, sc);
 }
 
 using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
@@ -425,7 +473,9 @@ bool encode3d(CUtensorMap* map, CUtensorMapDataType type, size_t es, void* base,
 const int kTmaCfg[kNumTmaTiles][3] = {{8, 8, 256}, {12, 12, 512}, {16, 12, 512}, {16, 16, 512},
                                       {8, 8, 256}, {8, 8, 512}, {16, 8, 512}, {12, 12, 512}};
 
-bool tma_supported(const Dom& d) { return !d.perx && !d.pery && !d.perz; }
+bool tma_supported(const Dom&) { return true; }
+
+bool pipe_supported(const Dom& d) { return !d.perx && !d.pery && !d.perz; }
 
 cudaError_t tma_prepare() {
     cudaError_t e = cudaSuccess, x;
@@ -448,6 +498,9 @@ bool tma_encode(const Dom& d, float* dl0, float* dl1, float* rr, uint8_t* flags,
     for (int c = 0; c < kNumTmaTiles; ++c) {
         const int by = kTmaCfg[c][0], bz = kTmaCfg[c][1];
         TmaMaps& m = maps[c];
+        m.dptr[0] = dl0;
+        m.dptr[1] = dl1;
+        m.rptr = rr;
         if (!encode3d(&m.d[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, dl0, d, 36, by + 4, bz + 4)) return false;
         if (!encode3d(&m.d[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, dl1, d, 36, by + 4, bz + 4)) return false;
         if (!encode3d(&m.r, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, rr, d, 36, by + 2, bz + 2)) return false;

@@ -243,7 +243,17 @@ def test_fused_sor_matches_two_pass(prec, case):
     ref.step(2)
     want = ref.fields()
     tol = 0.0 if prec == "fp64" else 1e-6
-    tiles = list(range(17)) + (list(range(17, 25)) if (case == "city" and prec == "fp32") else [])
+    # TMA block tiles (17-20) on every FP32 grid, periodic halos included; the
+    # persistent TMA tiles (21-24) only without periodic axes
+    tiles = list(range(17))
+    if prec == "fp32":
+        tiles += list(range(17, 21)) + (list(range(21, 25)) if case == "city" else [])
+    if prec == "fp32" and case != "city":
+        d = les.Domain(sc, precision=p)
+        for tile in range(21, 25):
+            with pytest.raises(les.LesError):
+                d.set_sor_config(tile, 0)
+        d.close()
     for tile in tiles:
         for kc in ((0, 3, 5) if tile < 6 else (0,)):
             d = les.Domain(sc, precision=p)
