@@ -122,6 +122,7 @@ struct les_s {
     bool tma_ok = false;
     bool pipe_ok = false;                 // persistent TMA tiles (no periodic axis)
     float* cn1tab = nullptr;              // cn1 over (plane, open-face mask) for the pipelined sweep
+    double* diag64 = nullptr;             // FP64 diagonal over (plane, open-face mask), the residual's
     // learned warm start and training-pair recording
     int warm = LES_WARM_PREV;
     les_net_s* net = nullptr;
@@ -254,6 +255,7 @@ Geo<T> geo(les_s* h) {
     g.cB64 = h->cB64;
     g.flags = h->flags;
     g.cn1 = std::is_same<T, float>::value ? (const T*)h->cn1tab : nullptr;
+    g.diag64 = h->diag64;
     return g;
 }
 
@@ -1003,6 +1005,10 @@ int create_impl(les_s* h, const uint8_t* solid) {
         CK(cudaStreamSynchronize(h->stream));
         h->n_unk = (double)hc;
     }
+    if ((rc = dalloc(h, (void**)&h->diag64, (size_t)(G.nz + 2) * 64 * sizeof(double)))) return rc;
+    if (h->prec == LES_FP32) launch_diag_table<float>(geo<float>(h), h->diag64, h->stream);
+    else launch_diag_table<double>(geo<double>(h), h->diag64, h->stream);
+    CK(cudaGetLastError());
     if (h->prec == LES_FP32) {
         // cn1 over (plane, open-face mask), read by the FP32 sweep kernels
         if ((rc = dalloc(h, (void**)&h->cn1tab, (size_t)(G.nz + 2) * 64 * sizeof(float)))) return rc;

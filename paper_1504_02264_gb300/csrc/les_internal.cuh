@@ -103,6 +103,7 @@ struct Geo {
     const double* cB64;     // [nz+2]
     const uint8_t* flags;   // padded cell flags
     const T* cn1;           // [nz+2][64] cn1 over (plane, open-face mask); FP32 grids only (else null)
+    const double* diag64;   // [nz+2][64] FP64 diagonal of the Poisson operator over (plane, open-face mask)
 };
 
 struct Reduce {
@@ -227,6 +228,7 @@ bool tma_encode(const Dom& d, float* dl0, float* dl1, float* rr, uint8_t* flags,
 int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, const float* cn1tab, int cfg, int in, float* dout,
                    int zero, Scalars* sc, cudaStream_t s);
 int launch_cn1_table(const Geo<float>& g, float* tab, cudaStream_t s);
+template <typename T> int launch_diag_table(const Geo<T>& g, double* tab, cudaStream_t s);
 int launch_wait_selftest(unsigned long long limit_ns, int* status, cudaStream_t s);
 
 // learned warm start (les_kernels.cu): energy-norm line search along q and p += alpha q

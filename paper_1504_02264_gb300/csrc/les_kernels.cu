@@ -367,35 +367,43 @@ __device__ __forceinline__ T sgs_w(const Geo<T>& g, const SA& S, const NA& N, in
     return (t13_e - t13_w) * g.rdx + (t23_n - t23_s) * g.rdy + (t33_kp - t33_k) * g.rdzs[k];
 }
 
-// Plane kk of NF fields into slot kk & 3 of their shared-memory windows
-// (MY rows of MX cells from padded cell (ib, jb); zeros outside the padded box).
-// The trip count is fixed, so every load of a plane is in flight before the
-// first store to shared memory.
+// Plane kk of NF fields for slot kk & 3 of their shared-memory windows (MY
+// rows of MX cells from padded cell (ib, jb); zeros outside the padded box),
+// in two halves: window_fetch issues the global loads into registers,
+// window_put stores them, so a plane's loads can be in flight while the
+// previous plane is computed.  Fixed trip counts keep everything in registers.
 template <typename T, int NF, int MX, int MY, int NT>
-__device__ __forceinline__ void window_load(const Dom& d, const T* const (&src)[NF], T* const (&dst)[NF], int ib,
-                                            int jb, int kk, int tid) {
-    constexpr int NP = MX * MY;
-    const int o = (kk & 3) * NP;
+struct Window {
+    static constexpr int NP = MX * MY, REPS = (NP + NT - 1) / NT;
+    T val[REPS][NF];
+    __device__ __forceinline__ void fetch(const Dom& d, const T* const (&src)[NF], int ib, int jb, int kk, int tid) {
 #pragma unroll
-    for (int rep = 0; rep < (NP + NT - 1) / NT; ++rep) {
-        const int q = tid + rep * NT;
-        if (q >= NP) break;
-        const int gi = ib + q % MX, gj = jb + q / MX;
-        T val[NF];
-        const bool in = gi <= d.nx + 1 && gj <= d.ny + 1;
-        const long long x = in ? d.at(gi, gj, kk) : 0;
+        for (int rep = 0; rep < REPS; ++rep) {
+            const int q = tid + rep * NT;
+            const int gi = ib + q % MX, gj = jb + q / MX;
+            const bool in = q < NP && gi <= d.nx + 1 && gj <= d.ny + 1;
+            const long long x = in ? d.at(gi, gj, kk) : 0;
 #pragma unroll
-        for (int f = 0; f < NF; ++f) val[f] = in ? src[f][x] : T(0);
-#pragma unroll
-        for (int f = 0; f < NF; ++f) dst[f][o + q] = val[f];
+            for (int f = 0; f < NF; ++f) val[rep][f] = in ? src[f][x] : T(0);
+        }
     }
-}
+    __device__ __forceinline__ void put(T* const (&dst)[NF], int kk, int tid) const {
+        const int o = (kk & 3) * NP;
+#pragma unroll
+        for (int rep = 0; rep < REPS; ++rep) {
+            const int q = tid + rep * NT;
+            if (q < NP)
+#pragma unroll
+                for (int f = 0; f < NF; ++f) dst[f][o + q] = val[rep][f];
+        }
+    }
+};
 
 // A CTA owns a 32 x 8 column of cells and marches up kc planes.  The planes
 // k-1 .. k+1 of u, v, w and nu_t, each with a 1-cell ring, sit in shared
-// memory in 4 rolling slots: the loads of plane k+1 go to the slot that plane
-// k-3 held, which no thread reads any more, so one barrier per plane
-// suffices.  Every read of the per-cell formulas then hits shared memory
+// memory in 4 rolling slots: plane k+1 goes to the slot that plane k-3 held,
+// which no thread reads any more, so one barrier per plane suffices, and the
+// loads of plane k+2 are in flight (in registers) while plane k is computed.  Every read of the per-cell formulas then hits shared memory
 // (the previous one-thread-per-cell version waited on ~150 dependent global
 // loads per cell).  The arithmetic is the per-cell formulas above, unchanged.
 constexpr int kMomTX = 32, kMomTY = 8;
@@ -415,15 +423,18 @@ k_momentum(Geo<T> g, const T* __restrict__ u, const T* __restrict__ v, const T* 
     const int k0 = 1 + blockIdx.z * kc, k1 = min(k0 + kc, d.nz + 1);
     const T* const src[4] = {u, v, w, nut};
     T* const dst[4] = {sU, sV, sW, sN};
-    auto load = [&](int kk) { window_load<T, 4, MX, MY, NT>(d, src, dst, ib, jb, kk, tid); };
+    Window<T, 4, MX, MY, NT> win;
     const SmemStencil<T, MX, MY> S(g, sU, sV, sW, ib, jb);
     const SmemNut<T, MX, MY> N(sN, ib, jb);
-    load(k0 - 1);
-    load(k0);
+    win.fetch(d, src, ib, jb, k0 - 1, tid);
+    win.put(dst, k0 - 1, tid);
+    win.fetch(d, src, ib, jb, k0, tid);
+    win.put(dst, k0, tid);
+    win.fetch(d, src, ib, jb, k0 + 1, tid);
     const bool own = i <= d.nx && j <= d.ny;
     for (int k = k0; k < k1; ++k) {
         // the cell's own flags and previous tendencies, issued before the
-        // window loads and the barrier so that their latency overlaps them
+        // barrier so that their latency overlaps it
         const long long c = own ? d.at(i, j, k) : 0;
         uint8_t f = 0;
         T fu0 = T(0), fv0 = T(0), fw0 = T(0);
@@ -435,8 +446,10 @@ k_momentum(Geo<T> g, const T* __restrict__ u, const T* __restrict__ v, const T* 
                 fw0 = fw[c];
             }
         }
-        load(k + 1);
+        // plane k+1 into the slot plane k-3 held; plane k+2 in flight during plane k
+        win.put(dst, k + 1, tid);
         __syncthreads();
+        if (k + 2 <= k1) win.fetch(d, src, ib, jb, k + 2, tid);
         if (!own) continue;
         if (i <= (d.perx ? d.nx : d.nx - 1)) {
             T F = velfg_u(g, S, i, j, k) + sgs_u(g, S, N, i, j, k);
@@ -474,15 +487,20 @@ k_nut(Geo<T> g, const T* __restrict__ u, const T* __restrict__ v, const T* __res
     const int k0 = 1 + blockIdx.z * kc, k1 = min(k0 + kc, d.nz + 1);
     const T* const src[3] = {u, v, w};
     T* const dst[3] = {sU, sV, sW};
+    Window<T, 3, MX, MY, NT> win;
     const SmemStencil<T, MX, MY> S(g, sU, sV, sW, ib, jb);
     const bool own = i <= d.nx && j <= d.ny;
-    window_load<T, 3, MX, MY, NT>(d, src, dst, ib, jb, k0 - 1, tid);
-    window_load<T, 3, MX, MY, NT>(d, src, dst, ib, jb, k0, tid);
+    win.fetch(d, src, ib, jb, k0 - 1, tid);
+    win.put(dst, k0 - 1, tid);
+    win.fetch(d, src, ib, jb, k0, tid);
+    win.put(dst, k0, tid);
+    win.fetch(d, src, ib, jb, k0 + 1, tid);
     for (int k = k0; k < k1; ++k) {
         const long long c = own ? d.at(i, j, k) : 0;
         const uint8_t f = own ? g.flags[c] : 0;
-        window_load<T, 3, MX, MY, NT>(d, src, dst, ib, jb, k + 1, tid);
+        win.put(dst, k + 1, tid);
         __syncthreads();
+        if (k + 2 <= k1) win.fetch(d, src, ib, jb, k + 2, tid);
         if (!own) continue;
         if (!(f & F_FLUID)) {
             nut[c] = T(0);
@@ -582,9 +600,18 @@ __device__ bool grid_sum_at(double (&x)[NV], const Reduce& r, unsigned nb, unsig
     const int nt = blockDim.x * blockDim.y;
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-        double s = 0.0;
-        for (unsigned m = tid; m < nb; m += nt) s += __ldcg(&r.partials[(size_t)q * nb + m]);
-        x[q] = s;
+        // four independent chains so that four loads are in flight
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        const double* pq = r.partials + (size_t)q * nb;
+        unsigned m = tid;
+        for (; m + 3 * nt < nb; m += 4 * nt) {
+            s0 += __ldcg(&pq[m]);
+            s1 += __ldcg(&pq[m + nt]);
+            s2 += __ldcg(&pq[m + 2 * nt]);
+            s3 += __ldcg(&pq[m + 3 * nt]);
+        }
+        for (; m < nb; m += nt) s0 += __ldcg(&pq[m]);
+        x[q] = (s0 + s1) + (s2 + s3);
     }
     block_sum<NV>(x);
     if (tid == 0) *r.counter = 0u;
@@ -682,12 +709,12 @@ int launch_outflow(const Geo<T>& g, const T* u, T* us, T* vs, T* ws, const Reduc
 // press: rhs = div(u*)/dt on fluid cells; FP64 dz-weighted mean (last block)
 
 // Column kernels with a grid reduction: each thread walks kc planes of its
-// (i, j) column, kc chosen so that at most ~2048 CTAs leave partial sums for
+// (i, j) column, kc chosen so that at most ~8192 CTAs leave partial sums for
 // the last block to add (one CTA per plane left it ~10^5 partials on large
-// grids, added serially).
+// grids).
 int column_kc(const Dom& d) {
     const long long cols = (long long)((d.nx + 31) / 32) * ((d.ny + 7) / 8);
-    const long long kc = (cols * d.nz + 2047) / 2048;
+    const long long kc = (cols * d.nz + 8191) / 8192;
     return (int)(kc < 1 ? 1 : (kc > d.nz ? d.nz : kc));
 }
 
@@ -895,6 +922,7 @@ __device__ __forceinline__ int residual64_body(const Geo<T>& g, const double* ph
     const Dom& d = g.d;
     const int n = d.nx * d.ny * d.nz;
     const double mean = red.sc->rhs_mean;
+    const bool init = ca.mode == RES_INIT;
     double x[3] = {0.0, 0.0, 0.0};
     for (int q = b * blockDim.x + threadIdx.x; q < n; q += nb * blockDim.x) {
         int i, j, k;
@@ -915,12 +943,14 @@ __device__ __forceinline__ int residual64_body(const Geo<T>& g, const double* ph
             s += as * ph[s_];
             s += at * ph[t];
             s += ab * ph[b];
-            const double diag = ae + aw + an + as + at + ab;
+            // the coefficient sum from the table: the same FP64 sum, off the
+            // narrow FP64 pipe
+            const double diag = g.diag64[k * 64 + (f & 63)];
             const double bb = (double)rhs[c] - mean;
             const double res = bb - (s - diag * pc);
             r[c] = (T)res;
             x[0] += res * res;
-            x[1] += bb * bb;
+            if (init) x[1] += bb * bb;      // |b| is fixed for the solve: summed once, at its start
         }
         if (f & F_FLUID) x[2] += g.dz64[k] * pc;
     }
@@ -928,8 +958,9 @@ __device__ __forceinline__ int residual64_body(const Geo<T>& g, const double* ph
         if (threadIdx.x == 0 && threadIdx.y == 0) {
             Scalars* sc = red.sc;
             sc->res2 = x[0];
-            sc->rhs2 = x[1];
-            const double rel = x[1] == 0.0 ? sqrt(x[0]) : sqrt(x[0] / x[1]);
+            if (init) sc->rhs2 = x[1];
+            const double rhs2 = sc->rhs2;
+            const double rel = rhs2 == 0.0 ? sqrt(x[0]) : sqrt(x[0] / rhs2);
             const bool conv = rel <= ca.tol;
             const bool bad = !isfinite(rel);
             sc->rel = rel;
@@ -1344,6 +1375,26 @@ int launch_count_unknowns(const Dom& d, const uint8_t* flags, unsigned long long
     return 1;
 }
 
+// FP64 diagonal of the Poisson operator over (plane, open-face mask): the
+// sum of the open faces' coefficients in the order of the residual kernels
+template <typename T>
+__global__ void k_diag_table(Geo<T> g, double* tab) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (g.d.nz + 2) * 64) return;
+    const int k = q >> 6, m = q & 63;
+    Poisson<T> Q{g};
+    double ae, aw, an, as, at, ab;
+    Q.coefs((uint8_t)m, k, g.cx64, g.cy64, g.cT64, g.cB64, ae, aw, an, as, at, ab);
+    tab[q] = ae + aw + an + as + at + ab;
+}
+
+template <typename T>
+int launch_diag_table(const Geo<T>& g, double* tab, cudaStream_t s) {
+    const int n = (g.d.nz + 2) * 64;
+    k_diag_table<T><<<(n + 255) / 256, 256, 0, s>>>(g, tab);
+    return 1;
+}
+
 int max_reduce_blocks(const Dom& d) { return ((d.nx + 31) / 32) * ((d.ny + 7) / 8) * d.nz; }
 
 // ---------------------------------------------------------------------------
@@ -1424,6 +1475,7 @@ int launch_refine_ens(const EnsTab<float>& tab, int dcur, const CondArgs& ca, cu
     template int launch_project<T>(const Geo<T>&, const T*, const T*, const T*, T*, T*, T*,             \
                                    const double*, double*, Scalars*, cudaStream_t);                     \
     template int launch_rhs_eff<T>(const Geo<T>&, const T*, T*, const Scalars*, cudaStream_t);          \
+    template int launch_diag_table<T>(const Geo<T>&, double*, cudaStream_t);                          \
     template int launch_gauge<T>(const Geo<T>&, const double*, double*, const Scalars*, cudaStream_t);   \
     template int launch_warm<T>(const Geo<T>&, const T*, const float*, double*, T*, double*, const Reduce&,     \
                                 cudaStream_t);                                                          \
