@@ -15,7 +15,32 @@
 
 #include "../../include/les.h"
 
+#include <utility>
+
 namespace les {
+
+// Programmatic dependent launch.  A kernel launched with launch_pdl may be
+// scheduled while the previous kernel of its stream is still finishing; its
+// first statement, pdl_wait(), blocks until that kernel has completed and its
+// writes are visible, so no read or write of the kernel can overlap it.  For
+// an ordinary launch pdl_wait() returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 constexpr int OX = 3;
 
@@ -190,7 +215,7 @@ struct EnsTab {
 };
 static_assert(sizeof(EnsTab<float>) < 32000, "ensemble table must fit in the kernel parameter space");
 constexpr int kFirstRowTile = 12, kNumEnsTiles = 5;
-constexpr int kEstChunk = 4;       // planes per thread in the estimate and line-search kernels
+constexpr int kEstChunk = 8;       // planes per thread in the estimate and line-search kernels
 
 struct SorTile { int tx, ty, tz; };   // tz = 0: k-marching column tile
 struct SorCfg { int tile; int kc; };   // tile < 0: two in-place half-sweep kernels

@@ -870,27 +870,40 @@ int launch_sor_sweep(const Geo<T>& g, T* dl, const T* r, int zero_start, const S
 }
 
 // Refinement: ph += d on the unknowns (own cell only, so in place).
+// kc planes from plane bz * kc + 1 of a 32 x 8 column tile
 template <typename T>
-__device__ __forceinline__ void accum_body(const Geo<T>& g, double* ph, const T* dl, int bx, int by, int bz) {
+__device__ __forceinline__ void accum_body(const Geo<T>& g, double* ph, const T* dl, int bx, int by, int bz,
+                                           int kc = 1) {
     const Dom& d = g.d;
-    int i = bx * blockDim.x + threadIdx.x + 1;
-    int j = by * blockDim.y + threadIdx.y + 1;
-    int k = bz + 1;
+    const int i = bx * blockDim.x + threadIdx.x + 1;
+    const int j = by * blockDim.y + threadIdx.y + 1;
+    const int kb = bz * kc + 1, ke = min(kb + kc, d.nz + 1);
     if (i > d.nx || j > d.ny) return;
-    long long c = d.at(i, j, k);
-    if (g.flags[c] & F_UNK) ph[c] += (double)dl[c];
+    long long c = d.at(i, j, kb);
+    for (int k = kb; k < ke; ++k, c += d.plane)
+        if (g.flags[c] & F_UNK) ph[c] += (double)dl[c];
 }
 
 template <typename T>
-__global__ void k_accum(Geo<T> g, double* ph, const T* dl, const Scalars* sc, int gate) {
+__global__ void k_accum(Geo<T> g, double* ph, const T* dl, const Scalars* sc, int gate, int kc) {
     if (gate && (sc->done || !sc->refine)) return;
-    accum_body<T>(g, ph, dl, blockIdx.x, blockIdx.y, blockIdx.z);
+    accum_body<T>(g, ph, dl, blockIdx.x, blockIdx.y, blockIdx.z, kc);
+}
+
+// planes per thread of the accumulation: about 8 CTAs per SM, so that a
+// launch gated off (no refinement asked for) costs little
+int accum_kc(const Dom& d) {
+    const long long cols = (long long)((d.nx + 31) / 32) * ((d.ny + 7) / 8);
+    const long long kc = (cols * d.nz + 1215) / 1216;
+    return (int)(kc < 1 ? 1 : (kc > d.nz ? d.nz : kc));
 }
 
 template <typename T>
 int launch_accum(const Geo<T>& g, double* ph, const T* dl, const Scalars* sc, int gate, cudaStream_t s) {
     const Dom& d = g.d;
-    k_accum<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), dim3(32, 8), 0, s>>>(g, ph, dl, sc, gate);
+    const int kc = accum_kc(d);
+    k_accum<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, (d.nz + kc - 1) / kc), dim3(32, 8), 0, s>>>(g, ph, dl, sc,
+                                                                                                 gate, kc);
     return 1;
 }
 
@@ -1013,11 +1026,14 @@ int launch_residual64(const Geo<T>& g, const double* ph, const T* rhs, T* r, dou
 // this is the residual of the current iterate up to rounding.  It only decides
 // when to take the FP64 refinement, which makes the stop decision.
 template <typename T>
-__device__ __forceinline__ void sor_est_body(const Geo<T>& g, const T* dl, const T* r, T* rout, const Reduce& red,
-                                             const CondArgs& ca, int bx, int by, int bz, unsigned nb, unsigned b) {
+__device__ __forceinline__ void sor_est_body(const Geo<T>& g, const T* __restrict__ dl, const T* __restrict__ r,
+                                             T* __restrict__ rout, const Reduce& red, const CondArgs& ca, int bx,
+                                             int by, int bz, unsigned nb, unsigned b) {
     const Dom& d = g.d;
-    // a (32 x 8) column tile marching over a chunk of kEstChunk planes; the
-    // cell index advances by one plane per step, neighbour offsets are 32-bit
+    // a (32 x 8) column tile over a chunk of kEstChunk planes, unrolled: the
+    // chunk's flags first, then every load of the chunk before its use (the
+    // padded array holds every neighbour, so the loads need no face test);
+    // neighbour offsets are 32-bit
     const int i = bx * 32 + threadIdx.x + 1;
     const int j = by * 8 + threadIdx.y + 1;
     const int kb = bz * kEstChunk + 1, ke = min(kb + kEstChunk, d.nz + 1);
@@ -1028,21 +1044,28 @@ __device__ __forceinline__ void sor_est_body(const Geo<T>& g, const T* dl, const
         const int ow = (d.perx && i == 1) ? (d.nx - 1) : -1;
         const int on = (d.pery && j == d.ny) ? -(d.ny - 1) * d.px : d.px;
         const int os = (d.pery && j == 1) ? (d.ny - 1) * d.px : -d.px;
-        long long c = d.at(i, j, kb);
-        for (int k = kb; k < ke; ++k, c += pl) {
-            const uint8_t f = g.flags[c];
+        const long long c0 = d.at(i, j, kb);
+        uint8_t fl[kEstChunk];
+#pragma unroll
+        for (int m = 0; m < kEstChunk; ++m) fl[m] = kb + m < ke ? g.flags[c0 + (long long)m * pl] : (uint8_t)0;
+#pragma unroll
+        for (int m = 0; m < kEstChunk; ++m) {
+            const uint8_t f = fl[m];
             if (!(f & F_UNK)) continue;
+            const int k = kb + m;
+            const long long c = c0 + (long long)m * pl;
             const int ot = (d.perz && k == d.nz) ? -(d.nz - 1) * pl : pl;
             const int ob = (d.perz && k == 1) ? (d.nz - 1) * pl : -pl;
-            const T dc = dl[c];
+            const T dc = dl[c], de = dl[c + oe], dw = dl[c + ow], dn = dl[c + on], ds = dl[c + os];
+            const T dt = dl[c + ot], db = dl[c + ob], rc = r[c];
             T s = T(0);
-            if (f & F_E) s += g.cx * (dl[c + oe] - dc);
-            if (f & F_W) s += g.cx * (dl[c + ow] - dc);
-            if (f & F_N) s += g.cy * (dl[c + on] - dc);
-            if (f & F_S) s += g.cy * (dl[c + os] - dc);
-            if (f & F_T) s += g.cT[k] * (dl[c + ot] - dc);
-            if (f & F_B) s += g.cB[k] * (dl[c + ob] - dc);
-            const T res = r[c] - s;
+            if (f & F_E) s += g.cx * (de - dc);
+            if (f & F_W) s += g.cx * (dw - dc);
+            if (f & F_N) s += g.cy * (dn - dc);
+            if (f & F_S) s += g.cy * (ds - dc);
+            if (f & F_T) s += g.cT[k] * (dt - dc);
+            if (f & F_B) s += g.cB[k] * (db - dc);
+            const T res = rc - s;
             if (rout) rout[c] = res;        // the current residual, input of the network correction
             acc += res * res;
         }
@@ -1233,7 +1256,8 @@ int launch_rhs_eff(const Geo<T>& g, const T* rhs, T* out, const Scalars* sc, cud
 // the field type and the grid sums in FP64.  Tiles of (32 x 8) columns march
 // over kEstChunk planes, like the estimate.
 template <typename T>
-__global__ void __launch_bounds__(256) k_warm_ls(Geo<T> g, const T* r, const float* q, double* alpha, Reduce red,
+__global__ void __launch_bounds__(256) k_warm_ls(Geo<T> g, const T* __restrict__ r, const float* __restrict__ q,
+                                                 double* alpha, Reduce red,
                                                  int in_loop) {
     const Dom& d = g.d;
     if (red.sc->done) return;      // uniform over the grid
@@ -1244,30 +1268,41 @@ __global__ void __launch_bounds__(256) k_warm_ls(Geo<T> g, const T* r, const flo
     if (i <= d.nx && j <= d.ny) {
         // dense offsets (the grid has < 2^31 cells); flags never open a face
         // across a non-periodic domain boundary, so every neighbour read
-        // stays inside the dense array
+        // stays inside the dense array.  The chunk is unrolled: its flags
+        // first, then its loads, then the sums.
         const int sy = d.nx, sz = d.nx * d.ny;
         const int oe = (d.perx && i == d.nx) ? -(d.nx - 1) : 1;
         const int ow = (d.perx && i == 1) ? (d.nx - 1) : -1;
         const int on = (d.pery && j == d.ny) ? -(d.ny - 1) * sy : sy;
         const int os = (d.pery && j == 1) ? (d.ny - 1) * sy : -sy;
         const int pl = (int)d.plane;
-        long long c = d.at(i, j, kb);
-        int v = ((kb - 1) * d.ny + (j - 1)) * d.nx + (i - 1);
-        for (int k = kb; k < ke; ++k, c += pl, v += sz) {
-            const uint8_t f = g.flags[c];
+        const long long c0 = d.at(i, j, kb);
+        const int v0 = ((kb - 1) * d.ny + (j - 1)) * d.nx + (i - 1);
+        uint8_t fl[kEstChunk];
+#pragma unroll
+        for (int m = 0; m < kEstChunk; ++m) fl[m] = kb + m < ke ? g.flags[c0 + (long long)m * pl] : (uint8_t)0;
+#pragma unroll
+        for (int m = 0; m < kEstChunk; ++m) {
+            const uint8_t f = fl[m];
             if (!(f & F_UNK)) continue;
+            const int k = kb + m;
+            const long long c = c0 + (long long)m * pl;
+            const int v = v0 + m * sz;
             const int ot = (d.perz && k == d.nz) ? -(d.nz - 1) * sz : sz;
             const int ob = (d.perz && k == 1) ? (d.nz - 1) * sz : -sz;
-            const T qc = (T)q[v];
+            const T qc = (T)q[v], rc = r[c];
+            const T qe = (f & F_E) ? (T)q[v + oe] : T(0), qw = (f & F_W) ? (T)q[v + ow] : T(0);
+            const T qn = (f & F_N) ? (T)q[v + on] : T(0), qs = (f & F_S) ? (T)q[v + os] : T(0);
+            const T qt = (f & F_T) ? (T)q[v + ot] : T(0), qb = (f & F_B) ? (T)q[v + ob] : T(0);
             T aq = T(0);
-            if (f & F_E) aq += g.cx * ((T)q[v + oe] - qc);
-            if (f & F_W) aq += g.cx * ((T)q[v + ow] - qc);
-            if (f & F_N) aq += g.cy * ((T)q[v + on] - qc);
-            if (f & F_S) aq += g.cy * ((T)q[v + os] - qc);
-            if (f & F_T) aq += g.cT[k] * ((T)q[v + ot] - qc);
-            if (f & F_B) aq += g.cB[k] * ((T)q[v + ob] - qc);
+            if (f & F_E) aq += g.cx * (qe - qc);
+            if (f & F_W) aq += g.cx * (qw - qc);
+            if (f & F_N) aq += g.cy * (qn - qc);
+            if (f & F_S) aq += g.cy * (qs - qc);
+            if (f & F_T) aq += g.cT[k] * (qt - qc);
+            if (f & F_B) aq += g.cB[k] * (qb - qc);
             const T vq = g.dz[k] * qc;
-            s0 += vq * r[c];
+            s0 += vq * rc;
             s1 += vq * aq;
         }
     }
@@ -1286,16 +1321,21 @@ __global__ void __launch_bounds__(256) k_warm_ls(Geo<T> g, const T* r, const flo
     }
 }
 
+// the steps along q: a (32 x 8) column tile over kEstChunk planes per CTA
+// (few CTAs: the launch, not the work, bounds these kernels otherwise)
 template <typename T>
 __global__ void k_warm_apply(Geo<T> g, double* ph, const float* q, const double* alpha, const Scalars* sc) {
     const Dom& d = g.d;
     if (sc->done) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
     const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    const int k = blockIdx.z + 1;
+    const int kb = blockIdx.z * kEstChunk + 1, ke = min(kb + kEstChunk, d.nz + 1);
     if (i > d.nx || j > d.ny) return;
-    const long long c = d.at(i, j, k);
-    if (g.flags[c] & F_UNK) ph[c] += *alpha * (double)q[((k - 1) * d.ny + (j - 1)) * d.nx + (i - 1)];
+    const double a = *alpha;
+    long long c = d.at(i, j, kb);
+    int v = ((kb - 1) * d.ny + (j - 1)) * d.nx + (i - 1);
+    for (int k = kb; k < ke; ++k, c += d.plane, v += d.nx * d.ny)
+        if (g.flags[c] & F_UNK) ph[c] += a * (double)q[v];
 }
 
 // inside the solve loop: the SOR correction d (field type) takes the step,
@@ -1307,23 +1347,25 @@ __global__ void k_warm_apply_dl(Geo<T> g, T* dl, const float* q, const double* a
     if (sc->done) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
     const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    const int k = blockIdx.z + 1;
+    const int kb = blockIdx.z * kEstChunk + 1, ke = min(kb + kEstChunk, d.nz + 1);
     if (i > d.nx || j > d.ny) return;
-    const long long c = d.at(i, j, k);
     const T a = (T)*alpha;
     const bool zero = sc->zcopy != 0;
-    if (!(g.flags[c] & F_UNK)) return;
-    const T base = zero ? T(0) : dl[c];
-    dl[c] = base + a * (T)q[((k - 1) * d.ny + (j - 1)) * d.nx + (i - 1)];
+    long long c = d.at(i, j, kb);
+    int v = ((kb - 1) * d.ny + (j - 1)) * d.nx + (i - 1);
+    for (int k = kb; k < ke; ++k, c += d.plane, v += d.nx * d.ny) {
+        if (!(g.flags[c] & F_UNK)) continue;
+        const T base = zero ? T(0) : dl[c];
+        dl[c] = base + a * (T)q[v];
+    }
 }
 
 template <typename T>
 int launch_warm(const Geo<T>& g, const T* r, const float* q, double* ph, T* dl, double* alpha, const Reduce& red,
                 cudaStream_t s) {
     const Dom& d = g.d;
-    const dim3 grid((d.nx + 31) / 32, (d.ny + 7) / 8, d.nz), blk(32, 8);
-    const dim3 grid_ls((d.nx + 31) / 32, (d.ny + 7) / 8, (d.nz + kEstChunk - 1) / kEstChunk);
-    k_warm_ls<T><<<grid_ls, blk, 0, s>>>(g, r, q, alpha, red, dl ? 1 : 0);
+    const dim3 grid((d.nx + 31) / 32, (d.ny + 7) / 8, (d.nz + kEstChunk - 1) / kEstChunk), blk(32, 8);
+    k_warm_ls<T><<<grid, blk, 0, s>>>(g, r, q, alpha, red, dl ? 1 : 0);
     if (dl)
         k_warm_apply_dl<T><<<grid, blk, 0, s>>>(g, dl, q, alpha, red.sc);
     else

@@ -155,6 +155,9 @@ struct les_net_s {
     // persistent inference: per-CTA sums, grid barrier state
     double* cta = nullptr;              // [4 * kMaxInferGrid]
     unsigned* bar = nullptr;            // [2]: count, generation
+    double* pp_part = nullptr;          // [2 * kPoolRmsMax] per-block partials of the pooling + RMS kernel
+    unsigned* pp_count = nullptr;       // its completion counter (zero between launches)
+    int last_launches = 0;              // kernels of the last inference
     char err[256] = {0};
 };
 
@@ -487,18 +490,29 @@ int net_predict(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t
     n->stream = s;
     int rc = ensure_ws(n, L0);
     if (!rc) {
-        nn::pool_padded_s(r_padded, flags, d, n->stride, n->rc, n->mc, s, gate);
-        rc = pack_sample(n, L0, n->rc, n->mc, nullptr, nullptr, gate);
+        if (L0.v() <= nn::kPoolRmsMax) {
+            // pooling and RMS in one launch, the pooled mask straight into the
+            // head's mask, then the packing
+            nn::pool_rms(r_padded, flags, d, n->stride, n->rc, n->mask, n->pp_part, n->pp_count, n->dscal, s, gate);
+            k_pack_dense<<<(unsigned)((L0.v() + 255) / 256), 256, 0, s>>>(n->rc, n->mask, n->dscal, n->xin, L0.v(),
+                                                                         gate);
+            n->last_launches = 2;
+        } else {
+            nn::pool_padded_s(r_padded, flags, d, n->stride, n->rc, n->mc, s, gate);
+            rc = pack_sample(n, L0, n->rc, n->mc, nullptr, nullptr, gate);
+            n->last_launches = 1 + 3 + 1;
+        }
     }
     if (!rc) {
         forward_fused(n, L0, gate);
         nn::prolong_flags(n->y, flags, d, n->stride, out_dense, s, gate);
+        n->last_launches += 8 + 1;
         if (cudaGetLastError() != cudaSuccess) rc = LES_ECUDA;
     }
     n->stream = keep;
     return rc;
 }
-int net_launches(const les_net_s*) { return 1 + 4 + 8 + 1; }     // pool, rms + pack, network, prolongation
+int net_launches(const les_net_s* n) { return n->last_launches; }   // of the last net_predict
 }  // namespace les
 
 extern "C" {
@@ -536,7 +550,9 @@ int les_net_create(uint64_t seed, void* stream, les_net* out) {
     };
     bool ok = get(n->nparam * 4, (void**)&n->w32) && get(n->nparam * 4, (void**)&n->g32) &&
               get(n->nparam * 4, (void**)&n->m32) && get(n->nparam * 4, (void**)&n->v32) &&
-              get(4 * kMaxInferGrid * sizeof(double), (void**)&n->cta) && get(2 * sizeof(unsigned), (void**)&n->bar);
+              get(4 * kMaxInferGrid * sizeof(double), (void**)&n->cta) && get(2 * sizeof(unsigned), (void**)&n->bar) &&
+              get(2 * nn::kPoolRmsMax * sizeof(double), (void**)&n->pp_part) &&
+              get(sizeof(unsigned), (void**)&n->pp_count);
     for (int c = 0; ok && c < kConvs; ++c) {
         const size_t cnt = (size_t)27 * kCin[c] * kCout[c];
         ok = get(cnt * 2, (void**)&n->wb[c]) && get(cnt * 2, (void**)&n->wt[c]);

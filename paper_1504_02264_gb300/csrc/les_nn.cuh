@@ -42,6 +42,12 @@ void head_bwd(const __nv_bfloat16* d, const float* w1, const float* mask, const 
 void pool_dense_s(const float* a, float* b, int Xf, int Yf, int Zf, int st, cudaStream_t s);
 void pool_padded_s(const float* r, const uint8_t* flags, const Dom& d, int st, float* rc, float* mc, cudaStream_t s,
                    const int* gate = nullptr);
+// pool_padded_s and the RMS of the pooled residual (scal[0], mask sum in
+// scal[1]) in one launch; part holds 2 doubles per block (grids of at most
+// kPoolRmsMax coarse voxels), counter starts at 0
+constexpr size_t kPoolRmsMax = 32768;
+void pool_rms(const float* r, const uint8_t* flags, const Dom& d, int st, float* rc, float* mc, double* part,
+              unsigned* counter, double* scal, cudaStream_t s, const int* gate = nullptr);
 void prolong_dense(const float* yc, const float* mask, float* out, int Xf, int Yf, int Zf, int st, cudaStream_t s);
 void prolong_flags(const float* yc, const uint8_t* flags, const Dom& d, int st, float* out, cudaStream_t s,
                    const int* gate = nullptr);

@@ -551,6 +551,105 @@ __global__ void k_pool_padded_s(const float* r, const uint8_t* flags, Dom d, flo
     }
 }
 
+// Pooling and the RMS of the inference input in one launch: every block
+// pools its coarse cells as k_pool_padded_s does (same sums, same order) and
+// leaves its partial sums of m r^2 and m (FP64); the last block to finish adds
+// the partials in block order (fixed: deterministic) and stores the RMS and
+// the mask sum, as k_rms and k_rms_final do.
+template <int S>
+__global__ void k_pool_rms(const float* r, const uint8_t* flags, Dom d, float* rc, float* mc, double* part,
+                           unsigned* counter, double* scal, const int* gate) {
+    constexpr int SZ = S < 4 ? S : 4;
+    constexpr int NT = 32 * S * SZ, NW = NT / 32;
+    __shared__ float sr[SZ][S][32], sm[SZ][S][32];
+    __shared__ double ws[NW], wm[NW];
+    __shared__ bool last;
+    if (gate && *(volatile const int*)gate) return;
+    const int Xc = (d.nx + S - 1) / S, Yc = (d.ny + S - 1) / S;
+    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+    const int tid = tx + 32 * (ty + S * tz);
+    const int cx = blockIdx.x * 32 + tx, cy = blockIdx.y, cz = blockIdx.z;
+    float ar = 0.f, am = 0.f;
+    const int fy = cy * S + ty;
+    if (cx < Xc && fy < d.ny) {
+#pragma unroll
+        for (int zz = 0; zz < S; zz += SZ) {
+            const int fz = cz * S + tz + zz;
+            if (fz >= d.nz) break;
+            const long long row = d.at(1, fy + 1, fz + 1) + (long long)cx * S;
+#pragma unroll
+            for (int dx = 0; dx < S; ++dx)
+                if (cx * S + dx < d.nx && (flags[row + dx] & F_UNK)) {
+                    ar += r[row + dx];
+                    am += 1.f;
+                }
+        }
+    }
+    sr[tz][ty][tx] = ar;
+    sm[tz][ty][tx] = am;
+    __syncthreads();
+    const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+    if (ty == 0 && tz == 0) {
+        double a = 0.0, m = 0.0;
+        if (cx < Xc) {
+            float tr = 0.f, tm = 0.f;
+#pragma unroll
+            for (int p = 0; p < SZ; ++p)
+#pragma unroll
+                for (int q = 0; q < S; ++q) {
+                    tr += sr[p][q][tx];
+                    tm += sm[p][q][tx];
+                }
+            const float inv = 1.f / (float)(S * S * S);
+            const int v = (cz * Yc + cy) * Xc + cx;
+            const float vr = tr * inv, vm = tm * inv;
+            rc[v] = vr;
+            mc[v] = vm;
+            a = (double)vm * (double)vr * (double)vr;
+            m = (double)vm;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            m += __shfl_down_sync(0xffffffffu, m, o);
+        }
+        __threadfence();
+        if (tx == 0) {
+            const unsigned b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+            part[2 * b] = a;
+            part[2 * b + 1] = m;
+            __threadfence();
+            last = atomicAdd(counter, 1u) == nb - 1;
+        }
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double a = 0.0, m = 0.0;
+    for (unsigned q = tid; q < nb; q += NT) {
+        a += __ldcg(&part[2 * q]);
+        m += __ldcg(&part[2 * q + 1]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        m += __shfl_down_sync(0xffffffffu, m, o);
+    }
+    if ((tid & 31) == 0) {
+        ws[tid >> 5] = a;
+        wm[tid >> 5] = m;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double ts = 0.0, tm = 0.0;
+        for (int w = 0; w < NW; ++w) {
+            ts += ws[w];
+            tm += wm[w];
+        }
+        scal[0] = tm > 0.0 ? sqrt(ts / tm) : 0.0;
+        scal[1] = tm;
+        *counter = 0u;
+    }
+}
+
 // trilinear prolongation of a coarse cell-centred field to the fine cells,
 // times the fine mask: fine centre f sits at coarse coordinate (f + 1/2)/s - 1/2
 // on each axis, clamped to the first / last coarse centre
@@ -590,41 +689,38 @@ __global__ void k_prolong_dense(const float* yc, const float* mask, float* out, 
     const int Xc = (Xf + s - 1) / s, Yc = (Yf + s - 1) / s, Zc = (Zf + s - 1) / s;
     out[q] = mask[q] * trilinear(yc, Xc, Yc, Zc, s, x, y, z);
 }
-// dense fine output on the solver's unknowns: a thread takes the S fine
-// cells of one fine row under coarse column cx, interpolating between the
-// (y, z)-interpolated coarse columns cx-1, cx, cx+1
+// dense fine output on the solver's unknowns: a CTA takes a 32 x 8 tile of
+// fine columns over kProlongKC planes (few CTAs: with one CTA per fine row
+// the launch, not the work, bounded the kernel); each fine cell interpolates
+// the (y, z)-interpolated coarse columns x0 and x1, then in x
+constexpr int kProlongKC = 8;
 template <int S>
-__global__ void k_prolong_flags(const float* yc, const uint8_t* flags, Dom d, float* out, const int* gate) {
+__global__ void __launch_bounds__(256) k_prolong_flags(const float* yc, const uint8_t* flags, Dom d, float* out,
+                                                       const int* gate) {
     if (gate && *(volatile const int*)gate) return;
     const int Xc = (d.nx + S - 1) / S, Yc = (d.ny + S - 1) / S, Zc = (d.nz + S - 1) / S;
-    const int cx = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
-    if (cx >= Xc) return;
-    int y0, z0;
-    float wy, wz;
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+    const int zb = blockIdx.z * kProlongKC, ze = min(zb + kProlongKC, d.nz);
+    if (x >= d.nx || y >= d.ny) return;
+    int y0, x0;
+    float wy, wx;
     lin_w(y, S, Yc, y0, wy);
-    lin_w(z, S, Zc, z0, wz);
-    const int y1 = min(y0 + 1, Yc - 1), z1 = min(z0 + 1, Zc - 1);
-    auto col = [&](int c) {
-        c = max(0, min(c, Xc - 1));
-        auto at = [&](int b, int cc) { return yc[((size_t)cc * Yc + b) * Xc + c]; };
-        const float a0 = (1.f - wy) * at(y0, z0) + wy * at(y1, z0);
-        const float a1 = (1.f - wy) * at(y0, z1) + wy * at(y1, z1);
-        return (1.f - wz) * a0 + wz * a1;
-    };
-    const float cm = col(cx - 1), c0v = col(cx), cp = col(cx + 1);
-    const long long row = d.at(1, y + 1, z + 1);
-    float* o = out + ((size_t)z * d.ny + y) * d.nx;
-#pragma unroll
-    for (int m = 0; m < S; ++m) {
-        const int x = cx * S + m;
-        if (x >= d.nx) break;
-        int x0;
-        float wx;
-        lin_w(x, S, Xc, x0, wx);
-        const int x1 = min(x0 + 1, Xc - 1);
-        const float v0 = x0 < cx ? cm : (x0 == cx ? c0v : cp);
-        const float v1 = x1 < cx ? cm : (x1 == cx ? c0v : cp);
-        o[x] = (flags[row + x] & F_UNK) ? (1.f - wx) * v0 + wx * v1 : 0.f;
+    lin_w(x, S, Xc, x0, wx);
+    const int y1 = min(y0 + 1, Yc - 1), x1 = min(x0 + 1, Xc - 1);
+    for (int z = zb; z < ze; ++z) {
+        int z0;
+        float wz;
+        lin_w(z, S, Zc, z0, wz);
+        const int z1 = min(z0 + 1, Zc - 1);
+        auto col = [&](int c) {
+            auto at = [&](int b, int cc) { return yc[((size_t)cc * Yc + b) * Xc + c]; };
+            const float a0 = (1.f - wy) * at(y0, z0) + wy * at(y1, z0);
+            const float a1 = (1.f - wy) * at(y0, z1) + wy * at(y1, z1);
+            return (1.f - wz) * a0 + wz * a1;
+        };
+        const float v0 = col(x0), v1 = col(x1);
+        const long long row = d.at(1, y + 1, z + 1);
+        out[((size_t)z * d.ny + y) * d.nx + x] = (flags[row + x] & F_UNK) ? (1.f - wx) * v0 + wx * v1 : 0.f;
     }
 }
 
@@ -706,18 +802,28 @@ void pool_padded_s(const float* r, const uint8_t* flags, const Dom& d, int st, f
         default: k_pool_padded_s<8><<<grid, dim3(32, 8, 4), 0, s>>>(r, flags, d, rc, mc, gate); break;
     }
 }
+void pool_rms(const float* r, const uint8_t* flags, const Dom& d, int st, float* rc, float* mc, double* part,
+              unsigned* counter, double* scal, cudaStream_t s, const int* gate) {
+    const int Xc = (d.nx + st - 1) / st, Yc = (d.ny + st - 1) / st, Zc = (d.nz + st - 1) / st;
+    const dim3 grid((Xc + 31) / 32, Yc, Zc);
+    switch (st) {
+        case 1: k_pool_rms<1><<<grid, dim3(32, 1, 1), 0, s>>>(r, flags, d, rc, mc, part, counter, scal, gate); break;
+        case 2: k_pool_rms<2><<<grid, dim3(32, 2, 2), 0, s>>>(r, flags, d, rc, mc, part, counter, scal, gate); break;
+        case 4: k_pool_rms<4><<<grid, dim3(32, 4, 4), 0, s>>>(r, flags, d, rc, mc, part, counter, scal, gate); break;
+        default: k_pool_rms<8><<<grid, dim3(32, 8, 4), 0, s>>>(r, flags, d, rc, mc, part, counter, scal, gate); break;
+    }
+}
 void prolong_dense(const float* yc, const float* mask, float* out, int Xf, int Yf, int Zf, int st, cudaStream_t s) {
     k_prolong_dense<<<blocks_for((size_t)Xf * Yf * Zf), 256, 0, s>>>(yc, mask, out, Xf, Yf, Zf, st);
 }
 void prolong_flags(const float* yc, const uint8_t* flags, const Dom& d, int st, float* out, cudaStream_t s,
                    const int* gate) {
-    const int Xc = (d.nx + st - 1) / st;
-    const dim3 grid((Xc + 63) / 64, d.ny, d.nz);
+    const dim3 grid((d.nx + 31) / 32, (d.ny + 7) / 8, (d.nz + kProlongKC - 1) / kProlongKC), blk(32, 8);
     switch (st) {
-        case 1: k_prolong_flags<1><<<grid, 64, 0, s>>>(yc, flags, d, out, gate); break;
-        case 2: k_prolong_flags<2><<<grid, 64, 0, s>>>(yc, flags, d, out, gate); break;
-        case 4: k_prolong_flags<4><<<grid, 64, 0, s>>>(yc, flags, d, out, gate); break;
-        default: k_prolong_flags<8><<<grid, 64, 0, s>>>(yc, flags, d, out, gate); break;
+        case 1: k_prolong_flags<1><<<grid, blk, 0, s>>>(yc, flags, d, out, gate); break;
+        case 2: k_prolong_flags<2><<<grid, blk, 0, s>>>(yc, flags, d, out, gate); break;
+        case 4: k_prolong_flags<4><<<grid, blk, 0, s>>>(yc, flags, d, out, gate); break;
+        default: k_prolong_flags<8><<<grid, blk, 0, s>>>(yc, flags, d, out, gate); break;
     }
 }
 void mse(const float* y, const float* t, const float* mask, float* g, double* loss, size_t n, double inv_n,

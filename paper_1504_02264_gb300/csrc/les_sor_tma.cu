@@ -117,6 +117,7 @@ k_sor_tma(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtens
     float(*sCN)[64] = reinterpret_cast<float(*)[64]>(sm + TT::OFF_CN);
     float* sCT = reinterpret_cast<float*>(sm + TT::OFF_CT);
     float* sCB = sCT + RZ;
+    pdl_wait();
     if (sc->done) return;
     const Dom& d = g.d;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -435,8 +436,8 @@ void launch_tma_cfg(const Geo<float>& g, const TmaMaps& m, int in, float* dout, 
                     cudaStream_t s) {
     const Dom& d = g.d;
     dim3 grid((d.nx + 27) / 28, (d.ny + BY - 1) / BY, (d.nz + BZ - 1) / BZ);
-    k_sor_tma<BY, BZ, NT><<<grid, NT, TmaTile<BY, BZ>::SMEM, s>>>(m.d[in], m.r, m.f, g, m.dptr[in], m.rptr, dout,
-                                                                  zero, sc);
+    launch_pdl(k_sor_tma<BY, BZ, NT>, grid, dim3(NT), TmaTile<BY, BZ>::SMEM, s, m.d[in], m.r, m.f, g, m.dptr[in],
+               m.rptr, dout, zero, sc);
 }
 
 using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
