@@ -58,6 +58,9 @@ double normal_at(uint64_t seed, uint64_t c) {
 // block writes its two partial sums to part[2*block], k_rms_final adds the
 // partials in block order into out[0] (rms) and out[1] (sum of the mask)
 constexpr int kRmsBlocks = 256;
+// input-channel split workspace: up to 2 CTAs per SM x 256 threads x 8 floats
+constexpr size_t kSplitFloats = (size_t)2 * 160 * 256 * 8;
+constexpr size_t kSplitCounters = 4096;
 __global__ void __launch_bounds__(256) k_rms(const float* a, const float* mask, size_t n, double* part,
                                              const int* gate) {
     if (gate && *(volatile const int*)gate) return;
@@ -157,6 +160,7 @@ struct les_net_s {
     unsigned* bar = nullptr;            // [2]: count, generation
     double* pp_part = nullptr;          // [2 * kPoolRmsMax] per-block partials of the pooling + RMS kernel
     unsigned* pp_count = nullptr;       // its completion counter (zero between launches)
+    nn::ConvSplit split = {};           // input-channel split workspace of the inference convolutions
     int last_launches = 0;              // kernels of the last inference
     char err[256] = {0};
 };
@@ -266,13 +270,14 @@ int ensure_ws(les_net_s* n, const Level& L0) {
 void forward_fused(les_net_s* n, const Level& L0, const int* gate) {
     cudaStream_t s = n->stream;
     const Level L1 = level(L0, 1), L2 = level(L0, 2), L3 = level(L0, 3);
-    nn::conv3_fwd(n->xin, n->wb[0], n->e[0], nullptr, nullptr, L0.X, L0.Y, L0.Z, 16, 16, 1, s, gate);
-    nn::conv3_fwd_pool(n->e[0], n->wb[1], n->e[1], L0.X, L0.Y, L0.Z, 16, 32, 1, s, gate);
-    nn::conv3_fwd_pool(n->e[1], n->wb[2], n->e[2], L1.X, L1.Y, L1.Z, 32, 64, 1, s, gate);
-    nn::conv3_fwd_pool(n->e[2], n->wb[3], n->e[3], L2.X, L2.Y, L2.Z, 64, 128, 1, s, gate);
-    nn::conv3_fwd_up(n->e[3], n->wb[4], n->r[2], n->e[2], n->dd[2], L2.X, L2.Y, L2.Z, 128, 64, 1, s, gate);
-    nn::conv3_fwd_up(n->dd[2], n->wb[5], n->r[1], n->e[1], n->dd[1], L1.X, L1.Y, L1.Z, 64, 32, 1, s, gate);
-    nn::conv3_fwd_up(n->dd[1], n->wb[6], n->r[0], n->e[0], n->dd[0], L0.X, L0.Y, L0.Z, 32, 16, 1, s, gate);
+    const nn::ConvSplit* sp = &n->split;
+    nn::conv3_fwd(n->xin, n->wb[0], n->e[0], nullptr, nullptr, L0.X, L0.Y, L0.Z, 16, 16, 1, s, gate, sp);
+    nn::conv3_fwd_pool(n->e[0], n->wb[1], n->e[1], L0.X, L0.Y, L0.Z, 16, 32, 1, s, gate, sp);
+    nn::conv3_fwd_pool(n->e[1], n->wb[2], n->e[2], L1.X, L1.Y, L1.Z, 32, 64, 1, s, gate, sp);
+    nn::conv3_fwd_pool(n->e[2], n->wb[3], n->e[3], L2.X, L2.Y, L2.Z, 64, 128, 1, s, gate, sp);
+    nn::conv3_fwd_up(n->e[3], n->wb[4], n->r[2], n->e[2], n->dd[2], L2.X, L2.Y, L2.Z, 128, 64, 1, s, gate, sp);
+    nn::conv3_fwd_up(n->dd[2], n->wb[5], n->r[1], n->e[1], n->dd[1], L1.X, L1.Y, L1.Z, 64, 32, 1, s, gate, sp);
+    nn::conv3_fwd_up(n->dd[1], n->wb[6], n->r[0], n->e[0], n->dd[0], L0.X, L0.Y, L0.Z, 32, 16, 1, s, gate, sp);
     nn::head(n->dd[0], n->w32 + n->off[kConvs], n->mask, n->y, L0.v(), kHeadC, s, gate);
 }
 
@@ -552,7 +557,11 @@ int les_net_create(uint64_t seed, void* stream, les_net* out) {
               get(n->nparam * 4, (void**)&n->m32) && get(n->nparam * 4, (void**)&n->v32) &&
               get(4 * kMaxInferGrid * sizeof(double), (void**)&n->cta) && get(2 * sizeof(unsigned), (void**)&n->bar) &&
               get(2 * nn::kPoolRmsMax * sizeof(double), (void**)&n->pp_part) &&
-              get(sizeof(unsigned), (void**)&n->pp_count);
+              get(sizeof(unsigned), (void**)&n->pp_count) &&
+              get(kSplitFloats * sizeof(float), (void**)&n->split.part) &&
+              get(kSplitCounters * sizeof(unsigned), (void**)&n->split.cnt);
+    n->split.part_floats = kSplitFloats;
+    n->split.counters = kSplitCounters;
     for (int c = 0; ok && c < kConvs; ++c) {
         const size_t cnt = (size_t)27 * kCin[c] * kCout[c];
         ok = get(cnt * 2, (void**)&n->wb[c]) && get(cnt * 2, (void**)&n->wt[c]);

@@ -10,17 +10,26 @@ namespace nn {
 
 // set the convolution kernels' dynamic shared memory limit on the current device (0 = ok)
 int conv3_prepare();
+// workspace of the input-channel split of small convolutions (inference):
+// FP32 partial accumulators and per-tile counters (zero between launches)
+struct ConvSplit {
+    float* part;
+    size_t part_floats;
+    unsigned* cnt;
+    size_t counters;
+};
 void conv3_fwd(const __nv_bfloat16* x, const __nv_bfloat16* w, __nv_bfloat16* y, const __nv_bfloat16* skip,
                __nv_bfloat16* ysum, int X, int Y, int Z, int Cin, int Cout, int relu, cudaStream_t s,
-               const int* gate = nullptr);
+               const int* gate = nullptr, const ConvSplit* split = nullptr);
 // the same convolution reading its input through nearest upsampling of a
 // coarser tensor xc (output grid X x Y x Z, xc is ceil-halved) or through 2x2x2
 // mean pooling of a finer tensor xf (Xf x Yf x Zf; output is ceil-halved)
 void conv3_fwd_up(const __nv_bfloat16* xc, const __nv_bfloat16* w, __nv_bfloat16* y, const __nv_bfloat16* skip,
                   __nv_bfloat16* ysum, int X, int Y, int Z, int Cin, int Cout, int relu, cudaStream_t s,
-                  const int* gate = nullptr);
+                  const int* gate = nullptr, const ConvSplit* split = nullptr);
 void conv3_fwd_pool(const __nv_bfloat16* xf, const __nv_bfloat16* w, __nv_bfloat16* y, int Xf, int Yf, int Zf,
-                    int Cin, int Cout, int relu, cudaStream_t s, const int* gate = nullptr);
+                    int Cin, int Cout, int relu, cudaStream_t s, const int* gate = nullptr,
+                    const ConvSplit* split = nullptr);
 void wflip(const __nv_bfloat16* w, __nv_bfloat16* wt, int Cin, int Cout, cudaStream_t s);
 void conv3_wgrad(const __nv_bfloat16* x, const __nv_bfloat16* dy, float* dw, int X, int Y, int Z, int Cin, int Cout,
                  cudaStream_t s);

@@ -90,11 +90,19 @@ struct ConvArgs {
     const __nv_bfloat16* skip;
     __nv_bfloat16* ysum;
     int X, Y, Z, Cin, Cout, relu, Xs, Ys, Zs;
+    // split over the input-channel chunks (ks > 1): CTA kq of an output tile
+    // takes chunks [kq * nch / ks, (kq + 1) * nch / ks) and leaves its FP32
+    // accumulators in part; the last CTA of the tile (counter cnt[tile]) adds
+    // the ks partials in the order kq = 0, 1, ... and runs the epilogue
+    float* part;
+    unsigned* cnt;
+    int ks;
 };
 
-// one output tile: (bx, by) and bz = z tile + ntz * output-channel tile
+// one output tile: (bx, by) and bz = z tile + ntz * output-channel tile;
+// kq: the tile's input-channel split (0 without a split)
 template <int CO, int IN>
-__device__ __forceinline__ void conv_tile(const ConvArgs& A, int bx, int by, int bz, ConvStage<CO>* st) {
+__device__ __forceinline__ void conv_tile(const ConvArgs& A, int bx, int by, int bz, ConvStage<CO>* st, int kq = 0) {
     const __nv_bfloat16* __restrict__ x = A.x;
     const __nv_bfloat16* __restrict__ w = A.w;
     __nv_bfloat16* __restrict__ y = A.y;
@@ -151,18 +159,20 @@ __device__ __forceinline__ void conv_tile(const ConvArgs& A, int bx, int by, int
 #pragma unroll
     for (int n = 0; n < CO / 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
     const int nch = Cin / 16;
+    const int ks = A.ks > 1 ? A.ks : 1;
+    const int cb = kq * nch / ks, ce = (kq + 1) * nch / ks;
     const int mat = lane >> 3, r8 = lane & 7;
     const int vrow = r8 + 8 * (mat & 1), khalf = mat >> 1;
-    stage(0, st[0]);
-    for (int c = 0; c < nch; ++c) {
-        if (c + 1 < nch) {
-            stage(16 * (c + 1), st[(c + 1) & 1]);
+    stage(16 * cb, st[0]);
+    for (int c = cb; c < ce; ++c) {
+        if (c + 1 < ce) {
+            stage(16 * (c + 1), st[(c + 1 - cb) & 1]);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
         }
         __syncthreads();      // (also orders the plain shared stores of IN_POOL staging)
-        const ConvStage<CO>& S = st[c & 1];
+        const ConvStage<CO>& S = st[(c - cb) & 1];
 #pragma unroll
         for (int tap = 0; tap < 27; ++tap) {
             const int dx = tap % 3, dy = (tap / 3) % 3, dz = tap / 9;
@@ -180,6 +190,34 @@ __device__ __forceinline__ void conv_tile(const ConvArgs& A, int bx, int by, int
             }
         }
         __syncthreads();
+    }
+    if (ks > 1) {
+        // leave this split's accumulators; the tile's last CTA adds them all
+        __shared__ bool conv_last;
+        const size_t tile = (size_t)bx + gridDim.x * ((size_t)by + gridDim.y * (size_t)bz);
+        float4* mine = reinterpret_cast<float4*>(A.part) + ((tile * ks + kq) * 256 + tid) * (CO / 8);
+#pragma unroll
+        for (int n = 0; n < CO / 8; ++n) mine[n] = make_float4(acc[n][0], acc[n][1], acc[n][2], acc[n][3]);
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) conv_last = atomicAdd(&A.cnt[tile], 1u) == (unsigned)(ks - 1);
+        __syncthreads();
+        if (!conv_last) return;
+        __threadfence();
+#pragma unroll
+        for (int n = 0; n < CO / 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+        for (int k = 0; k < ks; ++k) {
+            const float4* p = reinterpret_cast<const float4*>(A.part) + ((tile * ks + k) * 256 + tid) * (CO / 8);
+#pragma unroll
+            for (int n = 0; n < CO / 8; ++n) {
+                const float4 v = __ldcg(p + n);
+                acc[n][0] += v.x;
+                acc[n][1] += v.y;
+                acc[n][2] += v.z;
+                acc[n][3] += v.w;
+            }
+        }
+        if (tid == 0) A.cnt[tile] = 0u;
     }
     // epilogue: thread holds rows g and g+8 (voxels), columns 2*(lane%4) + {0,1}
     const int g = lane >> 2, cq = 2 * (lane & 3);
@@ -215,7 +253,9 @@ template <int CO, int IN>
 __global__ void __launch_bounds__(256) k_conv3(ConvArgs A, const int* gate) {
     if (gate && *(volatile const int*)gate) return;      // the solve this inference serves has ended
     extern __shared__ __align__(16) unsigned char conv_smem[];
-    conv_tile<CO, IN>(A, blockIdx.x, blockIdx.y, blockIdx.z, reinterpret_cast<ConvStage<CO>*>(conv_smem));
+    const int ks = A.ks > 1 ? A.ks : 1;
+    conv_tile<CO, IN>(A, blockIdx.x, blockIdx.y, blockIdx.z / ks, reinterpret_cast<ConvStage<CO>*>(conv_smem),
+                      blockIdx.z % ks);
 }
 
 template <int CO, int IN>
@@ -238,14 +278,26 @@ int conv3_prepare() {
 template <int IN>
 static void conv3_launch(const __nv_bfloat16* x, const __nv_bfloat16* w, __nv_bfloat16* y, const __nv_bfloat16* skip,
                          __nv_bfloat16* ysum, int X, int Y, int Z, int Cin, int Cout, int relu, cudaStream_t s,
-                         const int* gate, int Xs, int Ys, int Zs) {
+                         const int* gate, int Xs, int Ys, int Zs, const ConvSplit* split) {
     // 32 output channels per CTA when the grid fills the GPU, else 16 (twice
     // the CTAs, half the weights staged per CTA: small levels are latency-bound)
     const int ntz = (Z + TZ - 1) / TZ;
     const long long tiles = (long long)((X + TX - 1) / TX) * ((Y + TY - 1) / TY) * ntz;
     const int co = (Cout >= 32 && tiles * (Cout / 32) >= 2 * 152) ? 32 : 16;
     dim3 grid((X + TX - 1) / TX, (Y + TY - 1) / TY, ntz * ((Cout + co - 1) / co));
-    const ConvArgs A{x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu, Xs, Ys, Zs};
+    // with a split workspace, small grids (few CTAs, latency-bound) split the
+    // input-channel chunks over more CTAs, up to about two per SM
+    int ks = 1;
+    if (split && co == 16) {
+        const long long ctas = (long long)grid.x * grid.y * grid.z;
+        const int nch = Cin / 16;
+        while (nch % (2 * ks) == 0 && ctas * 2 * ks <= 2 * 152 &&
+               (size_t)ctas * 2 * ks * 256 * (co / 2) <= split->part_floats && (size_t)ctas <= split->counters)
+            ks *= 2;
+        grid.z *= ks;
+    }
+    const ConvArgs A{x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu, Xs, Ys, Zs,
+                     ks > 1 ? split->part : nullptr, ks > 1 ? split->cnt : nullptr, ks};
     if (co == 32)
         k_conv3<32, IN><<<grid, 256, 2 * sizeof(ConvStage<32>), s>>>(A, gate);
     else
@@ -254,21 +306,21 @@ static void conv3_launch(const __nv_bfloat16* x, const __nv_bfloat16* w, __nv_bf
 
 void conv3_fwd(const __nv_bfloat16* x, const __nv_bfloat16* w, __nv_bfloat16* y, const __nv_bfloat16* skip,
                __nv_bfloat16* ysum, int X, int Y, int Z, int Cin, int Cout, int relu, cudaStream_t s,
-               const int* gate) {
-    conv3_launch<IN_DIRECT>(x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu, s, gate, X, Y, Z);
+               const int* gate, const ConvSplit* split) {
+    conv3_launch<IN_DIRECT>(x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu, s, gate, X, Y, Z, split);
 }
 
 void conv3_fwd_up(const __nv_bfloat16* xc, const __nv_bfloat16* w, __nv_bfloat16* y, const __nv_bfloat16* skip,
                   __nv_bfloat16* ysum, int X, int Y, int Z, int Cin, int Cout, int relu, cudaStream_t s,
-                  const int* gate) {
+                  const int* gate, const ConvSplit* split) {
     conv3_launch<IN_UP>(xc, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu, s, gate, (X + 1) / 2, (Y + 1) / 2,
-                        (Z + 1) / 2);
+                        (Z + 1) / 2, split);
 }
 
 void conv3_fwd_pool(const __nv_bfloat16* xf, const __nv_bfloat16* w, __nv_bfloat16* y, int Xf, int Yf, int Zf,
-                    int Cin, int Cout, int relu, cudaStream_t s, const int* gate) {
+                    int Cin, int Cout, int relu, cudaStream_t s, const int* gate, const ConvSplit* split) {
     conv3_launch<IN_POOL>(xf, w, y, nullptr, nullptr, (Xf + 1) / 2, (Yf + 1) / 2, (Zf + 1) / 2, Cin, Cout, relu, s,
-                          gate, Xf, Yf, Zf);
+                          gate, Xf, Yf, Zf, split);
 }
 
 // dgrad weights: W'[tap][ci][co] = W[26 - tap][co][ci] (flipped taps, swapped roles)
@@ -560,9 +612,7 @@ template <int S>
 __global__ void k_pool_rms(const float* r, const uint8_t* flags, Dom d, float* rc, float* mc, double* part,
                            unsigned* counter, double* scal, const int* gate) {
     constexpr int SZ = S < 4 ? S : 4;
-    constexpr int NT = 32 * S * SZ, NW = NT / 32;
     __shared__ float sr[SZ][S][32], sm[SZ][S][32];
-    __shared__ double ws[NW], wm[NW];
     __shared__ bool last;
     if (gate && *(volatile const int*)gate) return;
     const int Xc = (d.nx + S - 1) / S, Yc = (d.ny + S - 1) / S;
@@ -622,10 +672,12 @@ __global__ void k_pool_rms(const float* r, const uint8_t* flags, Dom d, float* r
         }
     }
     __syncthreads();
-    if (!last) return;
+    if (!last || tid >= 32) return;
+    // one warp adds the partials: FP64 arithmetic is narrow on this part, so
+    // a whole-block tree would queue on it
     __threadfence();
     double a = 0.0, m = 0.0;
-    for (unsigned q = tid; q < nb; q += NT) {
+    for (unsigned q = tid; q < nb; q += 32) {
         a += __ldcg(&part[2 * q]);
         m += __ldcg(&part[2 * q + 1]);
     }
@@ -633,19 +685,9 @@ __global__ void k_pool_rms(const float* r, const uint8_t* flags, Dom d, float* r
         a += __shfl_down_sync(0xffffffffu, a, o);
         m += __shfl_down_sync(0xffffffffu, m, o);
     }
-    if ((tid & 31) == 0) {
-        ws[tid >> 5] = a;
-        wm[tid >> 5] = m;
-    }
-    __syncthreads();
     if (tid == 0) {
-        double ts = 0.0, tm = 0.0;
-        for (int w = 0; w < NW; ++w) {
-            ts += ws[w];
-            tm += wm[w];
-        }
-        scal[0] = tm > 0.0 ? sqrt(ts / tm) : 0.0;
-        scal[1] = tm;
+        scal[0] = m > 0.0 ? sqrt(a / m) : 0.0;
+        scal[1] = m;
         *counter = 0u;
     }
 }
