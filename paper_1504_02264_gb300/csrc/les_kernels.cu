@@ -554,28 +554,30 @@ int launch_momentum(const Geo<T>& g, const T* u, const T* v, const T* w, const T
 }
 
 // ---------------------------------------------------------------------------
-// FP64 block reductions (warp shuffles, then one value per warp in shared
-// memory); deterministic for a fixed launch shape.
+// FP64 block reductions, deterministic for a fixed launch shape.  FP64
+// arithmetic is narrow on this part (a warp-wide add queues for many cycles),
+// so the values go to shared memory and one warp adds them: 8 sequential adds
+// per lane and a 5-level shuffle tree, 13 warp-wide adds per value instead of
+// a shuffle tree in every warp.  Blocks of at most 256 threads; the total is
+// valid on thread 0.
+constexpr int kSumThreads = 256;
 
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&x)[NV]) {
-    __shared__ double sh[NV][32];
-    const int lane = (threadIdx.x + threadIdx.y * blockDim.x) & 31;
-    const int warp = (threadIdx.x + threadIdx.y * blockDim.x) >> 5;
-    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    __shared__ double sh[NV][kSumThreads];
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nt = blockDim.x * blockDim.y;
+    __syncthreads();          // a previous call's readers are done with sh
 #pragma unroll
-    for (int q = 0; q < NV; ++q)
-        for (int o = 16; o > 0; o >>= 1) x[q] += __shfl_down_sync(0xffffffffu, x[q], o);
+    for (int q = 0; q < NV; ++q) sh[q][tid] = x[q];
     __syncthreads();
-    if (lane == 0)
-#pragma unroll
-        for (int q = 0; q < NV; ++q) sh[q][warp] = x[q];
-    __syncthreads();
-    if (warp == 0) {
+    if (tid < 32) {
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
-            x[q] = lane < nw ? sh[q][lane] : 0.0;
-            for (int o = 16; o > 0; o >>= 1) x[q] += __shfl_down_sync(0xffffffffu, x[q], o);
+            double v = 0.0;
+            for (int m = tid; m < nt; m += 32) v += sh[q][m];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            x[q] = v;
         }
     }
 }
