@@ -42,8 +42,15 @@ SOR_BYTES_PER_CELL = 13.0       # per sweep: read p, rhs (4+4), flags (1), write
 # DRAM bytes (read + write) of one k_sor_tma launch on this workload from one
 # ncu capture (cold L2; profiles/sor_tma_28x8x8_random150x150x90.md); reported
 # only while that kernel is the one timed
-SOR_TMA_TILE, SOR_TMA_DRAM_BYTES = 17, 20.147968e6 + 2.048e3
+SOR_TMA_TILE, SOR_TMA_DRAM_BYTES = 17, 20.180480e6 + 1.536e3
 L2_FLUSH_BYTES = 256 << 20
+# algorithmic bytes per cell of the HBM-bound phases (every array read or
+# written once): the stencil phase = les (u, v, w, flags in; nu_t out: 17 B)
+# + velfg/SGS/Adams-Bashforth/feedbf (u, v, w, nu_t, flags, F^{n-1} in; F^n,
+# u* out: 53 B) + rhs (u*, flags in; rhs out: 17 B); the projection (u*, p,
+# flags in; u and the gauged p out: 41 B)
+STENCIL_BYTES_PER_CELL = 17.0 + 53.0 + 17.0
+PROJECT_BYTES_PER_CELL = 41.0
 # mean SOR sweeps per step of this workload after the default warm-up, from the
 # GPU arm (the FP64 path takes the same sweeps as the oracle); used only to scale
 # the bounded oracle sample to a full step when no GPU run is available
@@ -158,6 +165,42 @@ def oracle_sample(sc, sweeps_per_step, n_sample_sweeps=40, state=None):
     t_step = (t1 - t0) + (t4 - t3) + sweeps_per_step * t_sweep + checks * (t3 - t2)
     return t_step, {"non_sor_s": (t1 - t0) + (t4 - t3), "sweep_s": t_sweep, "residual_s": t3 - t2,
                     "sample_wall_s": t4 - t0}
+
+
+def hbm_large(peak, peak_kind):
+    """The HBM-bound kernels where the state does not fit in L2: the
+    512x512x128 periodic-y city (1200 buildings), 20 fixed sweeps per step,
+    host loop with CUDA events around each phase (stencil phase: bondv1, les,
+    velfg/SGS/AB2/feedbf, outflow, rhs; projection), and the SOR sweep of the
+    TMA block tile timed alone (20 back-to-back sweeps, best of 3)."""
+    from paper_1504_02264_gb300 import les
+    sc = scene.large_scene(0)
+    sc.fixed_sweeps, sc.max_sweeps = 1, 20
+    d = les.Domain(sc)
+    try:
+        d.set_graph(False)
+        d.step(1)
+        d.set_timing(True)
+        d.step(2)
+        tm = d.timing()
+        d.set_timing(False)
+        sweep_ms = min(d.time_sor(SOR_TMA_TILE, 0, sweeps=20) for _ in range(3))
+    finally:
+        d.close()
+    n = sc.ncells
+    steps = max(tm["steps"], 1)
+
+    def entry(bytes_per_cell, ms):
+        gbs = bytes_per_cell * n / (ms * 1e-3) / 1e9
+        return {"ms": ms, "bytes_per_cell": bytes_per_cell, "achieved_gbs": gbs, "frac": gbs / peak}
+
+    return {"workload": "large_512x512x128_periodic_y", "cells": n, "peak_gbs": peak, "peak_kind": peak_kind,
+            "l2": "state (~3.5 GB) far larger than L2",
+            "sor_sweep": {"kernel": f"{sor_kernel_name(SOR_TMA_TILE)} tile {les.les_sor_tile(SOR_TMA_TILE)}",
+                          **entry(SOR_BYTES_PER_CELL, sweep_ms)},
+            "stencil_phase": entry(STENCIL_BYTES_PER_CELL, tm["ms_momentum"] / steps),
+            "projection": {**entry(PROJECT_BYTES_PER_CELL, tm["ms_project"] / steps),
+                           "note": "FP64 pressure differences: bound by the FP64 pipe, not HBM"}}
 
 
 def run_reference(args):
@@ -404,6 +447,8 @@ def run_ours(args):
                            f"part scaled to the plain GPU step's {plain_sweeps:.0f} sweeps/step (the oracle "
                            f"runs plain SOR)"),
                 "detail": det}
+        if not args.no_large:
+            line["hbm_large"] = hbm_large(peak, peak_kind)
         print(json.dumps(line))
     if world > 1:
         dist.barrier()
@@ -419,6 +464,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="time the plain SOR step only")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the HBM-bound kernel timings on the 512x512x128 grid")
     ap.add_argument("--ncu-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     args = ap.parse_args()

@@ -888,6 +888,7 @@ __device__ __forceinline__ void accum_body(const Geo<T>& g, double* ph, const T*
 
 template <typename T>
 __global__ void k_accum(Geo<T> g, double* ph, const T* dl, const Scalars* sc, int gate, int kc) {
+    pdl_wait();
     if (gate && (sc->done || !sc->refine)) return;
     accum_body<T>(g, ph, dl, blockIdx.x, blockIdx.y, blockIdx.z, kc);
 }
@@ -904,8 +905,8 @@ template <typename T>
 int launch_accum(const Geo<T>& g, double* ph, const T* dl, const Scalars* sc, int gate, cudaStream_t s) {
     const Dom& d = g.d;
     const int kc = accum_kc(d);
-    k_accum<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, (d.nz + kc - 1) / kc), dim3(32, 8), 0, s>>>(g, ph, dl, sc,
-                                                                                                 gate, kc);
+    launch_pdl(k_accum<T>, dim3((d.nx + 31) / 32, (d.ny + 7) / 8, (d.nz + kc - 1) / kc), dim3(32, 8), 0, s, g, ph,
+               dl, sc, gate, kc);
     return 1;
 }
 
@@ -1010,6 +1011,7 @@ __device__ __forceinline__ int residual64_body(const Geo<T>& g, const double* ph
 template <typename T>
 __global__ void __launch_bounds__(256) k_residual64(Geo<T> g, const double* ph, const T* rhs, T* r, double vfluid,
                                                     Reduce red, CondArgs ca) {
+    pdl_wait();
     if (ca.gate == 1 && (red.sc->done || !red.sc->refine)) return;     // uniform over the grid
     if (ca.gate == 2 && red.sc->done) return;
     residual64_body<T>(g, ph, rhs, r, vfluid, red, ca, blockIdx.x, gridDim.x);
@@ -1018,7 +1020,7 @@ __global__ void __launch_bounds__(256) k_residual64(Geo<T> g, const double* ph, 
 template <typename T>
 int launch_residual64(const Geo<T>& g, const double* ph, const T* rhs, T* r, double vfluid, const Reduce& red,
                       CondArgs ca, cudaStream_t s) {
-    k_residual64<T><<<reduce_blocks(g.d), 256, 0, s>>>(g, ph, rhs, r, vfluid, red, ca);
+    launch_pdl(k_residual64<T>, dim3(reduce_blocks(g.d)), dim3(256), 0, s, g, ph, rhs, r, vfluid, red, ca);
     return 1;
 }
 
@@ -1092,6 +1094,7 @@ __device__ __forceinline__ void sor_est_body(const Geo<T>& g, const T* __restric
 template <typename T>
 __global__ void __launch_bounds__(256) k_sor_est(Geo<T> g, const T* dl, const T* r, T* rout, Reduce red,
                                                  CondArgs ca) {
+    pdl_wait();
     if (red.sc->done) return;      // uniform over the grid
     sor_est_body<T>(g, dl, r, rout, red, ca, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x * gridDim.y * gridDim.z,
                     blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
@@ -1102,7 +1105,7 @@ int launch_sor_est(const Geo<T>& g, const T* dl, const T* r, T* rout, const Redu
                    cudaStream_t s) {
     const Dom& d = g.d;
     dim3 grid((d.nx + 31) / 32, (d.ny + 7) / 8, (d.nz + kEstChunk - 1) / kEstChunk);
-    k_sor_est<T><<<grid, dim3(32, 8), 0, s>>>(g, dl, r, rout, red, ca);
+    launch_pdl(k_sor_est<T>, grid, dim3(32, 8), 0, s, g, dl, r, rout, red, ca);
     return 1;
 }
 
@@ -1261,6 +1264,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_warm_ls(Geo<T> g, const T* __restrict__ r, const float* __restrict__ q,
                                                  double* alpha, Reduce red,
                                                  int in_loop) {
+    pdl_wait();
     const Dom& d = g.d;
     if (red.sc->done) return;      // uniform over the grid
     const int i = blockIdx.x * 32 + threadIdx.x + 1;
@@ -1327,6 +1331,7 @@ __global__ void __launch_bounds__(256) k_warm_ls(Geo<T> g, const T* __restrict__
 // (few CTAs: the launch, not the work, bounds these kernels otherwise)
 template <typename T>
 __global__ void k_warm_apply(Geo<T> g, double* ph, const float* q, const double* alpha, const Scalars* sc) {
+    pdl_wait();
     const Dom& d = g.d;
     if (sc->done) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
@@ -1345,6 +1350,7 @@ __global__ void k_warm_apply(Geo<T> g, double* ph, const float* q, const double*
 // next refinement
 template <typename T>
 __global__ void k_warm_apply_dl(Geo<T> g, T* dl, const float* q, const double* alpha, const Scalars* sc) {
+    pdl_wait();
     const Dom& d = g.d;
     if (sc->done) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
@@ -1367,11 +1373,11 @@ int launch_warm(const Geo<T>& g, const T* r, const float* q, double* ph, T* dl, 
                 cudaStream_t s) {
     const Dom& d = g.d;
     const dim3 grid((d.nx + 31) / 32, (d.ny + 7) / 8, (d.nz + kEstChunk - 1) / kEstChunk), blk(32, 8);
-    k_warm_ls<T><<<grid, blk, 0, s>>>(g, r, q, alpha, red, dl ? 1 : 0);
+    launch_pdl(k_warm_ls<T>, grid, blk, 0, s, g, r, q, alpha, red, dl ? 1 : 0);
     if (dl)
-        k_warm_apply_dl<T><<<grid, blk, 0, s>>>(g, dl, q, alpha, red.sc);
+        launch_pdl(k_warm_apply_dl<T>, grid, blk, 0, s, g, dl, q, alpha, (const Scalars*)red.sc);
     else
-        k_warm_apply<T><<<grid, blk, 0, s>>>(g, ph, q, alpha, red.sc);
+        launch_pdl(k_warm_apply<T>, grid, blk, 0, s, g, ph, q, alpha, (const Scalars*)red.sc);
     return 2;
 }
 

@@ -116,6 +116,7 @@ __global__ void __launch_bounds__(kRmsBlocks) k_rms_final(const double* part, in
 // dense input: channel 0 = r / scale, channel 1 = mask
 __global__ void k_pack_dense(const float* r, const float* mask, const double* scale, __nv_bfloat16* xin, size_t n,
                              const int* gate) {
+    pdl_wait();
     if (gate && *(volatile const int*)gate) return;
     const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
@@ -499,8 +500,8 @@ int net_predict(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t
             // pooling and RMS in one launch, the pooled mask straight into the
             // head's mask, then the packing
             nn::pool_rms(r_padded, flags, d, n->stride, n->rc, n->mask, n->pp_part, n->pp_count, n->dscal, s, gate);
-            k_pack_dense<<<(unsigned)((L0.v() + 255) / 256), 256, 0, s>>>(n->rc, n->mask, n->dscal, n->xin, L0.v(),
-                                                                         gate);
+            launch_pdl(k_pack_dense, dim3((unsigned)((L0.v() + 255) / 256)), dim3(256), 0, s, (const float*)n->rc,
+                       (const float*)n->mask, (const double*)n->dscal, n->xin, (size_t)L0.v(), gate);
             n->last_launches = 2;
         } else {
             nn::pool_padded_s(r_padded, flags, d, n->stride, n->rc, n->mc, s, gate);

@@ -251,6 +251,7 @@ __device__ __forceinline__ void conv_tile(const ConvArgs& A, int bx, int by, int
 
 template <int CO, int IN>
 __global__ void __launch_bounds__(256) k_conv3(ConvArgs A, const int* gate) {
+    pdl_wait();
     if (gate && *(volatile const int*)gate) return;      // the solve this inference serves has ended
     extern __shared__ __align__(16) unsigned char conv_smem[];
     const int ks = A.ks > 1 ? A.ks : 1;
@@ -299,9 +300,9 @@ static void conv3_launch(const __nv_bfloat16* x, const __nv_bfloat16* w, __nv_bf
     const ConvArgs A{x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu, Xs, Ys, Zs,
                      ks > 1 ? split->part : nullptr, ks > 1 ? split->cnt : nullptr, ks};
     if (co == 32)
-        k_conv3<32, IN><<<grid, 256, 2 * sizeof(ConvStage<32>), s>>>(A, gate);
+        launch_pdl(k_conv3<32, IN>, grid, dim3(256), 2 * sizeof(ConvStage<32>), s, A, gate);
     else
-        k_conv3<16, IN><<<grid, 256, 2 * sizeof(ConvStage<16>), s>>>(A, gate);
+        launch_pdl(k_conv3<16, IN>, grid, dim3(256), 2 * sizeof(ConvStage<16>), s, A, gate);
 }
 
 void conv3_fwd(const __nv_bfloat16* x, const __nv_bfloat16* w, __nv_bfloat16* y, const __nv_bfloat16* skip,
@@ -501,6 +502,7 @@ __global__ void k_add(const __nv_bfloat16* a, const __nv_bfloat16* b, __nv_bfloa
 // head: y[v] = mask[v] * sum_c w1[c] * d[v][c]  (FP32 output)
 __global__ void k_head(const __nv_bfloat16* d, const float* w1, const float* mask, float* y, size_t nv, int C,
                        const int* gate) {
+    pdl_wait();
     if (gate && *(volatile const int*)gate) return;
     const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
@@ -614,6 +616,7 @@ __global__ void k_pool_rms(const float* r, const uint8_t* flags, Dom d, float* r
     constexpr int SZ = S < 4 ? S : 4;
     __shared__ float sr[SZ][S][32], sm[SZ][S][32];
     __shared__ bool last;
+    pdl_wait();
     if (gate && *(volatile const int*)gate) return;
     const int Xc = (d.nx + S - 1) / S, Yc = (d.ny + S - 1) / S;
     const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
@@ -739,6 +742,7 @@ constexpr int kProlongKC = 8;
 template <int S>
 __global__ void __launch_bounds__(256) k_prolong_flags(const float* yc, const uint8_t* flags, Dom d, float* out,
                                                        const int* gate) {
+    pdl_wait();
     if (gate && *(volatile const int*)gate) return;
     const int Xc = (d.nx + S - 1) / S, Yc = (d.ny + S - 1) / S, Zc = (d.nz + S - 1) / S;
     const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
@@ -823,7 +827,7 @@ void add(const __nv_bfloat16* a, const __nv_bfloat16* b, __nv_bfloat16* out, siz
 }
 void head(const __nv_bfloat16* d, const float* w1, const float* mask, float* y, size_t nv, int C, cudaStream_t s,
           const int* gate) {
-    k_head<<<blocks_for(nv), 256, 0, s>>>(d, w1, mask, y, nv, C, gate);
+    launch_pdl(k_head, dim3(blocks_for(nv)), dim3(256), 0, s, d, w1, mask, y, nv, C, gate);
 }
 void head_bwd(const __nv_bfloat16* d, const float* w1, const float* mask, const float* gy, __nv_bfloat16* gd,
               float* dw1, size_t nv, int C, cudaStream_t s) {
@@ -849,10 +853,10 @@ void pool_rms(const float* r, const uint8_t* flags, const Dom& d, int st, float*
     const int Xc = (d.nx + st - 1) / st, Yc = (d.ny + st - 1) / st, Zc = (d.nz + st - 1) / st;
     const dim3 grid((Xc + 31) / 32, Yc, Zc);
     switch (st) {
-        case 1: k_pool_rms<1><<<grid, dim3(32, 1, 1), 0, s>>>(r, flags, d, rc, mc, part, counter, scal, gate); break;
-        case 2: k_pool_rms<2><<<grid, dim3(32, 2, 2), 0, s>>>(r, flags, d, rc, mc, part, counter, scal, gate); break;
-        case 4: k_pool_rms<4><<<grid, dim3(32, 4, 4), 0, s>>>(r, flags, d, rc, mc, part, counter, scal, gate); break;
-        default: k_pool_rms<8><<<grid, dim3(32, 8, 4), 0, s>>>(r, flags, d, rc, mc, part, counter, scal, gate); break;
+        case 1: launch_pdl(k_pool_rms<1>, grid, dim3(32, 1, 1), 0, s, r, flags, d, rc, mc, part, counter, scal, gate); break;
+        case 2: launch_pdl(k_pool_rms<2>, grid, dim3(32, 2, 2), 0, s, r, flags, d, rc, mc, part, counter, scal, gate); break;
+        case 4: launch_pdl(k_pool_rms<4>, grid, dim3(32, 4, 4), 0, s, r, flags, d, rc, mc, part, counter, scal, gate); break;
+        default: launch_pdl(k_pool_rms<8>, grid, dim3(32, 8, 4), 0, s, r, flags, d, rc, mc, part, counter, scal, gate); break;
     }
 }
 void prolong_dense(const float* yc, const float* mask, float* out, int Xf, int Yf, int Zf, int st, cudaStream_t s) {
@@ -862,10 +866,10 @@ void prolong_flags(const float* yc, const uint8_t* flags, const Dom& d, int st, 
                    const int* gate) {
     const dim3 grid((d.nx + 31) / 32, (d.ny + 7) / 8, (d.nz + kProlongKC - 1) / kProlongKC), blk(32, 8);
     switch (st) {
-        case 1: k_prolong_flags<1><<<grid, blk, 0, s>>>(yc, flags, d, out, gate); break;
-        case 2: k_prolong_flags<2><<<grid, blk, 0, s>>>(yc, flags, d, out, gate); break;
-        case 4: k_prolong_flags<4><<<grid, blk, 0, s>>>(yc, flags, d, out, gate); break;
-        default: k_prolong_flags<8><<<grid, blk, 0, s>>>(yc, flags, d, out, gate); break;
+        case 1: launch_pdl(k_prolong_flags<1>, grid, blk, 0, s, yc, flags, d, out, gate); break;
+        case 2: launch_pdl(k_prolong_flags<2>, grid, blk, 0, s, yc, flags, d, out, gate); break;
+        case 4: launch_pdl(k_prolong_flags<4>, grid, blk, 0, s, yc, flags, d, out, gate); break;
+        default: launch_pdl(k_prolong_flags<8>, grid, blk, 0, s, yc, flags, d, out, gate); break;
     }
 }
 void mse(const float* y, const float* t, const float* mask, float* g, double* loss, size_t n, double inv_n,

@@ -86,10 +86,14 @@ def main():
                     help="time every SOR sweep configuration on the workload after the warm-up steps")
     ap.add_argument("--net", default=None, help="trained warm-start network (.npz: params, stride)")
     ap.add_argument("--net-every", type=int, default=0, help="network correction every n sweeps")
+    ap.add_argument("--fixed-sweeps", type=int, default=0,
+                    help="run exactly this many SOR sweeps per step (0: solve to the tolerance)")
     a = ap.parse_args()
     if a.workload == "ensemble":
         return run_ensemble(a)
     sc = make(a.workload, a.seed)
+    if a.fixed_sweeps > 0:
+        sc.fixed_sweeps, sc.max_sweeps = 1, a.fixed_sweeps
     d = les.Domain(sc, precision=les.LES_FP64 if a.fp64 else les.LES_FP32, stream=None)
     d.set_graph(bool(a.graph))
     if a.tile is not None:
