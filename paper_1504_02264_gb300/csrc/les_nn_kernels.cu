@@ -116,31 +116,60 @@ __device__ __forceinline__ void conv_tile(const ConvArgs& A, int bx, int by, int
     const int co0 = (bz / ntz) * CO;
     const int wy = warp % TY, wz = warp / TY;
     auto stage = [&](int c0, ConvStage<CO>& S) {
-        for (int q = tid; q < HZ * HY * HX * 2; q += 256) {
+        if constexpr (IN == IN_POOL) {
+            // the child loads of two items at a time in flight, then their
+            // averages: two memory round trips per thread instead of four
+            constexpr int NQ = HZ * HY * HX * 2, PER = (NQ + 255) / 256, R = 2;
+#pragma unroll
+            for (int p0 = 0; p0 < PER; p0 += R) {
+                uint4 ch[R][8];
+                bool in[R][8];
+#pragma unroll
+                for (int p = 0; p < R; ++p) {
+                    const int q = tid + 256 * (p0 + p);
+                    const int h = q & 1, v = q >> 1;
+                    const int hx = v % HX, hy = (v / HX) % HY, hz = v / (HX * HY);
+                    const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = z0 - 1 + hz;
+                    const bool ok = p0 + p < PER && q < NQ && gx >= 0 && gx < X && gy >= 0 && gy < Y && gz >= 0 &&
+                                    gz < Z;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int fx = 2 * gx + (e & 1), fy = 2 * gy + ((e >> 1) & 1), fz = 2 * gz + (e >> 2);
+                        in[p][e] = ok && fx < Xs && fy < Ys && fz < Zs;
+                        ch[p][e] = in[p][e] ? *reinterpret_cast<const uint4*>(
+                                                  x + (((size_t)fz * Ys + fy) * Xs + fx) * Cin + c0 + 8 * h)
+                                            : make_uint4(0u, 0u, 0u, 0u);
+                    }
+                }
+#pragma unroll
+                for (int p = 0; p < R; ++p) {
+                    const int q = tid + 256 * (p0 + p);
+                    if (p0 + p >= PER || q >= NQ) break;
+                    const int h = q & 1, v = q >> 1;
+                    const int hx = v % HX, hy = (v / HX) % HY, hz = v / (HX * HY);
+                    float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        if (in[p][e]) {
+                            const __nv_bfloat16* b = reinterpret_cast<const __nv_bfloat16*>(&ch[p][e]);
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) a[c] += __bfloat162float(b[c]);
+                        }
+                    __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) o[c] = __float2bfloat16(0.125f * a[c]);
+                    *reinterpret_cast<uint4*>(&S.in[hz][hy][hx][8 * (h ^ swz(hx))]) =
+                        *reinterpret_cast<const uint4*>(o);
+                }
+            }
+        }
+        for (int q = tid; IN != IN_POOL && q < HZ * HY * HX * 2; q += 256) {
             const int h = q & 1, v = q >> 1;
             const int hx = v % HX, hy = (v / HX) % HY, hz = v / (HX * HY);
             const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = z0 - 1 + hz;
             const bool ok = gx >= 0 && gx < X && gy >= 0 && gy < Y && gz >= 0 && gz < Z;
             __nv_bfloat16* dst = &S.in[hz][hy][hx][8 * (h ^ swz(hx))];
-            if constexpr (IN == IN_POOL) {
-                float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                if (ok)
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const int fx = 2 * gx + (e & 1), fy = 2 * gy + ((e >> 1) & 1), fz = 2 * gz + (e >> 2);
-                        if (fx < Xs && fy < Ys && fz < Zs) {
-                            const uint4 v = *reinterpret_cast<const uint4*>(
-                                x + (((size_t)fz * Ys + fy) * Xs + fx) * Cin + c0 + 8 * h);
-                            const __nv_bfloat16* b = reinterpret_cast<const __nv_bfloat16*>(&v);
-#pragma unroll
-                            for (int c = 0; c < 8; ++c) a[c] += __bfloat162float(b[c]);
-                        }
-                    }
-                __align__(16) __nv_bfloat16 o[8];
-#pragma unroll
-                for (int c = 0; c < 8; ++c) o[c] = __float2bfloat16(0.125f * a[c]);
-                *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(o);
-            } else {
+            {
                 const int sx = IN == IN_UP ? gx >> 1 : gx, sy = IN == IN_UP ? gy >> 1 : gy,
                           sz = IN == IN_UP ? gz >> 1 : gz;
                 const __nv_bfloat16* src = ok ? x + (((size_t)sz * Ys + sy) * Xs + sx) * Cin + c0 + 8 * h : x;
