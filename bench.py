@@ -94,11 +94,11 @@ class Clocks:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index=0):
+    def __init__(self, index=0, interval_ms=50):
         self.p = None
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", str(interval_ms)],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
@@ -310,7 +310,7 @@ def run_ours(args):
 
     # timed region 1: the plain step (red-black SOR from the previous
     # pressure, one chunked CUDA graph per step)
-    plain = timed("plain", net is None)
+    plain = timed("plain", True)
     if net is not None:
         # timed region 1b: the full hot path with the learned correction
         # (the package's network every NET_EVERY sweeps), same start state, same
@@ -409,7 +409,7 @@ def run_ours(args):
             "plain_sor": {"value": n * world / (plain["ms"] * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": plain["ms"],
                           "mean_sweeps_per_step": plain_sweeps, "max_rel_residual": plain["worst"],
                           "step_mode": "cuda_graph" if plain["graph"] else "host_loop",
-                          "gpu_launches": int(plain["launches"])},
+                          "gpu_launches": int(plain["launches"]), "clocks": plain["clocks"]},
             "learned": None if net is None else {
                 "ms_per_step": ms, "mean_sweeps_per_step": mean_sweeps,
                 "speedup_vs_plain_sor": plain["ms"] / ms, "sweeps_ratio": plain_sweeps / max(mean_sweeps, 1.0),
