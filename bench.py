@@ -203,6 +203,28 @@ def hbm_large(peak, peak_kind):
                            "note": "FP64 pressure differences: bound by the FP64 pipe, not HBM"}}
 
 
+# ---------------------------------------------------------------------------
+# multi-rank helpers (replicas: one independent domain per rank, weak scaling)
+
+def replica_seed(rank):
+    """Scene seed of a rank's replica: the ranks step different cities."""
+    return rank
+
+
+def max_over_ranks(x, dist, device):
+    """The slowest rank's time (every rank gets it)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_mcell_steps(cells_per_rank, world, ms_per_step):
+    """Whole-job throughput: the cells of all ranks per step over the slowest
+    rank's step time."""
+    return cells_per_rank * world / (ms_per_step * 1e-3) / 1e6
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -251,7 +273,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     # independent domain per rank (weak scaling: replicas, no data-path collective)
-    sc = workload(seed=rank)
+    sc = workload(seed=replica_seed(rank))
     n = sc.ncells
     dom = les.Domain(sc, precision=les.LES_FP32)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -302,9 +324,7 @@ def run_ours(args):
         launches = dom.timing()["launches"] - l0
         ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
         if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+            ms = max_over_ranks(ms, dist, dev)
         return {"ms": ms, "sweeps": sweeps, "worst": worst, "graph": graph_used, "clocks": clk,
                 "launches": launches}
 
@@ -382,9 +402,7 @@ def run_ours(args):
         ee.append(a.elapsed_time(b))
     e2e_ms = float(np.mean(ee))
     if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(e2e_ms, dist, dev)
 
     if rank == 0:
         peak, peak_kind = peaks()
@@ -396,7 +414,7 @@ def run_ours(args):
         mean_sweeps = float(np.mean(sweeps))
         plain_sweeps = float(np.mean(plain["sweeps"]))
         line = {
-            "metric": METRIC, "value": n * world / (ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": world,
+            "metric": METRIC, "value": aggregate_mcell_steps(n, world, ms), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 norms)",
             "data": "synthetic (seeded scene.py: random city, log-law inflow, 10% turbulence)",
@@ -406,7 +424,7 @@ def run_ours(args):
                        "sor_start": (f"previous-step pressure + learned correction (U-Net at stride {net.stride} "
                                      f"every {NET_EVERY} sweeps)" if net is not None else "previous-step pressure"),
                        "l2": "flushed (256 MiB write) before every timed step"},
-            "plain_sor": {"value": n * world / (plain["ms"] * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": plain["ms"],
+            "plain_sor": {"value": aggregate_mcell_steps(n, world, plain["ms"]), "unit": UNIT, "ms_per_step": plain["ms"],
                           "mean_sweeps_per_step": plain_sweeps, "max_rel_residual": plain["worst"],
                           "step_mode": "cuda_graph" if plain["graph"] else "host_loop",
                           "gpu_launches": int(plain["launches"]), "clocks": plain["clocks"]},
@@ -431,7 +449,7 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "step_mode": "cuda_graph" if graph_used else "host_loop",
             "sor_autotune": {"tile": tile, "kc": kc, "ms_per_sweep": tune_ms},
-            "e2e": {"value": n * world / (e2e_ms * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": aggregate_mcell_steps(n, world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": h2d, "ms_per_step": e2e_ms, "steps": e2e_steps},
             "clocks": clk,
         }
