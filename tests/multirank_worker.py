@@ -1,7 +1,7 @@
 """Rank body of tests/test_multirank.py, launched by torch.distributed.run with
 the gloo backend on the CPU: the benchmark's multi-rank host logic (slowest
-rank's time, whole-job throughput, per-rank replica seed), one JSON line per
-rank."""
+rank's time, whole-job throughput, per-rank replica seed); rank 0 prints one
+JSON line per rank."""
 import json
 import os
 import sys
@@ -21,9 +21,13 @@ def main():
         ms = 10.0 + 5.0 * rank              # rank r "took" 10 + 5 r ms per step
         slowest = bench.max_over_ranks(ms, dist, "cpu")
         value = bench.aggregate_mcell_steps(1_000_000, world, slowest)
-        dist.barrier()
-        print(json.dumps({"rank": rank, "world": world, "slowest_ms": slowest, "value": value,
-                          "seed": bench.replica_seed(rank)}), flush=True)
+        mine = {"rank": rank, "world": world, "slowest_ms": slowest, "value": value,
+                "seed": bench.replica_seed(rank)}
+        every = [None] * world
+        dist.all_gather_object(every, mine)
+        if rank == 0:                        # one writer: the ranks' lines cannot interleave
+            for d in every:
+                print(json.dumps(d), flush=True)
     finally:
         dist.destroy_process_group()
 
