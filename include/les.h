@@ -223,11 +223,13 @@ int les_set_timing(les_handle h, int32_t enable);
 int les_get_timing(les_handle h, les_timing_t* t);
 
 /*
- * Step execution mode.  enable = 1 (default): each step is one CUDA graph
- * launch (prefix kernels, device-side SOR stop test in a conditional WHILE
- * node, projection), with one host synchronisation per les_step call.
- * enable = 0: host-driven loop, reading the residual back after every batch
- * of check_every sweeps.  Phase timing (les_set_timing) always uses the
+ * Step execution mode.  enable = 1 (default): the solve loop runs as
+ * captured CUDA graphs of several batches of sweeps each (estimate and
+ * refinement included); every kernel in them returns at once when the
+ * device-side stop test has set its flag, and the host reads a mapped copy
+ * of the flag one graph behind (with fixed_sweeps the whole step is one
+ * graph).  enable = 0: host-driven loop, reading the residual back after
+ * every batch of check_every sweeps.  Phase timing (les_set_timing) always uses the
  * host-driven loop.  Both modes compute the same iterates.
  */
 int les_set_graph(les_handle h, int32_t enable);
@@ -238,8 +240,9 @@ int les_set_graph(les_handle h, int32_t enable);
  * whose les_sor_tile tz is 0 are column tiles marching kc planes per CTA
  * (kc <= 0: the whole column), the others are tx x ty x tz blocks (kc
  * ignored); tiles 17-24 are 28 x ty x tz blocks loaded by the tensor-memory
- * accelerator, 21-24 in persistent CTAs that prefetch their next block (FP32
- * grids without periodic axes only, else LES_EINVAL).
+ * accelerator (FP32 grids only, else LES_EINVAL), 21-24 in persistent CTAs
+ * that prefetch their next block (FP32 grids without periodic axes only,
+ * else LES_EINVAL).
  * Every choice computes the same iterate.
  * les_autotune_sor times each tile shape with a few k-chunk lengths on this
  * handle's grid (sweeps per candidate), keeps the fastest and reports it;
@@ -255,6 +258,35 @@ int les_autotune_sor(les_handle h, int32_t sweeps, double* best_ms_per_sweep);
  * correction buffers (state untouched, configuration kept).  LES_EINVAL for
  * a tile this grid cannot use. */
 int les_time_sor(les_handle h, int32_t tile, int32_t kc, int32_t sweeps, double* ms_per_sweep);
+
+/*
+ * les_sor_compare: the solver's red-black SOR next to the paper's "twinned
+ * double buffering" (Sec. 2.6) on one pressure problem.  From p0, run
+ * `sweeps` sweeps of the variant on the correction equation A d = rhs - A p0
+ * (FP64 residual, sweeps in the handle's field type) and report:
+ *   p_out        p0 + d (host, dense nx*ny*nz FP64, i fastest; nullable);
+ *   ms_per_sweep device time per sweep (CUDA events on the handle's stream);
+ *   rel_residual FP64 ||rhs - A (p0 + d)|| / ||rhs|| over the unknowns.
+ * Variants:
+ *   LES_SOR_REDBLACK  the update printed in Sec. 2.6, red cells (i+j+k odd)
+ *                     then black, with this handle's sweep kernel and tile;
+ *   LES_SOR_TWINNED   two copies of the correction interleaved as pairs
+ *                     (the paper's array of two-float vectors): for nrd = 0
+ *                     copy 1 takes the printed update of every unknown with
+ *                     all neighbours from copy 0, for nrd = 1 copy 0 from
+ *                     copy 1.  This is a weighted Jacobi iteration: it
+ *                     converges for 0 < omega < 1 on these operators and
+ *                     diverges at the SOR value 1.7.
+ * omega > 0 overrides the grid's relaxation factor for the call; omega <= 0
+ * keeps it.  rhs and p0: host, dense nx*ny*nz FP64; rhs must be compatible
+ * (zero dz-weighted mean over the fluid cells) for the residual to fall.
+ * The handle's state is untouched (scratch buffers are allocated on first
+ * use and kept); sweeps >= 1.  LES_EINVAL for a bad variant or argument.
+ */
+#define LES_SOR_REDBLACK 0
+#define LES_SOR_TWINNED 1
+int les_sor_compare(les_handle h, int32_t variant, double omega, int32_t sweeps, const double* rhs,
+                    const double* p0, double* p_out, double* ms_per_sweep, double* rel_residual);
 
 /*
  * les_residual_noalloc: FP64 norms of the pressure Poisson residual for

@@ -61,6 +61,7 @@ typedef struct {
     double *dz, *dzs, *inflow;
     unsigned char* solid;
     double *u, *v, *w, *p, *rhs, *nut;
+    double *p_twin;           /* second copy of p for the twinned double buffer (on first use) */
     double *us, *vs, *ws;     /* u* (after AB2 + forcing) */
     double *fu, *fv, *fw;     /* F_old: previous tendency (AB2 history) */
     int64_t step;
@@ -606,6 +607,26 @@ static void sor_sweep(orc_t* o) {
     sor_half(o, 1);
 }
 
+/* "Twinned double buffering" (Sec. 2.6): two copies of p.  For nrd = 0 every
+ * unknown of the second copy takes the printed update with its own value and
+ * all its neighbours from the first copy; for nrd = 1 the first copy from the
+ * second.  Every cell of a half-sweep reads only the other copy (a weighted
+ * Jacobi iteration with relaxation omega).                                 */
+static void twin_half(orc_t* o, int nrd, double omega) {
+    const orc_params* P = &o->P;
+    const double* src = nrd == 0 ? o->p : o->p_twin;
+    double* dst = nrd == 0 ? o->p_twin : o->p;
+    for (int k = 1; k <= P->nz; ++k)
+        for (int j = 1; j <= P->ny; ++j)
+            for (int i = 1; i <= P->nx; ++i) {
+                coef_t c;
+                if (!coefs(o, i, j, k, &c)) continue;
+                size_t ix = IX(o, i, j, k);
+                double reltmp = omega * (c.cn1 * (nb_sum(o, src, i, j, k, &c) - o->rhs[ix]) - src[ix]);
+                dst[ix] = src[ix] + reltmp;
+            }
+}
+
 /* (A p)_c = sum_nb a_nb (p_nb - p_c) on fluid cells, 0 elsewhere */
 static double apply_A_cell(const orc_t* o, const double* p, int i, int j, int k) {
     coef_t c;
@@ -770,7 +791,7 @@ orc_t* orc_create(const orc_params* P, const double* dz, const unsigned char* so
 void orc_destroy(orc_t* o) {
     if (!o) return;
     double* arrs[] = {o->u, o->v, o->w, o->p, o->rhs, o->nut, o->us, o->vs, o->ws,
-                      o->fu, o->fv, o->fw, o->dz, o->dzs, o->inflow};
+                      o->fu, o->fv, o->fw, o->dz, o->dzs, o->inflow, o->p_twin};
     for (size_t a = 0; a < sizeof(arrs) / sizeof(arrs[0]); ++a) free(arrs[a]);
     free(o->series_t);
     free(o->series_p);
@@ -885,6 +906,17 @@ void orc_outflow_fix(orc_t* o) { outflow_fix(o); }
 void orc_make_rhs(orc_t* o) { make_rhs(o); }
 void orc_sor_half(orc_t* o, int nrd) { sor_half(o, nrd); }
 void orc_sor_sweeps(orc_t* o, int n) { for (int s = 0; s < n; ++s) sor_sweep(o); }
+/* n twinned sweeps (nrd = 0 then 1) starting with both copies equal to p */
+int orc_twin_sweeps(orc_t* o, int n, double omega) {
+    const size_t cells = (size_t)o->sx * o->sy * o->sz;
+    if (!o->p_twin && !(o->p_twin = (double*)malloc(cells * sizeof(double)))) return -1;
+    memcpy(o->p_twin, o->p, cells * sizeof(double));
+    for (int s = 0; s < n; ++s) {
+        twin_half(o, 0, omega);
+        twin_half(o, 1, omega);
+    }
+    return 0;
+}
 double orc_residual(orc_t* o) { return residual(o); }
 void orc_sor_solve(orc_t* o) { sor_solve(o); }
 void orc_gauge(orc_t* o) { gauge(o); }

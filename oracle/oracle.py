@@ -94,6 +94,8 @@ def lib():
             getattr(L, name).argtypes = [vp]
         L.orc_sor_half.argtypes = [vp, ctypes.c_int]
         L.orc_sor_sweeps.argtypes = [vp, ctypes.c_int]
+        L.orc_twin_sweeps.argtypes = [vp, ctypes.c_int, ctypes.c_double]
+        L.orc_twin_sweeps.restype = ctypes.c_int
         L.orc_residual.restype = ctypes.c_double
         L.orc_residual.argtypes = [vp]
         L.orc_tendency.argtypes = [vp, ctypes.c_int]
@@ -209,6 +211,10 @@ class Oracle:
     def make_rhs(self): lib().orc_make_rhs(self.h)
     def sor_half(self, nrd): lib().orc_sor_half(self.h, nrd)
     def sor_sweeps(self, n): lib().orc_sor_sweeps(self.h, n)
+    def twin_sweeps(self, n, omega):
+        """n sweeps of the twinned double buffer (Sec. 2.6) with relaxation omega."""
+        if lib().orc_twin_sweeps(self.h, n, omega) != 0:
+            raise MemoryError("orc_twin_sweeps")
     def residual(self) -> float: return lib().orc_residual(self.h)
     def sor_solve(self): lib().orc_sor_solve(self.h)
     def gauge(self): lib().orc_gauge(self.h)

@@ -123,6 +123,13 @@ struct les_s {
     bool pipe_ok = false;                 // persistent TMA tiles (no periodic axis)
     float* cn1tab = nullptr;              // cn1 over (plane, open-face mask) for the pipelined sweep
     double* diag64 = nullptr;             // FP64 diagonal over (plane, open-face mask), the residual's
+    // les_sor_compare scratch (allocated on first use): p0, rhs, p0 + d (FP64,
+    // padded), the four norms, and the twinned pair array of the correction
+    double* cmp_p0 = nullptr;
+    double* cmp_b = nullptr;
+    double* cmp_pn = nullptr;
+    double* cmp_out = nullptr;
+    void* twin = nullptr;
     // learned warm start and training-pair recording
     int warm = LES_WARM_PREV;
     les_net_s* net = nullptr;
@@ -1115,6 +1122,74 @@ int pressure_solve_impl(les_s* h, const void* rhs, les_stats_t* st) {
     return rc;
 }
 
+// les_sor_compare: sweeps of one variant on A d = rhs - A p0 from d = 0 on
+// the scratch correction buffers (the solver's residual buffer holds r; both
+// are re-formed at the next solve), p0 + d and its FP64 residual
+template <typename T>
+int sor_compare_impl(les_s* h, int variant, double omega, int sweeps, const double* rhs, const double* p0,
+                     double* p_out, double* ms_per_sweep, double* rel_residual) {
+    Geo<T> g = geo<T>(h);
+    if (omega > 0.0) g.omega = (T)omega;
+    const size_t nbytes = h->n * sizeof(double);
+    int rc;
+    if (!h->cmp_p0) {
+        if ((rc = dalloc(h, (void**)&h->cmp_p0, nbytes)) || (rc = dalloc(h, (void**)&h->cmp_b, nbytes)) ||
+            (rc = dalloc(h, (void**)&h->cmp_pn, nbytes)) || (rc = dalloc(h, (void**)&h->cmp_out, 4 * sizeof(double))))
+            return rc;
+        CK(cudaMemsetAsync(h->cmp_p0, 0, nbytes, h->stream));
+        CK(cudaMemsetAsync(h->cmp_b, 0, nbytes, h->stream));
+    }
+    if (variant == LES_SOR_TWINNED && !h->twin && (rc = dalloc(h, &h->twin, 2 * h->n * h->es))) return rc;
+    if ((rc = upload<double, double>(h, h->cmp_p0, 0, p0, 0))) return rc;
+    if ((rc = upload<double, double>(h, h->cmp_b, 0, rhs, 0))) return rc;
+    const Reduce red{h->partials, h->counter, h->sc};
+    h->launches += launch_cmp_residual<T>(g, h->cmp_p0, h->cmp_b, (T*)h->rr, red, h->cmp_out, h->stream);
+    // the sweep kernels return at once once a solve is done: clear the flag for
+    // the call and put it back afterwards
+    int done_save = 0;
+    CK(cudaMemcpyAsync(&done_save, &h->sc->done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemsetAsync(&h->sc->done, 0, sizeof(int), h->stream));
+    const int dcur_save = h->dcur;
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    CK(cudaEventRecord(a, h->stream));
+    long long nl = 0;
+    const T* dres;
+    int stride;
+    if (variant == LES_SOR_REDBLACK) {
+        const int dc = run_sweeps<T>(h, g, sweeps, 1, nl, h->stream);
+        dres = (const T*)h->dl[dc];
+        stride = 1;
+    } else {
+        CK(cudaMemsetAsync(h->twin, 0, 2 * h->n * h->es, h->stream));
+        for (int sw = 0; sw < sweeps; ++sw) {
+            nl += launch_twin_half<T>(g, h->twin, (const T*)h->rr, 0, g.omega, h->stream);
+            nl += launch_twin_half<T>(g, h->twin, (const T*)h->rr, 1, g.omega, h->stream);
+        }
+        dres = (const T*)h->twin;      // copy 0 holds the iterate after a whole sweep
+        stride = 2;
+    }
+    CK(cudaEventRecord(b, h->stream));
+    h->launches += nl;
+    h->launches += launch_cmp_add<T>(g, h->cmp_p0, dres, stride, h->cmp_pn, h->n, h->stream);
+    h->launches += launch_cmp_residual<T>(g, h->cmp_pn, h->cmp_b, (T*)h->rr, red, h->cmp_out + 2, h->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&h->sc->done, &done_save, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    double norms[4];
+    CK(cudaMemcpyAsync(norms, h->cmp_out, sizeof norms, cudaMemcpyDeviceToHost, h->stream));
+    if (p_out && (rc = download<double, double>(h, h->cmp_pn, 0, p_out, 0))) return rc;
+    CK(cudaStreamSynchronize(h->stream));
+    h->dcur = dcur_save;
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *ms_per_sweep = ms / sweeps;
+    *rel_residual = norms[3] > 0.0 ? std::sqrt(norms[2] / norms[3]) : std::sqrt(norms[2]);
+    return LES_OK;
+}
+
 // checkpoint blob: header, then the raw padded arrays and the inflow
 struct StateHeader {
     uint64_t magic;
@@ -1397,6 +1472,19 @@ int les_sor_tile(int32_t tile, int32_t* tx, int32_t* ty, int32_t* tz) {
     if (ty) *ty = kSorTiles[tile].ty;
     if (tz) *tz = kSorTiles[tile].tz;
     return LES_OK;
+}
+
+int les_sor_compare(les_handle h, int32_t variant, double omega, int32_t sweeps, const double* rhs,
+                    const double* p0, double* p_out, double* ms_per_sweep, double* rel_residual) {
+    if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
+    if (variant != LES_SOR_REDBLACK && variant != LES_SOR_TWINNED)
+        return fail(h, LES_EINVAL, "variant %d is not LES_SOR_REDBLACK or LES_SOR_TWINNED", variant);
+    if (sweeps < 1) return fail(h, LES_EINVAL, "sweeps must be >= 1");
+    if (!rhs || !p0 || !ms_per_sweep || !rel_residual)
+        return fail(h, LES_EINVAL, "rhs, p0, ms_per_sweep and rel_residual must be set");
+    return h->prec == LES_FP64
+               ? sor_compare_impl<double>(h, variant, omega, sweeps, rhs, p0, p_out, ms_per_sweep, rel_residual)
+               : sor_compare_impl<float>(h, variant, omega, sweeps, rhs, p0, p_out, ms_per_sweep, rel_residual);
 }
 
 int les_time_sor(les_handle h, int32_t tile, int32_t kc, int32_t sweeps, double* ms_per_sweep) {

@@ -254,6 +254,12 @@ int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, const float* cn1tab
                    int zero, Scalars* sc, cudaStream_t s);
 int launch_cn1_table(const Geo<float>& g, float* tab, cudaStream_t s);
 template <typename T> int launch_diag_table(const Geo<T>& g, double* tab, cudaStream_t s);
+// comparison of SOR variants (les_sor_compare)
+template <typename T> int launch_cmp_residual(const Geo<T>& g, const double* p, const double* b, T* r,
+                                              const Reduce& red, double* out, cudaStream_t s);
+template <typename T> int launch_cmp_add(const Geo<T>& g, const double* p0, const T* dv, int stride, double* pn,
+                                         size_t n, cudaStream_t s);
+template <typename T> int launch_twin_half(const Geo<T>& g, void* tw, const T* r, int nrd, T omega, cudaStream_t s);
 int launch_wait_selftest(unsigned long long limit_ns, int* status, cudaStream_t s);
 
 // learned warm start (les_kernels.cu): energy-norm line search along q and p += alpha q

@@ -1425,6 +1425,133 @@ int launch_count_unknowns(const Dom& d, const uint8_t* flags, unsigned long long
     return 1;
 }
 
+// ---------------------------------------------------------------------------
+// Comparison of SOR variants (les_sor_compare): the FP64 residual of a given
+// pressure without the solver's bookkeeping, p0 + d, and the paper's twinned
+// double-buffer half-sweep (Sec. 2.6).
+
+// r = b - A p (FP64, stored in T) on the unknowns, 0 elsewhere; out[0] =
+// ||r||^2, out[1] = ||b||^2 over the unknowns (last-block sums)
+template <typename T>
+__global__ void __launch_bounds__(256) k_cmp_residual(Geo<T> g, const double* p, const double* b, T* r, Reduce red,
+                                                      double* out) {
+    const Dom& d = g.d;
+    const int n = d.nx * d.ny * d.nz;
+    double x[2] = {0.0, 0.0};
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        int i, j, k;
+        cell_of(d, q, i, j, k);
+        const long long c = d.at(i, j, k);
+        const uint8_t f = g.flags[c];
+        if (!(f & F_UNK)) {
+            r[c] = T(0);
+            continue;
+        }
+        Poisson<T> Q{g};
+        double ae, aw, an, as, at, ab;
+        Q.coefs(f, k, g.cx64, g.cy64, g.cT64, g.cB64, ae, aw, an, as, at, ab);
+        long long e, w, nn, s_, t, bt;
+        Q.nbr(i, j, k, e, w, nn, s_, t, bt);
+        double s = 0.0;
+        s += ae * p[e];
+        s += aw * p[w];
+        s += an * p[nn];
+        s += as * p[s_];
+        s += at * p[t];
+        s += ab * p[bt];
+        const double res = b[c] - (s - g.diag64[k * 64 + (f & 63)] * p[c]);
+        r[c] = (T)res;
+        x[0] += res * res;
+        x[1] += b[c] * b[c];
+    }
+    if (grid_sum_at<2>(x, red, gridDim.x, blockIdx.x)) {
+        if (threadIdx.x == 0) {
+            out[0] = x[0];
+            out[1] = x[1];
+        }
+    }
+}
+
+template <typename T>
+int launch_cmp_residual(const Geo<T>& g, const double* p, const double* b, T* r, const Reduce& red, double* out,
+                        cudaStream_t s) {
+    k_cmp_residual<T><<<reduce_blocks(g.d), 256, 0, s>>>(g, p, b, r, red, out);
+    return 1;
+}
+
+// p_new = p0 + d on the unknowns (d read with a stride: 2 for one copy of a
+// twinned pair array), p0 elsewhere; over the whole padded array
+template <typename T>
+__global__ void k_cmp_add(const uint8_t* flags, const double* p0, const T* dv, int stride, double* pn, size_t n) {
+    const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    pn[c] = p0[c] + ((flags[c] & F_UNK) ? (double)dv[c * stride] : 0.0);
+}
+
+template <typename T>
+int launch_cmp_add(const Geo<T>& g, const double* p0, const T* dv, int stride, double* pn, size_t n,
+                   cudaStream_t s) {
+    k_cmp_add<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g.flags, p0, dv, stride, pn, n);
+    return 1;
+}
+
+// the two copies of a twinned correction, interleaved (the paper's array of
+// two-element vectors): one aligned access reads both
+template <typename T>
+struct alignas(2 * sizeof(T)) Twin {
+    T c[2];
+};
+
+// One half of a twinned double-buffer sweep (Sec. 2.6) on the correction
+// equation A d = r: copy 1 - nrd of every unknown takes the printed update
+// with its own value and every neighbour from copy nrd (the same per-cell
+// arithmetic as the red-black kernels).  A 32 x 8 column tile walks kc planes.
+template <typename T>
+__global__ void k_twin_half(Geo<T> g, Twin<T>* tw, const T* __restrict__ r, int nrd, T omega, int kc) {
+    const Dom& d = g.d;
+    const int i = blockIdx.x * 32 + threadIdx.x + 1, j = blockIdx.y * 8 + threadIdx.y + 1;
+    const int kb = blockIdx.z * kc + 1, ke = min(kb + kc, d.nz + 1);
+    if (i > d.nx || j > d.ny) return;
+    const int src = nrd, dst = 1 - nrd;
+    const int pl = (int)d.plane;
+    const int oe = (d.perx && i == d.nx) ? -(d.nx - 1) : 1;
+    const int ow = (d.perx && i == 1) ? (d.nx - 1) : -1;
+    const int on = (d.pery && j == d.ny) ? -(d.ny - 1) * d.px : d.px;
+    const int os = (d.pery && j == 1) ? (d.ny - 1) * d.px : -d.px;
+    long long c = d.at(i, j, kb);
+    for (int k = kb; k < ke; ++k, c += pl) {
+        const uint8_t f = g.flags[c];
+        if (!(f & F_UNK)) continue;
+        const int ot = (d.perz && k == d.nz) ? -(d.nz - 1) * pl : pl;
+        const int ob = (d.perz && k == 1) ? (d.nz - 1) * pl : -pl;
+        const T ae = (f & F_E) ? g.cx : T(0), aw = (f & F_W) ? g.cx : T(0);
+        const T an = (f & F_N) ? g.cy : T(0), as = (f & F_S) ? g.cy : T(0);
+        const T at = (f & F_T) ? g.cT[k] : T(0), ab = (f & F_B) ? g.cB[k] : T(0);
+        const T cn1 = T(1) / (ae + aw + an + as + at + ab);
+        const Twin<T> ve = tw[c + oe], vw = tw[c + ow], vn = tw[c + on], vs = tw[c + os], vt = tw[c + ot],
+                      vb = tw[c + ob], vc = tw[c];
+        T s = T(0);
+        s += ae * ve.c[src];
+        s += aw * vw.c[src];
+        s += an * vn.c[src];
+        s += as * vs.c[src];
+        s += at * vt.c[src];
+        s += ab * vb.c[src];
+        const T own = vc.c[src];
+        const T reltmp = omega * (cn1 * (s - r[c]) - own);
+        tw[c].c[dst] = own + reltmp;
+    }
+}
+
+template <typename T>
+int launch_twin_half(const Geo<T>& g, void* tw, const T* r, int nrd, T omega, cudaStream_t s) {
+    const Dom& d = g.d;
+    const int kc = accum_kc(d);
+    k_twin_half<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, (d.nz + kc - 1) / kc), dim3(32, 8), 0, s>>>(
+        g, (Twin<T>*)tw, r, nrd, omega, kc);
+    return 1;
+}
+
 // FP64 diagonal of the Poisson operator over (plane, open-face mask): the
 // sum of the open faces' coefficients in the order of the residual kernels
 template <typename T>
@@ -1526,6 +1653,11 @@ int launch_refine_ens(const EnsTab<float>& tab, int dcur, const CondArgs& ca, cu
                                    const double*, double*, Scalars*, cudaStream_t);                     \
     template int launch_rhs_eff<T>(const Geo<T>&, const T*, T*, const Scalars*, cudaStream_t);          \
     template int launch_diag_table<T>(const Geo<T>&, double*, cudaStream_t);                          \
+    template int launch_cmp_residual<T>(const Geo<T>&, const double*, const double*, T*, const Reduce&,       \
+                                        double*, cudaStream_t);                                          \
+    template int launch_cmp_add<T>(const Geo<T>&, const double*, const T*, int, double*, size_t,            \
+                                   cudaStream_t);                                                       \
+    template int launch_twin_half<T>(const Geo<T>&, void*, const T*, int, T, cudaStream_t);               \
     template int launch_gauge<T>(const Geo<T>&, const double*, double*, const Scalars*, cudaStream_t);   \
     template int launch_warm<T>(const Geo<T>&, const T*, const float*, double*, T*, double*, const Reduce&,     \
                                 cudaStream_t);                                                          \

@@ -22,6 +22,7 @@ LES_FP32, LES_FP64 = 0, 1
 (LES_AUX_NUT, LES_AUX_RHS, LES_AUX_USTAR, LES_AUX_VSTAR, LES_AUX_WSTAR,
  LES_AUX_FU, LES_AUX_FV, LES_AUX_FW, LES_AUX_R0, LES_AUX_DELTA, LES_AUX_MASK) = range(11)
 LES_WARM_PREV, LES_WARM_NET, LES_WARM_ZERO = 0, 1, 2
+LES_SOR_REDBLACK, LES_SOR_TWINNED = 0, 1
 
 
 class les_grid_t(ctypes.Structure):
@@ -103,6 +104,8 @@ def lib(build_if_missing: bool = False):
         L.les_ensemble_set_warmstart.argtypes = [vp, vp, i32]
         L.les_selftest_wait_timeout.argtypes = [ctypes.c_int64, vp]
         L.les_time_sor.argtypes = [vp, i32, i32, i32, ctypes.POINTER(ctypes.c_double)]
+        L.les_sor_compare.argtypes = [vp, i32, ctypes.c_double, i32, vp, vp, vp, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double)]
         L.les_set_record.argtypes = [vp, i32]
         L.les_set_record_at.argtypes = [vp, i32]
         L.les_set_net_kernels.argtypes = [vp, i32]
@@ -616,6 +619,20 @@ class Domain:
 
     def sor_config(self):
         return les_get_sor_config(self.h)
+
+    def sor_compare(self, variant, omega, sweeps, rhs, p0):
+        """les_sor_compare: (p0 + d after `sweeps` sweeps of the variant, ms per
+        sweep, FP64 relative residual).  rhs, p0: (nz, ny, nx) float64."""
+        nx, ny, nz = self.nx, self.ny, self.nz
+        rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+        p0 = np.ascontiguousarray(p0, dtype=np.float64)
+        if rhs.shape != (nz, ny, nx) or p0.shape != (nz, ny, nx):
+            raise ValueError("rhs and p0 must be (nz, ny, nx)")
+        out = np.empty((nz, ny, nx), dtype=np.float64)
+        ms, rel = ctypes.c_double(), ctypes.c_double()
+        _check(lib().les_sor_compare(self.h, variant, float(omega), int(sweeps), rhs.ctypes.data,
+                                     p0.ctypes.data, out.ctypes.data, ctypes.byref(ms), ctypes.byref(rel)), self.h)
+        return out, ms.value, rel.value
 
     def time_sor(self, tile, kc=0, sweeps=20):
         ms = ctypes.c_double()

@@ -14,6 +14,8 @@ import argparse
 import json
 import time
 
+import numpy as np
+
 from . import les, scene
 
 
@@ -27,7 +29,6 @@ def run_ensemble(a):
     ens.set_graph(bool(a.graph))
     net = None
     if a.net:
-        import numpy as np
         z = np.load(a.net)
         net = les.Net(seed=0, stream=None, stride=int(z["stride"]))
         net.set_params(z["params"])
@@ -86,6 +87,10 @@ def main():
                     help="time every SOR sweep configuration on the workload after the warm-up steps")
     ap.add_argument("--net", default=None, help="trained warm-start network (.npz: params, stride)")
     ap.add_argument("--net-every", type=int, default=0, help="network correction every n sweeps")
+    ap.add_argument("--sor-compare", default=None,
+                    help="comma-separated sweep counts: red-black SOR vs the twinned double buffer "
+                         "(les_sor_compare) from the previous step's pressure and the next step's rhs")
+    ap.add_argument("--twin-omega", type=float, default=0.9, help="relaxation of the twinned double buffer")
     ap.add_argument("--fixed-sweeps", type=int, default=0,
                     help="run exactly this many SOR sweeps per step (0: solve to the tolerance)")
     a = ap.parse_args()
@@ -100,13 +105,30 @@ def main():
         d.set_sor_config(a.tile, a.kc)
     net = None
     if a.net:
-        import numpy as np
         z = np.load(a.net)
         net = les.Net(seed=0, stream=None, stride=int(z["stride"]))
         net.set_params(z["params"])
     for _ in range(a.warmup):
         d.step(1)
     tune = None
+    if a.sor_compare:
+        # the pressure problem of a real step: the previous step's pressure and
+        # the rhs (mean removed) the next step solves
+        p_prev = d.fields()[3].astype(np.float64)
+        d.step(1)
+        rhs = d.aux(les.LES_AUX_RHS).astype(np.float64)
+        rows = []
+        for n in (int(x) for x in a.sor_compare.split(",")):
+            for name, vid, om in (("red-black SOR", les.LES_SOR_REDBLACK, -1.0),
+                                  ("twinned double buffer", les.LES_SOR_TWINNED, a.twin_omega)):
+                _, ms, rel = d.sor_compare(vid, om, n, rhs, p_prev)
+                rows.append({"variant": name, "omega": sc.omega if om <= 0 else om, "sweeps": n,
+                             "ms_per_sweep": ms, "rel_residual": rel})
+        _, ms17, rel17 = d.sor_compare(les.LES_SOR_TWINNED, 1.7, 20, rhs, p_prev)
+        rows.append({"variant": "twinned double buffer", "omega": 1.7, "sweeps": 20, "ms_per_sweep": ms17,
+                     "rel_residual": rel17})
+        print(json.dumps({"workload": a.workload, "cells": sc.ncells, "sor_config": d.sor_config(), "rows": rows}))
+        return
     if a.sweep_table:
         rows = []
         for t in range(-1, 25):

@@ -333,3 +333,67 @@ def test_fp64_inflow_series_matches_oracle():
     d.step(6)
     compare_fields(d, o, 1e-11)
     d.close()
+
+
+# ---------------------------------------------------------------------------
+# les_sor_compare: the solver's red-black SOR and the paper's twinned double
+# buffer (Sec. 2.6) on one pressure problem, against the oracle
+
+def _compatible_problem(sc, seed):
+    rng = np.random.default_rng(seed)
+    fluid = sc.solid == 0
+    rhs = rng.standard_normal(sc.solid.shape) * fluid
+    w = np.broadcast_to(sc.dz[:, None, None], rhs.shape)[fluid]
+    rhs[fluid] -= np.sum(w * rhs[fluid]) / np.sum(w)
+    p0 = rng.standard_normal(sc.solid.shape) * fluid
+    return rhs, p0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("variant", ["redblack", "twinned"])
+def test_sor_compare_matches_oracle(prec, variant):
+    sc = city(nx=40, ny=24, nz=12, periodic_y=True, fixed_sweeps=1, max_sweeps=10)
+    rhs, p0 = _compatible_problem(sc, 21)
+    sweeps = 7
+    o = Oracle(sc)
+    o.set(A_P, p0)
+    o.set(A_RHS, rhs)
+    if variant == "twinned":
+        omega, vid = 0.9, les.LES_SOR_TWINNED
+        o.twin_sweeps(sweeps, omega)
+    else:
+        omega, vid = -1.0, les.LES_SOR_REDBLACK      # the grid's 1.7, as in the oracle
+        o.sor_sweeps(sweeps)
+    want = o.get(A_P)
+    want_rel = o.residual()
+    d = les.Domain(sc, precision=les.LES_FP64 if prec == "fp64" else les.LES_FP32)
+    d.step(1)
+    before = d.fields()
+    got, ms, rel = d.sor_compare(vid, omega, sweeps, rhs, p0)
+    after = d.fields()
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)                  # the handle's state is untouched
+    scale = np.abs(want).max()
+    tol = 1e-11 if prec == "fp64" else 1e-5
+    assert np.abs(got - want).max() <= tol * scale, (np.abs(got - want).max(), scale)
+    assert rel == pytest.approx(want_rel, rel=1e-9 if prec == "fp64" else 1e-3)
+    assert ms > 0.0
+    d.close()
+
+
+def test_sor_compare_leaves_the_next_step_unchanged():
+    sc = city(nx=40, ny=24, nz=12, turb=0.1, fixed_sweeps=1, max_sweeps=10)
+    rhs, p0 = _compatible_problem(sc, 4)
+    a, b = les.Domain(sc), les.Domain(sc)
+    a.step(1)
+    b.step(1)
+    a.sor_compare(les.LES_SOR_TWINNED, 0.9, 5, rhs, p0)
+    a.sor_compare(les.LES_SOR_REDBLACK, -1.0, 5, rhs, p0)
+    a.step(1)
+    b.step(1)
+    for x, y in zip(a.fields(), b.fields()):
+        assert np.array_equal(x, y)
+    with pytest.raises(les.LesError):
+        a.sor_compare(7, 0.9, 5, rhs, p0)
+    a.close()
+    b.close()

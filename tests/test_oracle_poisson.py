@@ -250,3 +250,60 @@ def test_matrix_form_sor(omega):
             s = A[m] @ x - A[m, m] * x[m]
             x[m] = x[m] + omega * ((bb[m] - s) / A[m, m] - x[m])
     np.testing.assert_allclose(got, x, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("omega", [0.6, 0.9])
+def test_twinned_sweep_is_two_jacobi_steps(omega):
+    """One twinned double-buffer sweep (Sec. 2.6: the second copy from the
+    first, then the first from the second) equals two steps of the textbook
+    weighted Jacobi recurrence on the assembled matrix, every unknown updated
+    from the previous iterate only."""
+    nx, ny, nz = 4, 5, 3
+    solid = np.zeros((nz, ny, nx), np.uint8)
+    solid[0, 2, 1] = 1
+    sc = scene.box_scene(nx, ny, nz, dz=scene.stretched_dz(nz), solid=solid)
+    o = Oracle(sc)
+    A = assemble(o, nx, ny, nz)
+    rng = np.random.default_rng(9)
+    p0 = rng.standard_normal((nz, ny, nx)) * (solid == 0)
+    b = rng.standard_normal((nz, ny, nx)) * (solid == 0)
+    o.set(A_P, p0)
+    o.set(A_RHS, b)
+    o.twin_sweeps(2, omega)
+    got = o.get(A_P).ravel()
+    x = p0.ravel().copy()
+    bb = b.ravel()
+    d = np.diag(A)
+    live = d != 0.0
+    for _ in range(4):
+        s = A @ x - d * x
+        xn = x.copy()
+        xn[live] = x[live] + omega * ((bb[live] - s[live]) / d[live] - x[live])
+        x = xn
+    np.testing.assert_allclose(got, x, rtol=0, atol=1e-13)
+
+
+def test_twinned_relaxation_range():
+    """The twinned scheme is a weighted Jacobi iteration: on a compatible
+    problem it converges for a relaxation below 1 and diverges at the SOR value
+    1.7 (the iteration multiplies the checkerboard mode by about 1 - 2 omega)."""
+    n = 8
+    solid = np.zeros((n, n, n), np.uint8)
+    solid[:3, 2:4, 2:4] = 1
+    solid[:5, 5, 5] = 1
+    dz = scene.stretched_dz(n)
+    sc = scene.box_scene(n, n, n, dz=dz, solid=solid)
+    fluid = solid == 0
+    rng = np.random.default_rng(5)
+    rhs = rng.standard_normal((n, n, n)) * fluid
+    rhs[fluid] -= _vmean(rhs, dz, fluid)
+    res = {}
+    for omega, sweeps in ((0.9, 100), (1.7, 30)):
+        o = Oracle(sc)
+        o.set(A_P, np.zeros((n, n, n)))
+        o.set(A_RHS, rhs)
+        r0 = o.residual()
+        o.twin_sweeps(sweeps, omega)
+        res[omega] = o.residual() / r0
+    assert res[0.9] < 1e-2
+    assert res[1.7] > 1e6
