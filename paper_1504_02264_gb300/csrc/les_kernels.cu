@@ -165,25 +165,6 @@ struct StrainOps {
     }
 };
 
-template <typename T>
-struct Stencil : StrainOps<T, Stencil<T>> {
-    const Geo<T>& g;
-    const T* u;
-    const T* v;
-    const T* w;
-    long long c0;
-    int i0, j0, k0, px, pl;
-    __device__ __forceinline__ Stencil(const Geo<T>& g_, const T* u_, const T* v_, const T* w_, int i, int j, int k)
-        : g(g_), u(u_), v(v_), w(w_), c0(g_.d.at(i, j, k)), i0(i), j0(j), k0(k), px(g_.d.px),
-          pl((int)g_.d.plane) {}
-    __device__ __forceinline__ long long at(int i, int j, int k) const {
-        return c0 + ((i - i0) + (j - j0) * px + (k - k0) * pl);
-    }
-    __device__ __forceinline__ T U(int i, int j, int k) const { return u[at(i, j, k)]; }
-    __device__ __forceinline__ T V(int i, int j, int k) const { return v[at(i, j, k)]; }
-    __device__ __forceinline__ T W(int i, int j, int k) const { return w[at(i, j, k)]; }
-};
-
 // nu_t ghost layer: zero gradient (the adjacent interior value) or periodic
 // wrap, axis by axis (x over interior j, k; y over all i; z over all i, j), so
 // a ghost read equals the read of the index clamped / wrapped on each axis
@@ -230,21 +211,9 @@ struct NutOps {
     }
 };
 
-template <typename T>
-struct Nut : NutOps<T, Nut<T>> {
-    const T* nut;
-    long long c0;
-    int i0, j0, k0, px, pl;
-    __device__ __forceinline__ Nut(const Dom& d, const T* nut_, int i, int j, int k)
-        : nut(nut_), c0(d.at(i, j, k)), i0(i), j0(j), k0(k), px(d.px), pl((int)d.plane) {}
-    __device__ __forceinline__ T operator()(int i, int j, int k) const {
-        return nut[c0 + ((i - i0) + (j - j0) * px + (k - k0) * pl)];
-    }
-};
-
-// the same reads from a shared-memory window: planes in 4 rolling slots
-// (plane k in slot k & 3), each MY rows of MX cells, the window's first cell
-// being (ib, jb)
+// velocity and nu_t reads from a shared-memory window: planes in 4 rolling
+// slots (plane k in slot k & 3), each MY rows of MX cells, the window's first
+// cell being (ib, jb)
 template <typename T, int MX, int MY>
 struct SmemStencil : StrainOps<T, SmemStencil<T, MX, MY>> {
     const Geo<T>& g;
