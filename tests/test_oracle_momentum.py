@@ -351,3 +351,58 @@ def test_mass_flux_balanced_after_correction():
     st = o.stats()
     assert abs(st["q_out"] - st["q_in"]) <= 1e-12 * abs(st["q_in"])
     assert st["mass_factor"] != 1.0
+
+
+# ----------------------------------------------------------------------------
+# axis exchange: on a uniform, all-periodic cube the readings of v and w (not
+# printed in the paper) must be the printed u-formula with the axes exchanged
+
+def _periodic_raw(n, rng):
+    """A random field on the padded (n+2)^3 array whose ghosts hold the
+    periodic images (index 0 = n, n+1 = 1 on every axis)."""
+    a = rng.standard_normal((n, n, n))
+    idx = (np.arange(n + 2) - 1) % n
+    return a[np.ix_(idx, idx, idx)]
+
+
+@pytest.mark.parametrize("sgs", [False, True])
+@pytest.mark.parametrize("swap", ["xy", "xz"])
+def test_tendency_axis_exchange(swap, sgs):
+    """Exchanging two axes of the flow (velocity components and coordinates)
+    exchanges the corresponding tendencies: pins the v and w advection,
+    diffusion and SGS readings against the printed u formula."""
+    n = 6
+    per = (scene.BC_PERIODIC,) * 3
+    # unequal spacings, exchanged with the axes (a dx / dy / dz mix-up in a
+    # reading breaks the symmetry); dz uniform so that z can trade with x
+    sp = {"xy": ((3.0, 5.0, 4.0), (5.0, 3.0, 4.0)), "xz": ((3.0, 4.0, 5.0), (5.0, 4.0, 3.0))}[swap]
+    scenes = [scene.box_scene(n, n, n, dx=a, dy=b, dz=np.full(n, c), bc=per, nu=NU) for a, b, c in sp]
+    rng = np.random.default_rng(12)
+    u, v, w, nut = (_periodic_raw(n, rng) for _ in range(4))
+    nut = np.abs(nut)
+    if swap == "xy":
+        t = lambda a: np.transpose(a, (0, 2, 1))        # [k, j, i] -> [k, i, j]
+        u2, v2, w2 = t(v), t(u), t(w)
+    else:
+        t = lambda a: np.transpose(a, (2, 1, 0))        # [k, j, i] -> [i, j, k]
+        u2, v2, w2 = t(w), t(v), t(u)
+
+    def tend(sc, uu, vv, ww, nn):
+        o = Oracle(sc)
+        o.raw(A_U)[...] = uu
+        o.raw(A_V)[...] = vv
+        o.raw(A_W)[...] = ww
+        o.raw(A_NUT)[...] = nn
+        o.tendency(with_sgs=sgs)
+        s = slice(1, n + 1)
+        return [o.raw(a)[s, s, s].copy() for a in (A_FU, A_FV, A_FW)]
+
+    fu, fv, fw = tend(scenes[0], u, v, w, nut)
+    gu, gv, gw = tend(scenes[1], u2, v2, w2, t(nut))
+    scale = max(np.abs(f).max() for f in (fu, fv, fw))
+    if swap == "xy":
+        pairs = ((gu, t(fv)), (gv, t(fu)), (gw, t(fw)))
+    else:
+        pairs = ((gu, t(fw)), (gv, t(fv)), (gw, t(fu)))
+    for got, want in pairs:
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * scale)
