@@ -406,3 +406,56 @@ def test_tendency_axis_exchange(swap, sgs):
         pairs = ((gu, t(fw)), (gv, t(fv)), (gw, t(fu)))
     for got, want in pairs:
         np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * scale)
+
+
+# ----------------------------------------------------------------------------
+# wall ghosts (bondv1 reading): no-slip at the ground face, free slip at the
+# lid and at the side walls, each against the closed form it makes exact
+
+def _wall_scene():
+    # x periodic so that the inflow plays no part; y free-slip walls; z ground + lid
+    return scene.box_scene(6, 5, 7, dz=np.full(7, 3.0), nu=NU,
+                           bc=(scene.BC_PERIODIC, scene.BC_FREESLIP, scene.BC_WALL))
+
+
+def _filled_tendency(sc, fu, fv, fw):
+    o = Oracle(sc)
+    set_field(o, A_U, fu, sc, "u")
+    set_field(o, A_V, fv, sc, "v")
+    set_field(o, A_W, fw, sc, "w")
+    o.bc_fill()
+    o.tendency(with_sgs=False)
+    return o
+
+
+def test_ground_no_slip_at_the_face():
+    """u = a z vanishes on the ground face: with the ground ghost = -u(1) the
+    linear profile continues through the face and its discrete diffusion is 0
+    in the first cell too (a no-slip point at the first centre would not give
+    this)."""
+    sc = _wall_scene()
+    a = 0.13
+    o = _filled_tendency(sc, lambda X, Y, Z: a * Z, zero, zero)
+    fu = o.raw(A_FU)[1:sc.nz, 1:sc.ny + 1, 1:sc.nx + 1]        # the lid cell feels the free-slip lid
+    np.testing.assert_allclose(fu, 0.0, atol=1e-14)
+
+
+def test_lid_free_slip_mirror():
+    """u = b (z - H)^2 is symmetric about the lid face z = H: the free-slip
+    mirror ghost makes the discrete diffusion exact (2 nu b) up to the lid cell."""
+    sc = _wall_scene()
+    H = float(np.sum(sc.dz))
+    b = 0.021
+    o = _filled_tendency(sc, lambda X, Y, Z: b * (Z - H) ** 2, zero, zero)
+    fu = o.raw(A_FU)[2:sc.nz + 1, 1:sc.ny + 1, 1:sc.nx + 1]     # cell 1 feels the no-slip ground
+    np.testing.assert_allclose(fu, 2 * NU * b, rtol=1e-12)
+
+
+def test_side_wall_free_slip_mirror():
+    """u = b y^2 is symmetric about the side wall y = 0: the free-slip mirror
+    ghost makes the discrete y-diffusion exact (2 nu b) in the first row."""
+    sc = _wall_scene()
+    b = 0.017
+    o = _filled_tendency(sc, lambda X, Y, Z: b * Y * Y, zero, zero)
+    fu = o.raw(A_FU)[2:sc.nz + 1, 1:3, 1:sc.nx + 1]             # cell k = 1 feels the no-slip ground
+    np.testing.assert_allclose(fu, 2 * NU * b, rtol=1e-12)
