@@ -6,7 +6,7 @@
  * of the benchmark may load it.  It shares no code, header, table or constant
  * generator with the CUDA path.
  *
- * Plain, slow, sequential loops in the order of the paper's LES routines
+ * Plain, slow loops in the order of the paper's LES routines
  * (Sec. 2.1 "LES Code Structure -- Functional"):
  *   bondv1 (boundary conditions), les (Smagorinsky eddy viscosity),
  *   velfg (advection + diffusion "body force", Sec. 2.5 "Pre-computing
@@ -28,11 +28,21 @@
  * out in full in the comment of each routine.  Parity of those readings is
  * pinned only by the invariants and closed forms in the test-suite
  * (polynomial exactness, Taylor-Green decay, symmetry, dissipation sign).
+ *
+ * Threads.  The same source builds twice: sequential, and with -fopenmp for
+ * timing the CPU baseline on every host core.  Only loops over k whose
+ * iterations write disjoint cells carry a parallel-for (the cells of one SOR
+ * colour read only the other colour, so a half-sweep is order-independent);
+ * every FP64 sum is formed per k-plane into its own slot and the planes are
+ * added in k order afterwards, so both builds give bit-identical results.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define BC_INOUT 0
 #define BC_FREESLIP 1
@@ -70,6 +80,7 @@ typedef struct {
      * mesoscale model, Sec. 4): n profiles U_m(z_k) at times t_m */
     int nseries;
     double *series_t, *series_p;   /* [n], [n][nz+2] */
+    double *plane_a, *plane_b;     /* [nz+2] per-plane partial sums (added in k order) */
 } orc_t;
 
 #define IX(o, i, j, k) (((size_t)(k) * (o)->sy + (size_t)(j)) * (o)->sx + (size_t)(i))
@@ -270,6 +281,7 @@ static double s23_edge(const orc_t* o, int i, int j, int k) {  /* edge (y_j face
 
 static void les_nut(orc_t* o) {
     const orc_params* P = &o->P;
+#pragma omp parallel for schedule(static)
     for (int k = 1; k <= P->nz; ++k)
         for (int j = 1; j <= P->ny; ++j)
             for (int i = 1; i <= P->nx; ++i) {
@@ -455,6 +467,7 @@ static void momentum(orc_t* o) {
     memcpy(o->us, o->u, n * sizeof(double));
     memcpy(o->vs, o->v, n * sizeof(double));
     memcpy(o->ws, o->w, n * sizeof(double));
+#pragma omp parallel for schedule(static)
     for (int k = 1; k <= nz; ++k)
         for (int j = 1; j <= ny; ++j)
             for (int i = 1; i <= face_hi(P->bc_x, nx); ++i) {
@@ -464,6 +477,7 @@ static void momentum(orc_t* o) {
                 o->fu[c] = F;
                 o->us[c] = open_x(o, i, j, k) ? o->u[c] + P->dt * Fh : 0.0;
             }
+#pragma omp parallel for schedule(static)
     for (int k = 1; k <= nz; ++k)
         for (int j = 1; j <= face_hi(P->bc_y, ny); ++j)
             for (int i = 1; i <= nx; ++i) {
@@ -473,6 +487,7 @@ static void momentum(orc_t* o) {
                 o->fv[c] = F;
                 o->vs[c] = open_y(o, i, j, k) ? o->v[c] + P->dt * Fh : 0.0;
             }
+#pragma omp parallel for schedule(static)
     for (int k = 1; k <= face_hi(P->bc_z, nz); ++k)
         for (int j = 1; j <= ny; ++j)
             for (int i = 1; i <= nx; ++i) {
@@ -566,8 +581,9 @@ static double nb_sum(const orc_t* o, const double* p, int i, int j, int k, const
 
 static void make_rhs(orc_t* o) {
     const orc_params* P = &o->P;
-    double num = 0.0, den = 0.0;
-    for (int k = 1; k <= P->nz; ++k)
+#pragma omp parallel for schedule(static)
+    for (int k = 1; k <= P->nz; ++k) {
+        double num = 0.0, den = 0.0;
         for (int j = 1; j <= P->ny; ++j)
             for (int i = 1; i <= P->nx; ++i) {
                 size_t c = IX(o, i, j, k);
@@ -579,7 +595,16 @@ static void make_rhs(orc_t* o) {
                 num += o->dz[k] * o->rhs[c];
                 den += o->dz[k];
             }
+        o->plane_a[k] = num;
+        o->plane_b[k] = den;
+    }
+    double num = 0.0, den = 0.0;
+    for (int k = 1; k <= P->nz; ++k) {
+        num += o->plane_a[k];
+        den += o->plane_b[k];
+    }
     double mean = den > 0.0 ? num / den : 0.0;
+#pragma omp parallel for schedule(static)
     for (int k = 1; k <= P->nz; ++k)
         for (int j = 1; j <= P->ny; ++j)
             for (int i = 1; i <= P->nx; ++i)
@@ -591,6 +616,7 @@ static void make_rhs(orc_t* o) {
  * (cells with i+j+k odd, from i = 1 + mod(k+j+nrd, 2)), then nrd = 1.       */
 static void sor_half(orc_t* o, int nrd) {
     const orc_params* P = &o->P;
+#pragma omp parallel for schedule(static)
     for (int k = 1; k <= P->nz; ++k)
         for (int j = 1; j <= P->ny; ++j)
             for (int i = 1 + (k + j + nrd) % 2; i <= P->nx; i += 2) {
@@ -616,6 +642,7 @@ static void twin_half(orc_t* o, int nrd, double omega) {
     const orc_params* P = &o->P;
     const double* src = nrd == 0 ? o->p : o->p_twin;
     double* dst = nrd == 0 ? o->p_twin : o->p;
+#pragma omp parallel for schedule(static)
     for (int k = 1; k <= P->nz; ++k)
         for (int j = 1; j <= P->ny; ++j)
             for (int i = 1; i <= P->nx; ++i) {
@@ -638,8 +665,9 @@ static double apply_A_cell(const orc_t* o, const double* p, int i, int j, int k)
 /* relative residual ||rhs - A p||_2 / ||rhs||_2 over the fluid cells (FP64) */
 static double residual(orc_t* o) {
     const orc_params* P = &o->P;
-    double rn = 0.0, bn = 0.0;
-    for (int k = 1; k <= P->nz; ++k)
+#pragma omp parallel for schedule(static)
+    for (int k = 1; k <= P->nz; ++k) {
+        double rn = 0.0, bn = 0.0;
         for (int j = 1; j <= P->ny; ++j)
             for (int i = 1; i <= P->nx; ++i) {
                 coef_t c;
@@ -649,6 +677,14 @@ static double residual(orc_t* o) {
                 rn += r * r;
                 bn += o->rhs[ix] * o->rhs[ix];
             }
+        o->plane_a[k] = rn;
+        o->plane_b[k] = bn;
+    }
+    double rn = 0.0, bn = 0.0;
+    for (int k = 1; k <= P->nz; ++k) {
+        rn += o->plane_a[k];
+        bn += o->plane_b[k];
+    }
     o->st.rhs_norm = sqrt(bn);
     if (bn == 0.0) return sqrt(rn);
     return sqrt(rn / bn);
@@ -656,15 +692,25 @@ static double residual(orc_t* o) {
 
 static void gauge(orc_t* o) {
     const orc_params* P = &o->P;
-    double num = 0.0, den = 0.0;
-    for (int k = 1; k <= P->nz; ++k)
+#pragma omp parallel for schedule(static)
+    for (int k = 1; k <= P->nz; ++k) {
+        double num = 0.0, den = 0.0;
         for (int j = 1; j <= P->ny; ++j)
             for (int i = 1; i <= P->nx; ++i)
                 if (is_fluid(o, i, j, k)) {
                     num += o->dz[k] * o->p[IX(o, i, j, k)];
                     den += o->dz[k];
                 }
+        o->plane_a[k] = num;
+        o->plane_b[k] = den;
+    }
+    double num = 0.0, den = 0.0;
+    for (int k = 1; k <= P->nz; ++k) {
+        num += o->plane_a[k];
+        den += o->plane_b[k];
+    }
     double m = den > 0.0 ? num / den : 0.0;
+#pragma omp parallel for schedule(static)
     for (int k = 1; k <= P->nz; ++k)
         for (int j = 1; j <= P->ny; ++j)
             for (int i = 1; i <= P->nx; ++i)
@@ -709,6 +755,7 @@ static void project(orc_t* o) {
     memcpy(o->u, o->us, n * sizeof(double));
     memcpy(o->v, o->vs, n * sizeof(double));
     memcpy(o->w, o->ws, n * sizeof(double));
+#pragma omp parallel for schedule(static)
     for (int k = 1; k <= nz; ++k)
         for (int j = 1; j <= ny; ++j)
             for (int i = 1; i <= face_hi(P->bc_x, nx); ++i) {
@@ -718,6 +765,7 @@ static void project(orc_t* o) {
                               ? o->us[c] - P->dt * (o->p[IX(o, ie, j, k)] - o->p[c]) / P->dx
                               : 0.0;
             }
+#pragma omp parallel for schedule(static)
     for (int k = 1; k <= nz; ++k)
         for (int j = 1; j <= face_hi(P->bc_y, ny); ++j)
             for (int i = 1; i <= nx; ++i) {
@@ -727,6 +775,7 @@ static void project(orc_t* o) {
                               ? o->vs[c] - P->dt * (o->p[IX(o, i, jn, k)] - o->p[c]) / P->dy
                               : 0.0;
             }
+#pragma omp parallel for schedule(static)
     for (int k = 1; k <= face_hi(P->bc_z, nz); ++k)
         for (int j = 1; j <= ny; ++j)
             for (int i = 1; i <= nx; ++i) {
@@ -762,6 +811,8 @@ orc_t* orc_create(const orc_params* P, const double* dz, const unsigned char* so
     o->dz = (double*)calloc(o->sz, sizeof(double));
     o->dzs = (double*)calloc(o->sz, sizeof(double));
     o->inflow = (double*)calloc(o->sz, sizeof(double));
+    o->plane_a = (double*)calloc(o->sz, sizeof(double));
+    o->plane_b = (double*)calloc(o->sz, sizeof(double));
     for (int k = 1; k <= P->nz; ++k) {
         o->dz[k] = dz[k - 1];
         o->inflow[k] = inflow[k - 1];
@@ -791,7 +842,8 @@ orc_t* orc_create(const orc_params* P, const double* dz, const unsigned char* so
 void orc_destroy(orc_t* o) {
     if (!o) return;
     double* arrs[] = {o->u, o->v, o->w, o->p, o->rhs, o->nut, o->us, o->vs, o->ws,
-                      o->fu, o->fv, o->fw, o->dz, o->dzs, o->inflow, o->p_twin};
+                      o->fu, o->fv, o->fw, o->dz, o->dzs, o->inflow, o->p_twin,
+                      o->plane_a, o->plane_b};
     for (size_t a = 0; a < sizeof(arrs) / sizeof(arrs[0]); ++a) free(arrs[a]);
     free(o->series_t);
     free(o->series_p);
@@ -1012,6 +1064,22 @@ void orc_step(orc_t* o, int nsteps) {
         project(o);
         o->step += 1;
     }
+}
+
+/* threads of the OpenMP build (the sequential build always reports 1) */
+int orc_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
 }
 
 /* raw inflow noise, for pinning the generator to its published definition */

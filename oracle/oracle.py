@@ -55,26 +55,39 @@ class OrcStats(ctypes.Structure):
                 ("q_out", ctypes.c_double)]
 
 
+LIB_OMP = os.path.join(LIBDIR, "liblesoracle_omp.so")
+
+
+def _compile(out: str, extra) -> None:
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared"] + list(extra) + ["-o", tmp, SRC, "-lm"]
+    try:
+        subprocess.check_call(cmd)
+        os.replace(tmp, out)
+    finally:
+        if os.path.exists(tmp):
+            os.remove(tmp)
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, no fast-math, no FMA contraction)."""
+    """Compile the oracle with gcc (plain -O2, no fast-math, no FMA contraction),
+    once sequential and once with -fopenmp (same source, bit-identical results;
+    the threaded build times the CPU baseline on every host core)."""
     os.makedirs(LIBDIR, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
-        return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, SRC, "-lm"]
-    subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+    for out, extra in ((LIB, []), (LIB_OMP, ["-fopenmp"])):
+        if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(SRC):
+            _compile(out, extra)
     return LIB
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
+def lib(omp: bool = False):
+    """The sequential oracle library, or the OpenMP build with omp=True."""
+    if omp not in _libs:
         build()
-        L = ctypes.CDLL(LIB)
+        L = ctypes.CDLL(LIB_OMP if omp else LIB)
         vp = ctypes.c_void_p
         dp = ctypes.POINTER(ctypes.c_double)
         L.orc_create.restype = vp
@@ -110,8 +123,21 @@ def lib():
         L.orc_set_inflow_series.restype = ctypes.c_int
         L.orc_set_inflow_series.argtypes = [vp, ctypes.c_int, dp, dp]
         L.orc_inflow_profile.argtypes = [vp, dp]
-        _lib = L
-    return _lib
+        L.orc_threads.restype = ctypes.c_int
+        L.orc_threads.argtypes = []
+        L.orc_set_threads.argtypes = [ctypes.c_int]
+        _libs[omp] = L
+    return _libs[omp]
+
+
+def threads(omp: bool = True) -> int:
+    """Threads the oracle build uses (1 for the sequential build)."""
+    return lib(omp).orc_threads()
+
+
+def set_threads(n: int) -> None:
+    """Thread count of the OpenMP build."""
+    lib(True).orc_set_threads(int(n))
 
 
 def _dp(a: np.ndarray):
@@ -121,8 +147,8 @@ def _dp(a: np.ndarray):
 class Oracle:
     """One FP64 LES domain on the CPU."""
 
-    def __init__(self, sc, **override):
-        L = lib()
+    def __init__(self, sc, omp=False, **override):
+        self.L = L = lib(omp)
         prm = sc.params()
         prm.update(override)
         self.nx, self.ny, self.nz = prm["nx"], prm["ny"], prm["nz"]
@@ -146,7 +172,7 @@ class Oracle:
     def __del__(self):
         h = getattr(self, "h", None)
         if h:
-            lib().orc_destroy(h)
+            self.L.orc_destroy(h)
             self.h = None
 
     # shapes in I/O layout
@@ -162,20 +188,20 @@ class Oracle:
 
     def get(self, which) -> np.ndarray:
         out = np.empty(self.shape(which), dtype=np.float64)
-        lib().orc_get(self.h, which, _dp(out))
+        self.L.orc_get(self.h, which, _dp(out))
         return out
 
     def set(self, which, a):
         a = np.ascontiguousarray(a, dtype=np.float64)
         assert a.shape == self.shape(which), (a.shape, self.shape(which))
-        lib().orc_set(self.h, which, _dp(a))
+        self.L.orc_set(self.h, which, _dp(a))
 
     def raw(self, which) -> np.ndarray:
         """Writable view of a padded array, shape (nz+2, ny+2, nx+2), index [k, j, i]."""
         d = (ctypes.c_int32 * 3)()
-        lib().orc_dims(self.h, d)
+        self.L.orc_dims(self.h, d)
         sx, sy, sz = d[0], d[1], d[2]
-        ptr = lib().orc_raw(self.h, which)
+        ptr = self.L.orc_raw(self.h, which)
         return np.ctypeslib.as_array(ptr, shape=(sz, sy, sx))
 
     def set_fields(self, u, v, w, p):
@@ -189,68 +215,68 @@ class Oracle:
 
     def stats(self) -> dict:
         s = OrcStats()
-        lib().orc_stats_get(self.h, ctypes.byref(s))
+        self.L.orc_stats_get(self.h, ctypes.byref(s))
         return {f: getattr(s, f) for f, _ in OrcStats._fields_}
 
     @property
     def step_index(self) -> int:
-        return lib().orc_step_index(self.h)
+        return self.L.orc_step_index(self.h)
 
     @step_index.setter
     def step_index(self, s):
-        lib().orc_set_step_index(self.h, s)
+        self.L.orc_set_step_index(self.h, s)
 
     def step(self, n=1):
-        lib().orc_step(self.h, n)
+        self.L.orc_step(self.h, n)
 
     # phases
-    def bc_fill(self): lib().orc_bc_fill(self.h)
-    def les_nut(self): lib().orc_les_nut(self.h)
-    def momentum(self): lib().orc_momentum(self.h)
-    def outflow_fix(self): lib().orc_outflow_fix(self.h)
-    def make_rhs(self): lib().orc_make_rhs(self.h)
-    def sor_half(self, nrd): lib().orc_sor_half(self.h, nrd)
-    def sor_sweeps(self, n): lib().orc_sor_sweeps(self.h, n)
+    def bc_fill(self): self.L.orc_bc_fill(self.h)
+    def les_nut(self): self.L.orc_les_nut(self.h)
+    def momentum(self): self.L.orc_momentum(self.h)
+    def outflow_fix(self): self.L.orc_outflow_fix(self.h)
+    def make_rhs(self): self.L.orc_make_rhs(self.h)
+    def sor_half(self, nrd): self.L.orc_sor_half(self.h, nrd)
+    def sor_sweeps(self, n): self.L.orc_sor_sweeps(self.h, n)
     def twin_sweeps(self, n, omega):
         """n sweeps of the twinned double buffer (Sec. 2.6) with relaxation omega."""
-        if lib().orc_twin_sweeps(self.h, n, omega) != 0:
+        if self.L.orc_twin_sweeps(self.h, n, omega) != 0:
             raise MemoryError("orc_twin_sweeps")
-    def residual(self) -> float: return lib().orc_residual(self.h)
-    def sor_solve(self): lib().orc_sor_solve(self.h)
-    def gauge(self): lib().orc_gauge(self.h)
-    def project(self): lib().orc_project(self.h)
-    def tendency(self, with_sgs=True): lib().orc_tendency(self.h, 1 if with_sgs else 0)
+    def residual(self) -> float: return self.L.orc_residual(self.h)
+    def sor_solve(self): self.L.orc_sor_solve(self.h)
+    def gauge(self): self.L.orc_gauge(self.h)
+    def project(self): self.L.orc_project(self.h)
+    def tendency(self, with_sgs=True): self.L.orc_tendency(self.h, 1 if with_sgs else 0)
 
     def set_inflow_series(self, times, profiles):
         """Inflow profiles [n][nz] at increasing times [n] (n = 0: the fixed profile)."""
         self._st = np.ascontiguousarray(times, dtype=np.float64)
         self._sp = np.ascontiguousarray(profiles, dtype=np.float64)
         n = len(self._st)
-        if lib().orc_set_inflow_series(self.h, n, _dp(self._st) if n else None, _dp(self._sp) if n else None):
+        if self.L.orc_set_inflow_series(self.h, n, _dp(self._st) if n else None, _dp(self._sp) if n else None):
             raise ValueError("inflow series: times must increase")
 
     def inflow_profile(self) -> np.ndarray:
         out = np.empty(self.nz)
-        lib().orc_inflow_profile(self.h, _dp(out))
+        self.L.orc_inflow_profile(self.h, _dp(out))
         return out
 
     def apply_A(self, p) -> np.ndarray:
         p = np.ascontiguousarray(p, dtype=np.float64)
         out = np.empty_like(p)
-        lib().orc_apply_A(self.h, _dp(p), _dp(out))
+        self.L.orc_apply_A(self.h, _dp(p), _dp(out))
         return out
 
     def divergence(self) -> np.ndarray:
         out = np.empty((self.nz, self.ny, self.nx))
-        lib().orc_divergence(self.h, _dp(out))
+        self.L.orc_divergence(self.h, _dp(out))
         return out
 
     def pressure_solve(self, rhs=None):
         if rhs is None:
-            lib().orc_pressure_solve(self.h, None)
+            self.L.orc_pressure_solve(self.h, None)
         else:
             r = np.ascontiguousarray(rhs, dtype=np.float64)
-            lib().orc_pressure_solve(self.h, _dp(r))
+            self.L.orc_pressure_solve(self.h, _dp(r))
 
 
 def gauss(seed: int, ctr: int) -> float:
