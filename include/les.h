@@ -176,6 +176,11 @@ int les_pressure_solve(les_handle h, const void* rhs, les_stats_t* stats);
 #define LES_AUX_R0 8         /* initial residual rhs - mean - A p_prev of the last solve (recording on) */
 #define LES_AUX_DELTA 9      /* correction p_solved - p_prev of the last solve, before the gauge (recording on) */
 #define LES_AUX_MASK 10      /* 1 on Poisson unknowns (fluid cells with an open face), else 0 */
+#define LES_AUX_NET_IN 11    /* residual (nz, ny, nx) the learned start-of-solve correction of the last
+                                solve that ran one took as the network input (recording on; FP32 grids) */
+#define LES_AUX_NET_Q 12     /* that correction's network prediction q (nz, ny, nx), 0 off the unknowns */
+/* LES_AUX_R0 / DELTA / NET_IN / NET_Q need recording on (LES_EINVAL otherwise)
+ * and a solve that recorded them (LES_ESTATE otherwise). */
 int les_get_aux(les_handle h, int32_t which, void* out);
 
 /* les_set_record: keep the initial residual and the total correction of every
@@ -242,13 +247,16 @@ int les_set_graph(les_handle h, int32_t enable);
  * ignored); tiles 17-24 are 28 x ty x tz blocks loaded by the tensor-memory
  * accelerator (FP32 grids only, else LES_EINVAL), 21-24 in persistent CTAs
  * that prefetch their next block (FP32 grids without periodic axes only,
- * else LES_EINVAL).
+ * else LES_EINVAL); tiles 25-28 are 30 x ty columns that march through kc
+ * planes per CTA with a pipeline of per-plane TMA copies (FP32 grids, any
+ * boundary conditions; kc <= 0 picks the chunk that gives at least two CTAs
+ * per SM).
  * Every choice computes the same iterate.
  * les_autotune_sor times each tile shape with a few k-chunk lengths on this
  * handle's grid (sweeps per candidate), keeps the fastest and reports it;
  * the field state is saved and restored around the trial sweeps.
  */
-#define LES_SOR_NTILES 25
+#define LES_SOR_NTILES 29
 int les_set_sor_config(les_handle h, int32_t tile, int32_t kc);
 int les_get_sor_config(les_handle h, int32_t* tile, int32_t* kc);
 int les_sor_tile(int32_t tile, int32_t* tx, int32_t* ty, int32_t* tz);
@@ -310,17 +318,23 @@ int les_sor_compare(les_handle h, int32_t variant, double omega, int32_t sweeps,
  *            open face, A the operator of les_pressure_solve.
  *   stream   cudaStream_t the work is ordered on (NULL = legacy default).
  * The caller owns every buffer.  The only scratch is a fixed device array of
- * about 64 KB in this library (4096 FP64 partial-sum pairs and a counter),
- * present on every GPU that loads the library until the process exits; the
- * entry point never calls cudaMalloc, cudaFree or any allocating routine.
- * On its first call on a device (with that device current) it looks up the
- * array's device address once; make that first call before any stream
- * capture.  Each call clears the counter before use.  All calls share the
- * array, so calls whose kernels overlap on the GPU (different streams, or
- * different host threads) race and give wrong norms: order them.
- * Grids above LES_NOALLOC_MAX_CELLS cells (the 32-bit index limit) and bad
- * arguments give LES_EINVAL; CUDA failures LES_ECUDA.  Asynchronous: read
- * d_out after synchronising the stream.
+ * about 64 KB in this library (4096 FP64 partial-sum pairs and a counter);
+ * the entry point never calls cudaMalloc, cudaFree or any allocating routine.
+ * The array is placed on a device when the library's module loads there:
+ * with CUDA's default lazy module loading that is the first call of this
+ * entry point on the device, so callers on a fixed device-memory budget make
+ * one call at start-up (or set CUDA_MODULE_LOADING=EAGER); it then stays
+ * resident on that GPU until the process exits.  On its first call on a
+ * device (with that device current), and again whenever the device's current
+ * context has changed (after a device reset, say), it looks up the array's
+ * device address; make that first call before any stream capture.  Each call
+ * clears the counter before use.  All calls share the array, so calls whose
+ * kernels overlap on the GPU (different streams, or different host threads)
+ * race and give wrong norms: order them.  Grids above LES_NOALLOC_MAX_CELLS
+ * cells (a chosen bound; grids of any size below it run with at most 4096
+ * blocks striding over the cells) and bad arguments give LES_EINVAL; CUDA
+ * failures LES_ECUDA.  Asynchronous: read d_out after synchronising the
+ * stream.
  */
 #define LES_NOALLOC_MAX_CELLS 2147483647LL
 int les_residual_noalloc(const les_grid_t* grid, const void* d_p, const void* d_rhs, const uint8_t* d_solid,

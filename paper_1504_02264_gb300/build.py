@@ -61,21 +61,25 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(" ".join(cmd))
         procs.append((subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT), src))
         objs.append(obj)
-    failed = []
-    for p, src in procs:
-        out, _ = p.communicate()
-        if p.returncode != 0:
-            failed.append((src, out.decode(errors="replace")))
-        elif verbose and out:
-            print(out.decode(errors="replace"))
-    if failed:
-        msg = "\n".join(f"--- {s}\n{o}" for s, o in failed)
-        raise RuntimeError("nvcc failed:\n" + msg)
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call([cc] + ARCH + ["-shared", "-o", tmp] + objs)
-    os.replace(tmp, LIB)
-    for o in objs:
-        os.remove(o)
+    try:
+        failed = []
+        for p, src in procs:
+            out, _ = p.communicate()
+            if p.returncode != 0:
+                failed.append((src, out.decode(errors="replace")))
+            elif verbose and out:
+                print(out.decode(errors="replace"))
+        if failed:
+            msg = "\n".join(f"--- {s}\n{o}" for s, o in failed)
+            raise RuntimeError("nvcc failed:\n" + msg)
+        subprocess.check_call([cc] + ARCH + ["-shared", "-o", tmp] + objs)
+        os.replace(tmp, LIB)
+    finally:
+        # this build's objects and partial library go whether it succeeded or not
+        for f in objs + [tmp]:
+            if os.path.exists(f):
+                os.remove(f)
     return LIB
 
 

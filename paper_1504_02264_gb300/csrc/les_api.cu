@@ -152,6 +152,9 @@ struct les_s {
     double* rec_p0 = nullptr;             // pressure before the last solve
     void* rec_r0 = nullptr;               // initial residual of the last solve
     void* rec_delta = nullptr;            // correction applied by the last solve
+    void* rec_netin = nullptr;            // residual the start-of-solve network correction saw
+    float* rec_netq = nullptr;            // its prediction q (dense (nz, ny, nx))
+    bool net_taken = false;               // a start-of-solve prediction has been recorded
     // phase timing
     bool timing = false;
     cudaEvent_t ev[8] = {};
@@ -312,7 +315,7 @@ int run_sweeps(les_s* h, const Geo<T>& g, int n, int zero, long long& launched, 
         const int in = h->dcur, out = 1 - h->dcur;
         if constexpr (std::is_same<T, float>::value) {
             if (h->sor.tile >= kFirstTmaTile) {
-                launched += launch_sor_tma(g, h->tma, h->cn1tab, h->sor.tile - kFirstTmaTile, in,
+                launched += launch_sor_tma(g, h->tma, h->cn1tab, h->sor.tile - kFirstTmaTile, h->sor.kc, in,
                                            (float*)h->dl[out], s == 0 ? zero : 0, h->sc, st);
                 h->dcur = out;
                 continue;
@@ -359,8 +362,14 @@ int predict(les_s* h, const float* r, cudaStream_t st, const int* gate) {
 
 template <typename T>
 int net_correct(les_s* h, const Geo<T>& g, cudaStream_t st) {
+    if (h->record) CK(cudaMemcpyAsync(h->rec_netin, h->rr, h->n * h->es, cudaMemcpyDeviceToDevice, st));
     int rc = predict(h, (const float*)h->rr, st, nullptr);
     if (rc) return rc;
+    if (h->record) {
+        CK(cudaMemcpyAsync(h->rec_netq, h->pred, (size_t)h->g.nx * h->g.ny * h->g.nz * sizeof(float),
+                           cudaMemcpyDeviceToDevice, st));
+        h->net_taken = true;
+    }
     h->launches += launch_warm<T>(g, (const T*)h->rr, h->pred, h->ph[h->cur], (T*)nullptr, h->warm_scal + 1,
                                   reducer(h), st);
     h->launches += launch_residual64<T>(g, h->ph[h->cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h),
@@ -541,7 +550,8 @@ int sor_solve(les_s* h) {
 bool tile_available(const les_s* h, int t) {
     if (t < 0 || t >= kNumSorTiles + kNumTmaTiles) return false;
     if (t < kNumSorTiles) return true;
-    return h->tma_ok && (t < kNumSorTiles + kNumTmaBlockTiles || h->pipe_ok);
+    const int c = t - kNumSorTiles;
+    return h->tma_ok && (c < kNumTmaBlockTiles || c >= kFirstMarchCfg || h->pipe_ok);
 }
 
 // Time `sweeps` sweeps per candidate (tile shape x k-chunk) on the current
@@ -575,7 +585,9 @@ int autotune_impl(les_s* h, int sweeps, double* best_ms, int only_tile, int only
         for (int kc : kcs) {
             if (!tile_available(h, t)) continue;
             if (kc > h->g.nz) continue;
-            if ((t >= kNumSorTiles || kSorTiles[t].tz > 0) && kc != 0) continue;      // 3-D blocks ignore kc
+            const bool march = t >= kNumSorTiles + kFirstMarchCfg;       // k-marching TMA columns take kc
+            if (((t >= kNumSorTiles && !march) || (t < kNumSorTiles && kSorTiles[t].tz > 0)) && kc != 0)
+                continue;      // 3-D blocks ignore kc
             if (only_tile >= -1 && (t != only_tile || kc != only_kc)) continue;
             h->sor = SorCfg{t, kc};
             long long nl = 0;
@@ -1087,6 +1099,18 @@ int get_aux_impl(les_s* h, int which, void* out) {
                 return fail(h, LES_ESTATE, "the last solve recorded no pair (it ended before the record point)");
             src = which == LES_AUX_R0 ? h->rec_r0 : h->rec_delta;
             break;
+        case LES_AUX_NET_IN:
+        case LES_AUX_NET_Q:
+            if (!h->record) return fail(h, LES_EINVAL, "recording is off (les_set_record)");
+            if (!h->net_taken) return fail(h, LES_ESTATE, "no start-of-solve network prediction recorded yet");
+            if (which == LES_AUX_NET_Q) {
+                CK(cudaMemcpyAsync(out, h->rec_netq, (size_t)h->g.nx * h->g.ny * h->g.nz * sizeof(float),
+                                   cudaMemcpyDeviceToHost, h->stream));
+                CK(cudaStreamSynchronize(h->stream));
+                return LES_OK;
+            }
+            src = h->rec_netin;
+            break;
         case LES_AUX_MASK: {
             Geo<T> g = geo<T>(h);
             h->launches += launch_record<T>(g, nullptr, nullptr, (T*)h->tmp, 1, h->stream);
@@ -1462,9 +1486,11 @@ int les_get_sor_config(les_handle h, int32_t* tile, int32_t* kc) {
 
 int les_sor_tile(int32_t tile, int32_t* tx, int32_t* ty, int32_t* tz) {
     if (tile >= kNumSorTiles && tile < kNumSorTiles + kNumTmaTiles) {
-        if (tx) *tx = 28;
-        if (ty) *ty = kTmaCfg[tile - kNumSorTiles][0];
-        if (tz) *tz = kTmaCfg[tile - kNumSorTiles][1];
+        const int c = tile - kNumSorTiles;
+        const bool march = c >= kFirstMarchCfg;           // k-marching column: tz = 0
+        if (tx) *tx = march ? 30 : 28;
+        if (ty) *ty = kTmaCfg[c][0];
+        if (tz) *tz = march ? 0 : kTmaCfg[c][1];
         return LES_OK;
     }
     if (tile < 0 || tile >= kNumSorTiles) return fail(nullptr, LES_EINVAL, "tile %d out of range", tile);
@@ -1562,6 +1588,8 @@ int les_set_record(les_handle h, int32_t enable) {
         if (rc) return rc;
         if ((rc = dalloc(h, &h->rec_r0, h->n * h->es))) return rc;
         if ((rc = dalloc(h, &h->rec_delta, h->n * h->es))) return rc;
+        if ((rc = dalloc(h, &h->rec_netin, h->n * h->es))) return rc;
+        if ((rc = dalloc(h, (void**)&h->rec_netq, (size_t)h->g.nx * h->g.ny * h->g.nz * sizeof(float)))) return rc;
     }
     h->record = enable != 0;
     return LES_OK;

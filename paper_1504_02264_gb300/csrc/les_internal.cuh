@@ -235,11 +235,13 @@ template <typename T> cudaError_t sor_prepare();
 
 // TMA variants (les_sor_tma.cu), FP32; tile indices kFirstTmaTile ..
 // kFirstTmaTile + kNumTmaTiles - 1: the first kNumTmaBlockTiles are one CTA
-// per block (any boundary conditions), the rest persistent double-buffered
-// (no periodic axis)
+// per block (any boundary conditions), the next four persistent
+// double-buffered (no periodic axis), the last four k-marching columns with
+// a plane pipeline (any boundary conditions; kc = planes per chunk)
 constexpr int kFirstTmaTile = 17;
-constexpr int kNumTmaTiles = 8;
+constexpr int kNumTmaTiles = 12;
 constexpr int kNumTmaBlockTiles = 4;
+constexpr int kFirstMarchCfg = 8;
 extern const int kTmaCfg[kNumTmaTiles][3];
 struct TmaMaps {
     CUtensorMap d[2], r, f;
@@ -250,8 +252,8 @@ bool tma_supported(const Dom& d);
 bool pipe_supported(const Dom& d);
 cudaError_t tma_prepare();
 bool tma_encode(const Dom& d, float* dl0, float* dl1, float* rr, uint8_t* flags, TmaMaps* maps);
-int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, const float* cn1tab, int cfg, int in, float* dout,
-                   int zero, Scalars* sc, cudaStream_t s);
+int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, const float* cn1tab, int cfg, int kc, int in,
+                   float* dout, int zero, Scalars* sc, cudaStream_t s);
 int launch_cn1_table(const Geo<float>& g, float* tab, cudaStream_t s);
 template <typename T> int launch_diag_table(const Geo<T>& g, double* tab, cudaStream_t s);
 // comparison of SOR variants (les_sor_compare)

@@ -10,9 +10,13 @@
 // fixed file-scope device array below.  Nothing here calls cudaMalloc,
 // cudaFree or any allocating library routine.
 //
-// The fixed array is allocated by the CUDA runtime when the library's module
-// is loaded on a device and stays resident on every GPU that loads the
-// library until the process exits (about 64 KB per device).
+// The fixed array is placed on a device when the library's module is loaded
+// there.  With CUDA's default lazy module loading that happens at the first
+// les_residual_noalloc call on the device (inside cudaGetSymbolAddress), so
+// that first call is the one that can grow device memory: fixed-budget
+// callers make it at start-up (or set CUDA_MODULE_LOADING=EAGER, which loads
+// the module with the context).  From then on the array (about 64 KB) stays
+// resident on that GPU until the process exits.
 #include <mutex>
 
 #include "../../include/les.h"
@@ -28,8 +32,28 @@ constexpr int kNaMaxDevices = 64;
 // [0]: completion counter (as unsigned), [1 .. 2*kNaBlocks]: partial sums
 static __device__ __align__(256) double g_na_scratch[1 + 2 * kNaBlocks];
 
+// per device: the array's address and the context it was looked up in (a
+// device reset or a released primary context loads the module again, maybe
+// elsewhere; a different current context means the address is looked up again)
 void* g_na_ptr[kNaMaxDevices] = {};
+CUcontext g_na_ctx[kNaMaxDevices] = {};
 std::mutex g_na_mutex;
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+
+CUcontext current_context() {
+    static CtxGetCurrentFn fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        fn = (CtxGetCurrentFn)f;
+    }
+    CUcontext c = nullptr;
+    return fn(&c) == CUDA_SUCCESS ? c : nullptr;
+}
 
 __device__ __forceinline__ bool na_fluid(const uint8_t* solid, const Dom& d, int i, int j, int k) {
     if (d.perx) i = i < 0 ? i + d.nx : (i >= d.nx ? i - d.nx : i);
@@ -150,17 +174,19 @@ extern "C" int les_residual_noalloc(const les_grid_t* grid, const void* d_p, con
     if (grid->bc_y != LES_BC_FREESLIP && grid->bc_y != LES_BC_PERIODIC) return LES_EINVAL;
     if (grid->bc_z != LES_BC_WALL && grid->bc_z != LES_BC_PERIODIC) return LES_EINVAL;
 
-    // once per device, with that device current: the device address of the
-    // fixed scratch array (its host-side name is only a stand-in)
+    // once per device (and again if the device's context changed), with that
+    // device current: the device address of the fixed scratch array (its
+    // host-side name is only a stand-in)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) return LES_ECUDA;
     void* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_na_mutex);
-        if (!g_na_ptr[dev]) {
+        if (!g_na_ptr[dev] || current_context() != g_na_ctx[dev]) {
             void* ptr = nullptr;
             if (cudaGetSymbolAddress(&ptr, g_na_scratch) != cudaSuccess || !ptr) return LES_ECUDA;
             g_na_ptr[dev] = ptr;
+            g_na_ctx[dev] = current_context();        // the lookup made the device's context current
         }
         scratch = g_na_ptr[dev];
     }

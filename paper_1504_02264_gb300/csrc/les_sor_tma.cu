@@ -398,6 +398,240 @@ k_sor_pipe(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUten
     }
 }
 
+// k-marching variant: a CTA owns a 30 x TY column of cells over a chunk of
+// planes [kb, ke) and walks it bottom to top with both colours in one pass
+// (a wavefront two planes deep): at step t it relaxes the red cells of plane
+// kb-1+t on the column plus a 1-cell ring, then the black cells of the plane
+// below on the column, and stores that plane, whose cells are then final.
+// Red at plane k reads black neighbours at k-1 and k+1 that are still the
+// old values (black k-1 is relaxed after red k), black at k-1 reads the new
+// red values of k-2, k-1 (ring included) and k: the iterate of the in-order
+// red-black sweep, bit for bit.  Each plane is one TMA copy of d (2-cell
+// ring), r and the flags (1-cell ring) into one of NS shared-memory slots on
+// its own mbarrier, issued NS - 2 planes ahead of use, so the copies of
+// later planes are in flight while the current ones are relaxed; only the
+// x-y ring is loaded twice (by the neighbouring columns), planes are read
+// once per chunk plus four halo planes.  One barrier per plane: red(k+1)
+// touches neither the cells black(k-1) writes nor those it reads.
+//
+// Lanes: 16 per row, two rows per warp (their colours differ, so the
+// stride-2 shared-memory accesses of the two rows fall on opposite bank
+// parities: no conflicts); a red row has 16 cells of the ring-extended
+// 32-wide row, a black row 15 of the 30 interior cells, and the lane that
+// relaxed the black cell of a pair stores the pair (8-byte aligned).
+//
+// Periodic axes: the plane of a copy wraps on a periodic z axis; columns
+// whose ring crosses a periodic x or y face overwrite the out-of-range cells
+// of each landed plane with plain loads of their images before relaxing.
+template <int TY, int NS>
+struct MarchTile {
+    static constexpr int TX = 30, W = 36, FW = 48;
+    static constexpr int DY = TY + 4, RY = TY + 2;
+    static constexpr int NW = RY / 2, NT = 32 * NW;       // one warp per red row pair
+    static constexpr uint32_t BYTES_D = W * DY * 4;
+    static constexpr uint32_t BYTES_R = W * RY * 4;
+    static constexpr uint32_t BYTES_F = FW * RY;
+    static constexpr uint32_t OFF_R = align_up(BYTES_D, 128);
+    static constexpr uint32_t OFF_F = OFF_R + align_up(BYTES_R, 128);
+    static constexpr uint32_t OFF_C = OFF_F + align_up(BYTES_F, 128);   // cn1 row [64], cT, cB
+    static constexpr uint32_t SLOT = align_up(OFF_C + 66 * 4, 128);
+    static constexpr uint32_t OFF_BAR = NS * SLOT;
+    static constexpr uint32_t SMEM = OFF_BAR + NS * 8;
+};
+
+template <int TY, int NS>
+__global__ void __launch_bounds__(MarchTile<TY, NS>::NT)
+k_sor_march(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtensorMap tr,
+            const __grid_constant__ CUtensorMap tf, Geo<float> g, const float* __restrict__ cn1tab,
+            const float* __restrict__ din, const float* __restrict__ rin, float* __restrict__ dout, int kc,
+            int zero_arg, Scalars* __restrict__ sc) {
+    using MT = MarchTile<TY, NS>;
+    constexpr int TX = MT::TX, W = MT::W, FW = MT::FW, DY = MT::DY, RY = MT::RY, NT = MT::NT;
+    extern __shared__ __align__(128) unsigned char sm[];
+    pdl_wait();
+    if (sc->done) return;
+    const Dom& d = g.d;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int half = lane >> 4, m = lane & 15;
+    const int i0 = 1 + blockIdx.x * TX, j0 = 1 + blockIdx.y * TY;
+    const int kb = 1 + blockIdx.z * kc, ke = min(kb + kc, d.nz + 1);
+    const int nq = ke - kb + 4;                    // planes kb-2 .. ke+1
+    const int xa = (i0 - 2 + OX) & ~3;             // padded column of the d and r boxes (16-byte aligned)
+    const int xf = (i0 - 2 + OX) & ~15;            // of the flag box
+    const int ox = OX - xa, oxf = OX - xf;         // shared column of cell i: i + ox (flags: i + oxf)
+    const bool zero_start = zero_arg == 1 || (zero_arg == 2 && sc->zflag);
+    const bool wrap_xy = (d.perx && (i0 - 2 < 1 || i0 + TX + 1 > d.nx)) || (d.pery && (j0 - 2 < 1 || j0 + TY + 1 > d.ny));
+    const uint32_t bar0 = smem_u32(sm + MT::OFF_BAR);
+    auto base = [&](int q) { return sm + (q % NS) * MT::SLOT; };
+    auto sD = [&](int q) { return reinterpret_cast<float(*)[W]>(base(q)); };
+    auto sR = [&](int q) { return reinterpret_cast<float(*)[W]>(base(q) + MT::OFF_R); };
+    auto sF = [&](int q) { return reinterpret_cast<uint8_t(*)[FW]>(base(q) + MT::OFF_F); };
+    auto sC = [&](int q) { return reinterpret_cast<float*>(base(q) + MT::OFF_C); };
+    // plane of slot index q, and the plane its copy reads (periodic z: the image)
+    auto src_plane = [&](int q) {
+        const int k = kb - 2 + q;
+        return (d.perz && (k < 1 || k > d.nz)) ? ((k - 1) % d.nz + d.nz) % d.nz + 1 : k;
+    };
+    auto issue = [&](int q) {       // one thread
+        const uint32_t bar = bar0 + 8 * (q % NS);
+        unsigned char* b = base(q);
+        const int zc = src_plane(q);
+        mbar_expect_tx(bar, MT::BYTES_R + MT::BYTES_F + (zero_start ? 0u : MT::BYTES_D));
+        if (!zero_start) tma_load_3d(smem_u32(b), &td, xa, j0 - 2, zc, bar);
+        tma_load_3d(smem_u32(b + MT::OFF_R), &tr, xa, j0 - 1, zc, bar);
+        tma_load_3d(smem_u32(b + MT::OFF_F), &tf, xf, j0 - 1, zc, bar);
+    };
+    // coefficients of slot q's plane (and zeros for d on a zero start); all threads
+    auto fill = [&](int q) {
+        const int k = coef_plane(d, kb - 2 + q);
+        float* c = sC(q);
+        for (int e = tid; e < 66; e += NT) c[e] = e < 64 ? cn1tab[k * 64 + e] : (e == 64 ? g.cT[k] : g.cB[k]);
+        if (zero_start) {
+            float* p = &sD(q)[0][0];
+            for (int e = tid; e < W * DY; e += NT) p[e] = 0.f;
+        }
+    };
+    // images of the ring cells across a periodic x or y face; all threads
+    auto fixup = [&](int q) {
+        const int k = src_plane(q);
+        float(*D)[W] = sD(q);
+        float(*R)[W] = sR(q);
+        uint8_t(*F)[FW] = sF(q);
+        long long s_;
+        if (!zero_start)
+            for (int e = tid; e < DY * (TX + 4); e += NT) {
+                const int y = e / (TX + 4), i = i0 - 2 + e % (TX + 4);
+                if (periodic_image(d, i, j0 - 2 + y, k, s_)) D[y][i + ox] = s_ >= 0 ? din[s_] : 0.f;
+            }
+        for (int e = tid; e < RY * (TX + 2); e += NT) {
+            const int y = e / (TX + 2), i = i0 - 1 + e % (TX + 2);
+            if (periodic_image(d, i, j0 - 1 + y, k, s_)) {
+                R[y][i + ox] = s_ >= 0 ? rin[s_] : 0.f;
+                F[y][i + oxf] = s_ >= 0 ? g.flags[s_] : (uint8_t)0;
+            }
+        }
+    };
+    auto wait = [&](int q) {
+        const uint32_t bar = bar0 + 8 * (q % NS), par = (uint32_t)(q / NS) & 1u;
+        bool ok;
+        const uint64_t t0 = global_ns();
+        while (!(ok = mbar_try_wait(bar, par)))
+            if (global_ns() - t0 > 1000000000ull) break;
+        return ok;
+    };
+    const int nfirst = nq < NS ? nq : NS;
+    if (tid == 0) {
+        for (int q = 0; q < NS; ++q) mbar_init(bar0 + 8 * q, 1);
+        mbar_fence_init();
+        for (int q = 0; q < nfirst; ++q) issue(q);
+    }
+    for (int q = 0; q < nfirst; ++q) fill(q);
+    __syncthreads();
+    int issued = nfirst, landed = 0;
+    const float omega = g.omega, cx = g.cx, cy = g.cy;
+    // the update of Sec. 2.6 at the shared cell p of plane k, with the same
+    // cell of planes k+1 (pt) and k-1 (pb)
+    auto relax = [&](float* p, const float* pt, const float* pb, const float* C, uint8_t f, float rhs) {
+        const float ct = C[64], cb = C[65];
+        const float cn1 = C[f & 63];
+        float s = 0.f;
+        if ((f & 63) == 63) {
+            s += cx * p[1];
+            s += cx * p[-1];
+            s += cy * p[W];
+            s += cy * p[-W];
+            s += ct * pt[0];
+            s += cb * pb[0];
+        } else {
+            const float ae = (f & F_E) ? cx : 0.f, aw = (f & F_W) ? cx : 0.f;
+            const float an = (f & F_N) ? cy : 0.f, as = (f & F_S) ? cy : 0.f;
+            const float at = (f & F_T) ? ct : 0.f, ab = (f & F_B) ? cb : 0.f;
+            s += ae * p[1];
+            s += aw * p[-1];
+            s += an * p[W];
+            s += as * p[-W];
+            s += at * pt[0];
+            s += ab * pb[0];
+        }
+        float own = p[0];
+        float reltmp = omega * (cn1 * (s - rhs) - own);
+        p[0] = own + reltmp;
+    };
+    // this lane's cells: red row j0 - 1 + yr (16 cells from i0 - 1), black
+    // row j0 + yr (15 cells from i0); shared offsets before the colour's
+    // parity shift (floats from the slot base for d and r, bytes for flags)
+    const int yr = 2 * warp + half;
+    const int jr = j0 - 1 + yr, jb = j0 + yr;
+    const int xr = i0 - 1 + 2 * m, xb = i0 + 2 * m;
+    const int oDr = (yr + 1) * W + xr + ox, oRr = (int)(MT::OFF_R / 4) + yr * W + xr + ox;
+    const int oFr = (int)MT::OFF_F + yr * FW + xr + oxf;
+    const int oDb = (yr + 2) * W + xb + ox, oRb = (int)(MT::OFF_R / 4) + (yr + 1) * W + xb + ox;
+    const int oFb = (int)MT::OFF_F + (yr + 1) * FW + xb + oxf;
+    const bool black_lane = warp < TY / 2 && m < TX / 2;
+    const bool store_lane = black_lane && jb <= d.ny && xb <= d.nx;
+    const bool store_pair = xb + 1 <= d.nx;
+    float* ob = dout + d.at(xb, jb, 0);           // this lane's pair on plane 0; + k * plane
+    for (int t = 0; t + 2 < nq; ++t) {
+        // red plane q = t + 1 needs slots t .. t + 2
+        bool ok = true;
+        while (landed <= t + 2 && ok) {
+            ok = wait(landed);
+            if (ok) ++landed;
+        }
+        if (wrap_xy) {
+            // the planes that landed this step get their periodic images
+            // (the first step: slots 0, 1, 2)
+            if (ok)
+                for (int q = (t == 0 ? 0 : t + 2); q <= t + 2; ++q) fixup(q);
+            __syncthreads();
+        }
+        if (ok) {
+            // red (i+j+k odd) on rows j0-1 .. j0+TY, cells i0-1 .. i0+30
+            const int q = t + 1, k = kb - 2 + q;
+            float* S = reinterpret_cast<float*>(base(q));
+            const int par = (i0 + jr + k) & 1;
+            const uint8_t f = reinterpret_cast<const uint8_t*>(S)[oFr + par];
+            if (f & F_UNK) {
+                float* p = S + oDr + par;
+                relax(p, reinterpret_cast<const float*>(base(q + 1)) + oDr + par,
+                      reinterpret_cast<const float*>(base(q - 1)) + oDr + par, sC(q), f, S[oRr + par]);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) atomicExch(&sc->timeout, 1);
+            for (int q = landed; q < issued; ++q) wait(q);      // bounded: copies still in flight land
+            return;
+        }
+        // slot of plane t - 2 is free (its last reader, black t - 1, finished before this barrier)
+        if (t >= 2 && issued < nq) {
+            if (tid == 0) issue(issued);
+            fill(issued);
+            ++issued;
+        }
+        // black (i+j+k even) on plane q = t (interior rows), then store the plane
+        if (t >= 2 && black_lane) {
+            const int q = t, k = kb - 2 + q;
+            float* S = reinterpret_cast<float*>(base(q));
+            const int par = (i0 + jb + k) & 1;
+            const uint8_t f = reinterpret_cast<const uint8_t*>(S)[oFb + par];
+            if (f & F_UNK) {
+                float* p = S + oDb + par;
+                relax(p, reinterpret_cast<const float*>(base(q + 1)) + oDb + par,
+                      reinterpret_cast<const float*>(base(q - 1)) + oDb + par, sC(q), f, S[oRb + par]);
+            }
+            if (store_lane) {
+                float* o = ob + (long long)k * d.plane;
+                if (store_pair) {
+                    *reinterpret_cast<float2*>(o) = make_float2(S[oDb], S[oDb + 1]);
+                } else {
+                    *o = S[oDb];
+                }
+            }
+        }
+    }
+}
+
 template <int BY, int BZ, int NT>
 cudaError_t allow_pipe() {
     return cudaFuncSetAttribute(k_sor_pipe<BY, BZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -440,6 +674,36 @@ void launch_tma_cfg(const Geo<float>& g, const TmaMaps& m, int in, float* dout, 
                m.rptr, dout, zero, sc);
 }
 
+template <int TY, int NS>
+cudaError_t allow_march() {
+    return cudaFuncSetAttribute(k_sor_march<TY, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)MarchTile<TY, NS>::SMEM);
+}
+
+int g_sms = 0;
+
+// planes per chunk: kc > 0 as given; kc <= 0: whole columns when they give at
+// least two CTAs per SM, else the chunk length that does (at least 4 planes)
+int march_chunk(const Dom& d, int ty, int kc) {
+    if (kc > 0) return kc < d.nz ? kc : d.nz;
+    const int cols = ((d.nx + 29) / 30) * ((d.ny + ty - 1) / ty);
+    const int want = 2 * (g_sms > 0 ? g_sms : 152);
+    const int chunks = (want + cols - 1) / cols;
+    int c = (d.nz + chunks - 1) / chunks;
+    if (c < 4) c = 4;
+    return c < d.nz ? c : d.nz;
+}
+
+template <int TY, int NS>
+void launch_march_cfg(const Geo<float>& g, const TmaMaps& m, const float* cn1tab, int in, float* dout, int kc,
+                      int zero, Scalars* sc, cudaStream_t s) {
+    const Dom& d = g.d;
+    const int c = march_chunk(d, TY, kc);
+    dim3 grid((d.nx + 29) / 30, (d.ny + TY - 1) / TY, (d.nz + c - 1) / c);
+    launch_pdl(k_sor_march<TY, NS>, grid, dim3(MarchTile<TY, NS>::NT), MarchTile<TY, NS>::SMEM, s, m.d[in], m.r,
+               m.f, g, cn1tab, m.dptr[in], m.rptr, dout, c, zero, sc);
+}
+
 using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
 
 EncodeFn encoder() {
@@ -470,9 +734,11 @@ bool encode3d(CUtensorMap* map, CUtensorMapDataType type, size_t es, void* base,
 
 }  // namespace
 
-// (BY, BZ, threads) of the TMA tiles, in the order of their tile indices
+// (BY, BZ, threads) of the TMA tiles, in the order of their tile indices; the
+// k-marching tiles (kFirstMarchCfg ..) as (TY, plane slots, threads)
 const int kTmaCfg[kNumTmaTiles][3] = {{8, 8, 256}, {12, 12, 512}, {16, 12, 512}, {16, 16, 512},
-                                      {8, 8, 256}, {8, 8, 512}, {16, 8, 512}, {12, 12, 512}};
+                                      {8, 8, 256}, {8, 8, 512}, {16, 8, 512}, {12, 12, 512},
+                                      {16, 6, 288}, {16, 8, 288}, {8, 8, 160}, {24, 6, 416}};
 
 bool tma_supported(const Dom&) { return true; }
 
@@ -492,28 +758,41 @@ cudaError_t tma_prepare() {
     g_pipe_blocks[1] = pipe_blocks<8, 8, 512>();
     g_pipe_blocks[2] = pipe_blocks<16, 8, 512>();
     g_pipe_blocks[3] = pipe_blocks<12, 12, 512>();
+    if ((x = allow_march<16, 6>()) != cudaSuccess) e = x;
+    if ((x = allow_march<16, 8>()) != cudaSuccess) e = x;
+    if ((x = allow_march<8, 8>()) != cudaSuccess) e = x;
+    if ((x = allow_march<24, 6>()) != cudaSuccess) e = x;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
     return e;
 }
 
 bool tma_encode(const Dom& d, float* dl0, float* dl1, float* rr, uint8_t* flags, TmaMaps* maps) {
     for (int c = 0; c < kNumTmaTiles; ++c) {
-        const int by = kTmaCfg[c][0], bz = kTmaCfg[c][1];
+        const bool march = c >= kFirstMarchCfg;
+        const int by = kTmaCfg[c][0], bz = march ? -1 : kTmaCfg[c][1];    // march: one plane per copy
         TmaMaps& m = maps[c];
         m.dptr[0] = dl0;
         m.dptr[1] = dl1;
         m.rptr = rr;
-        if (!encode3d(&m.d[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, dl0, d, 36, by + 4, bz + 4)) return false;
-        if (!encode3d(&m.d[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, dl1, d, 36, by + 4, bz + 4)) return false;
-        if (!encode3d(&m.r, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, rr, d, 36, by + 2, bz + 2)) return false;
-        if (!encode3d(&m.f, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, flags, d, 48, by + 2, bz + 2)) return false;
+        const int dz = march ? 1 : bz + 4;
+        if (!encode3d(&m.d[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, dl0, d, 36, by + 4, dz)) return false;
+        if (!encode3d(&m.d[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, dl1, d, 36, by + 4, dz)) return false;
+        if (!encode3d(&m.r, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, rr, d, 36, by + 2, march ? 1 : bz + 2)) return false;
+        if (!encode3d(&m.f, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, flags, d, 48, by + 2, march ? 1 : bz + 2)) return false;
     }
     return true;
 }
 
-int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, const float* cn1tab, int cfg, int in, float* dout,
-                   int zero, Scalars* sc, cudaStream_t s) {
+int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, const float* cn1tab, int cfg, int kc, int in,
+                   float* dout, int zero, Scalars* sc, cudaStream_t s) {
     const TmaMaps& m = maps[cfg];
     switch (cfg) {
+        case 8: launch_march_cfg<16, 6>(g, m, cn1tab, in, dout, kc, zero, sc, s); break;
+        case 9: launch_march_cfg<16, 8>(g, m, cn1tab, in, dout, kc, zero, sc, s); break;
+        case 10: launch_march_cfg<8, 8>(g, m, cn1tab, in, dout, kc, zero, sc, s); break;
+        case 11: launch_march_cfg<24, 6>(g, m, cn1tab, in, dout, kc, zero, sc, s); break;
         case 0: launch_tma_cfg<8, 8, 256>(g, m, in, dout, zero, sc, s); break;
         case 1: launch_tma_cfg<12, 12, 512>(g, m, in, dout, zero, sc, s); break;
         case 2: launch_tma_cfg<16, 12, 512>(g, m, in, dout, zero, sc, s); break;
@@ -521,7 +800,8 @@ int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, const float* cn1tab
         case 4: launch_pipe_cfg<8, 8, 256>(g, m, cn1tab, in, dout, zero, sc, s, 0); break;
         case 5: launch_pipe_cfg<8, 8, 512>(g, m, cn1tab, in, dout, zero, sc, s, 1); break;
         case 6: launch_pipe_cfg<16, 8, 512>(g, m, cn1tab, in, dout, zero, sc, s, 2); break;
-        default: launch_pipe_cfg<12, 12, 512>(g, m, cn1tab, in, dout, zero, sc, s, 3); break;
+        case 7: launch_pipe_cfg<12, 12, 512>(g, m, cn1tab, in, dout, zero, sc, s, 3); break;
+        default: break;
     }
     return 1;
 }

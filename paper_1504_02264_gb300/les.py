@@ -20,9 +20,11 @@ LES_EINVAL, LES_ENOMEM, LES_ECUDA, LES_ETIMEOUT, LES_ENONFINITE, LES_ESTATE = -1
 LES_BC_INOUT, LES_BC_FREESLIP, LES_BC_WALL, LES_BC_PERIODIC = 0, 1, 2, 3
 LES_FP32, LES_FP64 = 0, 1
 (LES_AUX_NUT, LES_AUX_RHS, LES_AUX_USTAR, LES_AUX_VSTAR, LES_AUX_WSTAR,
- LES_AUX_FU, LES_AUX_FV, LES_AUX_FW, LES_AUX_R0, LES_AUX_DELTA, LES_AUX_MASK) = range(11)
+ LES_AUX_FU, LES_AUX_FV, LES_AUX_FW, LES_AUX_R0, LES_AUX_DELTA, LES_AUX_MASK,
+ LES_AUX_NET_IN, LES_AUX_NET_Q) = range(13)
 LES_WARM_PREV, LES_WARM_NET, LES_WARM_ZERO = 0, 1, 2
 LES_SOR_REDBLACK, LES_SOR_TWINNED = 0, 1
+LES_SOR_NTILES = 29                 # sweep tile indices 0 .. LES_SOR_NTILES - 1 (les_set_sor_config)
 
 
 class les_grid_t(ctypes.Structure):
@@ -564,11 +566,12 @@ class Domain:
     def aux(self, which) -> np.ndarray:
         nx, ny, nz = self.nx, self.ny, self.nz
         shape = {LES_AUX_NUT: (nz, ny, nx), LES_AUX_RHS: (nz, ny, nx), LES_AUX_R0: (nz, ny, nx),
-                 LES_AUX_DELTA: (nz, ny, nx), LES_AUX_MASK: (nz, ny, nx),
+                 LES_AUX_DELTA: (nz, ny, nx), LES_AUX_MASK: (nz, ny, nx), LES_AUX_NET_IN: (nz, ny, nx),
+                 LES_AUX_NET_Q: (nz, ny, nx),
                  LES_AUX_USTAR: (nz, ny, nx + 1), LES_AUX_FU: (nz, ny, nx + 1),
                  LES_AUX_VSTAR: (nz, ny + 1, nx), LES_AUX_FV: (nz, ny + 1, nx),
                  LES_AUX_WSTAR: (nz + 1, ny, nx), LES_AUX_FW: (nz + 1, ny, nx)}[which]
-        out = np.empty(shape, dtype=self.dtype)
+        out = np.empty(shape, dtype=np.float32 if which == LES_AUX_NET_Q else self.dtype)
         les_get_aux(self.h, which, out)
         return out
 

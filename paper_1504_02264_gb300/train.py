@@ -48,6 +48,27 @@ def load(path: str, seed: int = 0) -> les.Net:
     return net
 
 
+def coarse_residual_params(nparam: int) -> np.ndarray:
+    """Weights under which the network computes q = r_coarse / rms: the
+    non-learned coarse-grid correction that the learned one is measured
+    against (same cycle, same kernels, same cost).  The first convolution
+    passes the residual channel as +x and -x through its centre tap, the
+    ReLU splits it into positive and negative parts, every other
+    convolution is zero (the decoder adds its skips back unchanged, so the
+    finest level's output is conv0's), and the head recombines the two
+    parts: y = relu(x) - relu(-x) = x."""
+    theta = np.zeros(nparam, np.float32)
+    cin0, cout0 = 16, 16
+    centre = 13                       # tap (dz, dy, dx) = (1, 1, 1)
+    w0 = np.zeros((27, cout0, cin0), np.float32)
+    w0[centre, 0, 0] = 1.0
+    w0[centre, 1, 0] = -1.0
+    theta[:w0.size] = w0.ravel()
+    theta[-16] = 1.0                  # head: channel 0 minus channel 1
+    theta[-15] = -1.0
+    return theta
+
+
 def training_scenes(n_lattice: int, n_city: int, seed: int, city_shape=(96, 96, 48), n_city2: int = 0,
                     city_shape2=(150, 150, 90)):
     """Lattice scenes (turbulent inflow for variety) and random cities of two

@@ -243,11 +243,12 @@ def test_fused_sor_matches_two_pass(prec, case):
     ref.step(2)
     want = ref.fields()
     tol = 0.0 if prec == "fp64" else 1e-6
-    # TMA block tiles (17-20) on every FP32 grid, periodic halos included; the
-    # persistent TMA tiles (21-24) only without periodic axes
+    # TMA block tiles (17-20) and k-marching TMA columns (25-28) on every FP32
+    # grid, periodic halos included; the persistent TMA tiles (21-24) only
+    # without periodic axes
     tiles = list(range(17))
     if prec == "fp32":
-        tiles += list(range(17, 21)) + (list(range(21, 25)) if case == "city" else [])
+        tiles += list(range(17, 21)) + (list(range(21, 25)) if case == "city" else []) + list(range(25, 29))
     if prec == "fp32" and case != "city":
         d = les.Domain(sc, precision=p)
         for tile in range(21, 25):
@@ -255,7 +256,7 @@ def test_fused_sor_matches_two_pass(prec, case):
                 d.set_sor_config(tile, 0)
         d.close()
     for tile in tiles:
-        for kc in ((0, 3, 5) if tile < 6 else (0,)):
+        for kc in ((0, 3, 5) if (tile < 6 or tile >= 25) else (0,)):
             d = les.Domain(sc, precision=p)
             d.set_sor_config(tile, kc)
             d.step(2)
@@ -270,7 +271,7 @@ def test_autotune_picks_a_valid_config():
     d = les.Domain(sc, precision=les.LES_FP32)
     d.step(1)
     (tile, kc), ms = d.autotune_sor(sweeps=5)
-    assert 0 <= tile < 25 and ms > 0
+    assert 0 <= tile < les.LES_SOR_NTILES and ms > 0
     before = d.fields()
     d2 = les.Domain(sc, precision=les.LES_FP32)
     d2.step(1)

@@ -53,11 +53,15 @@ def test_reference_arm_two_ranks_rank0_reports():
     """--impl reference under torchrun: rank 0 alone times the oracle and prints
     one line; the other rank exits 0 without work."""
     pytest.importorskip("torch")
-    r = torchrun(["bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "3"], timeout=600)
+    r = torchrun(["bench.py", "--impl", "reference", "--gpus", "2", "--steps", "2", "--warmup", "3",
+                  "--ref-workload", "small"], timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = json_lines(r.stdout)
     assert len(lines) == 1
     d = lines[0]
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["nproc"] >= 1 and d["cpu_baseline"]["cpu_model"]
+    assert 1 <= d["steps"] <= 2 and len(d["sweeps_per_step"]) == d["steps"]
+    assert all(s > 0 for s in d["sweeps_per_step"])
     assert d["e2e"]["h2d_bytes_per_step"] == 0
