@@ -351,8 +351,11 @@ int les_residual_noalloc(const les_grid_t* grid, const void* d_p, const void* d_
  * the minimiser of the energy norm of the error along q, so p0 is never
  * further from the solution than p_prev in that norm, and runs the same
  * red-black SOR to the same tolerance: plain SOR stays the stop test.  Activations are BF16, accumulation FP32, on the
- * tensor cores (mma.sync m16n8k16).  Training runs on the GPU with the
- * network's own backward kernels and Adam.
+ * tensor cores: the forward convolutions (and the backward pass's input
+ * gradients) on tcgen05.mma with the accumulator in tensor memory by default,
+ * or on the warp-level mma.sync kernel (les_net_set_engine); the weight
+ * gradients on mma.sync.  Training runs on the GPU with the network's own
+ * backward kernels and Adam.
  *
  * Device arrays of the training / inference calls are dense float [b][nz][ny][nx]
  * (b = batch index): d_r residuals, d_mask 1/0 unknown masks, d_t target
@@ -381,6 +384,17 @@ int les_net_set_params(les_net n, const float* host);
  * against the pooled target. */
 int les_net_set_stride(les_net n, int32_t stride);
 int les_net_get_stride(les_net n, int32_t* stride);
+/* les_net_set_engine: the tensor-core path of the forward convolutions:
+ * LES_NET_TCGEN05 (default: tcgen05.mma, 128-voxel x 16/32-channel tiles,
+ * FP32 accumulator in tensor memory) or LES_NET_MMA_SYNC (warp-level
+ * m16n8k16).  Both stage the same BF16 operands and accumulate in FP32 (the
+ * summation order inside an MMA differs).  A tcgen05 kernel whose bounded
+ * wait gives up makes the next synchronous network call return
+ * LES_ETIMEOUT. */
+#define LES_NET_MMA_SYNC 0
+#define LES_NET_TCGEN05 1
+int les_net_set_engine(les_net n, int32_t engine);
+int les_net_get_engine(les_net n, int32_t* engine);
 int les_net_forward(les_net n, const float* d_r, const float* d_mask, float* d_y, int32_t nx, int32_t ny, int32_t nz);
 int les_net_gradient(les_net n, const float* d_r, const float* d_mask, const float* d_t, int32_t batch, int32_t nx,
                      int32_t ny, int32_t nz, float* d_grad, double* loss);

@@ -153,6 +153,8 @@ struct les_net_s {
                   *gpb = nullptr;
     float *y = nullptr, *gy = nullptr, *mask = nullptr, *tn = nullptr;
     int stride = 1;                     // the network runs on the grid coarsened stride times per axis
+    int engine = nn::kEngineTcgen05;    // forward convolutions: tcgen05 (default) or warp-level mma.sync
+    int* tc_timeout = nullptr;          // device flag: a bounded wait of a tcgen05 convolution gave up
     float *rc = nullptr, *mc = nullptr, *tc = nullptr;     // pooled sample (coarse level 0)
     double* dscal = nullptr;            // [0,1] rms / mask sum of r, [2,3] of t, [62] loss, [64..) partials
     long long ws_gen = 0;               // bumped whenever the workspace is reallocated
@@ -490,6 +492,7 @@ int net_persistent_launches() { return 4; }     // pool, barrier reset, network,
 long long net_generation(const les_net_s* n) { return n->ws_gen; }
 int net_predict(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, float* out_dense,
                 cudaStream_t s, const int* gate) {
+    nn::set_conv_engine(n->engine, n->tc_timeout);
     const Level Lf{d.nx, d.ny, d.nz};
     const Level L0 = coarse(n, Lf);
     cudaStream_t keep = n->stream;
@@ -560,7 +563,8 @@ int les_net_create(uint64_t seed, void* stream, les_net* out) {
               get(2 * nn::kPoolRmsMax * sizeof(double), (void**)&n->pp_part) &&
               get(sizeof(unsigned), (void**)&n->pp_count) &&
               get(kSplitFloats * sizeof(float), (void**)&n->split.part) &&
-              get(kSplitCounters * sizeof(unsigned), (void**)&n->split.cnt);
+              get(kSplitCounters * sizeof(unsigned), (void**)&n->split.cnt) &&
+              get(sizeof(int), (void**)&n->tc_timeout);
     n->split.part_floats = kSplitFloats;
     n->split.counters = kSplitCounters;
     for (int c = 0; ok && c < kConvs; ++c) {
@@ -628,9 +632,31 @@ int les_net_get_stride(les_net n, int32_t* stride) {
     return LES_OK;
 }
 
+// a tcgen05 convolution of the last synchronous call gave up a bounded wait
+int tc_check(les_net_s* n) {
+    int t = 0;
+    NCK(cudaMemcpy(&t, n->tc_timeout, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!t) return LES_OK;
+    NCK(cudaMemset(n->tc_timeout, 0, sizeof(int)));
+    return nfail(n, LES_ETIMEOUT, "a tcgen05 convolution's bounded wait timed out");
+}
+
+int les_net_set_engine(les_net n, int32_t engine) {
+    if (!n || (engine != LES_NET_MMA_SYNC && engine != LES_NET_TCGEN05)) return LES_EINVAL;
+    n->engine = engine == LES_NET_TCGEN05 ? nn::kEngineTcgen05 : nn::kEngineMmaSync;
+    return LES_OK;
+}
+
+int les_net_get_engine(les_net n, int32_t* engine) {
+    if (!n || !engine) return LES_EINVAL;
+    *engine = n->engine == nn::kEngineTcgen05 ? LES_NET_TCGEN05 : LES_NET_MMA_SYNC;
+    return LES_OK;
+}
+
 int les_net_forward(les_net n, const float* d_r, const float* d_mask, float* d_y, int32_t nx, int32_t ny,
                     int32_t nz) {
     if (!n || !d_r || !d_mask || !d_y || nx < 1 || ny < 1 || nz < 1) return LES_EINVAL;
+    nn::set_conv_engine(n->engine, n->tc_timeout);
     const Level Lf{nx, ny, nz};
     const Level L0 = coarse(n, Lf);
     int rc = ensure_ws(n, L0);
@@ -640,24 +666,26 @@ int les_net_forward(les_net n, const float* d_r, const float* d_mask, float* d_y
     nn::prolong_dense(n->y, d_mask, d_y, nx, ny, nz, n->stride, n->stream);
     NCK(cudaGetLastError());
     NCK(cudaStreamSynchronize(n->stream));
-    return LES_OK;
+    return tc_check(n);
 }
 
 int les_net_gradient(les_net n, const float* d_r, const float* d_mask, const float* d_t, int32_t batch, int32_t nx,
                      int32_t ny, int32_t nz, float* d_grad, double* loss) {
     if (!n || !d_r || !d_mask || !d_t || !d_grad || !loss || batch < 1 || nx < 1 || ny < 1 || nz < 1)
         return LES_EINVAL;
+    nn::set_conv_engine(n->engine, n->tc_timeout);
     int rc = batch_grad(n, Level{nx, ny, nz}, d_r, d_mask, d_t, batch, loss);
     if (rc) return rc;
     NCK(cudaMemcpyAsync(d_grad, n->g32, n->nparam * 4, cudaMemcpyDeviceToDevice, n->stream));
     NCK(cudaStreamSynchronize(n->stream));
-    return LES_OK;
+    return tc_check(n);
 }
 
 int les_net_train_step(les_net n, const float* d_r, const float* d_mask, const float* d_t, int32_t batch, int32_t nx,
                        int32_t ny, int32_t nz, float lr, double* loss) {
     if (!n || !d_r || !d_mask || !d_t || !loss || batch < 1 || nx < 1 || ny < 1 || nz < 1 || !(lr > 0))
         return LES_EINVAL;
+    nn::set_conv_engine(n->engine, n->tc_timeout);
     int rc = batch_grad(n, Level{nx, ny, nz}, d_r, d_mask, d_t, batch, loss);
     if (rc) return rc;
     n->adam_t += 1;
@@ -671,7 +699,7 @@ int les_net_train_step(les_net n, const float* d_r, const float* d_mask, const f
     for (int c = 0; c < kConvs; ++c) nn::wflip(n->wb[c], n->wt[c], kCin[c], kCout[c], n->stream);
     NCK(cudaGetLastError());
     NCK(cudaStreamSynchronize(n->stream));
-    return LES_OK;
+    return tc_check(n);
 }
 
 }  // extern "C"

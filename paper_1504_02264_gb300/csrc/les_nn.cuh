@@ -18,6 +18,40 @@ struct ConvSplit {
     unsigned* cnt;
     size_t counters;
 };
+// How a convolution reads input voxel (gx, gy, gz) of its X x Y x Z output
+// grid from its source tensor x (Xs x Ys x Zs):
+//   IN_DIRECT  x[gz][gy][gx]
+//   IN_UP      x[gz/2][gy/2][gx/2]               nearest upsampling of a coarser tensor
+//   IN_POOL    mean of the 8 children x[2gz+c][2gy+b][2gx+a] (missing children count as
+//              zero; summed in the order of the stand-alone pooling kernel, so the
+//              staged values are bit-identical to pooling first)
+enum { IN_DIRECT = 0, IN_UP = 1, IN_POOL = 2 };
+struct ConvArgs {
+    const __nv_bfloat16* x;
+    const __nv_bfloat16* w;
+    __nv_bfloat16* y;
+    const __nv_bfloat16* skip;
+    __nv_bfloat16* ysum;
+    int X, Y, Z, Cin, Cout, relu, Xs, Ys, Zs;
+    // split over the input-channel chunks (ks > 1): CTA kq of an output tile
+    // takes chunks [kq * nch / ks, (kq + 1) * nch / ks) and leaves its FP32
+    // accumulators in part; the last CTA of the tile (counter cnt[tile]) adds
+    // the ks partials in the order kq = 0, 1, ... and runs the epilogue
+    float* part;
+    unsigned* cnt;
+    int ks;
+};
+
+// Which tensor-core path the forward convolutions (inference, and the
+// backward pass's input gradient) run on: the warp-level mma.sync kernel or
+// the tcgen05 kernel (les_nn_tc.cu).  `timeout` (device int, nullable) records
+// a bounded wait of the tcgen05 kernel that gave up.  Process-wide; the
+// network entry points set it from the network's own choice before launching.
+constexpr int kEngineMmaSync = 0, kEngineTcgen05 = 1;
+void set_conv_engine(int engine, int* timeout);
+int conv3_tc_prepare();
+void conv3_tc_launch(ConvArgs A, int in_mode, cudaStream_t s, const int* gate, const ConvSplit* split, int* timeout);
+
 void conv3_fwd(const __nv_bfloat16* x, const __nv_bfloat16* w, __nv_bfloat16* y, const __nv_bfloat16* skip,
                __nv_bfloat16* ysum, int X, int Y, int Z, int Cin, int Cout, int relu, cudaStream_t s,
                const int* gate = nullptr, const ConvSplit* split = nullptr);

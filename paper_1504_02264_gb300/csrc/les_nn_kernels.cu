@@ -82,22 +82,7 @@ struct ConvStage {
 //   IN_POOL    mean of the 8 children x[2gz+c][2gy+b][2gx+a] (missing children count as
 //              zero; summed in the order of the stand-alone pooling kernel, so the
 //              staged values are bit-identical to pooling first)
-enum { IN_DIRECT = 0, IN_UP = 1, IN_POOL = 2 };
-struct ConvArgs {
-    const __nv_bfloat16* x;
-    const __nv_bfloat16* w;
-    __nv_bfloat16* y;
-    const __nv_bfloat16* skip;
-    __nv_bfloat16* ysum;
-    int X, Y, Z, Cin, Cout, relu, Xs, Ys, Zs;
-    // split over the input-channel chunks (ks > 1): CTA kq of an output tile
-    // takes chunks [kq * nch / ks, (kq + 1) * nch / ks) and leaves its FP32
-    // accumulators in part; the last CTA of the tile (counter cnt[tile]) adds
-    // the ks partials in the order kq = 0, 1, ... and runs the epilogue
-    float* part;
-    unsigned* cnt;
-    int ks;
-};
+// (IN_* and ConvArgs: les_nn.cuh)
 
 // one output tile: (bx, by) and bz = z tile + ntz * output-channel tile;
 // kq: the tile's input-channel split (0 without a split)
@@ -295,6 +280,7 @@ static cudaError_t allow_conv() {
 }
 
 int conv3_prepare() {
+    if (conv3_tc_prepare() != 0) return -1;
     cudaError_t e = cudaSuccess, x;
     if ((x = allow_conv<32, IN_DIRECT>()) != cudaSuccess) e = x;
     if ((x = allow_conv<16, IN_DIRECT>()) != cudaSuccess) e = x;
@@ -305,10 +291,23 @@ int conv3_prepare() {
     return e == cudaSuccess ? 0 : -1;
 }
 
+int g_conv_engine = kEngineTcgen05;
+int* g_conv_timeout = nullptr;
+
+void set_conv_engine(int engine, int* timeout) {
+    g_conv_engine = engine;
+    g_conv_timeout = timeout;
+}
+
 template <int IN>
 static void conv3_launch(const __nv_bfloat16* x, const __nv_bfloat16* w, __nv_bfloat16* y, const __nv_bfloat16* skip,
                          __nv_bfloat16* ysum, int X, int Y, int Z, int Cin, int Cout, int relu, cudaStream_t s,
                          const int* gate, int Xs, int Ys, int Zs, const ConvSplit* split) {
+    if (g_conv_engine == kEngineTcgen05) {
+        const ConvArgs A{x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu, Xs, Ys, Zs, nullptr, nullptr, 1};
+        conv3_tc_launch(A, IN, s, gate, split, g_conv_timeout);
+        return;
+    }
     // 32 output channels per CTA when the grid fills the GPU, else 16 (twice
     // the CTAs, half the weights staged per CTA: small levels are latency-bound)
     const int ntz = (Z + TZ - 1) / TZ;

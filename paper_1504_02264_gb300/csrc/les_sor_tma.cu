@@ -400,31 +400,40 @@ k_sor_pipe(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUten
 
 // k-marching variant: a CTA owns a 30 x TY column of cells over a chunk of
 // planes [kb, ke) and walks it bottom to top with both colours in one pass
-// (a wavefront two planes deep): at step t it relaxes the red cells of plane
-// kb-1+t on the column plus a 1-cell ring, then the black cells of the plane
-// below on the column, and stores that plane, whose cells are then final.
-// Red at plane k reads black neighbours at k-1 and k+1 that are still the
-// old values (black k-1 is relaxed after red k), black at k-1 reads the new
-// red values of k-2, k-1 (ring included) and k: the iterate of the in-order
-// red-black sweep, bit for bit.  Each plane is one TMA copy of d (2-cell
-// ring), r and the flags (1-cell ring) into one of NS shared-memory slots on
-// its own mbarrier, issued NS - 2 planes ahead of use, so the copies of
-// later planes are in flight while the current ones are relaxed; only the
-// x-y ring is loaded twice (by the neighbouring columns), planes are read
-// once per chunk plus four halo planes.  One barrier per plane: red(k+1)
-// touches neither the cells black(k-1) writes nor those it reads.
+// (a wavefront two planes deep): red at plane k reads black neighbours at
+// k-1 and k+1 that are still the old values (black k-1 is relaxed after red
+// k), black at k-1 reads the new red values of k-2, k-1 (ring included) and
+// k: the iterate of the in-order red-black sweep, bit for bit.  Each step
+// takes two planes: red on planes 2t+1 and 2t+2 of the chunk (column plus a
+// 1-cell ring), one barrier, then black on planes 2t and 2t+1 (column only)
+// and their stores, whose cells are then final.  Red of the next step
+// touches neither the cells black writes nor those it reads, so one barrier
+// per step suffices.
+//
+// Each plane is one TMA copy of d (2-cell ring), r and the flags (1-cell
+// ring) into one of NS shared-memory slots (plane q in slot q & (NS-1)) on
+// its own mbarrier; the slots freed by a step are refilled right after its
+// barrier, NS - 5 planes ahead of their first use, so the copies of later
+// planes are in flight while the current ones are relaxed.  Only the x-y
+// ring is loaded twice (by the neighbouring columns); planes are read once
+// per chunk plus four halo planes.
 //
 // Lanes: 16 per row, two rows per warp (their colours differ, so the
 // stride-2 shared-memory accesses of the two rows fall on opposite bank
 // parities: no conflicts); a red row has 16 cells of the ring-extended
 // 32-wide row, a black row 15 of the 30 interior cells, and the lane that
-// relaxed the black cell of a pair stores the pair (8-byte aligned).
+// relaxed the black cell of a pair stores the pair (8-byte aligned).  The
+// update is branch-free: the four in-plane coefficients of an open-face
+// mask come from a per-CTA table (one 16-byte read), the vertical ones and
+// cn1 from the plane's slot.
 //
 // Periodic axes: the plane of a copy wraps on a periodic z axis; columns
-// whose ring crosses a periodic x or y face overwrite the out-of-range cells
-// of each landed plane with plain loads of their images before relaxing.
+// whose ring crosses a periodic x or y face overwrite the out-of-range rows
+// and columns of each landed plane with plain loads of their images.
 template <int TY, int NS>
 struct MarchTile {
+    static_assert((NS & (NS - 1)) == 0 && NS >= 8, "plane slots: a power of two, at least 8");
+    static_assert(TY % 2 == 0, "rows come in pairs");
     static constexpr int TX = 30, W = 36, FW = 48;
     static constexpr int DY = TY + 4, RY = TY + 2;
     static constexpr int NW = RY / 2, NT = 32 * NW;       // one warp per red row pair
@@ -435,7 +444,8 @@ struct MarchTile {
     static constexpr uint32_t OFF_F = OFF_R + align_up(BYTES_R, 128);
     static constexpr uint32_t OFF_C = OFF_F + align_up(BYTES_F, 128);   // cn1 row [64], cT, cB
     static constexpr uint32_t SLOT = align_up(OFF_C + 66 * 4, 128);
-    static constexpr uint32_t OFF_BAR = NS * SLOT;
+    static constexpr uint32_t OFF_T4 = NS * SLOT;                         // float4 [64]: ae, aw, an, as
+    static constexpr uint32_t OFF_BAR = OFF_T4 + 64 * 16;
     static constexpr uint32_t SMEM = OFF_BAR + NS * 8;
 };
 
@@ -446,7 +456,7 @@ k_sor_march(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUte
             const float* __restrict__ din, const float* __restrict__ rin, float* __restrict__ dout, int kc,
             int zero_arg, Scalars* __restrict__ sc) {
     using MT = MarchTile<TY, NS>;
-    constexpr int TX = MT::TX, W = MT::W, FW = MT::FW, DY = MT::DY, RY = MT::RY, NT = MT::NT;
+    constexpr int TX = MT::TX, W = MT::W, DY = MT::DY, RY = MT::RY, NT = MT::NT, NW = MT::NW;
     extern __shared__ __align__(128) unsigned char sm[];
     pdl_wait();
     if (sc->done) return;
@@ -455,69 +465,68 @@ k_sor_march(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUte
     const int half = lane >> 4, m = lane & 15;
     const int i0 = 1 + blockIdx.x * TX, j0 = 1 + blockIdx.y * TY;
     const int kb = 1 + blockIdx.z * kc, ke = min(kb + kc, d.nz + 1);
-    const int nq = ke - kb + 4;                    // planes kb-2 .. ke+1
+    const int nq = ke - kb + 4;                    // planes kb-2 .. ke+1 (slot index q = plane - kb + 2)
     const int xa = (i0 - 2 + OX) & ~3;             // padded column of the d and r boxes (16-byte aligned)
     const int xf = (i0 - 2 + OX) & ~15;            // of the flag box
     const int ox = OX - xa, oxf = OX - xf;         // shared column of cell i: i + ox (flags: i + oxf)
     const bool zero_start = zero_arg == 1 || (zero_arg == 2 && sc->zflag);
-    const bool wrap_xy = (d.perx && (i0 - 2 < 1 || i0 + TX + 1 > d.nx)) || (d.pery && (j0 - 2 < 1 || j0 + TY + 1 > d.ny));
+    const bool wrap_x = d.perx && (i0 - 2 < 1 || i0 + TX + 1 > d.nx);
+    const bool wrap_y = d.pery && (j0 - 2 < 1 || j0 + TY + 1 > d.ny);
     const uint32_t bar0 = smem_u32(sm + MT::OFF_BAR);
-    auto base = [&](int q) { return sm + (q % NS) * MT::SLOT; };
-    auto sD = [&](int q) { return reinterpret_cast<float(*)[W]>(base(q)); };
-    auto sR = [&](int q) { return reinterpret_cast<float(*)[W]>(base(q) + MT::OFF_R); };
-    auto sF = [&](int q) { return reinterpret_cast<uint8_t(*)[FW]>(base(q) + MT::OFF_F); };
-    auto sC = [&](int q) { return reinterpret_cast<float*>(base(q) + MT::OFF_C); };
-    // plane of slot index q, and the plane its copy reads (periodic z: the image)
-    auto src_plane = [&](int q) {
-        const int k = kb - 2 + q;
-        return (d.perz && (k < 1 || k > d.nz)) ? ((k - 1) % d.nz + d.nz) % d.nz + 1 : k;
-    };
+    const float4* T4 = reinterpret_cast<const float4*>(sm + MT::OFF_T4);
+    auto slot = [&](int q) { return sm + (uint32_t)(q & (NS - 1)) * MT::SLOT; };
     auto issue = [&](int q) {       // one thread
-        const uint32_t bar = bar0 + 8 * (q % NS);
-        unsigned char* b = base(q);
-        const int zc = src_plane(q);
+        const uint32_t bar = bar0 + 8u * (uint32_t)(q & (NS - 1));
+        unsigned char* b = slot(q);
+        int zc = kb - 2 + q;       // the plane the copy reads: the image on a periodic z axis
+        if (d.perz && (zc < 1 || zc > d.nz)) zc = zc < 1 ? zc + d.nz : zc - d.nz;
         mbar_expect_tx(bar, MT::BYTES_R + MT::BYTES_F + (zero_start ? 0u : MT::BYTES_D));
         if (!zero_start) tma_load_3d(smem_u32(b), &td, xa, j0 - 2, zc, bar);
         tma_load_3d(smem_u32(b + MT::OFF_R), &tr, xa, j0 - 1, zc, bar);
         tma_load_3d(smem_u32(b + MT::OFF_F), &tf, xf, j0 - 1, zc, bar);
     };
-    // coefficients of slot q's plane (and zeros for d on a zero start); all threads
-    auto fill = [&](int q) {
-        const int k = coef_plane(d, kb - 2 + q);
-        float* c = sC(q);
-        for (int e = tid; e < 66; e += NT) c[e] = e < 64 ? cn1tab[k * 64 + e] : (e == 64 ? g.cT[k] : g.cB[k]);
+    // coefficient row of slot q's plane (threads 0..65 of the group starting
+    // at `first`) and, on a zero start, zeros for its d
+    auto fill = [&](int q, int first) {
+        const int e = tid - first;
+        if (e >= 0 && e < 66) {
+            const int k = coef_plane(d, kb - 2 + q);
+            float* c = reinterpret_cast<float*>(slot(q) + MT::OFF_C);
+            c[e] = e < 64 ? cn1tab[k * 64 + e] : (e == 64 ? g.cT[k] : g.cB[k]);
+        }
         if (zero_start) {
-            float* p = &sD(q)[0][0];
-            for (int e = tid; e < W * DY; e += NT) p[e] = 0.f;
+            float* p = reinterpret_cast<float*>(slot(q));
+            for (int x = tid; x < W * DY; x += NT) p[x] = 0.f;
         }
     };
-    // images of the ring cells across a periodic x or y face; all threads
+    // images across a periodic x or y face of the ring cells of a landed plane
     auto fixup = [&](int q) {
-        const int k = src_plane(q);
-        float(*D)[W] = sD(q);
-        float(*R)[W] = sR(q);
-        uint8_t(*F)[FW] = sF(q);
+        int k = kb - 2 + q;
+        if (d.perz && (k < 1 || k > d.nz)) k = k < 1 ? k + d.nz : k - d.nz;
+        unsigned char* b = slot(q);
+        float* D = reinterpret_cast<float*>(b);
+        float* R = reinterpret_cast<float*>(b + MT::OFF_R);
+        uint8_t* F = b + MT::OFF_F;
         long long s_;
-        if (!zero_start)
-            for (int e = tid; e < DY * (TX + 4); e += NT) {
-                const int y = e / (TX + 4), i = i0 - 2 + e % (TX + 4);
-                if (periodic_image(d, i, j0 - 2 + y, k, s_)) D[y][i + ox] = s_ >= 0 ? din[s_] : 0.f;
+        for (int y = warp; y < DY; y += NW)
+            for (int x = lane; x < TX + 4; x += 32) {
+                const int i = i0 - 2 + x, j = j0 - 2 + y;
+                const bool edge = (wrap_x && (i < 1 || i > d.nx)) || (wrap_y && (j < 1 || j > d.ny));
+                if (!edge || !periodic_image(d, i, j, k, s_)) continue;
+                if (!zero_start) D[y * W + i + ox] = s_ >= 0 ? din[s_] : 0.f;
+                if (y >= 1 && y <= RY && x >= 1 && x <= TX + 2) {
+                    R[(y - 1) * W + i + ox] = s_ >= 0 ? rin[s_] : 0.f;
+                    F[(y - 1) * MT::FW + i + oxf] = s_ >= 0 ? g.flags[s_] : (uint8_t)0;
+                }
             }
-        for (int e = tid; e < RY * (TX + 2); e += NT) {
-            const int y = e / (TX + 2), i = i0 - 1 + e % (TX + 2);
-            if (periodic_image(d, i, j0 - 1 + y, k, s_)) {
-                R[y][i + ox] = s_ >= 0 ? rin[s_] : 0.f;
-                F[y][i + oxf] = s_ >= 0 ? g.flags[s_] : (uint8_t)0;
-            }
-        }
     };
     auto wait = [&](int q) {
-        const uint32_t bar = bar0 + 8 * (q % NS), par = (uint32_t)(q / NS) & 1u;
-        bool ok;
+        const uint32_t bar = bar0 + 8u * (uint32_t)(q & (NS - 1)), par = (uint32_t)(q / NS) & 1u;
+        if (mbar_try_wait(bar, par)) return true;
         const uint64_t t0 = global_ns();
-        while (!(ok = mbar_try_wait(bar, par)))
-            if (global_ns() - t0 > 1000000000ull) break;
-        return ok;
+        while (!mbar_try_wait(bar, par))
+            if (global_ns() - t0 > 1000000000ull) return false;
+        return true;
     };
     const int nfirst = nq < NS ? nq : NS;
     if (tid == 0) {
@@ -525,34 +534,29 @@ k_sor_march(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUte
         mbar_fence_init();
         for (int q = 0; q < nfirst; ++q) issue(q);
     }
-    for (int q = 0; q < nfirst; ++q) fill(q);
+    for (int q = 0; q < nfirst; ++q) fill(q, 0);
+    if (tid < 64) {
+        const float cx = g.cx, cy = g.cy;
+        reinterpret_cast<float4*>(sm + MT::OFF_T4)[tid] =
+            make_float4((tid & F_E) ? cx : 0.f, (tid & F_W) ? cx : 0.f, (tid & F_N) ? cy : 0.f, (tid & F_S) ? cy : 0.f);
+    }
     __syncthreads();
     int issued = nfirst, landed = 0;
-    const float omega = g.omega, cx = g.cx, cy = g.cy;
-    // the update of Sec. 2.6 at the shared cell p of plane k, with the same
-    // cell of planes k+1 (pt) and k-1 (pb)
-    auto relax = [&](float* p, const float* pt, const float* pb, const float* C, uint8_t f, float rhs) {
-        const float ct = C[64], cb = C[65];
+    const float omega = g.omega;
+    // the update of Sec. 2.6 at shared cell p of a plane whose slot starts at
+    // S, with the same cell of the planes above (pt) and below (pb)
+    auto relax = [&](const unsigned char* S, float* p, const float* pt, const float* pb, uint8_t f, float rhs) {
+        const float* C = reinterpret_cast<const float*>(S + MT::OFF_C);
+        const float4 a = T4[f & 63];
         const float cn1 = C[f & 63];
+        const float at = (f & F_T) ? C[64] : 0.f, ab = (f & F_B) ? C[65] : 0.f;
         float s = 0.f;
-        if ((f & 63) == 63) {
-            s += cx * p[1];
-            s += cx * p[-1];
-            s += cy * p[W];
-            s += cy * p[-W];
-            s += ct * pt[0];
-            s += cb * pb[0];
-        } else {
-            const float ae = (f & F_E) ? cx : 0.f, aw = (f & F_W) ? cx : 0.f;
-            const float an = (f & F_N) ? cy : 0.f, as = (f & F_S) ? cy : 0.f;
-            const float at = (f & F_T) ? ct : 0.f, ab = (f & F_B) ? cb : 0.f;
-            s += ae * p[1];
-            s += aw * p[-1];
-            s += an * p[W];
-            s += as * p[-W];
-            s += at * pt[0];
-            s += ab * pb[0];
-        }
+        s += a.x * p[1];
+        s += a.y * p[-1];
+        s += a.z * p[W];
+        s += a.w * p[-W];
+        s += at * pt[0];
+        s += ab * pb[0];
         float own = p[0];
         float reltmp = omega * (cn1 * (s - rhs) - own);
         p[0] = own + reltmp;
@@ -561,40 +565,45 @@ k_sor_march(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUte
     // row j0 + yr (15 cells from i0); shared offsets before the colour's
     // parity shift (floats from the slot base for d and r, bytes for flags)
     const int yr = 2 * warp + half;
-    const int jr = j0 - 1 + yr, jb = j0 + yr;
     const int xr = i0 - 1 + 2 * m, xb = i0 + 2 * m;
     const int oDr = (yr + 1) * W + xr + ox, oRr = (int)(MT::OFF_R / 4) + yr * W + xr + ox;
-    const int oFr = (int)MT::OFF_F + yr * FW + xr + oxf;
+    const int oFr = (int)MT::OFF_F + yr * MT::FW + xr + oxf;
     const int oDb = (yr + 2) * W + xb + ox, oRb = (int)(MT::OFF_R / 4) + (yr + 1) * W + xb + ox;
-    const int oFb = (int)MT::OFF_F + (yr + 1) * FW + xb + oxf;
+    const int oFb = (int)MT::OFF_F + (yr + 1) * MT::FW + xb + oxf;
+    // parity of the first cell of this lane's red / black row on slot plane q: (pr0 + q) & 1
+    const int pr0 = (i0 + (j0 - 1 + yr) + kb) & 1, pb0 = (i0 + (j0 + yr) + kb) & 1;
     const bool black_lane = warp < TY / 2 && m < TX / 2;
-    const bool store_lane = black_lane && jb <= d.ny && xb <= d.nx;
+    const bool store_lane = black_lane && j0 + yr <= d.ny && xb <= d.nx;
     const bool store_pair = xb + 1 <= d.nx;
-    float* ob = dout + d.at(xb, jb, 0);           // this lane's pair on plane 0; + k * plane
-    for (int t = 0; t + 2 < nq; ++t) {
-        // red plane q = t + 1 needs slots t .. t + 2
+    float* const ob0 = dout + d.at(xb, j0 + yr, kb - 2);    // this lane's pair on slot plane 0
+    const int nsteps = (nq - 1) / 2;
+    for (int t = 0; t < nsteps; ++t) {
+        // red planes 2t+1, 2t+2 read slots 2t .. 2t+3
+        const int need = min(2 * t + 3, nq - 1);
         bool ok = true;
-        while (landed <= t + 2 && ok) {
+        while (landed <= need && ok) {
             ok = wait(landed);
             if (ok) ++landed;
         }
-        if (wrap_xy) {
-            // the planes that landed this step get their periodic images
-            // (the first step: slots 0, 1, 2)
+        if (wrap_x || wrap_y) {
             if (ok)
-                for (int q = (t == 0 ? 0 : t + 2); q <= t + 2; ++q) fixup(q);
+                for (int q = (t == 0 ? 0 : 2 * t + 2); q <= need; ++q) fixup(q);
             __syncthreads();
         }
         if (ok) {
-            // red (i+j+k odd) on rows j0-1 .. j0+TY, cells i0-1 .. i0+30
-            const int q = t + 1, k = kb - 2 + q;
-            float* S = reinterpret_cast<float*>(base(q));
-            const int par = (i0 + jr + k) & 1;
-            const uint8_t f = reinterpret_cast<const uint8_t*>(S)[oFr + par];
-            if (f & F_UNK) {
-                float* p = S + oDr + par;
-                relax(p, reinterpret_cast<const float*>(base(q + 1)) + oDr + par,
-                      reinterpret_cast<const float*>(base(q - 1)) + oDr + par, sC(q), f, S[oRr + par]);
+#pragma unroll
+            for (int h = 1; h <= 2; ++h) {
+                const int q = 2 * t + h;
+                if (q > nq - 2) break;
+                unsigned char* S = slot(q);
+                const int par = (pr0 + q) & 1;
+                const uint8_t f = S[oFr + par];
+                if (f & F_UNK) {
+                    float* p = reinterpret_cast<float*>(S) + oDr + par;
+                    relax(S, p, reinterpret_cast<const float*>(slot(q + 1)) + oDr + par,
+                          reinterpret_cast<const float*>(slot(q - 1)) + oDr + par, f,
+                          reinterpret_cast<const float*>(S)[oRr + par]);
+                }
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -603,29 +612,35 @@ k_sor_march(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUte
             for (int q = landed; q < issued; ++q) wait(q);      // bounded: copies still in flight land
             return;
         }
-        // slot of plane t - 2 is free (its last reader, black t - 1, finished before this barrier)
-        if (t >= 2 && issued < nq) {
+        // slots of planes 2t-3 and 2t-2 are free (their last readers, black
+        // 2t-2 and 2t-1, finished before this barrier): planes up to 2t-2+NS
+        const int lim = min(2 * t - 2 + NS, nq - 1);
+        for (int g2 = 0; issued <= lim; ++g2, ++issued) {
             if (tid == 0) issue(issued);
-            fill(issued);
-            ++issued;
+            fill(issued, 66 * g2);
         }
-        // black (i+j+k even) on plane q = t (interior rows), then store the plane
-        if (t >= 2 && black_lane) {
-            const int q = t, k = kb - 2 + q;
-            float* S = reinterpret_cast<float*>(base(q));
-            const int par = (i0 + jb + k) & 1;
-            const uint8_t f = reinterpret_cast<const uint8_t*>(S)[oFb + par];
-            if (f & F_UNK) {
-                float* p = S + oDb + par;
-                relax(p, reinterpret_cast<const float*>(base(q + 1)) + oDb + par,
-                      reinterpret_cast<const float*>(base(q - 1)) + oDb + par, sC(q), f, S[oRb + par]);
-            }
-            if (store_lane) {
-                float* o = ob + (long long)k * d.plane;
-                if (store_pair) {
-                    *reinterpret_cast<float2*>(o) = make_float2(S[oDb], S[oDb + 1]);
-                } else {
-                    *o = S[oDb];
+        // black on planes 2t and 2t+1 (interior rows), then their stores
+        if (black_lane) {
+#pragma unroll
+            for (int h = 0; h <= 1; ++h) {
+                const int q = 2 * t + h;
+                if (q < 2 || q > nq - 3) continue;
+                unsigned char* S = slot(q);
+                float* Sf = reinterpret_cast<float*>(S);
+                const int par = (pb0 + q) & 1;
+                const uint8_t f = S[oFb + par];
+                if (f & F_UNK) {
+                    float* p = Sf + oDb + par;
+                    relax(S, p, reinterpret_cast<const float*>(slot(q + 1)) + oDb + par,
+                          reinterpret_cast<const float*>(slot(q - 1)) + oDb + par, f, Sf[oRb + par]);
+                }
+                if (store_lane) {
+                    float* o = ob0 + (long long)q * d.plane;
+                    if (store_pair) {
+                        *reinterpret_cast<float2*>(o) = make_float2(Sf[oDb], Sf[oDb + 1]);
+                    } else {
+                        *o = Sf[oDb];
+                    }
                 }
             }
         }
@@ -738,7 +753,7 @@ bool encode3d(CUtensorMap* map, CUtensorMapDataType type, size_t es, void* base,
 // k-marching tiles (kFirstMarchCfg ..) as (TY, plane slots, threads)
 const int kTmaCfg[kNumTmaTiles][3] = {{8, 8, 256}, {12, 12, 512}, {16, 12, 512}, {16, 16, 512},
                                       {8, 8, 256}, {8, 8, 512}, {16, 8, 512}, {12, 12, 512},
-                                      {16, 6, 288}, {16, 8, 288}, {8, 8, 160}, {24, 6, 416}};
+                                      {16, 16, 288}, {12, 16, 224}, {8, 16, 160}, {8, 32, 160}};
 
 bool tma_supported(const Dom&) { return true; }
 
@@ -758,10 +773,10 @@ cudaError_t tma_prepare() {
     g_pipe_blocks[1] = pipe_blocks<8, 8, 512>();
     g_pipe_blocks[2] = pipe_blocks<16, 8, 512>();
     g_pipe_blocks[3] = pipe_blocks<12, 12, 512>();
-    if ((x = allow_march<16, 6>()) != cudaSuccess) e = x;
-    if ((x = allow_march<16, 8>()) != cudaSuccess) e = x;
-    if ((x = allow_march<8, 8>()) != cudaSuccess) e = x;
-    if ((x = allow_march<24, 6>()) != cudaSuccess) e = x;
+    if ((x = allow_march<16, 16>()) != cudaSuccess) e = x;
+    if ((x = allow_march<12, 16>()) != cudaSuccess) e = x;
+    if ((x = allow_march<8, 16>()) != cudaSuccess) e = x;
+    if ((x = allow_march<8, 32>()) != cudaSuccess) e = x;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -789,10 +804,10 @@ int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, const float* cn1tab
                    float* dout, int zero, Scalars* sc, cudaStream_t s) {
     const TmaMaps& m = maps[cfg];
     switch (cfg) {
-        case 8: launch_march_cfg<16, 6>(g, m, cn1tab, in, dout, kc, zero, sc, s); break;
-        case 9: launch_march_cfg<16, 8>(g, m, cn1tab, in, dout, kc, zero, sc, s); break;
-        case 10: launch_march_cfg<8, 8>(g, m, cn1tab, in, dout, kc, zero, sc, s); break;
-        case 11: launch_march_cfg<24, 6>(g, m, cn1tab, in, dout, kc, zero, sc, s); break;
+        case 8: launch_march_cfg<16, 16>(g, m, cn1tab, in, dout, kc, zero, sc, s); break;
+        case 9: launch_march_cfg<12, 16>(g, m, cn1tab, in, dout, kc, zero, sc, s); break;
+        case 10: launch_march_cfg<8, 16>(g, m, cn1tab, in, dout, kc, zero, sc, s); break;
+        case 11: launch_march_cfg<8, 32>(g, m, cn1tab, in, dout, kc, zero, sc, s); break;
         case 0: launch_tma_cfg<8, 8, 256>(g, m, in, dout, zero, sc, s); break;
         case 1: launch_tma_cfg<12, 12, 512>(g, m, in, dout, zero, sc, s); break;
         case 2: launch_tma_cfg<16, 12, 512>(g, m, in, dout, zero, sc, s); break;

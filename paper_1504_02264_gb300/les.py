@@ -25,6 +25,7 @@ LES_FP32, LES_FP64 = 0, 1
 LES_WARM_PREV, LES_WARM_NET, LES_WARM_ZERO = 0, 1, 2
 LES_SOR_REDBLACK, LES_SOR_TWINNED = 0, 1
 LES_SOR_NTILES = 29                 # sweep tile indices 0 .. LES_SOR_NTILES - 1 (les_set_sor_config)
+LES_NET_MMA_SYNC, LES_NET_TCGEN05 = 0, 1
 
 
 class les_grid_t(ctypes.Structure):
@@ -123,6 +124,8 @@ def lib(build_if_missing: bool = False):
         L.les_net_num_params.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
         L.les_net_set_stride.argtypes = [vp, i32]
         L.les_net_get_stride.argtypes = [vp, ctypes.POINTER(i32)]
+        L.les_net_set_engine.argtypes = [vp, i32]
+        L.les_net_get_engine.argtypes = [vp, ctypes.POINTER(i32)]
         L.les_net_get_params.argtypes = [vp, vp]
         L.les_net_set_params.argtypes = [vp, vp]
         L.les_net_forward.argtypes = [vp, vp, vp, vp, i32, i32, i32]
@@ -140,6 +143,7 @@ def lib(build_if_missing: bool = False):
                      "les_ensemble_set_graph", "les_ensemble_set_tile", "les_ensemble_get_tile",
                      "les_ensemble_autotune", "les_ensemble_launches", "les_ensemble_set_warmstart", "les_selftest_wait_timeout", "les_time_sor", "les_set_net_kernels", "les_set_net_start", "les_set_inflow_series", "les_set_record", "les_set_record_at", "les_set_net_schedule", "les_set_warmstart",
                      "les_net_create", "les_net_num_params", "les_net_set_stride", "les_net_get_stride",
+                     "les_net_set_engine", "les_net_get_engine",
                      "les_net_get_params", "les_net_set_params", "les_net_forward", "les_net_gradient",
                      "les_net_train_step", "les_residual_noalloc", "les_profiler_range", "les_set_graph",
                      "les_set_sor_config", "les_get_sor_config", "les_sor_tile", "les_autotune_sor",
@@ -282,6 +286,16 @@ def les_net_get_stride(n):
     return s.value
 
 
+def les_net_set_engine(n, engine):
+    return _ncheck(lib().les_net_set_engine(n, engine), n)
+
+
+def les_net_get_engine(n):
+    e = ctypes.c_int32()
+    _ncheck(lib().les_net_get_engine(n, ctypes.byref(e)), n)
+    return e.value
+
+
 def les_net_get_params(n, out):
     return _ncheck(lib().les_net_get_params(n, _ptr(out)), n)
 
@@ -322,6 +336,15 @@ class Net:
     @stride.setter
     def stride(self, s):
         les_net_set_stride(self.h, s)
+
+    @property
+    def engine(self):
+        """LES_NET_TCGEN05 (default) or LES_NET_MMA_SYNC: the forward convolutions' tensor-core path."""
+        return les_net_get_engine(self.h)
+
+    @engine.setter
+    def engine(self, e):
+        les_net_set_engine(self.h, e)
 
     def close(self):
         if getattr(self, "h", None):

@@ -59,6 +59,54 @@ def run_ensemble(a):
     ens.close()
 
 
+def run_engines(a):
+    """The learned step (network every --net-every sweeps) and one network
+    forward on the workload's residual, per convolution engine (tcgen05 and
+    the warp-level mma.sync kernel): host wall time per step, CUDA events
+    around the forward."""
+    import torch
+    sc = make(a.workload, a.seed)
+    z = np.load(a.net)
+    out = {"workload": a.workload, "cells": sc.ncells, "rows": []}
+    for name, eng in (("tcgen05", les.LES_NET_TCGEN05), ("mma.sync", les.LES_NET_MMA_SYNC)):
+        d = les.Domain(sc)
+        net = les.Net(seed=0, stride=int(z["stride"]))
+        net.set_params(z["params"])
+        net.engine = eng
+        for _ in range(a.warmup):
+            d.step(1)
+        d.set_warmstart(net)
+        d.set_net_schedule(a.net_every)
+        d.set_record(True)
+        d.step(1)
+        r = d.aux(les.LES_AUX_NET_IN)
+        m = d.aux(les.LES_AUX_MASK)
+        d.set_record(False)
+        sw = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            sw.append(d.step(1)["sweeps"])
+        torch.cuda.synchronize()
+        ms_step = (time.perf_counter() - t0) * 1e3 / a.steps
+        dr = torch.from_numpy(np.ascontiguousarray(r, np.float32)).cuda()
+        dm = torch.from_numpy(np.ascontiguousarray(m, np.float32)).cuda()
+        y = torch.empty_like(dr)
+        for _ in range(3):
+            les.les_net_forward(net.h, dr.data_ptr(), dm.data_ptr(), y.data_ptr(), sc.nx, sc.ny, sc.nz)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(20):
+            les.les_net_forward(net.h, dr.data_ptr(), dm.data_ptr(), y.data_ptr(), sc.nx, sc.ny, sc.nz)
+        ev1.record()
+        torch.cuda.synchronize()
+        out["rows"].append({"engine": name, "ms_per_step": ms_step, "sweeps": sw,
+                            "forward_ms": ev0.elapsed_time(ev1) / 20, "y_norm": float(y.norm().item())})
+        d.close()
+        net.close()
+    print(json.dumps(out))
+
+
 def make(workload: str, seed: int):
     if workload == "lattice":
         return scene.lattice_scene(seed)
@@ -97,9 +145,13 @@ def main():
     ap.add_argument("--twin-omega", type=float, default=0.9, help="relaxation of the twinned double buffer")
     ap.add_argument("--fixed-sweeps", type=int, default=0,
                     help="run exactly this many SOR sweeps per step (0: solve to the tolerance)")
+    ap.add_argument("--engines", action="store_true",
+                    help="with --net: learned step time and network forward time for each convolution engine")
     a = ap.parse_args()
     if a.workload == "ensemble":
         return run_ensemble(a)
+    if a.engines:
+        return run_engines(a)
     sc = make(a.workload, a.seed)
     if a.fixed_sweeps > 0:
         sc.fixed_sweeps, sc.max_sweeps = 1, a.fixed_sweeps

@@ -70,6 +70,14 @@ def net():
     n.close()
 
 
+def test_engine_setting(net):
+    assert net.engine == les.LES_NET_TCGEN05            # the default
+    net.engine = les.LES_NET_MMA_SYNC
+    assert net.engine == les.LES_NET_MMA_SYNC
+    with pytest.raises(les.LesError):
+        net.engine = 7
+
+
 def test_stride_setting(net):
     assert net.stride == 1
     net.stride = 4
@@ -87,15 +95,19 @@ def test_param_count_and_roundtrip(net):
     assert np.all(np.isfinite(net.params()))
 
 
+@pytest.mark.parametrize("engine", ["tcgen05", "mma.sync"])
 @pytest.mark.parametrize("shape,stride", [((7, 11, 37), 1), ((1, 1, 1), 1), ((5, 9, 16), 1), ((3, 4, 17), 1),
-                                          ((13, 22, 70), 2), ((17, 30, 61), 4), ((3, 5, 6), 4)])
-def test_forward_matches_oracle(net, shape, stride):
+                                          ((13, 22, 70), 2), ((17, 30, 61), 4), ((3, 5, 6), 4), ((9, 40, 19), 1)])
+def test_forward_matches_oracle(net, shape, stride, engine):
     """(nz, ny, nx) = 7x11x37 spans 3x3x4 tiles with ragged tails on every
-    level; the strided cases pool to ragged coarse grids and prolongate back."""
+    level; the strided cases pool to ragged coarse grids and prolongate back;
+    9x40x19 spans several 8x16 tiles of the tcgen05 kernel with ragged tails.
+    Both tensor-core engines (tcgen05 and warp-level mma.sync)."""
     rng = np.random.default_rng(sum(shape))
     theta = net_oracle.init_params(7).astype(np.float32)
     net.set_params(theta)
     net.stride = stride
+    net.engine = les.LES_NET_TCGEN05 if engine == "tcgen05" else les.LES_NET_MMA_SYNC
     r, mask = sample(rng, shape)
     if mask.sum() == 0:
         mask.flat[0] = 1.0
@@ -126,13 +138,15 @@ def test_forward_scale_invariant(net):
     assert np.array_equal(ys[0], ys[1])
 
 
+@pytest.mark.parametrize("engine", ["tcgen05", "mma.sync"])
 @pytest.mark.parametrize("shape,stride", [((5, 9, 21), 1), ((10, 17, 40), 2)])
-def test_gradient_matches_oracle(net, shape, stride):
+def test_gradient_matches_oracle(net, shape, stride, engine):
     rng = np.random.default_rng(2)
     B = 2
     theta = net_oracle.init_params(9).astype(np.float32)
     net.set_params(theta)
     net.stride = stride
+    net.engine = les.LES_NET_TCGEN05 if engine == "tcgen05" else les.LES_NET_MMA_SYNC
     rs, ms, ts = [], [], []
     for _ in range(B):
         r, m = sample(rng, shape)

@@ -69,11 +69,13 @@ def load_net():
 # ---------------------------------------------------------------------------
 # the network inside the solver, production grid and weights
 
-def test_solver_network_production_grid():
+@pytest.mark.parametrize("engine", ["tcgen05", "mma.sync"])
+def test_solver_network_production_grid(engine):
     sc = scene.random_scene(seed=0)          # 150 x 150 x 90, 100 buildings
     sc.check_every, sc.max_sweeps = 10, 20000
     d = les.Domain(sc)
     net = load_net()
+    net.engine = les.LES_NET_TCGEN05 if engine == "tcgen05" else les.LES_NET_MMA_SYNC
     try:
         assert net.stride == 8
         for _ in range(2):
@@ -91,7 +93,8 @@ def test_solver_network_production_grid():
         yo = net_oracle.forward_strided(theta, r, m, 8)
         err = rel_l2(q, yo)
         cos = float(np.dot(q.ravel(), yo.ravel()) / (np.linalg.norm(q) * np.linalg.norm(yo)))
-        print(f"solver network, 150x150x90 stride 8 (19x19x12 coarse): rel L2 {err:.3e}, cosine {cos:.6f}")
+        print(f"solver network ({engine}), 150x150x90 stride 8 (19x19x12 coarse): rel L2 {err:.3e}, "
+              f"cosine {cos:.6f}")
         assert err <= 2e-2 and cos >= 0.9998
         # the public forward entry on the same input (dense pooling path)
         shape = r.shape
