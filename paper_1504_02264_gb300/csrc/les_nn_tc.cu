@@ -43,7 +43,7 @@ constexpr int TCX = 8, TCY = 16, HX = TCX + 2, HY = TCY + 2, HZ = 3;
 constexpr int NVOX = HX * HY * HZ;                 // halo voxels per channel half
 constexpr uint32_t HALF_A = NVOX * 16;             // bytes of one 8-channel half of the halo block
 constexpr int NTH = 256;
-constexpr size_t kTcSmemFloor = 200 * 1024;
+constexpr size_t kTcSmemFloor = 0;
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -331,8 +331,9 @@ __global__ void __launch_bounds__(NTH) k_conv3_tc(ConvArgs A, const int* gate, i
     }
 }
 
-// dynamic shared memory per CTA: the two stages, rounded up so that every
-// address the descriptors can form stays inside the CTA's allocation
+// dynamic shared memory per CTA: the two stages (kTcSmemFloor > 0 rounds the
+// allocation up, so that any address a descriptor could form, with its
+// strides read either way round, stays inside the CTA's shared memory)
 template <int CO>
 constexpr size_t tc_smem() {
     return sizeof(TcSmem<CO>) > kTcSmemFloor ? sizeof(TcSmem<CO>) : kTcSmemFloor;

@@ -99,7 +99,8 @@ struct TmaTile {
     static constexpr uint32_t OFF_F = OFF_R + align_up(BYTES_R, 128);
     static constexpr uint32_t OFF_CN = OFF_F + align_up(BYTES_F, 128);
     static constexpr uint32_t OFF_CT = OFF_CN + RZ * 64 * 4;
-    static constexpr uint32_t OFF_BAR = align_up(OFF_CT + 2 * RZ * 4, 8);
+    static constexpr uint32_t OFF_T4 = align_up(OFF_CT + 2 * RZ * 4, 16);   // float4 [64]: ae, aw, an, as
+    static constexpr uint32_t OFF_BAR = OFF_T4 + 64 * 16;
     static constexpr uint32_t SMEM = OFF_BAR + 8;
 };
 
@@ -150,6 +151,11 @@ k_sor_tma(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtens
         float* p = &sD[0][0][0];
         for (int q = tid; q < DXW * DY * TT::DZ; q += NT) p[q] = 0.f;
     }
+    if (tid < 64) {
+        const float cx = g.cx, cy = g.cy;
+        reinterpret_cast<float4*>(sm + TT::OFF_T4)[tid] =
+            make_float4((tid & F_E) ? cx : 0.f, (tid & F_W) ? cx : 0.f, (tid & F_N) ? cy : 0.f, (tid & F_S) ? cy : 0.f);
+    }
     __syncthreads();
     bool ok = false;
     const uint64_t t0 = global_ns();
@@ -183,65 +189,77 @@ k_sor_tma(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtens
         }
         __syncthreads();
     }
-    const float omega = g.omega, cx = g.cx, cy = g.cy;
-    auto relax = [&](int x, int y, int z, int kz, uint8_t f, float rhs) {
-        const float ct = sCT[kz], cb = sCB[kz];
+    const float omega = g.omega;
+    const float4* T4 = reinterpret_cast<const float4*>(sm + TT::OFF_T4);
+    // the update of Sec. 2.6 at shared cell p (plane row kz of the block's
+    // coefficient rows), branch-free: the in-plane coefficients of the
+    // cell's open-face mask from T4, the vertical ones selected by the mask
+    auto relax = [&](float* p, int kz, uint8_t f, float rhs) {
+        constexpr int PZ = DY * DXW;
+        const float4 a = T4[f & 63];
         const float cn1 = sCN[kz][f & 63];
+        const float at = (f & F_T) ? sCT[kz] : 0.f, ab = (f & F_B) ? sCB[kz] : 0.f;
         float s = 0.f;
-        if ((f & 63) == 63) {
-            // all six faces open (most fluid cells): the same sum without the selects
-            s += cx * sD[z][y][x + 1];
-            s += cx * sD[z][y][x - 1];
-            s += cy * sD[z][y + 1][x];
-            s += cy * sD[z][y - 1][x];
-            s += ct * sD[z + 1][y][x];
-            s += cb * sD[z - 1][y][x];
-        } else {
-            const float ae = (f & F_E) ? cx : 0.f, aw = (f & F_W) ? cx : 0.f;
-            const float an = (f & F_N) ? cy : 0.f, as = (f & F_S) ? cy : 0.f;
-            const float at = (f & F_T) ? ct : 0.f, ab = (f & F_B) ? cb : 0.f;
-            s += ae * sD[z][y][x + 1];
-            s += aw * sD[z][y][x - 1];
-            s += an * sD[z][y + 1][x];
-            s += as * sD[z][y - 1][x];
-            s += at * sD[z + 1][y][x];
-            s += ab * sD[z - 1][y][x];
-        }
-        float own = sD[z][y][x];
+        s += a.x * p[1];
+        s += a.y * p[-1];
+        s += a.z * p[DXW];
+        s += a.w * p[-DXW];
+        s += at * p[PZ];
+        s += ab * p[-PZ];
+        float own = p[0];
         float reltmp = omega * (cn1 * (s - rhs) - own);
-        sD[z][y][x] = own + reltmp;
+        p[0] = own + reltmp;
     };
+    float* const D0 = &sD[0][0][0];
+    const float* const R0 = &sR[0][0][0];
+    const uint8_t* const F0 = &sF[0][0][0];
     const int half = lane >> 4, m = lane & 15;
+    const int par0 = (i0 + j0 + k0) & 1;
     // red (i+j+k odd) on the block + 1 ring (i0-1 .. i0+28): 15 per row, two rows per warp pass
-    for (int p = warp; 2 * p < RY * RZ; p += NW) {
-        const int rw = 2 * p + half;
-        if (rw < RY * RZ && m < (BX + 2) / 2) {
+    if (m < (BX + 2) / 2)
+        for (int p = warp; 2 * p < RY * RZ; p += NW) {
+            const int rw = 2 * p + half;
+            if (rw >= RY * RZ) break;
             const int jj = rw % RY, kk = rw / RY;
-            const int ii = 2 * m + ((i0 + (j0 - 1 + jj) + (k0 - 1 + kk)) & 1);   // i = i0 - 1 + ii
-            const uint8_t f = sF[kk][jj][ii + 3 + off];
-            if (f & F_UNK) relax(ii + 3, jj + 1, kk + 1, kk, f, sR[kk][jj][ii + 3]);
+            const int ii = 2 * m + ((par0 + jj + kk) & 1);                   // i = i0 - 1 + ii
+            const uint8_t f = F0[(kk * RY + jj) * FXW + ii + 3 + off];
+            if (f & F_UNK)
+                relax(D0 + ((kk + 1) * DY + jj + 1) * DXW + ii + 3, kk, f, R0[(kk * RY + jj) * DXW + ii + 3]);
         }
-    }
     __syncthreads();
     // black (i+j+k even) on the block (i0 .. i0+27): 14 per row
-    for (int p = warp; 2 * p < BY * BZ; p += NW) {
-        const int rw = 2 * p + half;
-        if (rw < BY * BZ && m < BX / 2) {
+    if (m < BX / 2)
+        for (int p = warp; 2 * p < BY * BZ; p += NW) {
+            const int rw = 2 * p + half;
+            if (rw >= BY * BZ) break;
             const int jj = rw % BY, kk = rw / BY;
-            const int ii = 2 * m + ((i0 + (j0 + jj) + (k0 + kk)) & 1);           // i = i0 + ii
-            const uint8_t f = sF[kk + 1][jj + 1][ii + 4 + off];
-            if (f & F_UNK) relax(ii + 4, jj + 2, kk + 2, kk + 1, f, sR[kk + 1][jj + 1][ii + 4]);
+            const int ii = 2 * m + ((par0 + jj + kk) & 1);                   // i = i0 + ii
+            const uint8_t f = F0[((kk + 1) * RY + jj + 1) * FXW + ii + 4 + off];
+            if (f & F_UNK)
+                relax(D0 + ((kk + 2) * DY + jj + 2) * DXW + ii + 4, kk + 1, f,
+                      R0[((kk + 1) * RY + jj + 1) * DXW + ii + 4]);
         }
-    }
     __syncthreads();
-    // store the block (cells that are not unknowns hold 0 in d and in the tile)
-    const int i = i0 + lane;
-    if (lane < BX && i <= d.nx) {
+    // store the block (cells that are not unknowns hold 0 in d and in the
+    // tile): 4 rows per warp pass, 7 lanes x 4 cells (16-byte aligned) per row
+    {
+        const int c = lane & 7, sub = lane >> 3;
+        const int i = i0 + 4 * c;
         const int kend = min(BZ, d.nz + 1 - k0), jend = min(BY, d.ny + 1 - j0);
-        for (int rw = warp; rw < BY * BZ; rw += NW) {
-            const int jj = rw % BY, kk = rw / BY;
-            if (jj < jend && kk < kend) dout[((k0 + kk) * d.py + j0 + jj) * d.px + i + OX] = sD[kk + 2][jj + 2][lane + 4];
-        }
+        if (c < BX / 4 && i <= d.nx)
+            for (int rw = 4 * warp + sub; rw < BY * BZ; rw += 4 * NW) {
+                const int jj = rw % BY, kk = rw / BY;
+                if (jj >= jend || kk >= kend) continue;
+                const float4 v = *reinterpret_cast<const float4*>(D0 + ((kk + 2) * DY + jj + 2) * DXW + 4 + 4 * c);
+                float* o = dout + d.at(i, j0 + jj, k0 + kk);
+                if (i + 3 <= d.nx) {
+                    *reinterpret_cast<float4*>(o) = v;
+                } else {
+                    o[0] = v.x;
+                    if (i + 1 <= d.nx) o[1] = v.y;
+                    if (i + 2 <= d.nx) o[2] = v.z;
+                }
+            }
     }
 }
 
@@ -753,7 +771,7 @@ bool encode3d(CUtensorMap* map, CUtensorMapDataType type, size_t es, void* base,
 // k-marching tiles (kFirstMarchCfg ..) as (TY, plane slots, threads)
 const int kTmaCfg[kNumTmaTiles][3] = {{8, 8, 256}, {12, 12, 512}, {16, 12, 512}, {16, 16, 512},
                                       {8, 8, 256}, {8, 8, 512}, {16, 8, 512}, {12, 12, 512},
-                                      {16, 16, 288}, {12, 16, 224}, {8, 16, 160}, {8, 32, 160}};
+                                      {16, 16, 288}, {16, 8, 288}, {8, 16, 160}, {8, 8, 160}};
 
 bool tma_supported(const Dom&) { return true; }
 
@@ -774,9 +792,9 @@ cudaError_t tma_prepare() {
     g_pipe_blocks[2] = pipe_blocks<16, 8, 512>();
     g_pipe_blocks[3] = pipe_blocks<12, 12, 512>();
     if ((x = allow_march<16, 16>()) != cudaSuccess) e = x;
-    if ((x = allow_march<12, 16>()) != cudaSuccess) e = x;
+    if ((x = allow_march<16, 8>()) != cudaSuccess) e = x;
     if ((x = allow_march<8, 16>()) != cudaSuccess) e = x;
-    if ((x = allow_march<8, 32>()) != cudaSuccess) e = x;
+    if ((x = allow_march<8, 8>()) != cudaSuccess) e = x;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -805,9 +823,9 @@ int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, const float* cn1tab
     const TmaMaps& m = maps[cfg];
     switch (cfg) {
         case 8: launch_march_cfg<16, 16>(g, m, cn1tab, in, dout, kc, zero, sc, s); break;
-        case 9: launch_march_cfg<12, 16>(g, m, cn1tab, in, dout, kc, zero, sc, s); break;
+        case 9: launch_march_cfg<16, 8>(g, m, cn1tab, in, dout, kc, zero, sc, s); break;
         case 10: launch_march_cfg<8, 16>(g, m, cn1tab, in, dout, kc, zero, sc, s); break;
-        case 11: launch_march_cfg<8, 32>(g, m, cn1tab, in, dout, kc, zero, sc, s); break;
+        case 11: launch_march_cfg<8, 8>(g, m, cn1tab, in, dout, kc, zero, sc, s); break;
         case 0: launch_tma_cfg<8, 8, 256>(g, m, in, dout, zero, sc, s); break;
         case 1: launch_tma_cfg<12, 12, 512>(g, m, in, dout, zero, sc, s); break;
         case 2: launch_tma_cfg<16, 12, 512>(g, m, in, dout, zero, sc, s); break;
