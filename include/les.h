@@ -436,11 +436,14 @@ int les_set_net_start(les_handle h, int32_t enable);
  * 16x4, 4x16; ctas_per_sm CTAs per SM walk the list) -- or, with `tile` 5,
  * one launch per member per sweep with the member's own kernel and tile
  * (les_set_sor_config / les_autotune_sor of the member; TMA where its grid
- * allows) -- one estimate and one
+ * allows) -- or, with `tile` 6, one persistent launch per sweep whose CTAs
+ * walk every member's 28 x 8 x 8 blocks with that member's tensor maps (the
+ * TMA block kernel of tile 17, ctas_per_sm ignored) -- one estimate and one
  * refinement launch per batch of check_every sweeps, chunks of batches in
  * CUDA graphs; each member stops at its own tolerance and sweep count.  A
  * member evolves bit-identically to the same domain stepped alone with the
- * same row tile (les_set_sor_config(h, 12 + tile, 0)).
+ * same row tile (les_set_sor_config(h, 12 + tile, 0)), or with tile 17 in
+ * the batched TMA mode.
  * Requirements (else LES_EINVAL): 1 <= n <= 64; every member FP32, tolerance
  * mode (fixed_sweeps = 0), the same even check_every, and max_sweeps a
  * multiple of it.  The ensemble keeps no pointer to the caller's arrays.

@@ -1,7 +1,8 @@
 // Ensembles of uneven domains stepped together: every member is an ordinary
 // FP32 domain handle (its own grid, buildings, inflow and state); the SOR
 // solve of all members runs as batched launches over a flattened
-// (member, tile) work list -- one persistent sweep launch per sweep, one
+// (member, tile) work list -- one persistent sweep launch per sweep (row
+// tiles, or the members' TMA blocks with per-member tensor maps), one
 // estimate launch and one refinement launch per batch for the whole ensemble
 // -- each member gated by its own `done` flag, so members of different size
 // stop at their own sweep counts.  Chunks of batches are captured in CUDA
@@ -26,6 +27,9 @@ constexpr int kEnsChunkBatches = 10;
 // tile index of the per-member mode: every member sweeps with its own kernel
 // and tile (TMA where its grid allows), one launch per member per sweep
 constexpr int kPerMember = kNumEnsTiles;
+// tile index of the batched TMA mode: one persistent launch per sweep walks
+// the 28 x 8 x 8 TMA blocks of every member (tensor maps per member)
+constexpr int kBatchedTma = kNumEnsTiles + 1;
 }
 
 struct les_ensemble_s {
@@ -43,6 +47,7 @@ struct les_ensemble_s {
     int max_sweeps = 0;                          // largest member budget
     int cur = 0;                                 // parity of the members' pressure buffers
     int* ndone = nullptr;                        // device counter of members whose solve ended
+    CUtensorMap* maps = nullptr;                 // 4 tensor maps per member (batched TMA mode), device
     int* all_done_host = nullptr;                // mapped pinned flag
     int* all_done_dev = nullptr;
     bool use_graph = true;
@@ -89,13 +94,30 @@ void fill_tables(les_ensemble_s* e) {
         T.all_done_host = e->all_done_dev;
         for (int i = 0; i < e->n; ++i) {
             les_handle h = e->mem[i];
-            member_fill(h, T.m[i], e->tile == kPerMember ? 0 : e->tile, par);
+            member_fill(h, T.m[i], e->tile >= kPerMember ? 0 : e->tile, par);
             T.sbeg[i + 1] = T.sbeg[i] + T.m[i].sgrid[0] * T.m[i].sgrid[1] * T.m[i].sgrid[2];
             T.ebeg[i + 1] = T.ebeg[i] + T.m[i].egrid[0] * T.m[i].egrid[1] * T.m[i].egrid[2];
             T.abeg[i + 1] = T.abeg[i] + T.m[i].agrid[0] * T.m[i].agrid[1] * T.m[i].agrid[2];
             T.rbeg[i + 1] = T.rbeg[i] + T.m[i].rblocks;
+            const Dom& d = T.m[i].g.d;
+            T.tbeg[i + 1] = T.tbeg[i] + ((d.nx + 27) / 28) * ((d.ny + kEnsTmaBy - 1) / kEnsTmaBy) *
+                                            ((d.nz + kEnsTmaBz - 1) / kEnsTmaBz);
         }
     }
+}
+
+// the members' tensor maps of the batched TMA mode (device pointers of a
+// member never change, so the maps are written once)
+int fill_maps(les_ensemble_s* e) {
+    std::vector<CUtensorMap> h(4 * (size_t)e->n);
+    const EnsTab<float>& T = *e->tab[0];
+    for (int i = 0; i < e->n; ++i) {
+        const EnsMember<float>& M = T.m[i];
+        if (!tma_encode_member(M.g.d, M.dl[0], M.dl[1], M.rr, M.g.flags, &h[4 * (size_t)i]))
+            return efail(e, LES_ECUDA, "tensor maps of member %d could not be encoded", i);
+    }
+    ECK(cudaMemcpy(e->maps, h.data(), h.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+    return LES_OK;
 }
 
 CondArgs eargs(const les_ensemble_s* e, int mode, int n, int gate) {
@@ -118,6 +140,8 @@ int launch_chunk(les_ensemble_s* e, const EnsTab<float>& T, cudaStream_t s) {
             if (e->tile == kPerMember) {
                 for (les_handle h : e->mem) member_sweep(h, dcur, q == 0 ? 2 : 0, s);
                 e->launches += e->n;
+            } else if (e->tile == kBatchedTma) {
+                e->launches += launch_sor_tma_ens(T, e->maps, dcur, q == 0 ? 2 : 0, e->ctas, s);
             } else {
                 e->launches += launch_sor_ens(T, dcur, q == 0 ? 2 : 0, e->ctas, s);
             }
@@ -174,6 +198,10 @@ int choose_ctas(les_ensemble_s* e, int per_sm) {
         e->ctas = 0;
         return LES_OK;
     }
+    if (e->tile == kBatchedTma) {       // every resident CTA (the items are many small blocks)
+        e->ctas = std::max(1, std::min(e->tab[0]->tbeg[e->n], sor_tma_ens_resident()));
+        return LES_OK;
+    }
     int occ = 0;
     // the sweep kernels are opted in to their shared memory at member creation
     const int smem = ens_rows_smem(e->tile);
@@ -191,6 +219,7 @@ void release(les_ensemble_s* e) {
     }
     if (e->cap) cudaStreamDestroy(e->cap);
     if (e->ndone) cudaFree(e->ndone);
+    if (e->maps) cudaFree(e->maps);
     if (e->all_done_host) cudaFreeHost(e->all_done_host);
     for (les_handle h : e->mem) les_destroy(h);
     e->mem.clear();
@@ -237,6 +266,7 @@ int les_ensemble_create(int32_t n, const les_grid_t* grids, const uint8_t* const
         if (!e->tab[c]) rc = LES_ENOMEM;
     }
     if (!rc && cudaMalloc(&e->ndone, sizeof(int)) != cudaSuccess) rc = LES_ENOMEM;
+    if (!rc && cudaMalloc(&e->maps, 4 * (size_t)n * sizeof(CUtensorMap)) != cudaSuccess) rc = LES_ENOMEM;
     if (!rc && cudaHostAlloc(&e->all_done_host, sizeof(int), cudaHostAllocMapped) != cudaSuccess) rc = LES_ENOMEM;
     if (!rc && cudaHostGetDevicePointer(&e->all_done_dev, e->all_done_host, 0) != cudaSuccess) rc = LES_ECUDA;
     if (!rc && cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking) != cudaSuccess) rc = LES_ECUDA;
@@ -253,6 +283,11 @@ int les_ensemble_create(int32_t n, const les_grid_t* grids, const uint8_t* const
     e->tile = 0;
     fill_tables(e);
     choose_ctas(e, 4);
+    if ((rc = fill_maps(e))) {
+        release(e);
+        delete e;
+        return rc;
+    }
     *out = e;
     return LES_OK;
 }
@@ -287,7 +322,7 @@ int les_ensemble_set_graph(les_ensemble e, int32_t enable) {
 
 int les_ensemble_set_tile(les_ensemble e, int32_t tile, int32_t ctas_per_sm) {
     if (!e) return LES_EINVAL;
-    if (tile < 0 || tile > kPerMember) return efail(e, LES_EINVAL, "tile must be 0..%d", kPerMember);
+    if (tile < 0 || tile > kBatchedTma) return efail(e, LES_EINVAL, "tile must be 0..%d", kBatchedTma);
     if (ctas_per_sm < 1 || ctas_per_sm > 8) return efail(e, LES_EINVAL, "ctas_per_sm must be 1..8");
     e->tile = tile;
     fill_tables(e);
@@ -435,6 +470,26 @@ int les_ensemble_autotune(les_ensemble e, int32_t sweeps, double* best_ms_per_sw
         if (ms / sweeps < best) {
             best = ms / sweeps;
             best_tile = kPerMember;
+        }
+    }
+    {
+        // the batched TMA mode: one persistent launch per sweep over every member's blocks
+        e->tile = kBatchedTma;
+        fill_tables(e);
+        choose_ctas(e, 4);
+        const EnsTab<float>& T = *e->tab[e->cur];
+        launch_sor_tma_ens(T, e->maps, 0, 0, e->ctas, s);
+        launch_sor_tma_ens(T, e->maps, 1, 0, e->ctas, s);
+        ECK(cudaEventRecord(a, s));
+        for (int q = 0; q < sweeps; ++q) launch_sor_tma_ens(T, e->maps, q & 1, 0, e->ctas, s);
+        ECK(cudaEventRecord(b, s));
+        ECK(cudaEventSynchronize(b));
+        ECK(cudaGetLastError());
+        float ms = 0.f;
+        ECK(cudaEventElapsedTime(&ms, a, b));
+        if (ms / sweeps < best) {
+            best = ms / sweeps;
+            best_tile = kBatchedTma;
         }
     }
     cudaEventDestroy(a);

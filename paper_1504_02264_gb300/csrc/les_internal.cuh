@@ -209,6 +209,7 @@ struct EnsTab {
     int ebeg[kMaxMembers + 1];
     int abeg[kMaxMembers + 1];
     int rbeg[kMaxMembers + 1];
+    int tbeg[kMaxMembers + 1];      // first item of each member in the batched TMA sweep's list
     int* ndone;                     // members whose solve has ended (device counter)
     int* all_done_host;             // mapped host flag set when ndone reaches n
     EnsMember<T> m[kMaxMembers];
@@ -255,6 +256,14 @@ bool tma_encode(const Dom& d, float* dl0, float* dl1, float* rr, uint8_t* flags,
 int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, const float* cn1tab, int cfg, int kc, int in,
                    float* dout, int zero, Scalars* sc, cudaStream_t s);
 int launch_cn1_table(const Geo<float>& g, float* tab, cudaStream_t s);
+// batched TMA sweep of an ensemble (les_sor_tma.cu): the 28 x 8 x 8 blocks of
+// every member in one persistent launch; maps = 4 tensor maps per member
+// (d[0], d[1], r, flags) in global memory, encoded by tma_encode_member
+constexpr int kEnsTmaBy = 8, kEnsTmaBz = 8;
+bool tma_encode_member(const Dom& d, float* dl0, float* dl1, float* rr, const uint8_t* flags, CUtensorMap* out4);
+int launch_sor_tma_ens(const EnsTab<float>& tab, const CUtensorMap* maps, int in, int zero, int ctas,
+                       cudaStream_t s);
+int sor_tma_ens_resident();     // resident CTAs of the batched TMA sweep on this device
 template <typename T> int launch_diag_table(const Geo<T>& g, double* tab, cudaStream_t s);
 // comparison of SOR variants (les_sor_compare)
 template <typename T> int launch_cmp_residual(const Geo<T>& g, const double* p, const double* b, T* r,

@@ -104,37 +104,36 @@ struct TmaTile {
     static constexpr uint32_t SMEM = OFF_BAR + 8;
 };
 
+// One block (bx, by, bz) of the fused sweep on the CTA's shared memory sm,
+// whose mbarrier (initialised by the caller) completes phase `phase` when the
+// block's copies have landed.  Returns false after recording a timed-out
+// wait.  The caller separates two blocks on one CTA by a barrier.
 template <int BY, int BZ, int NT>
-__global__ void __launch_bounds__(NT)
-k_sor_tma(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtensorMap tr,
-          const __grid_constant__ CUtensorMap tf, Geo<float> g, const float* __restrict__ din,
-          const float* __restrict__ rin, float* __restrict__ dout, int zero_arg, Scalars* __restrict__ sc) {
+__device__ __forceinline__ bool sor_tma_block(unsigned char* sm, const CUtensorMap* td, const CUtensorMap* tr,
+                                              const CUtensorMap* tf, const Geo<float>& g,
+                                              const float* __restrict__ din, const float* __restrict__ rin,
+                                              float* __restrict__ dout, bool zero_start, Scalars* __restrict__ sc,
+                                              int bx, int by, int bz, uint32_t phase) {
     using TT = TmaTile<BY, BZ>;
     constexpr int BX = TT::BX, DXW = TT::DXW, FXW = TT::FXW, DY = TT::DY, RY = TT::RY, RZ = TT::RZ;
-    extern __shared__ __align__(128) unsigned char sm[];
     float(*sD)[DY][DXW] = reinterpret_cast<float(*)[DY][DXW]>(sm);
     float(*sR)[RY][DXW] = reinterpret_cast<float(*)[RY][DXW]>(sm + TT::OFF_R);
     uint8_t(*sF)[RY][FXW] = reinterpret_cast<uint8_t(*)[RY][FXW]>(sm + TT::OFF_F);
     float(*sCN)[64] = reinterpret_cast<float(*)[64]>(sm + TT::OFF_CN);
     float* sCT = reinterpret_cast<float*>(sm + TT::OFF_CT);
     float* sCB = sCT + RZ;
-    pdl_wait();
-    if (sc->done) return;
     const Dom& d = g.d;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = NT / 32;
-    const int i0 = 1 + blockIdx.x * BX, j0 = 1 + blockIdx.y * BY, k0 = 1 + blockIdx.z * BZ;
-    const int xd = blockIdx.x * BX;           // padded column of i0 - 4
+    const int i0 = 1 + bx * BX, j0 = 1 + by * BY, k0 = 1 + bz * BZ;
+    const int xd = bx * BX;                   // padded column of i0 - 4
     const int xf = xd & ~15, off = xd - xf;
-    const bool zero_start = zero_arg == 1 || (zero_arg == 2 && sc->zflag);
     const uint32_t bar = smem_u32(sm + TT::OFF_BAR);
     if (tid == 0) {
-        mbar_init(bar, 1);
-        mbar_fence_init();
         mbar_expect_tx(bar, TT::BYTES_R + TT::BYTES_F + (zero_start ? 0u : TT::BYTES_D));
-        if (!zero_start) tma_load_3d(smem_u32(sD), &td, xd, j0 - 2, k0 - 2, bar);
-        tma_load_3d(smem_u32(sR), &tr, xd, j0 - 1, k0 - 1, bar);
-        tma_load_3d(smem_u32(sF), &tf, xf, j0 - 1, k0 - 1, bar);
+        if (!zero_start) tma_load_3d(smem_u32(sD), td, xd, j0 - 2, k0 - 2, bar);
+        tma_load_3d(smem_u32(sR), tr, xd, j0 - 1, k0 - 1, bar);
+        tma_load_3d(smem_u32(sF), tf, xf, j0 - 1, k0 - 1, bar);
     }
     // per-plane coefficients and the block's rows of the cn1 table while the copies fly
     for (int q = tid; q < RZ * 64; q += NT) {
@@ -159,14 +158,14 @@ k_sor_tma(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtens
     __syncthreads();
     bool ok = false;
     const uint64_t t0 = global_ns();
-    while (!(ok = mbar_try_wait(bar, 0)))
+    while (!(ok = mbar_try_wait(bar, phase)))
         if (global_ns() - t0 > 1000000000ull) break;
     if (!__syncthreads_and(ok)) {
         if (tid == 0) atomicExch(&sc->timeout, 1);
         const uint64_t t1 = global_ns();     // give copies still in flight a bounded chance to land
-        while (!mbar_try_wait(bar, 0))
+        while (!mbar_try_wait(bar, phase))
             if (global_ns() - t1 > 1000000000ull) break;
-        return;
+        return false;
     }
     if ((d.perx && (i0 - 2 < 1 || i0 + BX + 1 > d.nx)) || (d.pery && (j0 - 2 < 1 || j0 + BY + 1 > d.ny)) ||
         (d.perz && (k0 - 2 < 1 || k0 + BZ + 1 > d.nz))) {
@@ -260,6 +259,70 @@ k_sor_tma(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtens
                     if (i + 2 <= d.nx) o[2] = v.z;
                 }
             }
+    }
+    return true;
+}
+
+template <int BY, int BZ, int NT>
+__global__ void __launch_bounds__(NT)
+k_sor_tma(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtensorMap tr,
+          const __grid_constant__ CUtensorMap tf, Geo<float> g, const float* __restrict__ din,
+          const float* __restrict__ rin, float* __restrict__ dout, int zero_arg, Scalars* __restrict__ sc) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    pdl_wait();
+    if (sc->done) return;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(sm + TmaTile<BY, BZ>::OFF_BAR), 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const bool zero_start = zero_arg == 1 || (zero_arg == 2 && sc->zflag);
+    sor_tma_block<BY, BZ, NT>(sm, &td, &tr, &tf, g, din, rin, dout, zero_start, sc, blockIdx.x, blockIdx.y, blockIdx.z,
+                              0u);
+}
+
+// The batched sweep of an ensemble: persistent CTAs walk the flattened list
+// of every member's 28 x BY x BZ blocks (member m owns items tbeg[m] ..
+// tbeg[m+1]-1) and sweep each block of the members whose solve is still
+// running, with the member's own tensor maps (four per member in global
+// memory: d[0], d[1], r, flags) and arguments -- the single-domain block
+// kernel's arithmetic, so a member evolves as it would alone with tile 17.
+// One launch per sweep covers every member.
+template <int BY, int BZ, int NT>
+__global__ void __launch_bounds__(NT)
+k_sor_tma_ens(const __grid_constant__ EnsTab<float> tab, const CUtensorMap* __restrict__ maps, int in, int zero_arg) {
+    using TT = TmaTile<BY, BZ>;
+    extern __shared__ __align__(128) unsigned char sm[];
+    pdl_wait();
+    const int n = tab.n, total = tab.tbeg[n];
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(sm + TT::OFF_BAR), 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    int m = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        while (t >= tab.tbeg[m + 1]) ++m;          // items of a CTA increase, so m only advances
+        const EnsMember<float>& M = tab.m[m];
+        Scalars* sc = M.red.sc;
+        if (*(volatile const int*)&sc->done) continue;
+        const Dom& d = M.g.d;
+        const int gx = (d.nx + TT::BX - 1) / TT::BX, gy = (d.ny + BY - 1) / BY;
+        const int q = t - tab.tbeg[m];
+        const int bx = q % gx, by = (q / gx) % gy, bz = q / (gx * gy);
+        const bool zero_start = zero_arg == 1 || (zero_arg == 2 && sc->zflag);
+        const CUtensorMap* mm = maps + 4 * m;
+        if (threadIdx.x == 0)       // the maps were written through the generic proxy (a host copy)
+            for (int c = 0; c < 4; ++c)
+                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mm + c) : "memory");
+        if (!sor_tma_block<BY, BZ, NT>(sm, mm + in, mm + 2, mm + 3, M.g, M.dl[in], M.rr, M.dl[1 - in], zero_start, sc,
+                                       bx, by, bz, phase))
+            return;
+        phase ^= 1u;
+        // the next block's copies overwrite the tiles: every thread is done with them
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
     }
 }
 
@@ -714,6 +777,7 @@ cudaError_t allow_march() {
 }
 
 int g_sms = 0;
+int g_ens_tma_resident = 0;     // resident CTAs of the batched TMA ensemble sweep (set at prepare)
 
 // planes per chunk: kc > 0 as given; kc <= 0: whole columns when they give at
 // least two CTAs per SM, else the chunk length that does (at least 4 planes)
@@ -798,6 +862,13 @@ cudaError_t tma_prepare() {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    if ((x = cudaFuncSetAttribute(k_sor_tma_ens<kEnsTmaBy, kEnsTmaBz, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)TmaTile<kEnsTmaBy, kEnsTmaBz>::SMEM)) != cudaSuccess)
+        e = x;
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sor_tma_ens<kEnsTmaBy, kEnsTmaBz, 256>, 256,
+                                                  TmaTile<kEnsTmaBy, kEnsTmaBz>::SMEM);
+    g_ens_tma_resident = g_sms * (per > 0 ? per : 1);
     return e;
 }
 
@@ -836,6 +907,26 @@ int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, const float* cn1tab
         case 7: launch_pipe_cfg<12, 12, 512>(g, m, cn1tab, in, dout, zero, sc, s, 3); break;
         default: break;
     }
+    return 1;
+}
+
+bool tma_encode_member(const Dom& d, float* dl0, float* dl1, float* rr, const uint8_t* flags, CUtensorMap* out4) {
+    constexpr int by = kEnsTmaBy, bz = kEnsTmaBz;
+    return encode3d(&out4[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, dl0, d, 36, by + 4, bz + 4) &&
+           encode3d(&out4[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, dl1, d, 36, by + 4, bz + 4) &&
+           encode3d(&out4[2], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, rr, d, 36, by + 2, bz + 2) &&
+           encode3d(&out4[3], CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, const_cast<uint8_t*>(flags), d, 48, by + 2, bz + 2);
+}
+
+int sor_tma_ens_resident() { return g_ens_tma_resident; }
+
+int launch_sor_tma_ens(const EnsTab<float>& tab, const CUtensorMap* maps, int in, int zero, int ctas,
+                       cudaStream_t s) {
+    const int total = tab.tbeg[tab.n];
+    const int grid = ctas < total ? ctas : total;
+    if (grid < 1) return 0;
+    launch_pdl(k_sor_tma_ens<kEnsTmaBy, kEnsTmaBz, 256>, dim3(grid), dim3(256), TmaTile<kEnsTmaBy, kEnsTmaBz>::SMEM,
+               s, tab, maps, in, zero);
     return 1;
 }
 
