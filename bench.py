@@ -368,6 +368,24 @@ def ensemble_leg(les, net, steps):
             out[mode] = {"steps": k, "ms_per_step": ms, "mcell_steps_per_s": cells / (ms * 1e-3) / 1e6,
                          "slowest_member_sweeps": float(np.mean(sw)), "max_rel_residual": worst,
                          "launches_per_step": (ens.launches() - l0) / k}
+        # the plain step again as one persistent cooperative launch per step
+        for m, s in zip(ens.members, states):
+            m.set_state(s)
+        ens.set_persistent(True)
+        l0 = ens.launches()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = ens.step(1)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3
+        if st[0]["rc"] != 0:
+            raise RuntimeError("ensemble persistent step did not converge")
+        out["plain_persistent"] = {"steps": 1, "ms_per_step": ms, "mcell_steps_per_s": cells / (ms * 1e-3) / 1e6,
+                                   "slowest_member_sweeps": float(max(x["sweeps"] for x in st)),
+                                   "max_rel_residual": max(x["rel_residual"] for x in st),
+                                   "launches_per_step": ens.launches() - l0,
+                                   "note": "the whole SOR solve of all members in one cooperative launch"}
+        ens.set_persistent(False)
         out["learned_speedup_vs_plain"] = out["plain"]["ms_per_step"] / out["learned"]["ms_per_step"]
         out["note"] = "host wall time around ens.step (CUDA graphs inside); tolerance 1e-6 per member"
     finally:

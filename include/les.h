@@ -467,6 +467,18 @@ int les_ensemble_set_tile(les_ensemble e, int32_t tile, int32_t ctas_per_sm);
 int les_ensemble_get_tile(les_ensemble e, int32_t* tile, int32_t* ctas);
 int les_ensemble_autotune(les_ensemble e, int32_t sweeps, double* best_ms_per_sweep);
 int les_ensemble_launches(les_ensemble e, int64_t* launches);
+/* les_ensemble_set_persistent: 1 runs the SOR solve of every plain-SOR step
+ * (no network set with les_ensemble_set_warmstart) as one persistent
+ * cooperative launch per step: its CTAs walk, batch after batch, every
+ * running member's TMA blocks for each sweep, then the estimates, the FP64
+ * accumulations and residuals with their stop decisions, separated by a
+ * bounded grid barrier, until every member's solve has ended; the launches
+ * of a step do not depend on its sweeps.  Selects the batched TMA mode
+ * (tile 6, whose arithmetic it shares bit for bit).  With a network the
+ * ensemble keeps its chunk graphs.  LES_EINVAL if the device cannot run a
+ * cooperative launch; a grid barrier that times out makes the step return
+ * LES_ETIMEOUT.  0 (default) returns to the chunk graphs. */
+int les_ensemble_set_persistent(les_ensemble e, int32_t enable);
 /* les_ensemble_set_warmstart: every member applies the learned correction
  * `net` at the start of its solve and every `every_sweeps` sweeps inside it
  * (even, dividing each member's max_sweeps; the batch size of the ensemble's

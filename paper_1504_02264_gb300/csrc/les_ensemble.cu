@@ -48,6 +48,9 @@ struct les_ensemble_s {
     int cur = 0;                                 // parity of the members' pressure buffers
     int* ndone = nullptr;                        // device counter of members whose solve ended
     CUtensorMap* maps = nullptr;                 // 4 tensor maps per member (batched TMA mode), device
+    bool persistent = false;                     // plain-SOR solves as one persistent launch per step
+    unsigned* pbar = nullptr;                    // its grid-barrier state [2] and error flag
+    int* perr = nullptr;
     int* all_done_host = nullptr;                // mapped pinned flag
     int* all_done_dev = nullptr;
     bool use_graph = true;
@@ -220,6 +223,8 @@ void release(les_ensemble_s* e) {
     if (e->cap) cudaStreamDestroy(e->cap);
     if (e->ndone) cudaFree(e->ndone);
     if (e->maps) cudaFree(e->maps);
+    if (e->pbar) cudaFree(e->pbar);
+    if (e->perr) cudaFree(e->perr);
     if (e->all_done_host) cudaFreeHost(e->all_done_host);
     for (les_handle h : e->mem) les_destroy(h);
     e->mem.clear();
@@ -267,6 +272,8 @@ int les_ensemble_create(int32_t n, const les_grid_t* grids, const uint8_t* const
     }
     if (!rc && cudaMalloc(&e->ndone, sizeof(int)) != cudaSuccess) rc = LES_ENOMEM;
     if (!rc && cudaMalloc(&e->maps, 4 * (size_t)n * sizeof(CUtensorMap)) != cudaSuccess) rc = LES_ENOMEM;
+    if (!rc && cudaMalloc(&e->pbar, 2 * sizeof(unsigned)) != cudaSuccess) rc = LES_ENOMEM;
+    if (!rc && cudaMalloc(&e->perr, sizeof(int)) != cudaSuccess) rc = LES_ENOMEM;
     if (!rc && cudaHostAlloc(&e->all_done_host, sizeof(int), cudaHostAllocMapped) != cudaSuccess) rc = LES_ENOMEM;
     if (!rc && cudaHostGetDevicePointer(&e->all_done_dev, e->all_done_host, 0) != cudaSuccess) rc = LES_ECUDA;
     if (!rc && cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking) != cudaSuccess) rc = LES_ECUDA;
@@ -376,7 +383,18 @@ int les_ensemble_step(les_ensemble e, int32_t nsteps, les_stats_t* stats) {
                 int rc = member_net_start(h, s);
                 if (rc) return efail(e, rc, "member network start: %s", les_last_error(h));
             }
-        for (int c = 0; c < max_chunks; ++c) {
+        const bool persist = e->persistent && !e->net && e->tile == kBatchedTma;
+        if (persist) {
+            // the whole solve of every member in one cooperative launch
+            ECK(cudaMemsetAsync(e->pbar, 0, 2 * sizeof(unsigned), s));
+            ECK(cudaMemsetAsync(e->perr, 0, sizeof(int), s));
+            const int batches = (e->max_sweeps + e->cycle - 1) / e->cycle + 1;
+            const int rc = launch_ens_persist(T, e->maps, e->cycle, batches, eargs(e, RES_LOOP, e->cycle, 1), e->pbar,
+                                              e->perr, s);
+            if (rc < 0) return efail(e, LES_ECUDA, "the persistent ensemble solve could not be launched");
+            e->launches += rc;
+        }
+        for (int c = 0; c < max_chunks && !persist; ++c) {
             if (e->use_graph) {
                 ECK(cudaGraphLaunch(e->chunk[par], s));
                 e->launches += kEnsChunkBatches * (e->cycle + 3 + (e->net ? 22 * e->n : 0));
@@ -399,6 +417,11 @@ int les_ensemble_step(les_ensemble e, int32_t nsteps, les_stats_t* stats) {
         e->cur = 1 - e->cur;
     }
     ECK(cudaStreamSynchronize(s));
+    if (e->persistent) {
+        int perr = 0;
+        ECK(cudaMemcpy(&perr, e->perr, sizeof(int), cudaMemcpyDeviceToHost));
+        if (perr) return efail(e, LES_ETIMEOUT, "a bounded wait of the persistent ensemble solve timed out");
+    }
     int worst = LES_OK;
     for (int i = 0; i < e->n; ++i) {
         int rc = member_stats(e->mem[i], stats ? &stats[i] : nullptr);
@@ -523,6 +546,20 @@ int les_ensemble_set_warmstart(les_ensemble e, les_net net, int32_t every_sweeps
     e->net_gen.assign(e->mem.size(), -1);
     fill_tables(e);
     invalidate(e);
+    return LES_OK;
+}
+
+int les_ensemble_set_persistent(les_ensemble e, int32_t enable) {
+    if (!e) return LES_EINVAL;
+    if (enable && ens_persist_grid() <= 0)
+        return efail(e, LES_EINVAL, "this device cannot run the cooperative persistent solve");
+    e->persistent = enable != 0;
+    if (e->persistent && e->tile != kBatchedTma) {
+        e->tile = kBatchedTma;
+        fill_tables(e);
+        choose_ctas(e, 4);
+        invalidate(e);
+    }
     return LES_OK;
 }
 

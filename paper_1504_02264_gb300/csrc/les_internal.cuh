@@ -264,6 +264,13 @@ bool tma_encode_member(const Dom& d, float* dl0, float* dl1, float* rr, const ui
 int launch_sor_tma_ens(const EnsTab<float>& tab, const CUtensorMap* maps, int in, int zero, int ctas,
                        cudaStream_t s);
 int sor_tma_ens_resident();     // resident CTAs of the batched TMA sweep on this device
+// the plain-SOR solve of an ensemble as one persistent cooperative launch
+// (les_kernels.cu); bar: 2 zeroed unsigned of grid-barrier state, err: a
+// zeroed device flag set when a bounded wait gave up; returns the launches
+// (1), or -1 when the device cannot run it
+int launch_ens_persist(const EnsTab<float>& tab, const CUtensorMap* maps, int cycle, int batches, const CondArgs& ca,
+                       unsigned* bar, int* err, cudaStream_t s);
+int ens_persist_grid();
 template <typename T> int launch_diag_table(const Geo<T>& g, double* tab, cudaStream_t s);
 // comparison of SOR variants (les_sor_compare)
 template <typename T> int launch_cmp_residual(const Geo<T>& g, const double* p, const double* b, T* r,

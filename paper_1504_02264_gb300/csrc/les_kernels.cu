@@ -8,6 +8,7 @@
 #include <type_traits>
 
 #include "les_internal.cuh"
+#include "les_tma.cuh"
 
 namespace les {
 
@@ -908,8 +909,9 @@ __device__ __forceinline__ int residual64_body(const Geo<T>& g, const double* ph
     const int n = d.nx * d.ny * d.nz;
     const double mean = red.sc->rhs_mean;
     const bool init = ca.mode == RES_INIT;
+    const int nt = blockDim.x * blockDim.y, tid = threadIdx.x + blockDim.x * threadIdx.y;    // 1-D or 32 x 8
     double x[3] = {0.0, 0.0, 0.0};
-    for (int q = b * blockDim.x + threadIdx.x; q < n; q += nb * blockDim.x) {
+    for (int q = b * nt + tid; q < n; q += nb * nt) {
         int i, j, k;
         cell_of(d, q, i, j, k);
         long long c = d.at(i, j, k);
@@ -1590,6 +1592,169 @@ __global__ void __launch_bounds__(256) k_residual64_ens(const __grid_constant__ 
         const int v = atomicAdd(tab.ndone, 1) + 1;
         if (v == tab.n && tab.all_done_host) *(volatile int*)tab.all_done_host = 1;
     }
+}
+
+// ---------------------------------------------------------------------------
+// The plain-SOR solve of an ensemble in one persistent cooperative launch:
+// every CTA walks, batch after batch, the flattened items of each phase --
+// `cycle` sweeps over every running member's 28 x 8 x 8 TMA blocks (with the
+// member's tensor maps), the estimate, the gated FP64 accumulation and the
+// gated FP64 residual with its stop decision -- the same per-item bodies as
+// the batched launches, separated by a bounded grid barrier, until every
+// member's solve has ended.  Members that have stopped are skipped.  The
+// launch count of a step no longer depends on its sweeps.
+
+// bounded grid barrier (1 s of global time); false on a timeout (recorded)
+__device__ bool ens_grid_barrier(unsigned* bar, int* err) {
+    __shared__ int ok_sh;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned* count = bar;
+        unsigned* gen = bar + 1;
+        const unsigned g0 = *(volatile unsigned*)gen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(count, 1u) == gridDim.x - 1) {
+            *(volatile unsigned*)count = 0u;
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            const uint64_t t0 = tma::global_ns();
+            while (*(volatile unsigned*)gen == g0)
+                if (tma::global_ns() - t0 > 1000000000ull) {
+                    ok = 0;
+                    atomicExch(err, 1);
+                    break;
+                }
+        }
+        __threadfence();
+        ok_sh = ok && !*(volatile int*)err;
+    }
+    __syncthreads();
+    return ok_sh != 0;
+}
+
+__global__ void __launch_bounds__(256) k_ens_persist(const __grid_constant__ EnsTab<float> tab,
+                                                     const CUtensorMap* __restrict__ maps, int cycle, int batches,
+                                                     CondArgs ca, unsigned* bar, int* err) {
+    using TT = tma::TmaTile<kEnsTmaBy, kEnsTmaBz>;
+    extern __shared__ __align__(128) unsigned char psm[];
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int n = tab.n;
+    if (tid == 0) {
+        tma::mbar_init(tma::smem_u32(psm + TT::OFF_BAR), 1);
+        tma::mbar_fence_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    for (int b = 0; b < batches; ++b) {
+        for (int s = 0; s < cycle; ++s) {
+            const int in = s & 1;
+            int m = 0;
+            for (int t = blockIdx.x; t < tab.tbeg[n]; t += gridDim.x) {
+                while (t >= tab.tbeg[m + 1]) ++m;
+                const EnsMember<float>& M = tab.m[m];
+                Scalars* sc = M.red.sc;
+                if (*(volatile const int*)&sc->done) continue;
+                const Dom& d = M.g.d;
+                const int gx = (d.nx + TT::BX - 1) / TT::BX, gy = (d.ny + kEnsTmaBy - 1) / kEnsTmaBy;
+                const int q = t - tab.tbeg[m];
+                const bool zero_start = s == 0 && sc->zflag;
+                const CUtensorMap* mm = maps + 4 * m;
+                if (tid == 0)
+                    for (int c = 0; c < 4; ++c)
+                        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mm + c) : "memory");
+                if (!tma::sor_tma_block<kEnsTmaBy, kEnsTmaBz, 256>(psm, mm + in, mm + 2, mm + 3, M.g, M.dl[in], M.rr,
+                                                                    M.dl[1 - in], zero_start, sc, q % gx,
+                                                                    (q / gx) % gy, q / (gx * gy), phase)) {
+                    if (tid == 0) atomicExch(err, 1);
+                    break;
+                }
+                phase ^= 1u;
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncthreads();
+            }
+            if (!ens_grid_barrier(bar, err)) return;
+        }
+        {   // estimate of every running member
+            int m = 0;
+            for (int t = blockIdx.x; t < tab.ebeg[n]; t += gridDim.x) {
+                while (t >= tab.ebeg[m + 1]) ++m;
+                const EnsMember<float>& M = tab.m[m];
+                if (M.red.sc->done) continue;
+                CondArgs c = ca;
+                c.tol = M.tol;
+                c.limit = M.limit;
+                const int lt = t - tab.ebeg[m], ex = M.egrid[0], ey = M.egrid[1];
+                sor_est_body<float>(M.g, M.dl[0], M.rr, M.rcur, M.red, c, lt % ex, (lt / ex) % ey, lt / (ex * ey),
+                                    ex * ey * M.egrid[2], lt);
+            }
+        }
+        if (!ens_grid_barrier(bar, err)) return;
+        {   // FP64 accumulation where a refinement was asked for
+            int m = 0;
+            for (int t = blockIdx.x; t < tab.abeg[n]; t += gridDim.x) {
+                while (t >= tab.abeg[m + 1]) ++m;
+                const EnsMember<float>& M = tab.m[m];
+                if (M.red.sc->done || !M.red.sc->refine) continue;
+                const int lt = t - tab.abeg[m], ax = M.agrid[0], ay = M.agrid[1];
+                accum_body<float>(M.g, M.ph, M.dl[0], lt % ax, (lt / ax) % ay, lt / (ax * ay));
+            }
+        }
+        if (!ens_grid_barrier(bar, err)) return;
+        {   // FP64 residual and stop decision
+            int m = 0;
+            for (int t = blockIdx.x; t < tab.rbeg[n]; t += gridDim.x) {
+                while (t >= tab.rbeg[m + 1]) ++m;
+                const EnsMember<float>& M = tab.m[m];
+                if (M.red.sc->done || !M.red.sc->refine) continue;
+                CondArgs c = ca;
+                c.tol = M.tol;
+                c.limit = M.limit;
+                c.done_host = nullptr;
+                const int done = residual64_body<float>(M.g, M.ph, M.rhs, M.rr, M.vfluid, M.red, c,
+                                                        t - tab.rbeg[m], M.rblocks);
+                if (done == 1 && tab.ndone) {
+                    const int v = atomicAdd(tab.ndone, 1) + 1;
+                    if (v == n && tab.all_done_host) *(volatile int*)tab.all_done_host = 1;
+                }
+            }
+        }
+        if (!ens_grid_barrier(bar, err)) return;
+        if (*(volatile int*)tab.ndone >= n) break;      // every member's solve has ended
+    }
+}
+
+int ens_persist_grid() {
+    static int grid = -1;
+    if (grid < 0) {
+        using TT = tma::TmaTile<kEnsTmaBy, kEnsTmaBz>;
+        int dev = 0, sms = 0, per = 0, coop = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        if (cudaFuncSetAttribute(k_ens_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT::SMEM) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ens_persist, 256, TT::SMEM) != cudaSuccess)
+            per = 0;
+        grid = coop ? sms * per : 0;
+        cudaGetLastError();
+    }
+    return grid;
+}
+
+int launch_ens_persist(const EnsTab<float>& tab, const CUtensorMap* maps, int cycle, int batches, const CondArgs& ca,
+                       unsigned* bar, int* err, cudaStream_t s) {
+    const int grid = ens_persist_grid();
+    if (grid <= 0) return -1;
+    using TT = tma::TmaTile<kEnsTmaBy, kEnsTmaBz>;
+    EnsTab<float> T = tab;
+    void* args[] = {(void*)&T, (void*)&maps, (void*)&cycle, (void*)&batches, (void*)&ca, (void*)&bar, (void*)&err};
+    if (cudaLaunchCooperativeKernel((const void*)k_ens_persist, dim3(grid), dim3(32, 8), args, TT::SMEM, s) !=
+        cudaSuccess)
+        return -1;
+    return 1;
 }
 
 int launch_est_ens(const EnsTab<float>& tab, int dcur, const CondArgs& ca, cudaStream_t s) {

@@ -104,6 +104,7 @@ def lib(build_if_missing: bool = False):
         L.les_ensemble_get_tile.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
         L.les_ensemble_autotune.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
         L.les_ensemble_launches.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+        L.les_ensemble_set_persistent.argtypes = [vp, i32]
         L.les_ensemble_set_warmstart.argtypes = [vp, vp, i32]
         L.les_selftest_wait_timeout.argtypes = [ctypes.c_int64, vp]
         L.les_time_sor.argtypes = [vp, i32, i32, i32, ctypes.POINTER(ctypes.c_double)]
@@ -141,7 +142,7 @@ def lib(build_if_missing: bool = False):
         L.les_get_timing.argtypes = [vp, ctypes.POINTER(les_timing_t)]
         for name in ("les_ensemble_create", "les_ensemble_size", "les_ensemble_member", "les_ensemble_step",
                      "les_ensemble_set_graph", "les_ensemble_set_tile", "les_ensemble_get_tile",
-                     "les_ensemble_autotune", "les_ensemble_launches", "les_ensemble_set_warmstart", "les_selftest_wait_timeout", "les_time_sor", "les_set_net_kernels", "les_set_net_start", "les_set_inflow_series", "les_set_record", "les_set_record_at", "les_set_net_schedule", "les_set_warmstart",
+                     "les_ensemble_autotune", "les_ensemble_launches", "les_ensemble_set_persistent", "les_ensemble_set_warmstart", "les_selftest_wait_timeout", "les_time_sor", "les_set_net_kernels", "les_set_net_start", "les_set_inflow_series", "les_set_record", "les_set_record_at", "les_set_net_schedule", "les_set_warmstart",
                      "les_net_create", "les_net_num_params", "les_net_set_stride", "les_net_get_stride",
                      "les_net_set_engine", "les_net_get_engine",
                      "les_net_get_params", "les_net_set_params", "les_net_forward", "les_net_gradient",
@@ -447,6 +448,10 @@ class Ensemble:
         v = ctypes.c_int64()
         _echeck(lib().les_ensemble_launches(self.h, ctypes.byref(v)), self.h)
         return v.value
+
+    def set_persistent(self, enable=True):
+        """Plain-SOR steps: the whole solve as one persistent cooperative launch per step."""
+        _echeck(lib().les_ensemble_set_persistent(self.h, 1 if enable else 0), self.h)
 
     def set_warmstart(self, net=None, every_sweeps=10):
         """Learned correction in every member's solve (net None: previous-step start)."""

@@ -36,6 +36,10 @@ def run_ensemble(a):
     for _ in range(a.warmup):
         ens.step(1)
     tune = ens.autotune(sweeps=10) if a.autotune else None
+    if a.ens_tile is not None:
+        ens.set_tile(a.ens_tile, 4)
+    if a.persistent:
+        ens.set_persistent(True)
     if a.range:
         les.les_profiler_range(1)
     t0 = time.perf_counter()
@@ -54,6 +58,7 @@ def run_ensemble(a):
                       "max_sweeps_per_step": [max(x) for x in sweeps],
                       "mean_member_sweeps": [sum(x) / len(x) for x in sweeps], "max_rel_residual": worst,
                       "rc": rcs, "tile": ens.tile(), "autotune": tune, "graph": a.graph, "net": a.net,
+                      "persistent": a.persistent, "launches": ens.launches(),
                       "net_every": a.net_every if a.net else None,
                       "shapes": [[sc.nx, sc.ny, sc.nz] for sc in scs]}))
     ens.close()
@@ -145,6 +150,8 @@ def main():
     ap.add_argument("--twin-omega", type=float, default=0.9, help="relaxation of the twinned double buffer")
     ap.add_argument("--fixed-sweeps", type=int, default=0,
                     help="run exactly this many SOR sweeps per step (0: solve to the tolerance)")
+    ap.add_argument("--ens-tile", type=int, default=None, help="ensemble sweep mode (les_ensemble_set_tile)")
+    ap.add_argument("--persistent", action="store_true", help="ensemble: plain steps as one persistent launch")
     ap.add_argument("--engines", action="store_true",
                     help="with --net: learned step time and network forward time for each convolution engine")
     a = ap.parse_args()

