@@ -417,6 +417,16 @@ int les_set_net_schedule(les_handle h, int32_t every_sweeps);
  * uses one launch per layer.  Both compute the same correction up to the
  * summation order of the RMS. */
 int les_set_net_kernels(les_handle h, int32_t persistent);
+/* les_set_net_async: with a schedule (every_sweeps > 0) in the CUDA-graph
+ * loop, 1 overlaps each network prediction with the next batch of sweeps:
+ * the prediction made from the residual of batch b runs on a second stream
+ * while batch b+1 sweeps, and is applied after it (the energy-norm step
+ * against the then current residual, which becomes the residual of the
+ * corrected iterate and the next prediction's input).  The step can never
+ * raise the error's energy, and the stop test is unchanged; the sweep count
+ * can differ from the in-place correction.  The host-driven loop (timing,
+ * recording) keeps the in-place correction.  Default 0. */
+int les_set_net_async(les_handle h, int32_t enable);
 /* les_set_net_start: with a schedule (every_sweeps > 0), whether the network
  * also corrects p at the start of each solve (default 1); without a schedule
  * the start correction is the warm start and always runs. */

@@ -144,6 +144,9 @@ struct les_s {
     int nseries = 0, series_cap = 0;
     long long net_gen = -1;               // network workspace generation the chunk graphs were captured with
     bool net_persistent = false;          // coarse network as one cooperative launch (les_set_net_kernels)
+    bool net_async = false;               // graph loop: each prediction overlaps the next batch of sweeps
+    cudaStream_t s2 = nullptr;            // its stream, and the events that order it with the loop
+    cudaEvent_t ev_fork = nullptr, ev_pool = nullptr, ev_q = nullptr;
     bool net_start = true;                // also correct at the start of each solve
     bool record = false;
     int rec_after = 0;                    // record at the first refinement after this many sweeps
@@ -414,6 +417,7 @@ int solve_start(les_s* h, const Geo<T>& g, cudaStream_t st) {
             if (rc) return rc;
         }
     }
+    if (h->net_async) CK(cudaMemsetAsync(&h->sc->qpend, 0, sizeof(int), st));   // no prediction pending yet
     h->rec_taken = false;
     if (h->record && h->rec_after == 0) record_start(h, st);
     CK(cudaGetLastError());
@@ -737,6 +741,35 @@ int build_graph(les_s* h, int cur) {
         launch_refine<T>(h, g, cond_args(h, RES_FIXED, G.max_sweeps, 0), cs);
         launch_project_step<T>(h, g, cur, cs);
         h->graph_launches[cur] = h->launches - l0 + nl;
+    } else if (net_in_loop(h) && h->net_async && !h->record) {
+        // the overlapped correction: each batch applies the prediction made
+        // from the previous batch's residual (line search against the current
+        // residual, which then becomes the residual of the corrected iterate)
+        // and forks the next prediction onto the second stream, where it runs
+        // during the next batch's sweeps; joined at the end of the chunk
+        if constexpr (std::is_same<T, float>::value) {
+            for (int b = 0; b < chunk_batches(h) && !rc; ++b) {
+                run_sweeps<T>(h, g, h->net_every, 2, nl, cs);     // net_every even: d returns to dl[0]
+                if (b > 0) CK(cudaStreamWaitEvent(cs, h->ev_pool, 0));      // the prediction has read rcur
+                launch_sor_est<T>(g, (const T*)h->dl[h->dcur], (const T*)h->rr, (T*)h->rcur, reducer(h),
+                                  cond_args(h, RES_LOOP, h->net_every, 1), cs);
+                launch_refine<T>(h, g, cond_args(h, RES_LOOP, h->net_every, 1), cs);
+                if (b > 0) CK(cudaStreamWaitEvent(cs, h->ev_q, 0));         // the prediction is complete
+                launch_warm_pending<T>(g, (T*)h->rcur, h->pred, (T*)h->dl[h->dcur], h->warm_scal + 1, reducer(h),
+                                       cs);
+                CK(cudaEventRecord(h->ev_fork, cs));
+                CK(cudaStreamWaitEvent(h->s2, h->ev_fork, 0));
+                rc = net_predict(h->net, h->d, (const float*)h->rcur, h->flags, h->pred, h->s2, &h->sc->done,
+                                 h->ev_pool);
+                if (rc) {
+                    fail(h, rc, "network prediction failed");
+                    break;
+                }
+                launch_set_flag(&h->sc->qpend, 1, &h->sc->done, h->s2);
+                CK(cudaEventRecord(h->ev_q, h->s2));
+            }
+            cudaStreamWaitEvent(cs, h->ev_q, 0);                            // join
+        }
     } else if (net_in_loop(h)) {
         // cycles of net_every sweeps, a forced refinement, the network
         // correction and the residual again, all gated on `done`
@@ -799,7 +832,8 @@ int step_graph(les_s* h, int nsteps, les_stats_t* stats) {
                 int rs = solve_start<T>(h, g, h->stream);
                 if (rs) return rs;
             }
-            const long long per_batch = net_in_loop(h) ? h->net_every + 3 + net_launches(h->net) + 2
+            const long long per_batch = net_in_loop(h) ? h->net_every + 3 + net_launches(h->net) + 2 +
+                                                             (h->net_async && !h->record ? 1 : 0)
                                                        : G.check_every + 3;
             for (int c = 0; c < max_chunks; ++c) {
                 CK(cudaGraphLaunch(h->gexec[h->cur], h->stream));
@@ -928,6 +962,13 @@ void release(les_s* h) {
             cudaEventDestroy(e);
             e = nullptr;
         }
+    for (cudaEvent_t* e : {&h->ev_fork, &h->ev_pool, &h->ev_q})
+        if (*e) {
+            cudaEventDestroy(*e);
+            *e = nullptr;
+        }
+    if (h->s2) cudaStreamSynchronize(h->s2), cudaStreamDestroy(h->s2);
+    h->s2 = nullptr;
     if (h->done_host) cudaFreeHost(h->done_host);
     h->done_host = nullptr;
     for (cudaEvent_t& e : h->ev)
@@ -1559,6 +1600,18 @@ int les_set_net_start(les_handle h, int32_t enable) {
     return LES_OK;
 }
 
+int les_set_net_async(les_handle h, int32_t enable) {
+    if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
+    if (enable && !h->s2) {
+        CK(cudaStreamCreateWithFlags(&h->s2, cudaStreamNonBlocking));
+        for (cudaEvent_t* e : {&h->ev_fork, &h->ev_pool, &h->ev_q})
+            CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    }
+    h->net_async = enable != 0;
+    h->graph_ok[0] = h->graph_ok[1] = false;
+    return LES_OK;
+}
+
 int les_set_net_kernels(les_handle h, int32_t persistent) {
     if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
     h->net_persistent = persistent != 0;
@@ -1583,6 +1636,7 @@ int les_set_record_at(les_handle h, int32_t after_sweeps) {
 
 int les_set_record(les_handle h, int32_t enable) {
     if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
+    h->graph_ok[0] = h->graph_ok[1] = false;      // the overlapped loop is captured without recording
     if (enable && !h->rec_p0) {
         int rc = dalloc(h, (void**)&h->rec_p0, h->n * sizeof(double));
         if (rc) return rc;

@@ -83,6 +83,7 @@ struct Scalars {
     int done;               // the current solve has finished (kernels of a chunk exit early)
     int zcopy;              // zflag as it was before a network step wrote into the correction
     int timeout;            // a bounded device-side wait gave up (sticky until reported)
+    int qpend;              // overlapped network correction: a prediction waits to be applied
 };
 
 // A refinement (FP64 accumulate + true residual) is taken when the cheap
@@ -285,6 +286,13 @@ int launch_wait_selftest(unsigned long long limit_ns, int* status, cudaStream_t 
 // SOR correction takes the step)
 template <typename T> int launch_warm(const Geo<T>& g, const T* r, const float* q, double* ph, T* dl, double* alpha,
                                       const Reduce& red, cudaStream_t s);
+// the overlapped correction inside the loop: the line search of the pending
+// prediction q against the current residual r, then d += alpha q and
+// r -= alpha A q (r becomes the residual after the step: the next
+// prediction's input); both kernels return at once unless sc->qpend is set
+template <typename T> int launch_warm_pending(const Geo<T>& g, T* r, const float* q, T* dl, double* alpha,
+                                              const Reduce& red, cudaStream_t s);
+int launch_set_flag(int* flag, int value, const int* gate, cudaStream_t s);
 // training-pair recording: what 0 = ph - ph0 into out, 1 = unknown mask into out
 template <typename T> int launch_record(const Geo<T>& g, const double* ph, const double* ph0, T* out, int what,
                                         cudaStream_t s);
@@ -326,8 +334,9 @@ namespace les {
 // the unknown flags in, the correction direction as a dense (nz, ny, nx)
 // array out (zero off the unknowns)
 // (`gate` nullable: every kernel returns at once while *gate != 0)
+// (after_pool, nullable: recorded on s once the residual has been read)
 int net_predict(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, float* out_dense,
-                cudaStream_t s, const int* gate = nullptr);
+                cudaStream_t s, const int* gate = nullptr, cudaEvent_t after_pool = nullptr);
 int net_launches(const les_net_s* n);
 // size the network's workspace for a solver grid ahead of a graph capture; the
 // generation changes whenever the workspace is reallocated (captured graphs

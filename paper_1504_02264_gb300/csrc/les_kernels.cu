@@ -1238,6 +1238,7 @@ __global__ void __launch_bounds__(256) k_warm_ls(Geo<T> g, const T* __restrict__
     pdl_wait();
     const Dom& d = g.d;
     if (red.sc->done) return;      // uniform over the grid
+    if (in_loop == 2 && !red.sc->qpend) return;
     const int i = blockIdx.x * 32 + threadIdx.x + 1;
     const int j = blockIdx.y * 8 + threadIdx.y + 1;
     const int kb = blockIdx.z * kEstChunk + 1, ke = min(kb + kEstChunk, d.nz + 1);
@@ -1337,6 +1338,70 @@ __global__ void k_warm_apply_dl(Geo<T> g, T* dl, const float* q, const double* a
         const T base = zero ? T(0) : dl[c];
         dl[c] = base + a * (T)q[v];
     }
+}
+
+// the overlapped correction's step: d = (zero ? 0 : d) + alpha q as in
+// k_warm_apply_dl, and r -= alpha (A q) with A q formed exactly as in the
+// line search, so r becomes the residual of the corrected iterate
+template <typename T>
+__global__ void k_warm_apply_dlr(Geo<T> g, T* dl, T* r, const float* __restrict__ q, const double* alpha,
+                                 const Scalars* sc) {
+    pdl_wait();
+    const Dom& d = g.d;
+    if (sc->done || !sc->qpend) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    const int kb = blockIdx.z * kEstChunk + 1, ke = min(kb + kEstChunk, d.nz + 1);
+    if (i > d.nx || j > d.ny) return;
+    const T a = (T)*alpha;
+    const bool zero = sc->zcopy != 0;
+    const int sy = d.nx, sz = d.nx * d.ny;
+    const int oe = (d.perx && i == d.nx) ? -(d.nx - 1) : 1;
+    const int ow = (d.perx && i == 1) ? (d.nx - 1) : -1;
+    const int on = (d.pery && j == d.ny) ? -(d.ny - 1) * sy : sy;
+    const int os = (d.pery && j == 1) ? (d.ny - 1) * sy : -sy;
+    long long c = d.at(i, j, kb);
+    int v = ((kb - 1) * d.ny + (j - 1)) * d.nx + (i - 1);
+    for (int k = kb; k < ke; ++k, c += d.plane, v += sz) {
+        const uint8_t f = g.flags[c];
+        if (!(f & F_UNK)) continue;
+        const int ot = (d.perz && k == d.nz) ? -(d.nz - 1) * sz : sz;
+        const int ob = (d.perz && k == 1) ? (d.nz - 1) * sz : -sz;
+        const T qc = (T)q[v];
+        const T qe = (f & F_E) ? (T)q[v + oe] : T(0), qw = (f & F_W) ? (T)q[v + ow] : T(0);
+        const T qn = (f & F_N) ? (T)q[v + on] : T(0), qs = (f & F_S) ? (T)q[v + os] : T(0);
+        const T qt = (f & F_T) ? (T)q[v + ot] : T(0), qb = (f & F_B) ? (T)q[v + ob] : T(0);
+        T aq = T(0);
+        if (f & F_E) aq += g.cx * (qe - qc);
+        if (f & F_W) aq += g.cx * (qw - qc);
+        if (f & F_N) aq += g.cy * (qn - qc);
+        if (f & F_S) aq += g.cy * (qs - qc);
+        if (f & F_T) aq += g.cT[k] * (qt - qc);
+        if (f & F_B) aq += g.cB[k] * (qb - qc);
+        const T base = zero ? T(0) : dl[c];
+        dl[c] = base + a * qc;
+        r[c] -= a * aq;
+    }
+}
+
+template <typename T>
+int launch_warm_pending(const Geo<T>& g, T* r, const float* q, T* dl, double* alpha, const Reduce& red,
+                        cudaStream_t s) {
+    const Dom& d = g.d;
+    const dim3 grid((d.nx + 31) / 32, (d.ny + 7) / 8, (d.nz + kEstChunk - 1) / kEstChunk), blk(32, 8);
+    launch_pdl(k_warm_ls<T>, grid, blk, 0, s, g, (const T*)r, q, alpha, red, 2);
+    launch_pdl(k_warm_apply_dlr<T>, grid, blk, 0, s, g, dl, r, q, (const double*)alpha, (const Scalars*)red.sc);
+    return 2;
+}
+
+__global__ void k_set_flag(int* flag, int value, const int* gate) {
+    if (gate && *(volatile const int*)gate) return;
+    *flag = value;
+}
+
+int launch_set_flag(int* flag, int value, const int* gate, cudaStream_t s) {
+    k_set_flag<<<1, 1, 0, s>>>(flag, value, gate);
+    return 1;
 }
 
 template <typename T>
@@ -1646,6 +1711,10 @@ __global__ void __launch_bounds__(256) k_ens_persist(const __grid_constant__ Ens
         tma::mbar_init(tma::smem_u32(psm + TT::OFF_BAR), 1);
         tma::mbar_fence_init();
     }
+    // the maps were written through the generic proxy (a host copy): acquire
+    // them for the tensor-map proxy once per CTA, one map per thread
+    for (int c = tid; c < 4 * n; c += 256)
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(maps + c) : "memory");
     __syncthreads();
     uint32_t phase = 0;
     for (int b = 0; b < batches; ++b) {
@@ -1662,9 +1731,6 @@ __global__ void __launch_bounds__(256) k_ens_persist(const __grid_constant__ Ens
                 const int q = t - tab.tbeg[m];
                 const bool zero_start = s == 0 && sc->zflag;
                 const CUtensorMap* mm = maps + 4 * m;
-                if (tid == 0)
-                    for (int c = 0; c < 4; ++c)
-                        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mm + c) : "memory");
                 if (!tma::sor_tma_block<kEnsTmaBy, kEnsTmaBz, 256>(psm, mm + in, mm + 2, mm + 3, M.g, M.dl[in], M.rr,
                                                                     M.dl[1 - in], zero_start, sc, q % gx,
                                                                     (q / gx) % gy, q / (gx * gy), phase)) {
@@ -1795,6 +1861,8 @@ int launch_refine_ens(const EnsTab<float>& tab, int dcur, const CondArgs& ca, cu
     template int launch_gauge<T>(const Geo<T>&, const double*, double*, const Scalars*, cudaStream_t);   \
     template int launch_warm<T>(const Geo<T>&, const T*, const float*, double*, T*, double*, const Reduce&,     \
                                 cudaStream_t);                                                          \
+    template int launch_warm_pending<T>(const Geo<T>&, T*, const float*, T*, double*, const Reduce&,            \
+                                        cudaStream_t);                                                  \
     template int launch_record<T>(const Geo<T>&, const double*, const double*, T*, int, cudaStream_t);
 
 LES_INSTANTIATE(float)

@@ -491,7 +491,7 @@ int net_persistent_launches() { return 4; }     // pool, barrier reset, network,
 
 long long net_generation(const les_net_s* n) { return n->ws_gen; }
 int net_predict(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, float* out_dense,
-                cudaStream_t s, const int* gate) {
+                cudaStream_t s, const int* gate, cudaEvent_t after_pool) {
     nn::set_conv_engine(n->engine, n->tc_timeout);
     const Level Lf{d.nx, d.ny, d.nz};
     const Level L0 = coarse(n, Lf);
@@ -503,11 +503,13 @@ int net_predict(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t
             // pooling and RMS in one launch, the pooled mask straight into the
             // head's mask, then the packing
             nn::pool_rms(r_padded, flags, d, n->stride, n->rc, n->mask, n->pp_part, n->pp_count, n->dscal, s, gate);
+            if (after_pool) cudaEventRecord(after_pool, s);      // the residual has been read
             launch_pdl(k_pack_dense, dim3((unsigned)((L0.v() + 255) / 256)), dim3(256), 0, s, (const float*)n->rc,
                        (const float*)n->mask, (const double*)n->dscal, n->xin, (size_t)L0.v(), gate);
             n->last_launches = 2;
         } else {
             nn::pool_padded_s(r_padded, flags, d, n->stride, n->rc, n->mc, s, gate);
+            if (after_pool) cudaEventRecord(after_pool, s);
             rc = pack_sample(n, L0, n->rc, n->mc, nullptr, nullptr, gate);
             n->last_launches = 1 + 3 + 1;
         }

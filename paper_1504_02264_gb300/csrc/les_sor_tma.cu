@@ -66,6 +66,10 @@ k_sor_tma_ens(const __grid_constant__ EnsTab<float> tab, const CUtensorMap* __re
         mbar_init(smem_u32(sm + TT::OFF_BAR), 1);
         mbar_fence_init();
     }
+    // the maps were written through the generic proxy (a host copy): acquire
+    // them for the tensor-map proxy once per CTA, one map per thread
+    for (int c = threadIdx.x; c < 4 * n; c += blockDim.x)
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(maps + c) : "memory");
     __syncthreads();
     uint32_t phase = 0;
     int m = 0;
@@ -80,9 +84,6 @@ k_sor_tma_ens(const __grid_constant__ EnsTab<float> tab, const CUtensorMap* __re
         const int bx = q % gx, by = (q / gx) % gy, bz = q / (gx * gy);
         const bool zero_start = zero_arg == 1 || (zero_arg == 2 && sc->zflag);
         const CUtensorMap* mm = maps + 4 * m;
-        if (threadIdx.x == 0)       // the maps were written through the generic proxy (a host copy)
-            for (int c = 0; c < 4; ++c)
-                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mm + c) : "memory");
         if (!sor_tma_block<BY, BZ, NT>(sm, mm + in, mm + 2, mm + 3, M.g, M.dl[in], M.rr, M.dl[1 - in], zero_start, sc,
                                        bx, by, bz, phase))
             return;

@@ -113,6 +113,7 @@ def lib(build_if_missing: bool = False):
         L.les_set_record.argtypes = [vp, i32]
         L.les_set_record_at.argtypes = [vp, i32]
         L.les_set_net_kernels.argtypes = [vp, i32]
+        L.les_set_net_async.argtypes = [vp, i32]
         L.les_set_net_start.argtypes = [vp, i32]
         L.les_set_inflow_series.argtypes = [vp, i32, vp, vp]
         L.les_set_net_schedule.argtypes = [vp, i32]
@@ -142,7 +143,7 @@ def lib(build_if_missing: bool = False):
         L.les_get_timing.argtypes = [vp, ctypes.POINTER(les_timing_t)]
         for name in ("les_ensemble_create", "les_ensemble_size", "les_ensemble_member", "les_ensemble_step",
                      "les_ensemble_set_graph", "les_ensemble_set_tile", "les_ensemble_get_tile",
-                     "les_ensemble_autotune", "les_ensemble_launches", "les_ensemble_set_persistent", "les_ensemble_set_warmstart", "les_selftest_wait_timeout", "les_time_sor", "les_set_net_kernels", "les_set_net_start", "les_set_inflow_series", "les_set_record", "les_set_record_at", "les_set_net_schedule", "les_set_warmstart",
+                     "les_ensemble_autotune", "les_ensemble_launches", "les_ensemble_set_persistent", "les_ensemble_set_warmstart", "les_selftest_wait_timeout", "les_time_sor", "les_set_net_kernels", "les_set_net_async", "les_set_net_start", "les_set_inflow_series", "les_set_record", "les_set_record_at", "les_set_net_schedule", "les_set_warmstart",
                      "les_net_create", "les_net_num_params", "les_net_set_stride", "les_net_get_stride",
                      "les_net_set_engine", "les_net_get_engine",
                      "les_net_get_params", "les_net_set_params", "les_net_forward", "les_net_gradient",
@@ -630,6 +631,9 @@ class Domain:
 
     def set_net_start(self, enable=True):
         _check(lib().les_set_net_start(self.h, 1 if enable else 0), self.h)
+
+    def set_net_async(self, enable=True):
+        _check(lib().les_set_net_async(self.h, 1 if enable else 0), self.h)
 
     def set_net_kernels(self, persistent=True):
         _check(lib().les_set_net_kernels(self.h, 1 if persistent else 0), self.h)

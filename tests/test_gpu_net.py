@@ -402,3 +402,47 @@ def test_trained_network_gain():
     # what training buys over the same cycle without it
     assert res["trained"][0] < res["untrained"][0], res
     assert res["trained"][0] < res["coarse_residual"][0], res
+
+
+def test_overlapped_correction_converges():
+    """The network prediction overlapped with the next batch of sweeps
+    (les_set_net_async): every step still ends at the tolerance, the sweeps
+    stay within a third of the in-place correction's, and the fields agree
+    with the in-place run to the accuracy both solves are held to."""
+    import os
+    import time
+    from paper_1504_02264_gb300 import train
+    net = train.load(os.path.join(os.path.dirname(les.__file__), "weights", "warmstart.npz"))
+    sc = scene.random_scene(seed=4242, nx=96, ny=96, nz=48, n_buildings=40, x_margin=12, max_sweeps=60000,
+                            check_every=20)
+    base = les.Domain(sc)
+    for _ in range(4):
+        base.step()
+    state = base.get_state()
+    base.close()
+    out = {}
+    for mode in ("in_place", "overlapped"):
+        d = les.Domain(sc)
+        d.set_state(state)
+        d.set_warmstart(net)
+        d.set_net_schedule(10)
+        d.set_net_async(mode == "overlapped")
+        d.step()
+        d.set_state(state)
+        sw, ms = [], []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = d.step()
+            torch.cuda.synchronize()
+            ms.append(1e3 * (time.perf_counter() - t0))
+            assert st["rc"] == 0 and st["rel_residual"] <= 1e-6 and st["graph"] == 1, (mode, st)
+            sw.append(st["sweeps"])
+        out[mode] = (sw, float(np.median(ms)), d.fields())
+        d.close()
+    net.close()
+    print("in-place vs overlapped (sweeps, ms per step):", out["in_place"][:2], out["overlapped"][:2])
+    assert sum(out["overlapped"][0]) <= 1.34 * sum(out["in_place"][0])
+    vel = max(np.abs(a).max() for a in out["in_place"][2][:3])
+    err = max(np.abs(a.astype(np.float64) - b).max() for a, b in zip(out["overlapped"][2][:3], out["in_place"][2][:3]))
+    assert err <= 1e-4 * vel
