@@ -410,13 +410,24 @@ int les_set_warmstart(les_handle h, int32_t mode, les_net net);
  * start (default).  A value > 0 runs solves from the host loop.  The stop
  * test is unchanged. */
 int les_set_net_schedule(les_handle h, int32_t every_sweeps);
-/* les_set_net_kernels: 1 runs the coarse network of each correction (RMS,
- * packing, the seven convolutions, head) as one cooperative persistent launch
- * with a bounded grid barrier between layers, when the device supports
- * cooperative launches; 0 (default, faster inside the CUDA graphs on GB300)
- * uses one launch per layer.  Both compute the same correction up to the
- * summation order of the RMS. */
-int les_set_net_kernels(les_handle h, int32_t persistent);
+/* les_set_net_kernels: how the kernels of a network correction are laid out.
+ * LES_NET_KERNELS_FOLDED (0, default, fastest inside the CUDA graphs on
+ * GB300): one launch per layer, with the packing of the network input run
+ * inside the first convolution's staging and the head inside the last
+ * convolution's epilogue (tcgen05 engine), and the trilinear prolongation
+ * inside the line search, which prolongs the coarse output on the fly.
+ * LES_NET_KERNELS_LAYERS (2): the same layers with the packing, head and
+ * prolongation as kernels of their own; it computes the same values as 0
+ * (bit-identical fields) and serves to check the folded kernels.
+ * LES_NET_KERNELS_PERSISTENT (1): the coarse network (RMS, packing, the
+ * seven convolutions, head) as one cooperative persistent launch with a
+ * bounded grid barrier between layers, when the device supports cooperative
+ * launches; the same correction up to the summation order of the RMS.
+ * Any other value: LES_EINVAL. */
+#define LES_NET_KERNELS_FOLDED 0
+#define LES_NET_KERNELS_PERSISTENT 1
+#define LES_NET_KERNELS_LAYERS 2
+int les_set_net_kernels(les_handle h, int32_t mode);
 /* les_set_net_async: with a schedule (every_sweeps > 0) in the CUDA-graph
  * loop, 1 overlaps each network prediction with the next batch of sweeps:
  * the prediction made from the residual of batch b runs on a second stream

@@ -143,7 +143,8 @@ struct les_s {
     double* series_t = nullptr;
     int nseries = 0, series_cap = 0;
     long long net_gen = -1;               // network workspace generation the chunk graphs were captured with
-    bool net_persistent = false;          // coarse network as one cooperative launch (les_set_net_kernels)
+    int net_kernels = LES_NET_KERNELS_FOLDED;   // how a correction's kernels are laid out (les_set_net_kernels)
+    bool net_persistent = false;          // coarse network as one cooperative launch
     bool net_async = false;               // graph loop: each prediction overlaps the next batch of sweeps
     cudaStream_t s2 = nullptr;            // its stream, and the events that order it with the loop
     cudaEvent_t ev_fork = nullptr, ev_pool = nullptr, ev_q = nullptr;
@@ -357,24 +358,44 @@ int predict(les_s* h, const float* r, cudaStream_t st, const int* gate) {
         }
         if (rc != LES_EINVAL) return fail(h, rc, "persistent network prediction failed");
     }
-    int rc = net_predict(h->net, h->d, r, h->flags, h->pred, st, gate);
+    int rc = net_predict(h->net, h->d, r, h->flags, h->pred, st, gate, nullptr,
+                         h->net_kernels != LES_NET_KERNELS_LAYERS);
     if (rc) return fail(h, rc, "network prediction failed");
     h->launches += net_launches(h->net);
+    return LES_OK;
+}
+
+// The prediction for residual r and the energy-norm step along it: into the
+// FP64 pressure ph (dl null) or into the SOR correction dl.  Folded kernels
+// (default): the prolongation runs inside the line search, which leaves the
+// fine correction in h->pred for the step; otherwise (the persistent network,
+// or the stand-alone kernels) the prolongation has its own kernel first.
+template <typename T>
+int net_step(les_s* h, const Geo<T>& g, const T* r, double* ph, T* dl, cudaStream_t st, const int* gate) {
+    if (h->net_kernels == LES_NET_KERNELS_FOLDED) {
+        int rc = net_predict_coarse(h->net, h->d, (const float*)r, h->flags, st, gate);
+        if (rc) return fail(h, rc, "network prediction failed");
+        h->launches += net_launches(h->net);
+        h->launches += launch_warm_coarse<T>(g, r, net_coarse_out(h->net), net_stride(h->net), h->pred, ph, dl,
+                                             h->warm_scal + 1, reducer(h), st);
+        return LES_OK;
+    }
+    int rc = predict(h, (const float*)r, st, gate);
+    if (rc) return rc;
+    h->launches += launch_warm<T>(g, r, h->pred, ph, dl, h->warm_scal + 1, reducer(h), st);
     return LES_OK;
 }
 
 template <typename T>
 int net_correct(les_s* h, const Geo<T>& g, cudaStream_t st) {
     if (h->record) CK(cudaMemcpyAsync(h->rec_netin, h->rr, h->n * h->es, cudaMemcpyDeviceToDevice, st));
-    int rc = predict(h, (const float*)h->rr, st, nullptr);
+    int rc = net_step<T>(h, g, (const T*)h->rr, h->ph[h->cur], (T*)nullptr, st, nullptr);
     if (rc) return rc;
     if (h->record) {
         CK(cudaMemcpyAsync(h->rec_netq, h->pred, (size_t)h->g.nx * h->g.ny * h->g.nz * sizeof(float),
                            cudaMemcpyDeviceToDevice, st));
         h->net_taken = true;
     }
-    h->launches += launch_warm<T>(g, (const T*)h->rr, h->pred, h->ph[h->cur], (T*)nullptr, h->warm_scal + 1,
-                                  reducer(h), st);
     h->launches += launch_residual64<T>(g, h->ph[h->cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h),
                                         cond_args(h, RES_INIT, 0, 0), st);
     CK(cudaGetLastError());
@@ -387,10 +408,8 @@ int net_correct(les_s* h, const Geo<T>& g, cudaStream_t st) {
 // chunk graph, every kernel returns at once when the solve is done.
 template <typename T>
 int net_correct_loop(les_s* h, const Geo<T>& g, cudaStream_t st, bool gated) {
-    int rc = predict(h, (const float*)h->rcur, st, gated ? &h->sc->done : nullptr);
+    int rc = net_step<T>(h, g, (const T*)h->rcur, nullptr, (T*)h->dl[h->dcur], st, gated ? &h->sc->done : nullptr);
     if (rc) return rc;
-    h->launches += launch_warm<T>(g, (const T*)h->rcur, h->pred, nullptr, (T*)h->dl[h->dcur], h->warm_scal + 1,
-                                  reducer(h), st);
     CK(cudaGetLastError());
     return LES_OK;
 }
@@ -1612,9 +1631,12 @@ int les_set_net_async(les_handle h, int32_t enable) {
     return LES_OK;
 }
 
-int les_set_net_kernels(les_handle h, int32_t persistent) {
+int les_set_net_kernels(les_handle h, int32_t mode) {
     if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
-    h->net_persistent = persistent != 0;
+    if (mode < LES_NET_KERNELS_FOLDED || mode > LES_NET_KERNELS_LAYERS)
+        return fail(h, LES_EINVAL, "network kernel layout must be 0, 1 or 2");
+    h->net_kernels = mode;
+    h->net_persistent = mode == LES_NET_KERNELS_PERSISTENT;
     h->graph_ok[0] = h->graph_ok[1] = false;
     return LES_OK;
 }

@@ -23,7 +23,9 @@ namespace les {
 // scheduled while the previous kernel of its stream is still finishing; its
 // first statement, pdl_wait(), blocks until that kernel has completed and its
 // writes are visible, so no read or write of the kernel can overlap it.  For
-// an ordinary launch pdl_wait() returns at once.
+// an ordinary launch pdl_wait() returns at once.  (No kernel triggers its
+// dependents early: with griddepcontrol.launch_dependents after the wait,
+// the SOR sweeps measured 2% slower on GB300 and the learned step 1%.)
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>
@@ -43,6 +45,40 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 }
 
 constexpr int OX = 3;
+
+// Trilinear prolongation of a cell-centred coarse field of stride s to the
+// fine cells: fine centre f sits at coarse coordinate (f + 1/2)/s - 1/2 on
+// each axis, clamped to the first / last coarse centre; a fine value is the
+// x-interpolation of the two (y, z)-interpolated coarse columns around it.
+// Shared by the network's prolongation kernel and the line search that
+// prolongs on the fly.  Every operation is an explicitly rounded intrinsic,
+// so the compiler cannot contract the two kernels' copies differently and
+// both form bit-identical values.
+__device__ __forceinline__ void prolong_w(int f, int s, int C, int& c0, float& w) {
+    const float x = __fsub_rn(__fdiv_rn(__fadd_rn((float)f, 0.5f), (float)s), 0.5f);
+    c0 = (int)floorf(x);
+    w = __fsub_rn(x, (float)c0);
+    if (c0 < 0) {
+        c0 = 0;
+        w = 0.f;
+    }
+    if (c0 >= C - 1) {
+        c0 = C - 1;
+        w = 0.f;
+    }
+}
+// (1 - w) a + w b, rounded as: the first product, then one fused multiply-add
+__device__ __forceinline__ float prolong_lerp(float a, float b, float w) {
+    return __fmaf_rn(w, b, __fmul_rn(__fsub_rn(1.f, w), a));
+}
+// coarse column c of yc (Xc x Yc x Zc, x fastest) interpolated in y and z
+__device__ __forceinline__ float prolong_col(const float* yc, int Xc, int Yc, int c, int y0, int y1, float wy, int z0,
+                                             int z1, float wz) {
+    const float a0 = prolong_lerp(yc[((size_t)z0 * Yc + y0) * Xc + c], yc[((size_t)z0 * Yc + y1) * Xc + c], wy);
+    const float a1 = prolong_lerp(yc[((size_t)z1 * Yc + y0) * Xc + c], yc[((size_t)z1 * Yc + y1) * Xc + c], wy);
+    return prolong_lerp(a0, a1, wz);
+}
+__device__ __forceinline__ float prolong_mix(float v0, float v1, float wx) { return prolong_lerp(v0, v1, wx); }
 
 // per-cell flag bits: open faces of the cell, Poisson unknown, fluid
 enum : uint8_t {
@@ -286,6 +322,12 @@ int launch_wait_selftest(unsigned long long limit_ns, int* status, cudaStream_t 
 // SOR correction takes the step)
 template <typename T> int launch_warm(const Geo<T>& g, const T* r, const float* q, double* ph, T* dl, double* alpha,
                                       const Reduce& red, cudaStream_t s);
+// the same with the network's prolongation folded into the line search: yc
+// is the coarse output (cell-centred, stride st in {1, 2, 4, 8}); the line
+// search prolongs it on the fly (the arithmetic of the stand-alone
+// prolongation kernel) and leaves the dense fine correction in q for the step
+template <typename T> int launch_warm_coarse(const Geo<T>& g, const T* r, const float* yc, int st, float* q,
+                                             double* ph, T* dl, double* alpha, const Reduce& red, cudaStream_t s);
 // the overlapped correction inside the loop: the line search of the pending
 // prediction q against the current residual r, then d += alpha q and
 // r -= alpha A q (r becomes the residual after the step: the next
@@ -335,8 +377,18 @@ namespace les {
 // array out (zero off the unknowns)
 // (`gate` nullable: every kernel returns at once while *gate != 0)
 // (after_pool, nullable: recorded on s once the residual has been read)
+// (fold: on the tcgen05 engine the packing runs inside the first
+// convolution and the head inside the last; false keeps their own kernels,
+// which compute the same values)
 int net_predict(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, float* out_dense,
-                cudaStream_t s, const int* gate = nullptr, cudaEvent_t after_pool = nullptr);
+                cudaStream_t s, const int* gate = nullptr, cudaEvent_t after_pool = nullptr, bool fold = true);
+// the same without the prolongation: the coarse output is left in
+// net_coarse_out(n) (stride net_stride(n)) for a line search that prolongs it
+// on the fly (launch_warm_coarse)
+int net_predict_coarse(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, cudaStream_t s,
+                       const int* gate = nullptr);
+const float* net_coarse_out(const les_net_s* n);
+int net_stride(const les_net_s* n);
 int net_launches(const les_net_s* n);
 // size the network's workspace for a solver grid ahead of a graph capture; the
 // generation changes whenever the workspace is reallocated (captured graphs

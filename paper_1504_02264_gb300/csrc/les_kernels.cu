@@ -457,24 +457,28 @@ k_nut(Geo<T> g, const T* __restrict__ u, const T* __restrict__ v, const T* __res
     const int k0 = 1 + blockIdx.z * kc, k1 = min(k0 + kc, d.nz + 1);
     const T* const src[3] = {u, v, w};
     T* const dst[3] = {sU, sV, sW};
-    Window<T, 3, MX, MY, NT> win;
+    // three register stages: the planes k+1, k+2 and k+3 are in flight while
+    // plane k is computed
+    Window<T, 3, MX, MY, NT> w0, w1, w2;
     const SmemStencil<T, MX, MY> S(g, sU, sV, sW, ib, jb);
     const bool own = i <= d.nx && j <= d.ny;
-    win.fetch(d, src, ib, jb, k0 - 1, tid);
-    win.put(dst, k0 - 1, tid);
-    win.fetch(d, src, ib, jb, k0, tid);
-    win.put(dst, k0, tid);
-    win.fetch(d, src, ib, jb, k0 + 1, tid);
-    for (int k = k0; k < k1; ++k) {
+    w0.fetch(d, src, ib, jb, k0 - 1, tid);
+    w0.put(dst, k0 - 1, tid);
+    w0.fetch(d, src, ib, jb, k0, tid);
+    w0.put(dst, k0, tid);
+    w0.fetch(d, src, ib, jb, k0 + 1, tid);
+    if (k0 + 2 <= k1) w1.fetch(d, src, ib, jb, k0 + 2, tid);
+    if (k0 + 3 <= k1) w2.fetch(d, src, ib, jb, k0 + 3, tid);
+    auto plane = [&](int k, Window<T, 3, MX, MY, NT>& stage) {
         const long long c = own ? d.at(i, j, k) : 0;
         const uint8_t f = own ? g.flags[c] : 0;
-        win.put(dst, k + 1, tid);
+        stage.put(dst, k + 1, tid);
         __syncthreads();
-        if (k + 2 <= k1) win.fetch(d, src, ib, jb, k + 2, tid);
-        if (!own) continue;
+        if (k + 4 <= k1) stage.fetch(d, src, ib, jb, k + 4, tid);
+        if (!own) return;
         if (!(f & F_FLUID)) {
             nut[c] = T(0);
-            continue;
+            return;
         }
         T s11 = (S.U(i, j, k) - S.U(i - 1, j, k)) * g.rdx;
         T s22 = (S.V(i, j, k) - S.V(i, j - 1, k)) * g.rdy;
@@ -484,6 +488,11 @@ k_nut(Geo<T> g, const T* __restrict__ u, const T* __restrict__ v, const T* __res
         T s23 = T(0.25) * (S.s23(i, j - 1, k - 1) + S.s23(i, j, k - 1) + S.s23(i, j - 1, k) + S.s23(i, j, k));
         T smag = sqrt(T(2) * (s11 * s11 + s22 * s22 + s33 * s33) + T(4) * (s12 * s12 + s13 * s13 + s23 * s23));
         nut[c] = g.delta2[k] * smag;
+    };
+    for (int k = k0; k < k1; k += 3) {
+        plane(k, w0);
+        if (k + 1 < k1) plane(k + 1, w1);
+        if (k + 2 < k1) plane(k + 2, w2);
     }
 }
 
@@ -690,6 +699,8 @@ int column_kc(const Dom& d) {
     return (int)(kc < 1 ? 1 : (kc > d.nz ? d.nz : kc));
 }
 
+constexpr int kRhsUnroll = 4;
+
 template <typename T>
 __global__ void k_rhs(Geo<T> g, const T* us, const T* vs, const T* ws, T* rhs, double vfluid, Reduce r, int kc) {
     const Dom& d = g.d;
@@ -698,16 +709,36 @@ __global__ void k_rhs(Geo<T> g, const T* us, const T* vs, const T* ws, T* rhs, d
     const int kb = blockIdx.z * kc + 1, ke = min(kb + kc, d.nz + 1);
     double x[1] = {0.0};
     if (i <= d.nx && j <= d.ny) {
+        // every load is issued unconditionally (the padded arrays hold each
+        // neighbour), kRhsUnroll planes at a time, so that the loads of
+        // several planes are in flight together; the flag selects the result
         long long c = d.at(i, j, kb);
-        for (int k = kb; k < ke; ++k, c += d.plane) {
-            T val = T(0);
-            if (g.flags[c] & F_FLUID) {
-                T div = (us[c] - us[c - 1]) / g.dx + (vs[c] - vs[c - d.px]) / g.dy +
-                        (ws[c] - ws[c - d.plane]) / g.dz[k];
-                val = div / g.dt;
-                x[0] += g.dz64[k] * (double)val;
+        for (int k = kb; k < ke; k += kRhsUnroll, c += kRhsUnroll * d.plane) {
+            uint8_t f[kRhsUnroll];
+            T ue[kRhsUnroll], uw[kRhsUnroll], vn[kRhsUnroll], vs_[kRhsUnroll], wt[kRhsUnroll], wb[kRhsUnroll];
+#pragma unroll
+            for (int m = 0; m < kRhsUnroll; ++m) {
+                const bool in = k + m < ke;
+                const long long cm = in ? c + m * d.plane : c;
+                f[m] = in ? g.flags[cm] : (uint8_t)0;
+                ue[m] = us[cm];
+                uw[m] = us[cm - 1];
+                vn[m] = vs[cm];
+                vs_[m] = vs[cm - d.px];
+                wt[m] = ws[cm];
+                wb[m] = ws[cm - d.plane];
             }
-            rhs[c] = val;
+#pragma unroll
+            for (int m = 0; m < kRhsUnroll; ++m) {
+                if (k + m >= ke) break;
+                T val = T(0);
+                if (f[m] & F_FLUID) {
+                    T div = (ue[m] - uw[m]) / g.dx + (vn[m] - vs_[m]) / g.dy + (wt[m] - wb[m]) / g.dz[k + m];
+                    val = div / g.dt;
+                    x[0] += g.dz64[k + m] * (double)val;
+                }
+                rhs[c + m * d.plane] = val;
+            }
         }
     }
     if (grid_sum<1>(x, r)) {
@@ -719,7 +750,10 @@ template <typename T>
 int launch_rhs(const Geo<T>& g, const T* us, const T* vs, const T* ws, T* rhs, double vfluid,
                const Reduce& r, cudaStream_t s) {
     const Dom& d = g.d;
-    const int kc = column_kc(d);
+    // one batch of kRhsUnroll planes per thread: every load of a thread is in
+    // flight at once and the grid holds many CTAs (at most one per plane of a
+    // column tile, the size of the reduction's partials array)
+    const int kc = kRhsUnroll < d.nz ? kRhsUnroll : d.nz;
     k_rhs<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, (d.nz + kc - 1) / kc), dim3(32, 8), 0, s>>>(
         g, us, vs, ws, rhs, vfluid, r, kc);
     return 1;
@@ -1299,6 +1333,161 @@ __global__ void __launch_bounds__(256) k_warm_ls(Geo<T> g, const T* __restrict__
     }
 }
 
+// The line search with the network's prolongation folded in.  The CTA's
+// 32 x 8 x kEstChunk tile and its one-cell halo of q are formed in shared
+// memory from the coarse output yc (stride S) with the arithmetic of the
+// stand-alone prolongation kernel: the (y, z)-interpolated coarse columns
+// once per (plane, row) of the halo box, then each cell's x-interpolation,
+// times its unknown flag.  Halo cells across a periodic face take the wrapped
+// cell's value; other cells outside the grid hold 0 (their faces are closed).
+// The sums are those of k_warm_ls, in the same order, and the owned cells'
+// q goes to qout for the step kernels.
+//
+// Column slots: the unwrapped halo cells fx in [fa, fb] (at most 34) need the
+// coarse columns c0(fa) .. c0(fb) + 1; c0 is floor((f + 1/2)/S - 1/2) before
+// the clamp, so c0(fb) - c0(fa) <= floor(33 / S) + 1 and at most
+// floor(33 / S) + 3 <= 34 / S + 3 slots are used.  Wrapped cells (a periodic
+// x face) take their columns from yc directly.
+template <int S>
+struct LsTile {
+    static constexpr int HX = 34, HY = 10, HZ = kEstChunk + 2, CW = 34 / S + 3;
+    float q[HZ][HY][HX];
+    float col[HZ][HY][CW];
+    float wx[HX], wy[HY], wz[HZ];
+    int fx[HX], fy[HY], fz[HZ];          // fine coordinate (wrapped), -1 outside the grid
+    int x0[HX], x1[HX];                  // column slots (>= 0) or -1 - coarse column (wrapped cell)
+    int y0[HY], y1[HY], z0[HZ], z1[HZ];  // coarse rows and planes
+};
+
+// fine coordinate of halo offset f on an axis of n cells: wrapped on a
+// periodic axis, else -1 outside the grid
+__device__ __forceinline__ int halo_coord(int f, int n, int per) {
+    if (f >= 0 && f < n) return f;
+    if (!per) return -1;
+    f %= n;
+    return f < 0 ? f + n : f;
+}
+
+template <typename T, int S>
+__global__ void __launch_bounds__(256) k_warm_ls_c(Geo<T> g, const T* __restrict__ r, const float* __restrict__ yc,
+                                                   float* __restrict__ qout, double* alpha, Reduce red, int in_loop) {
+    using LT = LsTile<S>;
+    __shared__ LT L;
+    pdl_wait();
+    const Dom& d = g.d;
+    if (red.sc->done) return;      // uniform over the grid
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    const int Xc = (d.nx + S - 1) / S, Yc = (d.ny + S - 1) / S, Zc = (d.nz + S - 1) / S;
+    const int X0 = blockIdx.x * 32 - 1, Y0 = blockIdx.y * 8 - 1, Z0 = blockIdx.z * kEstChunk - 1;
+    int cmin;
+    {
+        float w;
+        prolong_w(max(X0, 0), S, Xc, cmin, w);
+    }
+    if (tid < LT::HX) {
+        const int f = X0 + tid, fw = halo_coord(f, d.nx, d.perx);
+        const bool wrapped = fw >= 0 && fw != f;
+        int c0 = 0;
+        float w = 0.f;
+        if (fw >= 0) prolong_w(fw, S, Xc, c0, w);
+        const int c1 = min(c0 + 1, Xc - 1);
+        L.fx[tid] = fw;
+        L.wx[tid] = w;
+        L.x0[tid] = wrapped ? -1 - c0 : c0 - cmin;
+        L.x1[tid] = wrapped ? -1 - c1 : c1 - cmin;
+    } else if (tid >= 64 && tid < 64 + LT::HY) {
+        const int h = tid - 64, fw = halo_coord(Y0 + h, d.ny, d.pery);
+        int c0 = 0;
+        float w = 0.f;
+        if (fw >= 0) prolong_w(fw, S, Yc, c0, w);
+        L.fy[h] = fw;
+        L.wy[h] = w;
+        L.y0[h] = c0;
+        L.y1[h] = min(c0 + 1, Yc - 1);
+    } else if (tid >= 96 && tid < 96 + LT::HZ) {
+        const int h = tid - 96, fw = halo_coord(Z0 + h, d.nz, d.perz);
+        int c0 = 0;
+        float w = 0.f;
+        if (fw >= 0) prolong_w(fw, S, Zc, c0, w);
+        L.fz[h] = fw;
+        L.wz[h] = w;
+        L.z0[h] = c0;
+        L.z1[h] = min(c0 + 1, Zc - 1);
+    }
+    __syncthreads();
+    for (int q = tid; q < LT::HZ * LT::HY * LT::CW; q += 256) {
+        const int c = q % LT::CW, hy = (q / LT::CW) % LT::HY, hz = q / (LT::CW * LT::HY);
+        const int cc = cmin + c;
+        float v = 0.f;
+        if (cc < Xc && L.fy[hy] >= 0 && L.fz[hz] >= 0)
+            v = prolong_col(yc, Xc, Yc, cc, L.y0[hy], L.y1[hy], L.wy[hy], L.z0[hz], L.z1[hz], L.wz[hz]);
+        L.col[hz][hy][c] = v;
+    }
+    __syncthreads();
+    for (int q = tid; q < LT::HZ * LT::HY * LT::HX; q += 256) {
+        const int hx = q % LT::HX, hy = (q / LT::HX) % LT::HY, hz = q / (LT::HX * LT::HY);
+        const int fx = L.fx[hx], fy = L.fy[hy], fz = L.fz[hz];
+        float v = 0.f;
+        if (fx >= 0 && fy >= 0 && fz >= 0 && (g.flags[d.at(fx + 1, fy + 1, fz + 1)] & F_UNK)) {
+            const int a = L.x0[hx], b = L.x1[hx];
+            float v0, v1;
+            if (a >= 0) {
+                v0 = L.col[hz][hy][a];
+                v1 = L.col[hz][hy][b];
+            } else {
+                v0 = prolong_col(yc, Xc, Yc, -1 - a, L.y0[hy], L.y1[hy], L.wy[hy], L.z0[hz], L.z1[hz], L.wz[hz]);
+                v1 = prolong_col(yc, Xc, Yc, -1 - b, L.y0[hy], L.y1[hy], L.wy[hy], L.z0[hz], L.z1[hz], L.wz[hz]);
+            }
+            v = prolong_mix(v0, v1, L.wx[hx]);
+        }
+        L.q[hz][hy][hx] = v;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i = blockIdx.x * 32 + tx + 1, j = blockIdx.y * 8 + ty + 1;
+    const int kb = blockIdx.z * kEstChunk + 1, ke = min(kb + kEstChunk, d.nz + 1);
+    T s0 = T(0), s1 = T(0);
+    if (i <= d.nx && j <= d.ny) {
+        const int pl = (int)d.plane, sz = d.nx * d.ny;
+        const long long c0 = d.at(i, j, kb);
+        const int v0 = ((kb - 1) * d.ny + (j - 1)) * d.nx + (i - 1);
+#pragma unroll
+        for (int m = 0; m < kEstChunk; ++m) {
+            if (kb + m >= ke) break;
+            const float* qq = &L.q[m + 1][ty + 1][tx + 1];
+            qout[v0 + m * sz] = qq[0];
+            const uint8_t f = g.flags[c0 + (long long)m * pl];
+            if (!(f & F_UNK)) continue;
+            const int k = kb + m;
+            const T qc = (T)qq[0], rc = r[c0 + (long long)m * pl];
+            const T qe = (T)qq[1], qw = (T)qq[-1];
+            const T qn = (T)qq[LT::HX], qs = (T)qq[-LT::HX];
+            const T qt = (T)qq[LT::HY * LT::HX], qb = (T)qq[-LT::HY * LT::HX];
+            T aq = T(0);
+            if (f & F_E) aq += g.cx * (qe - qc);
+            if (f & F_W) aq += g.cx * (qw - qc);
+            if (f & F_N) aq += g.cy * (qn - qc);
+            if (f & F_S) aq += g.cy * (qs - qc);
+            if (f & F_T) aq += g.cT[k] * (qt - qc);
+            if (f & F_B) aq += g.cB[k] * (qb - qc);
+            const T vq = g.dz[k] * qc;
+            s0 += vq * rc;
+            s1 += vq * aq;
+        }
+    }
+    double x[2] = {(double)s0, (double)s1};
+    if (grid_sum<2>(x, red)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            const double a = x[0] / x[1];
+            *alpha = (x[1] != 0.0 && isfinite(a)) ? a : 0.0;
+            if (in_loop) {
+                red.sc->zcopy = red.sc->zflag;
+                red.sc->zflag = 0;
+            }
+        }
+    }
+}
+
 // the steps along q: a (32 x 8) column tile over kEstChunk planes per CTA
 // (few CTAs: the launch, not the work, bounds these kernels otherwise)
 template <typename T>
@@ -1414,6 +1603,27 @@ int launch_warm(const Geo<T>& g, const T* r, const float* q, double* ph, T* dl, 
         launch_pdl(k_warm_apply_dl<T>, grid, blk, 0, s, g, dl, q, alpha, (const Scalars*)red.sc);
     else
         launch_pdl(k_warm_apply<T>, grid, blk, 0, s, g, ph, q, alpha, (const Scalars*)red.sc);
+    return 2;
+}
+
+template <typename T>
+int launch_warm_coarse(const Geo<T>& g, const T* r, const float* yc, int st, float* q, double* ph, T* dl,
+                       double* alpha, const Reduce& red, cudaStream_t s) {
+    const Dom& d = g.d;
+    const dim3 grid((d.nx + 31) / 32, (d.ny + 7) / 8, (d.nz + kEstChunk - 1) / kEstChunk), blk(32, 8);
+    const int il = dl ? 1 : 0;
+    switch (st) {
+        case 1: launch_pdl(k_warm_ls_c<T, 1>, grid, blk, 0, s, g, r, yc, q, alpha, red, il); break;
+        case 2: launch_pdl(k_warm_ls_c<T, 2>, grid, blk, 0, s, g, r, yc, q, alpha, red, il); break;
+        case 4: launch_pdl(k_warm_ls_c<T, 4>, grid, blk, 0, s, g, r, yc, q, alpha, red, il); break;
+        default: launch_pdl(k_warm_ls_c<T, 8>, grid, blk, 0, s, g, r, yc, q, alpha, red, il); break;
+    }
+    if (dl)
+        launch_pdl(k_warm_apply_dl<T>, grid, blk, 0, s, g, dl, (const float*)q, (const double*)alpha,
+                   (const Scalars*)red.sc);
+    else
+        launch_pdl(k_warm_apply<T>, grid, blk, 0, s, g, ph, (const float*)q, (const double*)alpha,
+                   (const Scalars*)red.sc);
     return 2;
 }
 
@@ -1863,6 +2073,8 @@ int launch_refine_ens(const EnsTab<float>& tab, int dcur, const CondArgs& ca, cu
                                 cudaStream_t);                                                          \
     template int launch_warm_pending<T>(const Geo<T>&, T*, const float*, T*, double*, const Reduce&,            \
                                         cudaStream_t);                                                  \
+    template int launch_warm_coarse<T>(const Geo<T>&, const T*, const float*, int, float*, double*, T*, double*, \
+                                       const Reduce&, cudaStream_t);                                    \
     template int launch_record<T>(const Geo<T>&, const double*, const double*, T*, int, cudaStream_t);
 
 LES_INSTANTIATE(float)

@@ -284,6 +284,24 @@ void forward_fused(les_net_s* n, const Level& L0, const int* gate) {
     nn::head(n->dd[0], n->w32 + n->off[kConvs], n->mask, n->y, L0.v(), kHeadC, s, gate);
 }
 
+// the same on the tcgen05 engine with the packing folded into the first
+// convolution's staging (input from the pooled residual n->rc, the pooled
+// mask n->mask and the RMS n->dscal[0]) and the head into the last one's
+// epilogue; the values are those of forward_fused after k_pack_dense
+void forward_tc_folded(les_net_s* n, const Level& L0, const int* gate) {
+    cudaStream_t s = n->stream;
+    const Level L1 = level(L0, 1), L2 = level(L0, 2);
+    const nn::ConvSplit* sp = &n->split;
+    nn::conv3_tc_fwd_packed(n->rc, n->mask, n->dscal, n->wb[0], n->e[0], L0.X, L0.Y, L0.Z, 16, 1, s, gate, sp);
+    nn::conv3_fwd_pool(n->e[0], n->wb[1], n->e[1], L0.X, L0.Y, L0.Z, 16, 32, 1, s, gate, sp);
+    nn::conv3_fwd_pool(n->e[1], n->wb[2], n->e[2], L1.X, L1.Y, L1.Z, 32, 64, 1, s, gate, sp);
+    nn::conv3_fwd_pool(n->e[2], n->wb[3], n->e[3], L2.X, L2.Y, L2.Z, 64, 128, 1, s, gate, sp);
+    nn::conv3_fwd_up(n->e[3], n->wb[4], n->r[2], n->e[2], n->dd[2], L2.X, L2.Y, L2.Z, 128, 64, 1, s, gate, sp);
+    nn::conv3_fwd_up(n->dd[2], n->wb[5], n->r[1], n->e[1], n->dd[1], L1.X, L1.Y, L1.Z, 64, 32, 1, s, gate, sp);
+    nn::conv3_tc_fwd_up_head(n->dd[1], n->wb[6], n->e[0], L0.X, L0.Y, L0.Z, 32, 1, n->w32 + n->off[kConvs], n->mask,
+                             n->y, s, gate, sp);
+}
+
 // forward on the packed input n->xin with mask n->mask; output n->y
 // (every kernel returns at once while *gate != 0; gate may be null)
 void forward(les_net_s* n, const Level& L0, const int* gate = nullptr) {
@@ -490,23 +508,31 @@ int net_predict_persistent(les_net_s* n, const Dom& d, const float* r_padded, co
 int net_persistent_launches() { return 4; }     // pool, barrier reset, network, prolongation
 
 long long net_generation(const les_net_s* n) { return n->ws_gen; }
-int net_predict(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, float* out_dense,
-                cudaStream_t s, const int* gate, cudaEvent_t after_pool) {
+// pooling (+ RMS and packing), the network and, with out_dense set, the
+// prolongation onto the fine unknowns
+int predict_impl(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, float* out_dense,
+                 cudaStream_t s, const int* gate, cudaEvent_t after_pool, bool fold) {
     nn::set_conv_engine(n->engine, n->tc_timeout);
     const Level Lf{d.nx, d.ny, d.nz};
     const Level L0 = coarse(n, Lf);
     cudaStream_t keep = n->stream;
     n->stream = s;
     int rc = ensure_ws(n, L0);
+    // tcgen05 with the pooling + RMS kernel: packing and head folded into the convolutions
+    const bool folded = fold && n->engine == nn::kEngineTcgen05 && L0.v() <= nn::kPoolRmsMax;
     if (!rc) {
         if (L0.v() <= nn::kPoolRmsMax) {
             // pooling and RMS in one launch, the pooled mask straight into the
             // head's mask, then the packing
             nn::pool_rms(r_padded, flags, d, n->stride, n->rc, n->mask, n->pp_part, n->pp_count, n->dscal, s, gate);
             if (after_pool) cudaEventRecord(after_pool, s);      // the residual has been read
-            launch_pdl(k_pack_dense, dim3((unsigned)((L0.v() + 255) / 256)), dim3(256), 0, s, (const float*)n->rc,
-                       (const float*)n->mask, (const double*)n->dscal, n->xin, (size_t)L0.v(), gate);
-            n->last_launches = 2;
+            n->last_launches = 1;
+            if (!folded) {
+                launch_pdl(k_pack_dense, dim3((unsigned)((L0.v() + 255) / 256)), dim3(256), 0, s,
+                           (const float*)n->rc, (const float*)n->mask, (const double*)n->dscal, n->xin,
+                           (size_t)L0.v(), gate);
+                n->last_launches += 1;
+            }
         } else {
             nn::pool_padded_s(r_padded, flags, d, n->stride, n->rc, n->mc, s, gate);
             if (after_pool) cudaEventRecord(after_pool, s);
@@ -515,14 +541,33 @@ int net_predict(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t
         }
     }
     if (!rc) {
-        forward_fused(n, L0, gate);
-        nn::prolong_flags(n->y, flags, d, n->stride, out_dense, s, gate);
-        n->last_launches += 8 + 1;
+        if (folded) {
+            forward_tc_folded(n, L0, gate);
+            n->last_launches += 7;
+        } else {
+            forward_fused(n, L0, gate);
+            n->last_launches += 8;
+        }
+        if (out_dense) {
+            nn::prolong_flags(n->y, flags, d, n->stride, out_dense, s, gate);
+            n->last_launches += 1;
+        }
         if (cudaGetLastError() != cudaSuccess) rc = LES_ECUDA;
     }
     n->stream = keep;
     return rc;
 }
+
+int net_predict(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, float* out_dense,
+                cudaStream_t s, const int* gate, cudaEvent_t after_pool, bool fold) {
+    return predict_impl(n, d, r_padded, flags, out_dense, s, gate, after_pool, fold);
+}
+int net_predict_coarse(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, cudaStream_t s,
+                       const int* gate) {
+    return predict_impl(n, d, r_padded, flags, nullptr, s, gate, nullptr, true);
+}
+const float* net_coarse_out(const les_net_s* n) { return n->y; }
+int net_stride(const les_net_s* n) { return n->stride; }
 int net_launches(const les_net_s* n) { return n->last_launches; }   // of the last net_predict
 }  // namespace les
 

@@ -25,7 +25,10 @@ struct ConvSplit {
 //   IN_POOL    mean of the 8 children x[2gz+c][2gy+b][2gx+a] (missing children count as
 //              zero; summed in the order of the stand-alone pooling kernel, so the
 //              staged values are bit-identical to pooling first)
-enum { IN_DIRECT = 0, IN_UP = 1, IN_POOL = 2 };
+//   IN_PACK    the network input formed from the pooled residual: channel 0 =
+//              pm r / rms, channel 1 = pm, the rest 0 (pm the pooled unknown
+//              fraction, rms = scale[0]; the values of the packing kernel)
+enum { IN_DIRECT = 0, IN_UP = 1, IN_POOL = 2, IN_PACK = 3 };
 struct ConvArgs {
     const __nv_bfloat16* x;
     const __nv_bfloat16* w;
@@ -40,6 +43,17 @@ struct ConvArgs {
     float* part;
     unsigned* cnt;
     int ks;
+    // IN_PACK sources (level-0 volumes and the RMS)
+    const float* prc;
+    const float* pmask;
+    const double* pscale;
+    // head folded into the epilogue (head_y set; Cout == 16, one CTA holds
+    // every channel of a voxel): head_y = head_mask * sum_c head_w[c] d[c],
+    // d = BF16(BF16(relu(conv)) + skip) as the stand-alone head reads it, in
+    // its order c = 0, 1, ...; the convolution's own outputs are not stored
+    const float* head_w;
+    const float* head_mask;
+    float* head_y;
 };
 
 // Which tensor-core path the forward convolutions (inference, and the
@@ -51,6 +65,17 @@ constexpr int kEngineMmaSync = 0, kEngineTcgen05 = 1;
 void set_conv_engine(int engine, int* timeout);
 int conv3_tc_prepare();
 void conv3_tc_launch(ConvArgs A, int in_mode, cudaStream_t s, const int* gate, const ConvSplit* split, int* timeout);
+// tcgen05 inference: the first convolution (16 input channels) reading the
+// packed input straight from the pooled residual rc, the pooled mask pm and
+// the RMS scale[0]; the last decoder convolution (Cout 16, nearest
+// upsampling of xc, skip added) with the head folded in, writing only the
+// coarse output y_head (mask pm)
+void conv3_tc_fwd_packed(const float* rc, const float* pm, const double* scale, const __nv_bfloat16* w,
+                         __nv_bfloat16* y, int X, int Y, int Z, int Cout, int relu, cudaStream_t s, const int* gate,
+                         const ConvSplit* split);
+void conv3_tc_fwd_up_head(const __nv_bfloat16* xc, const __nv_bfloat16* w, const __nv_bfloat16* skip, int X, int Y,
+                          int Z, int Cin, int relu, const float* head_w, const float* pm, float* y_head, cudaStream_t s,
+                          const int* gate, const ConvSplit* split);
 
 void conv3_fwd(const __nv_bfloat16* x, const __nv_bfloat16* w, __nv_bfloat16* y, const __nv_bfloat16* skip,
                __nv_bfloat16* ysum, int X, int Y, int Z, int Cin, int Cout, int relu, cudaStream_t s,

@@ -346,6 +346,27 @@ void conv3_fwd_up(const __nv_bfloat16* xc, const __nv_bfloat16* w, __nv_bfloat16
                         (Z + 1) / 2, split);
 }
 
+void conv3_tc_fwd_packed(const float* rc, const float* pm, const double* scale, const __nv_bfloat16* w,
+                         __nv_bfloat16* y, int X, int Y, int Z, int Cout, int relu, cudaStream_t s, const int* gate,
+                         const ConvSplit* split) {
+    ConvArgs A{nullptr, w, y, nullptr, nullptr, X, Y, Z, 16, Cout, relu, X, Y, Z, nullptr, nullptr, 1};
+    A.prc = rc;
+    A.pmask = pm;
+    A.pscale = scale;
+    conv3_tc_launch(A, IN_PACK, s, gate, split, g_conv_timeout);
+}
+
+void conv3_tc_fwd_up_head(const __nv_bfloat16* xc, const __nv_bfloat16* w, const __nv_bfloat16* skip, int X, int Y,
+                          int Z, int Cin, int relu, const float* head_w, const float* pm, float* y_head, cudaStream_t s,
+                          const int* gate, const ConvSplit* split) {
+    ConvArgs A{xc, w, nullptr, skip, nullptr, X, Y, Z, Cin, 16, relu, (X + 1) / 2, (Y + 1) / 2, (Z + 1) / 2,
+               nullptr, nullptr, 1};
+    A.head_w = head_w;
+    A.head_mask = pm;
+    A.head_y = y_head;
+    conv3_tc_launch(A, IN_UP, s, gate, split, g_conv_timeout);
+}
+
 void conv3_fwd_pool(const __nv_bfloat16* xf, const __nv_bfloat16* w, __nv_bfloat16* y, int Xf, int Yf, int Zf,
                     int Cin, int Cout, int relu, cudaStream_t s, const int* gate, const ConvSplit* split) {
     conv3_launch<IN_POOL>(xf, w, y, nullptr, nullptr, (Xf + 1) / 2, (Yf + 1) / 2, (Zf + 1) / 2, Cin, Cout, relu, s,
@@ -723,22 +744,10 @@ __global__ void k_pool_rms(const float* r, const uint8_t* flags, Dom d, float* r
     }
 }
 
-// trilinear prolongation of a coarse cell-centred field to the fine cells,
-// times the fine mask: fine centre f sits at coarse coordinate (f + 1/2)/s - 1/2
-// on each axis, clamped to the first / last coarse centre
-__device__ __forceinline__ void lin_w(int f, int s, int C, int& c0, float& w) {
-    const float x = ((float)f + 0.5f) / (float)s - 0.5f;
-    c0 = (int)floorf(x);
-    w = x - (float)c0;
-    if (c0 < 0) {
-        c0 = 0;
-        w = 0.f;
-    }
-    if (c0 >= C - 1) {
-        c0 = C - 1;
-        w = 0.f;
-    }
-}
+// trilinear prolongation of a coarse cell-centred field to the fine cells
+// (the weights of prolong_w: fine centre f at coarse coordinate (f + 1/2)/s - 1/2,
+// clamped to the first / last coarse centre)
+__device__ __forceinline__ void lin_w(int f, int s, int C, int& c0, float& w) { prolong_w(f, s, C, c0, w); }
 __device__ __forceinline__ float trilinear(const float* y, int Xc, int Yc, int Zc, int s, int fx, int fy, int fz) {
     int x0, y0, z0;
     float wx, wy, wz;
@@ -786,15 +795,10 @@ __global__ void __launch_bounds__(256) k_prolong_flags(const float* yc, const ui
         float wz;
         lin_w(z, S, Zc, z0, wz);
         const int z1 = min(z0 + 1, Zc - 1);
-        auto col = [&](int c) {
-            auto at = [&](int b, int cc) { return yc[((size_t)cc * Yc + b) * Xc + c]; };
-            const float a0 = (1.f - wy) * at(y0, z0) + wy * at(y1, z0);
-            const float a1 = (1.f - wy) * at(y0, z1) + wy * at(y1, z1);
-            return (1.f - wz) * a0 + wz * a1;
-        };
-        const float v0 = col(x0), v1 = col(x1);
+        const float v0 = prolong_col(yc, Xc, Yc, x0, y0, y1, wy, z0, z1, wz);
+        const float v1 = prolong_col(yc, Xc, Yc, x1, y0, y1, wy, z0, z1, wz);
         const long long row = d.at(1, y + 1, z + 1);
-        out[((size_t)z * d.ny + y) * d.nx + x] = (flags[row + x] & F_UNK) ? (1.f - wx) * v0 + wx * v1 : 0.f;
+        out[((size_t)z * d.ny + y) * d.nx + x] = (flags[row + x] & F_UNK) ? prolong_mix(v0, v1, wx) : 0.f;
     }
 }
 

@@ -168,6 +168,18 @@ __device__ __forceinline__ void stage_half(const ConvArgs& A, int gx, int gy, in
 #pragma unroll
         for (int c = 0; c < 8; ++c) o[c] = __float2bfloat16(0.125f * a[c]);
         *reinterpret_cast<uint4*>(dstp) = *reinterpret_cast<const uint4*>(o);
+    } else if constexpr (IN == IN_PACK) {
+        __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) o[c] = __float2bfloat16(0.f);
+        if (ok && c0 == 0) {
+            const size_t v = ((size_t)gz * A.Y + gy) * A.X + gx;
+            const double sc = A.pscale[0];
+            const float s = (float)(sc > 0.0 ? 1.0 / sc : 0.0);
+            o[0] = __float2bfloat16(A.pmask[v] * A.prc[v] * s);
+            o[1] = __float2bfloat16(A.pmask[v]);
+        }
+        *reinterpret_cast<uint4*>(dstp) = *reinterpret_cast<const uint4*>(o);
     } else {
         const int sx = IN == IN_UP ? gx >> 1 : gx, sy = IN == IN_UP ? gy >> 1 : gy, sz = IN == IN_UP ? gz >> 1 : gz;
         const __nv_bfloat16* src = ok ? A.x + (((size_t)sz * A.Ys + sy) * A.Xs + sx) * A.Cin + c0 : A.x;
@@ -310,6 +322,37 @@ __global__ void __launch_bounds__(NTH) k_conv3_tc(ConvArgs A, const int* gate, i
         if (tid == 0) A.cnt[tile] = 0u;
     }
     const int gx = x0 + (row & 7), gy = y0 + (row >> 3);
+    if (A.head_y) {
+        // the head: warps 0-3 sum channels 0-7 of their rows, warps 4-7 carry
+        // the same rows' sums on through channels 8-15 (CO == Cout == 16)
+        __shared__ float hsum[128];
+        const bool valid = gx < X && gy < Y;
+        const size_t o = (((size_t)z0 * Y + gy) * X + gx) * 16 + cbase;
+        auto part = [&](float s) {
+#pragma unroll
+            for (int n = 0; n < NC; n += 2) {
+                float v0 = acc[n], v1 = acc[n + 1];
+                if (A.relu) {
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                }
+                const __nv_bfloat162 r = __floats2bfloat162_rn(v0, v1);
+                const __nv_bfloat162 sk = *reinterpret_cast<const __nv_bfloat162*>(A.skip + o + n);
+                const __nv_bfloat162 dv = __floats2bfloat162_rn(__bfloat162float(r.x) + __bfloat162float(sk.x),
+                                                                __bfloat162float(r.y) + __bfloat162float(sk.y));
+                s += A.head_w[cbase + n] * __bfloat162float(dv.x);
+                s += A.head_w[cbase + n + 1] * __bfloat162float(dv.y);
+            }
+            return s;
+        };
+        if (warp < 4) hsum[row] = valid ? part(0.f) : 0.f;
+        __syncthreads();
+        if (warp >= 4 && valid) {
+            const size_t v = ((size_t)z0 * Y + gy) * X + gx;
+            A.head_y[v] = A.head_mask[v] * part(hsum[row]);
+        }
+        return;
+    }
     if (gx >= X || gy >= Y) return;
     const size_t o = (((size_t)z0 * Y + gy) * X + gx) * Cout + co0 + cbase;
     if (co0 + cbase >= Cout) return;
@@ -354,6 +397,7 @@ int conv3_tc_prepare() {
     if ((x = allow_tc<16, IN_UP>()) != cudaSuccess) e = x;
     if ((x = allow_tc<32, IN_POOL>()) != cudaSuccess) e = x;
     if ((x = allow_tc<16, IN_POOL>()) != cudaSuccess) e = x;
+    if ((x = allow_tc<16, IN_PACK>()) != cudaSuccess) e = x;
     return e == cudaSuccess ? 0 : -1;
 }
 
@@ -361,7 +405,8 @@ void conv3_tc_launch(ConvArgs A, int in_mode, cudaStream_t s, const int* gate, c
     // 32 output channels per CTA when the grid fills the GPU, else 16; small
     // grids split their input-channel chunks over up to about two CTAs per SM
     const long long tiles = (long long)((A.X + TCX - 1) / TCX) * ((A.Y + TCY - 1) / TCY) * A.Z;
-    const int co = (A.Cout >= 32 && tiles * (A.Cout / 32) >= 2 * 152) ? 32 : 16;
+    const bool co16 = in_mode == IN_PACK || A.head_y;       // the modes built for 16 channels per CTA
+    const int co = (!co16 && A.Cout >= 32 && tiles * (A.Cout / 32) >= 2 * 152) ? 32 : 16;
     dim3 grid((A.X + TCX - 1) / TCX, (A.Y + TCY - 1) / TCY, A.Z * ((A.Cout + co - 1) / co));
     int ks = 1;
     if (split) {
@@ -377,7 +422,9 @@ void conv3_tc_launch(ConvArgs A, int in_mode, cudaStream_t s, const int* gate, c
     A.ks = ks;
     const size_t smem = co == 32 ? tc_smem<32>() : tc_smem<16>();
 #define LES_TC_LAUNCH(CO_, IN_) launch_pdl(k_conv3_tc<CO_, IN_>, grid, dim3(NTH), smem, s, A, gate, timeout)
-    if (co == 32) {
+    if (in_mode == IN_PACK) {
+        LES_TC_LAUNCH(16, IN_PACK);
+    } else if (co == 32) {
         if (in_mode == IN_UP) LES_TC_LAUNCH(32, IN_UP);
         else if (in_mode == IN_POOL) LES_TC_LAUNCH(32, IN_POOL);
         else LES_TC_LAUNCH(32, IN_DIRECT);

@@ -26,6 +26,7 @@ LES_WARM_PREV, LES_WARM_NET, LES_WARM_ZERO = 0, 1, 2
 LES_SOR_REDBLACK, LES_SOR_TWINNED = 0, 1
 LES_SOR_NTILES = 29                 # sweep tile indices 0 .. LES_SOR_NTILES - 1 (les_set_sor_config)
 LES_NET_MMA_SYNC, LES_NET_TCGEN05 = 0, 1
+LES_NET_KERNELS_FOLDED, LES_NET_KERNELS_PERSISTENT, LES_NET_KERNELS_LAYERS = 0, 1, 2
 
 
 class les_grid_t(ctypes.Structure):
@@ -636,7 +637,12 @@ class Domain:
         _check(lib().les_set_net_async(self.h, 1 if enable else 0), self.h)
 
     def set_net_kernels(self, persistent=True):
-        _check(lib().les_set_net_kernels(self.h, 1 if persistent else 0), self.h)
+        """True: the persistent network launch; False: per-layer launches with
+        the folded packing, head and prolongation (default); or one of the
+        LES_NET_KERNELS_* layouts."""
+        mode = persistent if not isinstance(persistent, bool) else (
+            LES_NET_KERNELS_PERSISTENT if persistent else LES_NET_KERNELS_FOLDED)
+        _check(lib().les_set_net_kernels(self.h, int(mode)), self.h)
 
     def set_warmstart(self, net=None, mode=None):
         """net given: learned warm start; else mode LES_WARM_PREV (default) or LES_WARM_ZERO."""

@@ -74,3 +74,16 @@ def test_null_handle_is_einval(libles):
     st = les.les_stats_t()
     assert libles.les_step(None, 1, ctypes.byref(st)) == les.LES_EINVAL
     assert libles.les_get_fields(None, None, None, None, None) == les.LES_EINVAL
+
+
+def test_header_constants_match_binding():
+    """Every integer #define of include/les.h that the Python binding also
+    names has the same value there."""
+    txt = open(os.path.join(ROOT, "include", "les.h")).read()
+    pat = r"^#define\s+(LES_\w+)\s+\(?(-?\d+)\)?\s*(?:/\*.*\*/)?\s*$"
+    defs = {m.group(1): int(m.group(2)) for m in re.finditer(pat, txt, flags=re.M)}
+    assert "LES_NET_KERNELS_LAYERS" in defs and "LES_EINVAL" in defs
+    shared = [k for k in defs if hasattr(les, k)]
+    assert len(shared) >= 10
+    for k in shared:
+        assert getattr(les, k) == defs[k], k

@@ -190,7 +190,7 @@ def test_train_step_reduces_loss(net):
     assert losses[-1] < 0.8 * losses[0], losses[::8]
 
 
-def city(nx=48, ny=32, nz=16, seed=4, **kw):
+def city(nx=48, ny=32, nz=16, seed=4, bc=(scene.BC_INOUT, scene.BC_FREESLIP, scene.BC_WALL), **kw):
     """A small FP32 city: five blocks, turbulent inflow, solves to tolerance."""
     kw.setdefault("fixed_sweeps", 0)
     rng = np.random.default_rng(seed)
@@ -200,7 +200,6 @@ def city(nx=48, ny=32, nz=16, seed=4, **kw):
         y0 = int(rng.integers(1, ny - 7))
         h = int(rng.integers(3, nz - 3))
         solid[:h, y0:y0 + 6, x0:x0 + 6] = 1
-    bc = (scene.BC_INOUT, scene.BC_FREESLIP, scene.BC_WALL)
     return scene.box_scene(nx, ny, nz, dz=scene.stretched_dz(nz), solid=solid, bc=bc, turb=0.1, seed=seed,
                            **kw)
 
@@ -338,6 +337,40 @@ def test_persistent_and_layer_kernels_agree(net):
     assert np.abs(u1 - u2).max() <= 1e-3 * np.abs(u2).max()
 
 
+@pytest.mark.parametrize("stride,engine,periodic", [(8, "tcgen05", True), (4, "tcgen05", False),
+                                                    (2, "mma.sync", True), (1, "tcgen05", True)])
+def test_folded_kernels_match_standalone(net, stride, engine, periodic):
+    """The folded kernel layout (packing inside the first convolution, head
+    inside the last, prolongation inside the line search) computes the values
+    of the stand-alone packing, head and prolongation kernels: identical
+    sweep counts and bit-identical fields after learned-mode steps in the
+    graph loop, with the correction at the start of each solve and every 10
+    sweeps.  Periodic x and y put wrapped cells in the line search's halo."""
+    net.stride = stride
+    net.engine = les.LES_NET_TCGEN05 if engine == "tcgen05" else les.LES_NET_MMA_SYNC
+    kw = dict(tol=1e-6, max_sweeps=40000, check_every=10)
+    if periodic:
+        kw["bc"] = (scene.BC_PERIODIC, scene.BC_PERIODIC, scene.BC_WALL)
+    sc = city(**kw)
+    doms = []
+    for mode in (les.LES_NET_KERNELS_FOLDED, les.LES_NET_KERNELS_LAYERS):
+        d = les.Domain(sc)
+        d.set_warmstart(net)
+        d.set_net_schedule(10)
+        d.set_net_kernels(mode)
+        doms.append(d)
+    try:
+        for _ in range(2):
+            a, b = doms[0].step(), doms[1].step()
+            assert a["rc"] == b["rc"] == 0 and a["sweeps"] == b["sweeps"], (a, b)
+        for fa, fb in zip(doms[0].fields(), doms[1].fields()):
+            assert np.array_equal(fa, fb)
+        print(f"stride {stride} {engine} periodic={periodic}: {a['sweeps']} sweeps, bit-identical")
+    finally:
+        for d in doms:
+            d.close()
+
+
 def test_warm_start_rejects_bad_use(net):
     sc = city()
     d64 = les.Domain(sc, precision=les.LES_FP64)
@@ -348,6 +381,8 @@ def test_warm_start_rejects_bad_use(net):
         d32.aux(les.LES_AUX_R0)                 # recording is off
     with pytest.raises(les.LesError):
         les.les_set_warmstart(d32.h, 7, None)
+    with pytest.raises(les.LesError):
+        d32.set_net_kernels(3)                  # no such kernel layout
     d64.close()
     d32.close()
 
