@@ -457,28 +457,24 @@ k_nut(Geo<T> g, const T* __restrict__ u, const T* __restrict__ v, const T* __res
     const int k0 = 1 + blockIdx.z * kc, k1 = min(k0 + kc, d.nz + 1);
     const T* const src[3] = {u, v, w};
     T* const dst[3] = {sU, sV, sW};
-    // three register stages: the planes k+1, k+2 and k+3 are in flight while
-    // plane k is computed
-    Window<T, 3, MX, MY, NT> w0, w1, w2;
+    Window<T, 3, MX, MY, NT> win;
     const SmemStencil<T, MX, MY> S(g, sU, sV, sW, ib, jb);
     const bool own = i <= d.nx && j <= d.ny;
-    w0.fetch(d, src, ib, jb, k0 - 1, tid);
-    w0.put(dst, k0 - 1, tid);
-    w0.fetch(d, src, ib, jb, k0, tid);
-    w0.put(dst, k0, tid);
-    w0.fetch(d, src, ib, jb, k0 + 1, tid);
-    if (k0 + 2 <= k1) w1.fetch(d, src, ib, jb, k0 + 2, tid);
-    if (k0 + 3 <= k1) w2.fetch(d, src, ib, jb, k0 + 3, tid);
-    auto plane = [&](int k, Window<T, 3, MX, MY, NT>& stage) {
+    win.fetch(d, src, ib, jb, k0 - 1, tid);
+    win.put(dst, k0 - 1, tid);
+    win.fetch(d, src, ib, jb, k0, tid);
+    win.put(dst, k0, tid);
+    win.fetch(d, src, ib, jb, k0 + 1, tid);
+    for (int k = k0; k < k1; ++k) {
         const long long c = own ? d.at(i, j, k) : 0;
         const uint8_t f = own ? g.flags[c] : 0;
-        stage.put(dst, k + 1, tid);
+        win.put(dst, k + 1, tid);
         __syncthreads();
-        if (k + 4 <= k1) stage.fetch(d, src, ib, jb, k + 4, tid);
-        if (!own) return;
+        if (k + 2 <= k1) win.fetch(d, src, ib, jb, k + 2, tid);
+        if (!own) continue;
         if (!(f & F_FLUID)) {
             nut[c] = T(0);
-            return;
+            continue;
         }
         T s11 = (S.U(i, j, k) - S.U(i - 1, j, k)) * g.rdx;
         T s22 = (S.V(i, j, k) - S.V(i, j - 1, k)) * g.rdy;
@@ -488,11 +484,6 @@ k_nut(Geo<T> g, const T* __restrict__ u, const T* __restrict__ v, const T* __res
         T s23 = T(0.25) * (S.s23(i, j - 1, k - 1) + S.s23(i, j, k - 1) + S.s23(i, j - 1, k) + S.s23(i, j, k));
         T smag = sqrt(T(2) * (s11 * s11 + s22 * s22 + s33 * s33) + T(4) * (s12 * s12 + s13 * s13 + s23 * s23));
         nut[c] = g.delta2[k] * smag;
-    };
-    for (int k = k0; k < k1; k += 3) {
-        plane(k, w0);
-        if (k + 1 < k1) plane(k + 1, w1);
-        if (k + 2 < k1) plane(k + 2, w2);
     }
 }
 
@@ -699,8 +690,6 @@ int column_kc(const Dom& d) {
     return (int)(kc < 1 ? 1 : (kc > d.nz ? d.nz : kc));
 }
 
-constexpr int kRhsUnroll = 4;
-
 template <typename T>
 __global__ void k_rhs(Geo<T> g, const T* us, const T* vs, const T* ws, T* rhs, double vfluid, Reduce r, int kc) {
     const Dom& d = g.d;
@@ -709,36 +698,92 @@ __global__ void k_rhs(Geo<T> g, const T* us, const T* vs, const T* ws, T* rhs, d
     const int kb = blockIdx.z * kc + 1, ke = min(kb + kc, d.nz + 1);
     double x[1] = {0.0};
     if (i <= d.nx && j <= d.ny) {
-        // every load is issued unconditionally (the padded arrays hold each
-        // neighbour), kRhsUnroll planes at a time, so that the loads of
-        // several planes are in flight together; the flag selects the result
         long long c = d.at(i, j, kb);
-        for (int k = kb; k < ke; k += kRhsUnroll, c += kRhsUnroll * d.plane) {
-            uint8_t f[kRhsUnroll];
-            T ue[kRhsUnroll], uw[kRhsUnroll], vn[kRhsUnroll], vs_[kRhsUnroll], wt[kRhsUnroll], wb[kRhsUnroll];
-#pragma unroll
-            for (int m = 0; m < kRhsUnroll; ++m) {
-                const bool in = k + m < ke;
-                const long long cm = in ? c + m * d.plane : c;
-                f[m] = in ? g.flags[cm] : (uint8_t)0;
-                ue[m] = us[cm];
-                uw[m] = us[cm - 1];
-                vn[m] = vs[cm];
-                vs_[m] = vs[cm - d.px];
-                wt[m] = ws[cm];
-                wb[m] = ws[cm - d.plane];
+        for (int k = kb; k < ke; ++k, c += d.plane) {
+            T val = T(0);
+            if (g.flags[c] & F_FLUID) {
+                T div = (us[c] - us[c - 1]) / g.dx + (vs[c] - vs[c - d.px]) / g.dy +
+                        (ws[c] - ws[c - d.plane]) / g.dz[k];
+                val = div / g.dt;
+                x[0] += g.dz64[k] * (double)val;
             }
+            rhs[c] = val;
+        }
+    }
+    if (grid_sum<1>(x, r)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) r.sc->rhs_mean = vfluid > 0.0 ? x[0] / vfluid : 0.0;
+    }
+}
+
+// FP32 fields: a thread takes 4 consecutive cells of a row with 16-byte
+// loads and stores (a padded row starts 16-byte aligned and cell i = 1 sits
+// 16 bytes into it, so cells 1 + 4t .. 4 + 4t are aligned), a CTA of 32 x 8
+// threads a 128 x 8 column tile over kc planes, two planes' loads in flight
+// at a time; the bottom face of a plane is the top face of the previous one,
+// kept in registers.  The per-cell arithmetic is that of k_rhs.
+struct RhsPlane {
+    uchar4 f;
+    float4 ue, vn, vsth, wt;
+    float uw;
+};
+__device__ __forceinline__ void rhs_load(const Geo<float>& g, const float* __restrict__ us,
+                                         const float* __restrict__ vs, const float* __restrict__ ws, long long c,
+                                         RhsPlane& P) {
+    P.f = *reinterpret_cast<const uchar4*>(g.flags + c);
+    P.ue = *reinterpret_cast<const float4*>(us + c);
+    P.uw = us[c - 1];
+    P.vn = *reinterpret_cast<const float4*>(vs + c);
+    P.vsth = *reinterpret_cast<const float4*>(vs + c - g.d.px);
+    P.wt = *reinterpret_cast<const float4*>(ws + c);
+}
+__global__ void __launch_bounds__(256) k_rhs4(Geo<float> g, const float* __restrict__ us, const float* __restrict__ vs,
+                                              const float* __restrict__ ws, float* __restrict__ rhs, double vfluid,
+                                              Reduce r, int kc) {
+    const Dom& d = g.d;
+    const int i = (blockIdx.x * 32 + threadIdx.x) * 4 + 1;
+    const int j = blockIdx.y * 8 + threadIdx.y + 1;
+    const int kb = blockIdx.z * kc + 1, ke = min(kb + kc, d.nz + 1);
+    double x[1] = {0.0};
+    if (i <= d.nx && j <= d.ny) {
+        const int ne = min(4, d.nx + 1 - i);             // cells of this thread inside the grid
+        long long c = d.at(i, j, kb);
+        float4 wb = *reinterpret_cast<const float4*>(ws + c - d.plane);
+        auto plane = [&](const RhsPlane& P, int k, long long cc) {
+            const uint8_t fl[4] = {P.f.x, P.f.y, P.f.z, P.f.w};
+            const float ue[4] = {P.ue.x, P.ue.y, P.ue.z, P.ue.w}, uw[4] = {P.uw, P.ue.x, P.ue.y, P.ue.z};
+            const float vn[4] = {P.vn.x, P.vn.y, P.vn.z, P.vn.w}, vsh[4] = {P.vsth.x, P.vsth.y, P.vsth.z, P.vsth.w};
+            const float wt[4] = {P.wt.x, P.wt.y, P.wt.z, P.wt.w}, wbb[4] = {wb.x, wb.y, wb.z, wb.w};
+            float val[4];
 #pragma unroll
-            for (int m = 0; m < kRhsUnroll; ++m) {
-                if (k + m >= ke) break;
-                T val = T(0);
-                if (f[m] & F_FLUID) {
-                    T div = (ue[m] - uw[m]) / g.dx + (vn[m] - vs_[m]) / g.dy + (wt[m] - wb[m]) / g.dz[k + m];
-                    val = div / g.dt;
-                    x[0] += g.dz64[k + m] * (double)val;
+            for (int e = 0; e < 4; ++e) {
+                val[e] = 0.f;
+                if (e < ne && (fl[e] & F_FLUID)) {
+                    const float div = (ue[e] - uw[e]) / g.dx + (vn[e] - vsh[e]) / g.dy + (wt[e] - wbb[e]) / g.dz[k];
+                    val[e] = div / g.dt;
+                    x[0] += g.dz64[k] * (double)val[e];
                 }
-                rhs[c + m * d.plane] = val;
             }
+            if (ne == 4) {
+                *reinterpret_cast<float4*>(rhs + cc) = make_float4(val[0], val[1], val[2], val[3]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (e < ne) rhs[cc + e] = val[e];
+            }
+            wb = P.wt;
+        };
+        int k = kb;
+        for (; k + 1 < ke; k += 2, c += 2 * d.plane) {
+            RhsPlane A, B;
+            rhs_load(g, us, vs, ws, c, A);
+            rhs_load(g, us, vs, ws, c + d.plane, B);
+            plane(A, k, c);
+            plane(B, k + 1, c + d.plane);
+        }
+        if (k < ke) {
+            RhsPlane A;
+            rhs_load(g, us, vs, ws, c, A);
+            plane(A, k, c);
         }
     }
     if (grid_sum<1>(x, r)) {
@@ -750,12 +795,19 @@ template <typename T>
 int launch_rhs(const Geo<T>& g, const T* us, const T* vs, const T* ws, T* rhs, double vfluid,
                const Reduce& r, cudaStream_t s) {
     const Dom& d = g.d;
-    // one batch of kRhsUnroll planes per thread: every load of a thread is in
-    // flight at once and the grid holds many CTAs (at most one per plane of a
-    // column tile, the size of the reduction's partials array)
-    const int kc = kRhsUnroll < d.nz ? kRhsUnroll : d.nz;
-    k_rhs<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, (d.nz + kc - 1) / kc), dim3(32, 8), 0, s>>>(
-        g, us, vs, ws, rhs, vfluid, r, kc);
+    if constexpr (std::is_same<T, float>::value) {
+        // about 4096 CTAs (a few waves), at most one per plane of a column
+        // tile (the size of the reduction's partials array)
+        const long long cols = (long long)((d.nx + 127) / 128) * ((d.ny + 7) / 8);
+        long long kc = (cols * d.nz + 4095) / 4096;
+        kc = kc < 1 ? 1 : (kc > d.nz ? d.nz : kc);
+        k_rhs4<<<dim3((d.nx + 127) / 128, (d.ny + 7) / 8, (d.nz + (int)kc - 1) / (int)kc), dim3(32, 8), 0, s>>>(
+            g, us, vs, ws, rhs, vfluid, r, (int)kc);
+    } else {
+        const int kc = column_kc(d);
+        k_rhs<T><<<dim3((d.nx + 31) / 32, (d.ny + 7) / 8, (d.nz + kc - 1) / kc), dim3(32, 8), 0, s>>>(
+            g, us, vs, ws, rhs, vfluid, r, kc);
+    }
     return 1;
 }
 
@@ -1057,26 +1109,46 @@ __device__ __forceinline__ void sor_est_body(const Geo<T>& g, const T* __restric
         uint8_t fl[kEstChunk];
 #pragma unroll
         for (int m = 0; m < kEstChunk; ++m) fl[m] = kb + m < ke ? g.flags[c0 + (long long)m * pl] : (uint8_t)0;
+        // half a chunk at a time, every load of the half issued before its
+        // use (unconditionally: the padded array holds each neighbour; a
+        // plane past the chunk reads the chunk's first plane)
+        constexpr int H = kEstChunk / 2;
 #pragma unroll
-        for (int m = 0; m < kEstChunk; ++m) {
-            const uint8_t f = fl[m];
-            if (!(f & F_UNK)) continue;
-            const int k = kb + m;
-            const long long c = c0 + (long long)m * pl;
-            const int ot = (d.perz && k == d.nz) ? -(d.nz - 1) * pl : pl;
-            const int ob = (d.perz && k == 1) ? (d.nz - 1) * pl : -pl;
-            const T dc = dl[c], de = dl[c + oe], dw = dl[c + ow], dn = dl[c + on], ds = dl[c + os];
-            const T dt = dl[c + ot], db = dl[c + ob], rc = r[c];
-            T s = T(0);
-            if (f & F_E) s += g.cx * (de - dc);
-            if (f & F_W) s += g.cx * (dw - dc);
-            if (f & F_N) s += g.cy * (dn - dc);
-            if (f & F_S) s += g.cy * (ds - dc);
-            if (f & F_T) s += g.cT[k] * (dt - dc);
-            if (f & F_B) s += g.cB[k] * (db - dc);
-            const T res = rc - s;
-            if (rout) rout[c] = res;        // the current residual, input of the network correction
-            acc += res * res;
+        for (int h = 0; h < kEstChunk; h += H) {
+            T dc[H], de[H], dw[H], dn[H], ds[H], dt[H], db[H], rc[H];
+#pragma unroll
+            for (int q = 0; q < H; ++q) {
+                const int m = h + q, k = kb + m;
+                const long long c = k < ke ? c0 + (long long)m * pl : c0;
+                const int kk = k < ke ? k : kb;
+                const int ot = (d.perz && kk == d.nz) ? -(d.nz - 1) * pl : pl;
+                const int ob = (d.perz && kk == 1) ? (d.nz - 1) * pl : -pl;
+                dc[q] = dl[c];
+                de[q] = dl[c + oe];
+                dw[q] = dl[c + ow];
+                dn[q] = dl[c + on];
+                ds[q] = dl[c + os];
+                dt[q] = dl[c + ot];
+                db[q] = dl[c + ob];
+                rc[q] = r[c];
+            }
+#pragma unroll
+            for (int q = 0; q < H; ++q) {
+                const int m = h + q;
+                const uint8_t f = fl[m];
+                if (!(f & F_UNK)) continue;
+                const int k = kb + m;
+                T s = T(0);
+                if (f & F_E) s += g.cx * (de[q] - dc[q]);
+                if (f & F_W) s += g.cx * (dw[q] - dc[q]);
+                if (f & F_N) s += g.cy * (dn[q] - dc[q]);
+                if (f & F_S) s += g.cy * (ds[q] - dc[q]);
+                if (f & F_T) s += g.cT[k] * (dt[q] - dc[q]);
+                if (f & F_B) s += g.cB[k] * (db[q] - dc[q]);
+                const T res = rc[q] - s;
+                if (rout) rout[c0 + (long long)m * pl] = res;   // the current residual, input of the network correction
+                acc += res * res;
+            }
         }
     }
     double x[1] = {(double)acc};
@@ -1337,9 +1409,13 @@ __global__ void __launch_bounds__(256) k_warm_ls(Geo<T> g, const T* __restrict__
 // 32 x 8 x kEstChunk tile and its one-cell halo of q are formed in shared
 // memory from the coarse output yc (stride S) with the arithmetic of the
 // stand-alone prolongation kernel: the (y, z)-interpolated coarse columns
-// once per (plane, row) of the halo box, then each cell's x-interpolation,
-// times its unknown flag.  Halo cells across a periodic face take the wrapped
-// cell's value; other cells outside the grid hold 0 (their faces are closed).
+// once per (plane, row) of the halo box, then each cell's x-interpolation.
+// The unknown mask is applied where the value is used: an owned cell takes q
+// only if it is an unknown, and a neighbour is read only across an open
+// face, which joins two fluid cells that both have an open face, i.e. two
+// unknowns, so the halo needs no flags.  Halo cells across a periodic face
+// take the wrapped cell's value; other cells outside the grid hold 0 (their
+// faces are closed).
 // The sums are those of k_warm_ls, in the same order, and the owned cells'
 // q goes to qout for the step kernels.
 //
@@ -1383,6 +1459,23 @@ __global__ void __launch_bounds__(256) k_warm_ls_c(Geo<T> g, const T* __restrict
     {
         float w;
         prolong_w(max(X0, 0), S, Xc, cmin, w);
+    }
+    // the owned cells' flags and residuals, issued first so that their latency
+    // overlaps the fill of the tile (r is read unconditionally: the padded
+    // array holds every cell of the chunk's columns)
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i = blockIdx.x * 32 + tx + 1, j = blockIdx.y * 8 + ty + 1;
+    const int kb = blockIdx.z * kEstChunk + 1, ke = min(kb + kEstChunk, d.nz + 1);
+    const bool own = i <= d.nx && j <= d.ny;
+    const int pl = (int)d.plane;
+    const long long cown = own ? d.at(i, j, kb) : 0;
+    uint8_t fl[kEstChunk];
+    T rr[kEstChunk];
+#pragma unroll
+    for (int m = 0; m < kEstChunk; ++m) {
+        const bool in = own && kb + m < ke;
+        fl[m] = in ? g.flags[cown + (long long)m * pl] : (uint8_t)0;
+        rr[m] = in ? r[cown + (long long)m * pl] : T(0);
     }
     if (tid < LT::HX) {
         const int f = X0 + tid, fw = halo_coord(f, d.nx, d.perx);
@@ -1428,7 +1521,7 @@ __global__ void __launch_bounds__(256) k_warm_ls_c(Geo<T> g, const T* __restrict
         const int hx = q % LT::HX, hy = (q / LT::HX) % LT::HY, hz = q / (LT::HX * LT::HY);
         const int fx = L.fx[hx], fy = L.fy[hy], fz = L.fz[hz];
         float v = 0.f;
-        if (fx >= 0 && fy >= 0 && fz >= 0 && (g.flags[d.at(fx + 1, fy + 1, fz + 1)] & F_UNK)) {
+        if (fx >= 0 && fy >= 0 && fz >= 0) {
             const int a = L.x0[hx], b = L.x1[hx];
             float v0, v1;
             if (a >= 0) {
@@ -1443,23 +1536,19 @@ __global__ void __launch_bounds__(256) k_warm_ls_c(Geo<T> g, const T* __restrict
         L.q[hz][hy][hx] = v;
     }
     __syncthreads();
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int i = blockIdx.x * 32 + tx + 1, j = blockIdx.y * 8 + ty + 1;
-    const int kb = blockIdx.z * kEstChunk + 1, ke = min(kb + kEstChunk, d.nz + 1);
     T s0 = T(0), s1 = T(0);
-    if (i <= d.nx && j <= d.ny) {
-        const int pl = (int)d.plane, sz = d.nx * d.ny;
-        const long long c0 = d.at(i, j, kb);
+    if (own) {
+        const int sz = d.nx * d.ny;
         const int v0 = ((kb - 1) * d.ny + (j - 1)) * d.nx + (i - 1);
 #pragma unroll
         for (int m = 0; m < kEstChunk; ++m) {
             if (kb + m >= ke) break;
             const float* qq = &L.q[m + 1][ty + 1][tx + 1];
-            qout[v0 + m * sz] = qq[0];
-            const uint8_t f = g.flags[c0 + (long long)m * pl];
+            const uint8_t f = fl[m];
+            qout[v0 + m * sz] = (f & F_UNK) ? qq[0] : 0.f;
             if (!(f & F_UNK)) continue;
             const int k = kb + m;
-            const T qc = (T)qq[0], rc = r[c0 + (long long)m * pl];
+            const T qc = (T)qq[0], rc = rr[m];
             const T qe = (T)qq[1], qw = (T)qq[-1];
             const T qn = (T)qq[LT::HX], qs = (T)qq[-LT::HX];
             const T qt = (T)qq[LT::HY * LT::HX], qb = (T)qq[-LT::HY * LT::HX];
@@ -1520,12 +1609,25 @@ __global__ void k_warm_apply_dl(Geo<T> g, T* dl, const float* q, const double* a
     if (i > d.nx || j > d.ny) return;
     const T a = (T)*alpha;
     const bool zero = sc->zcopy != 0;
-    long long c = d.at(i, j, kb);
-    int v = ((kb - 1) * d.ny + (j - 1)) * d.nx + (i - 1);
-    for (int k = kb; k < ke; ++k, c += d.plane, v += d.nx * d.ny) {
-        if (!(g.flags[c] & F_UNK)) continue;
-        const T base = zero ? T(0) : dl[c];
-        dl[c] = base + a * (T)q[v];
+    const long long c0 = d.at(i, j, kb);
+    const int v0 = ((kb - 1) * d.ny + (j - 1)) * d.nx + (i - 1), sz = d.nx * d.ny;
+    // every load of the chunk first (a plane past the chunk reads its first one)
+    uint8_t fl[kEstChunk];
+    T dv[kEstChunk];
+    float qv[kEstChunk];
+#pragma unroll
+    for (int m = 0; m < kEstChunk; ++m) {
+        const bool in = kb + m < ke;
+        const long long c = in ? c0 + (long long)m * d.plane : c0;
+        fl[m] = in ? g.flags[c] : (uint8_t)0;
+        dv[m] = dl[c];
+        qv[m] = q[in ? v0 + m * sz : v0];
+    }
+#pragma unroll
+    for (int m = 0; m < kEstChunk; ++m) {
+        if (!(fl[m] & F_UNK)) continue;
+        const T base = zero ? T(0) : dv[m];
+        dl[c0 + (long long)m * d.plane] = base + a * (T)qv[m];
     }
 }
 

@@ -627,10 +627,20 @@ __global__ void k_pool_padded_s(const float* r, const uint8_t* flags, Dom d, flo
             const int fz = cz * S + tz + zz;
             if (fz >= d.nz) break;
             const long long row = d.at(1, fy + 1, fz + 1) + (long long)cx * S;
+            // the row's flags and residuals are read first, unconditionally
+            // (past the grid's last cell the padded array holds the ghost
+            // column and the next row), then summed in order
+            uint8_t fl[S];
+            float rv[S];
+#pragma unroll
+            for (int dx = 0; dx < S; ++dx) {
+                fl[dx] = flags[row + dx];
+                rv[dx] = r[row + dx];
+            }
 #pragma unroll
             for (int dx = 0; dx < S; ++dx)
-                if (cx * S + dx < d.nx && (flags[row + dx] & F_UNK)) {
-                    ar += r[row + dx];
+                if (cx * S + dx < d.nx && (fl[dx] & F_UNK)) {
+                    ar += rv[dx];
                     am += 1.f;
                 }
         }
