@@ -388,11 +388,16 @@ int les_net_get_stride(les_net n, int32_t* stride);
  * LES_NET_TCGEN05 (default: tcgen05.mma, 128-voxel x 16/32-channel tiles,
  * FP32 accumulator in tensor memory) or LES_NET_MMA_SYNC (warp-level
  * m16n8k16).  Both stage the same BF16 operands and accumulate in FP32 (the
- * summation order inside an MMA differs).  A tcgen05 kernel whose bounded
- * wait gives up makes the next synchronous network call return
- * LES_ETIMEOUT. */
+ * summation order inside an MMA differs).  With LES_NET_TCGEN05 the CTAs
+ * that split a small layer's input channels form a thread-block cluster and
+ * add their partial sums over distributed shared memory (where the device
+ * can co-schedule such clusters); LES_NET_TCGEN05_GMEM_SPLIT adds them
+ * through global memory instead, with the same sums in the same order
+ * (bit-identical results).  A tcgen05 kernel whose bounded wait gives up
+ * makes the next synchronous network call return LES_ETIMEOUT. */
 #define LES_NET_MMA_SYNC 0
 #define LES_NET_TCGEN05 1
+#define LES_NET_TCGEN05_GMEM_SPLIT 2
 int les_net_set_engine(les_net n, int32_t engine);
 int les_net_get_engine(les_net n, int32_t* engine);
 int les_net_forward(les_net n, const float* d_r, const float* d_mask, float* d_y, int32_t nx, int32_t ny, int32_t nz);

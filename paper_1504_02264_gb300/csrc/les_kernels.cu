@@ -1168,8 +1168,10 @@ __device__ __forceinline__ void sor_est_body(const Geo<T>& g, const T* __restric
     }
 }
 
+// (at most 64 registers, four CTAs per SM: the half-chunk loads alone would
+// take 80 and three CTAs; the learned step measured 0.6% faster so)
 template <typename T>
-__global__ void __launch_bounds__(256) k_sor_est(Geo<T> g, const T* dl, const T* r, T* rout, Reduce red,
+__global__ void __launch_bounds__(256, 4) k_sor_est(Geo<T> g, const T* dl, const T* r, T* rout, Reduce red,
                                                  CondArgs ca) {
     pdl_wait();
     if (red.sc->done) return;      // uniform over the grid
@@ -1933,7 +1935,8 @@ __device__ __forceinline__ int ens_member(const int* beg, int n, int t) {
     return m;
 }
 
-__global__ void __launch_bounds__(256) k_sor_est_ens(const __grid_constant__ EnsTab<float> tab, int dcur, CondArgs ca) {
+__global__ void __launch_bounds__(256, 4) k_sor_est_ens(const __grid_constant__ EnsTab<float> tab, int dcur,
+                                                        CondArgs ca) {
     const int t = blockIdx.x, m = ens_member(tab.ebeg, tab.n, t);
     const EnsMember<float>& M = tab.m[m];
     if (M.red.sc->done) return;

@@ -519,7 +519,7 @@ int predict_impl(les_net_s* n, const Dom& d, const float* r_padded, const uint8_
     n->stream = s;
     int rc = ensure_ws(n, L0);
     // tcgen05 with the pooling + RMS kernel: packing and head folded into the convolutions
-    const bool folded = fold && n->engine == nn::kEngineTcgen05 && L0.v() <= nn::kPoolRmsMax;
+    const bool folded = fold && n->engine != nn::kEngineMmaSync && L0.v() <= nn::kPoolRmsMax;
     if (!rc) {
         if (L0.v() <= nn::kPoolRmsMax) {
             // pooling and RMS in one launch, the pooled mask straight into the
@@ -689,14 +689,19 @@ int tc_check(les_net_s* n) {
 }
 
 int les_net_set_engine(les_net n, int32_t engine) {
-    if (!n || (engine != LES_NET_MMA_SYNC && engine != LES_NET_TCGEN05)) return LES_EINVAL;
-    n->engine = engine == LES_NET_TCGEN05 ? nn::kEngineTcgen05 : nn::kEngineMmaSync;
+    if (!n || (engine != LES_NET_MMA_SYNC && engine != LES_NET_TCGEN05 && engine != LES_NET_TCGEN05_GMEM_SPLIT))
+        return LES_EINVAL;
+    n->engine = engine == LES_NET_TCGEN05 ? nn::kEngineTcgen05
+                : engine == LES_NET_TCGEN05_GMEM_SPLIT ? nn::kEngineTcgen05Gmem
+                                                       : nn::kEngineMmaSync;
     return LES_OK;
 }
 
 int les_net_get_engine(les_net n, int32_t* engine) {
     if (!n || !engine) return LES_EINVAL;
-    *engine = n->engine == nn::kEngineTcgen05 ? LES_NET_TCGEN05 : LES_NET_MMA_SYNC;
+    *engine = n->engine == nn::kEngineTcgen05       ? LES_NET_TCGEN05
+              : n->engine == nn::kEngineTcgen05Gmem ? LES_NET_TCGEN05_GMEM_SPLIT
+                                                    : LES_NET_MMA_SYNC;
     return LES_OK;
 }
 

@@ -43,6 +43,9 @@ struct ConvArgs {
     float* part;
     unsigned* cnt;
     int ks;
+    // tcgen05 kernel: the ks CTAs of a tile run as one thread-block cluster and
+    // add their partial sums over distributed shared memory (part, cnt unused)
+    int cluster;
     // IN_PACK sources (level-0 volumes and the RMS)
     const float* prc;
     const float* pmask;
@@ -58,13 +61,16 @@ struct ConvArgs {
 
 // Which tensor-core path the forward convolutions (inference, and the
 // backward pass's input gradient) run on: the warp-level mma.sync kernel or
-// the tcgen05 kernel (les_nn_tc.cu).  `timeout` (device int, nullable) records
+// the tcgen05 kernel (les_nn_tc.cu), whose input-channel split adds its
+// partial sums in a thread-block cluster or (kEngineTcgen05Gmem) through
+// global memory.  `timeout` (device int, nullable) records
 // a bounded wait of the tcgen05 kernel that gave up.  Process-wide; the
 // network entry points set it from the network's own choice before launching.
-constexpr int kEngineMmaSync = 0, kEngineTcgen05 = 1;
+constexpr int kEngineMmaSync = 0, kEngineTcgen05 = 1, kEngineTcgen05Gmem = 2;
 void set_conv_engine(int engine, int* timeout);
 int conv3_tc_prepare();
-void conv3_tc_launch(ConvArgs A, int in_mode, cudaStream_t s, const int* gate, const ConvSplit* split, int* timeout);
+void conv3_tc_launch(ConvArgs A, int in_mode, cudaStream_t s, const int* gate, const ConvSplit* split, int* timeout,
+                     bool cluster_split);
 // tcgen05 inference: the first convolution (16 input channels) reading the
 // packed input straight from the pooled residual rc, the pooled mask pm and
 // the RMS scale[0]; the last decoder convolution (Cout 16, nearest

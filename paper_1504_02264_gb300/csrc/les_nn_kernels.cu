@@ -303,9 +303,9 @@ template <int IN>
 static void conv3_launch(const __nv_bfloat16* x, const __nv_bfloat16* w, __nv_bfloat16* y, const __nv_bfloat16* skip,
                          __nv_bfloat16* ysum, int X, int Y, int Z, int Cin, int Cout, int relu, cudaStream_t s,
                          const int* gate, int Xs, int Ys, int Zs, const ConvSplit* split) {
-    if (g_conv_engine == kEngineTcgen05) {
+    if (g_conv_engine != kEngineMmaSync) {
         const ConvArgs A{x, w, y, skip, ysum, X, Y, Z, Cin, Cout, relu, Xs, Ys, Zs, nullptr, nullptr, 1};
-        conv3_tc_launch(A, IN, s, gate, split, g_conv_timeout);
+        conv3_tc_launch(A, IN, s, gate, split, g_conv_timeout, g_conv_engine == kEngineTcgen05);
         return;
     }
     // 32 output channels per CTA when the grid fills the GPU, else 16 (twice
@@ -353,7 +353,7 @@ void conv3_tc_fwd_packed(const float* rc, const float* pm, const double* scale, 
     A.prc = rc;
     A.pmask = pm;
     A.pscale = scale;
-    conv3_tc_launch(A, IN_PACK, s, gate, split, g_conv_timeout);
+    conv3_tc_launch(A, IN_PACK, s, gate, split, g_conv_timeout, g_conv_engine == kEngineTcgen05);
 }
 
 void conv3_tc_fwd_up_head(const __nv_bfloat16* xc, const __nv_bfloat16* w, const __nv_bfloat16* skip, int X, int Y,
@@ -364,7 +364,7 @@ void conv3_tc_fwd_up_head(const __nv_bfloat16* xc, const __nv_bfloat16* w, const
     A.head_w = head_w;
     A.head_mask = pm;
     A.head_y = y_head;
-    conv3_tc_launch(A, IN_UP, s, gate, split, g_conv_timeout);
+    conv3_tc_launch(A, IN_UP, s, gate, split, g_conv_timeout, g_conv_engine == kEngineTcgen05);
 }
 
 void conv3_fwd_pool(const __nv_bfloat16* xf, const __nv_bfloat16* w, __nv_bfloat16* y, int Xf, int Yf, int Zf,

@@ -109,6 +109,26 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
 }
+// thread-block cluster: barrier over every thread of every CTA (release /
+// acquire), the address of the same shared variable in CTA `rank`, a 16-byte
+// load from distributed shared memory
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_map(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ float4 cluster_ld4(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr)
+                 : "memory");
+    return v;
+}
+
 __device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -190,7 +210,9 @@ __device__ __forceinline__ void stage_half(const ConvArgs& A, int gx, int gy, in
 template <int CO, int IN>
 __global__ void __launch_bounds__(NTH) k_conv3_tc(ConvArgs A, const int* gate, int* timeout) {
     pdl_wait();
-    if (gate && *(volatile const int*)gate) return;      // the solve this inference serves has ended
+    // the solve this inference serves may have ended: the flag's load is
+    // issued here and tested after the first chunk's copies are under way
+    const int ended = gate ? *(volatile const int*)gate : 0;
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     TcSmem<CO>& S = *reinterpret_cast<TcSmem<CO>*>(tc_smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -237,6 +259,17 @@ __global__ void __launch_bounds__(NTH) k_conv3_tc(ConvArgs A, const int* gate, i
     bool ok = true;
     int issued = cb - 1;                           // the last chunk whose MMAs were issued
     stage(cb, S.st[0]);
+    if (ended) {
+        // uniform over the CTA: let the copies land, give the memory back
+        cp_wait<0>();
+        tc_before();
+        __syncthreads();
+        if (warp == 0) {
+            tc_after();
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TM_COLS) : "memory");
+        }
+        return;
+    }
     for (int c = cb; c < ce; ++c) {
         const int s = (c - cb) & 1;
         cp_wait<0>();
@@ -292,8 +325,41 @@ __global__ void __launch_bounds__(NTH) k_conv3_tc(ConvArgs A, const int* gate, i
         tc_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TM_COLS) : "memory");
     }
+    if (ks > 1 && A.cluster) {
+        // the split's CTAs form one thread-block cluster (rank = kq): each
+        // leaves its accumulators in its own idle stage buffer, and after a
+        // cluster barrier rank 0 adds them over distributed shared memory in
+        // the order kq = 0, 1, ... (the sums of the global-memory path) and
+        // runs the epilogue; a second barrier keeps every buffer alive until
+        // it has been read.  Every CTA of the cluster reaches both barriers
+        // (a CTA whose wait timed out contributes zeros and has flagged it).
+        float4* mine = reinterpret_cast<float4*>(&S.st[0]) + tid * (NC / 4);
+#pragma unroll
+        for (int n = 0; n < NC / 4; ++n)
+            mine[n] = ok ? make_float4(acc[4 * n], acc[4 * n + 1], acc[4 * n + 2], acc[4 * n + 3])
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+        cluster_sync();
+        if (kq == 0 && ok) {
+#pragma unroll
+            for (int n = 0; n < NC; ++n) acc[n] = 0.f;
+            const uint32_t own = saddr(mine);
+            for (int k = 0; k < ks; ++k) {
+                const uint32_t peer = cluster_map(own, (uint32_t)k);
+#pragma unroll
+                for (int n = 0; n < NC / 4; ++n) {
+                    const float4 v = cluster_ld4(peer + 16u * n);
+                    acc[4 * n] += v.x;
+                    acc[4 * n + 1] += v.y;
+                    acc[4 * n + 2] += v.z;
+                    acc[4 * n + 3] += v.w;
+                }
+            }
+        }
+        cluster_sync();
+        if (kq != 0) return;
+    }
     if (!ok) return;
-    if (ks > 1) {
+    if (ks > 1 && !A.cluster) {
         // this split's accumulators; the tile's last CTA adds them in order
         __shared__ bool last;
         const size_t tile = (size_t)blockIdx.x + gridDim.x * ((size_t)blockIdx.y + gridDim.y * (size_t)bz);
@@ -387,6 +453,35 @@ cudaError_t allow_tc() {
     return cudaFuncSetAttribute(k_conv3_tc<CO, IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem<CO>());
 }
 
+// 1 when the current device co-schedules clusters of up to kMaxCluster CTAs
+// of the largest convolution kernel (decided once per process, on the device
+// current at the first preparation), else 0
+constexpr int kMaxCluster = 8;
+int g_tc_cluster = -1;
+
+template <int CO, int IN>
+cudaError_t tc_launch(dim3 grid, int cz, cudaStream_t s, const ConvArgs& A, const int* gate, int* timeout) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(NTH);
+    cfg.dynamicSmemBytes = tc_smem<CO>();
+    cfg.stream = s;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    int na = 1;
+    if (cz > 1) {
+        at[1].id = cudaLaunchAttributeClusterDimension;
+        at[1].val.clusterDim.x = 1;
+        at[1].val.clusterDim.y = 1;
+        at[1].val.clusterDim.z = (unsigned)cz;
+        na = 2;
+    }
+    cfg.attrs = at;
+    cfg.numAttrs = na;
+    return cudaLaunchKernelEx(&cfg, k_conv3_tc<CO, IN>, A, gate, timeout);
+}
+
 }  // namespace
 
 int conv3_tc_prepare() {
@@ -398,10 +493,28 @@ int conv3_tc_prepare() {
     if ((x = allow_tc<32, IN_POOL>()) != cudaSuccess) e = x;
     if ((x = allow_tc<16, IN_POOL>()) != cudaSuccess) e = x;
     if ((x = allow_tc<16, IN_PACK>()) != cudaSuccess) e = x;
+    if (e == cudaSuccess && g_tc_cluster < 0) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(1, 1, kMaxCluster);
+        cfg.blockDim = dim3(NTH);
+        cfg.dynamicSmemBytes = tc_smem<32>();
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 1;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = kMaxCluster;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        const cudaError_t q = cudaOccupancyMaxActiveClusters(&n, k_conv3_tc<32, IN_UP>, &cfg);
+        if (q != cudaSuccess) cudaGetLastError();
+        g_tc_cluster = (q == cudaSuccess && n > 0) ? 1 : 0;
+    }
     return e == cudaSuccess ? 0 : -1;
 }
 
-void conv3_tc_launch(ConvArgs A, int in_mode, cudaStream_t s, const int* gate, const ConvSplit* split, int* timeout) {
+void conv3_tc_launch(ConvArgs A, int in_mode, cudaStream_t s, const int* gate, const ConvSplit* split, int* timeout,
+                     bool cluster_split) {
     // 32 output channels per CTA when the grid fills the GPU, else 16; small
     // grids split their input-channel chunks over up to about two CTAs per SM
     const long long tiles = (long long)((A.X + TCX - 1) / TCX) * ((A.Y + TCY - 1) / TCY) * A.Z;
@@ -417,11 +530,12 @@ void conv3_tc_launch(ConvArgs A, int in_mode, cudaStream_t s, const int* gate, c
             ks *= 2;
         grid.z *= ks;
     }
-    A.part = ks > 1 ? split->part : nullptr;
-    A.cnt = ks > 1 ? split->cnt : nullptr;
+    A.cluster = ks > 1 && ks <= kMaxCluster && cluster_split && g_tc_cluster == 1;
+    A.part = ks > 1 && !A.cluster ? split->part : nullptr;
+    A.cnt = ks > 1 && !A.cluster ? split->cnt : nullptr;
     A.ks = ks;
-    const size_t smem = co == 32 ? tc_smem<32>() : tc_smem<16>();
-#define LES_TC_LAUNCH(CO_, IN_) launch_pdl(k_conv3_tc<CO_, IN_>, grid, dim3(NTH), smem, s, A, gate, timeout)
+    const int cz = A.cluster ? ks : 1;
+#define LES_TC_LAUNCH(CO_, IN_) tc_launch<CO_, IN_>(grid, cz, s, A, gate, timeout)
     if (in_mode == IN_PACK) {
         LES_TC_LAUNCH(16, IN_PACK);
     } else if (co == 32) {

@@ -66,15 +66,20 @@ def run_ensemble(a):
 
 def run_engines(a):
     """The learned step (network every --net-every sweeps) and one network
-    forward on the workload's residual, per convolution engine (tcgen05 and
-    the warp-level mma.sync kernel): host wall time per step, CUDA events
-    around the forward."""
+    forward on the workload's residual, per convolution engine (tcgen05 with
+    the split partials added in a cluster or through global memory, and the
+    warp-level mma.sync kernel; the two tcgen05 rows run twice, interleaved):
+    host wall time per step, CUDA events around the forward."""
     import torch
     sc = make(a.workload, a.seed)
     z = np.load(a.net)
     out = {"workload": a.workload, "cells": sc.ncells, "rows": []}
-    for name, eng in (("tcgen05", les.LES_NET_TCGEN05), ("mma.sync", les.LES_NET_MMA_SYNC)):
+    engines = (("tcgen05", les.LES_NET_TCGEN05), ("tcgen05 gmem split", les.LES_NET_TCGEN05_GMEM_SPLIT),
+               ("mma.sync", les.LES_NET_MMA_SYNC))
+    for name, eng in engines + engines[:2]:
         d = les.Domain(sc)
+        if a.tile is not None:
+            d.set_sor_config(a.tile, a.kc)
         net = les.Net(seed=0, stride=int(z["stride"]))
         net.set_params(z["params"])
         net.engine = eng

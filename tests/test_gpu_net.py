@@ -74,6 +74,8 @@ def test_engine_setting(net):
     assert net.engine == les.LES_NET_TCGEN05            # the default
     net.engine = les.LES_NET_MMA_SYNC
     assert net.engine == les.LES_NET_MMA_SYNC
+    net.engine = les.LES_NET_TCGEN05_GMEM_SPLIT
+    assert net.engine == les.LES_NET_TCGEN05_GMEM_SPLIT
     with pytest.raises(les.LesError):
         net.engine = 7
 
@@ -369,6 +371,32 @@ def test_folded_kernels_match_standalone(net, stride, engine, periodic):
     finally:
         for d in doms:
             d.close()
+
+
+@pytest.mark.parametrize("stride", [8, 4])
+def test_cluster_split_matches_global_split(net, stride):
+    """The small layers split their input channels over CTAs; the tcgen05
+    engine adds the partial sums over distributed shared memory in a
+    thread-block cluster, LES_NET_TCGEN05_GMEM_SPLIT through global memory,
+    both in the order of the split.  At stride 8 on this city the coarse grid
+    is 6x4x2 and the splits reach 8 CTAs.  Identical sweep counts and
+    bit-identical fields after learned-mode steps."""
+    net.stride = stride
+    sc = city(tol=1e-6, max_sweeps=40000, check_every=10)
+    out = []
+    for engine in (les.LES_NET_TCGEN05, les.LES_NET_TCGEN05_GMEM_SPLIT):
+        net.engine = engine
+        d = les.Domain(sc)
+        try:
+            d.set_warmstart(net)
+            d.set_net_schedule(10)
+            sw = [d.step()["sweeps"] for _ in range(2)]
+            out.append((sw, d.fields()))
+        finally:
+            d.close()
+    assert out[0][0] == out[1][0], (out[0][0], out[1][0])
+    for a, b in zip(out[0][1], out[1][1]):
+        assert np.array_equal(a, b)
 
 
 def test_warm_start_rejects_bad_use(net):
