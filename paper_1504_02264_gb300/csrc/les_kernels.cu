@@ -1168,11 +1168,11 @@ __device__ __forceinline__ void sor_est_body(const Geo<T>& g, const T* __restric
     }
 }
 
-// (at most 64 registers, four CTAs per SM: the half-chunk loads alone would
+// (FP32: at most 64 registers, four CTAs per SM: the half-chunk loads alone would
 // take 80 and three CTAs; the learned step measured 0.6% faster so)
 template <typename T>
-__global__ void __launch_bounds__(256, 4) k_sor_est(Geo<T> g, const T* dl, const T* r, T* rout, Reduce red,
-                                                 CondArgs ca) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
+    k_sor_est(Geo<T> g, const T* dl, const T* r, T* rout, Reduce red, CondArgs ca) {
     pdl_wait();
     if (red.sc->done) return;      // uniform over the grid
     sor_est_body<T>(g, dl, r, rout, red, ca, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x * gridDim.y * gridDim.z,
