@@ -43,10 +43,12 @@ WEIGHTS = os.path.join(ROOT, "paper_1504_02264_gb300", "weights", "warmstart.npz
 NET_EVERY = 10                  # sweeps between learned corrections (trained schedule)
 UNIT = "Mcell-steps/s"
 SOR_BYTES_PER_CELL = 13.0       # per sweep: read p, rhs (4+4), flags (1), write p (4)
-# DRAM bytes (read + write) per launch of the TMA sweep kernel (tile 17) on this
-# workload from one ncu capture (cold L2); reported only while that kernel is the
-# one timed
-SOR_TMA_TILE, SOR_TMA_DRAM_BYTES = 17, 20.180736e6 + 3.072e3
+# DRAM bytes (read + write) per launch of the TMA sweep kernels on this
+# workload, by tile, from one ncu capture each (cold L2); reported only for the
+# tile the autotuner picked
+SOR_DRAM_BYTES = {17: 20.180736e6 + 3.072e3}
+# the sweep timed alone on the HBM-bound grid: the column-walk TMA block
+SOR_HBM_TILE = 29
 L2_FLUSH_BYTES = 256 << 20
 # algorithmic bytes per cell of the HBM-bound phases (every array read or
 # written once): the stencil phase = les (u, v, w, flags in; nu_t out: 17 B)
@@ -74,6 +76,10 @@ def small_workload(seed=0):
 
 def sor_kernel_name(tile):
     """The sweep kernel a tile index of les_set_sor_config runs."""
+    if tile >= 29:
+        return "k_sor_col"
+    if tile >= 25:
+        return "k_sor_march"
     if tile >= 21:
         return "k_sor_pipe"
     if tile >= 17:
@@ -254,7 +260,7 @@ def hbm_large(les, net, peak, peak_kind, steps):
     """The HBM-bound kernels where the state does not fit in L2, and the
     converged step rate.  (1) 20 fixed sweeps per step, host loop with CUDA
     events around each phase (stencil phase: bondv1, les, velfg/SGS/AB2/
-    feedbf, outflow, rhs; projection), and the SOR sweep of the TMA block
+    feedbf, outflow, rhs; projection), and the SOR sweep of the column-walk TMA block
     tile timed alone (20 back-to-back sweeps, best of 3).  (2) Steps to
     relative residual 1e-6, learned and plain, from the same state."""
     import torch
@@ -268,7 +274,7 @@ def hbm_large(les, net, peak, peak_kind, steps):
         d.step(2)
         tm = d.timing()
         d.set_timing(False)
-        sweep_ms = min(d.time_sor(SOR_TMA_TILE, 0, sweeps=20) for _ in range(3))
+        sweep_ms = min(d.time_sor(SOR_HBM_TILE, 0, sweeps=20) for _ in range(3))
     finally:
         d.close()
     n = sc.ncells
@@ -280,7 +286,7 @@ def hbm_large(les, net, peak, peak_kind, steps):
 
     out = {"workload": "large_512x512x128_periodic_y", "cells": n, "peak_gbs": peak, "peak_kind": peak_kind,
            "l2": "state (~3.5 GB) far larger than L2",
-           "sor_sweep": {"kernel": f"{sor_kernel_name(SOR_TMA_TILE)} tile {les.les_sor_tile(SOR_TMA_TILE)}",
+           "sor_sweep": {"kernel": f"{sor_kernel_name(SOR_HBM_TILE)} tile {les.les_sor_tile(SOR_HBM_TILE)}",
                          **entry(SOR_BYTES_PER_CELL, sweep_ms)},
            "stencil_phase": entry(STENCIL_BYTES_PER_CELL, tm["ms_momentum"] / nsteps),
            "projection": {**entry(PROJECT_BYTES_PER_CELL, tm["ms_project"] / nsteps),
@@ -717,7 +723,7 @@ def run_ours(args):
                          "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind,
-                         "traffic": SOR_TMA_DRAM_BYTES if tile == SOR_TMA_TILE else None,
+                         "traffic": SOR_DRAM_BYTES.get(tile),
                          "bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms,
                          "note": ("150x150x90 SOR state (p, rhs, flags ~18 MB) is L2-resident; timed on the "
                                   "plain step's sweep batches (host loop, events around each batch)")},

@@ -250,13 +250,14 @@ int les_set_graph(les_handle h, int32_t enable);
  * else LES_EINVAL); tiles 25-28 are 30 x ty columns that march through kc
  * planes per CTA with a pipeline of per-plane TMA copies (FP32 grids, any
  * boundary conditions; kc <= 0 picks the chunk that gives at least two CTAs
- * per SM).
+ * per SM); tiles 29-34 are 28 x ty x tz TMA blocks whose lanes walk columns of
+ * one colour up the block (FP32 grids, any boundary conditions).
  * Every choice computes the same iterate.
  * les_autotune_sor times each tile shape with a few k-chunk lengths on this
  * handle's grid (sweeps per candidate), keeps the fastest and reports it;
  * the field state is saved and restored around the trial sweeps.
  */
-#define LES_SOR_NTILES 29
+#define LES_SOR_NTILES 35
 int les_set_sor_config(les_handle h, int32_t tile, int32_t kc);
 int les_get_sor_config(les_handle h, int32_t* tile, int32_t* kc);
 int les_sor_tile(int32_t tile, int32_t* tx, int32_t* ty, int32_t* tz);

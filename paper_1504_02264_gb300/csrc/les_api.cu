@@ -122,6 +122,7 @@ struct les_s {
     bool tma_ok = false;
     bool pipe_ok = false;                 // persistent TMA tiles (no periodic axis)
     float* cn1tab = nullptr;              // cn1 over (plane, open-face mask) for the pipelined sweep
+    float* coltab = nullptr;              // per-plane coefficient rows of the column-walk sweeps
     double* diag64 = nullptr;             // FP64 diagonal over (plane, open-face mask), the residual's
     // les_sor_compare scratch (allocated on first use): p0, rhs, p0 + d (FP64,
     // padded), the four norms, and the twinned pair array of the correction
@@ -269,6 +270,7 @@ Geo<T> geo(les_s* h) {
     g.cB64 = h->cB64;
     g.flags = h->flags;
     g.cn1 = std::is_same<T, float>::value ? (const T*)h->cn1tab : nullptr;
+    g.ctab = std::is_same<T, float>::value ? (const T*)h->coltab : nullptr;
     g.diag64 = h->diag64;
     return g;
 }
@@ -608,7 +610,7 @@ int autotune_impl(les_s* h, int sweeps, double* best_ms, int only_tile, int only
         for (int kc : kcs) {
             if (!tile_available(h, t)) continue;
             if (kc > h->g.nz) continue;
-            const bool march = t >= kNumSorTiles + kFirstMarchCfg;       // k-marching TMA columns take kc
+            const bool march = t >= kNumSorTiles + kFirstMarchCfg && t < kNumSorTiles + kFirstColCfg;   // take kc
             if (((t >= kNumSorTiles && !march) || (t < kNumSorTiles && kSorTiles[t].tz > 0)) && kc != 0)
                 continue;      // 3-D blocks ignore kc
             if (only_tile >= -1 && (t != only_tile || kc != only_kc)) continue;
@@ -1093,6 +1095,9 @@ int create_impl(les_s* h, const uint8_t* solid) {
         if ((rc = dalloc(h, (void**)&h->cn1tab, (size_t)(G.nz + 2) * 64 * sizeof(float)))) return rc;
         launch_cn1_table(geo<float>(h), h->cn1tab, h->stream);
         CK(cudaGetLastError());
+        if ((rc = dalloc(h, (void**)&h->coltab, (size_t)(G.nz + 2 + kColTableRows) * 68 * sizeof(float)))) return rc;
+        launch_col_table(geo<float>(h), h->cn1tab, h->coltab, h->stream);
+        CK(cudaGetLastError());
         if (tma_supported(d)) {
             CK(tma_prepare());
             h->tma_ok = tma_encode(d, (float*)h->dl[0], (float*)h->dl[1], (float*)h->rr, h->flags, h->tma);
@@ -1547,7 +1552,7 @@ int les_get_sor_config(les_handle h, int32_t* tile, int32_t* kc) {
 int les_sor_tile(int32_t tile, int32_t* tx, int32_t* ty, int32_t* tz) {
     if (tile >= kNumSorTiles && tile < kNumSorTiles + kNumTmaTiles) {
         const int c = tile - kNumSorTiles;
-        const bool march = c >= kFirstMarchCfg;           // k-marching column: tz = 0
+        const bool march = c >= kFirstMarchCfg && c < kFirstColCfg;   // k-marching column: tz = 0
         if (tx) *tx = march ? 30 : 28;
         if (ty) *ty = kTmaCfg[c][0];
         if (tz) *tz = march ? 0 : kTmaCfg[c][1];

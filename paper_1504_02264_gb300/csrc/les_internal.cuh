@@ -165,6 +165,8 @@ struct Geo {
     const double* cB64;     // [nz+2]
     const uint8_t* flags;   // padded cell flags
     const T* cn1;           // [nz+2][64] cn1 over (plane, open-face mask); FP32 grids only (else null)
+    const T* ctab;          // [nz+2+16][68] per-plane rows of the column-walk sweeps: cn1[64], cT, cB, 0, 0
+                            // (wrapped on a periodic z axis, else clamped); FP32 grids only (else null)
     const double* diag64;   // [nz+2][64] FP64 diagonal of the Poisson operator over (plane, open-face mask)
 };
 
@@ -274,12 +276,15 @@ template <typename T> cudaError_t sor_prepare();
 // TMA variants (les_sor_tma.cu), FP32; tile indices kFirstTmaTile ..
 // kFirstTmaTile + kNumTmaTiles - 1: the first kNumTmaBlockTiles are one CTA
 // per block (any boundary conditions), the next four persistent
-// double-buffered (no periodic axis), the last four k-marching columns with
-// a plane pipeline (any boundary conditions; kc = planes per chunk)
+// double-buffered (no periodic axis), the next four k-marching columns with
+// a plane pipeline (any boundary conditions; kc = planes per chunk), the
+// last six one CTA per block with the column-walk update (any boundary
+// conditions)
 constexpr int kFirstTmaTile = 17;
-constexpr int kNumTmaTiles = 12;
+constexpr int kNumTmaTiles = 18;
 constexpr int kNumTmaBlockTiles = 4;
 constexpr int kFirstMarchCfg = 8;
+constexpr int kFirstColCfg = 12;
 extern const int kTmaCfg[kNumTmaTiles][3];
 struct TmaMaps {
     CUtensorMap d[2], r, f;
@@ -293,6 +298,9 @@ bool tma_encode(const Dom& d, float* dl0, float* dl1, float* rr, uint8_t* flags,
 int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, const float* cn1tab, int cfg, int kc, int in,
                    float* dout, int zero, Scalars* sc, cudaStream_t s);
 int launch_cn1_table(const Geo<float>& g, float* tab, cudaStream_t s);
+// the column-walk sweeps' coefficient rows from the cn1 table ((nz + 2 + 16) rows of 68 floats)
+int launch_col_table(const Geo<float>& g, const float* cn1tab, float* tab, cudaStream_t s);
+constexpr int kColTableRows = 16;    // rows past plane nz + 1
 // batched TMA sweep of an ensemble (les_sor_tma.cu): the 28 x 8 x 8 blocks of
 // every member in one persistent launch; maps = 4 tensor maps per member
 // (d[0], d[1], r, flags) in global memory, encoded by tma_encode_member

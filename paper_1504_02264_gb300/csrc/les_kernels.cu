@@ -2023,7 +2023,7 @@ __global__ void __launch_bounds__(256) k_ens_persist(const __grid_constant__ Ens
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     const int n = tab.n;
     if (tid == 0) {
-        tma::mbar_init(tma::smem_u32(psm + TT::OFF_BAR), 1);
+        tma::mbar_init(tma::smem_u32(psm + tma::ColTile<kEnsTmaBy, kEnsTmaBz>::STAGE), 1);
         tma::mbar_fence_init();
     }
     // the maps were written through the generic proxy (a host copy): acquire
@@ -2046,7 +2046,7 @@ __global__ void __launch_bounds__(256) k_ens_persist(const __grid_constant__ Ens
                 const int q = t - tab.tbeg[m];
                 const bool zero_start = s == 0 && sc->zflag;
                 const CUtensorMap* mm = maps + 4 * m;
-                if (!tma::sor_tma_block<kEnsTmaBy, kEnsTmaBz, 256>(psm, mm + in, mm + 2, mm + 3, M.g, M.dl[in], M.rr,
+                if (!tma::sor_col_block<kEnsTmaBy, kEnsTmaBz, 256>(psm, mm + in, mm + 2, mm + 3, M.g, M.dl[in], M.rr,
                                                                     M.dl[1 - in], zero_start, sc, q % gx,
                                                                     (q / gx) % gy, q / (gx * gy), phase)) {
                     if (tid == 0) atomicExch(err, 1);
@@ -2110,7 +2110,7 @@ __global__ void __launch_bounds__(256) k_ens_persist(const __grid_constant__ Ens
 int ens_persist_grid() {
     static int grid = -1;
     if (grid < 0) {
-        using TT = tma::TmaTile<kEnsTmaBy, kEnsTmaBz>;
+        using TT = tma::ColTile<kEnsTmaBy, kEnsTmaBz>;
         int dev = 0, sms = 0, per = 0, coop = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -2129,7 +2129,7 @@ int launch_ens_persist(const EnsTab<float>& tab, const CUtensorMap* maps, int cy
                        unsigned* bar, int* err, cudaStream_t s) {
     const int grid = ens_persist_grid();
     if (grid <= 0) return -1;
-    using TT = tma::TmaTile<kEnsTmaBy, kEnsTmaBz>;
+    using TT = tma::ColTile<kEnsTmaBy, kEnsTmaBz>;
     EnsTab<float> T = tab;
     void* args[] = {(void*)&T, (void*)&maps, (void*)&cycle, (void*)&batches, (void*)&ca, (void*)&bar, (void*)&err};
     if (cudaLaunchCooperativeKernel((const void*)k_ens_persist, dim3(grid), dim3(32, 8), args, TT::SMEM, s) !=

@@ -48,12 +48,33 @@ k_sor_tma(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtens
                               0u);
 }
 
+// The same block sweep with the column-walk update (sor_col_block): fewer
+// instructions per cell for the same iterate.
+template <int BY, int BZ, int NT>
+__global__ void __launch_bounds__(NT)
+k_sor_col(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtensorMap tr,
+          const __grid_constant__ CUtensorMap tf, Geo<float> g, const float* __restrict__ din,
+          const float* __restrict__ rin, float* __restrict__ dout, int zero_arg, Scalars* __restrict__ sc) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    pdl_wait();
+    if (sc->done) return;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(sm + ColTile<BY, BZ>::STAGE), 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const bool zero_start = zero_arg == 1 || (zero_arg == 2 && sc->zflag);
+    sor_col_block<BY, BZ, NT>(sm, &td, &tr, &tf, g, din, rin, dout, zero_start, sc, blockIdx.x, blockIdx.y, blockIdx.z,
+                              0u);
+}
+
 // The batched sweep of an ensemble: persistent CTAs walk the flattened list
 // of every member's 28 x BY x BZ blocks (member m owns items tbeg[m] ..
 // tbeg[m+1]-1) and sweep each block of the members whose solve is still
 // running, with the member's own tensor maps (four per member in global
-// memory: d[0], d[1], r, flags) and arguments -- the single-domain block
-// kernel's arithmetic, so a member evolves as it would alone with tile 17.
+// memory: d[0], d[1], r, flags) and arguments -- the column-walk block sweep
+// of the single-domain kernel, so a member evolves as it would alone with
+// tile 29.
 // One launch per sweep covers every member.
 template <int BY, int BZ, int NT>
 __global__ void __launch_bounds__(NT)
@@ -63,7 +84,7 @@ k_sor_tma_ens(const __grid_constant__ EnsTab<float> tab, const CUtensorMap* __re
     pdl_wait();
     const int n = tab.n, total = tab.tbeg[n];
     if (threadIdx.x == 0) {
-        mbar_init(smem_u32(sm + TT::OFF_BAR), 1);
+        mbar_init(smem_u32(sm + ColTile<BY, BZ>::STAGE), 1);
         mbar_fence_init();
     }
     // the maps were written through the generic proxy (a host copy): acquire
@@ -84,7 +105,7 @@ k_sor_tma_ens(const __grid_constant__ EnsTab<float> tab, const CUtensorMap* __re
         const int bx = q % gx, by = (q / gx) % gy, bz = q / (gx * gy);
         const bool zero_start = zero_arg == 1 || (zero_arg == 2 && sc->zflag);
         const CUtensorMap* mm = maps + 4 * m;
-        if (!sor_tma_block<BY, BZ, NT>(sm, mm + in, mm + 2, mm + 3, M.g, M.dl[in], M.rr, M.dl[1 - in], zero_start, sc,
+        if (!sor_col_block<BY, BZ, NT>(sm, mm + in, mm + 2, mm + 3, M.g, M.dl[in], M.rr, M.dl[1 - in], zero_start, sc,
                                        bx, by, bz, phase))
             return;
         phase ^= 1u;
@@ -538,6 +559,21 @@ void launch_tma_cfg(const Geo<float>& g, const TmaMaps& m, int in, float* dout, 
                m.rptr, dout, zero, sc);
 }
 
+template <int BY, int BZ, int NT>
+cudaError_t allow_col() {
+    return cudaFuncSetAttribute(k_sor_col<BY, BZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ColTile<BY, BZ>::SMEM);
+}
+
+template <int BY, int BZ, int NT>
+void launch_col_cfg(const Geo<float>& g, const TmaMaps& m, int in, float* dout, int zero, Scalars* sc,
+                    cudaStream_t s) {
+    const Dom& d = g.d;
+    dim3 grid((d.nx + 27) / 28, (d.ny + BY - 1) / BY, (d.nz + BZ - 1) / BZ);
+    launch_pdl(k_sor_col<BY, BZ, NT>, grid, dim3(NT), ColTile<BY, BZ>::SMEM, s, m.d[in], m.r, m.f, g, m.dptr[in],
+               m.rptr, dout, zero, sc);
+}
+
 template <int TY, int NS>
 cudaError_t allow_march() {
     return cudaFuncSetAttribute(k_sor_march<TY, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -603,7 +639,9 @@ bool encode3d(CUtensorMap* map, CUtensorMapDataType type, size_t es, void* base,
 // k-marching tiles (kFirstMarchCfg ..) as (TY, plane slots, threads)
 const int kTmaCfg[kNumTmaTiles][3] = {{8, 8, 256}, {12, 12, 512}, {16, 12, 512}, {16, 16, 512},
                                       {8, 8, 256}, {8, 8, 512}, {16, 8, 512}, {12, 12, 512},
-                                      {16, 16, 288}, {16, 8, 288}, {8, 16, 160}, {8, 8, 160}};
+                                      {16, 16, 288}, {16, 8, 288}, {8, 16, 160}, {8, 8, 160},
+                                      {8, 8, 256},   {8, 8, 320},   {8, 16, 320}, {16, 8, 512},
+                                      {8, 8, 128},   {8, 8, 192}};
 
 bool tma_supported(const Dom&) { return true; }
 
@@ -627,22 +665,28 @@ cudaError_t tma_prepare() {
     if ((x = allow_march<16, 8>()) != cudaSuccess) e = x;
     if ((x = allow_march<8, 16>()) != cudaSuccess) e = x;
     if ((x = allow_march<8, 8>()) != cudaSuccess) e = x;
+    if ((x = allow_col<8, 8, 256>()) != cudaSuccess) e = x;
+    if ((x = allow_col<8, 8, 320>()) != cudaSuccess) e = x;
+    if ((x = allow_col<8, 16, 320>()) != cudaSuccess) e = x;
+    if ((x = allow_col<16, 8, 512>()) != cudaSuccess) e = x;
+    if ((x = allow_col<8, 8, 128>()) != cudaSuccess) e = x;
+    if ((x = allow_col<8, 8, 192>()) != cudaSuccess) e = x;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
     if ((x = cudaFuncSetAttribute(k_sor_tma_ens<kEnsTmaBy, kEnsTmaBz, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)TmaTile<kEnsTmaBy, kEnsTmaBz>::SMEM)) != cudaSuccess)
+                                  (int)ColTile<kEnsTmaBy, kEnsTmaBz>::SMEM)) != cudaSuccess)
         e = x;
     int per = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sor_tma_ens<kEnsTmaBy, kEnsTmaBz, 256>, 256,
-                                                  TmaTile<kEnsTmaBy, kEnsTmaBz>::SMEM);
+                                                  ColTile<kEnsTmaBy, kEnsTmaBz>::SMEM);
     g_ens_tma_resident = g_sms * (per > 0 ? per : 1);
     return e;
 }
 
 bool tma_encode(const Dom& d, float* dl0, float* dl1, float* rr, uint8_t* flags, TmaMaps* maps) {
     for (int c = 0; c < kNumTmaTiles; ++c) {
-        const bool march = c >= kFirstMarchCfg;
+        const bool march = c >= kFirstMarchCfg && c < kFirstColCfg;
         const int by = kTmaCfg[c][0], bz = march ? -1 : kTmaCfg[c][1];    // march: one plane per copy
         TmaMaps& m = maps[c];
         m.dptr[0] = dl0;
@@ -673,6 +717,12 @@ int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, const float* cn1tab
         case 5: launch_pipe_cfg<8, 8, 512>(g, m, cn1tab, in, dout, zero, sc, s, 1); break;
         case 6: launch_pipe_cfg<16, 8, 512>(g, m, cn1tab, in, dout, zero, sc, s, 2); break;
         case 7: launch_pipe_cfg<12, 12, 512>(g, m, cn1tab, in, dout, zero, sc, s, 3); break;
+        case 12: launch_col_cfg<8, 8, 256>(g, m, in, dout, zero, sc, s); break;
+        case 13: launch_col_cfg<8, 8, 320>(g, m, in, dout, zero, sc, s); break;
+        case 14: launch_col_cfg<8, 16, 320>(g, m, in, dout, zero, sc, s); break;
+        case 15: launch_col_cfg<16, 8, 512>(g, m, in, dout, zero, sc, s); break;
+        case 16: launch_col_cfg<8, 8, 128>(g, m, in, dout, zero, sc, s); break;
+        case 17: launch_col_cfg<8, 8, 192>(g, m, in, dout, zero, sc, s); break;
         default: break;
     }
     return 1;
@@ -693,7 +743,7 @@ int launch_sor_tma_ens(const EnsTab<float>& tab, const CUtensorMap* maps, int in
     const int total = tab.tbeg[tab.n];
     const int grid = ctas < total ? ctas : total;
     if (grid < 1) return 0;
-    launch_pdl(k_sor_tma_ens<kEnsTmaBy, kEnsTmaBz, 256>, dim3(grid), dim3(256), TmaTile<kEnsTmaBy, kEnsTmaBz>::SMEM,
+    launch_pdl(k_sor_tma_ens<kEnsTmaBy, kEnsTmaBz, 256>, dim3(grid), dim3(256), ColTile<kEnsTmaBy, kEnsTmaBz>::SMEM,
                s, tab, maps, in, zero);
     return 1;
 }
@@ -711,6 +761,22 @@ __global__ void k_cn1_table(Geo<float> g, float* tab) {
     float ab = (m & F_B) ? g.cB[k] : 0.f;
     const float sum = ae + aw + an + as + at + ab;
     tab[q] = sum > 0.f ? 1.f / sum : 0.f;
+}
+
+// rows of the column-walk sweeps' coefficient table (les_tma.cuh, kColRow)
+__global__ void k_col_table(Geo<float> g, const float* cn1tab, float* tab) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int rows = g.d.nz + 2 + kColTableRows;
+    if (q >= rows * kColRow) return;
+    const int r = q / kColRow, e = q % kColRow;
+    const int k = coef_plane(g.d, r);
+    tab[q] = e < 64 ? cn1tab[k * 64 + e] : (e == 64 ? g.cT[k] : (e == 65 ? g.cB[k] : 0.f));
+}
+
+int launch_col_table(const Geo<float>& g, const float* cn1tab, float* tab, cudaStream_t s) {
+    const int n = (g.d.nz + 2 + kColTableRows) * kColRow;
+    k_col_table<<<(n + 255) / 256, 256, 0, s>>>(g, cn1tab, tab);
+    return 1;
 }
 
 int launch_cn1_table(const Geo<float>& g, float* tab, cudaStream_t s) {

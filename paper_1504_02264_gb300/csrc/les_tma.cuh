@@ -7,6 +7,8 @@
 
 #include "les_internal.cuh"
 
+#include <type_traits>
+
 namespace les {
 namespace tma {
 
@@ -246,6 +248,312 @@ __device__ __forceinline__ bool sor_tma_block(unsigned char* sm, const CUtensorM
     return true;
 }
 
+
+// Shared-memory accesses at a 32-bit shared address plus a compile-time byte
+// offset (one instruction each, the offset in the instruction's immediate).
+template <int OFF>
+__device__ __forceinline__ float lds_f32(uint32_t a) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(a), "n"(OFF) : "memory");
+    return v;
+}
+template <int OFF>
+__device__ __forceinline__ uint32_t lds_u8(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u8 %0, [%1+%2];" : "=r"(v) : "r"(a), "n"(OFF) : "memory");
+    return v;
+}
+template <int OFF>
+__device__ __forceinline__ float2 lds_f32x2(uint32_t a) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2+%3];" : "=f"(v.x), "=f"(v.y) : "r"(a), "n"(OFF) : "memory");
+    return v;
+}
+// store v at a + OFF when pred != 0
+template <int OFF>
+__device__ __forceinline__ void sts_f32_if(uint32_t a, float v, uint32_t pred) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %2, 0;\n @p st.shared.f32 [%0+%3], %1;\n}\n" ::"r"(a), "f"(v),
+                 "r"(pred), "n"(OFF)
+                 : "memory");
+}
+
+// Untiled bulk copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned) from global memory into shared memory, completing on mbarrier bar.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+// Rows of the per-plane coefficient table of the column-walk sweeps: for
+// padded plane k, cn1 over the 64 open-face masks, then cT, cB and two pad
+// floats (272 bytes).  The table has kColTableRows rows past plane nz + 1, so a
+// block near the top copies whole rows; ring planes across a periodic z face
+// hold the wrapped plane's values, other planes outside 0 .. nz + 1 the
+// nearest one's.
+constexpr int kColRow = 68;
+
+// One lane's walk up a column of one colour (NP updates, planes kk0, kk0+2,
+// ...) in the column-walk block sweep.  Shared addresses: ad = d cell one
+// plane below the first update, ar / af = its r / flag cell, acn = the
+// coefficient row of plane kk0.  PZ, PR, PF: plane strides of the d, r and
+// flag tiles (elements); DXW: row stride of d and r.  The next update's
+// loads are issued before this update's store; none of them reads a cell
+// the walk writes (the neighbours have the other colour).
+struct ColVals {
+    uint32_t fl;
+    float rhs, up, ve, vw, vn, vs, own, cn1;
+};
+template <int NP, int PZ, int PR, int PF, int DXW>
+struct ColWalk {
+    static constexpr int RB = kColRow * 4;        // bytes per coefficient row
+    uint32_t ad, ar, af, acn;
+    float cx, cy, omega;
+    template <int T>
+    __device__ __forceinline__ void load(ColVals& v) const {
+        constexpr int OD = 2 * T * PZ * 4;
+        v.fl = lds_u8<2 * T * PF>(af);
+        v.rhs = lds_f32<2 * T * PR * 4>(ar);
+        v.up = lds_f32<OD + 2 * PZ * 4>(ad);
+        v.ve = lds_f32<OD + (PZ + 1) * 4>(ad);
+        v.vw = lds_f32<OD + (PZ - 1) * 4>(ad);
+        v.vn = lds_f32<OD + (PZ + DXW) * 4>(ad);
+        v.vs = lds_f32<OD + (PZ - DXW) * 4>(ad);
+        v.own = lds_f32<OD + PZ * 4>(ad);
+        v.cn1 = lds_f32<2 * T * RB>(acn + ((v.fl & 63u) << 2));
+    }
+    template <int T>
+    __device__ __forceinline__ void step(ColVals& cur, float& lo) const {
+        ColVals nx{};
+        if constexpr (T + 1 < NP) load<T + 1>(nx);
+        const float2 cv = lds_f32x2<2 * T * RB + 256>(acn);
+        float s = 0.f;
+        s += cx * cur.ve;
+        s += cx * cur.vw;
+        s += cy * cur.vn;
+        s += cy * cur.vs;
+        s += cv.x * cur.up;
+        s += cv.y * lo;
+        float reltmp = omega * (cur.cn1 * (s - cur.rhs) - cur.own);
+        sts_f32_if<2 * T * PZ * 4 + PZ * 4>(ad, cur.own + reltmp, cur.fl & F_UNK);
+        lo = cur.up;
+        cur = nx;
+    }
+    template <int... T>
+    __device__ __forceinline__ void run(std::integer_sequence<int, T...>) const {
+        float lo = lds_f32<0>(ad);
+        ColVals cur;
+        load<0>(cur);
+        (step<T>(cur, lo), ...);
+    }
+    __device__ __forceinline__ void operator()() const { run(std::make_integer_sequence<int, NP>{}); }
+};
+
+// Shared memory of the column-walk sweep: the d, r and flag tiles of
+// TmaTile, then the block's RZ rows of the coefficient table (kColRow floats
+// each), then the mbarrier.
+template <int BY, int BZ>
+struct ColTile {
+    using TT = TmaTile<BY, BZ>;
+    static constexpr int RZ = TT::RZ;
+    static_assert(BZ <= kColTableRows, "the coefficient table is padded for BZ <= kColTableRows");
+    static constexpr uint32_t OFF_TAB = TT::OFF_CN;                   // 128-byte aligned
+    static constexpr uint32_t BYTES_TAB = RZ * kColRow * 4;
+    static constexpr uint32_t STAGE = align_up(OFF_TAB + BYTES_TAB, 128);
+    static constexpr uint32_t SMEM = STAGE + 8;                       // the stage + its mbarrier
+};
+
+// Issue the copies of block (bx, by, bz) into stage st on mbarrier bar (one
+// thread): d with a 2-cell halo (unless the sweep starts from zero), r and
+// the flags with a 1-cell ring, the block's coefficient rows.
+template <int BY, int BZ>
+__device__ __forceinline__ void col_issue(unsigned char* st, uint32_t bar, const CUtensorMap* td, const CUtensorMap* tr,
+                                          const CUtensorMap* tf, const float* ctab, int bx, int by, int bz,
+                                          bool zero_start) {
+    using TT = TmaTile<BY, BZ>;
+    using CT = ColTile<BY, BZ>;
+    const int xd = bx * TT::BX, xf = xd & ~15, j0 = 1 + by * BY, k0 = 1 + bz * BZ;
+    mbar_expect_tx(bar, TT::BYTES_R + TT::BYTES_F + CT::BYTES_TAB + (zero_start ? 0u : TT::BYTES_D));
+    if (!zero_start) tma_load_3d(smem_u32(st), td, xd, j0 - 2, k0 - 2, bar);
+    tma_load_3d(smem_u32(st + TT::OFF_R), tr, xd, j0 - 1, k0 - 1, bar);
+    tma_load_3d(smem_u32(st + TT::OFF_F), tf, xf, j0 - 1, k0 - 1, bar);
+    bulk_load(smem_u32(st + CT::OFF_TAB), ctab + (size_t)(k0 - 1) * kColRow, CT::BYTES_TAB, bar);
+}
+
+// After the copies of block (bx, by, bz) have landed in stage st: zero the d
+// tile on a zero start, the periodic halo images (a warp per tile row; rows
+// that cross no periodic y or z face are skipped whole unless the block
+// touches a periodic x face), red on the block + ring, black on the block.
+// Ends with a CTA barrier.
+template <int BY, int BZ, int NT>
+__device__ __forceinline__ void col_relax(unsigned char* st, const Geo<float>& g, const float* __restrict__ din,
+                                          const float* __restrict__ rin, bool zero_start, int bx, int by, int bz) {
+    using TT = TmaTile<BY, BZ>;
+    using CT = ColTile<BY, BZ>;
+    constexpr int BX = TT::BX, DXW = TT::DXW, FXW = TT::FXW, DY = TT::DY, DZ = TT::DZ, RY = TT::RY, RZ = TT::RZ;
+    constexpr int PZ = DY * DXW, PR = RY * DXW, PF = RY * FXW;
+    constexpr int NW = NT / 32;
+    static_assert(BY % 2 == 0 && BZ % 2 == 0, "the column walk pairs rows and planes");
+    const Dom& d = g.d;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y, lane = tid & 31, warp = tid >> 5;   // 1-D or 32 x 8
+    const int i0 = 1 + bx * BX, j0 = 1 + by * BY, k0 = 1 + bz * BZ;
+    const int xd = bx * BX, off = xd - (xd & ~15);
+    float* const D0 = reinterpret_cast<float*>(st);
+    if (zero_start) {
+        for (int q = tid; q < DXW * DY * DZ / 4; q += NT) reinterpret_cast<float4*>(D0)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();
+    }
+    const bool wx = d.perx && (i0 - 2 < 1 || i0 + BX + 1 > d.nx);
+    if (wx || (d.pery && (j0 - 2 < 1 || j0 + BY + 1 > d.ny)) || (d.perz && (k0 - 2 < 1 || k0 + BZ + 1 > d.nz))) {
+        float(*sD)[DY][DXW] = reinterpret_cast<float(*)[DY][DXW]>(st);
+        float(*sR)[RY][DXW] = reinterpret_cast<float(*)[RY][DXW]>(st + TT::OFF_R);
+        uint8_t(*sF)[RY][FXW] = reinterpret_cast<uint8_t(*)[RY][FXW]>(st + TT::OFF_F);
+        auto row_wraps = [&](int j, int k) {
+            return wx || (d.pery && (j < 1 || j > d.ny)) || (d.perz && (k < 1 || k > d.nz));
+        };
+        if (!zero_start)
+            for (int rw = warp; rw < DZ * DY; rw += NW) {
+                const int y = rw % DY, z = rw / DY;
+                if (!row_wraps(j0 - 2 + y, k0 - 2 + z)) continue;
+                for (int x = 2 + lane; x < BX + 6; x += 32) {
+                    long long s;
+                    if (periodic_image(d, i0 - 4 + x, j0 - 2 + y, k0 - 2 + z, s)) sD[z][y][x] = s >= 0 ? din[s] : 0.f;
+                }
+            }
+        for (int rw = warp; rw < RZ * RY; rw += NW) {
+            const int y = rw % RY, z = rw / RY;
+            if (!row_wraps(j0 - 1 + y, k0 - 1 + z)) continue;
+            for (int x = lane; x < BX + 2; x += 32) {
+                long long s;
+                if (periodic_image(d, i0 - 1 + x, j0 - 1 + y, k0 - 1 + z, s)) {
+                    sR[z][y][x + 3] = s >= 0 ? rin[s] : 0.f;
+                    sF[z][y][x + 3 + off] = s >= 0 ? g.flags[s] : (uint8_t)0;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    const float omega = g.omega, cx = g.cx, cy = g.cy;
+    const int half = lane >> 4, m = lane & 15;
+    const int par0 = (i0 + j0 + k0) & 1;
+    const uint32_t sD0 = smem_u32(st), sR0 = smem_u32(st + TT::OFF_R), sF0 = smem_u32(st + TT::OFF_F);
+    const uint32_t sT0 = smem_u32(st + CT::OFF_TAB);
+    constexpr uint32_t RB = kColRow * 4;
+    // red (i+j+k odd) on the block + ring: task = (row pair, plane parity);
+    // the lane's d cell one plane below its first update is (kp, jj+1, ii+3)
+    if (m < (BX + 2) / 2)
+        for (int task = warp; task < RY; task += NW) {
+            const int kp = task & 1, jj = (task >> 1) * 2 + half;
+            const int ii = 2 * m + ((par0 + jj + kp) & 1);                  // i = i0 - 1 + ii
+            const ColWalk<RZ / 2, PZ, PR, PF, DXW> w{sD0 + 4u * ((kp * DY + jj + 1) * DXW + ii + 3),
+                                                     sR0 + 4u * ((kp * RY + jj) * DXW + ii + 3),
+                                                     sF0 + (uint32_t)((kp * RY + jj) * FXW + ii + 3 + off),
+                                                     sT0 + RB * kp, cx, cy, omega};
+            w();
+        }
+    __syncthreads();
+    // black (i+j+k even) on the block: one plane below the first update is
+    // d cell (kp+1, jj+2, ii+4)
+    if (m < BX / 2)
+        for (int task = warp; task < BY; task += NW) {
+            const int kp = task & 1, jj = (task >> 1) * 2 + half;
+            const int ii = 2 * m + ((par0 + jj + kp) & 1);                  // i = i0 + ii
+            const ColWalk<BZ / 2, PZ, PR, PF, DXW> w{sD0 + 4u * (((kp + 1) * DY + jj + 2) * DXW + ii + 4),
+                                                     sR0 + 4u * (((kp + 1) * RY + jj + 1) * DXW + ii + 4),
+                                                     sF0 + (uint32_t)(((kp + 1) * RY + jj + 1) * FXW + ii + 4 + off),
+                                                     sT0 + RB * (kp + 1), cx, cy, omega};
+            w();
+        }
+    __syncthreads();
+}
+
+// Store block (bx, by, bz) of stage st (cells that are not unknowns hold 0
+// in d and in the tile): 4 rows per warp pass, 7 lanes x 4 cells (16-byte
+// aligned) per row.
+template <int BY, int BZ, int NT>
+__device__ __forceinline__ void col_store(const unsigned char* st, const Dom& d, float* __restrict__ dout, int bx, int by,
+                                          int bz) {
+    using TT = TmaTile<BY, BZ>;
+    constexpr int BX = TT::BX, DXW = TT::DXW, DY = TT::DY, NW = NT / 32;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y, lane = tid & 31, warp = tid >> 5;
+    const int i0 = 1 + bx * BX, j0 = 1 + by * BY, k0 = 1 + bz * BZ;
+    const float* D0 = reinterpret_cast<const float*>(st);
+    const int c = lane & 7, sub = lane >> 3;
+    const int i = i0 + 4 * c;
+    const int kend = min(BZ, d.nz + 1 - k0), jend = min(BY, d.ny + 1 - j0);
+    // rows rw = r0, r0 + 4 NW, ...: with BY | 4 NW the row jj stays and the
+    // plane kk advances by 4 NW / BY per pass
+    static_assert((4 * NW) % BY == 0, "store passes keep the row");
+    constexpr int DK = 4 * NW / BY;
+    const int r0 = 4 * warp + sub, jj = r0 % BY;
+    if (c < BX / 4 && i <= d.nx && jj < jend) {
+        const float* src = D0 + ((r0 / BY + 2) * DY + jj + 2) * DXW + 4 + 4 * c;
+        float* o = dout + d.at(i, j0 + jj, k0 + r0 / BY);
+        const bool full = i + 3 <= d.nx;
+        for (int kk = r0 / BY; kk < kend; kk += DK, src += DK * DY * DXW, o += DK * d.plane) {
+            const float4 v = *reinterpret_cast<const float4*>(src);
+            if (full) {
+                *reinterpret_cast<float4*>(o) = v;
+            } else {
+                o[0] = v.x;
+                if (i + 1 <= d.nx) o[1] = v.y;
+                if (i + 2 <= d.nx) o[2] = v.z;
+            }
+        }
+    }
+}
+
+// Bounded wait (1 s) of one thread for phase `phase` of mbarrier bar.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase) {
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, phase))
+        if (global_ns() - t0 > 1000000000ull) return false;
+    return true;
+}
+
+// The block sweep of sor_tma_block with fewer instructions per cell.  It
+// relies on the correction being zero on every cell that is not an unknown
+// (solid cells, ghost cells, padding; every kernel that writes d keeps it
+// so), so a closed face contributes c * 0 whatever its coefficient: the six
+// neighbour coefficients are the uniform cx, cx, cy, cy, cT(k), cB(k), and
+// only cn1 depends on the open-face mask.  The products and sums are those
+// of the masked update in the same order, so the iterate is the same.
+//
+// Work split: a warp relaxes two rows of one colour at every other plane,
+// one row per half-warp and one lane per column (every other cell of the
+// row), and each lane walks its column up the block; the cell below the
+// next update is the one above the current update, so it stays in a
+// register, and the plane (hence cT, cB and the cn1 row) is the same for
+// the whole warp.  Red runs on the block + 1-cell ring (RY rows, RZ planes),
+// black on the block (BY rows, BZ planes).  One thread polls the copies'
+// mbarrier; the CTA barrier then passes their completion on to every thread.
+template <int BY, int BZ, int NT>
+__device__ __forceinline__ bool sor_col_block(unsigned char* sm, const CUtensorMap* td, const CUtensorMap* tr,
+                                              const CUtensorMap* tf, const Geo<float>& g,
+                                              const float* __restrict__ din, const float* __restrict__ rin,
+                                              float* __restrict__ dout, bool zero_start, Scalars* __restrict__ sc,
+                                              int bx, int by, int bz, uint32_t phase) {
+    using CT = ColTile<BY, BZ>;
+    const uint32_t bar = smem_u32(sm + CT::STAGE);
+    const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+    bool ok = true;
+    if (lead) {
+        col_issue<BY, BZ>(sm, bar, td, tr, tf, g.ctab, bx, by, bz, zero_start);
+        ok = mbar_wait_bounded(bar, phase);
+    }
+    if (!__syncthreads_and(ok)) {
+        if (lead) {
+            atomicExch(&sc->timeout, 1);
+            mbar_wait_bounded(bar, phase);     // give copies still in flight a bounded chance to land
+        }
+        __syncthreads();
+        return false;
+    }
+    col_relax<BY, BZ, NT>(sm, g, din, rin, zero_start, bx, by, bz);
+    col_store<BY, BZ, NT>(sm, g.d, dout, bx, by, bz);
+    return true;
+}
 
 }  // namespace tma
 }  // namespace les

@@ -24,7 +24,7 @@ LES_FP32, LES_FP64 = 0, 1
  LES_AUX_NET_IN, LES_AUX_NET_Q) = range(13)
 LES_WARM_PREV, LES_WARM_NET, LES_WARM_ZERO = 0, 1, 2
 LES_SOR_REDBLACK, LES_SOR_TWINNED = 0, 1
-LES_SOR_NTILES = 29                 # sweep tile indices 0 .. LES_SOR_NTILES - 1 (les_set_sor_config)
+LES_SOR_NTILES = 35                 # sweep tile indices 0 .. LES_SOR_NTILES - 1 (les_set_sor_config)
 LES_NET_MMA_SYNC, LES_NET_TCGEN05, LES_NET_TCGEN05_GMEM_SPLIT = 0, 1, 2
 LES_NET_KERNELS_FOLDED, LES_NET_KERNELS_PERSISTENT, LES_NET_KERNELS_LAYERS = 0, 1, 2
 

@@ -200,7 +200,7 @@ def main():
     if a.sweep_table:
         rows = []
         for t in range(-1, les.LES_SOR_NTILES):
-            for kc in ((0, 8, 16) if (0 <= t <= 5 or t >= 25) else (0,)):
+            for kc in ((0, 8, 16) if (0 <= t <= 5 or 25 <= t < 29) else (0,)):
                 try:
                     ms = d.time_sor(t, kc, sweeps=20)
                 except les.LesError:

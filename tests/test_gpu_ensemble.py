@@ -49,7 +49,7 @@ def test_members_match_single_domains(tile):
     """Tiles 0-4: the batched row-tile sweep; 5: each member's own kernel
     (here the default configuration, the same as the single domains'); 6: the
     batched TMA blocks of every member in one launch per sweep, the same
-    arithmetic as tile 17 on a single domain."""
+    column-walk arithmetic as tile 29 on a single domain."""
     scs = scenes()
     ens = les.Ensemble(scs)
     ens.set_tile(tile, 4)
@@ -59,7 +59,7 @@ def test_members_match_single_domains(tile):
         if tile < 5:
             d.set_sor_config(12 + tile, 0)
         elif tile == 6:
-            d.set_sor_config(17, 0)
+            d.set_sor_config(29, 0)
         singles.append(d)
     for _ in range(3):
         est = ens.step()
@@ -132,7 +132,7 @@ def test_members_match_single_domains_with_learned_correction(tile):
     singles = []
     for sc in scs:
         d = les.Domain(sc)
-        d.set_sor_config(12 if tile == 0 else 17, 0)
+        d.set_sor_config(12 if tile == 0 else 29, 0)
         d.set_warmstart(net)
         d.set_net_schedule(10)
         singles.append(d)

@@ -243,12 +243,12 @@ def test_fused_sor_matches_two_pass(prec, case):
     ref.step(2)
     want = ref.fields()
     tol = 0.0 if prec == "fp64" else 1e-6
-    # TMA block tiles (17-20) and k-marching TMA columns (25-28) on every FP32
-    # grid, periodic halos included; the persistent TMA tiles (21-24) only
-    # without periodic axes
+    # TMA block tiles (17-20), k-marching TMA columns (25-28) and column-walk
+    # TMA blocks (29-34) on every FP32 grid, periodic halos
+    # included; the persistent TMA tiles (21-24) only without periodic axes
     tiles = list(range(17))
     if prec == "fp32":
-        tiles += list(range(17, 21)) + (list(range(21, 25)) if case == "city" else []) + list(range(25, 29))
+        tiles += list(range(17, 21)) + (list(range(21, 25)) if case == "city" else []) + list(range(25, 35))
     if prec == "fp32" and case != "city":
         d = les.Domain(sc, precision=p)
         for tile in range(21, 25):
@@ -256,7 +256,7 @@ def test_fused_sor_matches_two_pass(prec, case):
                 d.set_sor_config(tile, 0)
         d.close()
     for tile in tiles:
-        for kc in ((0, 3, 5) if (tile < 6 or tile >= 25) else (0,)):
+        for kc in ((0, 3, 5) if (tile < 6 or 25 <= tile < 29) else (0,)):
             d = les.Domain(sc, precision=p)
             d.set_sor_config(tile, kc)
             d.step(2)
@@ -264,6 +264,31 @@ def test_fused_sor_matches_two_pass(prec, case):
                 scale = max(np.abs(b).max(), 1e-30)
                 assert np.abs(a.astype(np.float64) - b).max() <= tol * scale, (tile, kc)
             d.close()
+
+
+@pytest.mark.parametrize("case", ["city", "periodic_y_odd"])
+def test_column_walk_equals_masked_update(case):
+    """The column-walk TMA blocks (tiles 29-34) drop the open-face masks of
+    the neighbour coefficients (a closed face meets a cell whose correction
+    is zero) and keep the masked update's products and sums in the same
+    order: after several steps of sweeps to tolerance the fields equal those
+    of the masked TMA block kernel (tile 17) bit for bit."""
+    if case == "city":
+        sc = city(nx=61, ny=37, nz=19, turb=0.1, fixed_sweeps=0, tol=1e-6, max_sweeps=4000, check_every=10)
+    else:
+        sc = city(nx=45, ny=18, nz=13, periodic_y=True, turb=0.1, fixed_sweeps=0, tol=1e-6, max_sweeps=4000,
+                  check_every=10)
+    out = {}
+    for tile in (17, 29, 30, 31, 32, 33, 34):
+        d = les.Domain(sc, precision=les.LES_FP32)
+        d.set_sor_config(tile, 0)
+        sweeps = [d.step(1)["sweeps"] for _ in range(3)]
+        out[tile] = (sweeps, d.fields())
+        d.close()
+    for tile in (29, 30, 31, 32, 33, 34):
+        assert out[tile][0] == out[17][0], tile
+        for a, b in zip(out[tile][1], out[17][1]):
+            assert np.array_equal(a, b), tile
 
 
 def test_autotune_picks_a_valid_config():

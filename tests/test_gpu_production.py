@@ -121,7 +121,7 @@ def lattice_oracle():
     return sc, o.fields()
 
 
-@pytest.mark.parametrize("tile", [17, 19, 21, 25, 27])
+@pytest.mark.parametrize("tile", [17, 19, 21, 25, 27, 29, 31, 32, 33, 34])
 def test_fp32_lattice_tma_tile(lattice_oracle, tile):
     sc, ref = lattice_oracle
     d = les.Domain(sc, precision=les.LES_FP32)
