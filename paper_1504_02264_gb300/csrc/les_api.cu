@@ -322,7 +322,7 @@ int run_sweeps(les_s* h, const Geo<T>& g, int n, int zero, long long& launched, 
         if constexpr (std::is_same<T, float>::value) {
             if (h->sor.tile >= kFirstTmaTile) {
                 launched += launch_sor_tma(g, h->tma, h->cn1tab, h->sor.tile - kFirstTmaTile, h->sor.kc, in,
-                                           (float*)h->dl[out], s == 0 ? zero : 0, h->sc, st);
+                                           (float*)h->dl[out], s == 0 ? zero : 0, h->sc, st, s > 0 ? 1 : 0);
                 h->dcur = out;
                 continue;
             }

@@ -295,8 +295,11 @@ bool tma_supported(const Dom& d);
 bool pipe_supported(const Dom& d);
 cudaError_t tma_prepare();
 bool tma_encode(const Dom& d, float* dl0, float* dl1, float* rr, uint8_t* flags, TmaMaps* maps);
+// pre = 1: the kernel before this one in the stream is a sweep of the same
+// batch (the column-walk tiles then copy r, flags and coefficients before
+// the dependency wait)
 int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, const float* cn1tab, int cfg, int kc, int in,
-                   float* dout, int zero, Scalars* sc, cudaStream_t s);
+                   float* dout, int zero, Scalars* sc, cudaStream_t s, int pre = 0);
 int launch_cn1_table(const Geo<float>& g, float* tab, cudaStream_t s);
 // the column-walk sweeps' coefficient rows from the cn1 table ((nz + 2 + 16) rows of 68 floats)
 int launch_col_table(const Geo<float>& g, const float* cn1tab, float* tab, cudaStream_t s);

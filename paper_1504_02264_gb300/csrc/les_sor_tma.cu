@@ -49,23 +49,47 @@ k_sor_tma(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtens
 }
 
 // The same block sweep with the column-walk update (sor_col_block): fewer
-// instructions per cell for the same iterate.
+// instructions per cell for the same iterate.  pre = 1 when the kernel
+// before it in the stream is a sweep of the same batch: sweeps write only d,
+// so the copies of r, the flags and the coefficient rows are issued before
+// the dependency wait (they overlap the tail of the previous sweep), and
+// only the copy of d after it.  Each CTA lets the next kernel launch once
+// its copies are issued (a dependent kernel waits for this grid to complete
+// before it touches anything this sweep writes).
 template <int BY, int BZ, int NT>
 __global__ void __launch_bounds__(NT)
 k_sor_col(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtensorMap tr,
           const __grid_constant__ CUtensorMap tf, Geo<float> g, const float* __restrict__ din,
-          const float* __restrict__ rin, float* __restrict__ dout, int zero_arg, Scalars* __restrict__ sc) {
+          const float* __restrict__ rin, float* __restrict__ dout, int zero_arg, Scalars* __restrict__ sc, int pre) {
+    using CT = ColTile<BY, BZ>;
     extern __shared__ __align__(128) unsigned char sm[];
-    pdl_wait();
-    if (sc->done) return;
-    if (threadIdx.x == 0) {
-        mbar_init(smem_u32(sm + ColTile<BY, BZ>::STAGE), 1);
+    const uint32_t bar = smem_u32(sm + CT::STAGE);
+    const bool lead = threadIdx.x == 0;
+    const int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
+    if (lead) {
+        mbar_init(bar, 1);
         mbar_fence_init();
+        if (pre) {
+            col_expect<BY, BZ>(bar, false);
+            col_issue_static<BY, BZ>(sm, bar, &tr, &tf, g.ctab, bx, by, bz);
+        }
     }
-    __syncthreads();
-    const bool zero_start = zero_arg == 1 || (zero_arg == 2 && sc->zflag);
-    sor_col_block<BY, BZ, NT>(sm, &td, &tr, &tf, g, din, rin, dout, zero_start, sc, blockIdx.x, blockIdx.y, blockIdx.z,
-                              0u);
+    pdl_wait();
+    const bool zero_start = !pre && (zero_arg == 1 || (zero_arg == 2 && sc->zflag));
+    if (lead) {
+        if (!pre) {
+            col_expect<BY, BZ>(bar, zero_start);
+            col_issue_static<BY, BZ>(sm, bar, &tr, &tf, g.ctab, bx, by, bz);
+        }
+        if (!zero_start) col_issue_d<BY, BZ>(sm, bar, &td, bx, by, bz);
+    }
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if (sc->done) {       // uniform over the grid: let the copies land (bounded), then leave
+        if (lead) mbar_wait_bounded(bar, 0u);
+        __syncthreads();
+        return;
+    }
+    sor_col_finish<BY, BZ, NT>(sm, g, din, rin, dout, zero_start, sc, bx, by, bz, 0u);
 }
 
 // The batched sweep of an ensemble: persistent CTAs walk the flattened list
@@ -567,11 +591,11 @@ cudaError_t allow_col() {
 
 template <int BY, int BZ, int NT>
 void launch_col_cfg(const Geo<float>& g, const TmaMaps& m, int in, float* dout, int zero, Scalars* sc,
-                    cudaStream_t s) {
+                    cudaStream_t s, int pre) {
     const Dom& d = g.d;
     dim3 grid((d.nx + 27) / 28, (d.ny + BY - 1) / BY, (d.nz + BZ - 1) / BZ);
     launch_pdl(k_sor_col<BY, BZ, NT>, grid, dim3(NT), ColTile<BY, BZ>::SMEM, s, m.d[in], m.r, m.f, g, m.dptr[in],
-               m.rptr, dout, zero, sc);
+               m.rptr, dout, zero, sc, pre);
 }
 
 template <int TY, int NS>
@@ -702,7 +726,7 @@ bool tma_encode(const Dom& d, float* dl0, float* dl1, float* rr, uint8_t* flags,
 }
 
 int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, const float* cn1tab, int cfg, int kc, int in,
-                   float* dout, int zero, Scalars* sc, cudaStream_t s) {
+                   float* dout, int zero, Scalars* sc, cudaStream_t s, int pre) {
     const TmaMaps& m = maps[cfg];
     switch (cfg) {
         case 8: launch_march_cfg<16, 16>(g, m, cn1tab, in, dout, kc, zero, sc, s); break;
@@ -717,12 +741,12 @@ int launch_sor_tma(const Geo<float>& g, const TmaMaps* maps, const float* cn1tab
         case 5: launch_pipe_cfg<8, 8, 512>(g, m, cn1tab, in, dout, zero, sc, s, 1); break;
         case 6: launch_pipe_cfg<16, 8, 512>(g, m, cn1tab, in, dout, zero, sc, s, 2); break;
         case 7: launch_pipe_cfg<12, 12, 512>(g, m, cn1tab, in, dout, zero, sc, s, 3); break;
-        case 12: launch_col_cfg<8, 8, 256>(g, m, in, dout, zero, sc, s); break;
-        case 13: launch_col_cfg<8, 8, 320>(g, m, in, dout, zero, sc, s); break;
-        case 14: launch_col_cfg<8, 16, 320>(g, m, in, dout, zero, sc, s); break;
-        case 15: launch_col_cfg<16, 8, 512>(g, m, in, dout, zero, sc, s); break;
-        case 16: launch_col_cfg<8, 8, 128>(g, m, in, dout, zero, sc, s); break;
-        case 17: launch_col_cfg<8, 8, 192>(g, m, in, dout, zero, sc, s); break;
+        case 12: launch_col_cfg<8, 8, 256>(g, m, in, dout, zero, sc, s, pre); break;
+        case 13: launch_col_cfg<8, 8, 320>(g, m, in, dout, zero, sc, s, pre); break;
+        case 14: launch_col_cfg<8, 16, 320>(g, m, in, dout, zero, sc, s, pre); break;
+        case 15: launch_col_cfg<16, 8, 512>(g, m, in, dout, zero, sc, s, pre); break;
+        case 16: launch_col_cfg<8, 8, 128>(g, m, in, dout, zero, sc, s, pre); break;
+        case 17: launch_col_cfg<8, 8, 192>(g, m, in, dout, zero, sc, s, pre); break;
         default: break;
     }
     return 1;

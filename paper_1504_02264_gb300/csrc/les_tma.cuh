@@ -364,21 +364,38 @@ struct ColTile {
     static constexpr uint32_t SMEM = STAGE + 8;                       // the stage + its mbarrier
 };
 
-// Issue the copies of block (bx, by, bz) into stage st on mbarrier bar (one
-// thread): d with a 2-cell halo (unless the sweep starts from zero), r and
-// the flags with a 1-cell ring, the block's coefficient rows.
+// The copies of block (bx, by, bz) into stage st on mbarrier bar (one
+// thread): col_expect arms the barrier for all of them, col_issue_static
+// copies what no sweep writes (r and the flags with a 1-cell ring, the
+// block's coefficient rows), col_issue_d the correction d with a 2-cell halo
+// (skipped when the sweep starts from zero).
+template <int BY, int BZ>
+__device__ __forceinline__ void col_expect(uint32_t bar, bool zero_start) {
+    using TT = TmaTile<BY, BZ>;
+    mbar_expect_tx(bar, TT::BYTES_R + TT::BYTES_F + ColTile<BY, BZ>::BYTES_TAB + (zero_start ? 0u : TT::BYTES_D));
+}
+template <int BY, int BZ>
+__device__ __forceinline__ void col_issue_static(unsigned char* st, uint32_t bar, const CUtensorMap* tr,
+                                                 const CUtensorMap* tf, const float* ctab, int bx, int by, int bz) {
+    using TT = TmaTile<BY, BZ>;
+    const int xd = bx * TT::BX, xf = xd & ~15, j0 = 1 + by * BY, k0 = 1 + bz * BZ;
+    tma_load_3d(smem_u32(st + TT::OFF_R), tr, xd, j0 - 1, k0 - 1, bar);
+    tma_load_3d(smem_u32(st + TT::OFF_F), tf, xf, j0 - 1, k0 - 1, bar);
+    bulk_load(smem_u32(st + ColTile<BY, BZ>::OFF_TAB), ctab + (size_t)(k0 - 1) * kColRow, ColTile<BY, BZ>::BYTES_TAB,
+              bar);
+}
+template <int BY, int BZ>
+__device__ __forceinline__ void col_issue_d(unsigned char* st, uint32_t bar, const CUtensorMap* td, int bx, int by,
+                                            int bz) {
+    tma_load_3d(smem_u32(st), td, bx * TmaTile<BY, BZ>::BX, 1 + by * BY - 2, 1 + bz * BZ - 2, bar);
+}
 template <int BY, int BZ>
 __device__ __forceinline__ void col_issue(unsigned char* st, uint32_t bar, const CUtensorMap* td, const CUtensorMap* tr,
                                           const CUtensorMap* tf, const float* ctab, int bx, int by, int bz,
                                           bool zero_start) {
-    using TT = TmaTile<BY, BZ>;
-    using CT = ColTile<BY, BZ>;
-    const int xd = bx * TT::BX, xf = xd & ~15, j0 = 1 + by * BY, k0 = 1 + bz * BZ;
-    mbar_expect_tx(bar, TT::BYTES_R + TT::BYTES_F + CT::BYTES_TAB + (zero_start ? 0u : TT::BYTES_D));
-    if (!zero_start) tma_load_3d(smem_u32(st), td, xd, j0 - 2, k0 - 2, bar);
-    tma_load_3d(smem_u32(st + TT::OFF_R), tr, xd, j0 - 1, k0 - 1, bar);
-    tma_load_3d(smem_u32(st + TT::OFF_F), tf, xf, j0 - 1, k0 - 1, bar);
-    bulk_load(smem_u32(st + CT::OFF_TAB), ctab + (size_t)(k0 - 1) * kColRow, CT::BYTES_TAB, bar);
+    col_expect<BY, BZ>(bar, zero_start);
+    if (!zero_start) col_issue_d<BY, BZ>(st, bar, td, bx, by, bz);
+    col_issue_static<BY, BZ>(st, bar, tr, tf, ctab, bx, by, bz);
 }
 
 // After the copies of block (bx, by, bz) have landed in stage st: zero the d
@@ -512,6 +529,31 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase) 
     return true;
 }
 
+// The rest of the column-walk block sweep once the block's copies are
+// issued on the stage's mbarrier: the bounded wait, the relaxation and the
+// store.  Returns false after recording a timed-out wait.
+template <int BY, int BZ, int NT>
+__device__ __forceinline__ bool sor_col_finish(unsigned char* sm, const Geo<float>& g, const float* __restrict__ din,
+                                               const float* __restrict__ rin, float* __restrict__ dout,
+                                               bool zero_start, Scalars* __restrict__ sc, int bx, int by, int bz,
+                                               uint32_t phase) {
+    const uint32_t bar = smem_u32(sm + ColTile<BY, BZ>::STAGE);
+    const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+    bool ok = true;
+    if (lead) ok = mbar_wait_bounded(bar, phase);
+    if (!__syncthreads_and(ok)) {
+        if (lead) {
+            atomicExch(&sc->timeout, 1);
+            mbar_wait_bounded(bar, phase);     // give copies still in flight a bounded chance to land
+        }
+        __syncthreads();
+        return false;
+    }
+    col_relax<BY, BZ, NT>(sm, g, din, rin, zero_start, bx, by, bz);
+    col_store<BY, BZ, NT>(sm, g.d, dout, bx, by, bz);
+    return true;
+}
+
 // The block sweep of sor_tma_block with fewer instructions per cell.  It
 // relies on the correction being zero on every cell that is not an unknown
 // (solid cells, ghost cells, padding; every kernel that writes d keeps it
@@ -537,22 +579,8 @@ __device__ __forceinline__ bool sor_col_block(unsigned char* sm, const CUtensorM
     using CT = ColTile<BY, BZ>;
     const uint32_t bar = smem_u32(sm + CT::STAGE);
     const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
-    bool ok = true;
-    if (lead) {
-        col_issue<BY, BZ>(sm, bar, td, tr, tf, g.ctab, bx, by, bz, zero_start);
-        ok = mbar_wait_bounded(bar, phase);
-    }
-    if (!__syncthreads_and(ok)) {
-        if (lead) {
-            atomicExch(&sc->timeout, 1);
-            mbar_wait_bounded(bar, phase);     // give copies still in flight a bounded chance to land
-        }
-        __syncthreads();
-        return false;
-    }
-    col_relax<BY, BZ, NT>(sm, g, din, rin, zero_start, bx, by, bz);
-    col_store<BY, BZ, NT>(sm, g.d, dout, bx, by, bz);
-    return true;
+    if (lead) col_issue<BY, BZ>(sm, bar, td, tr, tf, g.ctab, bx, by, bz, zero_start);
+    return sor_col_finish<BY, BZ, NT>(sm, g, din, rin, dout, zero_start, sc, bx, by, bz, phase);
 }
 
 }  // namespace tma
