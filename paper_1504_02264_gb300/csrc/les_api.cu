@@ -121,6 +121,8 @@ struct les_s {
     TmaMaps tma[kNumTmaTiles];            // tensor maps of the TMA sweep (FP32, no periodic axis)
     bool tma_ok = false;
     bool pipe_ok = false;                 // persistent TMA tiles (no periodic axis)
+    CUtensorMap est_maps[4];              // the TMA estimate's tiles (FP32, no periodic axis)
+    bool est_tma = false;
     float* cn1tab = nullptr;              // cn1 over (plane, open-face mask) for the pipelined sweep
     float* coltab = nullptr;              // per-plane coefficient rows of the column-walk sweeps
     double* diag64 = nullptr;             // FP64 diagonal over (plane, open-face mask), the residual's
@@ -305,6 +307,16 @@ double elapsed(les_s* h, int a, int b) {
 // k_residual64 forms the next right-hand side and the FP64 residual); the
 // relative residual is tested after each batch of check_every sweeps and at
 // max_sweeps, exactly where the sequential algorithm tests it.
+
+// the estimate after a batch of sweeps: from TMA tiles on FP32 grids with no
+// periodic axis, else the plain kernel (both give the same result)
+template <typename T>
+int launch_estimate(les_s* h, const Geo<T>& g, T* rout, CondArgs ca, cudaStream_t st) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (h->est_tma) return launch_sor_est_tma(g, h->est_maps, h->dcur, rout, reducer(h), ca, st);
+    }
+    return launch_sor_est<T>(g, (const T*)h->dl[h->dcur], (const T*)h->rr, rout, reducer(h), ca, st);
+}
 
 // n sweeps on the correction.  zero: 0 continue from d, 1 start from d = 0,
 // 2 read the device flag.  The fused kernel ping-pongs between the two d
@@ -509,9 +521,8 @@ int sor_solve(les_s* h) {
         sweeps += n;
         bool need = true;
         if (!G.fixed_sweeps) {
-            h->launches += launch_sor_est<T>(g, (const T*)h->dl[h->dcur], (const T*)h->rr,
-                                             net_loop ? (T*)h->rcur : nullptr, reducer(h),
-                                             cond_args(h, RES_LOOP, n, 0), h->stream);
+            h->launches += launch_estimate<T>(h, g, net_loop ? (T*)h->rcur : nullptr, cond_args(h, RES_LOOP, n, 0),
+                                              h->stream);
             CK(cudaGetLastError());
             int rc = fetch_scalars(h);
             if (rc) return rc;
@@ -772,8 +783,7 @@ int build_graph(les_s* h, int cur) {
             for (int b = 0; b < chunk_batches(h) && !rc; ++b) {
                 run_sweeps<T>(h, g, h->net_every, 2, nl, cs);     // net_every even: d returns to dl[0]
                 if (b > 0) CK(cudaStreamWaitEvent(cs, h->ev_pool, 0));      // the prediction has read rcur
-                launch_sor_est<T>(g, (const T*)h->dl[h->dcur], (const T*)h->rr, (T*)h->rcur, reducer(h),
-                                  cond_args(h, RES_LOOP, h->net_every, 1), cs);
+                launch_estimate<T>(h, g, (T*)h->rcur, cond_args(h, RES_LOOP, h->net_every, 1), cs);
                 launch_refine<T>(h, g, cond_args(h, RES_LOOP, h->net_every, 1), cs);
                 if (b > 0) CK(cudaStreamWaitEvent(cs, h->ev_q, 0));         // the prediction is complete
                 launch_warm_pending<T>(g, (T*)h->rcur, h->pred, (T*)h->dl[h->dcur], h->warm_scal + 1, reducer(h),
@@ -797,8 +807,7 @@ int build_graph(les_s* h, int cur) {
         if constexpr (std::is_same<T, float>::value) {
             for (int b = 0; b < chunk_batches(h); ++b) {
                 run_sweeps<T>(h, g, h->net_every, 2, nl, cs);     // net_every even: d returns to dl[0]
-                launch_sor_est<T>(g, (const T*)h->dl[h->dcur], (const T*)h->rr, (T*)h->rcur, reducer(h),
-                                  cond_args(h, RES_LOOP, h->net_every, 1), cs);
+                launch_estimate<T>(h, g, (T*)h->rcur, cond_args(h, RES_LOOP, h->net_every, 1), cs);
                 launch_refine<T>(h, g, cond_args(h, RES_LOOP, h->net_every, 1), cs);
                 rc = net_correct_loop<T>(h, g, cs, true);
                 if (rc) break;
@@ -807,8 +816,7 @@ int build_graph(les_s* h, int cur) {
     } else {
         for (int b = 0; b < kChunkBatches; ++b) {
             run_sweeps<T>(h, g, G.check_every, 2, nl, cs);     // check_every even: d returns to dl[0]
-            launch_sor_est<T>(g, (const T*)h->dl[h->dcur], (const T*)h->rr, (T*)nullptr, reducer(h),
-                              cond_args(h, RES_LOOP, G.check_every, 1), cs);
+            launch_estimate<T>(h, g, (T*)nullptr, cond_args(h, RES_LOOP, G.check_every, 1), cs);
             launch_refine<T>(h, g, cond_args(h, RES_LOOP, G.check_every, 1), cs);
         }
     }
@@ -1102,6 +1110,8 @@ int create_impl(les_s* h, const uint8_t* solid) {
             CK(tma_prepare());
             h->tma_ok = tma_encode(d, (float*)h->dl[0], (float*)h->dl[1], (float*)h->rr, h->flags, h->tma);
             h->pipe_ok = h->tma_ok && pipe_supported(d);
+            h->est_tma = h->tma_ok && !d.perx && !d.pery && !d.perz &&
+                         tma_encode_est(d, (float*)h->dl[0], (float*)h->dl[1], (float*)h->rr, h->flags, h->est_maps);
         }
         CK(cudaStreamSynchronize(h->stream));
     }

@@ -312,6 +312,12 @@ bool tma_encode_member(const Dom& d, float* dl0, float* dl1, float* rr, const ui
 int launch_sor_tma_ens(const EnsTab<float>& tab, const CUtensorMap* maps, int in, int zero, int ctas,
                        cudaStream_t s);
 int sor_tma_ens_resident();     // resident CTAs of the batched TMA sweep on this device
+// the estimate of an FP32 grid with no periodic axis from TMA tiles (the
+// cells, arithmetic and sums of launch_sor_est, so the same result): maps
+// from tma_encode_est (d[0], d[1], r, flags); dcur selects d
+bool tma_encode_est(const Dom& d, float* dl0, float* dl1, float* rr, const uint8_t* flags, CUtensorMap* out4);
+int launch_sor_est_tma(const Geo<float>& g, const CUtensorMap* maps4, int dcur, float* rout, const Reduce& red,
+                       CondArgs ca, cudaStream_t s);
 // the plain-SOR solve of an ensemble as one persistent cooperative launch
 // (les_kernels.cu); bar: 2 zeroed unsigned of grid-barrier state, err: a
 // zeroed device flag set when a bounded wait gave up; returns the launches

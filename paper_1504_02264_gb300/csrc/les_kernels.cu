@@ -1086,6 +1086,22 @@ int launch_residual64(const Geo<T>& g, const double* ph, const T* rhs, T* r, dou
 // diagonal), |e| / |rhs| with FP64 sums.  b - A(p + d) = r - A d exactly, so
 // this is the residual of the current iterate up to rounding.  It only decides
 // when to take the FP64 refinement, which makes the stop decision.
+// the estimate's bookkeeping from the grid's sum of squared residuals (one
+// thread): the relative estimate, the sweep counters and whether a
+// refinement is due
+__device__ __forceinline__ void est_finish(double sum, const Reduce& red, const CondArgs& ca) {
+    Scalars* sc = red.sc;
+    const double rhs2 = sc->rhs2;
+    const double est = rhs2 == 0.0 ? sqrt(sum) : sqrt(sum / rhs2);
+    sc->est = est;
+    sc->sweeps += ca.n;
+    sc->since += ca.n;
+    sc->zflag = 0;
+    const bool need = ca.force || !(est > ca.tol) || est <= kRefineDrop * sc->rho_ref ||
+                      sc->since >= kRefineEvery || sc->sweeps >= ca.limit;
+    sc->refine = need;
+}
+
 template <typename T>
 __device__ __forceinline__ void sor_est_body(const Geo<T>& g, const T* __restrict__ dl, const T* __restrict__ r,
                                              T* __restrict__ rout, const Reduce& red, const CondArgs& ca, int bx,
@@ -1152,20 +1168,8 @@ __device__ __forceinline__ void sor_est_body(const Geo<T>& g, const T* __restric
         }
     }
     double x[1] = {(double)acc};
-    if (grid_sum_at<1>(x, red, nb, b)) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
-            Scalars* sc = red.sc;
-            const double rhs2 = sc->rhs2;
-            const double est = rhs2 == 0.0 ? sqrt(x[0]) : sqrt(x[0] / rhs2);
-            sc->est = est;
-            sc->sweeps += ca.n;
-            sc->since += ca.n;
-            sc->zflag = 0;
-            const bool need = ca.force || !(est > ca.tol) || est <= kRefineDrop * sc->rho_ref ||
-                              sc->since >= kRefineEvery || sc->sweeps >= ca.limit;
-            sc->refine = need;
-        }
-    }
+    if (grid_sum_at<1>(x, red, nb, b))
+        if (threadIdx.x == 0 && threadIdx.y == 0) est_finish(x[0], red, ca);
 }
 
 // (FP32: at most 64 registers, four CTAs per SM: the half-chunk loads alone would
@@ -1185,6 +1189,83 @@ int launch_sor_est(const Geo<T>& g, const T* dl, const T* r, T* rout, const Redu
     const Dom& d = g.d;
     dim3 grid((d.nx + 31) / 32, (d.ny + 7) / 8, (d.nz + kEstChunk - 1) / kEstChunk);
     launch_pdl(k_sor_est<T>, grid, dim3(32, 8), 0, s, g, dl, r, rout, red, ca);
+    return 1;
+}
+
+// The same estimate on an FP32 grid with no periodic axis, its loads from
+// three TMA tile copies instead of eight global loads per cell: a CTA's
+// 32 x 8 x kEstChunk cells with d on a 1-cell ring (40 x 10 x 10 box from the
+// padded column of i0 - 4), r on the cells, the flags (48 wide from the
+// 16-byte column at or below that of i0 - 4).  Each thread takes the same
+// cells in the same order with the same arithmetic, and the block and grid
+// sums are those of k_sor_est (same launch shape), so the result is the same.
+__global__ void __launch_bounds__(256, 4)
+    k_sor_est_tma(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtensorMap tr,
+                  const __grid_constant__ CUtensorMap tf, Geo<float> g, float* __restrict__ rout, Reduce red,
+                  CondArgs ca) {
+    static_assert(kEstChunk == 8, "tile boxes of 8 planes");
+    __shared__ __align__(128) float sD[kEstChunk + 2][10][40];
+    __shared__ __align__(128) float sR[kEstChunk][8][32];
+    __shared__ __align__(128) uint8_t sF[kEstChunk][8][48];
+    __shared__ __align__(8) uint64_t bar_word;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
+    const uint32_t bar = tma::smem_u32(&bar_word);
+    if (tid == 0) {
+        tma::mbar_init(bar, 1);
+        tma::mbar_fence_init();
+    }
+    pdl_wait();
+    if (red.sc->done) return;      // uniform over the grid, before any copy
+    const Dom& d = g.d;
+    const int i0 = blockIdx.x * 32 + 1, j0 = blockIdx.y * 8 + 1, kb = blockIdx.z * kEstChunk + 1;
+    bool ok = true;
+    if (tid == 0) {
+        tma::mbar_expect_tx(bar, (uint32_t)(sizeof(sD) + sizeof(sR) + sizeof(sF)));
+        tma::tma_load_3d(tma::smem_u32(sD), &td, 32 * blockIdx.x, j0 - 1, kb - 1, bar);
+        tma::tma_load_3d(tma::smem_u32(sR), &tr, 32 * blockIdx.x + 4, j0, kb, bar);
+        tma::tma_load_3d(tma::smem_u32(sF), &tf, 32 * blockIdx.x, j0, kb, bar);
+        ok = tma::mbar_wait_bounded(bar, 0u);
+        if (!ok) {
+            atomicExch(&red.sc->timeout, 1);
+            tma::mbar_wait_bounded(bar, 0u);      // copies still in flight: a bounded chance to land
+        }
+    }
+    ok = __syncthreads_and(ok);
+    float acc = 0.f;
+    const int i = i0 + tx, j = j0 + ty;
+    if (ok && i <= d.nx && j <= d.ny) {
+        const int ke = min(kb + kEstChunk, d.nz + 1);
+        const long long c0 = d.at(i, j, kb);
+        const long long pl = d.plane;
+#pragma unroll
+        for (int m = 0; m < kEstChunk; ++m) {
+            if (kb + m >= ke) break;
+            const uint8_t f = sF[m][ty][tx + 4];
+            if (!(f & F_UNK)) continue;
+            const int k = kb + m;
+            const float dc = sD[m + 1][ty + 1][tx + 4];
+            float s = 0.f;
+            if (f & F_E) s += g.cx * (sD[m + 1][ty + 1][tx + 5] - dc);
+            if (f & F_W) s += g.cx * (sD[m + 1][ty + 1][tx + 3] - dc);
+            if (f & F_N) s += g.cy * (sD[m + 1][ty + 2][tx + 4] - dc);
+            if (f & F_S) s += g.cy * (sD[m + 1][ty][tx + 4] - dc);
+            if (f & F_T) s += g.cT[k] * (sD[m + 2][ty + 1][tx + 4] - dc);
+            if (f & F_B) s += g.cB[k] * (sD[m][ty + 1][tx + 4] - dc);
+            const float res = sR[m][ty][tx] - s;
+            if (rout) rout[c0 + m * pl] = res;
+            acc += res * res;
+        }
+    }
+    double x[1] = {(double)acc};
+    if (grid_sum<1>(x, red))
+        if (tid == 0) est_finish(x[0], red, ca);
+}
+
+int launch_sor_est_tma(const Geo<float>& g, const CUtensorMap* maps4, int dcur, float* rout, const Reduce& red,
+                       CondArgs ca, cudaStream_t s) {
+    const Dom& d = g.d;
+    dim3 grid((d.nx + 31) / 32, (d.ny + 7) / 8, (d.nz + kEstChunk - 1) / kEstChunk);
+    launch_pdl(k_sor_est_tma, grid, dim3(32, 8), 0, s, maps4[dcur], maps4[2], maps4[3], g, rout, red, ca);
     return 1;
 }
 

@@ -760,6 +760,17 @@ bool tma_encode_member(const Dom& d, float* dl0, float* dl1, float* rr, const ui
            encode3d(&out4[3], CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, const_cast<uint8_t*>(flags), d, 48, by + 2, bz + 2);
 }
 
+// tensor maps of the TMA estimate (32 x 8 x 8 cells per CTA): d[0], d[1] with a
+// 1-cell ring in a 40-wide box (x from the padded column of i0 - 4), r (the
+// block, x from the padded column of i0) and the flags (48 wide from the
+// 16-byte column at or below that of i0 - 4)
+bool tma_encode_est(const Dom& d, float* dl0, float* dl1, float* rr, const uint8_t* flags, CUtensorMap* out4) {
+    return encode3d(&out4[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, dl0, d, 40, 10, 10) &&
+           encode3d(&out4[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, dl1, d, 40, 10, 10) &&
+           encode3d(&out4[2], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, rr, d, 32, 8, 8) &&
+           encode3d(&out4[3], CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, const_cast<uint8_t*>(flags), d, 48, 8, 8);
+}
+
 int sor_tma_ens_resident() { return g_ens_tma_resident; }
 
 int launch_sor_tma_ens(const EnsTab<float>& tab, const CUtensorMap* maps, int in, int zero, int ctas,
