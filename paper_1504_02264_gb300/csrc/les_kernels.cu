@@ -1532,9 +1532,10 @@ __global__ void __launch_bounds__(256) k_warm_ls_c(Geo<T> g, const T* __restrict
                                                    float* __restrict__ qout, double* alpha, Reduce red, int in_loop) {
     using LT = LsTile<S>;
     __shared__ LT L;
-    pdl_wait();
+    // everything up to the dependency wait reads only what no kernel of the
+    // solve writes (the geometry and the flags): it overlaps the tail of the
+    // convolution before
     const Dom& d = g.d;
-    if (red.sc->done) return;      // uniform over the grid
     const int tid = threadIdx.x + 32 * threadIdx.y;
     const int Xc = (d.nx + S - 1) / S, Yc = (d.ny + S - 1) / S, Zc = (d.nz + S - 1) / S;
     const int X0 = blockIdx.x * 32 - 1, Y0 = blockIdx.y * 8 - 1, Z0 = blockIdx.z * kEstChunk - 1;
@@ -1543,9 +1544,8 @@ __global__ void __launch_bounds__(256) k_warm_ls_c(Geo<T> g, const T* __restrict
         float w;
         prolong_w(max(X0, 0), S, Xc, cmin, w);
     }
-    // the owned cells' flags and residuals, issued first so that their latency
-    // overlaps the fill of the tile (r is read unconditionally: the padded
-    // array holds every cell of the chunk's columns)
+    // the owned cells' flags, issued first so that their latency overlaps the
+    // set-up of the tile (the residuals after the wait)
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int i = blockIdx.x * 32 + tx + 1, j = blockIdx.y * 8 + ty + 1;
     const int kb = blockIdx.z * kEstChunk + 1, ke = min(kb + kEstChunk, d.nz + 1);
@@ -1555,11 +1555,7 @@ __global__ void __launch_bounds__(256) k_warm_ls_c(Geo<T> g, const T* __restrict
     uint8_t fl[kEstChunk];
     T rr[kEstChunk];
 #pragma unroll
-    for (int m = 0; m < kEstChunk; ++m) {
-        const bool in = own && kb + m < ke;
-        fl[m] = in ? g.flags[cown + (long long)m * pl] : (uint8_t)0;
-        rr[m] = in ? r[cown + (long long)m * pl] : T(0);
-    }
+    for (int m = 0; m < kEstChunk; ++m) fl[m] = own && kb + m < ke ? g.flags[cown + (long long)m * pl] : (uint8_t)0;
     if (tid < LT::HX) {
         const int f = X0 + tid, fw = halo_coord(f, d.nx, d.perx);
         const bool wrapped = fw >= 0 && fw != f;
@@ -1590,6 +1586,10 @@ __global__ void __launch_bounds__(256) k_warm_ls_c(Geo<T> g, const T* __restrict
         L.z0[h] = c0;
         L.z1[h] = min(c0 + 1, Zc - 1);
     }
+    pdl_wait();
+    if (red.sc->done) return;      // uniform over the grid (no barrier has been passed yet)
+#pragma unroll
+    for (int m = 0; m < kEstChunk; ++m) rr[m] = own && kb + m < ke ? r[cown + (long long)m * pl] : T(0);
     __syncthreads();
     for (int q = tid; q < LT::HZ * LT::HY * LT::CW; q += 256) {
         const int c = q % LT::CW, hy = (q / LT::CW) % LT::HY, hz = q / (LT::CW * LT::HY);

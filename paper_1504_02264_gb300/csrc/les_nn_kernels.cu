@@ -676,6 +676,8 @@ __global__ void k_pool_rms(const float* r, const uint8_t* flags, Dom d, float* r
     __shared__ float sr[SZ][S][32], sm[SZ][S][32];
     __shared__ bool last;
     pdl_wait();
+    // the next kernel (the first convolution) may launch and copy its weights
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (gate && *(volatile const int*)gate) return;
     const int Xc = (d.nx + S - 1) / S, Yc = (d.ny + S - 1) / S;
     const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;

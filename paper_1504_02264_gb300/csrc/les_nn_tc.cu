@@ -209,10 +209,6 @@ __device__ __forceinline__ void stage_half(const ConvArgs& A, int gx, int gy, in
 
 template <int CO, int IN>
 __global__ void __launch_bounds__(NTH) k_conv3_tc(ConvArgs A, const int* gate, int* timeout) {
-    pdl_wait();
-    // the solve this inference serves may have ended: the flag's load is
-    // issued here and tested after the first chunk's copies are under way
-    const int ended = gate ? *(volatile const int*)gate : 0;
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     TcSmem<CO>& S = *reinterpret_cast<TcSmem<CO>*>(tc_smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -240,25 +236,48 @@ __global__ void __launch_bounds__(NTH) k_conv3_tc(ConvArgs A, const int* gate, i
     tc_after();
     const uint32_t tmem = S.tmem;
 
-    auto stage = [&](int c, TcStage<CO>& T) {
+    // a chunk's weights (no kernel of the solve writes them) and its input halo
+    auto stage_w = [&](int c, TcStage<CO>& T) {
         const int c0 = 16 * c;
-        for (int q = tid; q < 2 * NVOX; q += NTH) {
-            const int h = q / NVOX, v = q % NVOX;
-            const int hx = v % HX, hy = (v / HX) % HY, hz = v / (HX * HY);
-            stage_half<IN>(A, x0 - 1 + hx, y0 - 1 + hy, z0 - 1 + hz, c0 + 8 * h, saddr(&T.a[h][v][0]), &T.a[h][v][0]);
-        }
         for (int q = tid; q < 27 * 2 * CO; q += NTH) {
             const int co = q % CO, h = (q / CO) & 1, tap = q / (2 * CO);
             const bool ok = co0 + co < Cout;
             const __nv_bfloat16* src = ok ? A.w + ((size_t)tap * Cout + co0 + co) * Cin + c0 + 8 * h : A.w;
             cp16(saddr(&T.b[tap][h][co][0]), src, ok ? 16 : 0);
         }
+    };
+    auto stage_x = [&](int c, TcStage<CO>& T) {
+        const int c0 = 16 * c;
+        for (int q = tid; q < 2 * NVOX; q += NTH) {
+            const int h = q / NVOX, v = q % NVOX;
+            const int hx = v % HX, hy = (v / HX) % HY, hz = v / (HX * HY);
+            stage_half<IN>(A, x0 - 1 + hx, y0 - 1 + hy, z0 - 1 + hz, c0 + 8 * h, saddr(&T.a[h][v][0]), &T.a[h][v][0]);
+        }
+    };
+    auto stage = [&](int c, TcStage<CO>& T) {
+        stage_x(c, T);
+        stage_w(c, T);
         cp_commit();
     };
 
     bool ok = true;
     int issued = cb - 1;                           // the last chunk whose MMAs were issued
-    stage(cb, S.st[0]);
+    // The pooled and upsampled layers run only inside an inference, right
+    // after the previous convolution, which does not write weights: their
+    // first chunk's weights are copied before the wait for that kernel (its
+    // tail overlaps the copies).  Every layer lets the next kernel launch once
+    // the wait has returned (every kernel that follows a convolution waits for
+    // it before it reads anything the convolution writes).
+    constexpr bool kWeightsEarly = IN == IN_POOL || IN == IN_UP;
+    if constexpr (kWeightsEarly) stage_w(cb, S.st[0]);
+    pdl_wait();
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    // the solve this inference serves may have ended: the flag's load is
+    // issued here and tested after the first chunk's copies are under way
+    const int ended = gate ? *(volatile const int*)gate : 0;
+    if constexpr (!kWeightsEarly) stage_w(cb, S.st[0]);
+    stage_x(cb, S.st[0]);
+    cp_commit();
     if (ended) {
         // uniform over the CTA: let the copies land, give the memory back
         cp_wait<0>();
