@@ -1600,12 +1600,13 @@ __global__ void __launch_bounds__(256) k_warm_ls_c(Geo<T> g, const T* __restrict
         L.col[hz][hy][c] = v;
     }
     __syncthreads();
-    for (int q = tid; q < LT::HZ * LT::HY * LT::HX; q += 256) {
-        const int hx = q % LT::HX, hy = (q / LT::HX) % LT::HY, hz = q / (LT::HX * LT::HY);
-        const int fx = L.fx[hx], fy = L.fy[hy], fz = L.fz[hz];
+    // the fine values of the tile: cell (hx, hy, hz) as the x-interpolation of
+    // its two coarse columns; warps take rows (hy, hz) with lanes along x (the
+    // x weights and column slots of a lane stay in registers), then the last
+    // LT::HX - 32 cells of every row go one per thread
+    auto fine = [&](int hx, int hy, int hz, int fx, int a, int b, float wxv) {
         float v = 0.f;
-        if (fx >= 0 && fy >= 0 && fz >= 0) {
-            const int a = L.x0[hx], b = L.x1[hx];
+        if (fx >= 0 && L.fy[hy] >= 0 && L.fz[hz] >= 0) {
             float v0, v1;
             if (a >= 0) {
                 v0 = L.col[hz][hy][a];
@@ -1614,9 +1615,28 @@ __global__ void __launch_bounds__(256) k_warm_ls_c(Geo<T> g, const T* __restrict
                 v0 = prolong_col(yc, Xc, Yc, -1 - a, L.y0[hy], L.y1[hy], L.wy[hy], L.z0[hz], L.z1[hz], L.wz[hz]);
                 v1 = prolong_col(yc, Xc, Yc, -1 - b, L.y0[hy], L.y1[hy], L.wy[hy], L.z0[hz], L.z1[hz], L.wz[hz]);
             }
-            v = prolong_mix(v0, v1, L.wx[hx]);
+            v = prolong_mix(v0, v1, wxv);
         }
         L.q[hz][hy][hx] = v;
+    };
+    static_assert(LT::HX > 32 && LT::HX - 32 <= 2 && (LT::HX - 32) * LT::HY * LT::HZ <= 256, "one tail pass");
+    {
+        const int fx = L.fx[tx], a = L.x0[tx], b = L.x1[tx];
+        const float wxv = L.wx[tx];
+        int hy = ty, hz = 0;                   // row ty, ty + 8, ... of the HZ x HY rows
+        for (int rw = ty; rw < LT::HZ * LT::HY; rw += 8) {
+            fine(tx, hy, hz, fx, a, b, wxv);
+            hy += 8;
+            while (hy >= LT::HY) {
+                hy -= LT::HY;
+                ++hz;
+            }
+        }
+        constexpr int NTAIL = LT::HX - 32;
+        if (tid < NTAIL * LT::HY * LT::HZ) {
+            const int hx = 32 + tid % NTAIL, rw = tid / NTAIL;
+            fine(hx, rw % LT::HY, rw / LT::HY, L.fx[hx], L.x0[hx], L.x1[hx], L.wx[hx]);
+        }
     }
     __syncthreads();
     T s0 = T(0), s1 = T(0);
