@@ -1210,20 +1210,29 @@ __global__ void __launch_bounds__(256, 4)
     __shared__ __align__(8) uint64_t bar_word;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
     const uint32_t bar = tma::smem_u32(&bar_word);
+    const Dom& d = g.d;
+    const int i0 = blockIdx.x * 32 + 1, j0 = blockIdx.y * 8 + 1, kb = blockIdx.z * kEstChunk + 1;
+    // the kernel before this one is a sweep, which writes only d: r and the
+    // flags are copied before the dependency wait, d after it
     if (tid == 0) {
         tma::mbar_init(bar, 1);
         tma::mbar_fence_init();
-    }
-    pdl_wait();
-    if (red.sc->done) return;      // uniform over the grid, before any copy
-    const Dom& d = g.d;
-    const int i0 = blockIdx.x * 32 + 1, j0 = blockIdx.y * 8 + 1, kb = blockIdx.z * kEstChunk + 1;
-    bool ok = true;
-    if (tid == 0) {
-        tma::mbar_expect_tx(bar, (uint32_t)(sizeof(sD) + sizeof(sR) + sizeof(sF)));
-        tma::tma_load_3d(tma::smem_u32(sD), &td, 32 * blockIdx.x, j0 - 1, kb - 1, bar);
+        tma::mbar_expect_tx_only(bar, (uint32_t)(sizeof(sR) + sizeof(sF)));
         tma::tma_load_3d(tma::smem_u32(sR), &tr, 32 * blockIdx.x + 4, j0, kb, bar);
         tma::tma_load_3d(tma::smem_u32(sF), &tf, 32 * blockIdx.x, j0, kb, bar);
+    }
+    pdl_wait();
+    if (tid == 0) {
+        tma::mbar_expect_tx(bar, (uint32_t)sizeof(sD));
+        tma::tma_load_3d(tma::smem_u32(sD), &td, 32 * blockIdx.x, j0 - 1, kb - 1, bar);
+    }
+    if (red.sc->done) {            // uniform over the grid: let the copies land (bounded), then leave
+        if (tid == 0) tma::mbar_wait_bounded(bar, 0u);
+        __syncthreads();
+        return;
+    }
+    bool ok = true;
+    if (tid == 0) {
         ok = tma::mbar_wait_bounded(bar, 0u);
         if (!ok) {
             atomicExch(&red.sc->timeout, 1);

@@ -49,11 +49,11 @@ k_sor_tma(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtens
 }
 
 // The same block sweep with the column-walk update (sor_col_block): fewer
-// instructions per cell for the same iterate.  pre = 1 when the kernel
-// before it in the stream is a sweep of the same batch: sweeps write only d,
-// so the copies of r, the flags and the coefficient rows are issued before
-// the dependency wait (they overlap the tail of the previous sweep), and
-// only the copy of d after it.  Each CTA lets the next kernel launch once
+// instructions per cell for the same iterate.  The flags and coefficient
+// rows (written by no kernel of a solve) are copied before the dependency
+// wait.  pre = 1 when the kernel before it in the stream is a sweep of the
+// same batch: sweeps write only d, so r is copied before the wait as well,
+// and only d after it.  Each CTA lets the next kernel launch once
 // its copies are issued (a dependent kernel waits for this grid to complete
 // before it touches anything this sweep writes).
 template <int BY, int BZ, int NT>
@@ -66,20 +66,25 @@ k_sor_col(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtens
     const uint32_t bar = smem_u32(sm + CT::STAGE);
     const bool lead = threadIdx.x == 0;
     const int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
+    using TT = TmaTile<BY, BZ>;
     if (lead) {
         mbar_init(bar, 1);
         mbar_fence_init();
         if (pre) {
             col_expect<BY, BZ>(bar, false);
             col_issue_static<BY, BZ>(sm, bar, &tr, &tf, g.ctab, bx, by, bz);
+        } else {
+            // the first sweep of a batch: only the constant tiles before the wait
+            mbar_expect_tx_only(bar, TT::BYTES_F + CT::BYTES_TAB);
+            col_issue_const<BY, BZ>(sm, bar, &tf, g.ctab, bx, by, bz);
         }
     }
     pdl_wait();
     const bool zero_start = !pre && (zero_arg == 1 || (zero_arg == 2 && sc->zflag));
     if (lead) {
         if (!pre) {
-            col_expect<BY, BZ>(bar, zero_start);
-            col_issue_static<BY, BZ>(sm, bar, &tr, &tf, g.ctab, bx, by, bz);
+            mbar_expect_tx(bar, TT::BYTES_R + (zero_start ? 0u : TT::BYTES_D));
+            col_issue_r<BY, BZ>(sm, bar, &tr, bx, by, bz);
         }
         if (!zero_start) col_issue_d<BY, BZ>(sm, bar, &td, bx, by, bz);
     }

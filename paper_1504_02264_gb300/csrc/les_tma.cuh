@@ -374,15 +374,33 @@ __device__ __forceinline__ void col_expect(uint32_t bar, bool zero_start) {
     using TT = TmaTile<BY, BZ>;
     mbar_expect_tx(bar, TT::BYTES_R + TT::BYTES_F + ColTile<BY, BZ>::BYTES_TAB + (zero_start ? 0u : TT::BYTES_D));
 }
+// the constant part (flags and coefficient rows: no kernel of a solve writes
+// them) and r (written only between batches of sweeps)
 template <int BY, int BZ>
-__device__ __forceinline__ void col_issue_static(unsigned char* st, uint32_t bar, const CUtensorMap* tr,
-                                                 const CUtensorMap* tf, const float* ctab, int bx, int by, int bz) {
+__device__ __forceinline__ void col_issue_const(unsigned char* st, uint32_t bar, const CUtensorMap* tf,
+                                                const float* ctab, int bx, int by, int bz) {
     using TT = TmaTile<BY, BZ>;
-    const int xd = bx * TT::BX, xf = xd & ~15, j0 = 1 + by * BY, k0 = 1 + bz * BZ;
-    tma_load_3d(smem_u32(st + TT::OFF_R), tr, xd, j0 - 1, k0 - 1, bar);
+    const int xf = (bx * TT::BX) & ~15, j0 = 1 + by * BY, k0 = 1 + bz * BZ;
     tma_load_3d(smem_u32(st + TT::OFF_F), tf, xf, j0 - 1, k0 - 1, bar);
     bulk_load(smem_u32(st + ColTile<BY, BZ>::OFF_TAB), ctab + (size_t)(k0 - 1) * kColRow, ColTile<BY, BZ>::BYTES_TAB,
               bar);
+}
+template <int BY, int BZ>
+__device__ __forceinline__ void col_issue_r(unsigned char* st, uint32_t bar, const CUtensorMap* tr, int bx, int by,
+                                            int bz) {
+    using TT = TmaTile<BY, BZ>;
+    tma_load_3d(smem_u32(st + TT::OFF_R), tr, bx * TT::BX, 1 + by * BY - 1, 1 + bz * BZ - 1, bar);
+}
+template <int BY, int BZ>
+__device__ __forceinline__ void col_issue_static(unsigned char* st, uint32_t bar, const CUtensorMap* tr,
+                                                 const CUtensorMap* tf, const float* ctab, int bx, int by, int bz) {
+    col_issue_r<BY, BZ>(st, bar, tr, bx, by, bz);
+    col_issue_const<BY, BZ>(st, bar, tf, ctab, bx, by, bz);
+}
+// expected bytes without an arrival (the arrival comes with a later
+// arrive.expect_tx of the remaining bytes)
+__device__ __forceinline__ void mbar_expect_tx_only(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 template <int BY, int BZ>
 __device__ __forceinline__ void col_issue_d(unsigned char* st, uint32_t bar, const CUtensorMap* td, int bx, int by,
