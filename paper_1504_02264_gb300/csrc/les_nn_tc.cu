@@ -262,13 +262,15 @@ __global__ void __launch_bounds__(NTH) k_conv3_tc(ConvArgs A, const int* gate, i
 
     bool ok = true;
     int issued = cb - 1;                           // the last chunk whose MMAs were issued
-    // The pooled and upsampled layers run only inside an inference, right
-    // after the previous convolution, which does not write weights: their
-    // first chunk's weights are copied before the wait for that kernel (its
-    // tail overlaps the copies).  Every layer lets the next kernel launch once
-    // the wait has returned (every kernel that follows a convolution waits for
-    // it before it reads anything the convolution writes).
-    constexpr bool kWeightsEarly = IN == IN_POOL || IN == IN_UP;
+    // The packed, pooled and upsampled layers run only inside an inference of
+    // the solve, right after the pooling kernel or the previous convolution,
+    // neither of which writes weights (and every kernel before those has
+    // completed by the time this one can launch): their first chunk's weights
+    // are copied before the wait for that kernel (its tail overlaps the
+    // copies).  Every layer lets the next kernel launch once the wait has
+    // returned (every kernel that follows a convolution waits for it before it
+    // reads anything the convolution writes).
+    constexpr bool kWeightsEarly = IN == IN_PACK || IN == IN_POOL || IN == IN_UP;
     if constexpr (kWeightsEarly) stage_w(cb, S.st[0]);
     pdl_wait();
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
