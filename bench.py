@@ -46,7 +46,8 @@ SOR_BYTES_PER_CELL = 13.0       # per sweep: read p, rhs (4+4), flags (1), write
 # DRAM bytes (read + write) per launch of the TMA sweep kernels on this
 # workload, by tile, from one ncu capture each (cold L2); reported only for the
 # tile the autotuner picked
-SOR_DRAM_BYTES = {17: 20.180736e6 + 3.072e3, 29: 20.183552e6 + 512.0, 30: 20.183296e6, 34: 20.184576e6 + 256.0}
+SOR_DRAM_BYTES = {17: 20.180736e6 + 3.072e3, 29: 20.188160e6, 30: 20.184832e6, 31: 20.187904e6, 32: 20.184320e6,
+                  33: 20.184832e6, 34: 20.185088e6}
 # the sweep timed alone on the HBM-bound grid: the column-walk TMA block
 SOR_HBM_TILE = 29
 L2_FLUSH_BYTES = 256 << 20
