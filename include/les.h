@@ -429,10 +429,17 @@ int les_set_net_schedule(les_handle h, int32_t every_sweeps);
  * seven convolutions, head) as one cooperative persistent launch with a
  * bounded grid barrier between layers, when the device supports cooperative
  * launches; the same correction up to the summation order of the RMS.
+ * With 0 or 2 on an FP32 grid with no periodic axis, at network stride 4 or
+ * 8 and the in-place schedule, the estimate after each batch of sweeps also
+ * pools the residual and the unknown mask over the stride cubes and forms
+ * their RMS, and the correction skips its pooling kernel; or-ing
+ * LES_NET_KERNELS_OWN_POOL (4) into the mode keeps the pooling kernel (the
+ * same pooled input up to the FP32 summation order of each cube).
  * Any other value: LES_EINVAL. */
 #define LES_NET_KERNELS_FOLDED 0
 #define LES_NET_KERNELS_PERSISTENT 1
 #define LES_NET_KERNELS_LAYERS 2
+#define LES_NET_KERNELS_OWN_POOL 4
 int les_set_net_kernels(les_handle h, int32_t mode);
 /* les_set_net_async: with a schedule (every_sweeps > 0) in the CUDA-graph
  * loop, 1 overlaps each network prediction with the next batch of sweeps:

@@ -147,6 +147,8 @@ struct les_s {
     int nseries = 0, series_cap = 0;
     long long net_gen = -1;               // network workspace generation the chunk graphs were captured with
     int net_kernels = LES_NET_KERNELS_FOLDED;   // how a correction's kernels are laid out (les_set_net_kernels)
+    bool net_own_pool = false;                  // the network pools on its own (LES_NET_KERNELS_OWN_POOL)
+    long long net_chunk_launches = 0;           // network kernels of one correction in the chunk graphs
     bool net_persistent = false;          // coarse network as one cooperative launch
     bool net_async = false;               // graph loop: each prediction overlaps the next batch of sweeps
     cudaStream_t s2 = nullptr;            // its stream, and the events that order it with the loop
@@ -310,10 +312,12 @@ double elapsed(les_s* h, int a, int b) {
 
 // the estimate after a batch of sweeps: from TMA tiles on FP32 grids with no
 // periodic axis, else the plain kernel (both give the same result)
+// (pool, nullable: the TMA estimate also forms the network's pooled input there)
 template <typename T>
-int launch_estimate(les_s* h, const Geo<T>& g, T* rout, CondArgs ca, cudaStream_t st) {
+int launch_estimate(les_s* h, const Geo<T>& g, T* rout, CondArgs ca, cudaStream_t st, const EstPool* pool = nullptr) {
     if constexpr (std::is_same<T, float>::value) {
-        if (h->est_tma) return launch_sor_est_tma(g, h->est_maps, h->dcur, rout, reducer(h), ca, st);
+        if (h->est_tma)
+            return launch_sor_est_tma(g, h->est_maps, h->dcur, rout, reducer(h), ca, st, pool ? *pool : EstPool{});
     }
     return launch_sor_est<T>(g, (const T*)h->dl[h->dcur], (const T*)h->rr, rout, reducer(h), ca, st);
 }
@@ -363,7 +367,7 @@ CondArgs cond_args(const les_s* h, int mode, int n, int gate) {
 // residual may already pass the stop test).
 // the network's prediction q of the correction for residual r: the coarse
 // network as one cooperative launch when the device can, else per layer
-int predict(les_s* h, const float* r, cudaStream_t st, const int* gate) {
+int predict(les_s* h, const float* r, cudaStream_t st, const int* gate, bool pooled = false) {
     if (h->net_persistent) {
         int rc = net_predict_persistent(h->net, h->d, r, h->flags, h->pred, h->sc, gate, st);
         if (rc == LES_OK) {
@@ -373,7 +377,7 @@ int predict(les_s* h, const float* r, cudaStream_t st, const int* gate) {
         if (rc != LES_EINVAL) return fail(h, rc, "persistent network prediction failed");
     }
     int rc = net_predict(h->net, h->d, r, h->flags, h->pred, st, gate, nullptr,
-                         h->net_kernels != LES_NET_KERNELS_LAYERS);
+                         h->net_kernels != LES_NET_KERNELS_LAYERS, pooled);
     if (rc) return fail(h, rc, "network prediction failed");
     h->launches += net_launches(h->net);
     return LES_OK;
@@ -384,17 +388,19 @@ int predict(les_s* h, const float* r, cudaStream_t st, const int* gate) {
 // (default): the prolongation runs inside the line search, which leaves the
 // fine correction in h->pred for the step; otherwise (the persistent network,
 // or the stand-alone kernels) the prolongation has its own kernel first.
+// (pooled: the estimate before this call left the network's pooled input)
 template <typename T>
-int net_step(les_s* h, const Geo<T>& g, const T* r, double* ph, T* dl, cudaStream_t st, const int* gate) {
+int net_step(les_s* h, const Geo<T>& g, const T* r, double* ph, T* dl, cudaStream_t st, const int* gate,
+             bool pooled = false) {
     if (h->net_kernels == LES_NET_KERNELS_FOLDED) {
-        int rc = net_predict_coarse(h->net, h->d, (const float*)r, h->flags, st, gate);
+        int rc = net_predict_coarse(h->net, h->d, (const float*)r, h->flags, st, gate, pooled);
         if (rc) return fail(h, rc, "network prediction failed");
         h->launches += net_launches(h->net);
         h->launches += launch_warm_coarse<T>(g, r, net_coarse_out(h->net), net_stride(h->net), h->pred, ph, dl,
                                              h->warm_scal + 1, reducer(h), st);
         return LES_OK;
     }
-    int rc = predict(h, (const float*)r, st, gate);
+    int rc = predict(h, (const float*)r, st, gate, pooled);
     if (rc) return rc;
     h->launches += launch_warm<T>(g, r, h->pred, ph, dl, h->warm_scal + 1, reducer(h), st);
     return LES_OK;
@@ -421,8 +427,9 @@ int net_correct(les_s* h, const Geo<T>& g, cudaStream_t st) {
 // (no FP64 pass: the next refinement folds it into p).  `gated`: captured in a
 // chunk graph, every kernel returns at once when the solve is done.
 template <typename T>
-int net_correct_loop(les_s* h, const Geo<T>& g, cudaStream_t st, bool gated) {
-    int rc = net_step<T>(h, g, (const T*)h->rcur, nullptr, (T*)h->dl[h->dcur], st, gated ? &h->sc->done : nullptr);
+int net_correct_loop(les_s* h, const Geo<T>& g, cudaStream_t st, bool gated, bool pooled = false) {
+    int rc = net_step<T>(h, g, (const T*)h->rcur, nullptr, (T*)h->dl[h->dcur], st, gated ? &h->sc->done : nullptr,
+                         pooled);
     if (rc) return rc;
     CK(cudaGetLastError());
     return LES_OK;
@@ -473,6 +480,8 @@ void launch_refine(les_s* h, const Geo<T>& g, const CondArgs& ca, cudaStream_t s
     h->launches += launch_residual64<T>(g, h->ph[h->cur], (const T*)h->rhs, (T*)h->rr, h->vfluid, reducer(h), ca, st);
 }
 
+bool est_pools(les_s* h, EstPool* pool);
+
 // Host-driven loop.  After each batch of check_every sweeps the cheap
 // estimate is read back; when it asks for it, the FP64 refinement runs and
 // its true relative residual decides convergence.
@@ -503,6 +512,8 @@ int sor_solve(les_s* h) {
     bool fresh = true, conv = false;
     bool recorded = !h->record || h->rec_taken;
     const bool net_loop = std::is_same<T, float>::value && h->warm == LES_WARM_NET && h->net && h->net_every > 0;
+    EstPool pool;
+    const bool pooled = net_loop && est_pools(h, &pool);
     if (!G.fixed_sweeps && h->warm != LES_WARM_PREV) {
         // the start of the solve moved p: its residual may already pass the test
         int rc = fetch_scalars(h);
@@ -522,7 +533,7 @@ int sor_solve(les_s* h) {
         bool need = true;
         if (!G.fixed_sweeps) {
             h->launches += launch_estimate<T>(h, g, net_loop ? (T*)h->rcur : nullptr, cond_args(h, RES_LOOP, n, 0),
-                                              h->stream);
+                                              h->stream, pooled ? &pool : nullptr);
             CK(cudaGetLastError());
             int rc = fetch_scalars(h);
             if (rc) return rc;
@@ -559,7 +570,7 @@ int sor_solve(les_s* h) {
             if (net_due) {
                 last_net = sweeps;
                 rec(h, 2);
-                int rc = net_correct_loop<T>(h, g, h->stream, false);
+                int rc = net_correct_loop<T>(h, g, h->stream, false, pooled);
                 if (rc) return rc;
                 rec(h, 3);
                 if (h->timing) {
@@ -710,6 +721,16 @@ bool net_in_loop(const les_s* h) {
     return h->prec == LES_FP32 && h->warm == LES_WARM_NET && h->net && h->net_every > 0;
 }
 
+// The estimate before each network correction inside the solve forms the
+// network's pooled input (the TMA estimate, the in-place schedule, strides 4
+// and 8): the correction then skips its pooling kernel and its re-read of
+// the residual.  The overlapped schedule keeps the pooling on its own
+// stream, since a prediction still running there reads the pooled input.
+bool est_pools(les_s* h, EstPool* pool) {
+    if (!net_in_loop(h) || !h->est_tma || h->net_async || h->net_own_pool || h->net_persistent) return false;
+    return net_pool_target(h->net, h->d, pool);
+}
+
 constexpr int kChunkBatches = 10;
 // with the network correction a batch is a whole cycle (sweeps, estimate,
 // network, step): shorter chunks waste fewer done-gated launches after the
@@ -753,6 +774,8 @@ int build_graph(les_s* h, int cur) {
     const long long l0 = h->launches;
     h->cur = cur;
     h->dcur = 0;
+    EstPool pool;
+    bool pooled = false;
     if (net_in_loop(h)) {
         // allocate the network's workspace before the capture
         int rp = net_prepare(h->net, h->d, &h->net_gen);
@@ -761,6 +784,7 @@ int build_graph(les_s* h, int cur) {
             h->dcur = save_dcur;
             return fail(h, rp, "network workspace");
         }
+        pooled = est_pools(h, &pool);
     }
     int rc = capture_begin<T>(h, cs);
     if (rc) return rc;
@@ -796,6 +820,7 @@ int build_graph(les_s* h, int cur) {
                     fail(h, rc, "network prediction failed");
                     break;
                 }
+                h->net_chunk_launches = net_launches(h->net);
                 launch_set_flag(&h->sc->qpend, 1, &h->sc->done, h->s2);
                 CK(cudaEventRecord(h->ev_q, h->s2));
             }
@@ -807,10 +832,12 @@ int build_graph(les_s* h, int cur) {
         if constexpr (std::is_same<T, float>::value) {
             for (int b = 0; b < chunk_batches(h); ++b) {
                 run_sweeps<T>(h, g, h->net_every, 2, nl, cs);     // net_every even: d returns to dl[0]
-                launch_estimate<T>(h, g, (T*)h->rcur, cond_args(h, RES_LOOP, h->net_every, 1), cs);
+                launch_estimate<T>(h, g, (T*)h->rcur, cond_args(h, RES_LOOP, h->net_every, 1), cs,
+                                   pooled ? &pool : nullptr);
                 launch_refine<T>(h, g, cond_args(h, RES_LOOP, h->net_every, 1), cs);
-                rc = net_correct_loop<T>(h, g, cs, true);
+                rc = net_correct_loop<T>(h, g, cs, true, pooled);
                 if (rc) break;
+                h->net_chunk_launches = net_launches(h->net);
             }
         }
     } else {
@@ -861,7 +888,7 @@ int step_graph(les_s* h, int nsteps, les_stats_t* stats) {
                 int rs = solve_start<T>(h, g, h->stream);
                 if (rs) return rs;
             }
-            const long long per_batch = net_in_loop(h) ? h->net_every + 3 + net_launches(h->net) + 2 +
+            const long long per_batch = net_in_loop(h) ? h->net_every + 3 + h->net_chunk_launches + 2 +
                                                              (h->net_async && !h->record ? 1 : 0)
                                                        : G.check_every + 3;
             for (int c = 0; c < max_chunks; ++c) {
@@ -1648,10 +1675,12 @@ int les_set_net_async(les_handle h, int32_t enable) {
 
 int les_set_net_kernels(les_handle h, int32_t mode) {
     if (!h) return fail(nullptr, LES_EINVAL, "handle is NULL");
-    if (mode < LES_NET_KERNELS_FOLDED || mode > LES_NET_KERNELS_LAYERS)
-        return fail(h, LES_EINVAL, "network kernel layout must be 0, 1 or 2");
-    h->net_kernels = mode;
-    h->net_persistent = mode == LES_NET_KERNELS_PERSISTENT;
+    const int layout = mode & ~LES_NET_KERNELS_OWN_POOL;
+    if (layout < LES_NET_KERNELS_FOLDED || layout > LES_NET_KERNELS_LAYERS)
+        return fail(h, LES_EINVAL, "network kernel layout must be 0, 1 or 2, optionally with LES_NET_KERNELS_OWN_POOL");
+    h->net_kernels = layout;
+    h->net_own_pool = (mode & LES_NET_KERNELS_OWN_POOL) != 0;
+    h->net_persistent = layout == LES_NET_KERNELS_PERSISTENT;
     h->graph_ok[0] = h->graph_ok[1] = false;
     return LES_OK;
 }

@@ -316,8 +316,20 @@ int sor_tma_ens_resident();     // resident CTAs of the batched TMA sweep on thi
 // cells, arithmetic and sums of launch_sor_est, so the same result): maps
 // from tma_encode_est (d[0], d[1], r, flags); dcur selects d
 bool tma_encode_est(const Dom& d, float* dl0, float* dl1, float* rr, const uint8_t* flags, CUtensorMap* out4);
+// The network's pooled input, formed by that estimate when it is given one
+// (the network correction that follows the estimate then skips its pooling
+// kernel): the residual r_out and the unknown mask averaged over stride-s
+// cubes (s = 4 or 8, which tile the estimate's 32 x 8 x 8 blocks), into rc
+// and mask (coarse volume xc * yc * zc, x fastest), and scal[0] = the
+// mask-weighted RMS of rc, scal[1] = the sum of the mask, both FP64.
+struct EstPool {
+    float* rc = nullptr;       // null: the estimate does not pool
+    float* mask = nullptr;
+    double* scal = nullptr;
+    int s = 0, xc = 0, yc = 0, zc = 0;
+};
 int launch_sor_est_tma(const Geo<float>& g, const CUtensorMap* maps4, int dcur, float* rout, const Reduce& red,
-                       CondArgs ca, cudaStream_t s);
+                       CondArgs ca, cudaStream_t s, const EstPool& pool = EstPool{});
 // the plain-SOR solve of an ensemble as one persistent cooperative launch
 // (les_kernels.cu); bar: 2 zeroed unsigned of grid-barrier state, err: a
 // zeroed device flag set when a bounded wait gave up; returns the launches
@@ -398,12 +410,19 @@ namespace les {
 // convolution and the head inside the last; false keeps their own kernels,
 // which compute the same values)
 int net_predict(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, float* out_dense,
-                cudaStream_t s, const int* gate = nullptr, cudaEvent_t after_pool = nullptr, bool fold = true);
+                cudaStream_t s, const int* gate = nullptr, cudaEvent_t after_pool = nullptr, bool fold = true,
+                bool pooled = false);
 // the same without the prolongation: the coarse output is left in
 // net_coarse_out(n) (stride net_stride(n)) for a line search that prolongs it
 // on the fly (launch_warm_coarse)
 int net_predict_coarse(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, cudaStream_t s,
-                       const int* gate = nullptr);
+                       const int* gate = nullptr, bool pooled = false);
+// where the estimate before a correction may leave the network's pooled input
+// (EstPool above) for solver grid d: false when the network pools on its own
+// (a stride other than 4 or 8, or a coarse grid beyond the pooling kernel's
+// size); sizes the workspace first.  `pooled` in net_predict /
+// net_predict_coarse then skips the pooling kernel.
+bool net_pool_target(les_net_s* n, const Dom& d, EstPool* out);
 const float* net_coarse_out(const les_net_s* n);
 int net_stride(const les_net_s* n);
 int net_launches(const les_net_s* n);

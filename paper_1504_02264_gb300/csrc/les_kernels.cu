@@ -1199,11 +1199,21 @@ int launch_sor_est(const Geo<T>& g, const T* dl, const T* r, T* rout, const Redu
 // 16-byte column at or below that of i0 - 4).  Each thread takes the same
 // cells in the same order with the same arithmetic, and the block and grid
 // sums are those of k_sor_est (same launch shape), so the result is the same.
+//
+// With S > 0 (S = 4 or 8) the CTA also forms the network's pooled input for
+// its cells, which the stride-S cubes tile exactly: the residual and the
+// unknown mask summed over each cube with the pooling kernel's sums in its
+// order (k_pool_rms: the same pooled values), scaled by 1/S^3, and each
+// cube's m r^2 and m added to the grid sums next to the residual's, so that
+// the last block also leaves the mask-weighted RMS and the mask sum (FP64,
+// summed in this kernel's fixed block order).
+template <int S>
 __global__ void __launch_bounds__(256, 4)
     k_sor_est_tma(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtensorMap tr,
                   const __grid_constant__ CUtensorMap tf, Geo<float> g, float* __restrict__ rout, Reduce red,
-                  CondArgs ca) {
+                  CondArgs ca, EstPool pool) {
     static_assert(kEstChunk == 8, "tile boxes of 8 planes");
+    static_assert(S == 0 || S == 4 || S == 8, "pooling strides that tile the 32 x 8 x 8 block");
     __shared__ __align__(128) float sD[kEstChunk + 2][10][40];
     __shared__ __align__(128) float sR[kEstChunk][8][32];
     __shared__ __align__(128) uint8_t sF[kEstChunk][8][48];
@@ -1241,6 +1251,13 @@ __global__ void __launch_bounds__(256, 4)
     }
     ok = __syncthreads_and(ok);
     float acc = 0.f;
+    float rv[kEstChunk];                           // the cell's residual if it is an unknown, else 0
+    bool uk[kEstChunk];                            // the cell is an unknown of the grid
+#pragma unroll
+    for (int m = 0; m < kEstChunk; ++m) {
+        rv[m] = 0.f;
+        uk[m] = false;
+    }
     const int i = i0 + tx, j = j0 + ty;
     if (ok && i <= d.nx && j <= d.ny) {
         const int ke = min(kb + kEstChunk, d.nz + 1);
@@ -1263,18 +1280,88 @@ __global__ void __launch_bounds__(256, 4)
             const float res = sR[m][ty][tx] - s;
             if (rout) rout[c0 + m * pl] = res;
             acc += res * res;
+            rv[m] = res;
+            uk[m] = true;
         }
     }
-    double x[1] = {(double)acc};
-    if (grid_sum<1>(x, red))
-        if (tid == 0) est_finish(x[0], red, ca);
+    double x[S > 0 ? 3 : 1];
+    x[0] = (double)acc;
+    if constexpr (S > 0) {
+        // the residual and the mask of the block's cells over r's and the
+        // flags' tiles (each thread overwrites only the entries it read);
+        // then the pooling kernel's sums in its order: per cube, for each of
+        // SZ z-offsets p and S rows q, the cells of planes p, p + SZ, ... of
+        // row q along x (into the d tile, read by no one any more), then
+        // those partials with p outer and q inner
+        constexpr int SZ = S < 4 ? S : 4;
+        constexpr int NXC = 32 / S, NYC = 8 / S, NZC = kEstChunk / S, NCUBE = NXC * NYC * NZC;
+        constexpr int NPART = NCUBE * SZ * S;
+        static_assert(2 * NPART <= (int)(sizeof(sD) / sizeof(float)) && NCUBE <= 256, "pooling scratch");
+#pragma unroll
+        for (int m = 0; m < kEstChunk; ++m) {
+            sR[m][ty][tx] = rv[m];
+            sF[m][ty][tx + 4] = uk[m] ? 1 : 0;
+        }
+        __syncthreads();
+        float* partr = &sD[0][0][0];
+        float* partm = partr + NPART;
+        for (int q = tid; q < NPART; q += 256) {
+            const int row = q % S, pz = (q / S) % SZ, cube = q / (S * SZ);
+            const int cx = cube % NXC, fy = (cube / NXC) % NYC * S + row, fz0 = cube / (NXC * NYC) * S + pz;
+            float ar = 0.f, am = 0.f;
+#pragma unroll
+            for (int zz = 0; zz < S; zz += SZ)
+#pragma unroll
+                for (int e = 0; e < S; ++e) {
+                    ar += sR[fz0 + zz][fy][cx * S + e];
+                    am += (float)sF[fz0 + zz][fy][cx * S + e + 4];
+                }
+            partr[q] = ar;
+            partm[q] = am;
+        }
+        __syncthreads();
+        x[1] = 0.0;
+        x[2] = 0.0;
+        if (tid < NCUBE) {
+            const int cx = tid % NXC, cy = (tid / NXC) % NYC, cz = tid / (NXC * NYC);
+            float tr = 0.f, tm = 0.f;
+#pragma unroll
+            for (int q = 0; q < SZ * S; ++q) {
+                tr += partr[tid * SZ * S + q];
+                tm += partm[tid * SZ * S + q];
+            }
+            const int gx = blockIdx.x * NXC + cx, gy = blockIdx.y * NYC + cy, gz = blockIdx.z * NZC + cz;
+            if (gx < pool.xc && gy < pool.yc && gz < pool.zc) {
+                const float inv = 1.f / (float)(S * S * S);
+                const float vr = tr * inv, vm = tm * inv;
+                const long long v = ((long long)gz * pool.yc + gy) * pool.xc + gx;
+                pool.rc[v] = vr;
+                pool.mask[v] = vm;
+                x[1] = (double)vm * (double)vr * (double)vr;
+                x[2] = (double)vm;
+            }
+        }
+    }
+    if (grid_sum<(S > 0 ? 3 : 1)>(x, red))
+        if (tid == 0) {
+            est_finish(x[0], red, ca);
+            if constexpr (S > 0) {
+                pool.scal[0] = x[2] > 0.0 ? sqrt(x[1] / x[2]) : 0.0;
+                pool.scal[1] = x[2];
+            }
+        }
 }
 
 int launch_sor_est_tma(const Geo<float>& g, const CUtensorMap* maps4, int dcur, float* rout, const Reduce& red,
-                       CondArgs ca, cudaStream_t s) {
+                       CondArgs ca, cudaStream_t s, const EstPool& pool) {
     const Dom& d = g.d;
     dim3 grid((d.nx + 31) / 32, (d.ny + 7) / 8, (d.nz + kEstChunk - 1) / kEstChunk);
-    launch_pdl(k_sor_est_tma, grid, dim3(32, 8), 0, s, maps4[dcur], maps4[2], maps4[3], g, rout, red, ca);
+    if (pool.rc && pool.s == 8)
+        launch_pdl(k_sor_est_tma<8>, grid, dim3(32, 8), 0, s, maps4[dcur], maps4[2], maps4[3], g, rout, red, ca, pool);
+    else if (pool.rc && pool.s == 4)
+        launch_pdl(k_sor_est_tma<4>, grid, dim3(32, 8), 0, s, maps4[dcur], maps4[2], maps4[3], g, rout, red, ca, pool);
+    else
+        launch_pdl(k_sor_est_tma<0>, grid, dim3(32, 8), 0, s, maps4[dcur], maps4[2], maps4[3], g, rout, red, ca, pool);
     return 1;
 }
 

@@ -511,7 +511,7 @@ long long net_generation(const les_net_s* n) { return n->ws_gen; }
 // pooling (+ RMS and packing), the network and, with out_dense set, the
 // prolongation onto the fine unknowns
 int predict_impl(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, float* out_dense,
-                 cudaStream_t s, const int* gate, cudaEvent_t after_pool, bool fold) {
+                 cudaStream_t s, const int* gate, cudaEvent_t after_pool, bool fold, bool pooled) {
     nn::set_conv_engine(n->engine, n->tc_timeout);
     const Level Lf{d.nx, d.ny, d.nz};
     const Level L0 = coarse(n, Lf);
@@ -523,10 +523,15 @@ int predict_impl(les_net_s* n, const Dom& d, const float* r_padded, const uint8_
     if (!rc) {
         if (L0.v() <= nn::kPoolRmsMax) {
             // pooling and RMS in one launch, the pooled mask straight into the
-            // head's mask, then the packing
-            nn::pool_rms(r_padded, flags, d, n->stride, n->rc, n->mask, n->pp_part, n->pp_count, n->dscal, s, gate);
+            // head's mask, then the packing (`pooled`: the estimate before
+            // this call left them, see net_pool_target)
+            n->last_launches = 0;
+            if (!pooled) {
+                nn::pool_rms(r_padded, flags, d, n->stride, n->rc, n->mask, n->pp_part, n->pp_count, n->dscal, s,
+                             gate);
+                n->last_launches = 1;
+            }
             if (after_pool) cudaEventRecord(after_pool, s);      // the residual has been read
-            n->last_launches = 1;
             if (!folded) {
                 launch_pdl(k_pack_dense, dim3((unsigned)((L0.v() + 255) / 256)), dim3(256), 0, s,
                            (const float*)n->rc, (const float*)n->mask, (const double*)n->dscal, n->xin,
@@ -559,12 +564,27 @@ int predict_impl(les_net_s* n, const Dom& d, const float* r_padded, const uint8_
 }
 
 int net_predict(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, float* out_dense,
-                cudaStream_t s, const int* gate, cudaEvent_t after_pool, bool fold) {
-    return predict_impl(n, d, r_padded, flags, out_dense, s, gate, after_pool, fold);
+                cudaStream_t s, const int* gate, cudaEvent_t after_pool, bool fold, bool pooled) {
+    return predict_impl(n, d, r_padded, flags, out_dense, s, gate, after_pool, fold, pooled);
 }
 int net_predict_coarse(les_net_s* n, const Dom& d, const float* r_padded, const uint8_t* flags, cudaStream_t s,
-                       const int* gate) {
-    return predict_impl(n, d, r_padded, flags, nullptr, s, gate, nullptr, true);
+                       const int* gate, bool pooled) {
+    return predict_impl(n, d, r_padded, flags, nullptr, s, gate, nullptr, true, pooled);
+}
+// the buffers pool_rms fills (pooled residual, pooled mask into the head's
+// mask, RMS and mask sum), for an estimate that pools in its place
+bool net_pool_target(les_net_s* n, const Dom& d, EstPool* out) {
+    const Level L0 = coarse(n, Level{d.nx, d.ny, d.nz});
+    if ((n->stride != 4 && n->stride != 8) || L0.v() > nn::kPoolRmsMax) return false;
+    if (ensure_ws(n, L0) != LES_OK) return false;
+    out->rc = n->rc;
+    out->mask = n->mask;
+    out->scal = n->dscal;
+    out->s = n->stride;
+    out->xc = L0.X;
+    out->yc = L0.Y;
+    out->zc = L0.Z;
+    return true;
 }
 const float* net_coarse_out(const les_net_s* n) { return n->y; }
 int net_stride(const les_net_s* n) { return n->stride; }

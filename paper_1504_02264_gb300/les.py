@@ -27,6 +27,7 @@ LES_SOR_REDBLACK, LES_SOR_TWINNED = 0, 1
 LES_SOR_NTILES = 35                 # sweep tile indices 0 .. LES_SOR_NTILES - 1 (les_set_sor_config)
 LES_NET_MMA_SYNC, LES_NET_TCGEN05, LES_NET_TCGEN05_GMEM_SPLIT = 0, 1, 2
 LES_NET_KERNELS_FOLDED, LES_NET_KERNELS_PERSISTENT, LES_NET_KERNELS_LAYERS = 0, 1, 2
+LES_NET_KERNELS_OWN_POOL = 4     # or-ed into a layout: the network's own pooling kernel
 
 
 class les_grid_t(ctypes.Structure):

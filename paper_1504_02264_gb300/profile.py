@@ -149,6 +149,8 @@ def main():
                     help="time every SOR sweep configuration on the workload after the warm-up steps")
     ap.add_argument("--net", default=None, help="trained warm-start network (.npz: params, stride)")
     ap.add_argument("--net-every", type=int, default=0, help="network correction every n sweeps")
+    ap.add_argument("--net-kernels", type=int, default=0,
+                    help="les_set_net_kernels layout (0 folded, 1 persistent, 2 layers; + 4: the network's own pooling)")
     ap.add_argument("--sor-compare", default=None,
                     help="comma-separated sweep counts: red-black SOR vs the twinned double buffer "
                          "(les_sor_compare) from the previous step's pressure and the next step's rhs")
@@ -214,6 +216,7 @@ def main():
     if net is not None:
         d.set_warmstart(net)
         d.set_net_schedule(a.net_every)
+        d.set_net_kernels(a.net_kernels)
         d.step(1)
     if a.range:
         les.les_profiler_range(1)

@@ -374,6 +374,35 @@ def test_folded_kernels_match_standalone(net, stride, engine, periodic):
 
 
 @pytest.mark.parametrize("stride", [8, 4])
+def test_estimate_pooling_matches_pooling_kernel(net, stride):
+    """On an FP32 grid with no periodic axis the estimate before each network
+    correction also pools the residual and the mask (in the pooling kernel's
+    order) and forms the RMS, and the correction skips its pooling kernel;
+    LES_NET_KERNELS_OWN_POOL keeps that kernel.  The pooled input is the same,
+    and the RMS (FP64, summed in another block order) gives the same FP32
+    scale here: identical sweep counts and bit-identical fields after
+    learned-mode steps in the graph loop, with fewer launches."""
+    net.stride = stride
+    sc = city(tol=1e-6, max_sweeps=40000, check_every=10)
+    out = []
+    for mode in (les.LES_NET_KERNELS_FOLDED, les.LES_NET_KERNELS_FOLDED | les.LES_NET_KERNELS_OWN_POOL):
+        d = les.Domain(sc)
+        try:
+            d.set_warmstart(net)
+            d.set_net_schedule(10)
+            d.set_net_kernels(mode)
+            sts = [d.step() for _ in range(2)]
+            assert all(st["rc"] == 0 and st["graph"] == 1 for st in sts), sts
+            out.append(([st["sweeps"] for st in sts], sts[-1]["launches"], d.fields()))
+        finally:
+            d.close()
+    assert out[0][0] == out[1][0], (out[0][0], out[1][0])
+    assert out[0][1] < out[1][1], (out[0][1], out[1][1])
+    for a, b in zip(out[0][2], out[1][2]):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("stride", [8, 4])
 def test_cluster_split_matches_global_split(net, stride):
     """The small layers split their input channels over CTAs; the tcgen05
     engine adds the partial sums over distributed shared memory in a
