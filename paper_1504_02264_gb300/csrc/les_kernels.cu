@@ -1208,7 +1208,7 @@ int launch_sor_est(const Geo<T>& g, const T* dl, const T* r, T* rout, const Redu
 // the last block also leaves the mask-weighted RMS and the mask sum (FP64,
 // summed in this kernel's fixed block order).
 template <int S>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, S > 0 ? 6 : 4)
     k_sor_est_tma(const __grid_constant__ CUtensorMap td, const __grid_constant__ CUtensorMap tr,
                   const __grid_constant__ CUtensorMap tf, Geo<float> g, float* __restrict__ rout, Reduce red,
                   CondArgs ca, EstPool pool) {
@@ -1251,13 +1251,7 @@ __global__ void __launch_bounds__(256, 4)
     }
     ok = __syncthreads_and(ok);
     float acc = 0.f;
-    float rv[kEstChunk];                           // the cell's residual if it is an unknown, else 0
-    bool uk[kEstChunk];                            // the cell is an unknown of the grid
-#pragma unroll
-    for (int m = 0; m < kEstChunk; ++m) {
-        rv[m] = 0.f;
-        uk[m] = false;
-    }
+    unsigned umask = 0;                            // bit m: plane m's cell is an unknown of the grid
     const int i = i0 + tx, j = j0 + ty;
     if (ok && i <= d.nx && j <= d.ny) {
         const int ke = min(kb + kEstChunk, d.nz + 1);
@@ -1280,15 +1274,18 @@ __global__ void __launch_bounds__(256, 4)
             const float res = sR[m][ty][tx] - s;
             if (rout) rout[c0 + m * pl] = res;
             acc += res * res;
-            rv[m] = res;
-            uk[m] = true;
+            if constexpr (S > 0) {
+                sR[m][ty][tx] = res;       // no other thread reads this entry
+                umask |= 1u << m;
+            }
         }
     }
     double x[S > 0 ? 3 : 1];
     x[0] = (double)acc;
     if constexpr (S > 0) {
-        // the residual and the mask of the block's cells over r's and the
-        // flags' tiles (each thread overwrites only the entries it read);
+        // the residual (stored above) and the mask of the block's cells over
+        // r's and the flags' tiles (each thread writes only the entries it
+        // read; six CTAs per SM, as many as the plain estimate's registers give);
         // then the pooling kernel's sums in its order: per cube, for each of
         // SZ z-offsets p and S rows q, the cells of planes p, p + SZ, ... of
         // row q along x (into the d tile, read by no one any more), then
@@ -1299,8 +1296,9 @@ __global__ void __launch_bounds__(256, 4)
         static_assert(2 * NPART <= (int)(sizeof(sD) / sizeof(float)) && NCUBE <= 256, "pooling scratch");
 #pragma unroll
         for (int m = 0; m < kEstChunk; ++m) {
-            sR[m][ty][tx] = rv[m];
-            sF[m][ty][tx + 4] = uk[m] ? 1 : 0;
+            const bool u = (umask >> m) & 1u;
+            if (!u) sR[m][ty][tx] = 0.f;
+            sF[m][ty][tx + 4] = u ? 1 : 0;
         }
         __syncthreads();
         float* partr = &sD[0][0][0];
